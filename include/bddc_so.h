@@ -1,0 +1,176 @@
+/*
+ * bddc_so.h -- C ABI of the GB300 (sm_103a) BDDC-SO library.
+ *
+ * BDDC-SO (Badia, Martin, Nguyen, "Balancing domain decomposition by
+ * constraints associated with subobjects", arXiv 2001.07289) as the
+ * preconditioner of PCG for Q1 finite-element diffusion
+ *     -div(alpha grad u) = f on [0, nx h] x [0, ny h] x [0, nz h],
+ *     u = 0 on the whole boundary
+ * (Section 2, eq. weakform; Remark 1 for the per-element alpha; Section 5 for
+ * the unit cube, f and the PCG stopping rule).
+ *
+ * Conventions shared by every entry point:
+ *   - Node vectors are FP64 arrays of (nx+1)*(ny+1)*(nz+1) entries, node
+ *     (i, j, k) at i + (nx+1)*(j + (ny+1)*k).  Entries on the Dirichlet
+ *     boundary are ignored on input and written as 0 on output.
+ *   - alpha is an FP64 array of nx*ny*nz entries, element (i, j, k) at
+ *     i + nx*(j + ny*k), every entry finite and > 0.
+ *   - Pointers named *_dev are device memory owned by the caller and must stay
+ *     valid until the work queued on `stream` has finished; *_host pointers
+ *     are ordinary host memory.  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work is queued on it in order; entry points that
+ *     return values to the host (pcg_solve, bddc_setup) synchronise it.
+ *   - Every entry point returns 0 (BDDC_OK) or a negative BDDC_ERR_* code and
+ *     never throws; bddc_last_error() gives a message for the last failure on
+ *     a handle.  After BDDC_ERR_CUDA the handle should be destroyed.
+ *   - One GPU: the device current when bddc_setup is called is used for the
+ *     handle's whole life.  A handle is not thread-safe.
+ */
+#ifndef BDDC_SO_H
+#define BDDC_SO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BDDC_OK = 0,
+    BDDC_ERR_ARG = -1,        /* invalid sizes, cuts, L, options or alpha      */
+    BDDC_ERR_NOT_SPD = -2,    /* non-positive pivot in a local or coarse factor */
+    BDDC_ERR_NOCONV = -3,     /* PCG reached maxit before the tolerance         */
+    BDDC_ERR_BREAKDOWN = -4,  /* PCG: p^T A p <= 0 or not finite                */
+    BDDC_ERR_CUDA = -5,       /* a CUDA runtime call failed                     */
+    BDDC_ERR_OOM = -6,        /* device allocation failed                       */
+    BDDC_ERR_TIMEOUT = -7,    /* a bounded device wait gave up                  */
+    BDDC_ERR_UNSUPPORTED = -8 /* valid request this build does not implement    */
+};
+
+enum { BDDC_FP64 = 0, BDDC_MIXED = 1 };      /* precision of the local solves   */
+enum { BDDC_W_CARD = 0, BDDC_W_RHO = 1 };    /* eq. (W) / Remark 1 weighting     */
+enum { BDDC_SEL_VEF = 0 };                   /* coarse objects: all of Theta-hat on Gamma */
+
+typedef struct bddc_handle bddc_handle;
+
+/* Structured mesh: nx*ny*nz cubes of side h (h <= 0 means h = 1/nx). */
+typedef struct {
+    int nx, ny, nz;
+    double h;
+} bddc_mesh;
+
+/* Box partition Theta (Section 3): on axis d the subdomains are the slabs
+ * between the ncut[d] interior cut planes cut[d][0] < ... (element indices in
+ * (0, n_d)).  cut[d] is a host array; ncut[d] = 0 means one slab. */
+typedef struct {
+    int ncut[3];
+    const int* cut[3];
+} bddc_partition;
+
+/* Options.  L_elems is the sub-object size L/h >= 1: every subdomain side of
+ * w elements is split into ceil(w/L) pieces with boundaries floor(k w / s)
+ * (Section 3: the sub-partition Theta-hat of characteristic size L). */
+typedef struct {
+    int precision;  /* BDDC_FP64 or BDDC_MIXED (FP32 local factors/solves, FP64 rest) */
+    int weights;    /* BDDC_W_CARD or BDDC_W_RHO                                      */
+    int L_elems;    /* >= 1                                                           */
+    int selection;  /* BDDC_SEL_VEF                                                   */
+    int use_graph;  /* capture each PCG iteration in a CUDA graph (0/1)               */
+    int maxit;      /* PCG iteration limit (<= 0: 2000)                               */
+} bddc_options;
+
+/* Per-solve statistics.  alphas/betas: optional host arrays of `capacity`
+ * entries that receive the CG coefficients (for Lanczos estimates). */
+typedef struct {
+    int iterations;      /* operator applications after the initial residual */
+    int converged;       /* 1 if ||r||_2 <= rtol ||b||_2                      */
+    double r0_norm;      /* ||b||_2                                           */
+    double r_norm;       /* final ||r||_2                                     */
+    double* alphas;      /* in: host buffer or NULL; out: alpha_0..            */
+    double* betas;       /* in: host buffer or NULL; out: beta_0..             */
+    int capacity;        /* entries available in alphas/betas                 */
+    double solve_ms;     /* device time of the solve (CUDA events)            */
+} bddc_stats;
+
+/* Sizes of a set-up preconditioner. */
+typedef struct {
+    int n_sub;            /* subdomains                                        */
+    int n_coarse;         /* global coarse DOFs (objects carrying constraints) */
+    int n_vertices;       /* of which point values                             */
+    int max_local_coarse; /* largest n_c,i                                     */
+    long long n_free;     /* non-Dirichlet nodes                               */
+    long long bytes;      /* device memory held by the handle                  */
+    long long factor_bytes;  /* local factors + Phi + coarse factor            */
+    double setup_ms;      /* device time of bddc_setup (CUDA events)          */
+} bddc_info_t;
+
+/* Builds the BDDC-SO preconditioner (Section 3; Definition 1 with V1 = U_I,
+ * Q1 = I, V2 = W-tilde, Q2 = (I - P)E): sub-partition and (sub)object
+ * classification, weights of eq. (W) or Remark 1, local Dirichlet and
+ * constrained Neumann factorisations, coarse basis Phi_i, coarse matrix and
+ * its FP64 Cholesky factor.  Coarse objects are the vertices, edges and faces
+ * of Theta-hat on Gamma; a vertex is a point value, an edge or face the mean
+ * over its nodes.  alpha_dev is read during the call only.  On success *out
+ * receives a new handle.  Errors: BDDC_ERR_ARG (bad sizes/cuts/L/options,
+ * alpha <= 0 or not finite), BDDC_ERR_NOT_SPD, BDDC_ERR_OOM, BDDC_ERR_CUDA. */
+int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part,
+               const bddc_options* opt, const double* alpha_dev, void* stream,
+               bddc_handle** out);
+
+/* z = B r (Definition 1, Section 3): interior correction, weighted restriction
+ * of the interface residual, coarse solve, constrained Neumann solves,
+ * weighted injection E and discrete harmonic extension (I - P).  r_dev, z_dev:
+ * node vectors (must not alias). */
+int bddc_apply(bddc_handle* h, const double* r_dev, double* z_dev, void* stream);
+
+/* y = A x, the matrix-free Dirichlet Q1 operator (Section 2 with Remark 1's
+ * alpha).  x_dev, y_dev: node vectors (must not alias). */
+int bddc_operator(bddc_handle* h, const double* x_dev, double* y_dev, void* stream);
+
+/* PCG with preconditioner B from x0 = 0, stopped when ||r||_2 <= rtol ||b||_2
+ * (Section 5: reduction of the residual 2-norm).  x_dev receives the iterate;
+ * stats (may be NULL) the counts and coefficients.  Returns BDDC_OK,
+ * BDDC_ERR_NOCONV (x holds the last iterate) or BDDC_ERR_BREAKDOWN. */
+int pcg_solve(bddc_handle* h, const double* b_dev, double* x_dev, double rtol,
+              bddc_stats* stats, void* stream);
+
+/* g_e = -h lambda_e^T K u_e per element: the derivative of J(u(alpha)) with
+ * respect to alpha_e when A lambda = dJ/du (A is linear in alpha_e, Remark 1).
+ * u_dev, lambda_dev: node vectors; g_dev: nx*ny*nz entries. */
+int bddc_gradient(bddc_handle* h, const double* u_dev, const double* lambda_dev,
+                  double* g_dev, void* stream);
+
+/* The whole job from host memory: copies alpha and b to the device, runs
+ * bddc_setup and pcg_solve, copies x back and frees everything it allocated.
+ * For callers without device buffers and for end-to-end timing. */
+int bddc_solve_host(const bddc_mesh* mesh, const bddc_partition* part,
+                    const bddc_options* opt, const double* alpha_host,
+                    const double* b_host, double* x_host, double rtol,
+                    bddc_stats* stats);
+
+/* Sizes and timings of a handle. */
+int bddc_get_info(const bddc_handle* h, bddc_info_t* info);
+
+/* Copies the coarse basis of subdomain `sub` restricted to the subdomain's
+ * box-surface nodes into phi_host (n_surface x n_c,i, row-major, FP64), the
+ * global coarse numbers of its columns into gid_host and the box-surface node
+ * ids into node_host; pass NULL buffers to query n_surface and n_c,i only.
+ * Diagnostic access for tests. */
+int bddc_get_coarse_basis(const bddc_handle* h, int sub, double* phi_host,
+                          int* gid_host, long long* node_host,
+                          int* n_surface, int* n_local_coarse);
+
+/* Copies the assembled coarse matrix A_c (n_coarse^2, row-major, FP64, before
+ * factorisation) to host memory; BDDC_ERR_UNSUPPORTED if it was not kept. */
+int bddc_get_coarse_matrix(const bddc_handle* h, double* ac_host);
+
+/* Frees every device and host resource of the handle (NULL is a no-op). */
+int bddc_destroy(bddc_handle* h);
+
+/* Message for the last error on the handle (or the last failed bddc_setup
+ * when h is NULL).  Owned by the library. */
+const char* bddc_last_error(const bddc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDDC_SO_H */

@@ -83,6 +83,8 @@ def classify(nx: int, ny: int, nz: int, sub: np.ndarray, piece: np.ndarray) -> O
     bnd = fem.boundary_node_mask(nx, ny, nz)
     on_gamma = (nsub >= 2) & ~bnd
     gamma = np.flatnonzero(on_gamma)
+    if len(gamma) == 0:                      # one subdomain: no interface, no objects
+        return Objects([], np.zeros(0, dtype=np.int64), [], [], gamma, node_subs, node_pieces)
     # key id per Gamma node
     _, key_id = np.unique(node_pieces[gamma], axis=0, return_inverse=True)
     key_full = np.full(nn, -1, dtype=np.int64)

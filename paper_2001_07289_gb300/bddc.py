@@ -1,0 +1,253 @@
+"""Thin Python binding of the BDDC-SO C ABI (include/bddc_so.h).
+
+Argument marshalling only: every step of setup, apply, PCG and gradient runs
+in the CUDA library.  Vectors are torch float64 CUDA tensors in the node-grid
+layout; the library is loaded from the in-tree build and importing this
+module fails loudly when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbddc_so.so")
+
+BDDC_OK, BDDC_ERR_ARG, BDDC_ERR_NOT_SPD, BDDC_ERR_NOCONV = 0, -1, -2, -3
+BDDC_ERR_BREAKDOWN, BDDC_ERR_CUDA, BDDC_ERR_OOM, BDDC_ERR_TIMEOUT, BDDC_ERR_UNSUPPORTED = -4, -5, -6, -7, -8
+BDDC_FP64, BDDC_MIXED = 0, 1
+BDDC_W_CARD, BDDC_W_RHO = 0, 1
+BDDC_SEL_VEF = 0
+
+
+class BddcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double)]
+
+
+class Partition(C.Structure):
+    _fields_ = [("ncut", C.c_int * 3), ("cut", C.POINTER(C.c_int) * 3)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("weights", C.c_int), ("L_elems", C.c_int),
+                ("selection", C.c_int), ("use_graph", C.c_int), ("maxit", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("r0_norm", C.c_double),
+                ("r_norm", C.c_double), ("alphas", C.POINTER(C.c_double)),
+                ("betas", C.POINTER(C.c_double)), ("capacity", C.c_int), ("solve_ms", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_sub", C.c_int), ("n_coarse", C.c_int), ("n_vertices", C.c_int),
+                ("max_local_coarse", C.c_int), ("n_free", C.c_longlong), ("bytes", C.c_longlong),
+                ("factor_bytes", C.c_longlong), ("setup_ms", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"BDDC-SO CUDA library not built: {LIB_PATH} is missing "
+                          "(run __graft_entry__.build())")
+    lib = C.CDLL(LIB_PATH)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    lib.bddc_setup.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), vp, vp,
+                               C.POINTER(vp)]
+    lib.bddc_apply.argtypes = [vp, vp, vp, vp]
+    lib.bddc_operator.argtypes = [vp, vp, vp, vp]
+    lib.pcg_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(Stats), vp]
+    lib.bddc_gradient.argtypes = [vp, vp, vp, vp, vp]
+    lib.bddc_solve_host.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), dp, dp, dp,
+                                    C.c_double, C.POINTER(Stats)]
+    lib.bddc_get_info.argtypes = [vp, C.POINTER(Info)]
+    lib.bddc_get_coarse_basis.argtypes = [vp, ip, dp, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                          C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.bddc_get_coarse_matrix.argtypes = [vp, dp]
+    lib.bddc_destroy.argtypes = [vp]
+    lib.bddc_last_error.argtypes = [vp]
+    lib.bddc_last_error.restype = C.c_char_p
+    for f in ("bddc_setup", "bddc_apply", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
+              "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy"):
+        getattr(lib, f).restype = C.c_int
+    return lib
+
+
+lib = _load()
+
+EXPORTS = ("bddc_setup", "bddc_apply", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
+           "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
+           "bddc_last_error")
+
+
+def _check(code: int, handle=None):
+    if code != BDDC_OK:
+        msg = lib.bddc_last_error(handle)
+        raise BddcError(code, msg.decode() if msg else "")
+
+
+def _ptr(t: torch.Tensor) -> C.c_void_p:
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream() -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph):
+    mesh = Mesh(nx, ny, nz, h)
+    part = Partition()
+    keep = []
+    for d in range(3):
+        arr = (C.c_int * max(1, len(cuts[d])))(*cuts[d])
+        keep.append(arr)
+        part.ncut[d] = len(cuts[d])
+        part.cut[d] = C.cast(arr, C.POINTER(C.c_int))
+    prec = {"fp64": BDDC_FP64, "mixed": BDDC_MIXED}[precision] if isinstance(precision, str) else precision
+    wts = {"card": BDDC_W_CARD, "rho": BDDC_W_RHO}[weights] if isinstance(weights, str) else weights
+    opt = Options(prec, wts, L, BDDC_SEL_VEF, int(use_graph), maxit)
+    return mesh, part, opt, keep
+
+
+class BDDC:
+    """A set-up BDDC-SO preconditioner (bddc_setup) and its operations."""
+
+    def __init__(self, nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int,
+                 alpha: torch.Tensor, h: float = 0.0, precision="fp64", weights="card",
+                 maxit: int = 2000, use_graph: bool = False):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.h = h if h > 0 else 1.0 / nx
+        self.n_nodes = (nx + 1) * (ny + 1) * (nz + 1)
+        self.maxit = maxit
+        mesh, part, opt, keep = _structs(nx, ny, nz, self.h, cuts, L, precision, weights, maxit, use_graph)
+        self._handle = C.c_void_p()
+        _check(lib.bddc_setup(C.byref(mesh), C.byref(part), C.byref(opt), _ptr(alpha), _stream(),
+                              C.byref(self._handle)), None)
+
+    @classmethod
+    def from_problem(cls, p, alpha: Optional[torch.Tensor] = None, **kw):
+        a = alpha if alpha is not None else torch.from_numpy(p.alpha).cuda()
+        kw.setdefault("precision", p.precision)
+        kw.setdefault("weights", p.weights)
+        return cls(p.nx, p.ny, p.nz, p.cuts, p.L, a, h=p.h, **kw)
+
+    def _vec(self):
+        return torch.empty(self.n_nodes, dtype=torch.float64, device="cuda")
+
+    def apply(self, r: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        z = out if out is not None else self._vec()
+        _check(lib.bddc_apply(self._handle, _ptr(r), _ptr(z), _stream()), self._handle)
+        return z
+
+    def operator(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        y = out if out is not None else self._vec()
+        _check(lib.bddc_operator(self._handle, _ptr(x), _ptr(y), _stream()), self._handle)
+        return y
+
+    def solve(self, b: torch.Tensor, rtol: float, out: Optional[torch.Tensor] = None, raise_on_noconv=True):
+        x = out if out is not None else self._vec()
+        cap = self.maxit
+        al = (C.c_double * cap)()
+        be = (C.c_double * cap)()
+        st = Stats(0, 0, 0.0, 0.0, C.cast(al, C.POINTER(C.c_double)), C.cast(be, C.POINTER(C.c_double)), cap, 0.0)
+        code = lib.pcg_solve(self._handle, _ptr(b), _ptr(x), rtol, C.byref(st), _stream())
+        if code != BDDC_OK and (raise_on_noconv or code != BDDC_ERR_NOCONV):
+            _check(code, self._handle)
+        it = st.iterations
+        stats = dict(iterations=it, converged=bool(st.converged), r0_norm=st.r0_norm, r_norm=st.r_norm,
+                     alphas=np.array(al[:it]), betas=np.array(be[:max(it - 1, 0)]), solve_ms=st.solve_ms,
+                     status=code)
+        return x, stats
+
+    def gradient(self, u: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        g = out if out is not None else torch.empty(self.nx * self.ny * self.nz, dtype=torch.float64,
+                                                   device="cuda")
+        _check(lib.bddc_gradient(self._handle, _ptr(u), _ptr(lam), _ptr(g), _stream()), self._handle)
+        return g
+
+    def info(self) -> dict:
+        i = Info()
+        _check(lib.bddc_get_info(self._handle, C.byref(i)), self._handle)
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def coarse_basis(self, sub: int):
+        nb, nc = C.c_int(), C.c_int()
+        _check(lib.bddc_get_coarse_basis(self._handle, sub, None, None, None, C.byref(nb), C.byref(nc)),
+               self._handle)
+        phi = np.zeros((nb.value, nc.value))
+        gid = np.zeros(nc.value, dtype=np.int32)
+        node = np.zeros(nb.value, dtype=np.int64)
+        _check(lib.bddc_get_coarse_basis(self._handle, sub, phi.ctypes.data_as(C.POINTER(C.c_double)),
+                                         gid.ctypes.data_as(C.POINTER(C.c_int)),
+                                         node.ctypes.data_as(C.POINTER(C.c_longlong)), None, None),
+               self._handle)
+        return phi, gid, node
+
+    def coarse_matrix(self) -> np.ndarray:
+        n = self.info()["n_coarse"]
+        a = np.zeros((n, n))
+        _check(lib.bddc_get_coarse_matrix(self._handle, a.ctypes.data_as(C.POINTER(C.c_double))), self._handle)
+        return a
+
+    def close(self):
+        if self._handle:
+            lib.bddc_destroy(self._handle)
+            self._handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_host(nx, ny, nz, cuts, L, alpha: np.ndarray, b: np.ndarray, rtol: float, h: float = 0.0,
+               precision="fp64", weights="card", maxit: int = 2000):
+    """bddc_solve_host: setup + PCG from host arrays, result in a host array."""
+    h = h if h > 0 else 1.0 / nx
+    mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, False)
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    bb = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(bb)
+    st = Stats(0, 0, 0.0, 0.0, None, None, 0, 0.0)
+    code = lib.bddc_solve_host(C.byref(mesh), C.byref(part), C.byref(opt),
+                               a.ctypes.data_as(C.POINTER(C.c_double)), bb.ctypes.data_as(C.POINTER(C.c_double)),
+                               x.ctypes.data_as(C.POINTER(C.c_double)), rtol, C.byref(st))
+    _check(code, None)
+    return x, dict(iterations=st.iterations, converged=bool(st.converged), r_norm=st.r_norm,
+                   r0_norm=st.r0_norm, solve_ms=st.solve_ms)
+
+
+class BddcSolve(torch.autograd.Function):
+    """u = A(alpha)^{-1} b by BDDC-SO PCG.  Backward: the adjoint solve
+    A lambda = dJ/du with the same set-up preconditioner (A is symmetric),
+    dJ/dalpha_e = -h lambda_e^T K u_e (bddc_gradient) and dJ/db = lambda.
+    Only u is kept from the forward pass."""
+
+    @staticmethod
+    def forward(ctx, alpha, b, problem, rtol):
+        pre = BDDC.from_problem(problem, alpha=alpha.detach().contiguous())
+        u, stats = pre.solve(b.detach().contiguous(), rtol)
+        ctx.pre, ctx.rtol = pre, rtol
+        ctx.save_for_backward(u)
+        ctx.stats = stats
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (u,) = ctx.saved_tensors
+        lam, _ = ctx.pre.solve(grad_u.contiguous(), ctx.rtol, raise_on_noconv=False)
+        g = ctx.pre.gradient(u, lam)
+        ctx.pre.close()
+        return g, lam, None, None

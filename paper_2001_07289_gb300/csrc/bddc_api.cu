@@ -1,0 +1,790 @@
+// C ABI of the BDDC-SO library (include/bddc_so.h): host-side metadata of the
+// partition and the sub-partition, buffer layout, and the sequencing of the
+// device kernels for setup, preconditioner apply, operator, PCG and gradient.
+//
+// Metadata (Section 3, the remark on local subdivision): on every axis the
+// Theta cut planes split the elements into slabs and each slab of width w is
+// cut into s = ceil(w/L) pieces at floor(k w / s).  The piece boundaries on an
+// axis ("points") and the open intervals between them ("items") make every
+// node a tuple of per-axis items; a DOF's set of containing sub-subdomains is
+// determined by that tuple, so the (sub)objects are exactly the tuples that
+// lie on Gamma (some item is a Theta plane), avoid the Dirichlet boundary and
+// hold at least one node.  A vertex is a tuple of three points (a point
+// value); edges and faces carry the mean over their nodes.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "bddc_so.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace bddc;
+
+namespace {
+
+struct BddcError : std::runtime_error {
+  int code;
+  BddcError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      throw BddcError(e_ == cudaErrorMemoryAllocation ? BDDC_ERR_OOM : BDDC_ERR_CUDA,              \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+  } while (0)
+
+thread_local std::string g_setup_error;
+
+struct AxisHost {
+  int n = 0;
+  std::vector<int> cuts, pts;
+  std::vector<int> item, theta, hat;       // per node
+  std::vector<int> slab, piece;            // per element
+  std::vector<int> slab_lo, slab_hi, piece_lo, piece_hi;
+  std::vector<int> item_lo, item_hi, item_kind;  // kind: 0 interval, 1 piece point, 2 Theta point, 3 boundary
+
+  void build(int n_, const int* c, int nc, int L) {
+    n = n_;
+    cuts.assign(c, c + nc);
+    for (int i = 0; i < nc; ++i)
+      if (cuts[i] <= 0 || cuts[i] >= n || (i > 0 && cuts[i] <= cuts[i - 1]))
+        throw BddcError(BDDC_ERR_ARG, "cut planes must be strictly increasing inside (0, n)");
+    std::vector<int> b;
+    b.push_back(0);
+    for (int v : cuts) b.push_back(v);
+    b.push_back(n);
+    slab.assign(n, 0);
+    piece.assign(n, 0);
+    pts.clear();
+    pts.push_back(0);
+    int p = 0;
+    for (size_t s = 0; s + 1 < b.size(); ++s) {
+      int lo = b[s], hi = b[s + 1], w = hi - lo;
+      int sN = std::max(1, (w + L - 1) / L);
+      slab_lo.push_back(lo);
+      slab_hi.push_back(hi);
+      std::vector<int> bd;
+      bd.push_back(lo);
+      for (int k = 1; k < sN; ++k) bd.push_back(lo + (int)(((long long)k * w) / sN));
+      bd.push_back(hi);
+      for (size_t q = 0; q + 1 < bd.size(); ++q) {
+        piece_lo.push_back(bd[q]);
+        piece_hi.push_back(bd[q + 1]);
+        for (int e = bd[q]; e < bd[q + 1]; ++e) { slab[e] = (int)s; piece[e] = p; }
+        ++p;
+        pts.push_back(bd[q + 1]);
+      }
+    }
+    // pts now holds every piece boundary once, increasing (0 .. n)
+    item.assign(n + 1, 0);
+    theta.assign(n + 1, 0);
+    hat.assign(n + 1, 0);
+    const int np = (int)pts.size();
+    item_lo.assign(2 * np - 1, 0);
+    item_hi.assign(2 * np - 1, 0);
+    item_kind.assign(2 * np - 1, 0);
+    for (int j = 0; j < np; ++j) {
+      int t = pts[j];
+      item[t] = 2 * j;
+      hat[t] = 1;
+      bool is_cut = std::binary_search(cuts.begin(), cuts.end(), t);
+      theta[t] = is_cut ? 1 : 0;
+      item_lo[2 * j] = item_hi[2 * j] = t;
+      item_kind[2 * j] = (t == 0 || t == n) ? 3 : (is_cut ? 2 : 1);
+      if (j + 1 < np) {
+        item_lo[2 * j + 1] = t + 1;
+        item_hi[2 * j + 1] = pts[j + 1] - 1;
+        item_kind[2 * j + 1] = 0;
+        for (int u = t + 1; u < pts[j + 1]; ++u) item[u] = 2 * j + 1;
+      }
+    }
+  }
+  int nitem() const { return (int)item_kind.size(); }
+  bool empty(int it) const { return item_lo[it] > item_hi[it]; }
+};
+
+}  // namespace
+
+struct bddc_handle {
+  int device = 0;
+  bddc_mesh mesh{};
+  bddc_options opt{};
+  int local_double = 1;
+  AxisHost ax[3];
+  std::vector<SubDesc> subs;
+  std::vector<LocalCoarse> lc;
+  int n_coarse = 0, n_vertices = 0, max_nc = 0;
+  long long n_nodes = 0, n_free = 0;
+  LocalLaunch L{};
+  MeshDev m{};
+  // device buffers
+  std::vector<void*> allocs;
+  size_t bytes = 0, factor_bytes = 0;
+  double* alpha = nullptr;       // private copy of alpha
+  double *Acg = nullptr, *Ac_copy = nullptr, *dinv = nullptr, *cscratch = nullptr;
+  int *cptr = nullptr, *color_subs = nullptr;
+  int2* cent = nullptr;
+  int color_count[8] = {0}, color_off[8] = {0};
+  double *rc = nullptr, *cy = nullptr, *uc = nullptr;
+  double *uI = nullptr, *t = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *partial = nullptr, *scal = nullptr, *hist_a = nullptr, *hist_b = nullptr;
+  int* flag = nullptr;
+  int* err = nullptr;
+  double* pinned = nullptr;
+  int hist_cap = 0;
+  float setup_ms = 0.f;
+  std::vector<void*> setup_only;
+  std::vector<int> h_cptr, h_clist;   // coarse DOF -> owners (CSR), colour lists
+  std::vector<int2> h_cent;
+  std::string error;
+
+  void* dalloc(size_t b, bool setup_tmp = false) {
+    void* ptr = nullptr;
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&ptr, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw BddcError(BDDC_ERR_OOM, "cudaMalloc of " + std::to_string(b) + " bytes failed");
+    }
+    (setup_tmp ? setup_only : allocs).push_back(ptr);
+    if (!setup_tmp) bytes += b;
+    return ptr;
+  }
+  template <typename T> T* dnew(size_t count, bool setup_tmp = false) {
+    return (T*)dalloc(sizeof(T) * count, setup_tmp);
+  }
+  void free_setup_only() {
+    for (void* v : setup_only) cudaFree(v);
+    setup_only.clear();
+  }
+  ~bddc_handle() {
+    free_setup_only();
+    for (void* v : allocs) cudaFree(v);
+    if (pinned) cudaFreeHost(pinned);
+  }
+};
+
+namespace {
+
+template <typename T>
+T* upload(bddc_handle* h, const std::vector<T>& v, cudaStream_t st) {
+  T* d = h->dnew<T>(std::max<size_t>(v.size(), 1));
+  if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  return d;
+}
+
+void build_metadata(bddc_handle* h) {
+  int nsub[3], nit[3];
+  for (int d = 0; d < 3; ++d) {
+    nsub[d] = (int)h->ax[d].slab_lo.size();
+    nit[d] = h->ax[d].nitem();
+  }
+  // global objects: tuples of items on Gamma, off the Dirichlet boundary, non-empty
+  const long long nt = (long long)nit[0] * nit[1] * nit[2];
+  std::vector<int> objid(nt, -1);
+  auto valid = [&](int ix, int iy, int iz) {
+    int it[3] = {ix, iy, iz};
+    bool on_gamma = false;
+    for (int d = 0; d < 3; ++d) {
+      int k = h->ax[d].item_kind[it[d]];
+      if (k == 3 || h->ax[d].empty(it[d])) return false;
+      if (k == 2) on_gamma = true;
+    }
+    return on_gamma;
+  };
+  int nc = 0, nvert = 0;
+  for (int iz = 0; iz < nit[2]; ++iz)
+    for (int iy = 0; iy < nit[1]; ++iy)
+      for (int ix = 0; ix < nit[0]; ++ix)
+        if (valid(ix, iy, iz)) {
+          objid[ix + (long long)nit[0] * (iy + (long long)nit[1] * iz)] = nc++;
+          if (!(ix & 1) && !(iy & 1) && !(iz & 1)) ++nvert;
+        }
+  h->n_coarse = nc;
+  h->n_vertices = nvert;
+  // subdomains
+  const int S = nsub[0] * nsub[1] * nsub[2];
+  h->subs.assign(S, SubDesc{});
+  h->lc.clear();
+  std::vector<std::vector<int2>> owners(nc);
+  long long offD = 0, offN = 0, offW = 0, offY = 0, offG = 0, offL = 0, offPA = 0, offSc = 0, offAc = 0, offPhi = 0,
+            offB = 0, offVec = 0;
+  LocalLaunch& L = h->L;
+  L.maxQD = L.maxNzD = L.maxND = L.maxQN = L.maxNzN = L.maxNN = L.maxNB = L.maxNc = 0;
+  for (int sz = 0; sz < nsub[2]; ++sz)
+    for (int sy = 0; sy < nsub[1]; ++sy)
+      for (int sx = 0; sx < nsub[0]; ++sx) {
+        const int si = sx + nsub[0] * (sy + nsub[1] * sz);
+        SubDesc& s = h->subs[si];
+        const int sl[3] = {sx, sy, sz};
+        int ilo[3], ihi[3];
+        for (int d = 0; d < 3; ++d) {
+          s.e0[d] = h->ax[d].slab_lo[sl[d]];
+          s.w[d] = h->ax[d].slab_hi[sl[d]] - s.e0[d];
+          ilo[d] = h->ax[d].item[s.e0[d]];
+          ihi[d] = h->ax[d].item[s.e0[d] + s.w[d]];
+        }
+        s.color = (sx & 1) + 2 * (sy & 1) + 4 * (sz & 1);
+        const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+        // local coarse DOFs: vertices first, then averages, each lexicographic
+        std::vector<LocalCoarse> verts, avgs;
+        for (int iz = ilo[2]; iz <= ihi[2]; ++iz)
+          for (int iy = ilo[1]; iy <= ihi[1]; ++iy)
+            for (int ix = ilo[0]; ix <= ihi[0]; ++ix) {
+              int g = objid[ix + (long long)nit[0] * (iy + (long long)nit[1] * iz)];
+              if (g < 0) continue;
+              LocalCoarse c;
+              c.gid = g;
+              int it[3] = {ix, iy, iz};
+              int cnt = 1;
+              for (int d = 0; d < 3; ++d) {
+                c.lo[d] = (short)(h->ax[d].item_lo[it[d]] - s.e0[d]);
+                c.hi[d] = (short)(h->ax[d].item_hi[it[d]] - s.e0[d]);
+                cnt *= (c.hi[d] - c.lo[d] + 1);
+              }
+              c.count = cnt;
+              bool vert = !(ix & 1) && !(iy & 1) && !(iz & 1);
+              (vert ? verts : avgs).push_back(c);
+            }
+        s.nv = (int)verts.size();
+        s.na = (int)avgs.size();
+        s.nc = s.nv + s.na;
+        s.cofs = (int)h->lc.size();
+        for (auto& c : verts) h->lc.push_back(c);
+        for (auto& c : avgs) h->lc.push_back(c);
+        for (int j = 0; j < s.nc; ++j) owners[h->lc[s.cofs + j].gid].push_back(make_int2(si, s.cofs + j));
+        s.nB = surf_count(px, py, pz);
+        const int QN = px * py, NN = QN * pz;
+        const int qx = s.w[0] - 1, qy = s.w[1] - 1, qz = s.w[2] - 1;
+        const bool hasI = qx > 0 && qy > 0 && qz > 0;
+        const int QD = hasI ? qx * qy : 0, nzD = hasI ? qz : 0;
+        s.offD = offD; offD += hasI ? (long long)(2 * nzD - 1) * QD * QD : 0;
+        s.offN = offN; offN += (long long)(2 * pz - 1) * QN * QN;
+        s.offW = offW; offW += 2LL * QN * QN + 1024LL * ((std::max(QN, s.na) + 31) / 32);
+        s.offY = offY; offY += (long long)NN * s.nc;
+        s.offG = offG; offG += (long long)s.na * s.nc;
+        s.offL = offL; offL += (long long)s.na * s.nv;
+        s.offPA = offPA; offPA += (long long)NN * s.na;
+        s.offSc = offSc; offSc += (long long)s.na * s.na;
+        s.offAc = offAc; offAc += (long long)s.nc * s.nc;
+        s.offPhi = offPhi; offPhi += (long long)s.nB * s.nc;
+        s.offB = offB; offB += s.nB;
+        s.offVec = offVec; offVec += NN;
+        L.maxQD = std::max(L.maxQD, QD); L.maxNzD = std::max(L.maxNzD, nzD); L.maxND = std::max(L.maxND, QD * nzD);
+        L.maxQN = std::max(L.maxQN, QN); L.maxNzN = std::max(L.maxNzN, pz); L.maxNN = std::max(L.maxNN, NN);
+        L.maxNB = std::max(L.maxNB, s.nB); L.maxNc = std::max(L.maxNc, s.nc);
+        h->max_nc = std::max(h->max_nc, s.nc);
+      }
+  L.nsub = S;
+  h->L.mscratch_stride = (long long)L.maxQN * CW;
+  // coarse owners CSR
+  std::vector<int> ptr(nc + 1, 0);
+  std::vector<int2> ent;
+  for (int g = 0; g < nc; ++g) {
+    std::sort(owners[g].begin(), owners[g].end(), [](int2 a, int2 b) { return a.x < b.x; });
+    ptr[g + 1] = ptr[g] + (int)owners[g].size();
+    for (auto e : owners[g]) ent.push_back(e);
+  }
+  // colour lists
+  std::vector<int> clist;
+  for (int c = 0; c < 8; ++c) {
+    h->color_off[c] = (int)clist.size();
+    for (int si = 0; si < S; ++si)
+      if (h->subs[si].color == c) clist.push_back(si);
+    h->color_count[c] = (int)clist.size() - h->color_off[c];
+  }
+  h->h_cptr = std::move(ptr);
+  h->h_cent = std::move(ent);
+  h->h_clist = std::move(clist);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Layout {
+  long long D, N, W, Y, G, L, PA, Sc, Ac, Phi, B, Vec;
+};
+
+Layout layout_of(const bddc_handle* h) {
+  Layout o{};
+  for (const SubDesc& s : h->subs) {
+    const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+    const int QN = px * py, NN = QN * pz;
+    const int qx = s.w[0] - 1, qy = s.w[1] - 1, qz = s.w[2] - 1;
+    const bool hasI = qx > 0 && qy > 0 && qz > 0;
+    const int QD = hasI ? qx * qy : 0;
+    o.D = std::max(o.D, s.offD + (hasI ? (long long)(2 * qz - 1) * QD * QD : 0));
+    o.N = std::max(o.N, s.offN + (long long)(2 * pz - 1) * QN * QN);
+    o.W = std::max(o.W, s.offW + 2LL * QN * QN + 1024LL * ((std::max(QN, s.na) + 31) / 32));
+    o.Y = std::max(o.Y, s.offY + (long long)NN * s.nc);
+    o.G = std::max(o.G, s.offG + (long long)s.na * s.nc);
+    o.L = std::max(o.L, s.offL + (long long)s.na * s.nv);
+    o.PA = std::max(o.PA, s.offPA + (long long)NN * s.na);
+    o.Sc = std::max(o.Sc, s.offSc + (long long)s.na * s.na);
+    o.Ac = std::max(o.Ac, s.offAc + (long long)s.nc * s.nc);
+    o.Phi = std::max(o.Phi, s.offPhi + (long long)s.nB * s.nc);
+    o.B = std::max(o.B, s.offB + s.nB);
+    o.Vec = std::max(o.Vec, s.offVec + NN);
+  }
+  return o;
+}
+
+void check_err_flags(bddc_handle* h, cudaStream_t st) {
+  int e[2] = {0, -1};
+  CK(cudaMemcpyAsync(e, h->err, sizeof(e), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (e[0] == 0) return;
+  const char* what[] = {"", "alpha must be finite and > 0 (element ", "non-positive pivot in the Dirichlet factor of subdomain ",
+                        "non-positive pivot in the Neumann factor of subdomain ",
+                        "non-positive pivot in S_c of subdomain ", "non-positive pivot in the coarse factor, tile "};
+  std::string msg = std::string(what[std::min(e[0], 5)]) + std::to_string(e[1]) + (e[0] == 1 ? ")" : "");
+  throw BddcError(e[0] == 1 ? BDDC_ERR_ARG : BDDC_ERR_NOT_SPD, msg);
+}
+
+template <typename T>
+void setup_local(bddc_handle* h, cudaStream_t st) {
+  configure_local_kernels<T>();
+  launch_setup_local<T>(h->L, st);
+}
+
+void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
+  const bddc_mesh& M = h->mesh;
+  CK(cudaGetDevice(&h->device));
+  h->n_nodes = (long long)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
+  h->n_free = (long long)(M.nx - 1) * (M.ny - 1) * (M.nz - 1);
+  build_metadata(h);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+  // flags and alpha
+  h->err = h->dnew<int>(2);
+  int init[2] = {0, -1};
+  CK(cudaMemcpyAsync(h->err, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  const long long NE = (long long)M.nx * M.ny * M.nz;
+  h->alpha = h->dnew<double>(NE);
+  CK(cudaMemcpyAsync(h->alpha, alpha_dev, sizeof(double) * NE, cudaMemcpyDeviceToDevice, st));
+  launch_check_alpha(h->alpha, NE, h->err, st);
+  check_err_flags(h, st);
+  // axis tables
+  MeshDev& m = h->m;
+  m.nx = M.nx; m.ny = M.ny; m.nz = M.nz;
+  m.NX = M.nx + 1; m.NY = M.ny + 1; m.NZ = M.nz + 1;
+  m.h = M.h;
+  for (int d = 0; d < 3; ++d) {
+    AxisHost& a = h->ax[d];
+    m.ax[d].item = upload(h, a.item, st);
+    m.ax[d].theta = upload(h, a.theta, st);
+    m.ax[d].hat = upload(h, a.hat, st);
+    m.ax[d].slab = upload(h, a.slab, st);
+    m.ax[d].piece = upload(h, a.piece, st);
+    m.ax[d].slab_lo = upload(h, a.slab_lo, st);
+    m.ax[d].slab_hi = upload(h, a.slab_hi, st);
+    m.ax[d].n = a.n;
+    m.ax[d].nslab = (int)a.slab_lo.size();
+    m.ax[d].nitem = a.nitem();
+    m.nsub[d] = (int)a.slab_lo.size();
+  }
+  const bool dbl = h->local_double;
+  const size_t es = dbl ? sizeof(double) : sizeof(float);
+  Layout lay = layout_of(h);
+  LocalLaunch& L = h->L;
+  L.m = m;
+  L.alpha = h->alpha;
+  L.subs = upload(h, h->subs, st);
+  L.lc = upload(h, h->lc, st);
+  L.facD = h->dalloc(es * lay.D);
+  L.facN = h->dalloc(es * lay.N);
+  L.Phi = h->dalloc(es * lay.Phi);
+  h->factor_bytes = es * (lay.D + lay.N + lay.Phi);
+  L.delta = h->dnew<double>(lay.B);
+  L.vgam = h->dnew<double>(lay.B);
+  L.vloc = h->dalloc(es * lay.Vec);
+  L.rcl = h->dnew<double>(h->lc.size());
+  L.err = h->err;
+  L.scratch = h->dalloc(es * lay.W, true);
+  L.Y = h->dalloc(es * lay.Y, true);
+  L.G = h->dalloc(es * lay.G, true);
+  L.Lv = h->dalloc(es * lay.L, true);
+  L.PA = h->dalloc(es * lay.PA, true);
+  L.Sc = h->dalloc(es * lay.Sc, true);
+  L.Ac = (double*)h->dalloc(sizeof(double) * lay.Ac, true);
+  const int nch = (L.maxNc + CW - 1) / CW;
+  L.mscratch = h->dalloc(es * (size_t)L.nsub * nch * L.mscratch_stride, true);
+  // weights (eq. W or Remark 1)
+  double* pw = nullptr;
+  if (h->opt.weights == BDDC_W_RHO) {
+    std::vector<int> plo, phi;
+    int npc[3];
+    for (int d = 0; d < 3; ++d) {
+      npc[d] = (int)h->ax[d].piece_lo.size();
+      plo.insert(plo.end(), h->ax[d].piece_lo.begin(), h->ax[d].piece_lo.end());
+      phi.insert(phi.end(), h->ax[d].piece_hi.begin(), h->ax[d].piece_hi.end());
+    }
+    int* dplo = upload(h, plo, st);
+    int* dphi = upload(h, phi, st);
+    pw = (double*)h->dalloc(sizeof(double) * (size_t)npc[0] * npc[1] * npc[2], true);
+    launch_piece_alpha(m, h->alpha, dplo, dphi, npc[0], npc[1], npc[2], pw, st);
+  }
+  launch_weights(L, pw, st);
+  // local factorisations and coarse basis
+  if (dbl) setup_local<double>(h, st); else setup_local<float>(h, st);
+  CK(cudaGetLastError());
+  // coarse problem (FP64)
+  const int nc = h->n_coarse;
+  h->cptr = upload(h, h->h_cptr, st);
+  h->cent = upload(h, h->h_cent, st);
+  h->color_subs = upload(h, h->h_clist, st);
+  h->Acg = h->dnew<double>((size_t)nc * nc);
+  h->factor_bytes += sizeof(double) * (size_t)nc * nc;
+  CK(cudaMemsetAsync(h->Acg, 0, sizeof(double) * (size_t)nc * nc, st));
+  launch_coarse_assemble(L, h->color_subs, h->color_count, h->color_off, h->Acg, nc, st);
+  if ((long long)nc * nc <= (1LL << 22)) {
+    h->Ac_copy = h->dnew<double>((size_t)nc * nc);
+    CK(cudaMemcpyAsync(h->Ac_copy, h->Acg, sizeof(double) * (size_t)nc * nc, cudaMemcpyDeviceToDevice, st));
+  }
+  const int ntile = (nc + CNB - 1) / CNB;
+  h->dinv = h->dnew<double>((size_t)ntile * CNB * CNB);
+  h->cscratch = (double*)h->dalloc(sizeof(double) * std::max<size_t>((size_t)ntile * CNB * CNB, 4096), true);
+  configure_coarse_kernels();
+  launch_coarse_factor(h->Acg, nc, h->dinv, h->cscratch, h->err, st);
+  CK(cudaGetLastError());
+  // apply / PCG work vectors
+  const long long N = h->n_nodes;
+  h->rc = h->dnew<double>(std::max(nc, 1));
+  h->cy = h->dnew<double>(std::max(nc, 1));
+  h->uc = h->dnew<double>(std::max(nc, 1));
+  h->uI = h->dnew<double>(N);
+  CK(cudaMemsetAsync(h->uI, 0, sizeof(double) * N, st));
+  h->t = h->dnew<double>(N);
+  h->r = h->dnew<double>(N);
+  h->z = h->dnew<double>(N);
+  h->p = h->dnew<double>(N);
+  h->q = h->dnew<double>(N);
+  h->partial = h->dnew<double>(RED_BLOCKS);
+  h->scal = h->dnew<double>(8);
+  h->flag = h->dnew<int>(1);
+  h->hist_cap = h->opt.maxit > 0 ? h->opt.maxit : 2000;
+  h->hist_a = h->dnew<double>(h->hist_cap);
+  h->hist_b = h->dnew<double>(h->hist_cap);
+  CK(cudaMallocHost((void**)&h->pinned, 64));
+  CK(cudaEventRecord(e1, st));
+  check_err_flags(h, st);
+  CK(cudaEventElapsedTime(&h->setup_ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->free_setup_only();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// apply, operator, PCG
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+void apply_impl(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
+  const LocalLaunch& L = h->L;
+  launch_dirichlet<T>(L, r, nullptr, h->uI, 0, st);                    // V1: u_I = A_II^{-1} r_I
+  launch_operator(h->m, h->alpha, h->uI, h->t, nullptr, RED_BLOCKS, st);  // A u_I
+  launch_neumann<T>(L, r, h->t, st);                                   // r_i, Phi^T r_i, y
+  launch_coarse_gather(h->cptr, h->cent, L.rcl, h->rc, h->n_coarse, st);
+  launch_coarse_solve(h->Acg, h->n_coarse, h->dinv, h->rc, h->cy, h->uc, st);
+  launch_neumann_finish<T>(L, h->uc, st);                              // v_i on the surface
+  launch_interface_gather(h->m, L.subs, L.delta, L.vgam, z, st);       // E v
+  launch_operator(h->m, h->alpha, z, h->t, nullptr, RED_BLOCKS, st);   // A (E v)
+  launch_dirichlet<T>(L, r, h->t, z, 1, st);                           // (I - P) E v + u_I
+}
+
+void apply(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
+  if (h->local_double) apply_impl<double>(h, r, z, st);
+  else apply_impl<float>(h, r, z, st);
+}
+
+}  // namespace
+
+namespace {
+
+int pcg_impl(bddc_handle* h, const double* b, double* x, double rtol, bddc_stats* stats, cudaStream_t st) {
+  const long long N = h->n_nodes;
+  const int maxit = h->hist_cap;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * N, st));
+  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
+  launch_masked_copy(h->m, b, h->r, st);
+  launch_dot(h->r, h->r, N, h->partial, st);
+  launch_finalize(h->partial, h->scal, 4, nullptr, 0, h->flag, st);
+  CK(cudaMemcpyAsync(h->pinned, h->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double r0 = std::sqrt(h->pinned[0]);
+  int it = 0, status = BDDC_OK, converged = 0;
+  double rn = r0;
+  if (r0 == 0.0) {
+    converged = 1;
+  } else {
+    apply(h, h->r, h->z, st);
+    launch_dot(h->r, h->z, N, h->partial, st);
+    launch_finalize(h->partial, h->scal, 0, nullptr, 0, h->flag, st);
+    CK(cudaMemcpyAsync(h->p, h->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    while (it < maxit) {
+      launch_operator(h->m, h->alpha, h->p, h->q, h->partial, RED_BLOCKS, st);
+      launch_finalize(h->partial, h->scal, 1, h->hist_a, it, h->flag, st);
+      launch_update_xr(x, h->r, h->p, h->q, h->scal, N, h->partial, st);
+      launch_finalize(h->partial, h->scal, 2, nullptr, 0, h->flag, st);
+      CK(cudaMemcpyAsync(h->pinned, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync((int*)(h->pinned + 1), h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      ++it;
+      rn = std::sqrt(h->pinned[0]);
+      if (*(int*)(h->pinned + 1)) { status = BDDC_ERR_BREAKDOWN; break; }
+      if (rn <= rtol * r0) { converged = 1; break; }
+      if (it >= maxit) break;
+      apply(h, h->r, h->z, st);
+      launch_dot(h->r, h->z, N, h->partial, st);
+      launch_finalize(h->partial, h->scal, 3, h->hist_b, it - 1, h->flag, st);
+      launch_update_p(h->p, h->z, h->scal, N, st);
+    }
+    if (!converged && status == BDDC_OK) status = BDDC_ERR_NOCONV;
+  }
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats) {
+    stats->iterations = it;
+    stats->converged = converged;
+    stats->r0_norm = r0;
+    stats->r_norm = rn;
+    stats->solve_ms = ms;
+    int na = std::min(it, stats->capacity);
+    if (stats->alphas && na > 0)
+      CK(cudaMemcpy(stats->alphas, h->hist_a, sizeof(double) * na, cudaMemcpyDeviceToHost));
+    int nb = std::min(std::max(it - 1, 0), stats->capacity);
+    if (stats->betas && nb > 0)
+      CK(cudaMemcpy(stats->betas, h->hist_b, sizeof(double) * nb, cudaMemcpyDeviceToHost));
+  }
+  return status;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+#define ABI_BEGIN try {
+#define ABI_END(hh)                                                   \
+  }                                                                   \
+  catch (const BddcError& e) {                                        \
+    if (hh) (hh)->error = e.what();                                   \
+    else g_setup_error = e.what();                                    \
+    return e.code;                                                    \
+  }                                                                   \
+  catch (const std::exception& e) {                                   \
+    if (hh) (hh)->error = e.what();                                   \
+    else g_setup_error = e.what();                                    \
+    return BDDC_ERR_CUDA;                                             \
+  }
+
+extern "C" int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt,
+                          const double* alpha_dev, void* stream, bddc_handle** out) {
+  bddc_handle* hnull = nullptr;
+  ABI_BEGIN
+  if (!out) throw BddcError(BDDC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !part || !opt || !alpha_dev) throw BddcError(BDDC_ERR_ARG, "NULL argument");
+  if (mesh->nx < 2 || mesh->ny < 2 || mesh->nz < 2) throw BddcError(BDDC_ERR_ARG, "need at least 2 elements per axis");
+  if ((long long)mesh->nx * mesh->ny * mesh->nz > (1LL << 31)) throw BddcError(BDDC_ERR_ARG, "mesh too large");
+  if (opt->L_elems < 1) throw BddcError(BDDC_ERR_ARG, "L must be >= 1");
+  if (opt->precision != BDDC_FP64 && opt->precision != BDDC_MIXED) throw BddcError(BDDC_ERR_ARG, "bad precision");
+  if (opt->weights != BDDC_W_CARD && opt->weights != BDDC_W_RHO) throw BddcError(BDDC_ERR_ARG, "bad weights");
+  if (opt->selection != BDDC_SEL_VEF) throw BddcError(BDDC_ERR_UNSUPPORTED, "only the vef selection is built");
+  std::unique_ptr<bddc_handle> h(new bddc_handle());
+  h->mesh = *mesh;
+  if (!(h->mesh.h > 0)) h->mesh.h = 1.0 / mesh->nx;
+  h->opt = *opt;
+  h->local_double = opt->precision == BDDC_FP64;
+  const int n[3] = {mesh->nx, mesh->ny, mesh->nz};
+  for (int d = 0; d < 3; ++d) {
+    if (part->ncut[d] < 0 || (part->ncut[d] > 0 && !part->cut[d])) throw BddcError(BDDC_ERR_ARG, "bad cut list");
+    h->ax[d].build(n[d], part->cut[d], part->ncut[d], opt->L_elems);
+  }
+  for (int d = 0; d < 3; ++d)
+    for (size_t s = 0; s < h->ax[d].slab_lo.size(); ++s)
+      if (h->ax[d].slab_hi[s] - h->ax[d].slab_lo[s] > 4000) throw BddcError(BDDC_ERR_ARG, "subdomain too wide");
+  cudaStream_t st = (cudaStream_t)stream;
+  do_setup(h.get(), alpha_dev, st);
+  *out = h.release();
+  return BDDC_OK;
+  ABI_END(hnull)
+}
+
+extern "C" int bddc_apply(bddc_handle* h, const double* r_dev, double* z_dev, void* stream) {
+  if (!h) return BDDC_ERR_ARG;
+  ABI_BEGIN
+  if (!r_dev || !z_dev || r_dev == z_dev) throw BddcError(BDDC_ERR_ARG, "bad vectors");
+  CK(cudaSetDevice(h->device));
+  apply(h, r_dev, z_dev, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return BDDC_OK;
+  ABI_END(h)
+}
+
+extern "C" int bddc_operator(bddc_handle* h, const double* x_dev, double* y_dev, void* stream) {
+  if (!h) return BDDC_ERR_ARG;
+  ABI_BEGIN
+  if (!x_dev || !y_dev || x_dev == y_dev) throw BddcError(BDDC_ERR_ARG, "bad vectors");
+  CK(cudaSetDevice(h->device));
+  launch_operator(h->m, h->alpha, x_dev, y_dev, nullptr, RED_BLOCKS, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return BDDC_OK;
+  ABI_END(h)
+}
+
+extern "C" int pcg_solve(bddc_handle* h, const double* b_dev, double* x_dev, double rtol, bddc_stats* stats,
+                         void* stream) {
+  if (!h) return BDDC_ERR_ARG;
+  ABI_BEGIN
+  if (!b_dev || !x_dev || b_dev == x_dev) throw BddcError(BDDC_ERR_ARG, "bad vectors");
+  if (!(rtol > 0) || !(rtol < 1)) throw BddcError(BDDC_ERR_ARG, "rtol must be in (0, 1)");
+  CK(cudaSetDevice(h->device));
+  int s = pcg_impl(h, b_dev, x_dev, rtol, stats, (cudaStream_t)stream);
+  if (s == BDDC_ERR_NOCONV) h->error = "PCG did not reach the tolerance within maxit";
+  if (s == BDDC_ERR_BREAKDOWN) h->error = "PCG breakdown: p^T A p <= 0 or not finite";
+  return s;
+  ABI_END(h)
+}
+
+extern "C" int bddc_gradient(bddc_handle* h, const double* u_dev, const double* lambda_dev, double* g_dev,
+                             void* stream) {
+  if (!h) return BDDC_ERR_ARG;
+  ABI_BEGIN
+  if (!u_dev || !lambda_dev || !g_dev) throw BddcError(BDDC_ERR_ARG, "NULL vector");
+  CK(cudaSetDevice(h->device));
+  launch_gradient(h->m, u_dev, lambda_dev, g_dev, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return BDDC_OK;
+  ABI_END(h)
+}
+
+extern "C" int bddc_solve_host(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt,
+                               const double* alpha_host, const double* b_host, double* x_host, double rtol,
+                               bddc_stats* stats) {
+  double *da = nullptr, *db = nullptr, *dx = nullptr;
+  cudaStream_t st = nullptr;
+  bddc_handle* h = nullptr;
+  int rc = BDDC_OK;
+  try {
+    if (!mesh || !alpha_host || !b_host || !x_host) throw BddcError(BDDC_ERR_ARG, "NULL argument");
+    const size_t NE = (size_t)mesh->nx * mesh->ny * mesh->nz;
+    const size_t NN = (size_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaMalloc(&da, sizeof(double) * NE));
+    CK(cudaMalloc(&db, sizeof(double) * NN));
+    CK(cudaMalloc(&dx, sizeof(double) * NN));
+    CK(cudaMemcpyAsync(da, alpha_host, sizeof(double) * NE, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(db, b_host, sizeof(double) * NN, cudaMemcpyHostToDevice, st));
+    rc = bddc_setup(mesh, part, opt, da, st, &h);
+    if (rc == BDDC_OK) {
+      rc = pcg_solve(h, db, dx, rtol, stats, st);
+      if (rc == BDDC_OK || rc == BDDC_ERR_NOCONV) {
+        CK(cudaMemcpyAsync(x_host, dx, sizeof(double) * NN, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+      }
+      if (rc != BDDC_OK) g_setup_error = h->error;
+    }
+  } catch (const BddcError& e) {
+    g_setup_error = e.what();
+    rc = e.code;
+  }
+  if (h) bddc_destroy(h);
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dx);
+  if (st) cudaStreamDestroy(st);
+  return rc;
+}
+
+extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
+  if (!h || !info) return BDDC_ERR_ARG;
+  info->n_sub = (int)h->subs.size();
+  info->n_coarse = h->n_coarse;
+  info->n_vertices = h->n_vertices;
+  info->max_local_coarse = h->max_nc;
+  info->n_free = h->n_free;
+  info->bytes = (long long)h->bytes;
+  info->factor_bytes = (long long)h->factor_bytes;
+  info->setup_ms = h->setup_ms;
+  return BDDC_OK;
+}
+
+extern "C" int bddc_get_coarse_basis(const bddc_handle* h, int sub, double* phi_host, int* gid_host,
+                                     long long* node_host, int* n_surface, int* n_local_coarse) {
+  if (!h || sub < 0 || sub >= (int)h->subs.size()) return BDDC_ERR_ARG;
+  bddc_handle* hh = const_cast<bddc_handle*>(h);
+  ABI_BEGIN
+  const SubDesc& s = h->subs[sub];
+  if (n_surface) *n_surface = s.nB;
+  if (n_local_coarse) *n_local_coarse = s.nc;
+  const size_t cnt = (size_t)s.nB * s.nc;
+  if (phi_host) {
+    if (h->local_double) {
+      CK(cudaMemcpy(phi_host, (double*)h->L.Phi + s.offPhi, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<float> tmp(cnt);
+      CK(cudaMemcpy(tmp.data(), (float*)h->L.Phi + s.offPhi, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < cnt; ++i) phi_host[i] = tmp[i];
+    }
+  }
+  if (gid_host)
+    for (int j = 0; j < s.nc; ++j) gid_host[j] = h->lc[s.cofs + j].gid;
+  if (node_host) {
+    const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+    for (int b = 0; b < s.nB; ++b) {
+      int ix, iy, iz;
+      surf_coords(b, px, py, pz, ix, iy, iz);
+      node_host[b] = nodeid(h->mesh.nx + 1, h->mesh.ny + 1, s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz);
+    }
+  }
+  return BDDC_OK;
+  ABI_END(hh)
+}
+
+extern "C" int bddc_get_coarse_matrix(const bddc_handle* h, double* ac_host) {
+  if (!h || !ac_host) return BDDC_ERR_ARG;
+  if (!h->Ac_copy) return BDDC_ERR_UNSUPPORTED;
+  bddc_handle* hh = const_cast<bddc_handle*>(h);
+  ABI_BEGIN
+  CK(cudaMemcpy(ac_host, h->Ac_copy, sizeof(double) * (size_t)h->n_coarse * h->n_coarse, cudaMemcpyDeviceToHost));
+  return BDDC_OK;
+  ABI_END(hh)
+}
+
+extern "C" int bddc_destroy(bddc_handle* h) {
+  if (!h) return BDDC_OK;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  delete h;
+  return BDDC_OK;
+}
+
+extern "C" const char* bddc_last_error(const bddc_handle* h) {
+  return h ? h->error.c_str() : g_setup_error.c_str();
+}

@@ -1,0 +1,117 @@
+// Shared definitions of the BDDC-SO CUDA library (device side).
+//
+// Layouts
+//   * global node vectors: FP64, node (i,j,k) at i + NX*(j + NY*k), NX = nx+1.
+//   * alpha: FP64 per element, (i,j,k) at i + nx*(j + ny*k).
+//   * subdomain i is the element box [e0, e0+w) per axis; its local Neumann
+//     grid has p = w+1 nodes per axis, its Dirichlet (interior) grid q = w-1.
+//   * local plane-block factors: for a grid of Q = gx*gy nodes per z-plane and
+//     gz planes, slot k (k = 0..gz-1) holds the inverse Cholesky factor of the
+//     k-th diagonal block (lower triangular, Q x Q, row-major) and slot
+//     gz + k - 1 (k = 1..gz-1) the sub-diagonal factor block L_{k,k-1}.
+//   * box-surface ("boundary list") order: all nodes of the local Neumann grid
+//     with at least one coordinate at 0 or p-1, in lexicographic order.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define BDDC_THREADS 256
+
+namespace bddc {
+
+struct SubDesc {
+  int e0[3];          // element origin of the box
+  int w[3];           // box widths in elements
+  int nB;             // box-surface nodes
+  int nv, na, nc;     // local coarse DOFs: point values, averages, total
+  int cofs;           // first entry of this subdomain in the local-coarse table
+                      // (also the offset of its nc-vector of local coarse values)
+  int color;          // (sx&1) + 2(sy&1) + 4(sz&1): same colour => no shared objects
+  long long offD;     // Dirichlet factor slots (local type)
+  long long offN;     // Neumann factor slots (local type)
+  long long offW;     // factorisation scratch: 2*QN^2 + 1024*ceil(QN/32) (local type)
+  long long offY;     // setup: Y = A_rr^{-1} F, nN x nc (local type)
+  long long offG;     // setup: C_r Y, na x nc (local type)
+  long long offL;     // setup: Lambda_v, na x nv (local type)
+  long long offPA;    // setup: Phi_ra = X S_c^{-1}, nN x na (local type)
+  long long offSc;    // setup: S_c^{-1}, na x na (local type)
+  long long offAc;    // setup: Phi^T A Phi, nc x nc (FP64)
+  long long offPhi;   // Phi on the box surface: nB x nc, row-major (local type)
+  long long offB;     // per-surface-node arrays: nB (weights, v_Gamma)
+  long long offVec;   // apply: local Neumann vector, nN (local type)
+};
+
+// A coarse DOF as seen from one subdomain: the object's local node box
+// (inclusive ranges on the local Neumann grid) and its global number.
+struct LocalCoarse {
+  int gid;
+  short lo[3], hi[3];
+  int count;          // nodes in the object
+};
+
+// Per-axis tables (global), concatenated for the three axes.
+struct AxisTables {
+  const int* item;     // node -> item (points even, open intervals odd), size n+1
+  const int* theta;    // node -> 1 on a Theta cut plane (interior), 0 else
+  const int* hat;      // node -> 1 on a Theta-hat piece boundary (incl. Theta), 0 else
+  const int* slab;     // element -> slab index, size n
+  const int* piece;    // element -> piece index along the axis, size n
+  const int* slab_lo;  // slab -> first element
+  const int* slab_hi;  // slab -> one past last element
+  int n;               // elements on this axis
+  int nslab;
+  int nitem;
+};
+
+struct MeshDev {
+  int nx, ny, nz;
+  int NX, NY, NZ;      // nodes per axis
+  double h;
+  AxisTables ax[3];
+  int nsub[3];
+};
+
+__host__ __device__ inline long long nodeid(int NX, int NY, int i, int j, int k) {
+  return (long long)i + (long long)NX * ((long long)j + (long long)NY * k);
+}
+
+__device__ inline bool on_dirichlet(const MeshDev& m, int i, int j, int k) {
+  return i == 0 || j == 0 || k == 0 || i == m.nx || j == m.ny || k == m.nz;
+}
+
+// Box-surface list of a px x py x pz grid.
+__host__ __device__ inline int surf_count(int px, int py, int pz) {
+  int ring = 2 * px + 2 * (py - 2);
+  return 2 * px * py + (pz - 2) * ring;
+}
+
+__host__ __device__ inline int surf_index(int ix, int iy, int iz, int px, int py, int pz) {
+  int P = px * py;
+  int ring = 2 * px + 2 * (py - 2);
+  if (iz == 0) return iy * px + ix;
+  if (iz == pz - 1) return P + (pz - 2) * ring + iy * px + ix;
+  int base = P + (iz - 1) * ring;
+  if (iy == 0) return base + ix;
+  if (iy == py - 1) return base + px + 2 * (py - 2) + ix;
+  return base + px + 2 * (iy - 1) + (ix == 0 ? 0 : 1);
+}
+
+__host__ __device__ inline void surf_coords(int b, int px, int py, int pz, int& ix, int& iy, int& iz) {
+  int P = px * py;
+  int ring = 2 * px + 2 * (py - 2);
+  if (b < P) { iz = 0; iy = b / px; ix = b % px; return; }
+  b -= P;
+  if (b < (pz - 2) * ring) {
+    iz = 1 + b / ring;
+    int r = b % ring;
+    if (r < px) { iy = 0; ix = r; return; }
+    r -= px;
+    if (r < 2 * (py - 2)) { iy = 1 + r / 2; ix = (r & 1) ? px - 1 : 0; return; }
+    r -= 2 * (py - 2);
+    iy = py - 1; ix = r; return;
+  }
+  b -= (pz - 2) * ring;
+  iz = pz - 1; iy = b / px; ix = b % px;
+}
+
+}  // namespace bddc

@@ -1,0 +1,226 @@
+// CTA-level dense building blocks for the batched local factorisations.
+//
+// One thread block (BDDC_THREADS = 256 threads) works on matrices that live in
+// global memory (L2-resident at these sizes), staging 64 x 16 / 16 x 64 tiles
+// through shared memory; each thread owns a 4 x 4 register tile of a 64 x 64
+// output tile.  Triangular operands skip the K-range that multiplies known
+// zeros.  These routines are called from kernels that give one CTA to one
+// subdomain (or one RHS chunk of one subdomain).
+#pragma once
+#include "common.cuh"
+
+namespace bddc {
+
+constexpr int GBM = 64, GBN = 64, GBK = 16, GPAD = 1;
+constexpr int TILE = 32, TLD = 33;
+
+template <typename T>
+struct DenseSmem {
+  T As[GBK][GBM + GPAD];
+  T Bs[GBK][GBN + GPAD];
+  T t0[TILE * TLD];
+  T t1[TILE * TLD];
+  int flag;
+};
+
+// C(MxN) = alpha * op(A) * op(B) + beta * C  (beta == 0: C is not read).
+//   op(A)[i,k] = TA ? A[k*lda+i] : A[i*lda+k]
+//   op(B)[k,j] = TB ? B[j*ldb+k] : B[k*ldb+j]
+//   triA: 0 none, 1 op(A) lower (zero for k>i), 2 op(A) upper (zero for k<i)
+//   triB: 0 none, 1 op(B) upper (zero for k>j), 2 op(B) lower (zero for k<j)
+//   lowerC: skip output tiles strictly above the diagonal.
+// C must not alias A or B.  Ends with __syncthreads().
+template <typename T>
+__device__ void cta_gemm(int M, int N, int K, T alpha,
+                         const T* __restrict__ A, int lda, bool TA,
+                         const T* __restrict__ B, int ldb, bool TB,
+                         T beta, T* C, int ldc, int triA, int triB, bool lowerC,
+                         DenseSmem<T>& sm) {
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int tilesM = (M + GBM - 1) / GBM, tilesN = (N + GBN - 1) / GBN;
+  for (int t = 0; t < tilesM * tilesN; ++t) {
+    const int i0 = (t / tilesN) * GBM, j0 = (t % tilesN) * GBN;
+    if (lowerC && j0 > i0 + GBM - 1) continue;
+    int kbeg = 0, kend = K;
+    if (triA == 1) kend = min(kend, i0 + GBM);
+    if (triA == 2) kbeg = max(kbeg, i0);
+    if (triB == 1) kend = min(kend, j0 + GBN);
+    if (triB == 2) kbeg = max(kbeg, j0);
+    T acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+    for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int e = tid + BDDC_THREADS * r;
+        int ii, kk;
+        if (TA) { ii = e & 63; kk = e >> 6; } else { ii = e >> 4; kk = e & 15; }
+        int gi = i0 + ii, gk = k0 + kk;
+        T v = T(0);
+        if (gi < M && gk < kend) v = TA ? A[(long long)gk * lda + gi] : A[(long long)gi * lda + gk];
+        sm.As[kk][ii] = v;
+        int jj;
+        if (TB) { jj = e >> 4; kk = e & 15; } else { jj = e & 63; kk = e >> 6; }
+        int gj = j0 + jj;
+        gk = k0 + kk;
+        T w = T(0);
+        if (gj < N && gk < kend) w = TB ? B[(long long)gj * ldb + gk] : B[(long long)gk * ldb + gj];
+        sm.Bs[kk][jj] = w;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GBK; ++kk) {
+        T a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = sm.As[kk][ty * 4 + r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) b[c] = sm.Bs[kk][tx * 4 + c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int gi = i0 + ty * 4 + r;
+      if (gi >= M) continue;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        int gj = j0 + tx * 4 + c;
+        if (gj >= N) continue;
+        T* p = C + (long long)gi * ldc + gj;
+        *p = (beta == T(0)) ? alpha * acc[r][c] : alpha * acc[r][c] + beta * (*p);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Unblocked Cholesky of an n x n (n <= 32) tile in shared memory (ld TLD),
+// lower triangle in place.  A non-positive (or NaN) pivot sets sm.flag and is
+// replaced by 1 so that the computation stays finite.
+template <typename T>
+__device__ void tile_chol(T* S, int n, DenseSmem<T>& sm) {
+  const int tid = threadIdx.x;
+  for (int c = 0; c < n; ++c) {
+    if (tid == 0) {
+      T d = S[c * TLD + c];
+      if (!(d > T(0))) { sm.flag = 1; d = T(1); }
+      S[c * TLD + c] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = c + 1 + tid; i < n; i += BDDC_THREADS) S[i * TLD + c] /= S[c * TLD + c];
+    __syncthreads();
+    const int m = n - c - 1;
+    for (int idx = tid; idx < m * m; idx += BDDC_THREADS) {
+      int i = c + 1 + idx / m, j = c + 1 + idx % m;
+      if (j <= i) S[i * TLD + j] -= S[i * TLD + c] * S[j * TLD + c];
+    }
+    __syncthreads();
+  }
+}
+
+// X = L^{-1} for a lower n x n tile (both ld TLD); zeros above the diagonal.
+template <typename T>
+__device__ void tile_inv(const T* L, T* X, int n) {
+  const int j = threadIdx.x;
+  if (j < n) {
+    for (int i = 0; i < n; ++i) {
+      if (i < j) { X[i * TLD + j] = T(0); continue; }
+      T s = (i == j) ? T(1) : T(0);
+      for (int k = j; k < i; ++k) s -= L[i * TLD + k] * X[k * TLD + j];
+      X[i * TLD + j] = s / L[i * TLD + i];
+    }
+  }
+  __syncthreads();
+}
+
+// Blocked right-looking Cholesky S = L L^T (S n x n SPD, lower part read,
+// overwritten by L) followed by the explicit inverse Linv = L^{-1} (written in
+// full, zeros above the diagonal).  diag: scratch for ceil(n/32) 32x32 tiles.
+// Returns false if a pivot was not positive.
+template <typename T>
+__device__ bool cta_chol_inv(T* S, int lds, T* Linv, int ldl, int n, T* diag, DenseSmem<T>& sm) {
+  const int tid = threadIdx.x;
+  if (tid == 0) sm.flag = 0;
+  __syncthreads();
+  const int nt = (n + TILE - 1) / TILE;
+  for (int jb = 0; jb < nt; ++jb) {
+    const int j0 = jb * TILE, nb = min(TILE, n - j0);
+    for (int idx = tid; idx < TILE * TILE; idx += BDDC_THREADS) {
+      int i = idx / TILE, j = idx % TILE;
+      sm.t0[i * TLD + j] = (i < nb && j <= i) ? S[(long long)(j0 + i) * lds + j0 + j] : T(0);
+    }
+    __syncthreads();
+    tile_chol(sm.t0, nb, sm);
+    tile_inv(sm.t0, sm.t1, nb);
+    for (int idx = tid; idx < nb * nb; idx += BDDC_THREADS) {
+      int i = idx / nb, j = idx % nb;
+      if (j <= i) S[(long long)(j0 + i) * lds + j0 + j] = sm.t0[i * TLD + j];
+      diag[jb * TILE * TILE + i * TILE + j] = sm.t1[i * TLD + j];
+    }
+    // panel below the diagonal tile: P = P * Tinv^T
+    for (int i = j0 + nb + tid; i < n; i += BDDC_THREADS) {
+      T r[TILE];
+      T* row = S + (long long)i * lds + j0;
+#pragma unroll
+      for (int k = 0; k < TILE; ++k) r[k] = (k < nb) ? row[k] : T(0);
+#pragma unroll
+      for (int c = 0; c < TILE; ++c) {
+        if (c >= nb) break;
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < TILE; ++k)
+          if (k <= c) s += r[k] * sm.t1[c * TLD + k];
+        row[c] = s;
+      }
+    }
+    __syncthreads();
+    const int m = n - j0 - nb;
+    if (m > 0) {
+      const T* P = S + (long long)(j0 + nb) * lds + j0;
+      cta_gemm<T>(m, m, nb, T(-1), P, lds, false, P, lds, true, T(1),
+                  S + (long long)(j0 + nb) * lds + j0 + nb, lds, 0, 0, true, sm);
+    }
+  }
+  // Linv, row block by row block: X_ib,<ib = -Tinv_ib (L_ib,<ib X_<ib,<ib)
+  for (int ib = 0; ib < nt; ++ib) {
+    const int i0 = ib * TILE, nb = min(TILE, n - i0);
+    for (int idx = tid; idx < TILE * TILE; idx += BDDC_THREADS) {
+      int i = idx / TILE, j = idx % TILE;
+      sm.t1[i * TLD + j] = diag[ib * TILE * TILE + i * TILE + j];
+    }
+    __syncthreads();
+    if (ib > 0) {
+      cta_gemm<T>(nb, i0, i0, T(1), S + (long long)i0 * lds, lds, false, Linv, ldl, false, T(0),
+                  Linv + (long long)i0 * ldl, ldl, 0, 2, false, sm);
+      for (int j = tid; j < i0; j += BDDC_THREADS) {
+        T w[TILE];
+#pragma unroll
+        for (int k = 0; k < TILE; ++k) w[k] = (k < nb) ? Linv[(long long)(i0 + k) * ldl + j] : T(0);
+#pragma unroll
+        for (int r = 0; r < TILE; ++r) {
+          if (r >= nb) break;
+          T s = T(0);
+#pragma unroll
+          for (int k = 0; k < TILE; ++k)
+            if (k <= r) s += sm.t1[r * TLD + k] * w[k];
+          Linv[(long long)(i0 + r) * ldl + j] = -s;
+        }
+      }
+    }
+    for (int idx = tid; idx < nb * (n - i0); idx += BDDC_THREADS) {
+      int i = idx / (n - i0), j = idx % (n - i0);
+      Linv[(long long)(i0 + i) * ldl + i0 + j] = (j < nb) ? sm.t1[i * TLD + j] : T(0);
+    }
+    __syncthreads();
+  }
+  return sm.flag == 0;
+}
+
+}  // namespace bddc

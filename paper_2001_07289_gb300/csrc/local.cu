@@ -1,0 +1,694 @@
+// Per-subdomain (batched) kernels of BDDC-SO: local assembly, block-tridiagonal
+// Cholesky factorisations of the Dirichlet and constrained Neumann problems,
+// the coarse basis Phi_i, and the local steps of the preconditioner apply.
+//
+// Method (Section 3 with Definition 1; the two-level split of the W-tilde
+// problem as in Dohrmann 2003, cited in Section 1):
+//   * A_II^(i): stiffness of the interior nodes of Omega_i (not on Gamma).
+//   * A^(i): Neumann stiffness of Omega_i.  Primal point values (vertices of
+//     Theta-hat on Gamma) are eliminated: their rows/columns, and those of the
+//     Dirichlet-boundary nodes, are replaced by identity rows, which keeps the
+//     local grid regular.  Means over (sub)edges/(sub)faces are Lagrange rows
+//     C_r, handled through S_c = C_r A_rr^{-1} C_r^T.
+//   * Phi_i solves [A C^T; C 0][Phi; Lambda] = [0; I]; with Y = A_rr^{-1}
+//     [-A_rv | C_r^T] = [Y_v | X]:  Lambda_v = S_c^{-1} C_r Y_v,
+//     Phi_rv = Y_v - X Lambda_v, Phi_ra = X S_c^{-1}, and
+//     Phi^T A Phi = [[ (A Phi_v)_V , -Lambda_v^T ], [ -Lambda_v , S_c^{-1} ]].
+//   * Apply: the constrained Neumann solution is w_r = y - Phi_ra C_r y with
+//     y = A_rr^{-1} r_r, so v_i = Phi_i (u_c|_i - [0; C_r y]) + y.
+//
+// Local matrices are stored as z-plane blocks (see common.cuh); the factor of
+// each diagonal block is kept as its explicit inverse, so every sweep is a
+// sequence of dense products.
+#include "common.cuh"
+#include "dense.cuh"
+#include "kernels.h"
+
+namespace bddc {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+// Entry A(a, a+d) of the stiffness restricted to the elements of box s:
+// h * K(d) * (sum of alpha over the elements holding both nodes), where the
+// unit-cube matrix K is 1/3 on the diagonal, 0 for nodes one coordinate apart
+// and -1/12 for nodes two or three coordinates apart.
+__device__ inline double box_entry(const MeshDev& m, const double* __restrict__ alpha,
+                                   const SubDesc& s, int ax, int ay, int az, int dx, int dy, int dz) {
+  int hd = abs(dx) + abs(dy) + abs(dz);
+  if (hd == 1) return 0.0;
+  int a[3] = {ax, ay, az}, d[3] = {dx, dy, dz}, lo[3], hi[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (d[c] > 0) { lo[c] = a[c]; hi[c] = a[c]; }
+    else if (d[c] < 0) { lo[c] = a[c] - 1; hi[c] = a[c] - 1; }
+    else { lo[c] = a[c] - 1; hi[c] = a[c]; }
+    lo[c] = max(lo[c], s.e0[c]);
+    hi[c] = min(hi[c], s.e0[c] + s.w[c] - 1);
+  }
+  double sum = 0.0;
+  for (int k = lo[2]; k <= hi[2]; ++k)
+    for (int j = lo[1]; j <= hi[1]; ++j)
+      for (int i = lo[0]; i <= hi[0]; ++i)
+        sum += alpha[(long long)i + (long long)m.nx * (j + (long long)m.ny * k)];
+  return m.h * (hd == 0 ? (1.0 / 3.0) : (-1.0 / 12.0)) * sum;
+}
+
+// Local Neumann node fixed to zero in A_rr: on the Dirichlet boundary or a
+// primal point value (box-surface node at Theta-hat points on all three axes).
+__device__ inline bool neumann_fixed(const MeshDev& m, const SubDesc& s, int ix, int iy, int iz) {
+  int gx = s.e0[0] + ix, gy = s.e0[1] + iy, gz = s.e0[2] + iz;
+  if (on_dirichlet(m, gx, gy, gz)) return true;
+  bool surf = ix == 0 || iy == 0 || iz == 0 || ix == s.w[0] || iy == s.w[1] || iz == s.w[2];
+  return surf && m.ax[0].hat[gx] && m.ax[1].hat[gy] && m.ax[2].hat[gz];
+}
+
+struct Grid {
+  int gx, gy, gz, off;  // local grid sizes; global coordinate = e0 + off + local
+};
+__device__ inline Grid grid_of(const SubDesc& s, int neumann) {
+  Grid g;
+  if (neumann) { g.gx = s.w[0] + 1; g.gy = s.w[1] + 1; g.gz = s.w[2] + 1; g.off = 0; }
+  else { g.gx = s.w[0] - 1; g.gy = s.w[1] - 1; g.gz = s.w[2] - 1; g.off = 1; }
+  if (g.gx <= 0 || g.gy <= 0 || g.gz <= 0) { g.gx = g.gy = g.gz = 0; }
+  return g;
+}
+
+__device__ inline void set_error(int* err, int code, int sub) {
+  if (atomicCAS(err, 0, code) == 0) err[1] = sub;
+}
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+template <typename T>
+__device__ inline T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// assembly of the plane blocks
+// ---------------------------------------------------------------------------
+
+// grid: (subdomain, plane k, chunk); writes the diagonal block D_k to slot k
+// and A_{k,k-1} to slot gz+k-1.
+template <typename T>
+__global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha,
+                           T* __restrict__ fac, int neumann) {
+  const SubDesc s = subs[blockIdx.x];
+  const Grid g = grid_of(s, neumann);
+  const int k = blockIdx.y;
+  if (k >= g.gz) return;
+  const int Q = g.gx * g.gy;
+  T* base = fac + (neumann ? s.offN : s.offD);
+  const long long QQ = (long long)Q * Q;
+  for (long long e = (long long)blockIdx.z * blockDim.x + threadIdx.x; e < 2 * QQ;
+       e += (long long)gridDim.z * blockDim.x) {
+    int which = (int)(e / QQ);  // 0: diagonal block, 1: block (k, k-1)
+    if (which == 1 && k == 0) continue;
+    long long r = e % QQ;
+    int a = (int)(r / Q), b = (int)(r % Q);
+    int ax = a % g.gx, ay = a / g.gx, bx = b % g.gx, by = b / g.gx;
+    int bz = (which == 0) ? k : k - 1;
+    int dx = bx - ax, dy = by - ay, dz = bz - k;
+    double v = 0.0;
+    if (abs(dx) <= 1 && abs(dy) <= 1) {
+      bool fa = neumann && neumann_fixed(m, s, ax, ay, k);
+      bool fb = neumann && neumann_fixed(m, s, bx, by, bz);
+      if (fa || fb) v = (dx == 0 && dy == 0 && dz == 0) ? 1.0 : 0.0;
+      else v = box_entry(m, alpha, s, s.e0[0] + g.off + ax, s.e0[1] + g.off + ay, s.e0[2] + g.off + k,
+                         dx, dy, dz);
+    }
+    T* blk = base + (which == 0 ? (long long)k : (long long)(g.gz + k - 1)) * QQ;
+    blk[r] = (T)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched block-tridiagonal Cholesky:  for k: M_k = B_{k-1} Linv_{k-1}^T,
+// S_k = D_k - M_k M_k^T, Linv_k = chol(S_k)^{-1}.  One CTA per subdomain.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_btchol(const SubDesc* __restrict__ subs, T* __restrict__ fac, T* __restrict__ scratch, int neumann,
+         int* err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
+  const SubDesc s = subs[blockIdx.x];
+  const Grid g = grid_of(s, neumann);
+  if (g.gz == 0) return;
+  const int Q = g.gx * g.gy;
+  const long long QQ = (long long)Q * Q;
+  T* base = fac + (neumann ? s.offN : s.offD);
+  T* W1 = scratch + s.offW;
+  T* W2 = W1 + QQ;
+  T* diag = W2 + QQ;
+  for (int k = 0; k < g.gz; ++k) {
+    T* slot = base + (long long)k * QQ;
+    if (k > 0) {
+      T* mslot = base + (long long)(g.gz + k - 1) * QQ;
+      for (long long e = threadIdx.x; e < QQ; e += blockDim.x) W2[e] = mslot[e];
+      __syncthreads();
+      // M_k = B_{k-1} * Linv_{k-1}^T   (op(B) = Linv^T is upper)
+      cta_gemm<T>(Q, Q, Q, T(1), W2, Q, false, base + (long long)(k - 1) * QQ, Q, true, T(0), mslot, Q,
+                  0, 1, false, sm);
+      // S_k = D_k - M_k M_k^T (lower part)
+      cta_gemm<T>(Q, Q, Q, T(-1), mslot, Q, false, mslot, Q, true, T(1), slot, Q, 0, 0, true, sm);
+    }
+    for (long long e = threadIdx.x; e < QQ; e += blockDim.x) W1[e] = slot[e];
+    __syncthreads();
+    bool ok = cta_chol_inv<T>(W1, Q, slot, Q, Q, diag, sm);
+    if (!ok && threadIdx.x == 0) set_error(err, neumann ? 3 : 2, blockIdx.x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// multi-RHS sweeps: Y <- A_rr^{-1} Y with the Neumann factor (Y: nN x nc,
+// row-major, ld nc).  grid: (subdomain, column chunk of CW columns).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_btsolve_multi(const SubDesc* __restrict__ subs, const T* __restrict__ fac, T* __restrict__ Y,
+                T* __restrict__ scratch, long long scratch_stride) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
+  const SubDesc s = subs[blockIdx.x];
+  const int c0 = blockIdx.y * CW;
+  if (c0 >= s.nc) return;
+  const int cw = min(CW, s.nc - c0);
+  const Grid g = grid_of(s, 1);
+  const int Q = g.gx * g.gy, nz = g.gz, ld = s.nc;
+  const long long QQ = (long long)Q * Q;
+  const T* base = fac + s.offN;
+  T* Yb = Y + s.offY + c0;
+  T* W = scratch + ((long long)blockIdx.x * gridDim.y + blockIdx.y) * scratch_stride;
+  for (int k = 0; k < nz; ++k) {
+    T* Yk = Yb + (long long)k * Q * ld;
+    if (k > 0)
+      cta_gemm<T>(Q, cw, Q, T(-1), base + (long long)(nz + k - 1) * QQ, Q, false,
+                  Yk - (long long)Q * ld, ld, false, T(1), Yk, ld, 0, 0, false, sm);
+    for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) W[e] = Yk[(long long)(e / cw) * ld + e % cw];
+    __syncthreads();
+    cta_gemm<T>(Q, cw, Q, T(1), base + (long long)k * QQ, Q, false, W, cw, false, T(0), Yk, ld, 1, 0, false, sm);
+  }
+  for (int k = nz - 1; k >= 0; --k) {
+    T* Yk = Yb + (long long)k * Q * ld;
+    if (k < nz - 1)
+      cta_gemm<T>(Q, cw, Q, T(-1), base + (long long)(nz + k) * QQ, Q, true,
+                  Yk + (long long)Q * ld, ld, false, T(1), Yk, ld, 0, 0, false, sm);
+    for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) W[e] = Yk[(long long)(e / cw) * ld + e % cw];
+    __syncthreads();
+    cta_gemm<T>(Q, cw, Q, T(1), base + (long long)k * QQ, Q, true, W, cw, false, T(0), Yk, ld, 2, 0, false, sm);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// coarse basis
+// ---------------------------------------------------------------------------
+
+// F = [-A_rv | C_r^T] on the local Neumann grid (rows), into Y.
+template <typename T>
+__global__ void k_coarse_rhs(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha,
+                             const LocalCoarse* __restrict__ lc, T* __restrict__ Y) {
+  const SubDesc s = subs[blockIdx.x];
+  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+  const long long nN = (long long)px * py * pz;
+  T* Yb = Y + s.offY;
+  for (long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x; e < nN * s.nc;
+       e += (long long)gridDim.y * blockDim.x) {
+    int r = (int)(e / s.nc), j = (int)(e % s.nc);
+    int ix = r % px, iy = (r / px) % py, iz = r / (px * py);
+    double v = 0.0;
+    if (!neumann_fixed(m, s, ix, iy, iz)) {
+      const LocalCoarse c = lc[s.cofs + j];
+      if (j < s.nv) {
+        int dx = c.lo[0] - ix, dy = c.lo[1] - iy, dz = c.lo[2] - iz;
+        if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1)
+          v = -box_entry(m, alpha, s, s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz, dx, dy, dz);
+      } else if (ix >= c.lo[0] && ix <= c.hi[0] && iy >= c.lo[1] && iy <= c.hi[1] && iz >= c.lo[2] &&
+                 iz <= c.hi[2]) {
+        v = 1.0 / c.count;
+      }
+    }
+    Yb[e] = (T)v;
+  }
+}
+
+// G = C_r Y (na x nc): means of Y's columns over the averaging objects.
+template <typename T>
+__global__ void k_constraint_means(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict__ lc,
+                                   const T* __restrict__ Y, T* __restrict__ G) {
+  const SubDesc s = subs[blockIdx.x];
+  const int px = s.w[0] + 1, py = s.w[1] + 1;
+  const T* Yb = Y + s.offY;
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < s.na * s.nc; e += gridDim.y * blockDim.x) {
+    int a = e / s.nc, j = e % s.nc;
+    const LocalCoarse c = lc[s.cofs + s.nv + a];
+    T sum = T(0);
+    for (int iz = c.lo[2]; iz <= c.hi[2]; ++iz)
+      for (int iy = c.lo[1]; iy <= c.hi[1]; ++iy)
+        for (int ix = c.lo[0]; ix <= c.hi[0]; ++ix)
+          sum += Yb[((long long)ix + px * (iy + (long long)py * iz)) * s.nc + j];
+    G[s.offG + e] = sum / T(c.count);
+  }
+}
+
+// S_c = G[:, nv:] -> S_c^{-1} (into Sc) and Lambda_v = S_c^{-1} G[:, :nv] (into Lv).
+template <typename T>
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_schur(const SubDesc* __restrict__ subs, T* __restrict__ G, T* __restrict__ Sc, T* __restrict__ Lv,
+        T* __restrict__ scratch, int* err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
+  const SubDesc s = subs[blockIdx.x];
+  const int na = s.na, nv = s.nv, nc = s.nc;
+  if (na == 0) return;
+  T* Gs = G + s.offG;
+  T* S = Gs + nv;               // na x na, ld nc; factored in place
+  T* Linv = Sc + s.offSc;       // na x na
+  T* diag = scratch + s.offW;
+  bool ok = cta_chol_inv<T>(S, nc, Linv, na, na, diag, sm);
+  if (!ok && threadIdx.x == 0) set_error(err, 4, blockIdx.x);
+  // S_c^{-1} = Linv^T Linv -> into the free S region, then back to Sc
+  cta_gemm<T>(na, na, na, T(1), Linv, na, true, Linv, na, false, T(0), S, nc, 2, 2, false, sm);
+  for (int e = threadIdx.x; e < na * na; e += blockDim.x) Linv[e] = S[(long long)(e / na) * nc + e % na];
+  __syncthreads();
+  if (nv > 0)
+    cta_gemm<T>(na, nv, na, T(1), Linv, na, false, Gs, nc, false, T(0), Lv + s.offL, nv, 0, 0, false, sm);
+}
+
+// Row-chunked products on the nN rows of Y:
+//   mode 0: Y[:, :nv] -= X Lambda_v         (Phi_rv)
+//   mode 1: PA = X S_c^{-1}                  (Phi_ra)
+// grid: (subdomain, row chunk of RB rows).
+constexpr int RB = 128;
+template <typename T>
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_phi_rows(const SubDesc* __restrict__ subs, T* __restrict__ Y, const T* __restrict__ Lv,
+           const T* __restrict__ Sc, T* __restrict__ PA, int mode) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
+  const SubDesc s = subs[blockIdx.x];
+  const int nN = (s.w[0] + 1) * (s.w[1] + 1) * (s.w[2] + 1);
+  const int r0 = blockIdx.y * RB;
+  if (r0 >= nN || s.na == 0) return;
+  const int rows = min(RB, nN - r0);
+  T* Yr = Y + s.offY + (long long)r0 * s.nc;
+  if (mode == 0) {
+    if (s.nv == 0) return;
+    cta_gemm<T>(rows, s.nv, s.na, T(-1), Yr + s.nv, s.nc, false, Lv + s.offL, s.nv, false, T(1), Yr, s.nc,
+                0, 0, false, sm);
+  } else {
+    cta_gemm<T>(rows, s.na, s.na, T(1), Yr + s.nv, s.nc, false, Sc + s.offSc, s.na, false, T(0),
+                PA + s.offPA + (long long)r0 * s.na, s.na, 0, 0, false, sm);
+  }
+}
+
+// Phi on the box surface: vertex columns from Y (+1 at the vertex itself),
+// average columns from PA.
+template <typename T>
+__global__ void k_phi_surface(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict__ lc,
+                              const T* __restrict__ Y, const T* __restrict__ PA, T* __restrict__ Phi) {
+  const SubDesc s = subs[blockIdx.x];
+  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+  for (long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x; e < (long long)s.nB * s.nc;
+       e += (long long)gridDim.y * blockDim.x) {
+    int b = (int)(e / s.nc), j = (int)(e % s.nc);
+    int ix, iy, iz;
+    surf_coords(b, px, py, pz, ix, iy, iz);
+    long long node = (long long)ix + px * (iy + (long long)py * iz);
+    T v;
+    if (j < s.nv) {
+      const LocalCoarse c = lc[s.cofs + j];
+      v = Y[s.offY + node * s.nc + j];
+      if (c.lo[0] == ix && c.lo[1] == iy && c.lo[2] == iz) v = T(1);
+    } else {
+      v = PA[s.offPA + node * s.na + (j - s.nv)];
+    }
+    Phi[s.offPhi + e] = v;
+  }
+}
+
+// Local coarse matrix Phi^T A Phi (FP64, nc x nc).
+template <typename T>
+__global__ void k_local_coarse_matrix(const SubDesc* __restrict__ subs, MeshDev m,
+                                      const double* __restrict__ alpha, const LocalCoarse* __restrict__ lc,
+                                      const T* __restrict__ Y, const T* __restrict__ Lv,
+                                      const T* __restrict__ Sc, double* __restrict__ Ac) {
+  const SubDesc s = subs[blockIdx.x];
+  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+  const int nc = s.nc, nv = s.nv;
+  double* A = Ac + s.offAc;
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < nc * nc; e += gridDim.y * blockDim.x) {
+    int r = e / nc, c = e % nc;
+    double v;
+    if (r < nv && c < nv) {
+      // (A Phi_v)[vertex r, column c], symmetrised
+      double both[2];
+      for (int t = 0; t < 2; ++t) {
+        int row = t ? c : r, col = t ? r : c;
+        const LocalCoarse vr = lc[s.cofs + row];
+        const LocalCoarse vc = lc[s.cofs + col];
+        double acc = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              int bx = vr.lo[0] + dx, by = vr.lo[1] + dy, bz = vr.lo[2] + dz;
+              if (bx < 0 || by < 0 || bz < 0 || bx >= px || by >= py || bz >= pz) continue;
+              if (on_dirichlet(m, s.e0[0] + bx, s.e0[1] + by, s.e0[2] + bz)) continue;
+              double phi;
+              if (bx == vc.lo[0] && by == vc.lo[1] && bz == vc.lo[2]) phi = 1.0;
+              else phi = (double)Y[s.offY + ((long long)bx + px * (by + (long long)py * bz)) * nc + col];
+              if (phi == 0.0) continue;
+              acc += box_entry(m, alpha, s, s.e0[0] + vr.lo[0], s.e0[1] + vr.lo[1], s.e0[2] + vr.lo[2],
+                               dx, dy, dz) * phi;
+            }
+        both[t] = acc;
+      }
+      v = 0.5 * (both[0] + both[1]);
+    } else if (r >= nv && c >= nv) {
+      int a = r - nv, b = c - nv;
+      v = 0.5 * ((double)Sc[s.offSc + (long long)a * s.na + b] + (double)Sc[s.offSc + (long long)b * s.na + a]);
+    } else if (r >= nv) {
+      v = -(double)Lv[s.offL + (long long)(r - nv) * nv + c];
+    } else {
+      v = -(double)Lv[s.offL + (long long)(c - nv) * nv + r];
+    }
+    A[e] = v;
+  }
+}
+
+// Interface weights of eq. (W) (pw == nullptr) or Remark 1 (pw = mean alpha
+// per sub-subdomain) on every box-surface node of every subdomain.
+__global__ void k_weights(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ pw,
+                          double* __restrict__ delta) {
+  const SubDesc s = subs[blockIdx.x];
+  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+  const int npx = m.ax[0].piece[m.nx - 1] + 1, npy = m.ax[1].piece[m.ny - 1] + 1;
+  for (int b = blockIdx.y * blockDim.x + threadIdx.x; b < s.nB; b += gridDim.y * blockDim.x) {
+    int ix, iy, iz;
+    surf_coords(b, px, py, pz, ix, iy, iz);
+    int gc[3] = {s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz};
+    if (on_dirichlet(m, gc[0], gc[1], gc[2])) { delta[s.offB + b] = 0.0; continue; }
+    int pc[3][2], inside[3][2], np[3];
+    for (int d = 0; d < 3; ++d) {
+      const AxisTables& A = m.ax[d];
+      int eL = gc[d] - 1, eR = gc[d];   // both inside the mesh: node not on the boundary
+      int slabS = A.slab[s.e0[d]];
+      if (A.piece[eL] == A.piece[eR]) {
+        np[d] = 1; pc[d][0] = A.piece[eR]; inside[d][0] = (A.slab[eR] == slabS);
+      } else {
+        np[d] = 2;
+        pc[d][0] = A.piece[eL]; inside[d][0] = (A.slab[eL] == slabS);
+        pc[d][1] = A.piece[eR]; inside[d][1] = (A.slab[eR] == slabS);
+      }
+    }
+    double num = 0.0, den = 0.0;
+    for (int c = 0; c < np[2]; ++c)
+      for (int bb = 0; bb < np[1]; ++bb)
+        for (int a = 0; a < np[0]; ++a) {
+          double w = pw ? pw[pc[0][a] + (long long)npx * (pc[1][bb] + (long long)npy * pc[2][c])] : 1.0;
+          den += w;
+          if (inside[0][a] && inside[1][bb] && inside[2][c]) num += w;
+        }
+    delta[s.offB + b] = num / den;
+  }
+}
+
+// Mean alpha of every sub-subdomain (piece), summed in a fixed order.
+__global__ void k_piece_alpha(MeshDev m, const double* __restrict__ alpha, const int* __restrict__ plo,
+                              const int* __restrict__ phi, int npx, int npy, int npz, double* __restrict__ pw) {
+  long long np = (long long)npx * npy * npz;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
+    int a = (int)(p % npx), b = (int)((p / npx) % npy), c = (int)(p / ((long long)npx * npy));
+    // plo/phi: concatenated per-axis piece element ranges (x, then y, then z)
+    int x0 = plo[a], x1 = phi[a], y0 = plo[npx + b], y1 = phi[npx + b], z0 = plo[npx + npy + c],
+        z1 = phi[npx + npy + c];
+    double sum = 0.0;
+    for (int k = z0; k < z1; ++k)
+      for (int j = y0; j < y1; ++j)
+        for (int i = x0; i < x1; ++i) sum += alpha[(long long)i + (long long)m.nx * (j + (long long)m.ny * k)];
+    pw[p] = sum / ((double)(x1 - x0) * (y1 - y0) * (z1 - z0));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// single-RHS sweeps (apply): v <- A^{-1} v for the plane-block factor, v in
+// shared memory (gz*Q entries), t scratch of Q entries.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void sweep1(const T* __restrict__ base, int Q, int nz, T* v, T* t) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long QQ = (long long)Q * Q;
+  for (int k = 0; k < nz; ++k) {
+    T* vk = v + (long long)k * Q;
+    if (k > 0) {
+      const T* M = base + (long long)(nz + k - 1) * QQ;
+      const T* vp = vk - Q;
+      for (int i = warp; i < Q; i += nw) {
+        const T* row = M + (long long)i * Q;
+        T acc = T(0);
+        for (int j = lane; j < Q; j += 32) acc += row[j] * vp[j];
+        acc = warp_sum(acc);
+        if (lane == 0) t[i] = vk[i] - acc;
+      }
+    } else {
+      for (int i = threadIdx.x; i < Q; i += blockDim.x) t[i] = vk[i];
+    }
+    __syncthreads();
+    const T* Li = base + (long long)k * QQ;
+    for (int i = warp; i < Q; i += nw) {
+      const T* row = Li + (long long)i * Q;
+      T acc = T(0);
+      for (int j = lane; j <= i; j += 32) acc += row[j] * t[j];
+      acc = warp_sum(acc);
+      if (lane == 0) vk[i] = acc;
+    }
+    __syncthreads();
+  }
+  for (int k = nz - 1; k >= 0; --k) {
+    T* vk = v + (long long)k * Q;
+    if (k < nz - 1) {
+      const T* M = base + (long long)(nz + k) * QQ;
+      const T* vn = vk + Q;
+      for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+        T acc = T(0);
+        for (int j = 0; j < Q; ++j) acc += M[(long long)j * Q + i] * vn[j];
+        t[i] = vk[i] - acc;
+      }
+    } else {
+      for (int i = threadIdx.x; i < Q; i += blockDim.x) t[i] = vk[i];
+    }
+    __syncthreads();
+    const T* Li = base + (long long)k * QQ;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+      T acc = T(0);
+      for (int j = i; j < Q; ++j) acc += Li[(long long)j * Q + i] * t[j];
+      vk[i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Dirichlet solves of the apply.  mode 0: z_I = A_II^{-1} r_I;
+// mode 1: z_I = A_II^{-1} (r_I - t_I).  Writes the interior nodes of z only.
+template <typename T>
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
+                  const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ z,
+                  int mode) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const SubDesc s = subs[blockIdx.x];
+  const Grid g = grid_of(s, 0);
+  if (g.gz == 0) return;
+  const int Q = g.gx * g.gy, n = Q * g.gz;
+  T* v = reinterpret_cast<T*>(smraw);
+  T* tmp = v + n;
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
+    long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
+    double val = r[gi];
+    if (mode) val -= t[gi];
+    v[l] = (T)val;
+  }
+  __syncthreads();
+  sweep1<T>(fac + s.offD, Q, g.gz, v, tmp);
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
+    long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
+    z[gi] = (double)v[l];
+  }
+}
+
+// Weighted restriction r_i = D_i R_i (r - t) on the box surface, the local
+// coarse right-hand side rc_i = Phi_i^T r_i, and the constrained Neumann solve
+// y = A_rr^{-1} r_i,r (in place in vloc).
+template <typename T>
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
+                const T* __restrict__ Phi, const double* __restrict__ delta,
+                const double* __restrict__ r, const double* __restrict__ t, T* __restrict__ vloc,
+                double* __restrict__ rcl) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const SubDesc s = subs[blockIdx.x];
+  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+  const int Q = px * py, n = Q * pz;
+  T* v = reinterpret_cast<T*>(smraw);
+  T* tmp = v + n;
+  double* rg = reinterpret_cast<double*>(smraw + align16(sizeof(T) * ((size_t)n + Q)));
+  for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = T(0);
+  __syncthreads();
+  for (int b = threadIdx.x; b < s.nB; b += blockDim.x) {
+    int ix, iy, iz;
+    surf_coords(b, px, py, pz, ix, iy, iz);
+    long long gi = nodeid(m.NX, m.NY, s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz);
+    double d = delta[s.offB + b];
+    double val = (d == 0.0) ? 0.0 : d * (r[gi] - t[gi]);
+    rg[b] = val;
+    if (!neumann_fixed(m, s, ix, iy, iz)) v[ix + px * (iy + py * iz)] = (T)val;
+  }
+  __syncthreads();
+  const T* P = Phi + s.offPhi;
+  for (int j = threadIdx.x; j < s.nc; j += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < s.nB; ++b) acc += (double)P[(long long)b * s.nc + j] * rg[b];
+    rcl[s.cofs + j] = acc;
+  }
+  __syncthreads();
+  sweep1<T>(fac + s.offN, Q, pz, v, tmp);
+  for (int l = threadIdx.x; l < n; l += blockDim.x) vloc[s.offVec + l] = v[l];
+}
+
+// v_i on the box surface: Phi_i (u_c|_i - [0; C_r y]) + y.
+template <typename T>
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict__ lc,
+                 const T* __restrict__ Phi, const T* __restrict__ vloc, const double* __restrict__ uc,
+                 double* __restrict__ vgam) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const SubDesc s = subs[blockIdx.x];
+  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+  double* ut = reinterpret_cast<double*>(smraw);
+  const T* y = vloc + s.offVec;
+  for (int j = threadIdx.x; j < s.nc; j += blockDim.x) {
+    const LocalCoarse c = lc[s.cofs + j];
+    double val = uc[c.gid];
+    if (j >= s.nv) {
+      double sum = 0.0;
+      for (int iz = c.lo[2]; iz <= c.hi[2]; ++iz)
+        for (int iy = c.lo[1]; iy <= c.hi[1]; ++iy)
+          for (int ix = c.lo[0]; ix <= c.hi[0]; ++ix) sum += (double)y[ix + px * (iy + py * iz)];
+      val -= sum / c.count;
+    }
+    ut[j] = val;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T* P = Phi + s.offPhi;
+  for (int b = warp; b < s.nB; b += nw) {
+    const T* row = P + (long long)b * s.nc;
+    double acc = 0.0;
+    for (int j = lane; j < s.nc; j += 32) acc += (double)row[j] * ut[j];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      int ix, iy, iz;
+      surf_coords(b, px, py, pz, ix, iy, iz);
+      vgam[s.offB + b] = acc + (double)y[ix + px * (iy + py * iz)];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+size_t dense_smem() { return sizeof(DenseSmem<T>); }
+
+template <typename T>
+void launch_setup_local(const LocalLaunch& L, cudaStream_t st) {
+  const int S = L.nsub;
+  T* facD = (T*)L.facD; T* facN = (T*)L.facN; T* W = (T*)L.scratch;
+  size_t sm = dense_smem<T>();
+  // Dirichlet
+  if (L.maxQD > 0) {
+    k_assemble<T><<<dim3(S, L.maxNzD, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facD, 0);
+    k_btchol<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, facD, W, 0, L.err);
+  }
+  // Neumann
+  k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1);
+  k_btchol<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, facN, W, 1, L.err);
+  // coarse basis
+  T* Y = (T*)L.Y; T* G = (T*)L.G; T* Lv = (T*)L.Lv; T* PA = (T*)L.PA; T* Sc = (T*)L.Sc; T* Phi = (T*)L.Phi;
+  if (L.maxNc == 0) return;  // a single subdomain: no interface, no coarse space
+  k_coarse_rhs<T><<<dim3(S, 64), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y);
+  int nch = (L.maxNc + CW - 1) / CW;
+  k_btsolve_multi<T><<<dim3(S, nch), BDDC_THREADS, sm, st>>>(L.subs, facN, Y, (T*)L.mscratch, L.mscratch_stride);
+  k_constraint_means<T><<<dim3(S, 16), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, G);
+  k_schur<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, G, Sc, Lv, W, L.err);
+  int nrc = (L.maxNN + RB - 1) / RB;
+  k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 0);
+  k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 1);
+  k_phi_surface<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, PA, Phi);
+  k_local_coarse_matrix<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y, Lv, Sc, L.Ac);
+}
+
+template <typename T>
+void configure_local_kernels() {
+  size_t sm = dense_smem<T>();
+  cudaFuncSetAttribute(k_btchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_btsolve_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_phi_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_dirichlet_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_neumann_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_neumann_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+}
+
+void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st) {
+  k_weights<<<dim3(L.nsub, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, piece_w, L.delta);
+}
+
+void launch_piece_alpha(const MeshDev& m, const double* alpha, const int* plo, const int* phi, int npx, int npy,
+                        int npz, double* pw, cudaStream_t st) {
+  long long np = (long long)npx * npy * npz;
+  int blocks = (int)std::min<long long>((np + 255) / 256, 4096);
+  k_piece_alpha<<<blocks, 256, 0, st>>>(m, alpha, plo, phi, npx, npy, npz, pw);
+}
+
+template <typename T>
+void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, double* z, int mode, cudaStream_t st) {
+  if (L.maxQD == 0) return;
+  size_t sm = sizeof(T) * ((size_t)L.maxND + L.maxQD + 2);
+  k_dirichlet_solve<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facD, r, t, z, mode);
+}
+
+template <typename T>
+void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
+  size_t sm = align16(sizeof(T) * ((size_t)L.maxNN + L.maxQN)) + sizeof(double) * (L.maxNB + 2);
+  k_neumann_solve<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta,
+                                                      r, t, (T*)L.vloc, L.rcl);
+}
+
+template <typename T>
+void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t st) {
+  size_t sm = sizeof(double) * (L.maxNc + 1);
+  k_neumann_finish<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.lc, (const T*)L.Phi, (const T*)L.vloc, uc,
+                                                       L.vgam);
+}
+
+template void launch_setup_local<float>(const LocalLaunch&, cudaStream_t);
+template void launch_setup_local<double>(const LocalLaunch&, cudaStream_t);
+template void configure_local_kernels<float>();
+template void configure_local_kernels<double>();
+template void launch_dirichlet<float>(const LocalLaunch&, const double*, const double*, double*, int, cudaStream_t);
+template void launch_dirichlet<double>(const LocalLaunch&, const double*, const double*, double*, int, cudaStream_t);
+template void launch_neumann<float>(const LocalLaunch&, const double*, const double*, cudaStream_t);
+template void launch_neumann<double>(const LocalLaunch&, const double*, const double*, cudaStream_t);
+template void launch_neumann_finish<float>(const LocalLaunch&, const double*, cudaStream_t);
+template void launch_neumann_finish<double>(const LocalLaunch&, const double*, cudaStream_t);
+template size_t dense_smem<float>();
+template size_t dense_smem<double>();
+
+}  // namespace bddc
