@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark of the BDDC-SO hot path on one GB300 (or N independent replicas).
+
+A step is one pass of the whole path on one synthetic problem with its inputs
+resident in HBM: bddc_setup (sub-partition, objects, weights, local Dirichlet
+and constrained Neumann factorisations, coarse basis, coarse assembly and FP64
+Cholesky) followed by pcg_solve with BDDC-SO to the workload's tolerance.
+Workload: 48^3 Q1 hexahedra on the unit cube, 4x4x4 box subdomains of 12^3,
+subobjects of size L = 4h, manufactured f, rtol 1e-10, FP32-local/FP64-outer
+("mixed") path; the FP64 path is timed beside it.
+
+value = free DOF solved per second (MDOF/s) over all ranks, i.e.
+n_free * N / time-to-solution.  Extra keys: preconditioner applies/s and MDOF/s
+(100 back-to-back bddc_apply), setup phases, iterations, roofline of the
+dominant phase, the oracle as CPU baseline, and end-to-end numbers through
+bddc_solve_host with host buffers.
+
+--impl reference times the FP64 CPU oracle (test infrastructure written from
+the paper) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BDDC-SO PCG time-to-solution and precond-apply MDOF/s, mixed vs FP64 at 1 GB300"
+WORKLOAD = ("poisson48: 48^3 Q1 hexahedra on the unit cube, 4x4x4 box subdomains of 12^3, "
+            "subobjects L=4h, alpha=1, manufactured f, PCG rtol 1e-10 from x0=0")
+FP64_PEAK_TFLOPS = 1.25    # GB300 FP64 (FMA and DMMA) nominal; probe measured 1.19
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm), run in a fresh process
+# ---------------------------------------------------------------------------
+def oracle_sample(spec: str) -> dict:
+    """Times the oracle's setup + PCG on a sample of the workload and returns
+    MDOF/s.  spec 'full' = the whole 48^3 workload; 'quarter' = the 24x24x48
+    sub-box holding 2x2x4 of its subdomains (same subdomain size, L and f)."""
+    import numpy as np
+    from paper_2001_07289_gb300 import inputs
+    from oracle import bddc as orc
+    if spec == "full":
+        p = inputs.workload(1)
+    else:
+        h = 1.0 / 48
+        b = inputs.rhs_quadrature(24, 24, 48, h, inputs.manufactured_f)
+        p = inputs.Problem("poisson48-quarter", 24, 24, 48, h, [[12], [12], [12, 24, 36]], 4,
+                           np.ones(24 * 24 * 48), b, rtol=1e-10)
+    t0 = time.perf_counter()
+    B = orc.build(p)
+    B.setup_two_level()
+    res = orc.pcg(B.operator, B.apply, p.b, p.rtol)
+    dt = time.perf_counter() - t0
+    return dict(seconds=dt, n_free=p.n_free, iterations=res.iterations, mdofs=p.n_free / dt / 1e6,
+                sample=p.name + f" ({p.nx}x{p.ny}x{p.nz}, {len(B.subs)} subdomains)")
+
+
+def run_oracle_subprocess(spec: str, threads: int = 1) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", spec],
+                         capture_output=True, text=True, env=env, cwd=ROOT)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.samples, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 3 + k and s[3 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-steps", action="store_true",
+                    help="run only the warm-up and timed steps (for profiler launch lists)")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.oracle_sample)))
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2001_07289_gb300 import inputs
+    from paper_2001_07289_gb300.bddc import BDDC, solve_host
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.only_steps):
+        cpu_base = run_oracle_subprocess("full", threads=1)
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    p = inputs.workload(1, L=4, precision=args.precision)
+    alpha = torch.from_numpy(p.alpha).cuda()
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(precision):
+        pre = BDDC.from_problem(p, alpha=alpha, precision=precision)
+        _, st = pre.solve(b, p.rtol, out=x)
+        return pre, st
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        pre, _ = step(args.precision)
+        pre.close()
+
+    # ---- timed steps: time-to-solution = setup + PCG, L2 flushed between steps
+    times, infos, stats = [], [], []
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pre, st = step(args.precision)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(pre.info())
+            stats.append(st)
+            pre.close()
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    ms = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if args.only_steps:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "ms_per_step": round(ms, 3), "steps": args.steps,
+                              "iterations": stats[-1]["iterations"], "phases_ms": infos[-1]["phase_ms"],
+                              "launches": int(sum(i["launches"] for i in infos))}))
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- preconditioner applies/s (100 back-to-back applies)
+    pre = BDDC.from_problem(p, alpha=alpha, precision=args.precision)
+    r = torch.from_numpy(inputs.random_node_vector(p.nx, p.ny, p.nz, 5)).cuda()
+    z = torch.empty_like(r)
+    for _ in range(5):
+        pre.apply(r, out=z)
+    flush.fill_(2.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n_apply = 100
+    for _ in range(n_apply):
+        pre.apply(r, out=z)
+    e1.record(stream)
+    e1.synchronize()
+    apply_ms = e0.elapsed_time(e1) / n_apply
+    info_apply = pre.info()
+    pre.close()
+
+    # ---- FP64 path for the mixed-vs-FP64 comparison
+    other = "fp64" if args.precision == "mixed" else "mixed"
+    pre, _ = step(other)
+    pre.close()
+    other_times, other_iters, other_info = [], [], None
+    for _ in range(2):
+        flush.fill_(3.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pre, st = step(other)
+        e1.record(stream)
+        e1.synchronize()
+        other_times.append(e0.elapsed_time(e1))
+        other_iters.append(st["iterations"])
+        other_info = pre.info()
+        pre.close()
+
+    # ---- end to end through the C ABI with host buffers
+    a_host = torch.from_numpy(p.alpha).pin_memory().numpy()
+    b_host = torch.from_numpy(p.b).pin_memory().numpy()
+    e2e_t = []
+    for k in range(1 + max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st_h = solve_host(p.nx, p.ny, p.nz, p.cuts, p.L, a_host, b_host, p.rtol, h=p.h,
+                             precision=args.precision)
+        dt = time.perf_counter() - t0
+        if k > 0:
+            e2e_t.append(dt)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    info = infos[-1]
+    n_free = info["n_free"]
+    iters = stats[-1]["iterations"]
+    phases = dict(zip(["checks_weights", "dirichlet_factor", "neumann_factor", "coarse_basis",
+                       "coarse_assembly", "coarse_cholesky"], [round(v, 3) for v in info["phase_ms"]]))
+    setup_ms = info["setup_ms"]
+    solve_ms = statistics.mean(s["solve_ms"] for s in stats)
+    # dominant phase and its roofline (FP64 ALU for the coarse Cholesky)
+    nc = info["n_coarse"]
+    chol_ms = info["phase_ms"][5]
+    chol_flops = nc ** 3 / 3.0
+    achieved = chol_flops / (chol_ms * 1e-3) / 1e12
+    roofline = {"kernel": "coarse Cholesky (k_coarse_potrf/trsm/syrk, FP64)", "bound": "alu",
+                "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "algorithmic": f"n_c^3/3 = {chol_flops:.3e} flop per factorisation (n_c = {nc})",
+                "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json)"}
+    out = {
+        "metric": METRIC,
+        "value": round(world * n_free / (ms * 1e-3) / 1e6, 4),
+        "unit": "MDOF/s (free DOF solved to rtol per second, setup included)",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": WORKLOAD, "n_free": n_free, "subdomains": info["n_sub"], "L_over_h": 4,
+                   "n_coarse": nc, "precision": args.precision,
+                   "parallelism": f"{world} independent replica(s), no data-path collective",
+                   "l2": "flushed between timed steps (256 MiB write outside the timed events)"},
+        "time_to_solution_ms": round(ms, 3),
+        "setup_ms": round(setup_ms, 3),
+        "solve_ms": round(solve_ms, 3),
+        "iterations": iters,
+        "setup_phases_ms": phases,
+        "precond_apply": {"ms": round(apply_ms, 4), "applies_per_s": round(1e3 / apply_ms, 1),
+                          "mdofs": round(n_free * 1e3 / apply_ms / 1e6, 2)},
+        f"{other}_path": {"time_to_solution_ms": round(statistics.mean(other_times), 3),
+                          "iterations": other_iters[-1], "setup_ms": round(other_info["setup_ms"], 3),
+                          "setup_phases_ms": [round(v, 3) for v in other_info["phase_ms"]]},
+        "roofline": roofline,
+        "wall_s_timed_region": round(t_wall, 3),
+        "gpu_launches": int(sum(i["launches"] for i in infos)),
+        "e2e": {"value": round(n_free / statistics.mean(e2e_t) / 1e6, 4), "unit": "MDOF/s",
+                "ms": round(1e3 * statistics.mean(e2e_t), 3),
+                "h2d_bytes_per_step": int(8 * (p.n_elems + p.n_nodes)), "d2h_bytes_per_step": int(8 * p.n_nodes),
+                "api": "bddc_solve_host (host alpha, b, x; copies, setup, PCG, teardown inside)"},
+        "clocks": clk.summary(),
+    }
+    if cpu_base:
+        out["cpu_baseline"] = {"value": round(cpu_base["mdofs"], 6), "unit": "MDOF/s", "cores": 1,
+                               "kind": "oracle", "sample": cpu_base["sample"] + " setup+PCG, 1 thread",
+                               "seconds": round(cpu_base["seconds"], 2), "iterations": cpu_base["iterations"]}
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, world):
+    """The oracle on the host cores, on the same metric and unit, each step a
+    bounded sample (2x2x4 of the 4x4x4 subdomains)."""
+    times, res = [], None
+    for k in range(args.warmup + args.steps):
+        res = run_oracle_subprocess("quarter", threads=1)
+        if k >= args.warmup:
+            times.append(res["seconds"])
+    sec = statistics.mean(times)
+    v = res["n_free"] / sec / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 6),
+           "unit": "MDOF/s (free DOF solved to rtol per second, setup included)",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sec, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded; no dataset)",
+           "config": {"workload": WORKLOAD, "sample": res["sample"]},
+           "cpu_baseline": {"value": round(v, 6), "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+                            "sample": res["sample"] + " setup+PCG, 1 thread"},
+           "e2e": {"value": round(v, 6), "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -101,6 +101,11 @@ typedef struct {
     long long bytes;      /* device memory held by the handle                  */
     long long factor_bytes;  /* local factors + Phi + coarse factor            */
     double setup_ms;      /* device time of bddc_setup (CUDA events)          */
+    double phase_ms[6];   /* setup phases: 0 checks+weights, 1 Dirichlet factor,
+                             2 Neumann factor, 3 coarse basis, 4 coarse assembly,
+                             5 coarse Cholesky                                 */
+    long long launches;   /* kernels launched for this handle since its setup
+                             began (setup, applies, solves, gradients)        */
 } bddc_info_t;
 
 /* Builds the BDDC-SO preconditioner (Section 3; Definition 1 with V1 = U_I,

@@ -52,7 +52,8 @@ class Stats(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n_sub", C.c_int), ("n_coarse", C.c_int), ("n_vertices", C.c_int),
                 ("max_local_coarse", C.c_int), ("n_free", C.c_longlong), ("bytes", C.c_longlong),
-                ("factor_bytes", C.c_longlong), ("setup_ms", C.c_double)]
+                ("factor_bytes", C.c_longlong), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 6),
+                ("launches", C.c_longlong)]
 
 
 def _load():
@@ -179,7 +180,9 @@ class BDDC:
     def info(self) -> dict:
         i = Info()
         _check(lib.bddc_get_info(self._handle, C.byref(i)), self._handle)
-        return {k: getattr(i, k) for k, _ in Info._fields_}
+        out = {k: getattr(i, k) for k, _ in Info._fields_}
+        out["phase_ms"] = list(out["phase_ms"])
+        return out
 
     def coarse_basis(self, sub: int):
         nb, nc = C.c_int(), C.c_int()

@@ -141,6 +141,8 @@ struct bddc_handle {
   double* pinned = nullptr;
   int hist_cap = 0;
   float setup_ms = 0.f;
+  float phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  long long launch_base = 0;
   std::vector<void*> setup_only;
   std::vector<int> h_cptr, h_clist;   // coarse DOF -> owners (CSR), colour lists
   std::vector<int2> h_cent;
@@ -354,9 +356,9 @@ void check_err_flags(bddc_handle* h, cudaStream_t st) {
 }
 
 template <typename T>
-void setup_local(bddc_handle* h, cudaStream_t st) {
+void setup_local(bddc_handle* h, cudaStream_t st, cudaEvent_t* ev) {
   configure_local_kernels<T>();
-  launch_setup_local<T>(h->L, st);
+  launch_setup_local<T>(h->L, st, ev);
 }
 
 void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
@@ -365,9 +367,11 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->n_nodes = (long long)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
   h->n_free = (long long)(M.nx - 1) * (M.ny - 1) * (M.nz - 1);
   build_metadata(h);
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  h->launch_base = g_launches;
+  // events: 0 start, 1 weights done, 2 Dirichlet, 3 Neumann, 4 basis, 5 assembly, 6 coarse factor
+  cudaEvent_t ev[7];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  cudaEvent_t e0 = ev[0], e1 = ev[6];
   CK(cudaEventRecord(e0, st));
   // flags and alpha
   h->err = h->dnew<int>(2);
@@ -439,8 +443,9 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     launch_piece_alpha(m, h->alpha, dplo, dphi, npc[0], npc[1], npc[2], pw, st);
   }
   launch_weights(L, pw, st);
+  CK(cudaEventRecord(ev[1], st));
   // local factorisations and coarse basis
-  if (dbl) setup_local<double>(h, st); else setup_local<float>(h, st);
+  if (dbl) setup_local<double>(h, st, ev + 2); else setup_local<float>(h, st, ev + 2);
   CK(cudaGetLastError());
   // coarse problem (FP64)
   const int nc = h->n_coarse;
@@ -451,6 +456,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->factor_bytes += sizeof(double) * (size_t)nc * nc;
   CK(cudaMemsetAsync(h->Acg, 0, sizeof(double) * (size_t)nc * nc, st));
   launch_coarse_assemble(L, h->color_subs, h->color_count, h->color_off, h->Acg, nc, st);
+  CK(cudaEventRecord(ev[5], st));
   if ((long long)nc * nc <= (1LL << 22)) {
     h->Ac_copy = h->dnew<double>((size_t)nc * nc);
     CK(cudaMemcpyAsync(h->Ac_copy, h->Acg, sizeof(double) * (size_t)nc * nc, cudaMemcpyDeviceToDevice, st));
@@ -460,6 +466,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->cscratch = (double*)h->dalloc(sizeof(double) * std::max<size_t>((size_t)ntile * CNB * CNB, 4096), true);
   configure_coarse_kernels();
   launch_coarse_factor(h->Acg, nc, h->dinv, h->cscratch, h->err, st);
+  CK(cudaEventRecord(ev[6], st));
   CK(cudaGetLastError());
   // apply / PCG work vectors
   const long long N = h->n_nodes;
@@ -480,11 +487,10 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->hist_a = h->dnew<double>(h->hist_cap);
   h->hist_b = h->dnew<double>(h->hist_cap);
   CK(cudaMallocHost((void**)&h->pinned, 64));
-  CK(cudaEventRecord(e1, st));
   check_err_flags(h, st);
   CK(cudaEventElapsedTime(&h->setup_ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (int k = 0; k < 6; ++k) CK(cudaEventElapsedTime(&h->phase_ms[k], ev[k], ev[k + 1]));
+  for (auto& e : ev) cudaEventDestroy(e);
   h->free_setup_only();
 }
 
@@ -732,6 +738,8 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   info->bytes = (long long)h->bytes;
   info->factor_bytes = (long long)h->factor_bytes;
   info->setup_ms = h->setup_ms;
+  for (int k = 0; k < 6; ++k) info->phase_ms[k] = h->phase_ms[k];
+  info->launches = g_launches - h->launch_base;
   return BDDC_OK;
 }
 

@@ -33,6 +33,7 @@ void launch_coarse_assemble(const LocalLaunch& L, const int* color_subs, const i
                             const int* color_offset_host, double* Acg, int nc, cudaStream_t st) {
   for (int c = 0; c < 8; ++c) {
     if (color_count_host[c] == 0) continue;
+    BDDC_COUNT(1);
     k_coarse_assemble<<<dim3(color_count_host[c], 16), BDDC_THREADS, 0, st>>>(
         L.subs, L.lc, color_subs + color_offset_host[c], L.Ac, Acg, nc);
   }
@@ -96,8 +97,10 @@ void launch_coarse_factor(double* A, int n, double* dinv, double* scratch, int* 
   const size_t sm = sizeof(DenseSmem<double>);
   for (int j = 0; j < nt; ++j) {
     k_coarse_potrf<<<1, BDDC_THREADS, sm, st>>>(A, n, j, dinv, scratch, err);
+    BDDC_COUNT(1);
     const int m = nt - j - 1;
     if (m > 0) {
+      BDDC_COUNT(2);
       k_coarse_trsm<<<m, BDDC_THREADS, sm, st>>>(A, n, j, dinv, scratch);
       k_coarse_syrk<<<m * m, BDDC_THREADS, sm, st>>>(A, n, j, nt);
     }
@@ -119,6 +122,7 @@ __global__ void k_coarse_gather(const int* __restrict__ ptr, const int2* __restr
 
 void launch_coarse_gather(const int* ptr, const int2* ent, const double* rcl, double* rc, int nc, cudaStream_t st) {
   if (nc <= 0) return;
+  BDDC_COUNT(1);
   k_coarse_gather<<<(nc + 255) / 256, 256, 0, st>>>(ptr, ent, rcl, rc, nc);
 }
 
@@ -195,6 +199,7 @@ k_coarse_bwd(const double* __restrict__ L, int n, int j, const double* __restric
 void launch_coarse_solve(const double* L, int n, const double* dinv, double* b, double* y, double* x,
                          cudaStream_t st) {
   const int nt = (n + CNB - 1) / CNB;
+  BDDC_COUNT(2 * nt);
   for (int j = 0; j < nt; ++j) {
     int m = std::max(1, nt - j - 1);
     k_coarse_fwd<<<m, BDDC_THREADS, 0, st>>>(L, n, j, dinv, b, y);

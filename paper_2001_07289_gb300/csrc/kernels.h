@@ -6,6 +6,10 @@
 
 namespace bddc {
 
+// Running count of kernel launches issued by this library (host side).
+extern long long g_launches;
+#define BDDC_COUNT(n) (::bddc::g_launches += (n))
+
 constexpr int CW = 64;       // RHS columns per CTA in the multi-RHS sweeps
 constexpr int CNB = 128;     // coarse Cholesky tile
 
@@ -29,7 +33,9 @@ struct LocalLaunch {
   int maxNB, maxNc;
 };
 
-template <typename T> void launch_setup_local(const LocalLaunch& L, cudaStream_t st);
+// ev (may be null): 3 events recorded after the Dirichlet factorisation, the
+// Neumann factorisation and the coarse basis.
+template <typename T> void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev);
 template <typename T> void configure_local_kernels();
 template <typename T> size_t dense_smem();
 template <typename T>

@@ -607,7 +607,7 @@ template <typename T>
 size_t dense_smem() { return sizeof(DenseSmem<T>); }
 
 template <typename T>
-void launch_setup_local(const LocalLaunch& L, cudaStream_t st) {
+void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) {
   const int S = L.nsub;
   T* facD = (T*)L.facD; T* facN = (T*)L.facN; T* W = (T*)L.scratch;
   size_t sm = dense_smem<T>();
@@ -615,23 +615,31 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st) {
   if (L.maxQD > 0) {
     k_assemble<T><<<dim3(S, L.maxNzD, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facD, 0);
     k_btchol<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, facD, W, 0, L.err);
+    BDDC_COUNT(2);
   }
+  if (ev) cudaEventRecord(ev[0], st);
   // Neumann
   k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1);
   k_btchol<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, facN, W, 1, L.err);
+  BDDC_COUNT(2);
+  if (ev) cudaEventRecord(ev[1], st);
   // coarse basis
   T* Y = (T*)L.Y; T* G = (T*)L.G; T* Lv = (T*)L.Lv; T* PA = (T*)L.PA; T* Sc = (T*)L.Sc; T* Phi = (T*)L.Phi;
-  if (L.maxNc == 0) return;  // a single subdomain: no interface, no coarse space
-  k_coarse_rhs<T><<<dim3(S, 64), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y);
-  int nch = (L.maxNc + CW - 1) / CW;
-  k_btsolve_multi<T><<<dim3(S, nch), BDDC_THREADS, sm, st>>>(L.subs, facN, Y, (T*)L.mscratch, L.mscratch_stride);
-  k_constraint_means<T><<<dim3(S, 16), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, G);
-  k_schur<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, G, Sc, Lv, W, L.err);
-  int nrc = (L.maxNN + RB - 1) / RB;
-  k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 0);
-  k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 1);
-  k_phi_surface<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, PA, Phi);
-  k_local_coarse_matrix<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y, Lv, Sc, L.Ac);
+  if (L.maxNc > 0) {  // one subdomain has no interface and no coarse space
+    k_coarse_rhs<T><<<dim3(S, 64), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y);
+    int nch = (L.maxNc + CW - 1) / CW;
+    k_btsolve_multi<T><<<dim3(S, nch), BDDC_THREADS, sm, st>>>(L.subs, facN, Y, (T*)L.mscratch,
+                                                                 L.mscratch_stride);
+    k_constraint_means<T><<<dim3(S, 16), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, G);
+    k_schur<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, G, Sc, Lv, W, L.err);
+    int nrc = (L.maxNN + RB - 1) / RB;
+    k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 0);
+    k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 1);
+    k_phi_surface<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, PA, Phi);
+    k_local_coarse_matrix<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y, Lv, Sc, L.Ac);
+    BDDC_COUNT(8);
+  }
+  if (ev) cudaEventRecord(ev[2], st);
 }
 
 template <typename T>
@@ -647,6 +655,7 @@ void configure_local_kernels() {
 }
 
 void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st) {
+  BDDC_COUNT(1);
   k_weights<<<dim3(L.nsub, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, piece_w, L.delta);
 }
 
@@ -654,12 +663,14 @@ void launch_piece_alpha(const MeshDev& m, const double* alpha, const int* plo, c
                         int npz, double* pw, cudaStream_t st) {
   long long np = (long long)npx * npy * npz;
   int blocks = (int)std::min<long long>((np + 255) / 256, 4096);
+  BDDC_COUNT(1);
   k_piece_alpha<<<blocks, 256, 0, st>>>(m, alpha, plo, phi, npx, npy, npz, pw);
 }
 
 template <typename T>
 void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, double* z, int mode, cudaStream_t st) {
   if (L.maxQD == 0) return;
+  BDDC_COUNT(1);
   size_t sm = sizeof(T) * ((size_t)L.maxND + L.maxQD + 2);
   k_dirichlet_solve<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facD, r, t, z, mode);
 }
@@ -667,6 +678,7 @@ void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, do
 template <typename T>
 void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
   size_t sm = align16(sizeof(T) * ((size_t)L.maxNN + L.maxQN)) + sizeof(double) * (L.maxNB + 2);
+  BDDC_COUNT(1);
   k_neumann_solve<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta,
                                                       r, t, (T*)L.vloc, L.rcl);
 }
@@ -674,12 +686,13 @@ void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cuda
 template <typename T>
 void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t st) {
   size_t sm = sizeof(double) * (L.maxNc + 1);
+  BDDC_COUNT(1);
   k_neumann_finish<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.lc, (const T*)L.Phi, (const T*)L.vloc, uc,
                                                        L.vgam);
 }
 
-template void launch_setup_local<float>(const LocalLaunch&, cudaStream_t);
-template void launch_setup_local<double>(const LocalLaunch&, cudaStream_t);
+template void launch_setup_local<float>(const LocalLaunch&, cudaStream_t, cudaEvent_t*);
+template void launch_setup_local<double>(const LocalLaunch&, cudaStream_t, cudaEvent_t*);
 template void configure_local_kernels<float>();
 template void configure_local_kernels<double>();
 template void launch_dirichlet<float>(const LocalLaunch&, const double*, const double*, double*, int, cudaStream_t);

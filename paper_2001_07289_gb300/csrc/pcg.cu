@@ -36,6 +36,7 @@ __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b
 }
 
 void launch_dot(const double* a, const double* b, long long n, double* partial, cudaStream_t st) {
+  BDDC_COUNT(1);
   k_dot<<<RED_BLOCKS, 256, 0, st>>>(a, b, n, partial);
 }
 
@@ -80,6 +81,7 @@ __global__ void k_finalize(const double* __restrict__ partial, double* scal, int
 }
 
 void launch_finalize(const double* partial, double* scal, int op, double* hist, int it, int* flag, cudaStream_t st) {
+  BDDC_COUNT(1);
   k_finalize<<<1, 256, 0, st>>>(partial, scal, op, hist, it, flag);
 }
 
@@ -100,6 +102,7 @@ __global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r, cons
 
 void launch_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, long long n,
                       double* partial, cudaStream_t st) {
+  BDDC_COUNT(1);
   k_update_xr<<<RED_BLOCKS, 256, 0, st>>>(x, r, p, q, scal, n, partial);
 }
 
@@ -112,6 +115,7 @@ __global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z,
 }
 
 void launch_update_p(double* p, const double* z, const double* scal, long long n, cudaStream_t st) {
+  BDDC_COUNT(1);
   k_update_p<<<RED_BLOCKS, 256, 0, st>>>(p, z, scal, n);
 }
 

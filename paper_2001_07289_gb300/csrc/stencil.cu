@@ -12,6 +12,8 @@
 
 namespace bddc {
 
+long long g_launches = 0;
+
 __device__ inline double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -83,6 +85,7 @@ k_operator(MeshDev m, const double* __restrict__ alpha, const double* __restrict
 
 void launch_operator(const MeshDev& m, const double* alpha, const double* x, double* y, double* dot_partial,
                      int nblocks, cudaStream_t st) {
+  BDDC_COUNT(1);
   k_operator<<<nblocks, 256, 0, st>>>(m, alpha, x, y, dot_partial);
 }
 
@@ -120,6 +123,7 @@ __global__ void k_gradient(MeshDev m, const double* __restrict__ u, const double
 void launch_gradient(const MeshDev& m, const double* u, const double* lam, double* g, cudaStream_t st) {
   long long NE = (long long)m.nx * m.ny * m.nz;
   int blocks = (int)std::min<long long>((NE + 255) / 256, 152 * 16);
+  BDDC_COUNT(1);
   k_gradient<<<blocks, 256, 0, st>>>(m, u, lam, g);
 }
 
@@ -157,6 +161,7 @@ void launch_interface_gather(const MeshDev& m, const SubDesc* subs, const double
                              double* z, cudaStream_t st) {
   long long N = (long long)m.NX * m.NY * m.NZ;
   int blocks = (int)std::min<long long>((N + 255) / 256, 152 * 16);
+  BDDC_COUNT(1);
   k_interface_gather<<<blocks, 256, 0, st>>>(m, subs, delta, vgam, z);
 }
 
@@ -171,6 +176,7 @@ __global__ void k_check_alpha(const double* __restrict__ a, long long n, int* er
 
 void launch_check_alpha(const double* alpha, long long n, int* err, cudaStream_t st) {
   int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  BDDC_COUNT(1);
   k_check_alpha<<<blocks, 256, 0, st>>>(alpha, n, err);
 }
 
@@ -187,6 +193,7 @@ __global__ void k_masked_copy(MeshDev m, const double* __restrict__ src, double*
 void launch_masked_copy(const MeshDev& m, const double* src, double* dst, cudaStream_t st) {
   long long N = (long long)m.NX * m.NY * m.NZ;
   int blocks = (int)std::min<long long>((N + 255) / 256, 152 * 16);
+  BDDC_COUNT(1);
   k_masked_copy<<<blocks, 256, 0, st>>>(m, src, dst);
 }
 
