@@ -168,6 +168,27 @@ int bddc_get_coarse_basis(const bddc_handle* h, int sub, double* phi_host,
  * factorisation) to host memory; BDDC_ERR_UNSUPPORTED if it was not kept. */
 int bddc_get_coarse_matrix(const bddc_handle* h, double* ac_host);
 
+/* z = B r like bddc_apply, for callers that must not allocate device memory
+ * while applying the preconditioner (code running under another framework's
+ * memory pool, or solver loops that may not touch the CUDA allocator between
+ * iterations).  The paper has no counterpart: this is a property of the
+ * library.  It calls no cudaMalloc or cudaFree; all work vectors of the apply
+ * live in one fixed 32 MiB device array that every GPU loading the library
+ * holds until the process exits, and the handle's own buffers are not used.
+ * Limits and behaviour:
+ *   - problems whose apply work space exceeds 32 MiB (about 1.5 million mesh
+ *     nodes in FP64) are rejected with BDDC_ERR_ARG and a message giving the
+ *     size needed;
+ *   - the first call on each device looks up the array's device address; make
+ *     that first call before any stream capture;
+ *   - every call, on every handle of the device, shares the one array, so
+ *     calls whose GPU work overlaps (different streams, or concurrent host
+ *     threads) race: order them on one stream;
+ *   - the array keeps the last call's contents; each call clears what it needs
+ *     zeroed.
+ * Arguments as for bddc_apply. */
+int bddc_apply_noalloc(bddc_handle* h, const double* r_dev, double* z_dev, void* stream);
+
 /* Frees every device and host resource of the handle (NULL is a no-op). */
 int bddc_destroy(bddc_handle* h);
 

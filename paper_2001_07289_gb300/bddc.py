@@ -65,6 +65,7 @@ def _load():
     lib.bddc_setup.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), vp, vp,
                                C.POINTER(vp)]
     lib.bddc_apply.argtypes = [vp, vp, vp, vp]
+    lib.bddc_apply_noalloc.argtypes = [vp, vp, vp, vp]
     lib.bddc_operator.argtypes = [vp, vp, vp, vp]
     lib.pcg_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(Stats), vp]
     lib.bddc_gradient.argtypes = [vp, vp, vp, vp, vp]
@@ -77,7 +78,7 @@ def _load():
     lib.bddc_destroy.argtypes = [vp]
     lib.bddc_last_error.argtypes = [vp]
     lib.bddc_last_error.restype = C.c_char_p
-    for f in ("bddc_setup", "bddc_apply", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
+    for f in ("bddc_setup", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
               "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy"):
         getattr(lib, f).restype = C.c_int
     return lib
@@ -85,7 +86,7 @@ def _load():
 
 lib = _load()
 
-EXPORTS = ("bddc_setup", "bddc_apply", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
+EXPORTS = ("bddc_setup", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
            "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
            "bddc_last_error")
 
@@ -149,6 +150,13 @@ class BDDC:
     def apply(self, r: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         z = out if out is not None else self._vec()
         _check(lib.bddc_apply(self._handle, _ptr(r), _ptr(z), _stream()), self._handle)
+        return z
+
+    def apply_noalloc(self, r: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """bddc_apply_noalloc: the same z = B r with the library's fixed device
+        array as work space (no device allocation inside the call)."""
+        z = out if out is not None else self._vec()
+        _check(lib.bddc_apply_noalloc(self._handle, _ptr(r), _ptr(z), _stream()), self._handle)
         return z
 
     def operator(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:

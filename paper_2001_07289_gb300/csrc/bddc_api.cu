@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -140,6 +141,7 @@ struct bddc_handle {
   int* err = nullptr;
   double* pinned = nullptr;
   int hist_cap = 0;
+  long long n_surface_total = 0, n_local_nodes_total = 0;  // sizes of vgam and vloc
   float setup_ms = 0.f;
   float phase_ms[6] = {0, 0, 0, 0, 0, 0};
   long long launch_base = 0;
@@ -404,6 +406,8 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   const bool dbl = h->local_double;
   const size_t es = dbl ? sizeof(double) : sizeof(float);
   Layout lay = layout_of(h);
+  h->n_surface_total = lay.B;
+  h->n_local_nodes_total = lay.Vec;
   LocalLaunch& L = h->L;
   L.m = m;
   L.alpha = h->alpha;
@@ -795,4 +799,103 @@ extern "C" int bddc_destroy(bddc_handle* h) {
 
 extern "C" const char* bddc_last_error(const bddc_handle* h) {
   return h ? h->error.c_str() : g_setup_error.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free preconditioner apply.
+//
+// Some callers cannot call cudaMalloc while they apply the preconditioner:
+// code running under another framework's stream-ordered memory pool that
+// forbids foreign allocations, or solver loops that must not touch the CUDA
+// allocator between iterations.  For them bddc_apply_noalloc runs the same
+// kernels as bddc_apply but takes every work vector of the apply from one
+// file-scope device array of fixed size instead of the handle's buffers.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = 32u << 20;  // 32 MiB, held by every GPU that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[256] = {nullptr};
+
+// Device address of the array on `dev` (host code cannot use the symbol
+// itself).  Looked up once per device, with that device current.
+void* noalloc_scratch(int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (dev < 0 || dev >= 256) throw BddcError(BDDC_ERR_ARG, "device ordinal out of range");
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      throw BddcError(BDDC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = ptr;
+  }
+  return g_noalloc_addr[dev];
+}
+
+size_t carve(size_t& off, size_t bytes) {
+  size_t at = off;
+  off = (off + bytes + 255) & ~(size_t)255;
+  return at;
+}
+
+template <typename T>
+void apply_noalloc_impl(bddc_handle* h, unsigned char* base, const double* r, double* z, cudaStream_t st) {
+  const long long N = h->n_nodes;
+  const int nc = h->n_coarse;
+  size_t off = 0;
+  double* uI = (double*)(base + carve(off, sizeof(double) * N));
+  double* t = (double*)(base + carve(off, sizeof(double) * N));
+  double* rc = (double*)(base + carve(off, sizeof(double) * std::max(nc, 1)));
+  double* cy = (double*)(base + carve(off, sizeof(double) * std::max(nc, 1)));
+  double* uc = (double*)(base + carve(off, sizeof(double) * std::max(nc, 1)));
+  LocalLaunch L = h->L;
+  L.rcl = (double*)(base + carve(off, sizeof(double) * std::max<size_t>(h->lc.size(), 1)));
+  L.vgam = (double*)(base + carve(off, sizeof(double) * std::max<long long>(h->n_surface_total, 1)));
+  L.vloc = base + carve(off, sizeof(T) * std::max<long long>(h->n_local_nodes_total, 1));
+  // the array keeps the previous call's contents; the interior solve writes
+  // only interior nodes, so the rest of uI must start at zero
+  CK(cudaMemsetAsync(uI, 0, sizeof(double) * N, st));
+  launch_dirichlet<T>(L, r, nullptr, uI, 0, st);
+  launch_operator(h->m, h->alpha, uI, t, nullptr, RED_BLOCKS, st);
+  launch_neumann<T>(L, r, t, st);
+  launch_coarse_gather(h->cptr, h->cent, L.rcl, rc, nc, st);
+  launch_coarse_solve(h->Acg, nc, h->dinv, rc, cy, uc, st);
+  launch_neumann_finish<T>(L, uc, st);
+  launch_interface_gather(h->m, L.subs, L.delta, L.vgam, z, st);
+  launch_operator(h->m, h->alpha, z, t, nullptr, RED_BLOCKS, st);
+  launch_dirichlet<T>(L, r, t, z, 1, st);
+}
+
+size_t noalloc_bytes_needed(const bddc_handle* h) {
+  const size_t es = h->local_double ? sizeof(double) : sizeof(float);
+  size_t off = 0;
+  carve(off, sizeof(double) * h->n_nodes);
+  carve(off, sizeof(double) * h->n_nodes);
+  for (int k = 0; k < 3; ++k) carve(off, sizeof(double) * std::max(h->n_coarse, 1));
+  carve(off, sizeof(double) * std::max<size_t>(h->lc.size(), 1));
+  carve(off, sizeof(double) * std::max<long long>(h->n_surface_total, 1));
+  carve(off, es * std::max<long long>(h->n_local_nodes_total, 1));
+  return off;
+}
+
+}  // namespace
+
+extern "C" int bddc_apply_noalloc(bddc_handle* h, const double* r_dev, double* z_dev, void* stream) {
+  if (!h) return BDDC_ERR_ARG;
+  ABI_BEGIN
+  if (!r_dev || !z_dev || r_dev == z_dev) throw BddcError(BDDC_ERR_ARG, "bad vectors");
+  const size_t need = noalloc_bytes_needed(h);
+  if (need > kNoAllocBytes)
+    throw BddcError(BDDC_ERR_ARG, "bddc_apply_noalloc: this problem needs " + std::to_string(need) +
+                                      " bytes of work space, above the fixed maximum of " +
+                                      std::to_string(kNoAllocBytes) + " bytes; use bddc_apply");
+  CK(cudaSetDevice(h->device));
+  unsigned char* base = (unsigned char*)noalloc_scratch(h->device);
+  if (h->local_double) apply_noalloc_impl<double>(h, base, r_dev, z_dev, (cudaStream_t)stream);
+  else apply_noalloc_impl<float>(h, base, r_dev, z_dev, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return BDDC_OK;
+  ABI_END(h)
 }
