@@ -106,7 +106,31 @@ typedef struct {
                              5 coarse Cholesky                                 */
     long long launches;   /* kernels launched for this handle since its setup
                              began (setup, applies, solves, gradients)        */
+    double coarse_fma;    /* multiply-adds of the coarse factorisation         */
+    double local_factor_fma;  /* multiply-adds of the local plane-block factorisations */
+    long long apply_bytes;    /* bytes one bddc_apply must read from HBM: local
+                                 factors (Dirichlet twice), Phi twice, coarse fronts */
 } bddc_info_t;
+
+/* Host-only analysis of a problem, no GPU needed: the counts that bddc_setup
+ * would produce for the same arguments. */
+typedef struct {
+    int n_sub;            /* subdomains                                        */
+    int n_coarse;         /* coarse DOFs: vertices + edges + faces of Theta-hat on Gamma */
+    int n_vertices, n_edges, n_faces;  /* by object type (points on 3/2/1 axes) */
+    int max_local_coarse; /* largest n_c,i                                     */
+    int n_fronts;         /* fronts of the nested-dissection coarse Cholesky   */
+    int n_levels;         /* depth of its front tree                           */
+    int max_front;        /* largest front (pivots + update set)               */
+    long long front_entries;  /* sum of squared front sizes (FP64 storage)    */
+    double coarse_fma;    /* multiply-adds of the coarse factorisation         */
+} bddc_analysis_t;
+
+/* Partition, sub-partition (Section 3 remark on local subdivision), object
+ * classification and the coarse elimination plan, on the host.  Errors:
+ * BDDC_ERR_ARG for invalid sizes, cuts or options. */
+int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part,
+                 const bddc_options* opt, bddc_analysis_t* out);
 
 /* Builds the BDDC-SO preconditioner (Section 3; Definition 1 with V1 = U_I,
  * Q1 = I, V2 = W-tilde, Q2 = (I - P)E): sub-partition and (sub)object

@@ -53,7 +53,15 @@ class Info(C.Structure):
     _fields_ = [("n_sub", C.c_int), ("n_coarse", C.c_int), ("n_vertices", C.c_int),
                 ("max_local_coarse", C.c_int), ("n_free", C.c_longlong), ("bytes", C.c_longlong),
                 ("factor_bytes", C.c_longlong), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 6),
-                ("launches", C.c_longlong)]
+                ("launches", C.c_longlong), ("coarse_fma", C.c_double), ("local_factor_fma", C.c_double),
+                ("apply_bytes", C.c_longlong)]
+
+
+class Analysis(C.Structure):
+    _fields_ = [("n_sub", C.c_int), ("n_coarse", C.c_int), ("n_vertices", C.c_int), ("n_edges", C.c_int),
+                ("n_faces", C.c_int), ("max_local_coarse", C.c_int), ("n_fronts", C.c_int),
+                ("n_levels", C.c_int), ("max_front", C.c_int), ("front_entries", C.c_longlong),
+                ("coarse_fma", C.c_double)]
 
 
 def _load():
@@ -72,13 +80,14 @@ def _load():
     lib.bddc_solve_host.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), dp, dp, dp,
                                     C.c_double, C.POINTER(Stats)]
     lib.bddc_get_info.argtypes = [vp, C.POINTER(Info)]
+    lib.bddc_analyze.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), C.POINTER(Analysis)]
     lib.bddc_get_coarse_basis.argtypes = [vp, ip, dp, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.bddc_get_coarse_matrix.argtypes = [vp, dp]
     lib.bddc_destroy.argtypes = [vp]
     lib.bddc_last_error.argtypes = [vp]
     lib.bddc_last_error.restype = C.c_char_p
-    for f in ("bddc_setup", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
+    for f in ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
               "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy"):
         getattr(lib, f).restype = C.c_int
     return lib
@@ -86,7 +95,7 @@ def _load():
 
 lib = _load()
 
-EXPORTS = ("bddc_setup", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
+EXPORTS = ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
            "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
            "bddc_last_error")
 
@@ -120,6 +129,15 @@ def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph):
     wts = {"card": BDDC_W_CARD, "rho": BDDC_W_RHO}[weights] if isinstance(weights, str) else weights
     opt = Options(prec, wts, L, BDDC_SEL_VEF, int(use_graph), maxit)
     return mesh, part, opt, keep
+
+
+def analyze(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int, h: float = 0.0,
+            precision="fp64", weights="card") -> dict:
+    """bddc_analyze: host-only counts of objects and of the coarse elimination plan."""
+    mesh, part, opt, keep = _structs(nx, ny, nz, h if h > 0 else 1.0 / nx, cuts, L, precision, weights, 2000, False)
+    out = Analysis()
+    _check(lib.bddc_analyze(C.byref(mesh), C.byref(part), C.byref(opt), C.byref(out)), None)
+    return {k: getattr(out, k) for k, _ in Analysis._fields_}
 
 
 class BDDC:

@@ -130,11 +130,13 @@ struct bddc_handle {
   std::vector<void*> allocs;
   size_t bytes = 0, factor_bytes = 0;
   double* alpha = nullptr;       // private copy of alpha
-  double *Acg = nullptr, *Ac_copy = nullptr, *dinv = nullptr, *cscratch = nullptr;
+  double* Ac_copy = nullptr;      // dense coarse matrix, kept for small problems (diagnostics)
+  CoarseGeom geom;
+  MFPlan mf;
   int *cptr = nullptr, *color_subs = nullptr;
   int2* cent = nullptr;
   int color_count[8] = {0}, color_off[8] = {0};
-  double *rc = nullptr, *cy = nullptr, *uc = nullptr;
+  double *rc = nullptr, *uc = nullptr;
   double *uI = nullptr, *t = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *partial = nullptr, *scal = nullptr, *hist_a = nullptr, *hist_b = nullptr;
   int* flag = nullptr;
@@ -214,6 +216,16 @@ void build_metadata(bddc_handle* h) {
         }
   h->n_coarse = nc;
   h->n_vertices = nvert;
+  for (int d = 0; d < 3; ++d) {
+    h->geom.nitem[d] = nit[d];
+    h->geom.nsub[d] = nsub[d];
+    h->geom.slab_item_lo[d].clear();
+    h->geom.slab_item_hi[d].clear();
+    for (int sl = 0; sl < nsub[d]; ++sl) {
+      h->geom.slab_item_lo[d].push_back(h->ax[d].item[h->ax[d].slab_lo[sl]]);
+      h->geom.slab_item_hi[d].push_back(h->ax[d].item[h->ax[d].slab_hi[sl]]);
+    }
+  }
   // subdomains
   const int S = nsub[0] * nsub[1] * nsub[2];
   h->subs.assign(S, SubDesc{});
@@ -270,8 +282,8 @@ void build_metadata(bddc_handle* h) {
         const int qx = s.w[0] - 1, qy = s.w[1] - 1, qz = s.w[2] - 1;
         const bool hasI = qx > 0 && qy > 0 && qz > 0;
         const int QD = hasI ? qx * qy : 0, nzD = hasI ? qz : 0;
-        s.offD = offD; offD += hasI ? (long long)(2 * nzD - 1) * QD * QD : 0;
-        s.offN = offN; offN += (long long)(2 * pz - 1) * QN * QN;
+        s.offD = offD; offD += hasI ? (long long)(2 * nzD - 1) * slot_stride(QD) : 0;
+        s.offN = offN; offN += (long long)(2 * pz - 1) * slot_stride(QN);
         s.offW = offW; offW += 2LL * QN * QN + 1024LL * ((std::max(QN, s.na) + 31) / 32);
         s.offY = offY; offY += (long long)NN * s.nc;
         s.offG = offG; offG += (long long)s.na * s.nc;
@@ -279,7 +291,7 @@ void build_metadata(bddc_handle* h) {
         s.offPA = offPA; offPA += (long long)NN * s.na;
         s.offSc = offSc; offSc += (long long)s.na * s.na;
         s.offAc = offAc; offAc += (long long)s.nc * s.nc;
-        s.offPhi = offPhi; offPhi += (long long)s.nB * s.nc;
+        s.offPhi = offPhi; offPhi += padded((long long)s.nB * s.nc);
         s.offB = offB; offB += s.nB;
         s.offVec = offVec; offVec += NN;
         L.maxQD = std::max(L.maxQD, QD); L.maxNzD = std::max(L.maxNzD, nzD); L.maxND = std::max(L.maxND, QD * nzD);
@@ -297,6 +309,7 @@ void build_metadata(bddc_handle* h) {
     ptr[g + 1] = ptr[g] + (int)owners[g].size();
     for (auto e : owners[g]) ent.push_back(e);
   }
+  h->geom.objid = std::move(objid);
   // colour lists
   std::vector<int> clist;
   for (int c = 0; c < 8; ++c) {
@@ -329,8 +342,8 @@ Layout layout_of(const bddc_handle* h) {
     const int qx = s.w[0] - 1, qy = s.w[1] - 1, qz = s.w[2] - 1;
     const bool hasI = qx > 0 && qy > 0 && qz > 0;
     const int QD = hasI ? qx * qy : 0;
-    o.D = std::max(o.D, s.offD + (hasI ? (long long)(2 * qz - 1) * QD * QD : 0));
-    o.N = std::max(o.N, s.offN + (long long)(2 * pz - 1) * QN * QN);
+    o.D = std::max(o.D, s.offD + (hasI ? (long long)(2 * qz - 1) * slot_stride(QD) : 0));
+    o.N = std::max(o.N, s.offN + (long long)(2 * pz - 1) * slot_stride(QN));
     o.W = std::max(o.W, s.offW + 2LL * QN * QN + 1024LL * ((std::max(QN, s.na) + 31) / 32));
     o.Y = std::max(o.Y, s.offY + (long long)NN * s.nc);
     o.G = std::max(o.G, s.offG + (long long)s.na * s.nc);
@@ -338,7 +351,7 @@ Layout layout_of(const bddc_handle* h) {
     o.PA = std::max(o.PA, s.offPA + (long long)NN * s.na);
     o.Sc = std::max(o.Sc, s.offSc + (long long)s.na * s.na);
     o.Ac = std::max(o.Ac, s.offAc + (long long)s.nc * s.nc);
-    o.Phi = std::max(o.Phi, s.offPhi + (long long)s.nB * s.nc);
+    o.Phi = std::max(o.Phi, s.offPhi + padded((long long)s.nB * s.nc));
     o.B = std::max(o.B, s.offB + s.nB);
     o.Vec = std::max(o.Vec, s.offVec + NN);
   }
@@ -369,6 +382,16 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->n_nodes = (long long)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
   h->n_free = (long long)(M.nx - 1) * (M.ny - 1) * (M.nz - 1);
   build_metadata(h);
+  {
+    // the apply streams rows of plane blocks and of Phi through 32 KiB chunks
+    // (at least 4 rows each) and keeps one subdomain's vectors in shared memory
+    const int es = h->local_double ? 8 : 4;
+    const LocalLaunch& L = h->L;
+    const size_t smem = (size_t)4 * 32768 + 32 + 8 * (L.maxNB + 1) + (size_t)es * (L.maxNN + 2 * L.maxQN + 2);
+    if ((size_t)L.maxQN * es * 4 > 32768 || (size_t)L.maxNc * es * 4 > 32768 || smem > 227 * 1024)
+      throw BddcError(BDDC_ERR_UNSUPPORTED, "subdomains too large for the streamed local solves "
+                                            "(at most 1024 FP64 / 2048 FP32 nodes per plane and 1024 coarse DOFs)");
+  }
   h->launch_base = g_launches;
   // events: 0 start, 1 weights done, 2 Dirichlet, 3 Neumann, 4 basis, 5 assembly, 6 coarse factor
   cudaEvent_t ev[7];
@@ -456,26 +479,23 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->cptr = upload(h, h->h_cptr, st);
   h->cent = upload(h, h->h_cent, st);
   h->color_subs = upload(h, h->h_clist, st);
-  h->Acg = h->dnew<double>((size_t)nc * nc);
-  h->factor_bytes += sizeof(double) * (size_t)nc * nc;
-  CK(cudaMemsetAsync(h->Acg, 0, sizeof(double) * (size_t)nc * nc, st));
-  launch_coarse_assemble(L, h->color_subs, h->color_count, h->color_off, h->Acg, nc, st);
-  CK(cudaEventRecord(ev[5], st));
-  if ((long long)nc * nc <= (1LL << 22)) {
+  if ((long long)nc * nc <= (1LL << 22)) {   // dense copy for bddc_get_coarse_matrix
     h->Ac_copy = h->dnew<double>((size_t)nc * nc);
-    CK(cudaMemcpyAsync(h->Ac_copy, h->Acg, sizeof(double) * (size_t)nc * nc, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(h->Ac_copy, 0, sizeof(double) * (size_t)nc * nc, st));
+    launch_coarse_assemble(L, h->color_subs, h->color_count, h->color_off, h->Ac_copy, nc, st);
   }
-  const int ntile = (nc + CNB - 1) / CNB;
-  h->dinv = h->dnew<double>((size_t)ntile * CNB * CNB);
-  h->cscratch = (double*)h->dalloc(sizeof(double) * std::max<size_t>((size_t)ntile * CNB * CNB, 4096), true);
-  configure_coarse_kernels();
-  launch_coarse_factor(h->Acg, nc, h->dinv, h->cscratch, h->err, st);
+  mf_plan(h->mf, h->geom, nc);
+  mf_upload(h->mf, [h](size_t b) { return h->dalloc(b); }, st);
+  h->factor_bytes += sizeof(double) * (size_t)(h->mf.fpool + h->mf.dpool);
+  configure_mf_kernels();
+  mf_assemble(h->mf, L, h->color_subs, h->color_count, h->color_off, st);
+  CK(cudaEventRecord(ev[5], st));
+  mf_factor(h->mf, h->err, st);
   CK(cudaEventRecord(ev[6], st));
   CK(cudaGetLastError());
   // apply / PCG work vectors
   const long long N = h->n_nodes;
   h->rc = h->dnew<double>(std::max(nc, 1));
-  h->cy = h->dnew<double>(std::max(nc, 1));
   h->uc = h->dnew<double>(std::max(nc, 1));
   h->uI = h->dnew<double>(N);
   CK(cudaMemsetAsync(h->uI, 0, sizeof(double) * N, st));
@@ -512,7 +532,7 @@ void apply_impl(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
   launch_operator(h->m, h->alpha, h->uI, h->t, nullptr, RED_BLOCKS, st);  // A u_I
   launch_neumann<T>(L, r, h->t, st);                                   // r_i, Phi^T r_i, y
   launch_coarse_gather(h->cptr, h->cent, L.rcl, h->rc, h->n_coarse, st);
-  launch_coarse_solve(h->Acg, h->n_coarse, h->dinv, h->rc, h->cy, h->uc, st);
+  mf_solve(h->mf, h->rc, h->uc, h->mf.W, st);                          // A_c u_c = r_c
   launch_neumann_finish<T>(L, h->uc, st);                              // v_i on the surface
   launch_interface_gather(h->m, L.subs, L.delta, L.vgam, z, st);       // E v
   launch_operator(h->m, h->alpha, z, h->t, nullptr, RED_BLOCKS, st);   // A (E v)
@@ -613,13 +633,10 @@ int pcg_impl(bddc_handle* h, const double* b, double* x, double rtol, bddc_stats
     return BDDC_ERR_CUDA;                                             \
   }
 
-extern "C" int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt,
-                          const double* alpha_dev, void* stream, bddc_handle** out) {
-  bddc_handle* hnull = nullptr;
-  ABI_BEGIN
-  if (!out) throw BddcError(BDDC_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  if (!mesh || !part || !opt || !alpha_dev) throw BddcError(BDDC_ERR_ARG, "NULL argument");
+namespace {
+// Validates the arguments and builds the per-axis tables of a new handle.
+std::unique_ptr<bddc_handle> make_handle(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt) {
+  if (!mesh || !part || !opt) throw BddcError(BDDC_ERR_ARG, "NULL argument");
   if (mesh->nx < 2 || mesh->ny < 2 || mesh->nz < 2) throw BddcError(BDDC_ERR_ARG, "need at least 2 elements per axis");
   if ((long long)mesh->nx * mesh->ny * mesh->nz > (1LL << 31)) throw BddcError(BDDC_ERR_ARG, "mesh too large");
   if (opt->L_elems < 1) throw BddcError(BDDC_ERR_ARG, "L must be >= 1");
@@ -639,9 +656,50 @@ extern "C" int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, con
   for (int d = 0; d < 3; ++d)
     for (size_t s = 0; s < h->ax[d].slab_lo.size(); ++s)
       if (h->ax[d].slab_hi[s] - h->ax[d].slab_lo[s] > 4000) throw BddcError(BDDC_ERR_ARG, "subdomain too wide");
+  return h;
+}
+}  // namespace
+
+extern "C" int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt,
+                          const double* alpha_dev, void* stream, bddc_handle** out) {
+  bddc_handle* hnull = nullptr;
+  ABI_BEGIN
+  if (!out) throw BddcError(BDDC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!alpha_dev) throw BddcError(BDDC_ERR_ARG, "NULL argument");
+  std::unique_ptr<bddc_handle> h = make_handle(mesh, part, opt);
   cudaStream_t st = (cudaStream_t)stream;
   do_setup(h.get(), alpha_dev, st);
   *out = h.release();
+  return BDDC_OK;
+  ABI_END(hnull)
+}
+
+extern "C" int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt,
+                            bddc_analysis_t* out) {
+  bddc_handle* hnull = nullptr;
+  ABI_BEGIN
+  if (!out) throw BddcError(BDDC_ERR_ARG, "out is NULL");
+  std::unique_ptr<bddc_handle> h = make_handle(mesh, part, opt);
+  build_metadata(h.get());
+  mf_plan(h->mf, h->geom, h->n_coarse);
+  *out = bddc_analysis_t{};
+  out->n_sub = (int)h->subs.size();
+  out->n_coarse = h->n_coarse;
+  const int* nit = h->geom.nitem;
+  for (int iz = 0; iz < nit[2]; ++iz)
+    for (int iy = 0; iy < nit[1]; ++iy)
+      for (int ix = 0; ix < nit[0]; ++ix)
+        if (h->geom.objid[ix + (long long)nit[0] * (iy + (long long)nit[1] * iz)] >= 0) {
+          int pts = !(ix & 1) + !(iy & 1) + !(iz & 1);
+          if (pts == 3) ++out->n_vertices; else if (pts == 2) ++out->n_edges; else ++out->n_faces;
+        }
+  out->max_local_coarse = h->max_nc;
+  out->n_fronts = h->mf.nfront;
+  out->n_levels = h->mf.nlevel;
+  for (int f = 0; f < h->mf.nfront; ++f) out->max_front = std::max(out->max_front, h->mf.np[f] + h->mf.nu[f]);
+  out->front_entries = h->mf.fpool;
+  out->coarse_fma = h->mf.flops;
   return BDDC_OK;
   ABI_END(hnull)
 }
@@ -744,6 +802,28 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   info->setup_ms = h->setup_ms;
   for (int k = 0; k < 6; ++k) info->phase_ms[k] = h->phase_ms[k];
   info->launches = g_launches - h->launch_base;
+  info->coarse_fma = h->mf.flops;
+  // local factorisation work and the bytes one apply has to stream: per
+  // subdomain and plane the inverse diagonal factor (lower half) and the
+  // sub-diagonal block, read twice per solve (forward and backward sweeps)
+  double fma = 0.0;
+  long long bytes = 0;
+  const int es = h->local_double ? 8 : 4;
+  for (const SubDesc& s : h->subs) {
+    const double QN = (double)(s.w[0] + 1) * (s.w[1] + 1), nzN = s.w[2] + 1;
+    const double QD = (s.w[0] > 1 && s.w[1] > 1 && s.w[2] > 1) ? (double)(s.w[0] - 1) * (s.w[1] - 1) : 0.0;
+    const double nzD = QD > 0 ? s.w[2] - 1 : 0;
+    fma += nzN * (QN * QN * QN * (1.0 + 0.5 + 1.0 / 3.0)) + nzD * (QD * QD * QD * (1.0 + 0.5 + 1.0 / 3.0));
+    const double perN = (nzN * QN * (QN + 1) / 2 + (nzN - 1) * QN * QN) * es;
+    const double perD = (nzD * QD * (QD + 1) / 2 + std::max(nzD - 1, 0.0) * QD * QD) * es;
+    bytes += (long long)(2 * perN + 4 * perD + 2.0 * s.nB * s.nc * es);
+  }
+  for (int f = 0; f < h->mf.nfront; ++f) {
+    const long long np = h->mf.np[f], nu = h->mf.nu[f];
+    bytes += 2 * 8 * (np * (np + 1) / 2 + nu * np);
+  }
+  info->local_factor_fma = fma;
+  info->apply_bytes = bytes;
   return BDDC_OK;
 }
 
@@ -848,8 +928,8 @@ void apply_noalloc_impl(bddc_handle* h, unsigned char* base, const double* r, do
   double* uI = (double*)(base + carve(off, sizeof(double) * N));
   double* t = (double*)(base + carve(off, sizeof(double) * N));
   double* rc = (double*)(base + carve(off, sizeof(double) * std::max(nc, 1)));
-  double* cy = (double*)(base + carve(off, sizeof(double) * std::max(nc, 1)));
   double* uc = (double*)(base + carve(off, sizeof(double) * std::max(nc, 1)));
+  double* wf = (double*)(base + carve(off, sizeof(double) * std::max<long long>(h->mf.wpool, 1)));
   LocalLaunch L = h->L;
   L.rcl = (double*)(base + carve(off, sizeof(double) * std::max<size_t>(h->lc.size(), 1)));
   L.vgam = (double*)(base + carve(off, sizeof(double) * std::max<long long>(h->n_surface_total, 1)));
@@ -861,7 +941,7 @@ void apply_noalloc_impl(bddc_handle* h, unsigned char* base, const double* r, do
   launch_operator(h->m, h->alpha, uI, t, nullptr, RED_BLOCKS, st);
   launch_neumann<T>(L, r, t, st);
   launch_coarse_gather(h->cptr, h->cent, L.rcl, rc, nc, st);
-  launch_coarse_solve(h->Acg, nc, h->dinv, rc, cy, uc, st);
+  mf_solve(h->mf, rc, uc, wf, st);
   launch_neumann_finish<T>(L, uc, st);
   launch_interface_gather(h->m, L.subs, L.delta, L.vgam, z, st);
   launch_operator(h->m, h->alpha, z, t, nullptr, RED_BLOCKS, st);
@@ -873,7 +953,8 @@ size_t noalloc_bytes_needed(const bddc_handle* h) {
   size_t off = 0;
   carve(off, sizeof(double) * h->n_nodes);
   carve(off, sizeof(double) * h->n_nodes);
-  for (int k = 0; k < 3; ++k) carve(off, sizeof(double) * std::max(h->n_coarse, 1));
+  for (int k = 0; k < 2; ++k) carve(off, sizeof(double) * std::max(h->n_coarse, 1));
+  carve(off, sizeof(double) * std::max<long long>(h->mf.wpool, 1));
   carve(off, sizeof(double) * std::max<size_t>(h->lc.size(), 1));
   carve(off, sizeof(double) * std::max<long long>(h->n_surface_total, 1));
   carve(off, es * std::max<long long>(h->n_local_nodes_total, 1));

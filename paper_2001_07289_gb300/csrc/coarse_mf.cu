@@ -1,0 +1,624 @@
+// Multifrontal FP64 Cholesky of the BDDC-SO coarse matrix.
+//
+// The coarse DOFs are the (sub)objects of Theta-hat on Gamma (Section 3); two
+// of them are coupled only through a shared subdomain, and the paper points at
+// the size of this coarse problem as BDDC-SO's cost (Sections 1 and 6).  The
+// elimination order is a nested dissection of the box-subdomain grid: a box of
+// subdomains is split at its middle Theta plane along its longest axis; the
+// objects on that plane strictly inside the box are the box's pivots (its
+// separator), eliminated after both halves.  A front holds its pivots P and
+// the objects on the closed box boundary U (all eliminated later); the
+// objects a front's pivots couple to after elimination lie in P u U.
+//
+// Numeric phase, tree level by tree level (deepest first): extend-add of the
+// children's update matrices, then a tiled right-looking partial Cholesky of
+// every front of the level at once (potrf of the 64x64 diagonal tile with its
+// explicit inverse, trsm of the tiles below it, syrk of the trailing tiles,
+// which include the update block U x U).  Solves run level by level with one
+// CTA per front.  Everything is summed in a fixed order (no atomics).
+#include <stdexcept>
+
+#include "common.cuh"
+#include "dense.cuh"
+#include "kernels.h"
+
+namespace bddc {
+
+constexpr int FNB = 64;
+
+__host__ __device__ inline int mf_ntiles(int np, int nu) { return (np + FNB - 1) / FNB + (nu + FNB - 1) / FNB; }
+__host__ __device__ inline void mf_tile(int t, int np, int nu, int& r0, int& nr) {
+  const int npt = (np + FNB - 1) / FNB;
+  if (t < npt) { r0 = t * FNB; nr = min(FNB, np - r0); }
+  else { int u = t - npt; r0 = np + u * FNB; nr = min(FNB, nu - u * FNB); }
+}
+
+// ---------------------------------------------------------------------------
+// symbolic analysis (host)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Box { int s0[3], s1[3]; };
+
+struct Builder {
+  const CoarseGeom& g;
+  MFPlan& P;
+  std::vector<std::vector<int>> piv, upd;   // per front
+  std::vector<std::vector<int>> children;
+  std::vector<int> depth;
+  Builder(const CoarseGeom& g_, MFPlan& P_) : g(g_), P(P_) {}
+
+  int obj(int ix, int iy, int iz) const { return g.objid[ix + (long long)g.nitem[0] * (iy + (long long)g.nitem[1] * iz)]; }
+
+  // item range [lo, hi] (closed) of a box along axis d
+  void range(const Box& b, int d, int& lo, int& hi) const {
+    lo = g.slab_item_lo[d][b.s0[d]];
+    hi = g.slab_item_hi[d][b.s1[d] - 1];
+  }
+
+  // returns the front id created for this box (or -1 if the box and all its
+  // descendants hold no pivots); children ids collected into `kids`.
+  void build(const Box& b, std::vector<int>& kids) {
+    int ext[3] = {b.s1[0] - b.s0[0], b.s1[1] - b.s0[1], b.s1[2] - b.s0[2]};
+    if (ext[0] <= 1 && ext[1] <= 1 && ext[2] <= 1) return;
+    int ax = 0;
+    for (int d = 1; d < 3; ++d)
+      if (ext[d] > ext[ax]) ax = d;
+    const int mid = b.s0[ax] + ext[ax] / 2;
+    const int cut_item = g.slab_item_lo[ax][mid];
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) range(b, d, lo[d], hi[d]);
+    // separator: item[ax] == cut_item, other items strictly inside the box
+    std::vector<int> sep;
+    {
+      int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+      int it[3];
+      it[ax] = cut_item;
+      for (int j = lo[a2] + 1; j < hi[a2]; ++j)
+        for (int i = lo[a1] + 1; i < hi[a1]; ++i) {
+          it[a1] = i; it[a2] = j;
+          int o = obj(it[0], it[1], it[2]);
+          if (o >= 0) sep.push_back(o);
+        }
+    }
+    Box c0 = b, c1 = b;
+    c0.s1[ax] = mid;
+    c1.s0[ax] = mid;
+    std::vector<int> my_kids;
+    build(c0, my_kids);
+    build(c1, my_kids);
+    if (sep.empty()) {  // nothing to eliminate here: the children attach to the ancestor
+      for (int k : my_kids) kids.push_back(k);
+      return;
+    }
+    // update set: valid objects on the closed box boundary
+    std::vector<int> u;
+    for (int iz = lo[2]; iz <= hi[2]; ++iz)
+      for (int iy = lo[1]; iy <= hi[1]; ++iy) {
+        const bool yz_bnd = iy == lo[1] || iy == hi[1] || iz == lo[2] || iz == hi[2];
+        for (int ix = lo[0]; ix <= hi[0]; ix = (yz_bnd || ix == hi[0]) ? ix + 1 : hi[0]) {
+          int o = obj(ix, iy, iz);
+          if (o >= 0) u.push_back(o);
+        }
+      }
+    std::sort(u.begin(), u.end());
+    const int f = (int)piv.size();
+    piv.push_back(sep);
+    upd.push_back(u);
+    children.push_back(my_kids);
+    depth.push_back(0);
+    kids.push_back(f);
+  }
+};
+
+void set_depth(Builder& B, int f, int d) {
+  B.depth[f] = d;
+  for (int c : B.children[f]) set_depth(B, c, d + 1);
+}
+
+}  // namespace
+
+void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
+  P = MFPlan();
+  P.nc = nc;
+  if (nc == 0) return;
+  Builder B(g, P);
+  Box root;
+  for (int d = 0; d < 3; ++d) { root.s0[d] = 0; root.s1[d] = g.nsub[d]; }
+  std::vector<int> tops;
+  B.build(root, tops);
+  const int nf = (int)B.piv.size();
+  P.nfront = nf;
+  P.parent.assign(nf, -1);
+  P.child_slot.assign(nf, 0);
+  for (int f = 0; f < nf; ++f)
+    for (size_t k = 0; k < B.children[f].size(); ++k) {
+      P.parent[B.children[f][k]] = f;
+      P.child_slot[B.children[f][k]] = (int)k;
+    }
+  for (int t : tops) set_depth(B, t, 0);
+  // several top fronts can exist only if the root box had no separator; they
+  // are independent and all sit at depth 0
+  P.level_of = B.depth;
+  P.nlevel = 0;
+  for (int f = 0; f < nf; ++f) P.nlevel = std::max(P.nlevel, P.level_of[f] + 1);
+  P.fronts_at_level.assign(P.nlevel, {});
+  for (int f = 0; f < nf; ++f) P.fronts_at_level[P.level_of[f]].push_back(f);
+  // elimination order: fronts are created in post-order (children first)
+  P.ord.assign(nc, -1);
+  P.fr.assign(nc, -1);
+  P.pp.assign(nc, -1);
+  int pos = 0;
+  P.np.resize(nf);
+  P.nu.resize(nf);
+  P.foff.resize(nf);
+  P.doff.resize(nf);
+  P.woff.resize(nf);
+  P.gid_off.resize(nf + 1);
+  long long fo = 0, dof = 0, wo = 0;
+  P.gid_off[0] = 0;
+  for (int f = 0; f < nf; ++f) {
+    for (size_t k = 0; k < B.piv[f].size(); ++k) {
+      int o = B.piv[f][k];
+      if (P.fr[o] != -1) throw std::runtime_error("coarse object in two separators");
+      P.ord[o] = pos++;
+      P.fr[o] = f;
+      P.pp[o] = (int)k;
+    }
+    P.np[f] = (int)B.piv[f].size();
+    P.nu[f] = (int)B.upd[f].size();
+    const long long F = P.np[f] + P.nu[f];
+    P.foff[f] = fo; fo += F * F;
+    P.doff[f] = dof; dof += (long long)((P.np[f] + FNB - 1) / FNB) * FNB * FNB;
+    P.woff[f] = wo; wo += F;
+    for (int o : B.piv[f]) P.gid.push_back(o);
+    for (int o : B.upd[f]) P.gid.push_back(o);
+    P.gid_off[f + 1] = (long long)P.gid.size();
+    const double np = P.np[f], nu = P.nu[f];
+    P.flops += np * np * np / 3.0 + nu * np * np + nu * nu * np / 2.0;
+  }
+  if (pos != nc) throw std::runtime_error("nested dissection missed coarse objects");
+  P.fpool = fo; P.dpool = dof; P.wpool = wo;
+  // child update rows -> positions in the parent front
+  P.pmap_off.assign(nf + 1, 0);
+  for (int f = 0; f < nf; ++f) {
+    const int p = P.parent[f];
+    if (p >= 0) {
+      const int* ub = P.gid.data() + P.gid_off[p] + P.np[p];
+      for (int o : B.upd[f]) {
+        int q;
+        if (P.fr[o] == p) q = P.pp[o];
+        else {
+          const int* it = std::lower_bound(ub, ub + P.nu[p], o);
+          if (it == ub + P.nu[p] || *it != o) throw std::runtime_error("update set not nested in the parent front");
+          q = P.np[p] + (int)(it - ub);
+        }
+        P.pmap.push_back(q);
+      }
+    }
+    P.pmap_off[f + 1] = (long long)P.pmap.size();
+  }
+  // work lists per (level, panel step)
+  P.step_potrf.clear(); P.step_trsm.clear(); P.step_syrk.clear();
+  P.list_len.clear();
+  for (int l = P.nlevel - 1; l >= 0; --l) {
+    int maxpt = 0;
+    for (int f : P.fronts_at_level[l]) maxpt = std::max(maxpt, (P.np[f] + FNB - 1) / FNB);
+    for (int j = 0; j < maxpt; ++j) {
+      std::vector<int> po, tr, sy;
+      for (int f : P.fronts_at_level[l]) {
+        const int npt = (P.np[f] + FNB - 1) / FNB, nt = mf_ntiles(P.np[f], P.nu[f]);
+        if (j >= npt) continue;
+        po.insert(po.end(), {f, j, j, 0});
+        for (int i = j + 1; i < nt; ++i) tr.insert(tr.end(), {f, i, j, 0});
+        for (int i = j + 1; i < nt; ++i)
+          for (int k = j + 1; k <= i; ++k) sy.insert(sy.end(), {f, i, k, j});
+      }
+      P.step_potrf.push_back(po);
+      P.step_trsm.push_back(tr);
+      P.step_syrk.push_back(sy);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// device kernels
+// ---------------------------------------------------------------------------
+struct MFDev {
+  const int *np, *nu, *gid, *fr, *pp, *ord, *pmap, *parent;
+  const long long *foff, *doff, *woff, *gid_off, *pmap_off;
+  double *F, *Dinv, *W;
+};
+
+__device__ inline int mf_pos(const MFDev& d, int f, int o) {
+  if (d.fr[o] == f) return d.pp[o];
+  const int np = d.np[f], nu = d.nu[f];
+  const int* ub = d.gid + d.gid_off[f] + np;
+  int lo = 0, hi = nu - 1;
+  while (lo <= hi) {
+    int m = (lo + hi) >> 1;
+    int v = ub[m];
+    if (v == o) return np + m;
+    if (v < o) lo = m + 1; else hi = m - 1;
+  }
+  return -1;  // not reached for a consistent plan
+}
+
+// original entries of the subdomain coarse matrices, one launch per colour
+__global__ void k_mf_assemble(MFDev d, const SubDesc* __restrict__ subs, const LocalCoarse* __restrict__ lc,
+                              const int* __restrict__ list, const double* __restrict__ Ac) {
+  const SubDesc s = subs[list[blockIdx.x]];
+  const int n = s.nc;
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < n * n; e += gridDim.y * blockDim.x) {
+    const int a = e / n, b = e % n;
+    const int ga = lc[s.cofs + a].gid, gb = lc[s.cofs + b].gid;
+    const int f = d.fr[d.ord[ga] <= d.ord[gb] ? ga : gb];
+    const int ra = mf_pos(d, f, ga), rb = mf_pos(d, f, gb);
+    if (ra < 0 || rb < 0) continue;
+    const long long F = d.np[f] + d.nu[f];
+    d.F[d.foff[f] + ra * F + rb] += Ac[s.offAc + e];
+  }
+}
+
+// child update matrices (lower triangle) into the parents; one launch per slot
+__global__ void k_mf_extend_add(MFDev d, const int* __restrict__ kids) {
+  const int c = kids[blockIdx.x];
+  const int p = d.parent[c];
+  const int npc = d.np[c], nuc = d.nu[c];
+  const long long Fc = npc + nuc, Fp = d.np[p] + d.nu[p];
+  const int* map = d.pmap + d.pmap_off[c];
+  const double* C = d.F + d.foff[c];
+  double* Pm = d.F + d.foff[p];
+  const long long tri = (long long)nuc * (nuc + 1) / 2;
+  for (long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x; e < tri; e += (long long)gridDim.y * blockDim.x) {
+    // e -> (i, j) with j <= i
+    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((long long)i * (i + 1) / 2 > e) --i;
+    while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
+    const int j = (int)(e - (long long)i * (i + 1) / 2);
+    const int pi = map[i], pj = map[j];
+    const int r = max(pi, pj), q = min(pi, pj);
+    Pm[(long long)r * Fp + q] += C[(long long)(npc + i) * Fc + npc + j];
+  }
+}
+
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_mf_potrf(MFDev d, const int4* __restrict__ work, double* scratch, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
+  const int4 w = work[blockIdx.x];
+  const int f = w.x, j = w.y;
+  const int np = d.np[f], nu = d.nu[f];
+  const long long F = np + nu;
+  int r0, nr;
+  mf_tile(j, np, nu, r0, nr);
+  double* A = d.F + d.foff[f];
+  bool ok = cta_chol_inv<double>(A + r0 * F + r0, (int)F, d.Dinv + d.doff[f] + (long long)j * FNB * FNB, FNB, nr,
+                                 scratch + (long long)blockIdx.x * 2 * 1024, sm);
+  if (!ok && threadIdx.x == 0)
+    if (atomicCAS(err, 0, 5) == 0) err[1] = f;
+}
+
+// A[i,j] <- A[i,j] Dinv_j^T (tile in shared memory)
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_mf_trsm(MFDev d, const int4* __restrict__ work) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  double* T = reinterpret_cast<double*>(smraw);       // FNB x (FNB+1)
+  double* D = T + FNB * (FNB + 1);                    // FNB x (FNB+1)
+  const int4 w = work[blockIdx.x];
+  const int f = w.x, i = w.y, j = w.z;
+  const int np = d.np[f], nu = d.nu[f];
+  const long long F = np + nu;
+  int ri, ni, rj, nj;
+  mf_tile(i, np, nu, ri, ni);
+  mf_tile(j, np, nu, rj, nj);
+  double* A = d.F + d.foff[f];
+  const double* Dg = d.Dinv + d.doff[f] + (long long)j * FNB * FNB;
+  for (int e = threadIdx.x; e < FNB * FNB; e += blockDim.x) {
+    int r = e / FNB, c = e % FNB;
+    T[r * (FNB + 1) + c] = (r < ni && c < nj) ? A[(ri + r) * F + rj + c] : 0.0;
+    D[r * (FNB + 1) + c] = (r < nj && c < nj) ? Dg[r * FNB + c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ni * nj; e += blockDim.x) {
+    int r = e / nj, c = e % nj;
+    double s = 0.0;
+    for (int k = 0; k <= c; ++k) s = fma(T[r * (FNB + 1) + k], D[c * (FNB + 1) + k], s);
+    A[(ri + r) * F + rj + c] = s;
+  }
+}
+
+// A[i,l] -= A[i,j] A[l,j]^T
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_mf_syrk(MFDev d, const int4* __restrict__ work) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
+  const int4 w = work[blockIdx.x];
+  const int f = w.x, i = w.y, l = w.z, j = w.w;
+  const int np = d.np[f], nu = d.nu[f];
+  const long long F = np + nu;
+  int ri, ni, rl, nl, rj, nj;
+  mf_tile(i, np, nu, ri, ni);
+  mf_tile(l, np, nu, rl, nl);
+  mf_tile(j, np, nu, rj, nj);
+  double* A = d.F + d.foff[f];
+  cta_gemm<double>(ni, nl, nj, -1.0, A + ri * F + rj, (int)F, false, A + rl * F + rj, (int)F, true, 1.0,
+                   A + ri * F + rl, (int)F, 0, 0, i == l, sm);
+}
+
+__device__ inline double mf_wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// forward: w = [b_P; 0] + children's update vectors; y_P = L_P^{-1} w_P,
+// w_U -= L_UP y_P.  W_f keeps [y_P; w_U].  One CTA per front of the level.
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_mf_fwd(MFDev d, const int* __restrict__ fronts, const int* __restrict__ kid_ptr, const int* __restrict__ kid_list,
+         const double* __restrict__ b) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  double* w = reinterpret_cast<double*>(smraw);
+  const int f = fronts[blockIdx.x];
+  const int np = d.np[f], nu = d.nu[f], F = np + nu;
+  const int* g = d.gid + d.gid_off[f];
+  for (int k = threadIdx.x; k < F; k += blockDim.x) w[k] = (k < np) ? b[g[k]] : 0.0;
+  __syncthreads();
+  for (int q = kid_ptr[blockIdx.x]; q < kid_ptr[blockIdx.x + 1]; ++q) {
+    const int c = kid_list[q];
+    const int npc = d.np[c], nuc = d.nu[c];
+    const int* map = d.pmap + d.pmap_off[c];
+    const double* wc = d.W + d.woff[c] + npc;
+    for (int k = threadIdx.x; k < nuc; k += blockDim.x) w[map[k]] += wc[k];   // map is injective
+    __syncthreads();
+  }
+  const double* A = d.F + d.foff[f];
+  const double* Dv = d.Dinv + d.doff[f];
+  const int npt = (np + FNB - 1) / FNB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double yt[FNB];
+  for (int t = 0; t < npt; ++t) {
+    const int r0 = t * FNB, nr = min(FNB, np - r0);
+    for (int r = warp; r < nr; r += nw) {
+      double acc = 0.0;
+      for (int c = lane; c <= r; c += 32) acc = fma(Dv[(long long)t * FNB * FNB + r * FNB + c], w[r0 + c], acc);
+      acc = mf_wsum(acc);
+      if (lane == 0) yt[r] = acc;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) w[r0 + r] = yt[r];
+    for (int row = r0 + nr + warp; row < F; row += nw) {
+      const double* a = A + (long long)row * F + r0;
+      double acc = 0.0;
+      for (int c = lane; c < nr; c += 32) acc = fma(a[c], yt[c], acc);
+      acc = mf_wsum(acc);
+      if (lane == 0) w[row] -= acc;
+    }
+    __syncthreads();
+  }
+  double* Wf = d.W + d.woff[f];
+  for (int k = threadIdx.x; k < F; k += blockDim.x) Wf[k] = w[k];
+}
+
+// backward: v = y_P - L_UP^T x_U; x_P = L_P^{-T} v; x[gid_P] = x_P.
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_mf_bwd(MFDev d, const int* __restrict__ fronts, double* x) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  double* v = reinterpret_cast<double*>(smraw);          // np
+  double* xu = v + d.np[fronts[blockIdx.x]];             // nu
+  const int f = fronts[blockIdx.x];
+  const int np = d.np[f], nu = d.nu[f];
+  const long long F = np + nu;
+  const int* g = d.gid + d.gid_off[f];
+  const double* A = d.F + d.foff[f];
+  const double* Dv = d.Dinv + d.doff[f];
+  const double* Wf = d.W + d.woff[f];
+  for (int k = threadIdx.x; k < nu; k += blockDim.x) xu[k] = x[g[np + k]];
+  __syncthreads();
+  for (int c = threadIdx.x; c < np; c += blockDim.x) {
+    double acc = Wf[c];
+    for (int r = 0; r < nu; ++r) acc = fma(-A[(np + r) * F + c], xu[r], acc);
+    v[c] = acc;
+  }
+  __syncthreads();
+  __shared__ double xt[FNB];
+  const int npt = (np + FNB - 1) / FNB;
+  for (int t = npt - 1; t >= 0; --t) {
+    const int r0 = t * FNB, nr = min(FNB, np - r0);
+    for (int c = threadIdx.x; c < nr; c += blockDim.x) {
+      double acc = 0.0;
+      for (int r = c; r < nr; ++r) acc = fma(Dv[(long long)t * FNB * FNB + r * FNB + c], v[r0 + r], acc);
+      xt[c] = acc;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < r0; c += blockDim.x) {
+      double acc = 0.0;
+      for (int r = 0; r < nr; ++r) acc = fma(A[(r0 + r) * F + c], xt[r], acc);
+      v[c] -= acc;
+    }
+    for (int c = threadIdx.x; c < nr; c += blockDim.x) v[r0 + c] = xt[c];
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < np; k += blockDim.x) x[g[k]] = v[k];
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+namespace {
+MFDev dev_of(const MFPlan& P) {
+  MFDev d;
+  d.np = P.d_np; d.nu = P.d_nu; d.gid = P.d_gid; d.fr = P.d_fr; d.pp = P.d_pp; d.ord = P.d_ord;
+  d.pmap = P.d_pmap; d.parent = P.d_parent;
+  d.foff = P.d_foff; d.doff = P.d_doff; d.woff = P.d_woff; d.gid_off = P.d_gid_off; d.pmap_off = P.d_pmap_off;
+  d.F = P.F; d.Dinv = P.Dinv; d.W = P.W;
+  return d;
+}
+
+template <typename T>
+T* up(const std::vector<T>& v, const std::function<void*(size_t)>& alloc, cudaStream_t st) {
+  T* p = (T*)alloc(sizeof(T) * std::max<size_t>(v.size(), 1));
+  if (!v.empty()) cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+  return p;
+}
+
+}  // namespace
+
+void configure_mf_kernels() {
+  int sm = (int)sizeof(DenseSmem<double>);
+  cudaFuncSetAttribute(k_mf_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_mf_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_mf_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(2 * FNB * (FNB + 1) * sizeof(double)));
+  cudaFuncSetAttribute(k_mf_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mf_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc, cudaStream_t st) {
+  if (P.nfront == 0) return;
+  P.d_np = up(P.np, alloc, st);
+  P.d_nu = up(P.nu, alloc, st);
+  P.d_gid = up(P.gid, alloc, st);
+  P.d_fr = up(P.fr, alloc, st);
+  P.d_pp = up(P.pp, alloc, st);
+  P.d_ord = up(P.ord, alloc, st);
+  P.d_pmap = up(P.pmap, alloc, st);
+  P.d_parent = up(P.parent, alloc, st);
+  P.d_foff = up(P.foff, alloc, st);
+  P.d_doff = up(P.doff, alloc, st);
+  P.d_woff = up(P.woff, alloc, st);
+  P.d_gid_off = up(P.gid_off, alloc, st);
+  P.d_pmap_off = up(P.pmap_off, alloc, st);
+  P.F = (double*)alloc(sizeof(double) * P.fpool);
+  P.Dinv = (double*)alloc(sizeof(double) * std::max<long long>(P.dpool, 1));
+  P.W = (double*)alloc(sizeof(double) * P.wpool);
+  cudaMemsetAsync(P.F, 0, sizeof(double) * P.fpool, st);
+  // work lists
+  std::vector<int> all;
+  P.list_off.clear();
+  auto push = [&](const std::vector<int>& v) {
+    P.list_off.push_back((long long)all.size() / 4);
+    all.insert(all.end(), v.begin(), v.end());
+  };
+  for (size_t k = 0; k < P.step_potrf.size(); ++k) {
+    push(P.step_potrf[k]);
+    push(P.step_trsm[k]);
+    push(P.step_syrk[k]);
+  }
+  P.d_lists = (int4*)alloc(sizeof(int) * std::max<size_t>(all.size(), 4));
+  if (!all.empty()) cudaMemcpyAsync(P.d_lists, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, st);
+  // per level: fronts, their children (for the solves), children by slot (extend-add)
+  std::vector<int> lv;
+  P.lvl_fronts_off.assign(P.nlevel + 1, 0);
+  for (int l = 0; l < P.nlevel; ++l) {
+    P.lvl_fronts_off[l] = (int)lv.size();
+    for (int f : P.fronts_at_level[l]) lv.push_back(f);
+  }
+  P.lvl_fronts_off[P.nlevel] = (int)lv.size();
+  std::vector<std::vector<int>> kids(P.nfront);
+  P.maxslot = 0;
+  for (int f = 0; f < P.nfront; ++f)
+    if (P.parent[f] >= 0) {
+      kids[P.parent[f]].push_back(f);
+      P.maxslot = std::max(P.maxslot, P.child_slot[f] + 1);
+    }
+  for (auto& k : kids) std::sort(k.begin(), k.end(), [&](int a, int b) { return P.child_slot[a] < P.child_slot[b]; });
+  std::vector<int> kptr, klist;
+  for (int f : lv) {
+    kptr.push_back((int)klist.size());
+    for (int c : kids[f]) klist.push_back(c);
+  }
+  kptr.push_back((int)klist.size());
+  std::vector<int> slots;
+  P.slot_off.assign((size_t)P.nlevel * P.maxslot + 1, 0);
+  for (int l = 0; l < P.nlevel; ++l)
+    for (int s2 = 0; s2 < P.maxslot; ++s2) {
+      P.slot_off[(size_t)l * P.maxslot + s2] = (int)slots.size();
+      for (int f : P.fronts_at_level[l])
+        for (int c : kids[f])
+          if (P.child_slot[c] == s2) slots.push_back(c);
+    }
+  P.slot_off[(size_t)P.nlevel * P.maxslot] = (int)slots.size();
+  std::vector<int> blob(lv);
+  P.blob_kptr = (long long)blob.size();
+  blob.insert(blob.end(), kptr.begin(), kptr.end());
+  P.blob_klist = (long long)blob.size();
+  blob.insert(blob.end(), klist.begin(), klist.end());
+  P.blob_slots = (long long)blob.size();
+  blob.insert(blob.end(), slots.begin(), slots.end());
+  P.d_blob = up(blob, alloc, st);
+  P.list_len.clear();
+  int maxpo = 1;
+  for (size_t k = 0; k < P.step_potrf.size(); ++k) {
+    P.list_len.push_back((int)P.step_potrf[k].size() / 4);
+    P.list_len.push_back((int)P.step_trsm[k].size() / 4);
+    P.list_len.push_back((int)P.step_syrk[k].size() / 4);
+    maxpo = std::max(maxpo, (int)P.step_potrf[k].size() / 4);
+  }
+  P.pscratch = (double*)alloc(sizeof(double) * 2048 * (size_t)maxpo);
+}
+
+void mf_assemble(const MFPlan& P, const LocalLaunch& L, const int* color_subs, const int* color_count_host,
+                 const int* color_offset_host, cudaStream_t st) {
+  if (P.nfront == 0) return;
+  MFDev d = dev_of(P);
+  for (int c = 0; c < 8; ++c) {
+    if (color_count_host[c] == 0) continue;
+    BDDC_COUNT(1);
+    k_mf_assemble<<<dim3(color_count_host[c], 16), BDDC_THREADS, 0, st>>>(d, L.subs, L.lc,
+                                                                          color_subs + color_offset_host[c], L.Ac);
+  }
+}
+
+void mf_factor(const MFPlan& P, int* err, cudaStream_t st) {
+  if (P.nfront == 0) return;
+  MFDev d = dev_of(P);
+  const int* slots = P.d_blob + P.blob_slots;
+  const size_t dsm = sizeof(DenseSmem<double>);
+  const size_t tsm = 2 * FNB * (FNB + 1) * sizeof(double);
+  size_t step = 0;
+  for (int l = P.nlevel - 1; l >= 0; --l) {
+    for (int s = 0; s < P.maxslot; ++s) {
+      const int a = P.slot_off[(size_t)l * P.maxslot + s], b = P.slot_off[(size_t)l * P.maxslot + s + 1];
+      if (b > a) {
+        BDDC_COUNT(1);
+        k_mf_extend_add<<<dim3(b - a, 32), BDDC_THREADS, 0, st>>>(d, slots + a);
+      }
+    }
+    int maxpt = 0;
+    for (int f : P.fronts_at_level[l]) maxpt = std::max(maxpt, (P.np[f] + FNB - 1) / FNB);
+    for (int j = 0; j < maxpt; ++j, ++step) {
+      const int npo = P.list_len[3 * step], ntr = P.list_len[3 * step + 1], nsy = P.list_len[3 * step + 2];
+      const int4* lp = P.d_lists + P.list_off[3 * step];
+      const int4* lt = P.d_lists + P.list_off[3 * step + 1];
+      const int4* ls = P.d_lists + P.list_off[3 * step + 2];
+      if (npo) { BDDC_COUNT(1); k_mf_potrf<<<npo, BDDC_THREADS, dsm, st>>>(d, lp, P.pscratch, err); }
+      if (ntr) { BDDC_COUNT(1); k_mf_trsm<<<ntr, BDDC_THREADS, tsm, st>>>(d, lt); }
+      if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, dsm, st>>>(d, ls); }
+    }
+  }
+}
+
+void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream_t st) {
+  if (P.nfront == 0) return;
+  MFDev d = dev_of(P);
+  d.W = W;
+  const int* lv = P.d_blob;
+  const int* kptr = P.d_blob + P.blob_kptr;
+  const int* klist = P.d_blob + P.blob_klist;
+  int maxF = 0;
+  for (int f = 0; f < P.nfront; ++f) maxF = std::max(maxF, P.np[f] + P.nu[f]);
+  const size_t sm = sizeof(double) * (size_t)maxF;
+  for (int l = P.nlevel - 1; l >= 0; --l) {
+    const int a = P.lvl_fronts_off[l], n = P.lvl_fronts_off[l + 1] - a;
+    BDDC_COUNT(1);
+    k_mf_fwd<<<n, BDDC_THREADS, sm, st>>>(d, lv + a, kptr + a, klist, b);
+  }
+  for (int l = 0; l < P.nlevel; ++l) {
+    const int a = P.lvl_fronts_off[l], n = P.lvl_fronts_off[l + 1] - a;
+    BDDC_COUNT(1);
+    k_mf_bwd<<<n, BDDC_THREADS, sm, st>>>(d, lv + a, x);
+  }
+}
+
+}  // namespace bddc

@@ -71,6 +71,16 @@ struct MeshDev {
   int nsub[3];
 };
 
+// Stride between the plane blocks of a factor (elements): Q*Q padded so that
+// every block starts 256-byte aligned and a chunk rounded up to 16 bytes
+// stays inside its slot.
+__host__ __device__ inline long long slot_stride(int Q) {
+  return ((long long)Q * Q + 4 + 63) / 64 * 64;
+}
+
+// Padded element count of a dense array that is streamed in 16-byte chunks.
+__host__ __device__ inline long long padded(long long n) { return (n + 4 + 63) / 64 * 64; }
+
 __host__ __device__ inline long long nodeid(int NX, int NY, int i, int j, int k) {
   return (long long)i + (long long)NX * ((long long)j + (long long)NY * k);
 }

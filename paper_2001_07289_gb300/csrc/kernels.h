@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <functional>
+#include <vector>
 #include "common.cuh"
 
 namespace bddc {
@@ -11,7 +13,6 @@ extern long long g_launches;
 #define BDDC_COUNT(n) (::bddc::g_launches += (n))
 
 constexpr int CW = 64;       // RHS columns per CTA in the multi-RHS sweeps
-constexpr int CNB = 128;     // coarse Cholesky tile
 
 // Everything a batched local kernel needs (device pointers; local type erased).
 struct LocalLaunch {
@@ -47,13 +48,63 @@ void launch_piece_alpha(const MeshDev& m, const double* alpha, const int* plo, c
                         int npz, double* pw, cudaStream_t st);
 
 // coarse.cu
-void configure_coarse_kernels();
 void launch_coarse_assemble(const LocalLaunch& L, const int* color_subs, const int* color_count_host,
                             const int* color_offset_host, double* Acg, int nc, cudaStream_t st);
-void launch_coarse_factor(double* Acg, int nc, double* dinv, double* scratch, int* err, cudaStream_t st);
 void launch_coarse_gather(const int* ptr, const int2* ent, const double* rcl, double* rc, int nc, cudaStream_t st);
-void launch_coarse_solve(const double* L, int nc, const double* dinv, double* b, double* y, double* x,
-                         cudaStream_t st);
+
+// coarse_mf.cu: multifrontal FP64 Cholesky of the coarse matrix in a nested-
+// dissection order over the subdomain grid.
+struct CoarseGeom {
+  int nitem[3];
+  int nsub[3];
+  std::vector<int> objid;                       // item tuple (x fastest) -> coarse id or -1
+  std::vector<int> slab_item_lo[3], slab_item_hi[3];  // item of each slab's first / last node
+};
+
+struct MFPlan {
+  int nfront = 0, nlevel = 0, nc = 0;
+  // host
+  std::vector<int> level_of, np, nu, parent, child_slot;   // per front
+  std::vector<long long> foff, doff, woff;                  // front, dinv, work-vector offsets
+  std::vector<int> gid;                                     // per front: P then U global ids (concatenated)
+  std::vector<long long> gid_off;
+  std::vector<int> ord, fr, pp;                             // per coarse dof: order, owning front, pivot pos
+  std::vector<std::vector<int>> fronts_at_level;
+  std::vector<int> pmap;                                    // child U -> position in parent front
+  std::vector<long long> pmap_off;
+  long long fpool = 0, dpool = 0, wpool = 0;
+  double flops = 0;                                         // FMA count of the partial factorisations
+  // device
+  int *d_np = nullptr, *d_nu = nullptr, *d_gid = nullptr, *d_fr = nullptr, *d_pp = nullptr, *d_ord = nullptr;
+  long long *d_foff = nullptr, *d_doff = nullptr, *d_woff = nullptr, *d_gid_off = nullptr, *d_pmap_off = nullptr;
+  int *d_pmap = nullptr, *d_parent = nullptr;
+  int *d_ugid = nullptr;            // per front: U ids sorted (for the assembly lookup) ...
+  int *d_upos = nullptr;            // ... and their positions in the front
+  long long* d_ugid_off = nullptr;
+  double *F = nullptr, *Dinv = nullptr, *W = nullptr;
+  // work lists per (level, panel step): int4 {front, i, l, j}, concatenated on the device
+  std::vector<std::vector<int>> step_potrf, step_trsm, step_syrk;
+  std::vector<long long> list_off;
+  std::vector<int> list_len;
+  int4* d_lists = nullptr;
+  double* pscratch = nullptr;       // potrf scratch: 2048 doubles per concurrent diagonal tile
+  // per level, on the device in one int array: fronts by level, each front's
+  // children (CSR aligned with that list), and children by (level, slot)
+  int maxslot = 0;
+  std::vector<int> lvl_fronts_off;  // per level into the level-ordered front list
+  std::vector<int> slot_off;        // per (level, slot) into the slot lists
+  long long blob_kptr = 0, blob_klist = 0, blob_slots = 0;
+  int* d_blob = nullptr;
+};
+
+void mf_plan(MFPlan& P, const CoarseGeom& g, int nc);
+void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc, cudaStream_t st);
+void mf_assemble(const MFPlan& P, const LocalLaunch& L, const int* color_subs, const int* color_count_host,
+                 const int* color_offset_host, cudaStream_t st);
+void mf_factor(const MFPlan& P, int* err, cudaStream_t st);
+// x = A_c^{-1} b; W: work vector pool of P.wpool doubles
+void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream_t st);
+void configure_mf_kernels();
 
 // stencil.cu
 void launch_operator(const MeshDev& m, const double* alpha, const double* x, double* y, double* dot_partial,

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "dense.cuh"
 #include "kernels.h"
+#include "stream.cuh"
 
 namespace bddc {
 
@@ -103,7 +104,7 @@ __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const do
   if (k >= g.gz) return;
   const int Q = g.gx * g.gy;
   T* base = fac + (neumann ? s.offN : s.offD);
-  const long long QQ = (long long)Q * Q;
+  const long long QQ = (long long)Q * Q, SS = slot_stride(Q);
   for (long long e = (long long)blockIdx.z * blockDim.x + threadIdx.x; e < 2 * QQ;
        e += (long long)gridDim.z * blockDim.x) {
     int which = (int)(e / QQ);  // 0: diagonal block, 1: block (k, k-1)
@@ -121,7 +122,7 @@ __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const do
       else v = box_entry(m, alpha, s, s.e0[0] + g.off + ax, s.e0[1] + g.off + ay, s.e0[2] + g.off + k,
                          dx, dy, dz);
     }
-    T* blk = base + (which == 0 ? (long long)k : (long long)(g.gz + k - 1)) * QQ;
+    T* blk = base + (which == 0 ? (long long)k : (long long)(g.gz + k - 1)) * SS;
     blk[r] = (T)v;
   }
 }
@@ -134,25 +135,25 @@ template <typename T>
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_btchol(const SubDesc* __restrict__ subs, T* __restrict__ fac, T* __restrict__ scratch, int neumann,
          int* err) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
   const SubDesc s = subs[blockIdx.x];
   const Grid g = grid_of(s, neumann);
   if (g.gz == 0) return;
   const int Q = g.gx * g.gy;
-  const long long QQ = (long long)Q * Q;
+  const long long QQ = (long long)Q * Q, SS = slot_stride(Q);
   T* base = fac + (neumann ? s.offN : s.offD);
   T* W1 = scratch + s.offW;
   T* W2 = W1 + QQ;
   T* diag = W2 + QQ;
   for (int k = 0; k < g.gz; ++k) {
-    T* slot = base + (long long)k * QQ;
+    T* slot = base + (long long)k * SS;
     if (k > 0) {
-      T* mslot = base + (long long)(g.gz + k - 1) * QQ;
+      T* mslot = base + (long long)(g.gz + k - 1) * SS;
       for (long long e = threadIdx.x; e < QQ; e += blockDim.x) W2[e] = mslot[e];
       __syncthreads();
       // M_k = B_{k-1} * Linv_{k-1}^T   (op(B) = Linv^T is upper)
-      cta_gemm<T>(Q, Q, Q, T(1), W2, Q, false, base + (long long)(k - 1) * QQ, Q, true, T(0), mslot, Q,
+      cta_gemm<T>(Q, Q, Q, T(1), W2, Q, false, base + (long long)(k - 1) * SS, Q, true, T(0), mslot, Q,
                   0, 1, false, sm);
       // S_k = D_k - M_k M_k^T (lower part)
       cta_gemm<T>(Q, Q, Q, T(-1), mslot, Q, false, mslot, Q, true, T(1), slot, Q, 0, 0, true, sm);
@@ -172,7 +173,7 @@ template <typename T>
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_btsolve_multi(const SubDesc* __restrict__ subs, const T* __restrict__ fac, T* __restrict__ Y,
                 T* __restrict__ scratch, long long scratch_stride) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
   const SubDesc s = subs[blockIdx.x];
   const int c0 = blockIdx.y * CW;
@@ -180,7 +181,7 @@ k_btsolve_multi(const SubDesc* __restrict__ subs, const T* __restrict__ fac, T* 
   const int cw = min(CW, s.nc - c0);
   const Grid g = grid_of(s, 1);
   const int Q = g.gx * g.gy, nz = g.gz, ld = s.nc;
-  const long long QQ = (long long)Q * Q;
+  const long long QQ = slot_stride(Q);
   const T* base = fac + s.offN;
   T* Yb = Y + s.offY + c0;
   T* W = scratch + ((long long)blockIdx.x * gridDim.y + blockIdx.y) * scratch_stride;
@@ -260,7 +261,7 @@ template <typename T>
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_schur(const SubDesc* __restrict__ subs, T* __restrict__ G, T* __restrict__ Sc, T* __restrict__ Lv,
         T* __restrict__ scratch, int* err) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
   const SubDesc s = subs[blockIdx.x];
   const int na = s.na, nv = s.nv, nc = s.nc;
@@ -288,7 +289,7 @@ template <typename T>
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_phi_rows(const SubDesc* __restrict__ subs, T* __restrict__ Y, const T* __restrict__ Lv,
            const T* __restrict__ Sc, T* __restrict__ PA, int mode) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
   const SubDesc s = subs[blockIdx.x];
   const int nN = (s.w[0] + 1) * (s.w[1] + 1) * (s.w[2] + 1);
@@ -435,62 +436,92 @@ __global__ void k_piece_alpha(MeshDev m, const double* __restrict__ alpha, const
 }
 
 // ---------------------------------------------------------------------------
-// single-RHS sweeps (apply): v <- A^{-1} v for the plane-block factor, v in
-// shared memory (gz*Q entries), t scratch of Q entries.
+// single-RHS sweeps (apply).  v <- A^{-1} v for a plane-block factor, with the
+// factor blocks streamed through the shared-memory ring in row chunks:
+//   forward  (k = 0..nz-1):  t = v_k - M_k v_{k-1};  v_k = Linv_k t
+//   backward (k = nz-1..0):  t = v_k - M_{k+1}^T v_{k+1};  v_k = Linv_k^T t
+// Row products use one warp per row; transposed products accumulate columns
+// per thread (columns tid, tid+256).  v (nz*Q), t, t2 (Q each) in shared memory.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void sweep1(const T* __restrict__ base, int Q, int nz, T* v, T* t) {
+__device__ void sweep_stream(Ring& ring, const T* __restrict__ base, int Q, int nz, T* v, T* t, T* t2, int* err) {
+  const int R = rows_per_chunk(Q, (int)sizeof(T));
+  const int nch = (Q + R - 1) / R;
+  const int nfwd = 2 * nz - 1;
+  const long long SS = slot_stride(Q);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const long long QQ = (long long)Q * Q;
-  for (int k = 0; k < nz; ++k) {
-    T* vk = v + (long long)k * Q;
-    if (k > 0) {
-      const T* M = base + (long long)(nz + k - 1) * QQ;
-      const T* vp = vk - Q;
-      for (int i = warp; i < Q; i += nw) {
-        const T* row = M + (long long)i * Q;
-        T acc = T(0);
-        for (int j = lane; j < Q; j += 32) acc += row[j] * vp[j];
-        acc = warp_sum(acc);
-        if (lane == 0) t[i] = vk[i] - acc;
+  for (int i = threadIdx.x; i < Q; i += blockDim.x) t[i] = v[i];
+  if (nz == 1)
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) t2[i] = v[i];
+  __syncthreads();
+  // block bi -> kind (0 fwd L, 1 fwd M, 2 bwd L, 3 bwd M), plane k, slot
+  auto decode = [&](int bi, int& kind, int& k, int& slot) {
+    if (bi < nfwd) {
+      if (bi == 0) { kind = 0; k = 0; }
+      else if (bi & 1) { kind = 1; k = (bi + 1) / 2; }
+      else { kind = 0; k = bi / 2; }
+    } else {
+      int q = bi - nfwd;
+      if (q == 0) { kind = 2; k = nz - 1; }
+      else if (q & 1) { kind = 3; k = nz - (q + 1) / 2; }    // M_k, target plane k-1
+      else { kind = 2; k = nz - 1 - q / 2; }
+    }
+    slot = (kind == 0 || kind == 2) ? k : nz + k - 1;
+  };
+  T acc0 = T(0), acc1 = T(0);
+  const int j0 = threadIdx.x, j1 = threadIdx.x + blockDim.x;
+  auto src = [&](int c, const void*& p, unsigned& bytes) {
+    int kind, k, slot;
+    decode(c / nch, kind, k, slot);
+    const int r0 = (c % nch) * R, nr = min(R, Q - r0);
+    p = base + slot * SS + (long long)r0 * Q;
+    bytes = (unsigned)(nr * Q * sizeof(T));
+  };
+  auto use = [&](int c, const unsigned char* raw) {
+    const T* ch = reinterpret_cast<const T*>(raw);
+    int kind, k, slot;
+    const int lc = c % nch;
+    decode(c / nch, kind, k, slot);
+    const int r0 = lc * R, nr = min(R, Q - r0);
+    if (kind == 0 || kind == 1) {
+      T* vk = v + (long long)k * Q;
+      for (int r = warp; r < nr; r += nw) {
+        const int i = r0 + r;
+        const T* row = ch + (long long)r * Q;
+        T a = T(0);
+        if (kind == 0) {
+          for (int j = lane; j <= i; j += 32) a += row[j] * t[j];
+        } else {
+          const T* vp = vk - Q;
+          for (int j = lane; j < Q; j += 32) a += row[j] * vp[j];
+        }
+        a = warp_sum(a);
+        if (lane == 0) {
+          if (kind == 0) { vk[i] = a; if (k == nz - 1) t2[i] = a; }
+          else t[i] = vk[i] - a;
+        }
       }
     } else {
-      for (int i = threadIdx.x; i < Q; i += blockDim.x) t[i] = vk[i];
-    }
-    __syncthreads();
-    const T* Li = base + (long long)k * QQ;
-    for (int i = warp; i < Q; i += nw) {
-      const T* row = Li + (long long)i * Q;
-      T acc = T(0);
-      for (int j = lane; j <= i; j += 32) acc += row[j] * t[j];
-      acc = warp_sum(acc);
-      if (lane == 0) vk[i] = acc;
-    }
-    __syncthreads();
-  }
-  for (int k = nz - 1; k >= 0; --k) {
-    T* vk = v + (long long)k * Q;
-    if (k < nz - 1) {
-      const T* M = base + (long long)(nz + k) * QQ;
-      const T* vn = vk + Q;
-      for (int i = threadIdx.x; i < Q; i += blockDim.x) {
-        T acc = T(0);
-        for (int j = 0; j < Q; ++j) acc += M[(long long)j * Q + i] * vn[j];
-        t[i] = vk[i] - acc;
+      const T* in = (kind == 2) ? ((k == nz - 1) ? t2 : t) : v + (long long)k * Q;
+      for (int r = 0; r < nr; ++r) {
+        const T x = in[r0 + r];
+        const T* row = ch + (long long)r * Q;
+        if (j0 < Q) acc0 += row[j0] * x;
+        if (j1 < Q) acc1 += row[j1] * x;
       }
-    } else {
-      for (int i = threadIdx.x; i < Q; i += blockDim.x) t[i] = vk[i];
+      if (lc == nch - 1) {
+        T* dst = (kind == 2) ? v + (long long)k * Q : t;
+        const T* sub = (kind == 3) ? v + (long long)(k - 1) * Q : nullptr;
+        if (j0 < Q) dst[j0] = sub ? sub[j0] - acc0 : acc0;
+        if (j1 < Q) dst[j1] = sub ? sub[j1] - acc1 : acc1;
+        acc0 = acc1 = T(0);
+      }
     }
-    __syncthreads();
-    const T* Li = base + (long long)k * QQ;
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) {
-      T acc = T(0);
-      for (int j = i; j < Q; ++j) acc += Li[(long long)j * Q + i] * t[j];
-      vk[i] = acc;
-    }
-    __syncthreads();
-  }
+  };
+  ring_run(ring, 2 * nfwd * nch, src, use, err);
 }
+
+__host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 8 * NBUF; }
 
 // Dirichlet solves of the apply.  mode 0: z_I = A_II^{-1} r_I;
 // mode 1: z_I = A_II^{-1} (r_I - t_I).  Writes the interior nodes of z only.
@@ -498,14 +529,17 @@ template <typename T>
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
                   const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ z,
-                  int mode) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+                  int mode, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
   const SubDesc s = subs[blockIdx.x];
   const Grid g = grid_of(s, 0);
   if (g.gz == 0) return;
   const int Q = g.gx * g.gy, n = Q * g.gz;
-  T* v = reinterpret_cast<T*>(smraw);
-  T* tmp = v + n;
+  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
+  T* v = reinterpret_cast<T*>(smraw + ring_bytes());
+  T* tq = v + n;
+  T* t2 = tq + Q;
+  ring_init(ring);
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
     long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
@@ -514,7 +548,7 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
     v[l] = (T)val;
   }
   __syncthreads();
-  sweep1<T>(fac + s.offD, Q, g.gz, v, tmp);
+  sweep_stream<T>(ring, fac + s.offD, Q, g.gz, v, tq, t2, err);
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
     long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
@@ -524,20 +558,23 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
 
 // Weighted restriction r_i = D_i R_i (r - t) on the box surface, the local
 // coarse right-hand side rc_i = Phi_i^T r_i, and the constrained Neumann solve
-// y = A_rr^{-1} r_i,r (in place in vloc).
+// y = A_rr^{-1} r_i,r (into vloc).
 template <typename T>
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
                 const T* __restrict__ Phi, const double* __restrict__ delta,
                 const double* __restrict__ r, const double* __restrict__ t, T* __restrict__ vloc,
-                double* __restrict__ rcl) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+                double* __restrict__ rcl, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
   const SubDesc s = subs[blockIdx.x];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const int Q = px * py, n = Q * pz;
-  T* v = reinterpret_cast<T*>(smraw);
-  T* tmp = v + n;
-  double* rg = reinterpret_cast<double*>(smraw + align16(sizeof(T) * ((size_t)n + Q)));
+  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
+  double* rg = reinterpret_cast<double*>(smraw + ring_bytes());
+  T* v = reinterpret_cast<T*>(rg + s.nB);
+  T* tq = v + n;
+  T* t2 = tq + Q;
+  ring_init(ring);
   for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = T(0);
   __syncthreads();
   for (int b = threadIdx.x; b < s.nB; b += blockDim.x) {
@@ -550,14 +587,38 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
     if (!neumann_fixed(m, s, ix, iy, iz)) v[ix + px * (iy + py * iz)] = (T)val;
   }
   __syncthreads();
-  const T* P = Phi + s.offPhi;
-  for (int j = threadIdx.x; j < s.nc; j += blockDim.x) {
-    double acc = 0.0;
-    for (int b = 0; b < s.nB; ++b) acc += (double)P[(long long)b * s.nc + j] * rg[b];
-    rcl[s.cofs + j] = acc;
+  if (s.nc > 0) {
+    // rc_i = Phi_i^T r_i: columns j = tid + 256 q accumulate over streamed rows
+    const int R = rows_per_chunk(s.nc, (int)sizeof(T));
+    const int nch = (s.nB + R - 1) / R;
+    const T* P = Phi + s.offPhi;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    auto src = [&](int c, const void*& p, unsigned& bytes) {
+      const int r0 = c * R, nr = min(R, s.nB - r0);
+      p = P + (long long)r0 * s.nc;
+      bytes = (unsigned)(nr * s.nc * sizeof(T));
+    };
+    auto use = [&](int c, const unsigned char* raw) {
+      const T* ch = reinterpret_cast<const T*>(raw);
+      const int r0 = c * R, nr = min(R, s.nB - r0);
+      for (int rr = 0; rr < nr; ++rr) {
+        const double x = rg[r0 + rr];
+        const T* row = ch + (long long)rr * s.nc;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = threadIdx.x + q * BDDC_THREADS;
+          if (j < s.nc) acc[q] += (double)row[j] * x;
+        }
+      }
+    };
+    ring_run(ring, nch, src, use, err);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = threadIdx.x + q * BDDC_THREADS;
+      if (j < s.nc) rcl[s.cofs + j] = acc[q];
+    }
   }
-  __syncthreads();
-  sweep1<T>(fac + s.offN, Q, pz, v, tmp);
+  sweep_stream<T>(ring, fac + s.offN, Q, pz, v, tq, t2, err);
   for (int l = threadIdx.x; l < n; l += blockDim.x) vloc[s.offVec + l] = v[l];
 }
 
@@ -566,11 +627,13 @@ template <typename T>
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict__ lc,
                  const T* __restrict__ Phi, const T* __restrict__ vloc, const double* __restrict__ uc,
-                 double* __restrict__ vgam) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+                 double* __restrict__ vgam, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
   const SubDesc s = subs[blockIdx.x];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
-  double* ut = reinterpret_cast<double*>(smraw);
+  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
+  double* ut = reinterpret_cast<double*>(smraw + ring_bytes());
+  ring_init(ring);
   const T* y = vloc + s.offVec;
   for (int j = threadIdx.x; j < s.nc; j += blockDim.x) {
     const LocalCoarse c = lc[s.cofs + j];
@@ -586,18 +649,39 @@ k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const T* P = Phi + s.offPhi;
-  for (int b = warp; b < s.nB; b += nw) {
-    const T* row = P + (long long)b * s.nc;
-    double acc = 0.0;
-    for (int j = lane; j < s.nc; j += 32) acc += (double)row[j] * ut[j];
-    acc = warp_sum(acc);
-    if (lane == 0) {
+  if (s.nc == 0) {
+    for (int b = threadIdx.x; b < s.nB; b += blockDim.x) {
       int ix, iy, iz;
       surf_coords(b, px, py, pz, ix, iy, iz);
-      vgam[s.offB + b] = acc + (double)y[ix + px * (iy + py * iz)];
+      vgam[s.offB + b] = (double)y[ix + px * (iy + py * iz)];
     }
+    return;
   }
+  const int R = rows_per_chunk(s.nc, (int)sizeof(T));
+  const int nch = (s.nB + R - 1) / R;
+  const T* P = Phi + s.offPhi;
+  auto src = [&](int c, const void*& p, unsigned& bytes) {
+    const int r0 = c * R, nr = min(R, s.nB - r0);
+    p = P + (long long)r0 * s.nc;
+    bytes = (unsigned)(nr * s.nc * sizeof(T));
+  };
+  auto use = [&](int c, const unsigned char* raw) {
+    const T* ch = reinterpret_cast<const T*>(raw);
+    const int r0 = c * R, nr = min(R, s.nB - r0);
+    for (int rr = warp; rr < nr; rr += nw) {
+      const T* row = ch + (long long)rr * s.nc;
+      double a = 0.0;
+      for (int j = lane; j < s.nc; j += 32) a += (double)row[j] * ut[j];
+      a = warp_sum(a);
+      if (lane == 0) {
+        int ix, iy, iz;
+        const int b = r0 + rr;
+        surf_coords(b, px, py, pz, ix, iy, iz);
+        vgam[s.offB + b] = a + (double)y[ix + px * (iy + py * iz)];
+      }
+    }
+  };
+  ring_run(ring, nch, src, use, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -649,9 +733,9 @@ void configure_local_kernels() {
   cudaFuncSetAttribute(k_btsolve_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_phi_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(k_dirichlet_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_neumann_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_neumann_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  cudaFuncSetAttribute(k_dirichlet_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(k_neumann_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(k_neumann_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st) {
@@ -671,24 +755,24 @@ template <typename T>
 void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, double* z, int mode, cudaStream_t st) {
   if (L.maxQD == 0) return;
   BDDC_COUNT(1);
-  size_t sm = sizeof(T) * ((size_t)L.maxND + L.maxQD + 2);
-  k_dirichlet_solve<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facD, r, t, z, mode);
+  size_t sm = ring_bytes() + sizeof(T) * ((size_t)L.maxND + 2 * L.maxQD + 2);
+  k_dirichlet_solve<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facD, r, t, z, mode, L.err);
 }
 
 template <typename T>
 void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
-  size_t sm = align16(sizeof(T) * ((size_t)L.maxNN + L.maxQN)) + sizeof(double) * (L.maxNB + 2);
+  size_t sm = ring_bytes() + sizeof(double) * (L.maxNB + 1) + sizeof(T) * ((size_t)L.maxNN + 2 * L.maxQN + 2);
   BDDC_COUNT(1);
   k_neumann_solve<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta,
-                                                      r, t, (T*)L.vloc, L.rcl);
+                                                      r, t, (T*)L.vloc, L.rcl, L.err);
 }
 
 template <typename T>
 void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t st) {
-  size_t sm = sizeof(double) * (L.maxNc + 1);
+  size_t sm = ring_bytes() + sizeof(double) * (L.maxNc + 1);
   BDDC_COUNT(1);
   k_neumann_finish<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.lc, (const T*)L.Phi, (const T*)L.vloc, uc,
-                                                       L.vgam);
+                                                       L.vgam, L.err);
 }
 
 template void launch_setup_local<float>(const LocalLaunch&, cudaStream_t, cudaEvent_t*);
