@@ -485,8 +485,8 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     launch_coarse_assemble(L, h->color_subs, h->color_count, h->color_off, h->Ac_copy, nc, st);
   }
   mf_plan(h->mf, h->geom, nc);
-  mf_upload(h->mf, [h](size_t b) { return h->dalloc(b); }, st);
-  h->factor_bytes += sizeof(double) * (size_t)(h->mf.fpool + h->mf.dpool);
+  mf_upload(h->mf, [h](size_t b) { return h->dalloc(b); }, [h](size_t b) { return h->dalloc(b, true); }, st);
+  h->factor_bytes += sizeof(double) * (size_t)h->mf.spool;
   configure_mf_kernels();
   mf_assemble(h->mf, L, h->color_subs, h->color_count, h->color_off, st);
   CK(cudaEventRecord(ev[5], st));
@@ -820,7 +820,7 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   }
   for (int f = 0; f < h->mf.nfront; ++f) {
     const long long np = h->mf.np[f], nu = h->mf.nu[f];
-    bytes += 2 * 8 * (np * (np + 1) / 2 + nu * np);
+    bytes += 2 * 8 * (np * (np + 1) / 2 + nu * np);   // solve matrices, read forward and backward
   }
   info->local_factor_fma = fma;
   info->apply_bytes = bytes;

@@ -14,8 +14,11 @@
 // children's update matrices, then a tiled right-looking partial Cholesky of
 // every front of the level at once (potrf of the 64x64 diagonal tile with its
 // explicit inverse, trsm of the tiles below it, syrk of the trailing tiles,
-// which include the update block U x U).  Solves run level by level with one
-// CTA per front.  Everything is summed in a fixed order (no atomics).
+// which include the update block U x U).  Afterwards every front gets its
+// solve matrix [Linv_P; G] with Linv_P = L_P^{-1} and G = L_UP Linv_P, so each
+// level of a triangular solve is one parallel mat-vec over all the level's
+// fronts (rows split across CTAs forward, columns backward).  Everything is
+// summed in a fixed order (no atomics).
 #include <stdexcept>
 
 #include "common.cuh"
@@ -179,6 +182,26 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
   }
   if (pos != nc) throw std::runtime_error("nested dissection missed coarse objects");
   P.fpool = fo; P.dpool = dof; P.wpool = wo;
+  // solve matrices and the work lists that build them
+  P.soff.resize(nf);
+  long long so = 0;
+  int maxpt_all = 0;
+  for (int f = 0; f < nf; ++f) {
+    P.soff[f] = so;
+    so += (long long)(P.np[f] + P.nu[f]) * P.np[f];
+    maxpt_all = std::max(maxpt_all, (P.np[f] + FNB - 1) / FNB);
+  }
+  P.spool = so;
+  P.diag_items.clear(); P.g_items.clear(); P.trtri_steps.assign(std::max(maxpt_all, 1), {});
+  for (int f = 0; f < nf; ++f) {
+    const int npt = (P.np[f] + FNB - 1) / FNB, nut = (P.nu[f] + FNB - 1) / FNB;
+    for (int t = 0; t < npt; ++t) P.diag_items.insert(P.diag_items.end(), {f, t, t, 0});
+    for (int t = 1; t < npt; ++t)
+      for (int s2 = 0; s2 < t; ++s2) P.trtri_steps[t].insert(P.trtri_steps[t].end(), {f, t, s2, 0});
+    for (int u = 0; u < nut; ++u)
+      for (int s2 = 0; s2 < npt; ++s2) P.g_items.insert(P.g_items.end(), {f, u, s2, 0});
+    P.flops += (double)P.np[f] * P.np[f] * P.np[f] / 6.0 + (double)P.nu[f] * P.np[f] * P.np[f] / 2.0;
+  }
   // child update rows -> positions in the parent front
   P.pmap_off.assign(nf + 1, 0);
   for (int f = 0; f < nf; ++f) {
@@ -226,8 +249,8 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
 // ---------------------------------------------------------------------------
 struct MFDev {
   const int *np, *nu, *gid, *fr, *pp, *ord, *pmap, *parent;
-  const long long *foff, *doff, *woff, *gid_off, *pmap_off;
-  double *F, *Dinv, *W;
+  const long long *foff, *doff, *woff, *gid_off, *pmap_off, *soff;
+  double *F, *Dinv, *W, *S;
 };
 
 __device__ inline int mf_pos(const MFDev& d, int f, int o) {
@@ -352,94 +375,123 @@ __device__ inline double mf_wsum(double v) {
   return v;
 }
 
-// forward: w = [b_P; 0] + children's update vectors; y_P = L_P^{-1} w_P,
-// w_U -= L_UP y_P.  W_f keeps [y_P; w_U].  One CTA per front of the level.
+
+// ---------------------------------------------------------------------------
+// solve matrices: X = L_P^{-1} by tile rows (X_tt = Dinv_t,
+// X_ts = -Dinv_t sum_{k=s}^{t-1} L_tk X_ks) and G = L_UP X.
+// ---------------------------------------------------------------------------
+__global__ void k_mf_inv_diag(MFDev d, const int4* __restrict__ work) {
+  const int4 w = work[blockIdx.x];
+  const int f = w.x, t = w.y;
+  const int np = d.np[f];
+  const int r0 = t * FNB, nr = min(FNB, np - r0);
+  double* X = d.S + d.soff[f];
+  const double* Dg = d.Dinv + d.doff[f] + (long long)t * FNB * FNB;
+  for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) {
+    int r = e / nr, c = e % nr;
+    X[(long long)(r0 + r) * np + r0 + c] = (c <= r) ? Dg[r * FNB + c] : 0.0;
+  }
+}
+
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_fwd(MFDev d, const int* __restrict__ fronts, const int* __restrict__ kid_ptr, const int* __restrict__ kid_list,
-         const double* __restrict__ b) {
+k_mf_inv_step(MFDev d, const int4* __restrict__ work, double* scratch) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
+  const int4 w = work[blockIdx.x];
+  const int f = w.x, t = w.y, sblk = w.z;
+  const int np = d.np[f], nu = d.nu[f];
+  const long long F = np + nu;
+  const int t0 = t * FNB, nt = min(FNB, np - t0);
+  const int s0 = sblk * FNB, ns = min(FNB, np - s0);
+  const double* L = d.F + d.foff[f];
+  double* X = d.S + d.soff[f];
+  double* tmp = scratch + (long long)blockIdx.x * FNB * FNB;
+  // tmp = L[t rows, s0:t0] X[s0:t0, s cols]   (X lower: zero for k < j)
+  cta_gemm<double>(nt, ns, t0 - s0, 1.0, L + t0 * F + s0, (int)F, false, X + (long long)s0 * np + s0, np, false, 0.0,
+                   tmp, FNB, 0, 2, false, sm);
+  // X_ts = -Dinv_t tmp
+  cta_gemm<double>(nt, ns, nt, -1.0, d.Dinv + d.doff[f] + (long long)t * FNB * FNB, FNB, false, tmp, FNB, false, 0.0,
+                   X + (long long)t0 * np + s0, np, 1, 0, false, sm);
+}
+
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_mf_g(MFDev d, const int4* __restrict__ work) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
+  const int4 w = work[blockIdx.x];
+  const int f = w.x, ut = w.y, st = w.z;
+  const int np = d.np[f], nu = d.nu[f];
+  const long long F = np + nu;
+  const int u0 = ut * FNB, nuu = min(FNB, nu - u0);
+  const int s0 = st * FNB, ns = min(FNB, np - s0);
+  const double* L = d.F + d.foff[f];
+  double* S = d.S + d.soff[f];
+  // G[u, s cols] = L_UP[u, s0:np] X[s0:np, s cols]
+  cta_gemm<double>(nuu, ns, np - s0, 1.0, L + (np + u0) * F + s0, (int)F, false, S + (long long)s0 * np + s0, np,
+                   false, 0.0, S + (long long)(np + u0) * np + s0, np, 0, 2, false, sm);
+}
+
+// forward, one launch per level; work item {front, row chunk of FNB rows}:
+// w_P = b_P + children's update vectors at P, w_U likewise at U;
+// rows r < np: W[r] = (Linv_P w_P)[r];  rows r >= np: W[r] = w_U[r-np] - (G w_P)[r-np]
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_mf_fwd2(MFDev d, const int2* __restrict__ items, const int* __restrict__ kid_ptr, const int* __restrict__ kid_list,
+          const int* __restrict__ lvl_index, const double* __restrict__ b) {
   extern __shared__ __align__(128) unsigned char smraw[];
   double* w = reinterpret_cast<double*>(smraw);
-  const int f = fronts[blockIdx.x];
+  const int2 it = items[blockIdx.x];
+  const int f = it.x, chunk = it.y;
   const int np = d.np[f], nu = d.nu[f], F = np + nu;
   const int* g = d.gid + d.gid_off[f];
   for (int k = threadIdx.x; k < F; k += blockDim.x) w[k] = (k < np) ? b[g[k]] : 0.0;
   __syncthreads();
-  for (int q = kid_ptr[blockIdx.x]; q < kid_ptr[blockIdx.x + 1]; ++q) {
+  const int li = lvl_index[f];
+  for (int q = kid_ptr[li]; q < kid_ptr[li + 1]; ++q) {
     const int c = kid_list[q];
-    const int npc = d.np[c], nuc = d.nu[c];
     const int* map = d.pmap + d.pmap_off[c];
-    const double* wc = d.W + d.woff[c] + npc;
-    for (int k = threadIdx.x; k < nuc; k += blockDim.x) w[map[k]] += wc[k];   // map is injective
+    const double* wc = d.W + d.woff[c] + d.np[c];
+    for (int k = threadIdx.x; k < d.nu[c]; k += blockDim.x) w[map[k]] += wc[k];
     __syncthreads();
   }
-  const double* A = d.F + d.foff[f];
-  const double* Dv = d.Dinv + d.doff[f];
-  const int npt = (np + FNB - 1) / FNB;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ double yt[FNB];
-  for (int t = 0; t < npt; ++t) {
-    const int r0 = t * FNB, nr = min(FNB, np - r0);
-    for (int r = warp; r < nr; r += nw) {
-      double acc = 0.0;
-      for (int c = lane; c <= r; c += 32) acc = fma(Dv[(long long)t * FNB * FNB + r * FNB + c], w[r0 + c], acc);
-      acc = mf_wsum(acc);
-      if (lane == 0) yt[r] = acc;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) w[r0 + r] = yt[r];
-    for (int row = r0 + nr + warp; row < F; row += nw) {
-      const double* a = A + (long long)row * F + r0;
-      double acc = 0.0;
-      for (int c = lane; c < nr; c += 32) acc = fma(a[c], yt[c], acc);
-      acc = mf_wsum(acc);
-      if (lane == 0) w[row] -= acc;
-    }
-    __syncthreads();
-  }
+  const double* S = d.S + d.soff[f];
   double* Wf = d.W + d.woff[f];
-  for (int k = threadIdx.x; k < F; k += blockDim.x) Wf[k] = w[k];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int r0 = chunk * FNB, r1 = min(F, r0 + FNB);
+  for (int r = r0 + warp; r < r1; r += nw) {
+    const double* row = S + (long long)r * np;
+    const int cend = (r < np) ? r + 1 : np;
+    double acc = 0.0;
+    for (int c = lane; c < cend; c += 32) acc = fma(row[c], w[c], acc);
+    acc = mf_wsum(acc);
+    if (lane == 0) Wf[r] = (r < np) ? acc : w[r] - acc;
+  }
 }
 
-// backward: v = y_P - L_UP^T x_U; x_P = L_P^{-T} v; x[gid_P] = x_P.
+// backward, one launch per level; work item {front, column chunk of 64}:
+// x_P[c] = sum_{r>=c} Linv_P[r][c] y_P[r] - sum_u G[u][c] x_U[u]
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_bwd(MFDev d, const int* __restrict__ fronts, double* x) {
+k_mf_bwd2(MFDev d, const int2* __restrict__ items, double* x) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  double* v = reinterpret_cast<double*>(smraw);          // np
-  double* xu = v + d.np[fronts[blockIdx.x]];             // nu
-  const int f = fronts[blockIdx.x];
-  const int np = d.np[f], nu = d.nu[f];
-  const long long F = np + nu;
+  double* vec = reinterpret_cast<double*>(smraw);        // [y_P; x_U]
+  __shared__ double part[4][64];
+  const int2 it = items[blockIdx.x];
+  const int f = it.x, chunk = it.y;
+  const int np = d.np[f], nu = d.nu[f], F = np + nu;
   const int* g = d.gid + d.gid_off[f];
-  const double* A = d.F + d.foff[f];
-  const double* Dv = d.Dinv + d.doff[f];
   const double* Wf = d.W + d.woff[f];
-  for (int k = threadIdx.x; k < nu; k += blockDim.x) xu[k] = x[g[np + k]];
+  for (int k = threadIdx.x; k < F; k += blockDim.x) vec[k] = (k < np) ? Wf[k] : x[g[k]];
   __syncthreads();
-  for (int c = threadIdx.x; c < np; c += blockDim.x) {
-    double acc = Wf[c];
-    for (int r = 0; r < nu; ++r) acc = fma(-A[(np + r) * F + c], xu[r], acc);
-    v[c] = acc;
+  const double* S = d.S + d.soff[f];
+  const int cl = threadIdx.x & 63, grp = threadIdx.x >> 6;   // 64 columns x 4 row groups
+  const int c = chunk * 64 + cl;
+  double acc = 0.0;
+  if (c < np) {
+    for (int r = c + grp; r < np; r += 4) acc = fma(S[(long long)r * np + c], vec[r], acc);
+    for (int r = np + grp; r < F; r += 4) acc = fma(-S[(long long)r * np + c], vec[r], acc);
   }
+  part[grp][cl] = acc;
   __syncthreads();
-  __shared__ double xt[FNB];
-  const int npt = (np + FNB - 1) / FNB;
-  for (int t = npt - 1; t >= 0; --t) {
-    const int r0 = t * FNB, nr = min(FNB, np - r0);
-    for (int c = threadIdx.x; c < nr; c += blockDim.x) {
-      double acc = 0.0;
-      for (int r = c; r < nr; ++r) acc = fma(Dv[(long long)t * FNB * FNB + r * FNB + c], v[r0 + r], acc);
-      xt[c] = acc;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < r0; c += blockDim.x) {
-      double acc = 0.0;
-      for (int r = 0; r < nr; ++r) acc = fma(A[(r0 + r) * F + c], xt[r], acc);
-      v[c] -= acc;
-    }
-    for (int c = threadIdx.x; c < nr; c += blockDim.x) v[r0 + c] = xt[c];
-    __syncthreads();
-  }
-  for (int k = threadIdx.x; k < np; k += blockDim.x) x[g[k]] = v[k];
+  if (grp == 0 && c < np) x[g[c]] = part[0][cl] + part[1][cl] + part[2][cl] + part[3][cl];
 }
 
 // ---------------------------------------------------------------------------
@@ -452,6 +504,7 @@ MFDev dev_of(const MFPlan& P) {
   d.pmap = P.d_pmap; d.parent = P.d_parent;
   d.foff = P.d_foff; d.doff = P.d_doff; d.woff = P.d_woff; d.gid_off = P.d_gid_off; d.pmap_off = P.d_pmap_off;
   d.F = P.F; d.Dinv = P.Dinv; d.W = P.W;
+  d.S = P.S; d.soff = P.d_soff;
   return d;
 }
 
@@ -466,15 +519,18 @@ T* up(const std::vector<T>& v, const std::function<void*(size_t)>& alloc, cudaSt
 
 void configure_mf_kernels() {
   int sm = (int)sizeof(DenseSmem<double>);
+  cudaFuncSetAttribute(k_mf_inv_step, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_mf_g, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_mf_fwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mf_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mf_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_mf_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_mf_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(2 * FNB * (FNB + 1) * sizeof(double)));
-  cudaFuncSetAttribute(k_mf_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_mf_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc, cudaStream_t st) {
+void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
+               const std::function<void*(size_t)>& tmp_alloc, cudaStream_t st) {
   if (P.nfront == 0) return;
   P.d_np = up(P.np, alloc, st);
   P.d_nu = up(P.nu, alloc, st);
@@ -489,10 +545,13 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc, cudaStream_
   P.d_woff = up(P.woff, alloc, st);
   P.d_gid_off = up(P.gid_off, alloc, st);
   P.d_pmap_off = up(P.pmap_off, alloc, st);
-  P.F = (double*)alloc(sizeof(double) * P.fpool);
-  P.Dinv = (double*)alloc(sizeof(double) * std::max<long long>(P.dpool, 1));
+  P.F = (double*)tmp_alloc(sizeof(double) * P.fpool);
+  P.Dinv = (double*)tmp_alloc(sizeof(double) * std::max<long long>(P.dpool, 1));
   P.W = (double*)alloc(sizeof(double) * P.wpool);
+  P.S = (double*)alloc(sizeof(double) * std::max<long long>(P.spool, 1));
+  P.d_soff = up(P.soff, alloc, st);
   cudaMemsetAsync(P.F, 0, sizeof(double) * P.fpool, st);
+  cudaMemsetAsync(P.S, 0, sizeof(double) * P.spool, st);
   // work lists
   std::vector<int> all;
   P.list_off.clear();
@@ -505,7 +564,21 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc, cudaStream_
     push(P.step_trsm[k]);
     push(P.step_syrk[k]);
   }
-  P.d_lists = (int4*)alloc(sizeof(int) * std::max<size_t>(all.size(), 4));
+  P.inv_off.clear(); P.inv_len.clear();
+  auto push_inv = [&](const std::vector<int>& v) {
+    P.inv_off.push_back((long long)all.size() / 4);
+    P.inv_len.push_back((int)v.size() / 4);
+    all.insert(all.end(), v.begin(), v.end());
+  };
+  push_inv(P.diag_items);
+  push_inv(P.g_items);
+  int maxinv = 1;
+  for (size_t t = 1; t < P.trtri_steps.size(); ++t) {
+    push_inv(P.trtri_steps[t]);
+    maxinv = std::max(maxinv, (int)P.trtri_steps[t].size() / 4);
+  }
+  P.tscratch = (double*)tmp_alloc(sizeof(double) * FNB * FNB * (size_t)maxinv);
+  P.d_lists = (int4*)tmp_alloc(sizeof(int) * std::max<size_t>(all.size(), 4));
   if (!all.empty()) cudaMemcpyAsync(P.d_lists, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, st);
   // per level: fronts, their children (for the solves), children by slot (extend-add)
   std::vector<int> lv;
@@ -540,6 +613,10 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc, cudaStream_
     }
   P.slot_off[(size_t)P.nlevel * P.maxslot] = (int)slots.size();
   std::vector<int> blob(lv);
+  std::vector<int> lvl_index(P.nfront, 0);
+  for (size_t q = 0; q < lv.size(); ++q) lvl_index[lv[q]] = (int)q;
+  P.blob_lvl_index = (long long)blob.size();
+  blob.insert(blob.end(), lvl_index.begin(), lvl_index.end());
   P.blob_kptr = (long long)blob.size();
   blob.insert(blob.end(), kptr.begin(), kptr.end());
   P.blob_klist = (long long)blob.size();
@@ -555,7 +632,26 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc, cudaStream_
     P.list_len.push_back((int)P.step_syrk[k].size() / 4);
     maxpo = std::max(maxpo, (int)P.step_potrf[k].size() / 4);
   }
-  P.pscratch = (double*)alloc(sizeof(double) * 2048 * (size_t)maxpo);
+  P.pscratch = (double*)tmp_alloc(sizeof(double) * 2048 * (size_t)maxpo);
+  // solve work lists: per level fwd items {front, row chunk}, bwd items {front, column chunk}
+  std::vector<int> items;
+  P.fwd_items_off.assign(P.nlevel, 0); P.fwd_items_len.assign(P.nlevel, 0);
+  P.bwd_items_off.assign(P.nlevel, 0); P.bwd_items_len.assign(P.nlevel, 0);
+  P.maxF = 0;
+  for (int l = 0; l < P.nlevel; ++l) {
+    P.fwd_items_off[l] = (int)items.size() / 2;
+    for (int f : P.fronts_at_level[l]) {
+      const int F = P.np[f] + P.nu[f];
+      P.maxF = std::max(P.maxF, F);
+      for (int c = 0; c < (F + FNB - 1) / FNB; ++c) items.insert(items.end(), {f, c});
+    }
+    P.fwd_items_len[l] = (int)items.size() / 2 - P.fwd_items_off[l];
+    P.bwd_items_off[l] = (int)items.size() / 2;
+    for (int f : P.fronts_at_level[l])
+      for (int c = 0; c < (P.np[f] + 63) / 64; ++c) items.insert(items.end(), {f, c});
+    P.bwd_items_len[l] = (int)items.size() / 2 - P.bwd_items_off[l];
+  }
+  P.d_solve_items = up(items, alloc, st);
 }
 
 void mf_assemble(const MFPlan& P, const LocalLaunch& L, const int* color_subs, const int* color_count_host,
@@ -597,27 +693,32 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st) {
       if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, dsm, st>>>(d, ls); }
     }
   }
+  // solve matrices: Linv_P by tile rows, then G = L_UP Linv_P
+  if (P.inv_len[0]) { BDDC_COUNT(1); k_mf_inv_diag<<<P.inv_len[0], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[0]); }
+  for (size_t q = 2; q < P.inv_len.size(); ++q)
+    if (P.inv_len[q]) {
+      BDDC_COUNT(1);
+      k_mf_inv_step<<<P.inv_len[q], BDDC_THREADS, dsm, st>>>(d, P.d_lists + P.inv_off[q], P.tscratch);
+    }
+  if (P.inv_len[1]) { BDDC_COUNT(1); k_mf_g<<<P.inv_len[1], BDDC_THREADS, dsm, st>>>(d, P.d_lists + P.inv_off[1]); }
 }
 
 void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream_t st) {
   if (P.nfront == 0) return;
   MFDev d = dev_of(P);
   d.W = W;
-  const int* lv = P.d_blob;
   const int* kptr = P.d_blob + P.blob_kptr;
   const int* klist = P.d_blob + P.blob_klist;
-  int maxF = 0;
-  for (int f = 0; f < P.nfront; ++f) maxF = std::max(maxF, P.np[f] + P.nu[f]);
-  const size_t sm = sizeof(double) * (size_t)maxF;
+  const int* lidx = P.d_blob + P.blob_lvl_index;
+  const int2* items = reinterpret_cast<const int2*>(P.d_solve_items);
+  const size_t sm = sizeof(double) * (size_t)P.maxF;
   for (int l = P.nlevel - 1; l >= 0; --l) {
-    const int a = P.lvl_fronts_off[l], n = P.lvl_fronts_off[l + 1] - a;
     BDDC_COUNT(1);
-    k_mf_fwd<<<n, BDDC_THREADS, sm, st>>>(d, lv + a, kptr + a, klist, b);
+    k_mf_fwd2<<<P.fwd_items_len[l], BDDC_THREADS, sm, st>>>(d, items + P.fwd_items_off[l], kptr, klist, lidx, b);
   }
   for (int l = 0; l < P.nlevel; ++l) {
-    const int a = P.lvl_fronts_off[l], n = P.lvl_fronts_off[l + 1] - a;
     BDDC_COUNT(1);
-    k_mf_bwd<<<n, BDDC_THREADS, sm, st>>>(d, lv + a, x);
+    k_mf_bwd2<<<P.bwd_items_len[l], BDDC_THREADS, sm, st>>>(d, items + P.bwd_items_off[l], x);
   }
 }
 

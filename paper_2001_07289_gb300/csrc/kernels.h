@@ -82,6 +82,22 @@ struct MFPlan {
   int *d_upos = nullptr;            // ... and their positions in the front
   long long* d_ugid_off = nullptr;
   double *F = nullptr, *Dinv = nullptr, *W = nullptr;
+  // solve matrices per front: S_f = [Linv_P; G] (F x np, row-major, ld np),
+  // Linv_P = L_P^{-1} and G = L_UP Linv_P
+  std::vector<long long> soff;
+  long long spool = 0;
+  double* S = nullptr;
+  long long* d_soff = nullptr;
+  std::vector<std::vector<int>> trtri_steps;   // per tile step t >= 1: int4 {front, t, s, 0}
+  std::vector<int> diag_items, g_items;        // int4 lists: {front, t, t, 0}, {front, ut, st, 0}
+  std::vector<long long> inv_off;              // device offsets of these lists
+  std::vector<int> inv_len;
+  double* tscratch = nullptr;                  // 4096 doubles per concurrent inverse work item
+  std::vector<int> fwd_items_off, bwd_items_off; // per level into the solve work lists
+  int* d_solve_items = nullptr;                // int2 {front, chunk} lists for the solves
+  std::vector<int> fwd_items_len, bwd_items_len;
+  long long blob_lvl_index = 0;                // per front: its index in the level-ordered list
+  int maxF = 0;
   // work lists per (level, panel step): int4 {front, i, l, j}, concatenated on the device
   std::vector<std::vector<int>> step_potrf, step_trsm, step_syrk;
   std::vector<long long> list_off;
@@ -98,7 +114,9 @@ struct MFPlan {
 };
 
 void mf_plan(MFPlan& P, const CoarseGeom& g, int nc);
-void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc, cudaStream_t st);
+// alloc: memory kept for the solves; tmp_alloc: memory needed during setup only
+void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
+               const std::function<void*(size_t)>& tmp_alloc, cudaStream_t st);
 void mf_assemble(const MFPlan& P, const LocalLaunch& L, const int* color_subs, const int* color_count_host,
                  const int* color_offset_host, cudaStream_t st);
 void mf_factor(const MFPlan& P, int* err, cudaStream_t st);
