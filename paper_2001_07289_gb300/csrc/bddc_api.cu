@@ -24,6 +24,7 @@
 #include "bddc_so.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "stream.cuh"
 
 using namespace bddc;
 
@@ -387,8 +388,14 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     // (at least 4 rows each) and keeps one subdomain's vectors in shared memory
     const int es = h->local_double ? 8 : 4;
     const LocalLaunch& L = h->L;
-    const size_t smem = (size_t)4 * 32768 + 32 + 8 * (L.maxNB + 1) + (size_t)es * (L.maxNN + 2 * L.maxQN + 2);
-    if ((size_t)L.maxQN * es * 4 > 32768 || (size_t)L.maxNc * es * 4 > 32768 || smem > 227 * 1024)
+    const size_t smem = (size_t)4 * 32768 + 32 + 8 * (512 + L.maxNB + 1) + (size_t)es * (512 + L.maxNN + L.maxQN + 2);
+    bool rows_ok = true;
+    for (const SubDesc& s : h->subs) {
+      const int QN = (s.w[0] + 1) * (s.w[1] + 1);
+      if (rows_per_chunk(QN, es) < 1 || (s.nc > 0 && (rows_per_chunk(s.nc, es) < 1 || rows_per_chunk(s.nB, es) < 1)))
+        rows_ok = false;
+    }
+    if (!rows_ok || L.maxQN > 2048 || L.maxNB > 2048 || L.maxNc > 2048 || smem > 227 * 1024)
       throw BddcError(BDDC_ERR_UNSUPPORTED, "subdomains too large for the streamed local solves "
                                             "(at most 1024 FP64 / 2048 FP32 nodes per plane and 1024 coarse DOFs)");
   }
@@ -439,7 +446,10 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   L.facD = h->dalloc(es * lay.D);
   L.facN = h->dalloc(es * lay.N);
   L.Phi = h->dalloc(es * lay.Phi);
-  h->factor_bytes = es * (lay.D + lay.N + lay.Phi);
+  L.facDT = h->dalloc(es * lay.D);
+  L.facNT = h->dalloc(es * lay.N);
+  L.PhiT = h->dalloc(es * lay.Phi);
+  h->factor_bytes = 2 * es * (lay.D + lay.N + lay.Phi);
   L.delta = h->dnew<double>(lay.B);
   L.vgam = h->dnew<double>(lay.B);
   L.vloc = h->dalloc(es * lay.Vec);

@@ -24,6 +24,7 @@ struct LocalLaunch {
   void *facD, *facN, *scratch, *mscratch;
   long long mscratch_stride;
   void *Y, *G, *Lv, *PA, *Sc, *Phi, *vloc;
+  void *facDT, *facNT, *PhiT;      // transposed copies read by the forward sweeps / Phi products
   double* Ac;
   double* delta;
   double* vgam;

@@ -436,25 +436,124 @@ __global__ void k_piece_alpha(MeshDev m, const double* __restrict__ alpha, const
 }
 
 // ---------------------------------------------------------------------------
-// single-RHS sweeps (apply).  v <- A^{-1} v for a plane-block factor, with the
-// factor blocks streamed through the shared-memory ring in row chunks:
-//   forward  (k = 0..nz-1):  t = v_k - M_k v_{k-1};  v_k = Linv_k t
-//   backward (k = nz-1..0):  t = v_k - M_{k+1}^T v_{k+1};  v_k = Linv_k^T t
-// Row products use one warp per row; transposed products accumulate columns
-// per thread (columns tid, tid+256).  v (nz*Q), t, t2 (Q each) in shared memory.
+// transposed copies (setup): every streamed matrix is kept in both
+// orientations so that each product of the apply is a column accumulation.
+// mode 0/1: the Dirichlet / Neumann plane-block slots; mode 2: Phi (nB x nc).
+// grid: (subdomain, matrix, 32x32 tile)
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void sweep_stream(Ring& ring, const T* __restrict__ base, int Q, int nz, T* v, T* t, T* t2, int* err) {
+__global__ void k_transpose(const SubDesc* __restrict__ subs, const T* __restrict__ src, T* __restrict__ dst,
+                            int mode) {
+  __shared__ T tile[32][33];
+  const SubDesc s = subs[blockIdx.x];
+  int rows, cols, nmat;
+  long long base, stride;
+  if (mode == 2) {
+    rows = s.nB; cols = s.nc; nmat = 1; base = s.offPhi; stride = 0;
+  } else {
+    const Grid g = grid_of(s, mode);
+    if (g.gz == 0) return;
+    rows = cols = g.gx * g.gy; nmat = 2 * g.gz - 1; base = mode ? s.offN : s.offD; stride = slot_stride(rows);
+  }
+  if ((int)blockIdx.y >= nmat || rows == 0 || cols == 0) return;
+  const int tc = (cols + 31) / 32, tr = (rows + 31) / 32;
+  for (int t = blockIdx.z; t < tr * tc; t += gridDim.z) {
+    const int r0 = (t / tc) * 32, c0 = (t % tc) * 32;
+    const T* A = src + base + blockIdx.y * stride;
+    T* B = dst + base + blockIdx.y * stride;
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+      int r = e / 32, c = e % 32;
+      if (r0 + r < rows && c0 + c < cols) tile[r][c] = A[(long long)(r0 + r) * cols + c0 + c];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+      int c = e / 32, r = e % 32;
+      if (r0 + r < rows && c0 + c < cols) B[(long long)(c0 + c) * rows + r0 + r] = tile[r][c];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// column accumulation over streamed row chunks: acc[c] += sum_r A[r][c] x[r].
+// With ncol <= blockDim the threads form G = blockDim / ncol row groups (one
+// column each); otherwise every thread owns up to 4 columns.
+// ---------------------------------------------------------------------------
+constexpr int APPLY_THREADS = 512;
+
+struct ColLayout {
+  int ncol, G, grp, col;  // col < 0: idle thread
+};
+__device__ inline ColLayout col_layout(int ncol) {
+  ColLayout L;
+  L.ncol = ncol;
+  if (ncol <= (int)blockDim.x) {
+    L.G = blockDim.x / ncol;
+    L.grp = threadIdx.x / ncol;
+    L.col = (L.grp < L.G) ? (int)(threadIdx.x % ncol) : -1;
+  } else {
+    L.G = 1; L.grp = 0; L.col = threadIdx.x;
+  }
+  return L;
+}
+
+template <typename A, typename T, typename X>
+__device__ inline void col_accumulate(const ColLayout& L, const T* __restrict__ ch, int nr, const X* __restrict__ x,
+                                      A acc[4]) {
+  if (L.col < 0) return;
+  for (int r = L.grp; r < nr; r += L.G) {
+    const A xv = (A)x[r];
+    const T* row = ch + (long long)r * L.ncol;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = L.col + q * (int)blockDim.x;
+      if (q > 0 && L.G > 1) break;
+      if (c < L.ncol) acc[q] += (A)row[c] * xv;
+    }
+  }
+}
+
+// Sums the row-group partials (every thread calls; contains a barrier) and
+// hands each column's total to out(c, total) on the group-0 threads.
+template <typename A, typename Out>
+__device__ inline void col_finish(const ColLayout& L, A acc[4], A* part, Out out) {
+  if (L.G > 1) {
+    if (L.col >= 0) part[L.grp * L.ncol + L.col] = acc[0];
+    __syncthreads();
+    if (L.col >= 0 && L.grp == 0) {
+      A s = A(0);
+      for (int g = 0; g < L.G; ++g) s += part[g * L.ncol + L.col];
+      out(L.col, s);
+    }
+    __syncthreads();
+  } else if (L.col >= 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = L.col + q * (int)blockDim.x;
+      if (c < L.ncol) out(c, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = A(0);
+}
+
+// ---------------------------------------------------------------------------
+// single-RHS sweeps (apply).  v <- A^{-1} v for a plane-block factor:
+//   forward  (k = 0..nz-1):  t = v_k - M_k v_{k-1};  v_k = Linv_k t
+//   backward (k = nz-1..0):  t = v_k - M_{k+1}^T v_{k+1};  v_k = Linv_k^T t
+// The forward products read the transposed slots (facT), the backward ones
+// the slots themselves (fac); both stream row chunks through the ring and
+// accumulate columns.  v (nz*Q), t (Q), part (blockDim) in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, const T* __restrict__ facT, int Q, int nz, T* v,
+                             T* t, T* part, int* err) {
   const int R = rows_per_chunk(Q, (int)sizeof(T));
   const int nch = (Q + R - 1) / R;
   const int nfwd = 2 * nz - 1;
   const long long SS = slot_stride(Q);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < Q; i += blockDim.x) t[i] = v[i];
-  if (nz == 1)
-    for (int i = threadIdx.x; i < Q; i += blockDim.x) t2[i] = v[i];
   __syncthreads();
-  // block bi -> kind (0 fwd L, 1 fwd M, 2 bwd L, 3 bwd M), plane k, slot
   auto decode = [&](int bi, int& kind, int& k, int& slot) {
     if (bi < nfwd) {
       if (bi == 0) { kind = 0; k = 0; }
@@ -468,53 +567,34 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ base, int Q, int 
     }
     slot = (kind == 0 || kind == 2) ? k : nz + k - 1;
   };
-  T acc0 = T(0), acc1 = T(0);
-  const int j0 = threadIdx.x, j1 = threadIdx.x + blockDim.x;
+  const ColLayout L = col_layout(Q);
+  T acc[4] = {T(0), T(0), T(0), T(0)};
   auto src = [&](int c, const void*& p, unsigned& bytes) {
     int kind, k, slot;
     decode(c / nch, kind, k, slot);
     const int r0 = (c % nch) * R, nr = min(R, Q - r0);
-    p = base + slot * SS + (long long)r0 * Q;
+    p = ((kind < 2) ? facT : fac) + slot * SS + (long long)r0 * Q;
     bytes = (unsigned)(nr * Q * sizeof(T));
   };
   auto use = [&](int c, const unsigned char* raw) {
-    const T* ch = reinterpret_cast<const T*>(raw);
     int kind, k, slot;
     const int lc = c % nch;
     decode(c / nch, kind, k, slot);
     const int r0 = lc * R, nr = min(R, Q - r0);
-    if (kind == 0 || kind == 1) {
-      T* vk = v + (long long)k * Q;
-      for (int r = warp; r < nr; r += nw) {
-        const int i = r0 + r;
-        const T* row = ch + (long long)r * Q;
-        T a = T(0);
-        if (kind == 0) {
-          for (int j = lane; j <= i; j += 32) a += row[j] * t[j];
-        } else {
-          const T* vp = vk - Q;
-          for (int j = lane; j < Q; j += 32) a += row[j] * vp[j];
-        }
-        a = warp_sum(a);
-        if (lane == 0) {
-          if (kind == 0) { vk[i] = a; if (k == nz - 1) t2[i] = a; }
-          else t[i] = vk[i] - a;
-        }
-      }
-    } else {
-      const T* in = (kind == 2) ? ((k == nz - 1) ? t2 : t) : v + (long long)k * Q;
-      for (int r = 0; r < nr; ++r) {
-        const T x = in[r0 + r];
-        const T* row = ch + (long long)r * Q;
-        if (j0 < Q) acc0 += row[j0] * x;
-        if (j1 < Q) acc1 += row[j1] * x;
-      }
-      if (lc == nch - 1) {
-        T* dst = (kind == 2) ? v + (long long)k * Q : t;
-        const T* sub = (kind == 3) ? v + (long long)(k - 1) * Q : nullptr;
-        if (j0 < Q) dst[j0] = sub ? sub[j0] - acc0 : acc0;
-        if (j1 < Q) dst[j1] = sub ? sub[j1] - acc1 : acc1;
-        acc0 = acc1 = T(0);
+    const T* in;
+    if (kind == 0) in = t;
+    else if (kind == 1) in = v + (long long)(k - 1) * Q;
+    else if (kind == 2) in = (k == nz - 1) ? v + (long long)k * Q : t;
+    else in = v + (long long)k * Q;
+    col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, in + r0, acc);
+    if (lc == nch - 1) {
+      __syncthreads();   // every row of the block is consumed before outputs overwrite inputs
+      if (kind == 0 || kind == 2) {
+        T* dst = v + (long long)k * Q;
+        col_finish<T>(L, acc, part, [&](int cc, T s) { dst[cc] = s; });
+      } else {
+        const T* base = v + (long long)((kind == 1) ? k : k - 1) * Q;
+        col_finish<T>(L, acc, part, [&](int cc, T s) { t[cc] = base[cc] - s; });
       }
     }
   };
@@ -526,19 +606,19 @@ __host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 8 *
 // Dirichlet solves of the apply.  mode 0: z_I = A_II^{-1} r_I;
 // mode 1: z_I = A_II^{-1} (r_I - t_I).  Writes the interior nodes of z only.
 template <typename T>
-__global__ void __launch_bounds__(BDDC_THREADS)
+__global__ void __launch_bounds__(APPLY_THREADS)
 k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
-                  const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ z,
-                  int mode, int* err) {
+                  const T* __restrict__ facT, const double* __restrict__ r, const double* __restrict__ t,
+                  double* __restrict__ z, int mode, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const SubDesc s = subs[blockIdx.x];
   const Grid g = grid_of(s, 0);
   if (g.gz == 0) return;
   const int Q = g.gx * g.gy, n = Q * g.gz;
   Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  T* v = reinterpret_cast<T*>(smraw + ring_bytes());
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
+  T* v = part + APPLY_THREADS;
   T* tq = v + n;
-  T* t2 = tq + Q;
   ring_init(ring);
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
@@ -548,7 +628,7 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
     v[l] = (T)val;
   }
   __syncthreads();
-  sweep_stream<T>(ring, fac + s.offD, Q, g.gz, v, tq, t2, err);
+  sweep_stream<T>(ring, fac + s.offD, facT + s.offD, Q, g.gz, v, tq, part, err);
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
     long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
@@ -560,8 +640,8 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
 // coarse right-hand side rc_i = Phi_i^T r_i, and the constrained Neumann solve
 // y = A_rr^{-1} r_i,r (into vloc).
 template <typename T>
-__global__ void __launch_bounds__(BDDC_THREADS)
-k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac, const T* __restrict__ facT,
                 const T* __restrict__ Phi, const double* __restrict__ delta,
                 const double* __restrict__ r, const double* __restrict__ t, T* __restrict__ vloc,
                 double* __restrict__ rcl, int* err) {
@@ -570,10 +650,11 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const int Q = px * py, n = Q * pz;
   Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  double* rg = reinterpret_cast<double*>(smraw + ring_bytes());
-  T* v = reinterpret_cast<T*>(rg + s.nB);
+  double* dpart = reinterpret_cast<double*>(smraw + ring_bytes());
+  double* rg = dpart + APPLY_THREADS;
+  T* part = reinterpret_cast<T*>(rg + s.nB + 1);
+  T* v = part + APPLY_THREADS;
   T* tq = v + n;
-  T* t2 = tq + Q;
   ring_init(ring);
   for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = T(0);
   __syncthreads();
@@ -588,10 +669,11 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
   }
   __syncthreads();
   if (s.nc > 0) {
-    // rc_i = Phi_i^T r_i: columns j = tid + 256 q accumulate over streamed rows
+    // rc_i = Phi_i^T r_i: columns of Phi accumulate over streamed rows
     const int R = rows_per_chunk(s.nc, (int)sizeof(T));
     const int nch = (s.nB + R - 1) / R;
     const T* P = Phi + s.offPhi;
+    const ColLayout L = col_layout(s.nc);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     auto src = [&](int c, const void*& p, unsigned& bytes) {
       const int r0 = c * R, nr = min(R, s.nB - r0);
@@ -599,40 +681,29 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
       bytes = (unsigned)(nr * s.nc * sizeof(T));
     };
     auto use = [&](int c, const unsigned char* raw) {
-      const T* ch = reinterpret_cast<const T*>(raw);
       const int r0 = c * R, nr = min(R, s.nB - r0);
-      for (int rr = 0; rr < nr; ++rr) {
-        const double x = rg[r0 + rr];
-        const T* row = ch + (long long)rr * s.nc;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int j = threadIdx.x + q * BDDC_THREADS;
-          if (j < s.nc) acc[q] += (double)row[j] * x;
-        }
-      }
+      col_accumulate<double, T, double>(L, reinterpret_cast<const T*>(raw), nr, rg + r0, acc);
     };
     ring_run(ring, nch, src, use, err);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = threadIdx.x + q * BDDC_THREADS;
-      if (j < s.nc) rcl[s.cofs + j] = acc[q];
-    }
+    col_finish<double>(L, acc, dpart, [&](int cc, double sum) { rcl[s.cofs + cc] = sum; });
   }
-  sweep_stream<T>(ring, fac + s.offN, Q, pz, v, tq, t2, err);
+  sweep_stream<T>(ring, fac + s.offN, facT + s.offN, Q, pz, v, tq, part, err);
   for (int l = threadIdx.x; l < n; l += blockDim.x) vloc[s.offVec + l] = v[l];
 }
 
-// v_i on the box surface: Phi_i (u_c|_i - [0; C_r y]) + y.
+// v_i on the box surface: Phi_i (u_c|_i - [0; C_r y]) + y, as a column
+// accumulation over the rows of Phi_i^T.
 template <typename T>
-__global__ void __launch_bounds__(BDDC_THREADS)
+__global__ void __launch_bounds__(APPLY_THREADS)
 k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict__ lc,
-                 const T* __restrict__ Phi, const T* __restrict__ vloc, const double* __restrict__ uc,
+                 const T* __restrict__ PhiT, const T* __restrict__ vloc, const double* __restrict__ uc,
                  double* __restrict__ vgam, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const SubDesc s = subs[blockIdx.x];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  double* ut = reinterpret_cast<double*>(smraw + ring_bytes());
+  double* dpart = reinterpret_cast<double*>(smraw + ring_bytes());
+  double* ut = dpart + APPLY_THREADS;
   ring_init(ring);
   const T* y = vloc + s.offVec;
   for (int j = threadIdx.x; j < s.nc; j += blockDim.x) {
@@ -648,40 +719,29 @@ k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict
     ut[j] = val;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (s.nc == 0) {
-    for (int b = threadIdx.x; b < s.nB; b += blockDim.x) {
-      int ix, iy, iz;
-      surf_coords(b, px, py, pz, ix, iy, iz);
-      vgam[s.offB + b] = (double)y[ix + px * (iy + py * iz)];
-    }
-    return;
+  auto out = [&](int b, double sum) {
+    int ix, iy, iz;
+    surf_coords(b, px, py, pz, ix, iy, iz);
+    vgam[s.offB + b] = sum + (double)y[ix + px * (iy + py * iz)];
+  };
+  const ColLayout L = col_layout(s.nB);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (s.nc > 0) {
+    const int R = rows_per_chunk(s.nB, (int)sizeof(T));
+    const int nch = (s.nc + R - 1) / R;
+    const T* P = PhiT + s.offPhi;
+    auto src = [&](int c, const void*& p, unsigned& bytes) {
+      const int r0 = c * R, nr = min(R, s.nc - r0);
+      p = P + (long long)r0 * s.nB;
+      bytes = (unsigned)(nr * s.nB * sizeof(T));
+    };
+    auto use = [&](int c, const unsigned char* raw) {
+      const int r0 = c * R, nr = min(R, s.nc - r0);
+      col_accumulate<double, T, double>(L, reinterpret_cast<const T*>(raw), nr, ut + r0, acc);
+    };
+    ring_run(ring, nch, src, use, err);
   }
-  const int R = rows_per_chunk(s.nc, (int)sizeof(T));
-  const int nch = (s.nB + R - 1) / R;
-  const T* P = Phi + s.offPhi;
-  auto src = [&](int c, const void*& p, unsigned& bytes) {
-    const int r0 = c * R, nr = min(R, s.nB - r0);
-    p = P + (long long)r0 * s.nc;
-    bytes = (unsigned)(nr * s.nc * sizeof(T));
-  };
-  auto use = [&](int c, const unsigned char* raw) {
-    const T* ch = reinterpret_cast<const T*>(raw);
-    const int r0 = c * R, nr = min(R, s.nB - r0);
-    for (int rr = warp; rr < nr; rr += nw) {
-      const T* row = ch + (long long)rr * s.nc;
-      double a = 0.0;
-      for (int j = lane; j < s.nc; j += 32) a += (double)row[j] * ut[j];
-      a = warp_sum(a);
-      if (lane == 0) {
-        int ix, iy, iz;
-        const int b = r0 + rr;
-        surf_coords(b, px, py, pz, ix, iy, iz);
-        vgam[s.offB + b] = a + (double)y[ix + px * (iy + py * iz)];
-      }
-    }
-  };
-  ring_run(ring, nch, src, use, err);
+  col_finish<double>(L, acc, dpart, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -699,13 +759,15 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
   if (L.maxQD > 0) {
     k_assemble<T><<<dim3(S, L.maxNzD, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facD, 0);
     k_btchol<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, facD, W, 0, L.err);
-    BDDC_COUNT(2);
+    k_transpose<T><<<dim3(S, 2 * L.maxNzD - 1, 32), 256, 0, st>>>(L.subs, facD, (T*)L.facDT, 0);
+    BDDC_COUNT(3);
   }
   if (ev) cudaEventRecord(ev[0], st);
   // Neumann
   k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1);
   k_btchol<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, facN, W, 1, L.err);
-  BDDC_COUNT(2);
+  k_transpose<T><<<dim3(S, 2 * L.maxNzN - 1, 32), 256, 0, st>>>(L.subs, facN, (T*)L.facNT, 1);
+  BDDC_COUNT(3);
   if (ev) cudaEventRecord(ev[1], st);
   // coarse basis
   T* Y = (T*)L.Y; T* G = (T*)L.G; T* Lv = (T*)L.Lv; T* PA = (T*)L.PA; T* Sc = (T*)L.Sc; T* Phi = (T*)L.Phi;
@@ -720,8 +782,9 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
     k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 0);
     k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 1);
     k_phi_surface<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, PA, Phi);
+    k_transpose<T><<<dim3(S, 1, 64), 256, 0, st>>>(L.subs, Phi, (T*)L.PhiT, 2);
     k_local_coarse_matrix<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y, Lv, Sc, L.Ac);
-    BDDC_COUNT(8);
+    BDDC_COUNT(9);
   }
   if (ev) cudaEventRecord(ev[2], st);
 }
@@ -755,24 +818,26 @@ template <typename T>
 void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, double* z, int mode, cudaStream_t st) {
   if (L.maxQD == 0) return;
   BDDC_COUNT(1);
-  size_t sm = ring_bytes() + sizeof(T) * ((size_t)L.maxND + 2 * L.maxQD + 2);
-  k_dirichlet_solve<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facD, r, t, z, mode, L.err);
+  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxND + L.maxQD + 2);
+  k_dirichlet_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facD, (const T*)L.facDT, r, t,
+                                                         z, mode, L.err);
 }
 
 template <typename T>
 void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
-  size_t sm = ring_bytes() + sizeof(double) * (L.maxNB + 1) + sizeof(T) * ((size_t)L.maxNN + 2 * L.maxQN + 2);
+  size_t sm = ring_bytes() + sizeof(double) * ((size_t)APPLY_THREADS + L.maxNB + 1) +
+              sizeof(T) * ((size_t)APPLY_THREADS + L.maxNN + L.maxQN + 2);
   BDDC_COUNT(1);
-  k_neumann_solve<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta,
-                                                      r, t, (T*)L.vloc, L.rcl, L.err);
+  k_neumann_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facN, (const T*)L.facNT,
+                                                       (const T*)L.Phi, L.delta, r, t, (T*)L.vloc, L.rcl, L.err);
 }
 
 template <typename T>
 void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t st) {
-  size_t sm = ring_bytes() + sizeof(double) * (L.maxNc + 1);
+  size_t sm = ring_bytes() + sizeof(double) * ((size_t)APPLY_THREADS + L.maxNc + 1);
   BDDC_COUNT(1);
-  k_neumann_finish<T><<<L.nsub, BDDC_THREADS, sm, st>>>(L.subs, L.lc, (const T*)L.Phi, (const T*)L.vloc, uc,
-                                                       L.vgam, L.err);
+  k_neumann_finish<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.lc, (const T*)L.PhiT, (const T*)L.vloc, uc,
+                                                        L.vgam, L.err);
 }
 
 template void launch_setup_local<float>(const LocalLaunch&, cudaStream_t, cudaEvent_t*);

@@ -103,11 +103,15 @@ __device__ void ring_run(Ring& r, int nchunks, Src src, Use use, int* err) {
   r.base = first + nchunks;
 }
 
-// Rows of a row-major matrix with `cols` entries of `es` bytes per chunk:
-// the largest multiple of 4 that fits a buffer (keeps 16-byte alignment).
+// Rows of a row-major matrix with `cols` entries of `es` bytes per chunk: the
+// largest count that fits a buffer and keeps every chunk start 16-byte aligned
+// (0 if no such count exists).
 __host__ __device__ inline int rows_per_chunk(int cols, int es) {
-  int r = CHB / (cols * es);
-  return r & ~3;
+  const int row = cols * es;
+  int step = 1;
+  while ((step * row) % 16) ++step;   // 1, 2 or 4
+  const int r = CHB / row;
+  return (r / step) * step;
 }
 
 }  // namespace bddc
