@@ -143,6 +143,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists)")
+    ap.add_argument("--only-applies", type=int, default=0,
+                    help="set up once, then run this many preconditioner applies (for profiler launch lists)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -190,6 +192,23 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+
+    if args.only_applies:
+        pre = BDDC.from_problem(p, alpha=alpha, precision=args.precision)
+        r = torch.from_numpy(inputs.random_node_vector(p.nx, p.ny, p.nz, 5)).cuda()
+        z = torch.empty_like(r)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.only_applies):
+            pre.apply(r, out=z)
+        e1.record(stream)
+        e1.synchronize()
+        if rank == 0:
+            print(json.dumps({"metric": "precond apply", "applies": args.only_applies,
+                              "ms_per_apply": round(e0.elapsed_time(e1) / args.only_applies, 4)}))
+        pre.close()
+        return
 
     for _ in range(args.warmup):
         pre, _ = step(args.precision)
@@ -283,7 +302,7 @@ def main():
     info = infos[-1]
     n_free = info["n_free"]
     iters = stats[-1]["iterations"]
-    phases = dict(zip(["checks_weights", "dirichlet_factor", "neumann_factor", "coarse_basis",
+    phases = dict(zip(["checks_weights", "local_assembly", "local_factorisations", "coarse_basis",
                        "coarse_assembly", "coarse_cholesky"], [round(v, 3) for v in info["phase_ms"]]))
     setup_ms = info["setup_ms"]
     solve_ms = statistics.mean(s["solve_ms"] for s in stats)

@@ -101,8 +101,9 @@ typedef struct {
     long long bytes;      /* device memory held by the handle                  */
     long long factor_bytes;  /* local factors + Phi + coarse factor            */
     double setup_ms;      /* device time of bddc_setup (CUDA events)          */
-    double phase_ms[6];   /* setup phases: 0 checks+weights, 1 Dirichlet factor,
-                             2 Neumann factor, 3 coarse basis, 4 coarse assembly,
+    double phase_ms[6];   /* setup phases: 0 checks+weights, 1 local assembly,
+                             2 local Dirichlet and Neumann factorisations (run
+                             together), 3 coarse basis, 4 coarse assembly,
                              5 coarse Cholesky                                 */
     long long launches;   /* kernels launched for this handle since its setup
                              began (setup, applies, solves, gradients)        */

@@ -285,7 +285,8 @@ void build_metadata(bddc_handle* h) {
         const int QD = hasI ? qx * qy : 0, nzD = hasI ? qz : 0;
         s.offD = offD; offD += hasI ? (long long)(2 * nzD - 1) * slot_stride(QD) : 0;
         s.offN = offN; offN += (long long)(2 * pz - 1) * slot_stride(QN);
-        s.offW = offW; offW += 2LL * QN * QN + 1024LL * ((std::max(QN, s.na) + 31) / 32);
+        s.offW = offW;   // Neumann scratch, then Dirichlet scratch (factored concurrently)
+        offW += 2LL * QN * QN + 1024LL * ((std::max(QN, s.na) + 31) / 32) + 2LL * QD * QD + 1024LL * ((QD + 31) / 32);
         s.offY = offY; offY += (long long)NN * s.nc;
         s.offG = offG; offG += (long long)s.na * s.nc;
         s.offL = offL; offL += (long long)s.na * s.nv;
@@ -345,7 +346,8 @@ Layout layout_of(const bddc_handle* h) {
     const int QD = hasI ? qx * qy : 0;
     o.D = std::max(o.D, s.offD + (hasI ? (long long)(2 * qz - 1) * slot_stride(QD) : 0));
     o.N = std::max(o.N, s.offN + (long long)(2 * pz - 1) * slot_stride(QN));
-    o.W = std::max(o.W, s.offW + 2LL * QN * QN + 1024LL * ((std::max(QN, s.na) + 31) / 32));
+    o.W = std::max(o.W, s.offW + 2LL * QN * QN + 1024LL * ((std::max(QN, s.na) + 31) / 32) + 2LL * QD * QD +
+                            1024LL * ((QD + 31) / 32));
     o.Y = std::max(o.Y, s.offY + (long long)NN * s.nc);
     o.G = std::max(o.G, s.offG + (long long)s.na * s.nc);
     o.L = std::max(o.L, s.offL + (long long)s.na * s.nv);

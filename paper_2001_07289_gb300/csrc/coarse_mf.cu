@@ -460,9 +460,16 @@ k_mf_fwd2(MFDev d, const int2* __restrict__ items, const int* __restrict__ kid_p
   for (int r = r0 + warp; r < r1; r += nw) {
     const double* row = S + (long long)r * np;
     const int cend = (r < np) ? r + 1 : np;
-    double acc = 0.0;
-    for (int c = lane; c < cend; c += 32) acc = fma(row[c], w[c], acc);
-    acc = mf_wsum(acc);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;   // four independent chains, loads in flight
+    int c = lane;
+    for (; c + 96 < cend; c += 128) {
+      a0 = fma(row[c], w[c], a0);
+      a1 = fma(row[c + 32], w[c + 32], a1);
+      a2 = fma(row[c + 64], w[c + 64], a2);
+      a3 = fma(row[c + 96], w[c + 96], a3);
+    }
+    for (; c < cend; c += 32) a0 = fma(row[c], w[c], a0);
+    double acc = mf_wsum((a0 + a1) + (a2 + a3));
     if (lane == 0) Wf[r] = (r < np) ? acc : w[r] - acc;
   }
 }
@@ -486,8 +493,19 @@ k_mf_bwd2(MFDev d, const int2* __restrict__ items, double* x) {
   const int c = chunk * 64 + cl;
   double acc = 0.0;
   if (c < np) {
-    for (int r = c + grp; r < np; r += 4) acc = fma(S[(long long)r * np + c], vec[r], acc);
-    for (int r = np + grp; r < F; r += 4) acc = fma(-S[(long long)r * np + c], vec[r], acc);
+    // rows r >= c of Linv_P (+) and all rows of G (-), four independent chains
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int r = c + grp;
+    for (; r + 12 < F; r += 16) {
+      const double s0 = (r < np) ? 1.0 : -1.0, s1 = (r + 4 < np) ? 1.0 : -1.0;
+      const double s2 = (r + 8 < np) ? 1.0 : -1.0, s3 = (r + 12 < np) ? 1.0 : -1.0;
+      a0 = fma(s0 * S[(long long)r * np + c], vec[r], a0);
+      a1 = fma(s1 * S[(long long)(r + 4) * np + c], vec[r + 4], a1);
+      a2 = fma(s2 * S[(long long)(r + 8) * np + c], vec[r + 8], a2);
+      a3 = fma(s3 * S[(long long)(r + 12) * np + c], vec[r + 12], a3);
+    }
+    for (; r < F; r += 4) a0 = fma(((r < np) ? 1.0 : -1.0) * S[(long long)r * np + c], vec[r], a0);
+    acc = (a0 + a1) + (a2 + a3);
   }
   part[grp][cl] = acc;
   __syncthreads();

@@ -39,6 +39,14 @@ __device__ void cta_gemm(int M, int N, int K, T alpha,
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int tilesM = (M + GBM - 1) / GBM, tilesN = (N + GBN - 1) / GBN;
+  // element e of a 64x16 (A) or 16x64 (B) slice handled by this thread
+  int aii[4], akk[4], bjj[4], bkk[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int e = tid + BDDC_THREADS * r;
+    if (TA) { aii[r] = e & 63; akk[r] = e >> 6; } else { aii[r] = e >> 4; akk[r] = e & 15; }
+    if (TB) { bjj[r] = e >> 4; bkk[r] = e & 15; } else { bjj[r] = e & 63; bkk[r] = e >> 6; }
+  }
   for (int t = 0; t < tilesM * tilesN; ++t) {
     const int i0 = (t / tilesN) * GBM, j0 = (t % tilesN) * GBN;
     if (lowerC && j0 > i0 + GBM - 1) continue;
@@ -52,25 +60,27 @@ __device__ void cta_gemm(int M, int N, int K, T alpha,
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+    // register prefetch of the first K-slice; the next slice's global loads
+    // are issued before the current slice is multiplied out of shared memory
+    T ra[4], rb[4];
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int gi = i0 + aii[r], gk = k0 + akk[r];
+        ra[r] = (gi < M && gk < kend) ? (TA ? A[(long long)gk * lda + gi] : A[(long long)gi * lda + gk]) : T(0);
+        const int gj = j0 + bjj[r], gk2 = k0 + bkk[r];
+        rb[r] = (gj < N && gk2 < kend) ? (TB ? B[(long long)gj * ldb + gk2] : B[(long long)gk2 * ldb + gj]) : T(0);
+      }
+    };
+    if (kbeg < kend) fetch(kbeg);
     for (int k0 = kbeg; k0 < kend; k0 += GBK) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        int e = tid + BDDC_THREADS * r;
-        int ii, kk;
-        if (TA) { ii = e & 63; kk = e >> 6; } else { ii = e >> 4; kk = e & 15; }
-        int gi = i0 + ii, gk = k0 + kk;
-        T v = T(0);
-        if (gi < M && gk < kend) v = TA ? A[(long long)gk * lda + gi] : A[(long long)gi * lda + gk];
-        sm.As[kk][ii] = v;
-        int jj;
-        if (TB) { jj = e >> 4; kk = e & 15; } else { jj = e & 63; kk = e >> 6; }
-        int gj = j0 + jj;
-        gk = k0 + kk;
-        T w = T(0);
-        if (gj < N && gk < kend) w = TB ? B[(long long)gj * ldb + gk] : B[(long long)gk * ldb + gj];
-        sm.Bs[kk][jj] = w;
+        sm.As[akk[r]][aii[r]] = ra[r];
+        sm.Bs[bkk[r]][bjj[r]] = rb[r];
       }
       __syncthreads();
+      if (k0 + GBK < kend) fetch(k0 + GBK);
 #pragma unroll
       for (int kk = 0; kk < GBK; ++kk) {
         T a[4], b[4];
@@ -114,7 +124,8 @@ __device__ void tile_chol(T* S, int n, DenseSmem<T>& sm) {
       S[c * TLD + c] = sqrt(d);
     }
     __syncthreads();
-    for (int i = c + 1 + tid; i < n; i += BDDC_THREADS) S[i * TLD + c] /= S[c * TLD + c];
+    const T rinv = T(1) / S[c * TLD + c];
+    for (int i = c + 1 + tid; i < n; i += BDDC_THREADS) S[i * TLD + c] *= rinv;
     __syncthreads();
     const int m = n - c - 1;
     for (int idx = tid; idx < m * m; idx += BDDC_THREADS) {

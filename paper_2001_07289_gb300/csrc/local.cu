@@ -133,17 +133,19 @@ __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const do
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_btchol(const SubDesc* __restrict__ subs, T* __restrict__ fac, T* __restrict__ scratch, int neumann,
+k_btchol(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict__ facD, T* __restrict__ scratch,
          int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
   const SubDesc s = subs[blockIdx.x];
+  const int neumann = blockIdx.y == 0;   // y = 0: Neumann, y = 1: Dirichlet (concurrent)
   const Grid g = grid_of(s, neumann);
   if (g.gz == 0) return;
   const int Q = g.gx * g.gy;
   const long long QQ = (long long)Q * Q, SS = slot_stride(Q);
-  T* base = fac + (neumann ? s.offN : s.offD);
-  T* W1 = scratch + s.offW;
+  T* base = neumann ? facN + s.offN : facD + s.offD;
+  const int QN = (s.w[0] + 1) * (s.w[1] + 1);
+  T* W1 = scratch + s.offW + (neumann ? 0 : 2LL * QN * QN + 1024LL * ((max(QN, s.na) + 31) / 32));
   T* W2 = W1 + QQ;
   T* diag = W2 + QQ;
   for (int k = 0; k < g.gz; ++k) {
@@ -755,19 +757,22 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
   const int S = L.nsub;
   T* facD = (T*)L.facD; T* facN = (T*)L.facN; T* W = (T*)L.scratch;
   size_t sm = dense_smem<T>();
-  // Dirichlet
+  // local assembly (Dirichlet and Neumann plane blocks)
   if (L.maxQD > 0) {
     k_assemble<T><<<dim3(S, L.maxNzD, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facD, 0);
-    k_btchol<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, facD, W, 0, L.err);
-    k_transpose<T><<<dim3(S, 2 * L.maxNzD - 1, 32), 256, 0, st>>>(L.subs, facD, (T*)L.facDT, 0);
-    BDDC_COUNT(3);
+    BDDC_COUNT(1);
   }
-  if (ev) cudaEventRecord(ev[0], st);
-  // Neumann
   k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1);
-  k_btchol<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, facN, W, 1, L.err);
+  BDDC_COUNT(1);
+  if (ev) cudaEventRecord(ev[0], st);
+  // both factorisations in one launch: y = 0 Neumann, y = 1 Dirichlet
+  k_btchol<T><<<dim3(S, L.maxQD > 0 ? 2 : 1), BDDC_THREADS, sm, st>>>(L.subs, facN, facD, W, L.err);
   k_transpose<T><<<dim3(S, 2 * L.maxNzN - 1, 32), 256, 0, st>>>(L.subs, facN, (T*)L.facNT, 1);
-  BDDC_COUNT(3);
+  BDDC_COUNT(2);
+  if (L.maxQD > 0) {
+    k_transpose<T><<<dim3(S, 2 * L.maxNzD - 1, 32), 256, 0, st>>>(L.subs, facD, (T*)L.facDT, 0);
+    BDDC_COUNT(1);
+  }
   if (ev) cudaEventRecord(ev[1], st);
   // coarse basis
   T* Y = (T*)L.Y; T* G = (T*)L.G; T* Lv = (T*)L.Lv; T* PA = (T*)L.PA; T* Sc = (T*)L.Sc; T* Phi = (T*)L.Phi;
