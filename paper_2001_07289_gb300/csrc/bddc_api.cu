@@ -386,11 +386,11 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->n_free = (long long)(M.nx - 1) * (M.ny - 1) * (M.nz - 1);
   build_metadata(h);
   {
-    // the apply streams rows of plane blocks and of Phi through 32 KiB chunks
-    // (at least 4 rows each) and keeps one subdomain's vectors in shared memory
+    // the apply streams rows of plane blocks and of Phi through the shared-
+    // memory ring and keeps one subdomain's vectors in shared memory
     const int es = h->local_double ? 8 : 4;
     const LocalLaunch& L = h->L;
-    const size_t smem = (size_t)4 * 32768 + 32 + 8 * (512 + L.maxNB + 1) + (size_t)es * (512 + L.maxNN + L.maxQN + 2);
+    const size_t smem = (size_t)NBUF * CHB + 8 * NBUF + (size_t)es * (512 + L.maxNB + 1 + L.maxNN + L.maxQN + 2);
     bool rows_ok = true;
     for (const SubDesc& s : h->subs) {
       const int QN = (s.w[0] + 1) * (s.w[1] + 1);

@@ -20,6 +20,8 @@ struct DenseSmem {
   T Bs[GBK][GBN + GPAD];
   T t0[TILE * TLD];
   T t1[TILE * TLD];
+  T t2[TILE * TLD];
+  T rd[TILE];
   int flag;
 };
 
@@ -37,7 +39,11 @@ __device__ void cta_gemm(int M, int N, int K, T alpha,
                          T beta, T* C, int ldc, int triA, int triB, bool lowerC,
                          DenseSmem<T>& sm) {
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  // output mapping: warp w owns the 16x32 sub-block (rows 16*(w>>1), cols
+  // 32*(w&1)) of the 64x64 tile; lane (lr, lc) owns its 4x4 cells.  Warps
+  // whose sub-block lies outside M x N skip the multiply-adds entirely.
+  const int warp = tid >> 5, lane = tid & 31;
+  const int orow = 16 * (warp >> 1) + 4 * (lane >> 3), ocol = 32 * (warp & 1) + 4 * (lane & 7);
   const int tilesM = (M + GBM - 1) / GBM, tilesN = (N + GBN - 1) / GBN;
   // element e of a 64x16 (A) or 16x64 (B) slice handled by this thread
   int aii[4], akk[4], bjj[4], bkk[4];
@@ -60,6 +66,8 @@ __device__ void cta_gemm(int M, int N, int K, T alpha,
     for (int r = 0; r < 4; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+    const bool wactive = (i0 + 16 * (warp >> 1) < M) && (j0 + 32 * (warp & 1) < N) &&
+                         !(lowerC && j0 + 32 * (warp & 1) > i0 + 16 * (warp >> 1) + 15);
     // register prefetch of the first K-slice; the next slice's global loads
     // are issued before the current slice is multiplied out of shared memory
     T ra[4], rb[4];
@@ -81,27 +89,29 @@ __device__ void cta_gemm(int M, int N, int K, T alpha,
       }
       __syncthreads();
       if (k0 + GBK < kend) fetch(k0 + GBK);
+      if (wactive) {
 #pragma unroll
-      for (int kk = 0; kk < GBK; ++kk) {
-        T a[4], b[4];
+        for (int kk = 0; kk < GBK; ++kk) {
+          T a[4], b[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = sm.As[kk][ty * 4 + r];
+          for (int r = 0; r < 4; ++r) a[r] = sm.As[kk][orow + r];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) b[c] = sm.Bs[kk][tx * 4 + c];
+          for (int c = 0; c < 4; ++c) b[c] = sm.Bs[kk][ocol + c];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+          for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+            for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
       }
       __syncthreads();
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      int gi = i0 + ty * 4 + r;
+      int gi = i0 + orow + r;
       if (gi >= M) continue;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        int gj = j0 + tx * 4 + c;
+        int gj = j0 + ocol + c;
         if (gj >= N) continue;
         T* p = C + (long long)gi * ldc + gj;
         *p = (beta == T(0)) ? alpha * acc[r][c] : alpha * acc[r][c] + beta * (*p);
@@ -137,15 +147,18 @@ __device__ void tile_chol(T* S, int n, DenseSmem<T>& sm) {
 }
 
 // X = L^{-1} for a lower n x n tile (both ld TLD); zeros above the diagonal.
+// rdiag: n entries of scratch for the reciprocal diagonal.
 template <typename T>
-__device__ void tile_inv(const T* L, T* X, int n) {
+__device__ void tile_inv(const T* L, T* X, int n, T* rdiag) {
   const int j = threadIdx.x;
+  if (j < n) rdiag[j] = T(1) / L[j * TLD + j];
+  __syncthreads();
   if (j < n) {
     for (int i = 0; i < n; ++i) {
       if (i < j) { X[i * TLD + j] = T(0); continue; }
       T s = (i == j) ? T(1) : T(0);
       for (int k = j; k < i; ++k) s -= L[i * TLD + k] * X[k * TLD + j];
-      X[i * TLD + j] = s / L[i * TLD + i];
+      X[i * TLD + j] = s * rdiag[i];
     }
   }
   __syncthreads();
@@ -169,29 +182,30 @@ __device__ bool cta_chol_inv(T* S, int lds, T* Linv, int ldl, int n, T* diag, De
     }
     __syncthreads();
     tile_chol(sm.t0, nb, sm);
-    tile_inv(sm.t0, sm.t1, nb);
+    tile_inv(sm.t0, sm.t1, nb, sm.rd);
     for (int idx = tid; idx < nb * nb; idx += BDDC_THREADS) {
       int i = idx / nb, j = idx % nb;
       if (j <= i) S[(long long)(j0 + i) * lds + j0 + j] = sm.t0[i * TLD + j];
       diag[jb * TILE * TILE + i * TILE + j] = sm.t1[i * TLD + j];
     }
-    // panel below the diagonal tile: P = P * Tinv^T
-    for (int i = j0 + nb + tid; i < n; i += BDDC_THREADS) {
-      T r[TILE];
-      T* row = S + (long long)i * lds + j0;
-#pragma unroll
-      for (int k = 0; k < TILE; ++k) r[k] = (k < nb) ? row[k] : T(0);
-#pragma unroll
-      for (int c = 0; c < TILE; ++c) {
-        if (c >= nb) break;
-        T s = T(0);
-#pragma unroll
-        for (int k = 0; k < TILE; ++k)
-          if (k <= c) s += r[k] * sm.t1[c * TLD + k];
-        row[c] = s;
-      }
-    }
+    // panel below the diagonal tile: P = P * Tinv^T, 32 rows at a time
+    // through shared memory, every thread producing 4 outputs
     __syncthreads();
+    for (int p0 = j0 + nb; p0 < n; p0 += TILE) {
+      const int pr = min(TILE, n - p0);
+      for (int idx = tid; idx < TILE * TILE; idx += BDDC_THREADS) {
+        int i = idx / TILE, k = idx % TILE;
+        sm.t2[i * TLD + k] = (i < pr && k < nb) ? S[(long long)(p0 + i) * lds + j0 + k] : T(0);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < pr * nb; idx += BDDC_THREADS) {
+        const int i = idx / nb, c = idx % nb;
+        T acc = T(0);
+        for (int k = 0; k <= c; ++k) acc += sm.t2[i * TLD + k] * sm.t1[c * TLD + k];
+        S[(long long)(p0 + i) * lds + j0 + c] = acc;
+      }
+      __syncthreads();
+    }
     const int m = n - j0 - nb;
     if (m > 0) {
       const T* P = S + (long long)(j0 + nb) * lds + j0;

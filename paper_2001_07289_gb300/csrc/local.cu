@@ -652,10 +652,9 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const int Q = px * py, n = Q * pz;
   Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  double* dpart = reinterpret_cast<double*>(smraw + ring_bytes());
-  double* rg = dpart + APPLY_THREADS;
-  T* part = reinterpret_cast<T*>(rg + s.nB + 1);
-  T* v = part + APPLY_THREADS;
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
+  T* rg = part + APPLY_THREADS;
+  T* v = rg + s.nB + 1;
   T* tq = v + n;
   ring_init(ring);
   for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = T(0);
@@ -666,17 +665,18 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
     long long gi = nodeid(m.NX, m.NY, s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz);
     double d = delta[s.offB + b];
     double val = (d == 0.0) ? 0.0 : d * (r[gi] - t[gi]);
-    rg[b] = val;
+    rg[b] = (T)val;
     if (!neumann_fixed(m, s, ix, iy, iz)) v[ix + px * (iy + py * iz)] = (T)val;
   }
   __syncthreads();
   if (s.nc > 0) {
-    // rc_i = Phi_i^T r_i: columns of Phi accumulate over streamed rows
+    // rc_i = Phi_i^T r_i in the local precision: columns of Phi accumulate
+    // over streamed rows
     const int R = rows_per_chunk(s.nc, (int)sizeof(T));
     const int nch = (s.nB + R - 1) / R;
     const T* P = Phi + s.offPhi;
     const ColLayout L = col_layout(s.nc);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    T acc[4] = {T(0), T(0), T(0), T(0)};
     auto src = [&](int c, const void*& p, unsigned& bytes) {
       const int r0 = c * R, nr = min(R, s.nB - r0);
       p = P + (long long)r0 * s.nc;
@@ -684,10 +684,10 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
     };
     auto use = [&](int c, const unsigned char* raw) {
       const int r0 = c * R, nr = min(R, s.nB - r0);
-      col_accumulate<double, T, double>(L, reinterpret_cast<const T*>(raw), nr, rg + r0, acc);
+      col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, rg + r0, acc);
     };
     ring_run(ring, nch, src, use, err);
-    col_finish<double>(L, acc, dpart, [&](int cc, double sum) { rcl[s.cofs + cc] = sum; });
+    col_finish<T>(L, acc, part, [&](int cc, T sum) { rcl[s.cofs + cc] = (double)sum; });
   }
   sweep_stream<T>(ring, fac + s.offN, facT + s.offN, Q, pz, v, tq, part, err);
   for (int l = threadIdx.x; l < n; l += blockDim.x) vloc[s.offVec + l] = v[l];
@@ -704,8 +704,8 @@ k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict
   const SubDesc s = subs[blockIdx.x];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  double* dpart = reinterpret_cast<double*>(smraw + ring_bytes());
-  double* ut = dpart + APPLY_THREADS;
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
+  T* ut = part + APPLY_THREADS;
   ring_init(ring);
   const T* y = vloc + s.offVec;
   for (int j = threadIdx.x; j < s.nc; j += blockDim.x) {
@@ -718,16 +718,16 @@ k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict
           for (int ix = c.lo[0]; ix <= c.hi[0]; ++ix) sum += (double)y[ix + px * (iy + py * iz)];
       val -= sum / c.count;
     }
-    ut[j] = val;
+    ut[j] = (T)val;
   }
   __syncthreads();
-  auto out = [&](int b, double sum) {
+  auto out = [&](int b, T sum) {
     int ix, iy, iz;
     surf_coords(b, px, py, pz, ix, iy, iz);
-    vgam[s.offB + b] = sum + (double)y[ix + px * (iy + py * iz)];
+    vgam[s.offB + b] = (double)sum + (double)y[ix + px * (iy + py * iz)];
   };
   const ColLayout L = col_layout(s.nB);
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  T acc[4] = {T(0), T(0), T(0), T(0)};
   if (s.nc > 0) {
     const int R = rows_per_chunk(s.nB, (int)sizeof(T));
     const int nch = (s.nc + R - 1) / R;
@@ -739,11 +739,11 @@ k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict
     };
     auto use = [&](int c, const unsigned char* raw) {
       const int r0 = c * R, nr = min(R, s.nc - r0);
-      col_accumulate<double, T, double>(L, reinterpret_cast<const T*>(raw), nr, ut + r0, acc);
+      col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, ut + r0, acc);
     };
     ring_run(ring, nch, src, use, err);
   }
-  col_finish<double>(L, acc, dpart, out);
+  col_finish<T>(L, acc, part, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -830,8 +830,7 @@ void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, do
 
 template <typename T>
 void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
-  size_t sm = ring_bytes() + sizeof(double) * ((size_t)APPLY_THREADS + L.maxNB + 1) +
-              sizeof(T) * ((size_t)APPLY_THREADS + L.maxNN + L.maxQN + 2);
+  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNB + 1 + L.maxNN + L.maxQN + 2);
   BDDC_COUNT(1);
   k_neumann_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facN, (const T*)L.facNT,
                                                        (const T*)L.Phi, L.delta, r, t, (T*)L.vloc, L.rcl, L.err);
@@ -839,7 +838,7 @@ void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cuda
 
 template <typename T>
 void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t st) {
-  size_t sm = ring_bytes() + sizeof(double) * ((size_t)APPLY_THREADS + L.maxNc + 1);
+  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNc + 1);
   BDDC_COUNT(1);
   k_neumann_finish<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.lc, (const T*)L.PhiT, (const T*)L.vloc, uc,
                                                         L.vgam, L.err);

@@ -3,7 +3,9 @@
 //
 // A CTA owns a ring of NBUF buffers of CHB bytes.  One thread issues the copy
 // of chunk c + NBUF as soon as chunk c has been consumed, so up to NBUF chunks
-// (128 KiB) are in flight per SM while the CTA computes.  Chunks must start on
+// (144 KiB) are in flight per SM while the CTA computes.  Only that thread
+// polls the chunk's mbarrier; the others wait at a CTA barrier, so waiting
+// costs no issue slots and does not compete with the copies for shared memory.  Chunks must start on
 // 16-byte boundaries and their byte counts are rounded up to 16; callers pad
 // their allocations accordingly.  Every wait is bounded: a wait that gives up
 // records error code 7 (timeout) and the kernel carries on to its end.
@@ -13,8 +15,8 @@
 
 namespace bddc {
 
-constexpr int NBUF = 4;
-constexpr int CHB = 32768;
+constexpr int NBUF = 6;
+constexpr int CHB = 24576;
 constexpr long long WAIT_TRIES = 1LL << 22;
 
 __device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -89,7 +91,8 @@ __device__ void ring_run(Ring& r, int nchunks, Src src, Use use, int* err) {
   }
   for (int c = 0; c < nchunks; ++c) {
     const int g = first + c, slot = g % NBUF;
-    mbar_wait_bounded(&r.bar[slot], (unsigned)((g / NBUF) & 1), err);
+    if (threadIdx.x == 0) mbar_wait_bounded(&r.bar[slot], (unsigned)((g / NBUF) & 1), err);
+    __syncthreads();
     use(c, r.buf + (size_t)slot * CHB);
     __syncthreads();
     if (threadIdx.x == 0 && c + NBUF < nchunks) {
