@@ -47,6 +47,19 @@ def _hbm_peak():
 
 
 HBM_PEAK_GBS = _hbm_peak()
+FP32_PEAK_TFLOPS = 80.5    # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+
+
+def _traffic():
+    """DRAM bytes per launch from the committed ncu summaries (null when absent)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return {k: v.get("bytes_per_launch") for k, v in json.load(f).items()}
+    except (OSError, ValueError, AttributeError):
+        return {}
+
+
+TRAFFIC = _traffic()
 
 
 # ---------------------------------------------------------------------------
@@ -130,6 +143,16 @@ class ClockSampler:
                           if len(s) > 3 + k and s[3 + k].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.samples)}
+
+
+def max_over_ranks(value: float, device: str = "cpu") -> float:
+    """The largest of every rank's value (the job's time is its slowest rank);
+    the only collective of the bench, outside the data path."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ---------------------------------------------------------------------------
@@ -234,9 +257,7 @@ def main():
         t_wall = time.perf_counter() - t_wall
     ms = statistics.mean(times)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
     if args.only_steps:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "ms_per_step": round(ms, 3), "steps": args.steps,
@@ -306,23 +327,34 @@ def main():
                        "coarse_assembly", "coarse_cholesky"], [round(v, 3) for v in info["phase_ms"]]))
     setup_ms = info["setup_ms"]
     solve_ms = statistics.mean(s["solve_ms"] for s in stats)
-    # rooflines: the preconditioner apply (HBM: bytes it must stream) and the
-    # coarse Cholesky (FP64 ALU: multiply-adds of the front plan)
+    # rooflines.  The largest single kernel of the step (launch list in
+    # profiles/) is the local factorisation k_btchol: FP32 multiply-adds of
+    # the plane-block Cholesky factorisations over the phase's event time.
     nc = info["n_coarse"]
+    fac_ms = info["phase_ms"][2]
+    fac_tflops = 2.0 * info["local_factor_fma"] / (fac_ms * 1e-3) / 1e12
+    peak_local = FP32_PEAK_TFLOPS if args.precision == "mixed" else FP64_PEAK_TFLOPS
+    roofline = {"kernel": "k_btchol (local Dirichlet + Neumann plane-block Cholesky, one launch)",
+                "bound": "alu", "achieved": round(fac_tflops, 4), "peak": peak_local, "unit": "TFLOP/s",
+                "frac": round(fac_tflops / peak_local, 4), "traffic": TRAFFIC.get("k_btchol"),
+                "algorithmic": f"{2 * info['local_factor_fma']:.3e} flop per launch (sum over subdomains and "
+                               "planes of Q^3 (1 + 1/2 + 1/3) multiply-adds)",
+                "peak_source": ("FP32 derived from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+                                if args.precision == "mixed" else "GB300 FP64 nominal 1.25 TFLOP/s")}
     chol_ms = info["phase_ms"][5]
     chol_tflops = 2.0 * info["coarse_fma"] / (chol_ms * 1e-3) / 1e12
     apply_gbs = info_apply["apply_bytes"] / (apply_ms * 1e-3) / 1e9
-    roofline = {"kernel": "preconditioner apply (bddc_apply: streamed local sweeps, Phi, coarse fronts)",
-                "bound": "hbm", "achieved": round(apply_gbs, 2), "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                "frac": round(apply_gbs / HBM_PEAK_GBS, 4), "traffic": None,
-                "algorithmic": f"{info_apply['apply_bytes']} bytes per apply (factors read per sweep, Phi twice, "
-                               "coarse fronts twice)",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst)"}
-    roofline_coarse = {"kernel": "coarse Cholesky (k_mf_potrf/trsm/syrk, FP64)", "bound": "alu",
+    roofline_apply = {"kernel": "preconditioner apply (bddc_apply: streamed local sweeps, Phi, coarse fronts)",
+                      "bound": "hbm", "achieved": round(apply_gbs, 2), "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                      "frac": round(apply_gbs / HBM_PEAK_GBS, 4), "traffic": TRAFFIC.get("apply"),
+                      "algorithmic": f"{info_apply['apply_bytes']} bytes per apply (factor halves read per "
+                                     "sweep, Phi twice, coarse solve matrices twice)",
+                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst)"}
+    roofline_coarse = {"kernel": "coarse Cholesky (k_mf_potrf/trsm/syrk + solve matrices, FP64)", "bound": "alu",
                        "achieved": round(chol_tflops, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                        "frac": round(chol_tflops / FP64_PEAK_TFLOPS, 4),
                        "algorithmic": f"{2 * info['coarse_fma']:.3e} flop (front plan, n_c = {nc})",
-                       "peak_source": "GB300 FP64 nominal (1.25 TFLOP/s); measured FMA probe 1.19"}
+                       "peak_source": "GB300 FP64 nominal (1.25 TFLOP/s); FMA probe measured 1.19"}
     out = {
         "metric": METRIC,
         "value": round(world * n_free / (ms * 1e-3) / 1e6, 4),
@@ -351,6 +383,7 @@ def main():
                           "iterations": other_iters[-1], "setup_ms": round(other_info["setup_ms"], 3),
                           "setup_phases_ms": [round(v, 3) for v in other_info["phase_ms"]]},
         "roofline": roofline,
+        "roofline_apply": roofline_apply,
         "roofline_coarse_cholesky": roofline_coarse,
         "wall_s_timed_region": round(t_wall, 3),
         "gpu_launches": int(sum(i["launches"] for i in infos)),

@@ -368,9 +368,11 @@ void check_err_flags(bddc_handle* h, cudaStream_t st) {
   if (e[0] == 0) return;
   const char* what[] = {"", "alpha must be finite and > 0 (element ", "non-positive pivot in the Dirichlet factor of subdomain ",
                         "non-positive pivot in the Neumann factor of subdomain ",
-                        "non-positive pivot in S_c of subdomain ", "non-positive pivot in the coarse factor, tile "};
-  std::string msg = std::string(what[std::min(e[0], 5)]) + std::to_string(e[1]) + (e[0] == 1 ? ")" : "");
-  throw BddcError(e[0] == 1 ? BDDC_ERR_ARG : BDDC_ERR_NOT_SPD, msg);
+                        "non-positive pivot in S_c of subdomain ", "non-positive pivot in the coarse factor, front ",
+                        "", "a bounded wait for a bulk copy gave up in block "};
+  const int code = std::min(std::max(e[0], 0), 7);
+  std::string msg = std::string(what[code]) + std::to_string(e[1]) + (code == 1 ? ")" : "");
+  throw BddcError(code == 1 ? BDDC_ERR_ARG : code == 7 ? BDDC_ERR_TIMEOUT : BDDC_ERR_NOT_SPD, msg);
 }
 
 template <typename T>
@@ -610,6 +612,7 @@ int pcg_impl(bddc_handle* h, const double* b, double* x, double rtol, bddc_stats
   CK(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  check_err_flags(h, st);   // device-side failures of the applies (bounded waits)
   if (stats) {
     stats->iterations = it;
     stats->converged = converged;
