@@ -163,6 +163,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--graph", action="store_true", help="timed steps run PCG as one CUDA graph (use_graph)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-steps", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists)")
@@ -207,7 +208,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step(precision):
-        pre = BDDC.from_problem(p, alpha=alpha, precision=precision)
+        pre = BDDC.from_problem(p, alpha=alpha, precision=precision, use_graph=args.graph)
         _, st = pre.solve(b, p.rtol, out=x)
         return pre, st
 
@@ -284,6 +285,25 @@ def main():
     apply_ms = e0.elapsed_time(e1) / n_apply
     info_apply = pre.info()
     pre.close()
+
+    # ---- repeated solves on one handle: host-driven loop vs one CUDA graph
+    repeat = {}
+    for mode in (False, True):
+        pre = BDDC.from_problem(p, alpha=alpha, precision=args.precision, use_graph=mode)
+        for _ in range(2):
+            pre.solve(b, p.rtol, out=x)
+        ts = []
+        for _ in range(5):
+            flush.fill_(4.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st_r = pre.solve(b, p.rtol, out=x)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        repeat["graph_ms" if mode else "host_loop_ms"] = round(statistics.mean(ts), 4)
+        repeat["iterations"] = st_r["iterations"]
+        pre.close()
 
     # ---- FP64 path for the mixed-vs-FP64 comparison
     other = "fp64" if args.precision == "mixed" else "mixed"
@@ -369,7 +389,7 @@ def main():
         "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic (seeded; no dataset)",
         "config": {"workload": WORKLOAD, "n_free": n_free, "subdomains": info["n_sub"], "L_over_h": 4,
-                   "n_coarse": nc, "precision": args.precision,
+                   "n_coarse": nc, "precision": args.precision, "pcg_graph": bool(args.graph),
                    "parallelism": f"{world} independent replica(s), no data-path collective",
                    "l2": "flushed between timed steps (256 MiB write outside the timed events)"},
         "time_to_solution_ms": round(ms, 3),
@@ -377,6 +397,7 @@ def main():
         "solve_ms": round(solve_ms, 3),
         "iterations": iters,
         "setup_phases_ms": phases,
+        "pcg_solve_repeat": dict(repeat, note="pcg_solve on a set-up handle, b resident, L2 flushed"),
         "precond_apply": {"ms": round(apply_ms, 4), "applies_per_s": round(1e3 / apply_ms, 1),
                           "mdofs": round(n_free * 1e3 / apply_ms / 1e6, 2)},
         f"{other}_path": {"time_to_solution_ms": round(statistics.mean(other_times), 3),

@@ -74,7 +74,7 @@ typedef struct {
     int weights;    /* BDDC_W_CARD or BDDC_W_RHO                                      */
     int L_elems;    /* >= 1                                                           */
     int selection;  /* BDDC_SEL_VEF                                                   */
-    int use_graph;  /* capture each PCG iteration in a CUDA graph (0/1)               */
+    int use_graph;  /* 1: pcg_solve runs its whole loop as one CUDA graph (below)      */
     int maxit;      /* PCG iteration limit (<= 0: 2000)                               */
 } bddc_options;
 
@@ -159,7 +159,16 @@ int bddc_operator(bddc_handle* h, const double* x_dev, double* y_dev, void* stre
 /* PCG with preconditioner B from x0 = 0, stopped when ||r||_2 <= rtol ||b||_2
  * (Section 5: reduction of the residual 2-norm).  x_dev receives the iterate;
  * stats (may be NULL) the counts and coefficients.  Returns BDDC_OK,
- * BDDC_ERR_NOCONV (x holds the last iterate) or BDDC_ERR_BREAKDOWN. */
+ * BDDC_ERR_NOCONV (x holds the last iterate) or BDDC_ERR_BREAKDOWN.
+ * The scalars and the stopping test stay on the device.  With
+ * options.use_graph = 0 the host launches one iteration at a time and reads
+ * the control flags after each; with use_graph = 1 the first solve on the
+ * handle captures one iteration as the body of a graph while-loop (a
+ * conditional node, ended by the device-side test, at most maxit times) on a
+ * private stream, and every solve launches that graph once on `stream` with
+ * no host round trip until the end.  Both modes launch the same kernels in
+ * the same order and return bitwise identical results.  The graph lives in
+ * the handle and is freed by bddc_destroy. */
 int pcg_solve(bddc_handle* h, const double* b_dev, double* x_dev, double rtol,
               bddc_stats* stats, void* stream);
 

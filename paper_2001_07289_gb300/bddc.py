@@ -242,10 +242,10 @@ class BDDC:
 
 
 def solve_host(nx, ny, nz, cuts, L, alpha: np.ndarray, b: np.ndarray, rtol: float, h: float = 0.0,
-               precision="fp64", weights="card", maxit: int = 2000):
+               precision="fp64", weights="card", maxit: int = 2000, use_graph: bool = False):
     """bddc_solve_host: setup + PCG from host arrays, result in a host array."""
     h = h if h > 0 else 1.0 / nx
-    mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, False)
+    mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph)
     a = np.ascontiguousarray(alpha, dtype=np.float64)
     bb = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros_like(bb)

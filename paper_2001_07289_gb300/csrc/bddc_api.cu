@@ -140,8 +140,15 @@ struct bddc_handle {
   double *rc = nullptr, *uc = nullptr;
   double *uI = nullptr, *t = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *partial = nullptr, *scal = nullptr, *hist_a = nullptr, *hist_b = nullptr;
-  int* flag = nullptr;
+  int* ctl = nullptr;             // PCG control block {it, continue, converged, breakdown}
   int* err = nullptr;
+  // PCG loop as one CUDA graph (use_graph): a kernel setting the loop condition,
+  // then a while node whose body is one PCG iteration writing into xw
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap = nullptr;
+  double* xw = nullptr;
+  long long graph_body_launches = 0;
   double* pinned = nullptr;
   int hist_cap = 0;
   long long n_surface_total = 0, n_local_nodes_total = 0;  // sizes of vgam and vloc
@@ -173,6 +180,9 @@ struct bddc_handle {
     setup_only.clear();
   }
   ~bddc_handle() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
     free_setup_only();
     for (void* v : allocs) cudaFree(v);
     if (pinned) cudaFreeHost(pinned);
@@ -520,7 +530,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->q = h->dnew<double>(N);
   h->partial = h->dnew<double>(RED_BLOCKS);
   h->scal = h->dnew<double>(8);
-  h->flag = h->dnew<int>(1);
+  h->ctl = h->dnew<int>(4);
   h->hist_cap = h->opt.maxit > 0 ? h->opt.maxit : 2000;
   h->hist_a = h->dnew<double>(h->hist_cap);
   h->hist_b = h->dnew<double>(h->hist_cap);
@@ -562,56 +572,123 @@ void apply(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
 
 namespace {
 
+// One PCG iteration (Section 5's PCG with B as preconditioner): z = B r,
+// beta and p, q = A p, alpha, x and r, and the stopping test.  The host loop
+// and the graph's while body launch exactly this sequence, so both give the
+// same iterates bit for bit.
+void pcg_body(bddc_handle* h, double* x, const cudaGraphConditionalHandle* cond, cudaStream_t st) {
+  const long long N = h->n_nodes;
+  const int maxit = h->hist_cap;
+  apply(h, h->r, h->z, st);
+  launch_dot(h->r, h->z, N, h->partial, st);
+  launch_finalize(h->partial, h->scal, 3, h->hist_b, h->ctl, maxit, 0.0, nullptr, st);
+  launch_update_p(h->p, h->z, h->scal, N, st);
+  launch_operator(h->m, h->alpha, h->p, h->q, h->partial, RED_BLOCKS, st);
+  launch_finalize(h->partial, h->scal, 1, h->hist_a, h->ctl, maxit, 0.0, nullptr, st);
+  launch_update_xr(x, h->r, h->p, h->q, h->scal, N, h->partial, st);
+  launch_finalize(h->partial, h->scal, 2, nullptr, h->ctl, maxit, 0.0, cond, st);
+}
+
+// Captures the PCG loop once per handle: [condition kernel] -> while(cond)
+// { pcg_body }.  The graph reads and writes only handle-owned buffers, so it
+// stays valid for every later solve; the caller's b and x are copied in and
+// out around its launch.
+void build_graph(bddc_handle* h) {
+  if (h->gexec) return;
+  if (!h->xw) h->xw = h->dnew<double>(h->n_nodes);
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  const long long before = g_launches;
+  bool capturing = false;
+  try {
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+    CK(cudaStreamBeginCaptureToGraph(h->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    launch_loop_condition(h->ctl, cond, h->cap);
+    CK(cudaGetLastError());
+    capturing = false;
+    CK(cudaStreamEndCapture(h->cap, &g));
+    cudaGraphNode_t first;
+    size_t n = 1;
+    CK(cudaGraphGetNodes(g, &first, &n));
+    if (n != 1) throw BddcError(BDDC_ERR_CUDA, "graph capture: unexpected node count");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    CK(cudaGraphAddNode(&loop, g, &first, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const long long b0 = g_launches;
+    CK(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    pcg_body(h, h->xw, &cond, h->cap);
+    CK(cudaGetLastError());
+    capturing = false;
+    CK(cudaStreamEndCapture(h->cap, &body));
+    h->graph_body_launches = g_launches - b0;
+    CK(cudaGraphInstantiate(&h->gexec, g, 0));
+  } catch (...) {
+    if (capturing) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(h->cap, &junk);
+    }
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    g_launches = before;
+    throw;
+  }
+  h->graph = g;
+  g_launches = before;   // captured, not yet launched
+}
+
 int pcg_impl(bddc_handle* h, const double* b, double* x, double rtol, bddc_stats* stats, cudaStream_t st) {
   const long long N = h->n_nodes;
   const int maxit = h->hist_cap;
+  const bool graph = h->opt.use_graph != 0;
+  if (graph) build_graph(h);
+  double* xs = graph ? h->xw : x;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, st));
-  CK(cudaMemsetAsync(x, 0, sizeof(double) * N, st));
-  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(xs, 0, sizeof(double) * N, st));
+  CK(cudaMemsetAsync(h->p, 0, sizeof(double) * N, st));
   launch_masked_copy(h->m, b, h->r, st);
   launch_dot(h->r, h->r, N, h->partial, st);
-  launch_finalize(h->partial, h->scal, 4, nullptr, 0, h->flag, st);
-  CK(cudaMemcpyAsync(h->pinned, h->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  const double r0 = std::sqrt(h->pinned[0]);
-  int it = 0, status = BDDC_OK, converged = 0;
-  double rn = r0;
-  if (r0 == 0.0) {
-    converged = 1;
+  launch_finalize(h->partial, h->scal, 4, nullptr, h->ctl, maxit, rtol, nullptr, st);
+  int* hc = (int*)(h->pinned + 2);   // ctl as read back: it, continue, converged, breakdown
+  if (graph) {
+    CK(cudaGraphLaunch(h->gexec, st));
+    CK(cudaMemcpyAsync(x, h->xw, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   } else {
-    apply(h, h->r, h->z, st);
-    launch_dot(h->r, h->z, N, h->partial, st);
-    launch_finalize(h->partial, h->scal, 0, nullptr, 0, h->flag, st);
-    CK(cudaMemcpyAsync(h->p, h->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-    while (it < maxit) {
-      launch_operator(h->m, h->alpha, h->p, h->q, h->partial, RED_BLOCKS, st);
-      launch_finalize(h->partial, h->scal, 1, h->hist_a, it, h->flag, st);
-      launch_update_xr(x, h->r, h->p, h->q, h->scal, N, h->partial, st);
-      launch_finalize(h->partial, h->scal, 2, nullptr, 0, h->flag, st);
-      CK(cudaMemcpyAsync(h->pinned, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync((int*)(h->pinned + 1), h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hc, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    while (hc[1]) {
+      pcg_body(h, x, nullptr, st);
+      CK(cudaMemcpyAsync(hc, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      ++it;
-      rn = std::sqrt(h->pinned[0]);
-      if (*(int*)(h->pinned + 1)) { status = BDDC_ERR_BREAKDOWN; break; }
-      if (rn <= rtol * r0) { converged = 1; break; }
-      if (it >= maxit) break;
-      apply(h, h->r, h->z, st);
-      launch_dot(h->r, h->z, N, h->partial, st);
-      launch_finalize(h->partial, h->scal, 3, h->hist_b, it - 1, h->flag, st);
-      launch_update_p(h->p, h->z, h->scal, N, st);
     }
-    if (!converged && status == BDDC_OK) status = BDDC_ERR_NOCONV;
   }
+  CK(cudaMemcpyAsync(h->pinned, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->pinned + 1, h->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hc, h->ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(e1, st));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  const int it = hc[0], converged = hc[2], breakdown = hc[3];
+  const double r0 = std::sqrt(h->pinned[1]);
+  const double rn = it > 0 ? std::sqrt(h->pinned[0]) : r0;
+  if (graph) g_launches += h->graph_body_launches * it + 1;
+  int status = BDDC_OK;
+  if (breakdown) status = BDDC_ERR_BREAKDOWN;
+  else if (!converged) status = BDDC_ERR_NOCONV;
   check_err_flags(h, st);   // device-side failures of the applies (bounded waits)
   if (stats) {
     stats->iterations = it;

@@ -137,9 +137,11 @@ void launch_masked_copy(const MeshDev& m, const double* src, double* dst, cudaSt
 // pcg.cu
 constexpr int RED_BLOCKS = 608;  // 4 x 152 SMs: fixed partial count => deterministic sums
 void launch_dot(const double* a, const double* b, long long n, double* partial, cudaStream_t st);
-// scalars: [0] rz, [1] pq, [2] alpha, [3] rr, [4] rz_new, [5] beta, [6] bb
-void launch_finalize(const double* partial, double* scal, int op, double* hist, int it, int* flag,
-                     cudaStream_t st);
+// scalars: [0] rz, [1] pq, [2] alpha, [3] rr, [4] rz_new, [5] beta, [6] bb,
+// [7] stopping threshold; ctl: [0] it, [1] continue, [2] converged, [3] breakdown
+void launch_finalize(const double* partial, double* scal, int op, double* hist, int* ctl, int maxit, double rtol,
+                     const cudaGraphConditionalHandle* cond, cudaStream_t st);
+void launch_loop_condition(const int* ctl, cudaGraphConditionalHandle cond, cudaStream_t st);
 void launch_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, long long n,
                       double* partial, cudaStream_t st);
 void launch_update_p(double* p, const double* z, const double* scal, long long n, cudaStream_t st);

@@ -1,8 +1,8 @@
 // PCG vector kernels (FP64) with deterministic reductions: every dot product
 // is accumulated into RED_BLOCKS fixed per-block partials and summed by one
 // block in a fixed order, so repeated runs are bitwise identical.  The CG
-// scalars live on the device; only ||r||^2 crosses to the host per iteration
-// (the stopping test on the residual 2-norm of Section 5).
+// scalars and the stopping test (the residual 2-norm rule of Section 5) live
+// on the device, so a PCG loop needs no host round trip per iteration.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -40,11 +40,21 @@ void launch_dot(const double* a, const double* b, long long n, double* partial, 
   k_dot<<<RED_BLOCKS, 256, 0, st>>>(a, b, n, partial);
 }
 
-// op: 0 rz = sum (initial r.z);  1 pq -> alpha = rz/pq (hist[it] = alpha),
-//     flag if pq <= 0 or not finite;  2 rr = sum;  3 rz_new -> beta =
-//     rz_new/rz (hist[it] = beta), rz = rz_new;  4 bb = sum.
-__global__ void k_finalize(const double* __restrict__ partial, double* scal, int op, double* hist, int it,
-                           int* flag) {
+// One block sums the partials in a fixed order and updates the CG scalars and
+// the control block ctl = {it, continue, converged, breakdown}.
+//   op 4 (start):  bb = sum; threshold rtol ||b||_2 (Section 5 stopping rule),
+//                  it = 0, converged iff b = 0, continue iff not converged.
+//   op 3 (beta):   rz_new = sum; beta = 0 on the first iteration, else
+//                  rz_new / rz (hist[it - 1] = beta); rz = rz_new.
+//   op 1 (alpha):  pq = sum; alpha = rz / pq (hist[it] = alpha); breakdown if
+//                  pq <= 0 or alpha is not finite.
+//   op 2 (test):   rr = sum; ++it; converged iff ||r||_2 <= threshold and no
+//                  breakdown; continue iff neither and it < maxit.
+// With use_cond the continue flag also sets the condition of the enclosing
+// graph's while node, which is what ends a PCG loop captured in a graph: it
+// grows by one per body, so the loop runs at most maxit times.
+__global__ void k_finalize(const double* __restrict__ partial, double* scal, int op, double* hist, int* ctl,
+                           int maxit, double rtol, cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double ws[32];
   double v = 0.0;
   for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) v += partial[i];
@@ -55,34 +65,71 @@ __global__ void k_finalize(const double* __restrict__ partial, double* scal, int
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+    int cont = -1;
     switch (op) {
-      case 0: scal[0] = s; break;
+      case 4: {
+        scal[6] = s;
+        scal[7] = rtol * sqrt(s);
+        const int conv = s == 0.0;
+        ctl[0] = 0;
+        ctl[2] = conv;
+        ctl[3] = 0;
+        cont = (!conv && maxit > 0) ? 1 : 0;
+        break;
+      }
+      case 3: {
+        scal[4] = s;
+        const int it = ctl[0];
+        double b = 0.0;
+        if (it > 0) {
+          b = s / scal[0];
+          if (!isfinite(b)) { ctl[3] = 1; b = 0.0; }
+          if (hist) hist[it - 1] = b;
+        }
+        scal[5] = b;
+        scal[0] = s;
+        break;
+      }
       case 1: {
         scal[1] = s;
         double a = scal[0] / s;
-        if (!(s > 0.0) || !isfinite(a)) { *flag = 1; a = 0.0; }
+        if (!(s > 0.0) || !isfinite(a)) { ctl[3] = 1; a = 0.0; }
         scal[2] = a;
-        if (hist) hist[it] = a;
+        if (hist) hist[ctl[0]] = a;
         break;
       }
-      case 2: scal[3] = s; break;
-      case 3: {
-        scal[4] = s;
-        double b = s / scal[0];
-        if (!isfinite(b)) { *flag = 1; b = 0.0; }
-        scal[5] = b;
-        scal[0] = s;
-        if (hist) hist[it] = b;
+      case 2: {
+        scal[3] = s;
+        const int it = ctl[0] + 1;
+        ctl[0] = it;
+        const int brk = ctl[3];
+        const int conv = !brk && sqrt(s) <= scal[7];
+        ctl[2] = conv;
+        cont = (!brk && !conv && it < maxit) ? 1 : 0;
         break;
       }
-      case 4: scal[6] = s; break;
+    }
+    if (cont >= 0) {
+      ctl[1] = cont;
+      if (use_cond) cudaGraphSetConditional(cond, (unsigned)cont);
     }
   }
 }
 
-void launch_finalize(const double* partial, double* scal, int op, double* hist, int it, int* flag, cudaStream_t st) {
+void launch_finalize(const double* partial, double* scal, int op, double* hist, int* ctl, int maxit, double rtol,
+                     const cudaGraphConditionalHandle* cond, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_finalize<<<1, 256, 0, st>>>(partial, scal, op, hist, it, flag);
+  k_finalize<<<1, 256, 0, st>>>(partial, scal, op, hist, ctl, maxit, rtol, cond ? *cond : 0, cond ? 1 : 0);
+}
+
+// Sets the condition of a graph's while node from ctl[1] (the continue flag).
+__global__ void k_loop_condition(const int* ctl, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(cond, ctl[1] ? 1u : 0u);
+}
+
+void launch_loop_condition(const int* ctl, cudaGraphConditionalHandle cond, cudaStream_t st) {
+  BDDC_COUNT(1);
+  k_loop_condition<<<1, 32, 0, st>>>(ctl, cond);
 }
 
 // x += alpha p; r -= alpha q; partials of r.r

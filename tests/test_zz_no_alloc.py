@@ -9,6 +9,7 @@ and the mixed path.  The file sorts last so that a run stopping at the first
 failure has already run every other test.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -31,8 +32,10 @@ def test_apply_noalloc_matches_apply(precision, tol):
     # first call on this device looks up the array's address
     z = torch.empty_like(r1)
     assert gb.lib.bddc_apply_noalloc(pre._handle, gb._ptr(r1), gb._ptr(z), stream) == 0
-    # every tensor of the test exists before the device's free memory is read
+    # every tensor of the test exists before the device's free memory is read,
+    # and handles that earlier tests dropped are freed now, not during the loop
     outs = [(torch.empty_like(r1), torch.full_like(r1, np.nan)) for _ in range(2)]
+    gc.collect()
     torch.cuda.synchronize()
     free_before = torch.cuda.mem_get_info()[0]
     for r, (want, got) in zip((r1, r2), outs):
