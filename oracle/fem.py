@@ -119,6 +119,29 @@ def dirichlet_system(nx, ny, nz, h, alpha):
     return A[free][:, free].tocsc(), free
 
 
+def apply_operator_by_elements(nx, ny, nz, h, alpha, x: np.ndarray) -> np.ndarray:
+    """The same Dirichlet operator without assembling: y = sum over elements
+    of alpha_e h K_unit x_e, done as 64 (a, b) passes over the element grid,
+    each adding alpha h K[a, b] times x at the elements' local node b to y at
+    their local node a.  For meshes too large to assemble in memory."""
+    K = q1_unit_stiffness()
+    bnd = boundary_node_mask(nx, ny, nz).reshape(nz + 1, ny + 1, nx + 1)
+    xg = np.where(bnd, 0.0, x.reshape(nz + 1, ny + 1, nx + 1))
+    ah = alpha.reshape(nz, ny, nx) * h
+    y = np.zeros_like(xg)
+
+    def corner(v, a):
+        ax, ay, az = a & 1, (a >> 1) & 1, (a >> 2) & 1
+        return v[az:az + nz, ay:ay + ny, ax:ax + nx]
+
+    for a in range(8):
+        ya = corner(y, a)
+        for b in range(8):
+            ya += K[a, b] * (ah * corner(xg, b))
+    y[bnd] = 0.0
+    return y.reshape(-1)
+
+
 def apply_operator(nx, ny, nz, h, alpha, x: np.ndarray) -> np.ndarray:
     """y = A x on the full node grid, x's boundary entries treated as 0 and y's
     boundary entries set to 0 (the Dirichlet operator in grid layout)."""

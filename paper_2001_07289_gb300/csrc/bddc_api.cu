@@ -905,7 +905,13 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
     const double QN = (double)(s.w[0] + 1) * (s.w[1] + 1), nzN = s.w[2] + 1;
     const double QD = (s.w[0] > 1 && s.w[1] > 1 && s.w[2] > 1) ? (double)(s.w[0] - 1) * (s.w[1] - 1) : 0.0;
     const double nzD = QD > 0 ? s.w[2] - 1 : 0;
-    fma += nzN * (QN * QN * QN * (1.0 + 0.5 + 1.0 / 3.0)) + nzD * (QD * QD * QD * (1.0 + 0.5 + 1.0 / 3.0));
+    // per plane: Cholesky and inverse of the Schur block (Q^3/3); per plane
+    // after the first: M_k = B Linv^T (nine stencil terms, 9 Q^2) and the
+    // lower half of M_k M_k^T (Q^3/2)
+    auto planes = [](double Q, double nz) {
+      return nz > 0 ? nz * Q * Q * Q / 3.0 + (nz - 1) * (Q * Q * Q / 2.0 + 9.0 * Q * Q) : 0.0;
+    };
+    fma += planes(QN, nzN) + planes(QD, nzD);
     const double perN = (nzN * QN * (QN + 1) / 2 + (nzN - 1) * QN * QN) * es;
     const double perD = (nzD * QD * (QD + 1) / 2 + std::max(nzD - 1, 0.0) * QD * QD) * es;
     bytes += (long long)(2 * perN + 4 * perD + 2.0 * s.nB * s.nc * es);

@@ -152,11 +152,50 @@ k_btchol(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict__
     T* slot = base + (long long)k * SS;
     if (k > 0) {
       T* mslot = base + (long long)(g.gz + k - 1) * SS;
-      for (long long e = threadIdx.x; e < QQ; e += blockDim.x) W2[e] = mslot[e];
+      const T* Lp = base + (long long)(k - 1) * SS;
+      // M_k = B_{k-1} Linv_{k-1}^T.  B couples a node only to the 3 x 3 nodes
+      // around it in the previous plane (the Q1 stencil), so row i of M_k is
+      // a combination of at most nine rows of Linv_{k-1}^T:
+      //   M_k[i][j] = sum_o B[i][i + off_o] Linv_{k-1}[j][i + off_o].
+      // (1) the nine diagonals of B into diag (free until the factorisation)
+      for (int e = threadIdx.x; e < 9 * Q; e += blockDim.x) {
+        const int o = e / Q, i = e % Q, dx = o % 3 - 1, dy = o / 3 - 1;
+        const int ix = i % g.gx + dx, iy = i / g.gx + dy;
+        diag[e] = (ix >= 0 && ix < g.gx && iy >= 0 && iy < g.gy) ? mslot[(long long)i * Q + i + dx + dy * g.gx]
+                                                                  : T(0);
+      }
+      // (2) W2 = Linv_{k-1}^T by 32 x 32 tiles through shared memory (tiles
+      // above the diagonal of Linv are zero and skipped; the product below
+      // never reads their transposes)
+      const int nt = (Q + 31) / 32;
+      for (int tb = 0; tb < nt * nt; ++tb) {
+        const int a0 = (tb / nt) * 32, b0 = (tb % nt) * 32;
+        if (b0 > a0) continue;
+        for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+          const int r = idx >> 5, c = idx & 31;
+          sm.t0[r * TLD + c] = (a0 + r < Q && b0 + c < Q) ? Lp[(long long)(a0 + r) * Q + b0 + c] : T(0);
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+          const int r = idx >> 5, c = idx & 31;
+          if (b0 + r < Q && a0 + c < Q) W2[(long long)(b0 + r) * Q + a0 + c] = sm.t0[c * TLD + r];
+        }
+        __syncthreads();
+      }
+      // (3) rows of M_k (Linv^T[l][j] = 0 for j < l)
+      for (long long e = threadIdx.x; e < QQ; e += blockDim.x) {
+        const int i = (int)(e / Q), j = (int)(e % Q);
+        const int ix = i % g.gx, iy = i / g.gx;
+        T acc = T(0);
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+          const int dx = o % 3 - 1, dy = o / 3 - 1, l = i + dx + dy * g.gx;
+          if (ix + dx >= 0 && ix + dx < g.gx && iy + dy >= 0 && iy + dy < g.gy && j >= l)
+            acc += diag[o * Q + i] * W2[(long long)l * Q + j];
+        }
+        mslot[e] = acc;
+      }
       __syncthreads();
-      // M_k = B_{k-1} * Linv_{k-1}^T   (op(B) = Linv^T is upper)
-      cta_gemm<T>(Q, Q, Q, T(1), W2, Q, false, base + (long long)(k - 1) * SS, Q, true, T(0), mslot, Q,
-                  0, 1, false, sm);
       // S_k = D_k - M_k M_k^T (lower part)
       cta_gemm<T>(Q, Q, Q, T(-1), mslot, Q, false, mslot, Q, true, T(1), slot, Q, 0, 0, true, sm);
     }

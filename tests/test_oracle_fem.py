@@ -90,3 +90,27 @@ def test_floating_neumann_kernel():
     # and the Dirichlet system is SPD
     A, free = fem.dirichlet_system(12, 12, 12, 1 / 12, np.ones(12 ** 3))
     assert spla.eigsh(A, k=1, which="SA", return_eigenvectors=False)[0] > 0
+
+
+def test_operator_by_elements_matches_assembled_and_stencil():
+    """The element-by-element operator (used where assembly does not fit)
+    equals the assembled one on a ragged mesh with variable alpha, and with
+    alpha = 1 reproduces the closed-form stencil at an interior node."""
+    nx, ny, nz = 7, 5, 6
+    h = 1.0 / nx
+    a = inputs.alpha_loguniform(nx, ny, nz, -2, 2, 3)
+    x = inputs.random_node_vector(nx, ny, nz, 4)
+    y1 = fem.apply_operator(nx, ny, nz, h, a, x)
+    y2 = fem.apply_operator_by_elements(nx, ny, nz, h, a, x)
+    assert np.abs(y1 - y2).max() <= 1e-13 * np.abs(y1).max()
+    # unit vector at an interior node: the stencil 8h/3, 0, -h/6, -h/12
+    e = np.zeros((nz + 1) * (ny + 1) * (nx + 1))
+    i, j, k = 3, 2, 3
+    e[i + (nx + 1) * (j + (ny + 1) * k)] = 1.0
+    y = fem.apply_operator_by_elements(nx, ny, nz, h, np.ones(nx * ny * nz), e).reshape(nz + 1, ny + 1, nx + 1)
+    want = {0: 8 * h / 3, 1: 0.0, 2: -h / 6, 3: -h / 12}
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                d = abs(dx) + abs(dy) + abs(dz)
+                assert abs(y[k + dz, j + dy, i + dx] - want[d]) <= 1e-15
