@@ -12,10 +12,12 @@
 //
 // Numeric phase, tree level by tree level (deepest first): extend-add of the
 // children's update matrices, then a tiled right-looking partial Cholesky of
-// every front of the level at once (potrf of the 64x64 diagonal tile with its
+// every front of the level at once (potrf of the 32x32 diagonal tile with its
 // explicit inverse, trsm of the tiles below it, syrk of the trailing tiles,
 // which include the update block U x U).  Afterwards every front gets its
-// solve matrix [Linv_P; G] with Linv_P = L_P^{-1} and G = L_UP Linv_P, so each
+// solve matrix [Linv_P; G] with Linv_P = L_P^{-1} (recursive doubling over
+// the diagonal tiles' inverses, all fronts at once: for L = [[A, 0], [B, C]],
+// L^{-1} has the off-diagonal block -C^{-1} B A^{-1}) and G = L_UP Linv_P, so each
 // level of a triangular solve is one parallel mat-vec over all the level's
 // fronts (rows split across CTAs forward, columns backward).  Everything is
 // summed in a fixed order (no atomics).
@@ -27,7 +29,12 @@
 
 namespace bddc {
 
-constexpr int FNB = 64;
+// Factor tiles are 32 wide: FP64 issue on this GPU is about two FMAs per
+// clock per SM, so a 64-wide tile step on one CTA would be long and the
+// chain of diagonal-tile steps short of parallel work.  The forward solve
+// works on row chunks of FSR rows.
+constexpr int FNB = 32;
+constexpr int FSR = 64;
 
 __host__ __device__ inline int mf_ntiles(int np, int nu) { return (np + FNB - 1) / FNB + (nu + FNB - 1) / FNB; }
 __host__ __device__ inline void mf_tile(int t, int np, int nu, int& r0, int& nr) {
@@ -185,23 +192,32 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
   // solve matrices and the work lists that build them
   P.soff.resize(nf);
   long long so = 0;
-  int maxpt_all = 0;
   for (int f = 0; f < nf; ++f) {
     P.soff[f] = so;
     so += (long long)(P.np[f] + P.nu[f]) * P.np[f];
-    maxpt_all = std::max(maxpt_all, (P.np[f] + FNB - 1) / FNB);
   }
   P.spool = so;
-  P.diag_items.clear(); P.g_items.clear(); P.trtri_steps.assign(std::max(maxpt_all, 1), {});
+  P.diag_items.clear(); P.g_items.clear(); P.trtri_steps.clear();
+  P.toff.resize(nf);
+  long long to = 0;
   for (int f = 0; f < nf; ++f) {
     const int npt = (P.np[f] + FNB - 1) / FNB, nut = (P.nu[f] + FNB - 1) / FNB;
+    P.toff[f] = to;
+    to += (long long)P.np[f] * P.np[f];
     for (int t = 0; t < npt; ++t) P.diag_items.insert(P.diag_items.end(), {f, t, t, 0});
-    for (int t = 1; t < npt; ++t)
-      for (int s2 = 0; s2 < t; ++s2) P.trtri_steps[t].insert(P.trtri_steps[t].end(), {f, t, s2, 0});
+    // doubling: blocks of 2 hb tiles, A = first hb tiles, C = the rest
+    int q = 0;
+    for (int hb = 1; hb < npt; hb *= 2, ++q) {
+      if ((int)P.trtri_steps.size() <= q) P.trtri_steps.emplace_back();
+      for (int b0 = 0; b0 + hb < npt; b0 += 2 * hb)
+        for (int r = b0 + hb; r < std::min(b0 + 2 * hb, npt); ++r)
+          for (int c = b0; c < b0 + hb; ++c) P.trtri_steps[q].insert(P.trtri_steps[q].end(), {f, r, c, hb});
+    }
     for (int u = 0; u < nut; ++u)
       for (int s2 = 0; s2 < npt; ++s2) P.g_items.insert(P.g_items.end(), {f, u, s2, 0});
     P.flops += (double)P.np[f] * P.np[f] * P.np[f] / 6.0 + (double)P.nu[f] * P.np[f] * P.np[f] / 2.0;
   }
+  P.tpool = to;
   // child update rows -> positions in the parent front
   P.pmap_off.assign(nf + 1, 0);
   for (int f = 0; f < nf; ++f) {
@@ -249,9 +265,55 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
 // ---------------------------------------------------------------------------
 struct MFDev {
   const int *np, *nu, *gid, *fr, *pp, *ord, *pmap, *parent;
-  const long long *foff, *doff, *woff, *gid_off, *pmap_off, *soff;
-  double *F, *Dinv, *W, *S;
+  const long long *foff, *doff, *woff, *gid_off, *pmap_off, *soff, *toff;
+  double *F, *Dinv, *W, *S, *T;
 };
+
+// One 32 x 32 FP64 output tile on one CTA of 256 threads, two rows by two
+// columns per thread: C = beta C + alpha sum_k A[i][k] op(B)[k][j] with
+// op(B)[k][j] = B[k][j] (TB false) or B[j][k] (TB true), k < K, row-major
+// operands; with lower only j <= i is written.  m, n <= 32.  K runs in 32-deep
+// slices staged in shared memory (As, Bs: 32 x 33 each); at two FP64 FMAs per
+// clock per SM the slice's arithmetic hides its loads, so every warp computes
+// rather than blocking registers.  beta = 0 does not read C.
+template <bool TB>
+__device__ void tile_gemm_f64(int m, int n, int K, double alpha, const double* __restrict__ A, long long lda,
+                              const double* __restrict__ B, long long ldb, double beta, double* C, long long ldc,
+                              bool lower, double* As, double* Bs) {
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    const int kb = min(32, K - k0);
+    for (int idx = tid; idx < 1024; idx += BDDC_THREADS) {
+      const int r = idx >> 5, kk = idx & 31;
+      As[r * 33 + kk] = (r < m && kk < kb) ? A[r * lda + k0 + kk] : 0.0;
+      if (TB) Bs[kk * 33 + r] = (r < n && kk < kb) ? B[r * ldb + k0 + kk] : 0.0;
+      else Bs[r * 33 + kk] = (r < kb && kk < n) ? B[(long long)(k0 + r) * ldb + kk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const double a0 = As[(2 * ty) * 33 + kk], a1 = As[(2 * ty + 1) * 33 + kk];
+      const double b0 = Bs[kk * 33 + tx], b1 = Bs[kk * 33 + tx + 16];
+      c00 = fma(a0, b0, c00);
+      c01 = fma(a0, b1, c01);
+      c10 = fma(a1, b0, c10);
+      c11 = fma(a1, b1, c11);
+    }
+    __syncthreads();
+  }
+  const double acc[2][2] = {{c00, c01}, {c10, c11}};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int r = 2 * ty + a, c = tx + 16 * b;
+      if (r < m && c < n && (!lower || c <= r)) {
+        double* p = C + r * ldc + c;
+        *p = (beta == 0.0) ? alpha * acc[a][b] : fma(beta, *p, alpha * acc[a][b]);
+      }
+    }
+}
 
 __device__ inline int mf_pos(const MFDev& d, int f, int o) {
   if (d.fr[o] == f) return d.pp[o];
@@ -354,8 +416,7 @@ k_mf_trsm(MFDev d, const int4* __restrict__ work) {
 // A[i,l] -= A[i,j] A[l,j]^T
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_syrk(MFDev d, const int4* __restrict__ work) {
-  extern __shared__ __align__(128) unsigned char smraw[];
-  DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
+  __shared__ double As[32 * 33], Bs[32 * 33];
   const int4 w = work[blockIdx.x];
   const int f = w.x, i = w.y, l = w.z, j = w.w;
   const int np = d.np[f], nu = d.nu[f];
@@ -365,8 +426,8 @@ k_mf_syrk(MFDev d, const int4* __restrict__ work) {
   mf_tile(l, np, nu, rl, nl);
   mf_tile(j, np, nu, rj, nj);
   double* A = d.F + d.foff[f];
-  cta_gemm<double>(ni, nl, nj, -1.0, A + ri * F + rj, (int)F, false, A + rl * F + rj, (int)F, true, 1.0,
-                   A + ri * F + rl, (int)F, 0, 0, i == l, sm);
+  tile_gemm_f64<true>(ni, nl, nj, -1.0, A + ri * F + rj, F, A + rl * F + rj, F, 1.0, A + ri * F + rl, F, i == l,
+                      As, Bs);
 }
 
 __device__ inline double mf_wsum(double v) {
@@ -393,31 +454,34 @@ __global__ void k_mf_inv_diag(MFDev d, const int4* __restrict__ work) {
   }
 }
 
+// one doubling step for every front at once; item {front, r, c, hb}: tile
+// (r, c) of the off-diagonal block [C rows] x [A cols] of a block of 2 hb
+// diagonal tiles.  mode 0: T = L_CA X_AA (X_AA lower, so k >= c);
+// mode 1: X_CA = -X_CC T (X_CC lower, so k <= r).
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_inv_step(MFDev d, const int4* __restrict__ work, double* scratch) {
-  extern __shared__ __align__(128) unsigned char smraw[];
-  DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
+k_mf_trtri(MFDev d, const int4* __restrict__ work, int mode) {
+  __shared__ double As[32 * 33], Bs[32 * 33];
   const int4 w = work[blockIdx.x];
-  const int f = w.x, t = w.y, sblk = w.z;
+  const int f = w.x, r = w.y, c = w.z, hb = w.w;
   const int np = d.np[f], nu = d.nu[f];
   const long long F = np + nu;
-  const int t0 = t * FNB, nt = min(FNB, np - t0);
-  const int s0 = sblk * FNB, ns = min(FNB, np - s0);
+  const int cstart = (c / (2 * hb)) * 2 * hb + hb;   // first tile of C = end of A
+  const int r0 = r * FNB, nr = min(FNB, np - r0), c0 = c * FNB, nc = min(FNB, np - c0);
   const double* L = d.F + d.foff[f];
   double* X = d.S + d.soff[f];
-  double* tmp = scratch + (long long)blockIdx.x * FNB * FNB;
-  // tmp = L[t rows, s0:t0] X[s0:t0, s cols]   (X lower: zero for k < j)
-  cta_gemm<double>(nt, ns, t0 - s0, 1.0, L + t0 * F + s0, (int)F, false, X + (long long)s0 * np + s0, np, false, 0.0,
-                   tmp, FNB, 0, 2, false, sm);
-  // X_ts = -Dinv_t tmp
-  cta_gemm<double>(nt, ns, nt, -1.0, d.Dinv + d.doff[f] + (long long)t * FNB * FNB, FNB, false, tmp, FNB, false, 0.0,
-                   X + (long long)t0 * np + s0, np, 1, 0, false, sm);
+  double* T = d.T + d.toff[f];
+  const int k1 = cstart * FNB;
+  if (mode == 0)
+    tile_gemm_f64<false>(nr, nc, k1 - c0, 1.0, L + r0 * F + c0, F, X + (long long)c0 * np + c0, np, 0.0,
+                         T + (long long)r0 * np + c0, np, false, As, Bs);
+  else
+    tile_gemm_f64<false>(nr, nc, r0 + nr - k1, -1.0, X + (long long)r0 * np + k1, np, T + (long long)k1 * np + c0,
+                         np, 0.0, X + (long long)r0 * np + c0, np, false, As, Bs);
 }
 
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_g(MFDev d, const int4* __restrict__ work) {
-  extern __shared__ __align__(128) unsigned char smraw[];
-  DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
+  __shared__ double As[32 * 33], Bs[32 * 33];
   const int4 w = work[blockIdx.x];
   const int f = w.x, ut = w.y, st = w.z;
   const int np = d.np[f], nu = d.nu[f];
@@ -426,12 +490,12 @@ k_mf_g(MFDev d, const int4* __restrict__ work) {
   const int s0 = st * FNB, ns = min(FNB, np - s0);
   const double* L = d.F + d.foff[f];
   double* S = d.S + d.soff[f];
-  // G[u, s cols] = L_UP[u, s0:np] X[s0:np, s cols]
-  cta_gemm<double>(nuu, ns, np - s0, 1.0, L + (np + u0) * F + s0, (int)F, false, S + (long long)s0 * np + s0, np,
-                   false, 0.0, S + (long long)(np + u0) * np + s0, np, 0, 2, false, sm);
+  // G[u, s cols] = L_UP[u, s0:np] X[s0:np, s cols]   (X lower: zero for k < s0)
+  tile_gemm_f64<false>(nuu, ns, np - s0, 1.0, L + (np + u0) * F + s0, F, S + (long long)s0 * np + s0, np, 0.0,
+                       S + (long long)(np + u0) * np + s0, np, false, As, Bs);
 }
 
-// forward, one launch per level; work item {front, row chunk of FNB rows}:
+// forward, one launch per level; work item {front, row chunk of FSR rows}:
 // w_P = b_P + children's update vectors at P, w_U likewise at U;
 // rows r < np: W[r] = (Linv_P w_P)[r];  rows r >= np: W[r] = w_U[r-np] - (G w_P)[r-np]
 __global__ void __launch_bounds__(BDDC_THREADS)
@@ -456,7 +520,7 @@ k_mf_fwd2(MFDev d, const int2* __restrict__ items, const int* __restrict__ kid_p
   const double* S = d.S + d.soff[f];
   double* Wf = d.W + d.woff[f];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int r0 = chunk * FNB, r1 = min(F, r0 + FNB);
+  const int r0 = chunk * FSR, r1 = min(F, r0 + FSR);
   for (int r = r0 + warp; r < r1; r += nw) {
     const double* row = S + (long long)r * np;
     const int cend = (r < np) ? r + 1 : np;
@@ -523,6 +587,7 @@ MFDev dev_of(const MFPlan& P) {
   d.foff = P.d_foff; d.doff = P.d_doff; d.woff = P.d_woff; d.gid_off = P.d_gid_off; d.pmap_off = P.d_pmap_off;
   d.F = P.F; d.Dinv = P.Dinv; d.W = P.W;
   d.S = P.S; d.soff = P.d_soff;
+  d.T = P.tscratch; d.toff = P.d_toff;
   return d;
 }
 
@@ -537,12 +602,9 @@ T* up(const std::vector<T>& v, const std::function<void*(size_t)>& alloc, cudaSt
 
 void configure_mf_kernels() {
   int sm = (int)sizeof(DenseSmem<double>);
-  cudaFuncSetAttribute(k_mf_inv_step, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_mf_g, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_mf_fwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mf_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mf_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  cudaFuncSetAttribute(k_mf_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_mf_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(2 * FNB * (FNB + 1) * sizeof(double)));
 }
@@ -590,12 +652,9 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
   };
   push_inv(P.diag_items);
   push_inv(P.g_items);
-  int maxinv = 1;
-  for (size_t t = 1; t < P.trtri_steps.size(); ++t) {
-    push_inv(P.trtri_steps[t]);
-    maxinv = std::max(maxinv, (int)P.trtri_steps[t].size() / 4);
-  }
-  P.tscratch = (double*)tmp_alloc(sizeof(double) * FNB * FNB * (size_t)maxinv);
+  for (size_t q = 0; q < P.trtri_steps.size(); ++q) push_inv(P.trtri_steps[q]);
+  P.tscratch = (double*)tmp_alloc(sizeof(double) * std::max<long long>(P.tpool, 1));
+  P.d_toff = up(P.toff, alloc, st);
   P.d_lists = (int4*)tmp_alloc(sizeof(int) * std::max<size_t>(all.size(), 4));
   if (!all.empty()) cudaMemcpyAsync(P.d_lists, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, st);
   // per level: fronts, their children (for the solves), children by slot (extend-add)
@@ -661,7 +720,7 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
     for (int f : P.fronts_at_level[l]) {
       const int F = P.np[f] + P.nu[f];
       P.maxF = std::max(P.maxF, F);
-      for (int c = 0; c < (F + FNB - 1) / FNB; ++c) items.insert(items.end(), {f, c});
+      for (int c = 0; c < (F + FSR - 1) / FSR; ++c) items.insert(items.end(), {f, c});
     }
     P.fwd_items_len[l] = (int)items.size() / 2 - P.fwd_items_off[l];
     P.bwd_items_off[l] = (int)items.size() / 2;
@@ -708,17 +767,18 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st) {
       const int4* ls = P.d_lists + P.list_off[3 * step + 2];
       if (npo) { BDDC_COUNT(1); k_mf_potrf<<<npo, BDDC_THREADS, dsm, st>>>(d, lp, P.pscratch, err); }
       if (ntr) { BDDC_COUNT(1); k_mf_trsm<<<ntr, BDDC_THREADS, tsm, st>>>(d, lt); }
-      if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, dsm, st>>>(d, ls); }
+      if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, 0, st>>>(d, ls); }
     }
   }
   // solve matrices: Linv_P by tile rows, then G = L_UP Linv_P
   if (P.inv_len[0]) { BDDC_COUNT(1); k_mf_inv_diag<<<P.inv_len[0], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[0]); }
   for (size_t q = 2; q < P.inv_len.size(); ++q)
     if (P.inv_len[q]) {
-      BDDC_COUNT(1);
-      k_mf_inv_step<<<P.inv_len[q], BDDC_THREADS, dsm, st>>>(d, P.d_lists + P.inv_off[q], P.tscratch);
+      BDDC_COUNT(2);
+      k_mf_trtri<<<P.inv_len[q], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[q], 0);
+      k_mf_trtri<<<P.inv_len[q], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[q], 1);
     }
-  if (P.inv_len[1]) { BDDC_COUNT(1); k_mf_g<<<P.inv_len[1], BDDC_THREADS, dsm, st>>>(d, P.d_lists + P.inv_off[1]); }
+  if (P.inv_len[1]) { BDDC_COUNT(1); k_mf_g<<<P.inv_len[1], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[1]); }
 }
 
 void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream_t st) {

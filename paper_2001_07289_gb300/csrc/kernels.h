@@ -89,11 +89,16 @@ struct MFPlan {
   long long spool = 0;
   double* S = nullptr;
   long long* d_soff = nullptr;
-  std::vector<std::vector<int>> trtri_steps;   // per tile step t >= 1: int4 {front, t, s, 0}
+  // L_P^{-1} by recursive doubling: at level q (half block hb = 2^q tiles)
+  // the items {front, r, c, hb} cover every tile of the off-diagonal blocks
+  std::vector<std::vector<int>> trtri_steps;
   std::vector<int> diag_items, g_items;        // int4 lists: {front, t, t, 0}, {front, ut, st, 0}
   std::vector<long long> inv_off;              // device offsets of these lists
   std::vector<int> inv_len;
-  double* tscratch = nullptr;                  // 4096 doubles per concurrent inverse work item
+  std::vector<long long> toff;                 // per front: np x np block of the product scratch
+  long long tpool = 0;
+  long long* d_toff = nullptr;
+  double* tscratch = nullptr;                  // L_CA X_AA products of the doubling steps
   std::vector<int> fwd_items_off, bwd_items_off; // per level into the solve work lists
   int* d_solve_items = nullptr;                // int2 {front, chunk} lists for the solves
   std::vector<int> fwd_items_len, bwd_items_len;
