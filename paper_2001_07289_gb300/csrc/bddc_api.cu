@@ -510,7 +510,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   }
   mf_plan(h->mf, h->geom, nc);
   mf_upload(h->mf, [h](size_t b) { return h->dalloc(b); }, [h](size_t b) { return h->dalloc(b, true); }, st);
-  h->factor_bytes += sizeof(double) * (size_t)h->mf.spool;
+  h->factor_bytes += 2 * sizeof(double) * (size_t)h->mf.spool;   // solve matrices and their transposes
   configure_mf_kernels();
   mf_assemble(h->mf, L, h->color_subs, h->color_count, h->color_off, st);
   CK(cudaEventRecord(ev[5], st));

@@ -31,10 +31,11 @@ namespace bddc {
 
 // Factor tiles are 32 wide: FP64 issue on this GPU is about two FMAs per
 // clock per SM, so a 64-wide tile step on one CTA would be long and the
-// chain of diagonal-tile steps short of parallel work.  The forward solve
-// works on row chunks of FSR rows.
+// chain of diagonal-tile steps short of parallel work.  Both solves are row
+// dot products (forward on S_f, backward on its transpose) in chunks of FSR
+// rows, so a level spreads over many CTAs.
 constexpr int FNB = 32;
-constexpr int FSR = 64;
+constexpr int FSR = 8;    // rows per CTA in the solves, one per warp
 
 __host__ __device__ inline int mf_ntiles(int np, int nu) { return (np + FNB - 1) / FNB + (nu + FNB - 1) / FNB; }
 __host__ __device__ inline void mf_tile(int t, int np, int nu, int& r0, int& nr) {
@@ -266,7 +267,7 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
 struct MFDev {
   const int *np, *nu, *gid, *fr, *pp, *ord, *pmap, *parent;
   const long long *foff, *doff, *woff, *gid_off, *pmap_off, *soff, *toff;
-  double *F, *Dinv, *W, *S, *T;
+  double *F, *Dinv, *W, *S, *T, *ST;
 };
 
 // One 32 x 32 FP64 output tile on one CTA of 256 threads, two rows by two
@@ -495,12 +496,50 @@ k_mf_g(MFDev d, const int4* __restrict__ work) {
                        S + (long long)(np + u0) * np + s0, np, false, As, Bs);
 }
 
-// forward, one launch per level; work item {front, row chunk of FSR rows}:
+// S_f^T for the backward solve, 32 x 32 tiles through shared memory;
+// grid (front, tile stride)
+__global__ void k_mf_transpose(MFDev d) {
+  __shared__ double t[32][33];
+  const int f = blockIdx.x;
+  const int np = d.np[f], F = np + d.nu[f];
+  const double* S = d.S + d.soff[f];
+  double* ST = d.ST + d.soff[f];
+  const int tc = (np + 31) / 32, ntile = ((F + 31) / 32) * tc;
+  for (int tile = blockIdx.y; tile < ntile; tile += gridDim.y) {
+    const int r0 = (tile / tc) * 32, c0 = (tile % tc) * 32;
+    for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+      const int i = idx >> 5, j = idx & 31;
+      t[i][j] = (r0 + i < F && c0 + j < np) ? S[(long long)(r0 + i) * np + c0 + j] : 0.0;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
+      const int i = idx >> 5, j = idx & 31;
+      if (c0 + i < np && r0 + j < F) ST[(long long)(c0 + i) * F + r0 + j] = t[j][i];
+    }
+    __syncthreads();
+  }
+}
+
+// sum over c in [c0, c1) of row[c] w[c] by one warp: lanes stride the row
+// with eight independent chains so that eight loads per lane are in flight
+__device__ inline double mf_row_dot(const double* __restrict__ row, const double* w, int c0, int c1) {
+  const int lane = threadIdx.x & 31;
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int c = c0 + lane;
+  for (; c + 224 < c1; c += 256) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fma(row[c + 32 * u], w[c + 32 * u], a[u]);
+  }
+  for (; c < c1; c += 32) a[0] = fma(row[c], w[c], a[0]);
+  return mf_wsum(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
+}
+
+// forward, one launch per level; work item {front, chunk of FSR rows}:
 // w_P = b_P + children's update vectors at P, w_U likewise at U;
 // rows r < np: W[r] = (Linv_P w_P)[r];  rows r >= np: W[r] = w_U[r-np] - (G w_P)[r-np]
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_fwd2(MFDev d, const int2* __restrict__ items, const int* __restrict__ kid_ptr, const int* __restrict__ kid_list,
-          const int* __restrict__ lvl_index, const double* __restrict__ b) {
+k_mf_fwd(MFDev d, const int2* __restrict__ items, const int* __restrict__ kid_ptr, const int* __restrict__ kid_list,
+         const int* __restrict__ lvl_index, const double* __restrict__ b) {
   extern __shared__ __align__(128) unsigned char smraw[];
   double* w = reinterpret_cast<double*>(smraw);
   const int2 it = items[blockIdx.x];
@@ -517,34 +556,20 @@ k_mf_fwd2(MFDev d, const int2* __restrict__ items, const int* __restrict__ kid_p
     for (int k = threadIdx.x; k < d.nu[c]; k += blockDim.x) w[map[k]] += wc[k];
     __syncthreads();
   }
-  const double* S = d.S + d.soff[f];
-  double* Wf = d.W + d.woff[f];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int r0 = chunk * FSR, r1 = min(F, r0 + FSR);
-  for (int r = r0 + warp; r < r1; r += nw) {
-    const double* row = S + (long long)r * np;
-    const int cend = (r < np) ? r + 1 : np;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;   // four independent chains, loads in flight
-    int c = lane;
-    for (; c + 96 < cend; c += 128) {
-      a0 = fma(row[c], w[c], a0);
-      a1 = fma(row[c + 32], w[c + 32], a1);
-      a2 = fma(row[c + 64], w[c + 64], a2);
-      a3 = fma(row[c + 96], w[c + 96], a3);
-    }
-    for (; c < cend; c += 32) a0 = fma(row[c], w[c], a0);
-    double acc = mf_wsum((a0 + a1) + (a2 + a3));
-    if (lane == 0) Wf[r] = (r < np) ? acc : w[r] - acc;
+  const int r = chunk * FSR + (threadIdx.x >> 5);
+  if (r < F) {
+    const double acc = mf_row_dot(d.S + d.soff[f] + (long long)r * np, w, 0, (r < np) ? r + 1 : np);
+    if ((threadIdx.x & 31) == 0) d.W[d.woff[f] + r] = (r < np) ? acc : w[r] - acc;
   }
 }
 
-// backward, one launch per level; work item {front, column chunk of 64}:
-// x_P[c] = sum_{r>=c} Linv_P[r][c] y_P[r] - sum_u G[u][c] x_U[u]
+// backward, one launch per level; work item {front, chunk of FSR pivots}:
+// x_P[c] = sum_{c<=r<np} Linv_P[r][c] y_P[r] - sum_u G[u][c] x_U[u], i.e. row c
+// of S_f^T against [y_P; x_U]
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_bwd2(MFDev d, const int2* __restrict__ items, double* x) {
+k_mf_bwd(MFDev d, const int2* __restrict__ items, double* x) {
   extern __shared__ __align__(128) unsigned char smraw[];
   double* vec = reinterpret_cast<double*>(smraw);        // [y_P; x_U]
-  __shared__ double part[4][64];
   const int2 it = items[blockIdx.x];
   const int f = it.x, chunk = it.y;
   const int np = d.np[f], nu = d.nu[f], F = np + nu;
@@ -552,28 +577,13 @@ k_mf_bwd2(MFDev d, const int2* __restrict__ items, double* x) {
   const double* Wf = d.W + d.woff[f];
   for (int k = threadIdx.x; k < F; k += blockDim.x) vec[k] = (k < np) ? Wf[k] : x[g[k]];
   __syncthreads();
-  const double* S = d.S + d.soff[f];
-  const int cl = threadIdx.x & 63, grp = threadIdx.x >> 6;   // 64 columns x 4 row groups
-  const int c = chunk * 64 + cl;
-  double acc = 0.0;
+  const int c = chunk * FSR + (threadIdx.x >> 5);
   if (c < np) {
-    // rows r >= c of Linv_P (+) and all rows of G (-), four independent chains
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int r = c + grp;
-    for (; r + 12 < F; r += 16) {
-      const double s0 = (r < np) ? 1.0 : -1.0, s1 = (r + 4 < np) ? 1.0 : -1.0;
-      const double s2 = (r + 8 < np) ? 1.0 : -1.0, s3 = (r + 12 < np) ? 1.0 : -1.0;
-      a0 = fma(s0 * S[(long long)r * np + c], vec[r], a0);
-      a1 = fma(s1 * S[(long long)(r + 4) * np + c], vec[r + 4], a1);
-      a2 = fma(s2 * S[(long long)(r + 8) * np + c], vec[r + 8], a2);
-      a3 = fma(s3 * S[(long long)(r + 12) * np + c], vec[r + 12], a3);
-    }
-    for (; r < F; r += 4) a0 = fma(((r < np) ? 1.0 : -1.0) * S[(long long)r * np + c], vec[r], a0);
-    acc = (a0 + a1) + (a2 + a3);
+    const double* row = d.ST + d.soff[f] + (long long)c * F;
+    const double pos = mf_row_dot(row, vec, c, np);
+    const double neg = mf_row_dot(row, vec, np, F);
+    if ((threadIdx.x & 31) == 0) x[g[c]] = pos - neg;
   }
-  part[grp][cl] = acc;
-  __syncthreads();
-  if (grp == 0 && c < np) x[g[c]] = part[0][cl] + part[1][cl] + part[2][cl] + part[3][cl];
 }
 
 // ---------------------------------------------------------------------------
@@ -587,7 +597,7 @@ MFDev dev_of(const MFPlan& P) {
   d.foff = P.d_foff; d.doff = P.d_doff; d.woff = P.d_woff; d.gid_off = P.d_gid_off; d.pmap_off = P.d_pmap_off;
   d.F = P.F; d.Dinv = P.Dinv; d.W = P.W;
   d.S = P.S; d.soff = P.d_soff;
-  d.T = P.tscratch; d.toff = P.d_toff;
+  d.T = P.tscratch; d.toff = P.d_toff; d.ST = P.ST;
   return d;
 }
 
@@ -602,8 +612,8 @@ T* up(const std::vector<T>& v, const std::function<void*(size_t)>& alloc, cudaSt
 
 void configure_mf_kernels() {
   int sm = (int)sizeof(DenseSmem<double>);
-  cudaFuncSetAttribute(k_mf_fwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_mf_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mf_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mf_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mf_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_mf_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(2 * FNB * (FNB + 1) * sizeof(double)));
@@ -629,6 +639,7 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
   P.Dinv = (double*)tmp_alloc(sizeof(double) * std::max<long long>(P.dpool, 1));
   P.W = (double*)alloc(sizeof(double) * P.wpool);
   P.S = (double*)alloc(sizeof(double) * std::max<long long>(P.spool, 1));
+  P.ST = (double*)alloc(sizeof(double) * std::max<long long>(P.spool, 1));
   P.d_soff = up(P.soff, alloc, st);
   cudaMemsetAsync(P.F, 0, sizeof(double) * P.fpool, st);
   cudaMemsetAsync(P.S, 0, sizeof(double) * P.spool, st);
@@ -725,7 +736,7 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
     P.fwd_items_len[l] = (int)items.size() / 2 - P.fwd_items_off[l];
     P.bwd_items_off[l] = (int)items.size() / 2;
     for (int f : P.fronts_at_level[l])
-      for (int c = 0; c < (P.np[f] + 63) / 64; ++c) items.insert(items.end(), {f, c});
+      for (int c = 0; c < (P.np[f] + FSR - 1) / FSR; ++c) items.insert(items.end(), {f, c});
     P.bwd_items_len[l] = (int)items.size() / 2 - P.bwd_items_off[l];
   }
   P.d_solve_items = up(items, alloc, st);
@@ -779,6 +790,8 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st) {
       k_mf_trtri<<<P.inv_len[q], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[q], 1);
     }
   if (P.inv_len[1]) { BDDC_COUNT(1); k_mf_g<<<P.inv_len[1], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[1]); }
+  BDDC_COUNT(1);
+  k_mf_transpose<<<dim3(P.nfront, 16), BDDC_THREADS, 0, st>>>(d);
 }
 
 void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream_t st) {
@@ -792,11 +805,11 @@ void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream
   const size_t sm = sizeof(double) * (size_t)P.maxF;
   for (int l = P.nlevel - 1; l >= 0; --l) {
     BDDC_COUNT(1);
-    k_mf_fwd2<<<P.fwd_items_len[l], BDDC_THREADS, sm, st>>>(d, items + P.fwd_items_off[l], kptr, klist, lidx, b);
+    k_mf_fwd<<<P.fwd_items_len[l], BDDC_THREADS, sm, st>>>(d, items + P.fwd_items_off[l], kptr, klist, lidx, b);
   }
   for (int l = 0; l < P.nlevel; ++l) {
     BDDC_COUNT(1);
-    k_mf_bwd2<<<P.bwd_items_len[l], BDDC_THREADS, sm, st>>>(d, items + P.bwd_items_off[l], x);
+    k_mf_bwd<<<P.bwd_items_len[l], BDDC_THREADS, sm, st>>>(d, items + P.bwd_items_off[l], x);
   }
 }
 

@@ -128,13 +128,18 @@ template <typename T>
 __device__ void tile_chol(T* S, int n, DenseSmem<T>& sm) {
   const int tid = threadIdx.x;
   for (int c = 0; c < n; ++c) {
+    // one thread takes the square root and the reciprocal (an FP64 divide is
+    // a long instruction sequence; every thread repeating it costs more than
+    // the column's whole update)
     if (tid == 0) {
       T d = S[c * TLD + c];
       if (!(d > T(0))) { sm.flag = 1; d = T(1); }
-      S[c * TLD + c] = sqrt(d);
+      const T l = sqrt(d);
+      S[c * TLD + c] = l;
+      sm.rd[c] = T(1) / l;
     }
     __syncthreads();
-    const T rinv = T(1) / S[c * TLD + c];
+    const T rinv = sm.rd[c];
     for (int i = c + 1 + tid; i < n; i += BDDC_THREADS) S[i * TLD + c] *= rinv;
     __syncthreads();
     const int m = n - c - 1;
@@ -147,19 +152,31 @@ __device__ void tile_chol(T* S, int n, DenseSmem<T>& sm) {
 }
 
 // X = L^{-1} for a lower n x n tile (both ld TLD); zeros above the diagonal.
-// rdiag: n entries of scratch for the reciprocal diagonal.
+// rdiag: n entries of scratch for the reciprocal diagonal.  Right-looking
+// substitution on the identity, every thread of the CTA taking part: after
+// step k row k holds (delta - sum_{m<k} L[k][m] X[m][.]) and X[k][.] is that
+// row times 1/L[k][k]; step k subtracts L[i][k] X[k][j] from the rows below.
 template <typename T>
 __device__ void tile_inv(const T* L, T* X, int n, T* rdiag) {
-  const int j = threadIdx.x;
-  if (j < n) rdiag[j] = T(1) / L[j * TLD + j];
+  const int tid = threadIdx.x;
+  if (tid < n) rdiag[tid] = T(1) / L[tid * TLD + tid];
+  for (int idx = tid; idx < TILE * TILE; idx += BDDC_THREADS) {
+    const int i = idx / TILE, j = idx % TILE;
+    X[i * TLD + j] = (i == j) ? T(1) : T(0);
+  }
   __syncthreads();
-  if (j < n) {
-    for (int i = 0; i < n; ++i) {
-      if (i < j) { X[i * TLD + j] = T(0); continue; }
-      T s = (i == j) ? T(1) : T(0);
-      for (int k = j; k < i; ++k) s -= L[i * TLD + k] * X[k * TLD + j];
-      X[i * TLD + j] = s * rdiag[i];
+  for (int k = 0; k + 1 < n; ++k) {
+    const int m = n - k - 1, w = k + 1;
+    const T rk = rdiag[k];
+    for (int idx = tid; idx < m * w; idx += BDDC_THREADS) {
+      const int i = k + 1 + idx / w, j = idx % w;
+      X[i * TLD + j] -= L[i * TLD + k] * (X[k * TLD + j] * rk);
     }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < n * n; idx += BDDC_THREADS) {
+    const int i = idx / n, j = idx % n;
+    if (j <= i) X[i * TLD + j] *= rdiag[i];
   }
   __syncthreads();
 }

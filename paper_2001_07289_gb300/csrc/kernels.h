@@ -88,6 +88,7 @@ struct MFPlan {
   std::vector<long long> soff;
   long long spool = 0;
   double* S = nullptr;
+  double* ST = nullptr;             // S_f^T (np x F, ld F) at the same offsets, for the backward solve
   long long* d_soff = nullptr;
   // L_P^{-1} by recursive doubling: at level q (half block hb = 2^q tiles)
   // the items {front, r, c, hb} cover every tile of the off-diagonal blocks
