@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <stdexcept>
@@ -44,6 +45,61 @@ struct BddcError : std::runtime_error {
   } while (0)
 
 thread_local std::string g_setup_error;
+
+// Device blocks of destroyed handles (and the setup scratch of live ones) are
+// kept per device and handed to later allocations of the same size class: a
+// solver that sets up one problem after another with the same shapes then
+// stops paying cudaMalloc and cudaFree in every setup.  Size classes waste at
+// most 1/8 above 1 MiB.  The cache holds at most an eighth of the device's
+// memory (16 GiB at most); a failed cudaMalloc empties it and retries.
+class BlockCache {
+ public:
+  static size_t round(size_t b) {
+    if (b <= (size_t(1) << 20)) return (b + 511) & ~size_t(511);
+    size_t p = size_t(1) << 20;
+    while (p < b) p <<= 1;
+    const size_t step = p >> 3;
+    return (b + step - 1) / step * step;
+  }
+  void* take(int dev, size_t rb) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto& m = free_[dev & 15];
+    auto it = m.find(rb);
+    if (it == m.end()) return nullptr;
+    void* p = it->second;
+    m.erase(it);
+    held_[dev & 15] -= rb;
+    return p;
+  }
+  void put(int dev, void* p, size_t rb) {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (limit_[dev & 15] == 0) {
+      size_t fr = 0, tot = 0;
+      cudaMemGetInfo(&fr, &tot);
+      limit_[dev & 15] = std::min<size_t>(tot / 8, size_t(16) << 30);
+    }
+    if (held_[dev & 15] + rb > limit_[dev & 15]) { cudaFree(p); return; }
+    free_[dev & 15].emplace(rb, p);
+    held_[dev & 15] += rb;
+  }
+  void release(int dev) {
+    std::lock_guard<std::mutex> lk(mu_);
+    for (auto& kv : free_[dev & 15]) cudaFree(kv.second);
+    free_[dev & 15].clear();
+    held_[dev & 15] = 0;
+  }
+
+ private:
+  std::mutex mu_;
+  std::multimap<size_t, void*> free_[16];
+  size_t held_[16] = {0};
+  size_t limit_[16] = {0};
+};
+
+BlockCache& block_cache() {
+  static BlockCache* c = new BlockCache();   // never destroyed: handles may outlive static teardown
+  return *c;
+}
 
 struct AxisHost {
   int n = 0;
@@ -127,8 +183,8 @@ struct bddc_handle {
   long long n_nodes = 0, n_free = 0;
   LocalLaunch L{};
   MeshDev m{};
-  // device buffers
-  std::vector<void*> allocs;
+  // device buffers (pointer, rounded size), returned to the block cache
+  std::vector<std::pair<void*, size_t>> allocs;
   size_t bytes = 0, factor_bytes = 0;
   double* alpha = nullptr;       // private copy of alpha
   double* Ac_copy = nullptr;      // dense coarse matrix, kept for small problems (diagnostics)
@@ -155,36 +211,48 @@ struct bddc_handle {
   float setup_ms = 0.f;
   float phase_ms[6] = {0, 0, 0, 0, 0, 0};
   long long launch_base = 0;
-  std::vector<void*> setup_only;
+  std::vector<std::pair<void*, size_t>> setup_only;
   std::vector<int> h_cptr, h_clist;   // coarse DOF -> owners (CSR), colour lists
   std::vector<int2> h_cent;
   std::string error;
 
   void* dalloc(size_t b, bool setup_tmp = false) {
-    void* ptr = nullptr;
     if (b == 0) b = 16;
-    cudaError_t e = cudaMalloc(&ptr, b);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      throw BddcError(BDDC_ERR_OOM, "cudaMalloc of " + std::to_string(b) + " bytes failed");
+    const size_t rb = BlockCache::round(b);
+    void* ptr = block_cache().take(device, rb);
+    if (!ptr) {
+      cudaError_t e = cudaMalloc(&ptr, rb);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        block_cache().release(device);
+        e = cudaMalloc(&ptr, rb);
+      }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw BddcError(BDDC_ERR_OOM, "cudaMalloc of " + std::to_string(b) + " bytes failed");
+      }
     }
-    (setup_tmp ? setup_only : allocs).push_back(ptr);
+    (setup_tmp ? setup_only : allocs).emplace_back(ptr, rb);
     if (!setup_tmp) bytes += b;
     return ptr;
   }
   template <typename T> T* dnew(size_t count, bool setup_tmp = false) {
     return (T*)dalloc(sizeof(T) * count, setup_tmp);
   }
+  // callers make sure no queued work still uses the blocks (setup ends with
+  // a stream synchronisation; the destructor synchronises the device, as
+  // cudaFree would)
   void free_setup_only() {
-    for (void* v : setup_only) cudaFree(v);
+    for (auto& v : setup_only) block_cache().put(device, v.first, v.second);
     setup_only.clear();
   }
   ~bddc_handle() {
+    cudaDeviceSynchronize();
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
     free_setup_only();
-    for (void* v : allocs) cudaFree(v);
+    for (auto& v : allocs) block_cache().put(device, v.first, v.second);
     if (pinned) cudaFreeHost(pinned);
   }
 };
@@ -241,7 +309,11 @@ void build_metadata(bddc_handle* h) {
   const int S = nsub[0] * nsub[1] * nsub[2];
   h->subs.assign(S, SubDesc{});
   h->lc.clear();
-  std::vector<std::vector<int2>> owners(nc);
+  // (coarse id, subdomain, local position) of every local coarse DOF, in
+  // subdomain order; a counting sort by coarse id gives the owner lists
+  std::vector<int> own_g;
+  std::vector<int2> own_e;
+  std::vector<LocalCoarse> verts, avgs;
   long long offD = 0, offN = 0, offW = 0, offY = 0, offG = 0, offL = 0, offPA = 0, offSc = 0, offAc = 0, offPhi = 0,
             offB = 0, offVec = 0;
   LocalLaunch& L = h->L;
@@ -262,7 +334,8 @@ void build_metadata(bddc_handle* h) {
         s.color = (sx & 1) + 2 * (sy & 1) + 4 * (sz & 1);
         const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
         // local coarse DOFs: vertices first, then averages, each lexicographic
-        std::vector<LocalCoarse> verts, avgs;
+        verts.clear();
+        avgs.clear();
         for (int iz = ilo[2]; iz <= ihi[2]; ++iz)
           for (int iy = ilo[1]; iy <= ihi[1]; ++iy)
             for (int ix = ilo[0]; ix <= ihi[0]; ++ix) {
@@ -287,7 +360,10 @@ void build_metadata(bddc_handle* h) {
         s.cofs = (int)h->lc.size();
         for (auto& c : verts) h->lc.push_back(c);
         for (auto& c : avgs) h->lc.push_back(c);
-        for (int j = 0; j < s.nc; ++j) owners[h->lc[s.cofs + j].gid].push_back(make_int2(si, s.cofs + j));
+        for (int j = 0; j < s.nc; ++j) {
+          own_g.push_back(h->lc[s.cofs + j].gid);
+          own_e.push_back(make_int2(si, s.cofs + j));
+        }
         s.nB = surf_count(px, py, pz);
         const int QN = px * py, NN = QN * pz;
         const int qx = s.w[0] - 1, qy = s.w[1] - 1, qz = s.w[2] - 1;
@@ -313,13 +389,15 @@ void build_metadata(bddc_handle* h) {
       }
   L.nsub = S;
   h->L.mscratch_stride = (long long)L.maxQN * CW;
-  // coarse owners CSR
+  // coarse owners CSR, owners of a coarse DOF in subdomain order (stable
+  // counting sort of the subdomain-ordered list)
   std::vector<int> ptr(nc + 1, 0);
-  std::vector<int2> ent;
-  for (int g = 0; g < nc; ++g) {
-    std::sort(owners[g].begin(), owners[g].end(), [](int2 a, int2 b) { return a.x < b.x; });
-    ptr[g + 1] = ptr[g] + (int)owners[g].size();
-    for (auto e : owners[g]) ent.push_back(e);
+  for (int g : own_g) ++ptr[g + 1];
+  for (int g = 0; g < nc; ++g) ptr[g + 1] += ptr[g];
+  std::vector<int2> ent(own_e.size());
+  {
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (size_t q = 0; q < own_g.size(); ++q) ent[fill[own_g[q]]++] = own_e[q];
   }
   h->geom.objid = std::move(objid);
   // colour lists
@@ -426,8 +504,10 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   const long long NE = (long long)M.nx * M.ny * M.nz;
   h->alpha = h->dnew<double>(NE);
   CK(cudaMemcpyAsync(h->alpha, alpha_dev, sizeof(double) * NE, cudaMemcpyDeviceToDevice, st));
+  // alpha's check sets the first error code; it is read with every other
+  // device-side failure at the end of setup (nothing below can hang or fault
+  // on a bad alpha: every loop is bounded by sizes and every wait by a count)
   launch_check_alpha(h->alpha, NE, h->err, st);
-  check_err_flags(h, st);
   // axis tables
   MeshDev& m = h->m;
   m.nx = M.nx; m.ny = M.ny; m.nz = M.nz;

@@ -219,24 +219,31 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
     P.flops += (double)P.np[f] * P.np[f] * P.np[f] / 6.0 + (double)P.nu[f] * P.np[f] * P.np[f] / 2.0;
   }
   P.tpool = to;
-  // child update rows -> positions in the parent front
+  // child update rows -> positions in the parent front: a table of each
+  // object's position in the current parent, stamped with the parent's id
   P.pmap_off.assign(nf + 1, 0);
-  for (int f = 0; f < nf; ++f) {
-    const int p = P.parent[f];
-    if (p >= 0) {
-      const int* ub = P.gid.data() + P.gid_off[p] + P.np[p];
-      for (int o : B.upd[f]) {
-        int q;
-        if (P.fr[o] == p) q = P.pp[o];
-        else {
-          const int* it = std::lower_bound(ub, ub + P.nu[p], o);
-          if (it == ub + P.nu[p] || *it != o) throw std::runtime_error("update set not nested in the parent front");
-          q = P.np[p] + (int)(it - ub);
+  {
+    std::vector<long long> cnt(nf + 1, 0);
+    for (int f = 0; f < nf; ++f) cnt[f + 1] = cnt[f] + (P.parent[f] >= 0 ? (long long)B.upd[f].size() : 0);
+    P.pmap_off = cnt;
+    P.pmap.assign(cnt[nf], 0);
+    std::vector<int> pos(nc, -1), stamp(nc, -1);
+    std::vector<std::vector<int>> kids_of(nf);
+    for (int f = 0; f < nf; ++f)
+      if (P.parent[f] >= 0) kids_of[P.parent[f]].push_back(f);
+    for (int p = 0; p < nf; ++p) {
+      if (kids_of[p].empty()) continue;
+      const int* gp = P.gid.data() + P.gid_off[p];
+      const int Fp = P.np[p] + P.nu[p];
+      for (int q = 0; q < Fp; ++q) { pos[gp[q]] = q; stamp[gp[q]] = p; }
+      for (int c : kids_of[p]) {
+        long long w = P.pmap_off[c];
+        for (int o : B.upd[c]) {
+          if (stamp[o] != p) throw std::runtime_error("update set not nested in the parent front");
+          P.pmap[w++] = pos[o];
         }
-        P.pmap.push_back(q);
       }
     }
-    P.pmap_off[f + 1] = (long long)P.pmap.size();
   }
   // work lists per (level, panel step)
   P.step_potrf.clear(); P.step_trsm.clear(); P.step_syrk.clear();
@@ -246,6 +253,13 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
     for (int f : P.fronts_at_level[l]) maxpt = std::max(maxpt, (P.np[f] + FNB - 1) / FNB);
     for (int j = 0; j < maxpt; ++j) {
       std::vector<int> po, tr, sy;
+      size_t ntr = 0, nsy = 0;
+      for (int f : P.fronts_at_level[l]) {
+        const int npt = (P.np[f] + FNB - 1) / FNB, nt = mf_ntiles(P.np[f], P.nu[f]);
+        if (j < npt) { ntr += nt - j - 1; nsy += (size_t)(nt - j - 1) * (nt - j) / 2; }
+      }
+      tr.reserve(4 * ntr);
+      sy.reserve(4 * nsy);
       for (int f : P.fronts_at_level[l]) {
         const int npt = (P.np[f] + FNB - 1) / FNB, nt = mf_ntiles(P.np[f], P.nu[f]);
         if (j >= npt) continue;
