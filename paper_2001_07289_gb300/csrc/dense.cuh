@@ -22,6 +22,7 @@ struct DenseSmem {
   T t1[TILE * TLD];
   T t2[TILE * TLD];
   T rd[TILE];
+  T lv[TILE];
   int flag;
 };
 
@@ -121,34 +122,51 @@ __device__ void cta_gemm(int M, int N, int K, T alpha,
   __syncthreads();
 }
 
+// Thread map of the 32 x 32 tile routines: thread t owns row t / 8 and the
+// columns t % 8 + 8q, q = 0..3 (no integer division in the loops).
+
 // Unblocked Cholesky of an n x n (n <= 32) tile in shared memory (ld TLD),
-// lower triangle in place.  A non-positive (or NaN) pivot sets sm.flag and is
-// replaced by 1 so that the computation stays finite.
+// lower triangle in place, one barrier per column: step c reads column c
+// unscaled and scales it on the fly (L[i][c] = S[i][c] / L[c][c]); the thread
+// that finishes S[c+1][c+1] takes its square root and reciprocal right away,
+// and column c is written back scaled in step c + 1, when nothing reads it.
+// A non-positive (or NaN) pivot sets sm.flag and is replaced by 1 so that the
+// computation stays finite.
 template <typename T>
 __device__ void tile_chol(T* S, int n, DenseSmem<T>& sm) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, i = tid >> 3, cg = tid & 7;
+  auto pivot = [&](int c, T d) {
+    if (!(d > T(0))) { sm.flag = 1; d = T(1); }
+    const T l = sqrt(d);
+    sm.lv[c] = l;
+    sm.rd[c] = T(1) / l;
+  };
+  if (tid == 0 && n > 0) pivot(0, S[0]);
+  __syncthreads();
   for (int c = 0; c < n; ++c) {
-    // one thread takes the square root and the reciprocal (an FP64 divide is
-    // a long instruction sequence; every thread repeating it costs more than
-    // the column's whole update)
-    if (tid == 0) {
-      T d = S[c * TLD + c];
-      if (!(d > T(0))) { sm.flag = 1; d = T(1); }
-      const T l = sqrt(d);
-      S[c * TLD + c] = l;
-      sm.rd[c] = T(1) / l;
-    }
-    __syncthreads();
-    const T rinv = sm.rd[c];
-    for (int i = c + 1 + tid; i < n; i += BDDC_THREADS) S[i * TLD + c] *= rinv;
-    __syncthreads();
-    const int m = n - c - 1;
-    for (int idx = tid; idx < m * m; idx += BDDC_THREADS) {
-      int i = c + 1 + idx / m, j = c + 1 + idx % m;
-      if (j <= i) S[i * TLD + j] -= S[i * TLD + c] * S[j * TLD + c];
+    const T r = sm.rd[c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = cg + 8 * q;
+      if (i >= n || j >= n) continue;
+      if (c > 0 && j == c - 1 && i >= j)   // write back column c - 1
+        S[i * TLD + j] = (i == j) ? sm.lv[j] : S[i * TLD + j] * sm.rd[j];
+      if (j > c && j <= i) {
+        const T v = S[i * TLD + j] - (S[i * TLD + c] * r) * (S[j * TLD + c] * r);
+        S[i * TLD + j] = v;
+        if (i == c + 1 && j == c + 1) pivot(c + 1, v);
+      }
     }
     __syncthreads();
   }
+  if (n > 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = cg + 8 * q;
+      if (j == n - 1 && i == n - 1) S[i * TLD + j] = sm.lv[j];
+    }
+  }
+  __syncthreads();
 }
 
 // X = L^{-1} for a lower n x n tile (both ld TLD); zeros above the diagonal.
@@ -158,25 +176,33 @@ __device__ void tile_chol(T* S, int n, DenseSmem<T>& sm) {
 // row times 1/L[k][k]; step k subtracts L[i][k] X[k][j] from the rows below.
 template <typename T>
 __device__ void tile_inv(const T* L, T* X, int n, T* rdiag) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, i = tid >> 3, cg = tid & 7;
   if (tid < n) rdiag[tid] = T(1) / L[tid * TLD + tid];
-  for (int idx = tid; idx < TILE * TILE; idx += BDDC_THREADS) {
-    const int i = idx / TILE, j = idx % TILE;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = cg + 8 * q;
     X[i * TLD + j] = (i == j) ? T(1) : T(0);
   }
   __syncthreads();
   for (int k = 0; k + 1 < n; ++k) {
-    const int m = n - k - 1, w = k + 1;
     const T rk = rdiag[k];
-    for (int idx = tid; idx < m * w; idx += BDDC_THREADS) {
-      const int i = k + 1 + idx / w, j = idx % w;
-      X[i * TLD + j] -= L[i * TLD + k] * (X[k * TLD + j] * rk);
+    if (i > k && i < n) {
+      const T lik = L[i * TLD + k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = cg + 8 * q;
+        if (j <= k) X[i * TLD + j] -= lik * (X[k * TLD + j] * rk);
+      }
     }
     __syncthreads();
   }
-  for (int idx = tid; idx < n * n; idx += BDDC_THREADS) {
-    const int i = idx / n, j = idx % n;
-    if (j <= i) X[i * TLD + j] *= rdiag[i];
+  if (i < n) {
+    const T ri = rdiag[i];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = cg + 8 * q;
+      if (j <= i) X[i * TLD + j] *= ri;
+    }
   }
   __syncthreads();
 }
@@ -200,10 +226,16 @@ __device__ bool cta_chol_inv(T* S, int lds, T* Linv, int ldl, int n, T* diag, De
     __syncthreads();
     tile_chol(sm.t0, nb, sm);
     tile_inv(sm.t0, sm.t1, nb, sm.rd);
-    for (int idx = tid; idx < nb * nb; idx += BDDC_THREADS) {
-      int i = idx / nb, j = idx % nb;
-      if (j <= i) S[(long long)(j0 + i) * lds + j0 + j] = sm.t0[i * TLD + j];
-      diag[jb * TILE * TILE + i * TILE + j] = sm.t1[i * TLD + j];
+    {
+      const int i = tid >> 3, cg = tid & 7;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = cg + 8 * q;
+        if (i < nb && j < nb) {
+          if (j <= i) S[(long long)(j0 + i) * lds + j0 + j] = sm.t0[i * TLD + j];
+          diag[jb * TILE * TILE + i * TILE + j] = sm.t1[i * TLD + j];
+        }
+      }
     }
     // panel below the diagonal tile: P = P * Tinv^T, 32 rows at a time
     // through shared memory, every thread producing 4 outputs
@@ -215,11 +247,17 @@ __device__ bool cta_chol_inv(T* S, int lds, T* Linv, int ldl, int n, T* diag, De
         sm.t2[i * TLD + k] = (i < pr && k < nb) ? S[(long long)(p0 + i) * lds + j0 + k] : T(0);
       }
       __syncthreads();
-      for (int idx = tid; idx < pr * nb; idx += BDDC_THREADS) {
-        const int i = idx / nb, c = idx % nb;
-        T acc = T(0);
-        for (int k = 0; k <= c; ++k) acc += sm.t2[i * TLD + k] * sm.t1[c * TLD + k];
-        S[(long long)(p0 + i) * lds + j0 + c] = acc;
+      {
+        const int i = tid >> 3, cg = tid & 7;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = cg + 8 * q;
+          if (i < pr && c < nb) {
+            T acc = T(0);
+            for (int k = 0; k <= c; ++k) acc += sm.t2[i * TLD + k] * sm.t1[c * TLD + k];
+            S[(long long)(p0 + i) * lds + j0 + c] = acc;
+          }
+        }
       }
       __syncthreads();
     }
