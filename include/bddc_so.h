@@ -108,7 +108,8 @@ typedef struct {
     long long launches;   /* kernels launched for this handle since its setup
                              began (setup, applies, solves, gradients)        */
     double coarse_fma;    /* multiply-adds of the coarse factorisation         */
-    double local_factor_fma;  /* multiply-adds of the local plane-block factorisations */
+    double local_factor_fma;  /* multiply-adds of the local factorisations (inverse
+                                 Schur complements of the plane blocks)           */
     long long apply_bytes;    /* bytes one bddc_apply must read from HBM: local
                                  factors (Dirichlet twice), Phi twice, coarse fronts */
 } bddc_info_t;

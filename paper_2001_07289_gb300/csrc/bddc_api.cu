@@ -540,10 +540,8 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   L.facD = h->dalloc(es * lay.D);
   L.facN = h->dalloc(es * lay.N);
   L.Phi = h->dalloc(es * lay.Phi);
-  L.facDT = h->dalloc(es * lay.D);
-  L.facNT = h->dalloc(es * lay.N);
   L.PhiT = h->dalloc(es * lay.Phi);
-  h->factor_bytes = 2 * es * (lay.D + lay.N + lay.Phi);
+  h->factor_bytes = es * (lay.D + lay.N + 2 * lay.Phi);   // inverse Schur slots, Phi and Phi^T
   L.delta = h->dnew<double>(lay.B);
   L.vgam = h->dnew<double>(lay.B);
   L.vloc = h->dalloc(es * lay.Vec);
@@ -976,8 +974,8 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   info->launches = g_launches - h->launch_base;
   info->coarse_fma = h->mf.flops;
   // local factorisation work and the bytes one apply has to stream: per
-  // subdomain and plane the inverse diagonal factor (lower half) and the
-  // sub-diagonal block, read twice per solve (forward and backward sweeps)
+  // subdomain and solve, the 2 nz - 1 symmetric inverse Schur slots (full
+  // Q x Q rows) and the nine diagonals of the couplings, forward and backward
   double fma = 0.0;
   long long bytes = 0;
   const int es = h->local_double ? 8 : 4;
@@ -985,16 +983,17 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
     const double QN = (double)(s.w[0] + 1) * (s.w[1] + 1), nzN = s.w[2] + 1;
     const double QD = (s.w[0] > 1 && s.w[1] > 1 && s.w[2] > 1) ? (double)(s.w[0] - 1) * (s.w[1] - 1) : 0.0;
     const double nzD = QD > 0 ? s.w[2] - 1 : 0;
-    // per plane: Cholesky and inverse of the Schur block (Q^3/3); per plane
-    // after the first: M_k = B Linv^T (nine stencil terms, 9 Q^2) and the
-    // lower half of M_k M_k^T (Q^3/2)
+    // per plane: symmetric sweep of the Schur block (Q pivots over the lower
+    // triangle, Q^3/2); per plane after the first: S_{k-1}^{-1} B_k^T and
+    // B_k (.) (nine stencil terms each, 18 Q^2)
     auto planes = [](double Q, double nz) {
-      return nz > 0 ? nz * Q * Q * Q / 3.0 + (nz - 1) * (Q * Q * Q / 2.0 + 9.0 * Q * Q) : 0.0;
+      return nz > 0 ? nz * Q * Q * Q / 2.0 + (nz - 1) * 18.0 * Q * Q : 0.0;
     };
     fma += planes(QN, nzN) + planes(QD, nzD);
-    const double perN = (nzN * QN * (QN + 1) / 2 + (nzN - 1) * QN * QN) * es;
-    const double perD = (nzD * QD * (QD + 1) / 2 + std::max(nzD - 1, 0.0) * QD * QD) * es;
-    bytes += (long long)(2 * perN + 4 * perD + 2.0 * s.nB * s.nc * es);
+    auto solve = [es](double Q, double nz) {
+      return nz > 0 ? ((2 * nz - 1) * Q * Q + 2 * (nz - 1) * 9 * Q) * es : 0.0;
+    };
+    bytes += (long long)(solve(QN, nzN) + 2 * solve(QD, nzD) + 2.0 * s.nB * s.nc * es);
   }
   for (int f = 0; f < h->mf.nfront; ++f) {
     const long long np = h->mf.np[f], nu = h->mf.nu[f];

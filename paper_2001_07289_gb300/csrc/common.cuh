@@ -6,9 +6,10 @@
 //   * subdomain i is the element box [e0, e0+w) per axis; its local Neumann
 //     grid has p = w+1 nodes per axis, its Dirichlet (interior) grid q = w-1.
 //   * local plane-block factors: for a grid of Q = gx*gy nodes per z-plane and
-//     gz planes, slot k (k = 0..gz-1) holds the inverse Cholesky factor of the
-//     k-th diagonal block (lower triangular, Q x Q, row-major) and slot
-//     gz + k - 1 (k = 1..gz-1) the sub-diagonal factor block L_{k,k-1}.
+//     gz planes, slot k (k = 0..gz-1) holds S_k^{-1}, the inverse of the k-th
+//     Schur complement of the block-tridiagonal matrix (symmetric, full Q x Q,
+//     row-major), and slot gz + k - 1 (k = 1..gz-1) the coupling
+//     B_k = A_{k,k-1} as nine stencil diagonals (9 x Q).
 //   * box-surface ("boundary list") order: all nodes of the local Neumann grid
 //     with at least one coordinate at 0 or p-1, in lexicographic order.
 #pragma once

@@ -24,7 +24,7 @@ struct LocalLaunch {
   void *facD, *facN, *scratch, *mscratch;
   long long mscratch_stride;
   void *Y, *G, *Lv, *PA, *Sc, *Phi, *vloc;
-  void *facDT, *facNT, *PhiT;      // transposed copies read by the forward sweeps / Phi products
+  void* PhiT;                      // transposed copy of Phi for the apply's column accumulations
   double* Ac;
   double* delta;
   double* vgam;

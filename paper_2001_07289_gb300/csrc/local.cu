@@ -20,6 +20,7 @@
 // Local matrices are stored as z-plane blocks (see common.cuh); the factor of
 // each diagonal block is kept as its explicit inverse, so every sweep is a
 // sequence of dense products.
+#include <type_traits>
 #include "common.cuh"
 #include "dense.cuh"
 #include "kernels.h"
@@ -94,7 +95,9 @@ __device__ inline T warp_sum(T v) {
 // ---------------------------------------------------------------------------
 
 // grid: (subdomain, plane k, chunk); writes the diagonal block D_k to slot k
-// and A_{k,k-1} to slot gz+k-1.
+// (dense Q x Q) and the coupling B_k = A_{k,k-1} to slot gz+k-1 as its nine
+// stencil diagonals: Bd[o][i] = B_k[i][i + dx + dy gx], o = 3 (dy+1) + dx+1
+// (zero where the neighbour is off the plane).
 template <typename T>
 __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha,
                            T* __restrict__ fac, int neumann) {
@@ -105,110 +108,320 @@ __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const do
   const int Q = g.gx * g.gy;
   T* base = fac + (neumann ? s.offN : s.offD);
   const long long QQ = (long long)Q * Q, SS = slot_stride(Q);
-  for (long long e = (long long)blockIdx.z * blockDim.x + threadIdx.x; e < 2 * QQ;
+  const long long n1 = (k > 0) ? 9LL * Q : 0;
+  for (long long e = (long long)blockIdx.z * blockDim.x + threadIdx.x; e < QQ + n1;
        e += (long long)gridDim.z * blockDim.x) {
-    int which = (int)(e / QQ);  // 0: diagonal block, 1: block (k, k-1)
-    if (which == 1 && k == 0) continue;
-    long long r = e % QQ;
-    int a = (int)(r / Q), b = (int)(r % Q);
-    int ax = a % g.gx, ay = a / g.gx, bx = b % g.gx, by = b / g.gx;
-    int bz = (which == 0) ? k : k - 1;
-    int dx = bx - ax, dy = by - ay, dz = bz - k;
+    int a, bx, by, bz, dx, dy;
+    if (e < QQ) {
+      a = (int)(e / Q);
+      const int b = (int)(e % Q);
+      bx = b % g.gx; by = b / g.gx; bz = k;
+      dx = bx - a % g.gx; dy = by - a / g.gx;
+    } else {
+      const int o = (int)((e - QQ) / Q);
+      a = (int)((e - QQ) % Q);
+      dx = o % 3 - 1; dy = o / 3 - 1;
+      bx = a % g.gx + dx; by = a / g.gx + dy; bz = k - 1;
+    }
+    const int ax = a % g.gx, ay = a / g.gx, dz = bz - k;
     double v = 0.0;
-    if (abs(dx) <= 1 && abs(dy) <= 1) {
+    if (abs(dx) <= 1 && abs(dy) <= 1 && bx >= 0 && bx < g.gx && by >= 0 && by < g.gy) {
       bool fa = neumann && neumann_fixed(m, s, ax, ay, k);
       bool fb = neumann && neumann_fixed(m, s, bx, by, bz);
       if (fa || fb) v = (dx == 0 && dy == 0 && dz == 0) ? 1.0 : 0.0;
       else v = box_entry(m, alpha, s, s.e0[0] + g.off + ax, s.e0[1] + g.off + ay, s.e0[2] + g.off + k,
                          dx, dy, dz);
     }
-    T* blk = base + (which == 0 ? (long long)k : (long long)(g.gz + k - 1)) * SS;
-    blk[r] = (T)v;
+    if (e < QQ) base[(long long)k * SS + e] = (T)v;
+    else base[(long long)(g.gz + k - 1) * SS + (e - QQ)] = (T)v;
   }
 }
 
 // ---------------------------------------------------------------------------
-// batched block-tridiagonal Cholesky:  for k: M_k = B_{k-1} Linv_{k-1}^T,
-// S_k = D_k - M_k M_k^T, Linv_k = chol(S_k)^{-1}.  One CTA per subdomain.
+// batched block-tridiagonal factorisation by inverse Schur complements:
+//   S_0 = D_0,  S_k = D_k - B_k S_{k-1}^{-1} B_k^T,  slot k <- S_k^{-1}.
+// B_k has nine stencil entries per row, so the sandwich costs 18 Q^2
+// multiply-adds (T = S_{k-1}^{-1} B_k^T, then S_k = D_k - B_k T).  S_k is
+// inverted by the symmetric sweep of its lower triangle (Gauss-Jordan
+// without pivoting, stable for SPD matrices): for pivot p with d = A[p][p],
+//   A[i][j] -= A[i][p] A[j][p] / d   (i, j != p),
+//   A[i][p] <- A[i][p] / d,   A[p][p] <- -1 / d,
+// which leaves -S^{-1} after all Q pivots.  The packed lower triangle lives in
+// shared memory when it fits (else in the scratch, L2-resident); thread t
+// owns the entries with i = t/16 (mod 16) and j = t (mod 16).  One barrier per
+// pivot: the pivot column is double-buffered and the threads owning column
+// p + 1 publish it, and the reciprocal of the next pivot, as they update it.
+// grid (subdomain, problem): y = 0 Neumann, y = 1 Dirichlet (concurrent).
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(BDDC_THREADS)
-k_btchol(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict__ facD, T* __restrict__ scratch,
-         int* err) {
-  extern __shared__ __align__(128) unsigned char smraw[];
-  DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
-  const SubDesc s = subs[blockIdx.x];
-  const int neumann = blockIdx.y == 0;   // y = 0: Neumann, y = 1: Dirichlet (concurrent)
-  const Grid g = grid_of(s, neumann);
-  if (g.gz == 0) return;
-  const int Q = g.gx * g.gy;
-  const long long QQ = (long long)Q * Q, SS = slot_stride(Q);
-  T* base = neumann ? facN + s.offN : facD + s.offD;
-  const int QN = (s.w[0] + 1) * (s.w[1] + 1);
-  T* W1 = scratch + s.offW + (neumann ? 0 : 2LL * QN * QN + 1024LL * ((max(QN, s.na) + 31) / 32));
-  T* W2 = W1 + QQ;
-  T* diag = W2 + QQ;
-  for (int k = 0; k < g.gz; ++k) {
-    T* slot = base + (long long)k * SS;
-    if (k > 0) {
-      T* mslot = base + (long long)(g.gz + k - 1) * SS;
-      const T* Lp = base + (long long)(k - 1) * SS;
-      // M_k = B_{k-1} Linv_{k-1}^T.  B couples a node only to the 3 x 3 nodes
-      // around it in the previous plane (the Q1 stencil), so row i of M_k is
-      // a combination of at most nine rows of Linv_{k-1}^T:
-      //   M_k[i][j] = sum_o B[i][i + off_o] Linv_{k-1}[j][i + off_o].
-      // (1) the nine diagonals of B into diag (free until the factorisation)
-      for (int e = threadIdx.x; e < 9 * Q; e += blockDim.x) {
-        const int o = e / Q, i = e % Q, dx = o % 3 - 1, dy = o / 3 - 1;
-        const int ix = i % g.gx + dx, iy = i / g.gx + dy;
-        diag[e] = (ix >= 0 && ix < g.gx && iy >= 0 && iy < g.gy) ? mslot[(long long)i * Q + i + dx + dy * g.gx]
-                                                                  : T(0);
-      }
-      // (2) W2 = Linv_{k-1}^T by 32 x 32 tiles through shared memory (tiles
-      // above the diagonal of Linv are zero and skipped; the product below
-      // never reads their transposes)
-      const int nt = (Q + 31) / 32;
-      for (int tb = 0; tb < nt * nt; ++tb) {
-        const int a0 = (tb / nt) * 32, b0 = (tb % nt) * 32;
-        if (b0 > a0) continue;
-        for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
-          const int r = idx >> 5, c = idx & 31;
-          sm.t0[r * TLD + c] = (a0 + r < Q && b0 + c < Q) ? Lp[(long long)(a0 + r) * Q + b0 + c] : T(0);
-        }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
-          const int r = idx >> 5, c = idx & 31;
-          if (b0 + r < Q && a0 + c < Q) W2[(long long)(b0 + r) * Q + a0 + c] = sm.t0[c * TLD + r];
-        }
-        __syncthreads();
-      }
-      // (3) rows of M_k (Linv^T[l][j] = 0 for j < l)
-      for (long long e = threadIdx.x; e < QQ; e += blockDim.x) {
-        const int i = (int)(e / Q), j = (int)(e % Q);
-        const int ix = i % g.gx, iy = i / g.gx;
+__host__ __device__ inline long long packed_size(int Q) { return (long long)Q * (Q + 1) / 2; }
+
+// Register-resident plane step for Q <= 16 R (FP32): thread (tr, tc) =
+// (t / 16, t % 16) holds the entries (tr + 16 a, tc + 16 b) of S_k in a[a][b]
+// (entries above the diagonal or past Q are carried along and never used), so
+// a pivot costs 2 R shared-memory reads of the pivot column and R^2 FMAs.
+// Tm: Q x Q shared memory for S_{k-1}^{-1} B_k^T.  Writes S_k^{-1} to slot.
+template <typename T, int R>
+__device__ void schur_plane_regs(int Q, int gx, int gy, int k, T* __restrict__ slot, const T* __restrict__ Sp,
+                                 const T* __restrict__ Bd, T* __restrict__ cb, T* __restrict__ rb,
+                                 T* __restrict__ Tm, int* err, int code) {
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  if (k > 0) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < Q; i += BDDC_THREADS / 32)
+      for (int j = lane; j < Q; j += 32) {
+        const int jx = j % gx, jy = j / gx;
         T acc = T(0);
 #pragma unroll
         for (int o = 0; o < 9; ++o) {
-          const int dx = o % 3 - 1, dy = o / 3 - 1, l = i + dx + dy * g.gx;
-          if (ix + dx >= 0 && ix + dx < g.gx && iy + dy >= 0 && iy + dy < g.gy && j >= l)
-            acc += diag[o * Q + i] * W2[(long long)l * Q + j];
+          const int dx = o % 3 - 1, dy = o / 3 - 1;
+          if (jx + dx >= 0 && jx + dx < gx && jy + dy >= 0 && jy + dy < gy)
+            acc += Sp[i * Q + j + dx + dy * gx] * Bd[o * Q + j];
         }
-        mslot[e] = acc;
+        Tm[i * Q + j] = acc;
+      }
+    __syncthreads();
+  }
+  T a[R][R];
+#pragma unroll
+  for (int ai = 0; ai < R; ++ai) {
+    const int i = tr + 16 * ai, ix = i % gx, iy = i / gx;
+#pragma unroll
+    for (int bj = 0; bj < R; ++bj) {
+      const int j = tc + 16 * bj;
+      T v = T(0);
+      if (i < Q && j <= i) {
+        v = slot[i * Q + j];
+        if (k > 0) {
+          T acc = T(0);
+#pragma unroll
+          for (int o = 0; o < 9; ++o) {
+            const int dx = o % 3 - 1, dy = o / 3 - 1;
+            if (ix + dx >= 0 && ix + dx < gx && iy + dy >= 0 && iy + dy < gy)
+              acc += Bd[o * Q + i] * Tm[(i + dx + dy * gx) * Q + j];
+          }
+          v -= acc;
+        }
+      }
+      a[ai][bj] = v;
+    }
+  }
+  if (tc == 0) {
+#pragma unroll
+    for (int ai = 0; ai < R; ++ai) {
+      const int i = tr + 16 * ai;
+      if (i < Q) cb[i] = a[ai][0];
+    }
+  }
+  if (threadIdx.x == 0) {
+    T d = a[0][0];
+    if (!(d > T(0))) { set_error(err, code, blockIdx.x); d = T(1); }
+    rb[0] = T(1) / d;
+  }
+  __syncthreads();
+  for (int p = 0; p < Q; ++p) {
+    const T* c = cb + (p & 1) * Q;
+    T* cn = cb + ((p + 1) & 1) * Q;
+    const T r = rb[p & 1];
+    T ci[R], cj[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int i = tr + 16 * t, j = tc + 16 * t;
+      ci[t] = (i < Q) ? c[i] * r : T(0);
+      cj[t] = (j < Q) ? c[j] : T(0);
+    }
+#pragma unroll
+    for (int ai = 0; ai < R; ++ai)
+#pragma unroll
+      for (int bj = 0; bj < R; ++bj) a[ai][bj] -= ci[ai] * cj[bj];
+    // row p: (p, j) <- c[j] / d, (p, p) <- -1/d;  column p: (i, p) <- c[i] / d
+    const int pa = p >> 4, pm = p & 15;
+    if (tr == pm) {
+#pragma unroll
+      for (int ai = 0; ai < R; ++ai)
+        if (ai == pa) {
+#pragma unroll
+          for (int bj = 0; bj < R; ++bj) a[ai][bj] = (tc + 16 * bj == p) ? -r : cj[bj] * r;
+        }
+    }
+    if (tc == pm) {
+#pragma unroll
+      for (int bj = 0; bj < R; ++bj)
+        if (bj == pa) {
+#pragma unroll
+          for (int ai = 0; ai < R; ++ai)
+            if (tr + 16 * ai != p) a[ai][bj] = ci[ai];
+        }
+    }
+    // publish column p + 1 and the reciprocal of its pivot
+    const int q = p + 1;
+    if (q < Q) {
+      const int qa = q >> 4, qm = q & 15;
+      if (tc == qm) {
+#pragma unroll
+        for (int bj = 0; bj < R; ++bj)
+          if (bj == qa) {
+#pragma unroll
+            for (int ai = 0; ai < R; ++ai) {
+              const int i = tr + 16 * ai;
+              if (i >= q && i < Q) cn[i] = a[ai][bj];
+              if (i == q) {
+                T d = a[ai][bj];
+                if (!(d > T(0))) { set_error(err, code, blockIdx.x); d = T(1); }
+                rb[q & 1] = T(1) / d;
+              }
+            }
+          }
+      }
+      if (tr == qm) {
+#pragma unroll
+        for (int ai = 0; ai < R; ++ai)
+          if (ai == qa) {
+#pragma unroll
+            for (int bj = 0; bj < R; ++bj) {
+              const int j = tc + 16 * bj;
+              if (j < q) cn[j] = a[ai][bj];
+            }
+          }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int ai = 0; ai < R; ++ai) {
+    const int i = tr + 16 * ai;
+#pragma unroll
+    for (int bj = 0; bj < R; ++bj) {
+      const int j = tc + 16 * bj;
+      if (i < Q && j <= i) {
+        slot[i * Q + j] = -a[ai][bj];
+        slot[j * Q + i] = -a[ai][bj];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict__ facD, T* __restrict__ scratch,
+          long long smem_cap, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const SubDesc s = subs[blockIdx.x];
+  const int neumann = blockIdx.y == 0;
+  const Grid g = grid_of(s, neumann);
+  if (g.gz == 0) return;
+  const int Q = g.gx * g.gy, gx = g.gx, gy = g.gy;
+  const long long SS = slot_stride(Q), QQ = (long long)Q * Q;
+  T* base = neumann ? facN + s.offN : facD + s.offD;
+  const int QN = (s.w[0] + 1) * (s.w[1] + 1);
+  T* Tm = scratch + s.offW + (neumann ? 0 : 2LL * QN * QN + 1024LL * ((max(QN, s.na) + 31) / 32));
+  T* cb = reinterpret_cast<T*>(smraw);     // pivot columns, 2 x Q
+  T* rb = cb + 2 * Q;                      // reciprocals of the pivots, 2
+  T* A = (packed_size(Q) <= smem_cap) ? rb + 2 : Tm + QQ;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  constexpr int RREG = 11;   // register path: FP32 planes of up to 176 nodes
+  const bool regs = std::is_same<T, float>::value && Q <= 16 * RREG && (long long)Q * Q <= smem_cap;
+  for (int k = 0; k < g.gz; ++k) {
+    T* slot = base + (long long)k * SS;
+    if (regs) {
+      if constexpr (std::is_same<T, float>::value)
+        schur_plane_regs<T, RREG>(Q, gx, gy, k, slot, k > 0 ? base + (long long)(k - 1) * SS : nullptr,
+                                  k > 0 ? base + (long long)(g.gz + k - 1) * SS : nullptr, cb, rb, rb + 2,
+                                  err, neumann ? 3 : 2);
+      continue;
+    }
+    if (k > 0) {
+      const T* Sp = base + (long long)(k - 1) * SS;       // S_{k-1}^{-1}, full
+      const T* Bd = base + (long long)(g.gz + k - 1) * SS;
+      // T = S_{k-1}^{-1} B_k^T:  T[i][j] = sum_o Sp[i][j + off_o] Bd[o][j]
+      for (long long e = threadIdx.x; e < QQ; e += blockDim.x) {
+        const int i = (int)(e / Q), j = (int)(e % Q), jx = j % gx, jy = j / gx;
+        T acc = T(0);
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+          const int dx = o % 3 - 1, dy = o / 3 - 1;
+          if (jx + dx >= 0 && jx + dx < gx && jy + dy >= 0 && jy + dy < gy)
+            acc += Sp[(long long)i * Q + j + dx + dy * gx] * Bd[o * Q + j];
+        }
+        Tm[e] = acc;
       }
       __syncthreads();
-      // S_k = D_k - M_k M_k^T (lower part)
-      cta_gemm<T>(Q, Q, Q, T(-1), mslot, Q, false, mslot, Q, true, T(1), slot, Q, 0, 0, true, sm);
+      // S_k = D_k - B_k T (lower triangle, packed)
+      for (int i = tr; i < Q; i += 16) {
+        const int ix = i % gx, iy = i / gx;
+        const long long ro = (long long)i * (i + 1) / 2;
+        for (int j = tc; j <= i; j += 16) {
+          T acc = T(0);
+#pragma unroll
+          for (int o = 0; o < 9; ++o) {
+            const int dx = o % 3 - 1, dy = o / 3 - 1;
+            if (ix + dx >= 0 && ix + dx < gx && iy + dy >= 0 && iy + dy < gy)
+              acc += Bd[o * Q + i] * Tm[(long long)(i + dx + dy * gx) * Q + j];
+          }
+          A[ro + j] = slot[(long long)i * Q + j] - acc;
+        }
+      }
+    } else {
+      for (int i = tr; i < Q; i += 16) {
+        const long long ro = (long long)i * (i + 1) / 2;
+        for (int j = tc; j <= i; j += 16) A[ro + j] = slot[(long long)i * Q + j];
+      }
     }
-    for (long long e = threadIdx.x; e < QQ; e += blockDim.x) W1[e] = slot[e];
     __syncthreads();
-    bool ok = cta_chol_inv<T>(W1, Q, slot, Q, Q, diag, sm);
-    if (!ok && threadIdx.x == 0) set_error(err, neumann ? 3 : 2, blockIdx.x);
+    // first pivot column and reciprocal
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) cb[i] = A[(long long)i * (i + 1) / 2];
+    if (threadIdx.x == 0) {
+      T d = A[0];
+      if (!(d > T(0))) { set_error(err, neumann ? 3 : 2, blockIdx.x); d = T(1); }
+      rb[0] = T(1) / d;
+    }
+    __syncthreads();
+    for (int p = 0; p < Q; ++p) {
+      const T* c = cb + (p & 1) * Q;
+      T* cn = cb + ((p + 1) & 1) * Q;
+      const T r = rb[p & 1];
+      const int q = p + 1;
+      for (int i = tr; i < Q; i += 16) {
+        const T ci = c[i], cir = ci * r;
+        const long long ro = (long long)i * (i + 1) / 2;
+        for (int j = tc; j <= i; j += 16) {
+          T v;
+          if (i == p) v = (j == p) ? -r : c[j] * r;
+          else if (j == p) v = cir;
+          else v = A[ro + j] - cir * c[j];
+          A[ro + j] = v;
+          if (j == q && i >= q) {
+            cn[i] = v;
+            if (i == q) {
+              T d = v;
+              if (!(d > T(0))) { set_error(err, neumann ? 3 : 2, blockIdx.x); d = T(1); }
+              rb[q & 1] = T(1) / d;
+            }
+          } else if (i == q && j < q) {
+            cn[j] = v;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // slot k <- S_k^{-1} = -A, both triangles
+    for (int i = tr; i < Q; i += 16) {
+      const long long ro = (long long)i * (i + 1) / 2;
+      for (int j = tc; j <= i; j += 16) {
+        const T v = -A[ro + j];
+        slot[(long long)i * Q + j] = v;
+        slot[(long long)j * Q + i] = v;
+      }
+    }
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// multi-RHS sweeps: Y <- A_rr^{-1} Y with the Neumann factor (Y: nN x nc,
+// multi-RHS solves: Y <- A_rr^{-1} Y with the Neumann factor (Y: nN x nc,
 // row-major, ld nc).  grid: (subdomain, column chunk of CW columns).
+//   forward  k = 1..nz-1:  Y_k -= B_k (S_{k-1}^{-1} Y_{k-1})
+//   backward k = nz-1..0:  Y_k <- S_k^{-1} (Y_k - B_{k+1}^T Y_{k+1})
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(BDDC_THREADS)
@@ -221,28 +434,52 @@ k_btsolve_multi(const SubDesc* __restrict__ subs, const T* __restrict__ fac, T* 
   if (c0 >= s.nc) return;
   const int cw = min(CW, s.nc - c0);
   const Grid g = grid_of(s, 1);
-  const int Q = g.gx * g.gy, nz = g.gz, ld = s.nc;
-  const long long QQ = slot_stride(Q);
+  const int Q = g.gx * g.gy, nz = g.gz, ld = s.nc, gx = g.gx, gy = g.gy;
+  const long long SS = slot_stride(Q);
   const T* base = fac + s.offN;
   T* Yb = Y + s.offY + c0;
-  T* W = scratch + ((long long)blockIdx.x * gridDim.y + blockIdx.y) * scratch_stride;
-  for (int k = 0; k < nz; ++k) {
+  T* U = scratch + ((long long)blockIdx.x * gridDim.y + blockIdx.y) * scratch_stride;   // Q x cw
+  for (int k = 1; k < nz; ++k) {
     T* Yk = Yb + (long long)k * Q * ld;
-    if (k > 0)
-      cta_gemm<T>(Q, cw, Q, T(-1), base + (long long)(nz + k - 1) * QQ, Q, false,
-                  Yk - (long long)Q * ld, ld, false, T(1), Yk, ld, 0, 0, false, sm);
-    for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) W[e] = Yk[(long long)(e / cw) * ld + e % cw];
+    cta_gemm<T>(Q, cw, Q, T(1), base + (long long)(k - 1) * SS, Q, false, Yk - (long long)Q * ld, ld, false, T(0),
+                U, cw, 0, 0, false, sm);
+    const T* Bd = base + (long long)(nz + k - 1) * SS;
+    for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) {
+      const int i = e / cw, c = e % cw, ix = i % gx, iy = i / gx;
+      T acc = T(0);
+#pragma unroll
+      for (int o = 0; o < 9; ++o) {
+        const int dx = o % 3 - 1, dy = o / 3 - 1;
+        if (ix + dx >= 0 && ix + dx < gx && iy + dy >= 0 && iy + dy < gy)
+          acc += Bd[o * Q + i] * U[(i + dx + dy * gx) * cw + c];
+      }
+      Yk[(long long)i * ld + c] -= acc;
+    }
     __syncthreads();
-    cta_gemm<T>(Q, cw, Q, T(1), base + (long long)k * QQ, Q, false, W, cw, false, T(0), Yk, ld, 1, 0, false, sm);
   }
   for (int k = nz - 1; k >= 0; --k) {
     T* Yk = Yb + (long long)k * Q * ld;
-    if (k < nz - 1)
-      cta_gemm<T>(Q, cw, Q, T(-1), base + (long long)(nz + k) * QQ, Q, true,
-                  Yk + (long long)Q * ld, ld, false, T(1), Yk, ld, 0, 0, false, sm);
-    for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) W[e] = Yk[(long long)(e / cw) * ld + e % cw];
+    if (k == nz - 1) {
+      for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) U[e] = Yk[(long long)(e / cw) * ld + e % cw];
+    } else {
+      const T* Bd = base + (long long)(nz + k) * SS;       // B_{k+1}
+      const T* Yn = Yk + (long long)Q * ld;
+      for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) {
+        const int l = e / cw, c = e % cw, lx = l % gx, ly = l / gx;
+        T acc = T(0);
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+          const int dx = o % 3 - 1, dy = o / 3 - 1;
+          if (lx - dx >= 0 && lx - dx < gx && ly - dy >= 0 && ly - dy < gy) {
+            const int i = l - dx - dy * gx;
+            acc += Bd[o * Q + i] * Yn[(long long)i * ld + c];
+          }
+        }
+        U[e] = Yk[(long long)l * ld + c] - acc;
+      }
+    }
     __syncthreads();
-    cta_gemm<T>(Q, cw, Q, T(1), base + (long long)k * QQ, Q, true, W, cw, false, T(0), Yk, ld, 2, 0, false, sm);
+    cta_gemm<T>(Q, cw, Q, T(1), base + (long long)k * SS, Q, false, U, cw, false, T(0), Yk, ld, 0, 0, false, sm);
   }
 }
 
@@ -477,31 +714,20 @@ __global__ void k_piece_alpha(MeshDev m, const double* __restrict__ alpha, const
 }
 
 // ---------------------------------------------------------------------------
-// transposed copies (setup): every streamed matrix is kept in both
-// orientations so that each product of the apply is a column accumulation.
-// mode 0/1: the Dirichlet / Neumann plane-block slots; mode 2: Phi (nB x nc).
-// grid: (subdomain, matrix, 32x32 tile)
+// transposed copy of Phi (nB x nc -> nc x nB) for the apply's column
+// accumulations.  grid: (subdomain, 1, 32x32 tile stride)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_transpose(const SubDesc* __restrict__ subs, const T* __restrict__ src, T* __restrict__ dst,
-                            int mode) {
+__global__ void k_transpose(const SubDesc* __restrict__ subs, const T* __restrict__ src, T* __restrict__ dst) {
   __shared__ T tile[32][33];
   const SubDesc s = subs[blockIdx.x];
-  int rows, cols, nmat;
-  long long base, stride;
-  if (mode == 2) {
-    rows = s.nB; cols = s.nc; nmat = 1; base = s.offPhi; stride = 0;
-  } else {
-    const Grid g = grid_of(s, mode);
-    if (g.gz == 0) return;
-    rows = cols = g.gx * g.gy; nmat = 2 * g.gz - 1; base = mode ? s.offN : s.offD; stride = slot_stride(rows);
-  }
-  if ((int)blockIdx.y >= nmat || rows == 0 || cols == 0) return;
+  const int rows = s.nB, cols = s.nc;
+  if (rows == 0 || cols == 0) return;
   const int tc = (cols + 31) / 32, tr = (rows + 31) / 32;
+  const T* A = src + s.offPhi;
+  T* B = dst + s.offPhi;
   for (int t = blockIdx.z; t < tr * tc; t += gridDim.z) {
     const int r0 = (t / tc) * 32, c0 = (t % tc) * 32;
-    const T* A = src + base + blockIdx.y * stride;
-    T* B = dst + base + blockIdx.y * stride;
     for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
       int r = e / 32, c = e % 32;
       if (r0 + r < rows && c0 + c < cols) tile[r][c] = A[(long long)(r0 + r) * cols + c0 + c];
@@ -579,67 +805,77 @@ __device__ inline void col_finish(const ColLayout& L, A acc[4], A* part, Out out
 }
 
 // ---------------------------------------------------------------------------
-// single-RHS sweeps (apply).  v <- A^{-1} v for a plane-block factor:
-//   forward  (k = 0..nz-1):  t = v_k - M_k v_{k-1};  v_k = Linv_k t
-//   backward (k = nz-1..0):  t = v_k - M_{k+1}^T v_{k+1};  v_k = Linv_k^T t
-// The forward products read the transposed slots (facT), the backward ones
-// the slots themselves (fac); both stream row chunks through the ring and
-// accumulate columns.  v (nz*Q), t (Q), part (blockDim) in shared memory.
+// single-RHS solve (apply): v <- A^{-1} v with the inverse Schur complements
+//   forward  k = 1..nz-1:  t = S_{k-1}^{-1} v_{k-1};  v_k -= B_k t
+//   backward k = nz-1..0:  v_k <- S_k^{-1} (v_k - B_{k+1}^T v_{k+1})
+// The 2 nz - 1 symmetric slots stream through the ring in that order and
+// their products are column accumulations (S^{-1} is symmetric, so rows are
+// columns); the nine-diagonal B_k and B_{k+1}^T products run between them.
+// v (nz*Q), t (Q), part (blockDim) in shared memory.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, const T* __restrict__ facT, int Q, int nz, T* v,
-                             T* t, T* part, int* err) {
+__device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int gy, int nz, T* v, T* t, T* part,
+                             int* err) {
+  const int Q = gx * gy;
   const int R = rows_per_chunk(Q, (int)sizeof(T));
   const int nch = (Q + R - 1) / R;
-  const int nfwd = 2 * nz - 1;
+  const int ngr = 2 * nz - 1;
   const long long SS = slot_stride(Q);
-  for (int i = threadIdx.x; i < Q; i += blockDim.x) t[i] = v[i];
-  __syncthreads();
-  auto decode = [&](int bi, int& kind, int& k, int& slot) {
-    if (bi < nfwd) {
-      if (bi == 0) { kind = 0; k = 0; }
-      else if (bi & 1) { kind = 1; k = (bi + 1) / 2; }
-      else { kind = 0; k = bi / 2; }
-    } else {
-      int q = bi - nfwd;
-      if (q == 0) { kind = 2; k = nz - 1; }
-      else if (q & 1) { kind = 3; k = nz - (q + 1) / 2; }    // M_k, target plane k-1
-      else { kind = 2; k = nz - 1 - q / 2; }
-    }
-    slot = (kind == 0 || kind == 2) ? k : nz + k - 1;
-  };
+  // group bi: forward slot bi (bi < nz - 1) or backward slot nz - 1 - (bi - nz + 1)
+  auto slot_of = [&](int bi) { return bi < nz - 1 ? bi : 2 * nz - 2 - bi; };
   const ColLayout L = col_layout(Q);
   T acc[4] = {T(0), T(0), T(0), T(0)};
   auto src = [&](int c, const void*& p, unsigned& bytes) {
-    int kind, k, slot;
-    decode(c / nch, kind, k, slot);
     const int r0 = (c % nch) * R, nr = min(R, Q - r0);
-    p = ((kind < 2) ? facT : fac) + slot * SS + (long long)r0 * Q;
+    p = fac + slot_of(c / nch) * SS + (long long)r0 * Q;
     bytes = (unsigned)(nr * Q * sizeof(T));
   };
   auto use = [&](int c, const unsigned char* raw) {
-    int kind, k, slot;
-    const int lc = c % nch;
-    decode(c / nch, kind, k, slot);
+    const int bi = c / nch, lc = c % nch, k = slot_of(bi);
+    const bool fwd = bi < nz - 1;
     const int r0 = lc * R, nr = min(R, Q - r0);
-    const T* in;
-    if (kind == 0) in = t;
-    else if (kind == 1) in = v + (long long)(k - 1) * Q;
-    else if (kind == 2) in = (k == nz - 1) ? v + (long long)k * Q : t;
-    else in = v + (long long)k * Q;
+    const T* in = (fwd || bi == nz - 1) ? v + (long long)k * Q : t;
     col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, in + r0, acc);
-    if (lc == nch - 1) {
-      __syncthreads();   // every row of the block is consumed before outputs overwrite inputs
-      if (kind == 0 || kind == 2) {
-        T* dst = v + (long long)k * Q;
-        col_finish<T>(L, acc, part, [&](int cc, T s) { dst[cc] = s; });
-      } else {
-        const T* base = v + (long long)((kind == 1) ? k : k - 1) * Q;
-        col_finish<T>(L, acc, part, [&](int cc, T s) { t[cc] = base[cc] - s; });
+    if (lc != nch - 1) return;
+    __syncthreads();   // every row of the slot is consumed before outputs overwrite inputs
+    T* dst = fwd ? t : v + (long long)k * Q;
+    col_finish<T>(L, acc, part, [&](int cc, T sum) { dst[cc] = sum; });
+    __syncthreads();
+    if (fwd) {
+      // v_{k+1} -= B_{k+1} t
+      const T* Bd = fac + (long long)(nz + k) * SS;
+      T* vn = v + (long long)(k + 1) * Q;
+      for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+        const int ix = i % gx, iy = i / gx;
+        T a = T(0);
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+          const int dx = o % 3 - 1, dy = o / 3 - 1;
+          if (ix + dx >= 0 && ix + dx < gx && iy + dy >= 0 && iy + dy < gy) a += Bd[o * Q + i] * t[i + dx + dy * gx];
+        }
+        vn[i] -= a;
+      }
+    } else if (k > 0) {
+      // t = v_{k-1} - B_k^T v_k
+      const T* Bd = fac + (long long)(nz + k - 1) * SS;
+      const T* vk = v + (long long)k * Q;
+      const T* vp = v + (long long)(k - 1) * Q;
+      for (int l = threadIdx.x; l < Q; l += blockDim.x) {
+        const int lx = l % gx, ly = l / gx;
+        T a = T(0);
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+          const int dx = o % 3 - 1, dy = o / 3 - 1;
+          if (lx - dx >= 0 && lx - dx < gx && ly - dy >= 0 && ly - dy < gy) {
+            const int i = l - dx - dy * gx;
+            a += Bd[o * Q + i] * vk[i];
+          }
+        }
+        t[l] = vp[l] - a;
       }
     }
   };
-  ring_run(ring, 2 * nfwd * nch, src, use, err);
+  ring_run(ring, ngr * nch, src, use, err);
 }
 
 __host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 8 * NBUF; }
@@ -649,8 +885,8 @@ __host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 8 *
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
-                  const T* __restrict__ facT, const double* __restrict__ r, const double* __restrict__ t,
-                  double* __restrict__ z, int mode, int* err) {
+                  const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ z, int mode,
+                  int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   const SubDesc s = subs[blockIdx.x];
   const Grid g = grid_of(s, 0);
@@ -669,7 +905,7 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
     v[l] = (T)val;
   }
   __syncthreads();
-  sweep_stream<T>(ring, fac + s.offD, facT + s.offD, Q, g.gz, v, tq, part, err);
+  sweep_stream<T>(ring, fac + s.offD, g.gx, g.gy, g.gz, v, tq, part, err);
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
     long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
@@ -682,8 +918,7 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
 // y = A_rr^{-1} r_i,r (into vloc).
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
-k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac, const T* __restrict__ facT,
-                const T* __restrict__ Phi, const double* __restrict__ delta,
+k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac, const T* __restrict__ Phi, const double* __restrict__ delta,
                 const double* __restrict__ r, const double* __restrict__ t, T* __restrict__ vloc,
                 double* __restrict__ rcl, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -728,7 +963,7 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
     ring_run(ring, nch, src, use, err);
     col_finish<T>(L, acc, part, [&](int cc, T sum) { rcl[s.cofs + cc] = (double)sum; });
   }
-  sweep_stream<T>(ring, fac + s.offN, facT + s.offN, Q, pz, v, tq, part, err);
+  sweep_stream<T>(ring, fac + s.offN, px, py, pz, v, tq, part, err);
   for (int l = threadIdx.x; l < n; l += blockDim.x) vloc[s.offVec + l] = v[l];
 }
 
@@ -804,12 +1039,13 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
   k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1);
   BDDC_COUNT(1);
   if (ev) cudaEventRecord(ev[0], st);
-  // both factorisations in one launch: y = 0 Neumann, y = 1 Dirichlet
-  k_btchol<T><<<dim3(S, L.maxQD > 0 ? 2 : 1), BDDC_THREADS, sm, st>>>(L.subs, facN, facD, W, L.err);
-  k_transpose<T><<<dim3(S, 2 * L.maxNzN - 1, 32), 256, 0, st>>>(L.subs, facN, (T*)L.facNT, 1);
-  BDDC_COUNT(2);
-  if (L.maxQD > 0) {
-    k_transpose<T><<<dim3(S, 2 * L.maxNzD - 1, 32), 256, 0, st>>>(L.subs, facD, (T*)L.facDT, 0);
+  // both factorisations in one launch: y = 0 Neumann, y = 1 Dirichlet; the
+  // packed Schur matrix takes the shared memory left after the pivot columns
+  {
+    const int maxQ = std::max(L.maxQN, L.maxQD);
+    const size_t smb = 227 * 1024;
+    const long long cap = (long long)(smb / sizeof(T)) - 2LL * maxQ - 2;
+    k_btschur<T><<<dim3(S, L.maxQD > 0 ? 2 : 1), BDDC_THREADS, smb, st>>>(L.subs, facN, facD, W, cap, L.err);
     BDDC_COUNT(1);
   }
   if (ev) cudaEventRecord(ev[1], st);
@@ -826,7 +1062,7 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
     k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 0);
     k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 1);
     k_phi_surface<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, PA, Phi);
-    k_transpose<T><<<dim3(S, 1, 64), 256, 0, st>>>(L.subs, Phi, (T*)L.PhiT, 2);
+    k_transpose<T><<<dim3(S, 1, 64), 256, 0, st>>>(L.subs, Phi, (T*)L.PhiT);
     k_local_coarse_matrix<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y, Lv, Sc, L.Ac);
     BDDC_COUNT(9);
   }
@@ -836,7 +1072,7 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
 template <typename T>
 void configure_local_kernels() {
   size_t sm = dense_smem<T>();
-  cudaFuncSetAttribute(k_btchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_btschur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_btsolve_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_phi_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -863,16 +1099,15 @@ void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, do
   if (L.maxQD == 0) return;
   BDDC_COUNT(1);
   size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxND + L.maxQD + 2);
-  k_dirichlet_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facD, (const T*)L.facDT, r, t,
-                                                         z, mode, L.err);
+  k_dirichlet_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facD, r, t, z, mode, L.err);
 }
 
 template <typename T>
 void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
   size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNB + 1 + L.maxNN + L.maxQN + 2);
   BDDC_COUNT(1);
-  k_neumann_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facN, (const T*)L.facNT,
-                                                       (const T*)L.Phi, L.delta, r, t, (T*)L.vloc, L.rcl, L.err);
+  k_neumann_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta, r,
+                                                       t, (T*)L.vloc, L.rcl, L.err);
 }
 
 template <typename T>
