@@ -147,30 +147,34 @@ __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const do
 //   A[i][j] -= A[i][p] A[j][p] / d   (i, j != p),
 //   A[i][p] <- A[i][p] / d,   A[p][p] <- -1 / d,
 // which leaves -S^{-1} after all Q pivots.  The packed lower triangle lives in
-// shared memory when it fits (else in the scratch, L2-resident); thread t
-// owns the entries with i = t/16 (mod 16) and j = t (mod 16).  One barrier per
+// shared memory when it fits (else in the scratch, L2-resident).  One barrier per
 // pivot: the pivot column is double-buffered and the threads owning column
 // p + 1 publish it, and the reciprocal of the next pivot, as they update it.
+// 512 threads; thread t owns the entries with i = t/16 (mod 32) and
+// j = t (mod 16).
 // grid (subdomain, problem): y = 0 Neumann, y = 1 Dirichlet (concurrent).
 // ---------------------------------------------------------------------------
 __host__ __device__ inline long long packed_size(int Q) { return (long long)Q * (Q + 1) / 2; }
 
-// Register-resident plane step for Q <= 16 R (FP32): thread (tr, tc) =
-// (t / 16, t % 16) holds the entries (tr + 16 a, tc + 16 b) of S_k in a[a][b]
-// (entries above the diagonal or past Q are carried along and never used), so
-// a pivot costs 2 R shared-memory reads of the pivot column and R^2 FMAs.
-// Tm: Q x Q shared memory for S_{k-1}^{-1} B_k^T.  Writes S_k^{-1} to slot.
-template <typename T, int R>
-__device__ void schur_plane_regs(int Q, int gx, int gy, int k, T* __restrict__ slot, const T* __restrict__ Sp,
-                                 const T* __restrict__ Bd, T* __restrict__ cb, T* __restrict__ rb,
-                                 T* __restrict__ Tm, int* err, int code) {
+constexpr int SCHUR_THREADS = 512;   // 32 x 16 owner grid
+
+// Register-resident plane step for Q <= 32 RI and Q <= 16 RJ (FP32): thread
+// (tr, tc) = (t / 16, t % 16) holds the entries (tr + 32 a, tc + 16 b) of S_k
+// in x[a][b] (entries above the diagonal or past Q are carried along and never
+// used), so a pivot costs RI + RJ shared-memory reads of the pivot column and
+// RI RJ FMAs per thread.  Tm: Q x Q shared memory for S_{k-1}^{-1} B_k^T.
+// Writes S_k^{-1} to slot.
+template <int RI, int RJ>
+__device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict__ slot,
+                                 const float* __restrict__ Sp, const float* __restrict__ Bd, float* __restrict__ cb,
+                                 float* __restrict__ rb, float* __restrict__ Tm, int* err, int code) {
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
   if (k > 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < Q; i += BDDC_THREADS / 32)
+    for (int i = warp; i < Q; i += SCHUR_THREADS / 32)
       for (int j = lane; j < Q; j += 32) {
         const int jx = j % gx, jy = j / gx;
-        T acc = T(0);
+        float acc = 0.0f;
 #pragma unroll
         for (int o = 0; o < 9; ++o) {
           const int dx = o % 3 - 1, dy = o / 3 - 1;
@@ -181,18 +185,18 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, T* __restrict__ s
       }
     __syncthreads();
   }
-  T a[R][R];
+  float x[RI][RJ];
 #pragma unroll
-  for (int ai = 0; ai < R; ++ai) {
-    const int i = tr + 16 * ai, ix = i % gx, iy = i / gx;
+  for (int ai = 0; ai < RI; ++ai) {
+    const int i = tr + 32 * ai, ix = i % gx, iy = i / gx;
 #pragma unroll
-    for (int bj = 0; bj < R; ++bj) {
+    for (int bj = 0; bj < RJ; ++bj) {
       const int j = tc + 16 * bj;
-      T v = T(0);
+      float v = 0.0f;
       if (i < Q && j <= i) {
         v = slot[i * Q + j];
         if (k > 0) {
-          T acc = T(0);
+          float acc = 0.0f;
 #pragma unroll
           for (int o = 0; o < 9; ++o) {
             const int dx = o % 3 - 1, dy = o / 3 - 1;
@@ -202,84 +206,86 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, T* __restrict__ s
           v -= acc;
         }
       }
-      a[ai][bj] = v;
+      x[ai][bj] = v;
     }
   }
+  auto publish_pivot = [&](int q, float d) {
+    if (!(d > 0.0f)) { set_error(err, code, blockIdx.x); d = 1.0f; }
+    rb[q & 1] = __frcp_rn(d);
+  };
   if (tc == 0) {
 #pragma unroll
-    for (int ai = 0; ai < R; ++ai) {
-      const int i = tr + 16 * ai;
-      if (i < Q) cb[i] = a[ai][0];
+    for (int ai = 0; ai < RI; ++ai) {
+      const int i = tr + 32 * ai;
+      if (i < Q) cb[i] = x[ai][0];
     }
   }
-  if (threadIdx.x == 0) {
-    T d = a[0][0];
-    if (!(d > T(0))) { set_error(err, code, blockIdx.x); d = T(1); }
-    rb[0] = T(1) / d;
-  }
+  if (threadIdx.x == 0) publish_pivot(0, x[0][0]);
   __syncthreads();
   for (int p = 0; p < Q; ++p) {
-    const T* c = cb + (p & 1) * Q;
-    T* cn = cb + ((p + 1) & 1) * Q;
-    const T r = rb[p & 1];
-    T ci[R], cj[R];
+    const float* c = cb + (p & 1) * Q;
+    float* cn = cb + ((p + 1) & 1) * Q;
+    const float r = rb[p & 1];
+    float ci[RI], cj[RJ];
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      const int i = tr + 16 * t, j = tc + 16 * t;
-      ci[t] = (i < Q) ? c[i] * r : T(0);
-      cj[t] = (j < Q) ? c[j] : T(0);
+    for (int t = 0; t < RI; ++t) {
+      const int i = tr + 32 * t;
+      ci[t] = (i < Q) ? c[i] * r : 0.0f;
     }
 #pragma unroll
-    for (int ai = 0; ai < R; ++ai)
+    for (int t = 0; t < RJ; ++t) {
+      const int j = tc + 16 * t;
+      cj[t] = (j < Q) ? c[j] : 0.0f;
+    }
 #pragma unroll
-      for (int bj = 0; bj < R; ++bj) a[ai][bj] -= ci[ai] * cj[bj];
+    for (int ai = 0; ai < RI; ++ai)
+#pragma unroll
+      for (int bj = 0; bj < RJ; ++bj) x[ai][bj] -= ci[ai] * cj[bj];
     // row p: (p, j) <- c[j] / d, (p, p) <- -1/d;  column p: (i, p) <- c[i] / d
-    const int pa = p >> 4, pm = p & 15;
-    if (tr == pm) {
+    if (tr == (p & 31)) {
+      const int pa = p >> 5;
 #pragma unroll
-      for (int ai = 0; ai < R; ++ai)
+      for (int ai = 0; ai < RI; ++ai)
         if (ai == pa) {
 #pragma unroll
-          for (int bj = 0; bj < R; ++bj) a[ai][bj] = (tc + 16 * bj == p) ? -r : cj[bj] * r;
+          for (int bj = 0; bj < RJ; ++bj) x[ai][bj] = (tc + 16 * bj == p) ? -r : cj[bj] * r;
         }
     }
-    if (tc == pm) {
+    if (tc == (p & 15)) {
+      const int pb = p >> 4;
 #pragma unroll
-      for (int bj = 0; bj < R; ++bj)
-        if (bj == pa) {
+      for (int bj = 0; bj < RJ; ++bj)
+        if (bj == pb) {
 #pragma unroll
-          for (int ai = 0; ai < R; ++ai)
-            if (tr + 16 * ai != p) a[ai][bj] = ci[ai];
+          for (int ai = 0; ai < RI; ++ai)
+            if (tr + 32 * ai != p) x[ai][bj] = ci[ai];
         }
     }
     // publish column p + 1 and the reciprocal of its pivot
     const int q = p + 1;
     if (q < Q) {
-      const int qa = q >> 4, qm = q & 15;
-      if (tc == qm) {
+      if (tc == (q & 15)) {
+        const int qb = q >> 4;
 #pragma unroll
-        for (int bj = 0; bj < R; ++bj)
-          if (bj == qa) {
+        for (int bj = 0; bj < RJ; ++bj)
+          if (bj == qb) {
 #pragma unroll
-            for (int ai = 0; ai < R; ++ai) {
-              const int i = tr + 16 * ai;
-              if (i >= q && i < Q) cn[i] = a[ai][bj];
-              if (i == q) {
-                T d = a[ai][bj];
-                if (!(d > T(0))) { set_error(err, code, blockIdx.x); d = T(1); }
-                rb[q & 1] = T(1) / d;
-              }
+            for (int ai = 0; ai < RI; ++ai) {
+              const int i = tr + 32 * ai;
+              if (i >= q && i < Q) cn[i] = x[ai][bj];
+              if (i == q) publish_pivot(q, x[ai][bj]);
             }
           }
       }
-      if (tr == qm) {
+      if (tr == (q & 31)) {
+        const int qa = q >> 5;
 #pragma unroll
-        for (int ai = 0; ai < R; ++ai)
+        for (int ai = 0; ai < RI; ++ai)
           if (ai == qa) {
 #pragma unroll
-            for (int bj = 0; bj < R; ++bj) {
+            for (int bj = 0; bj < RJ; ++bj) {
               const int j = tc + 16 * bj;
-              if (j < q) cn[j] = a[ai][bj];
+              if (j < q) cn[j] = x[ai][bj];
             }
           }
       }
@@ -287,14 +293,14 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, T* __restrict__ s
     __syncthreads();
   }
 #pragma unroll
-  for (int ai = 0; ai < R; ++ai) {
-    const int i = tr + 16 * ai;
+  for (int ai = 0; ai < RI; ++ai) {
+    const int i = tr + 32 * ai;
 #pragma unroll
-    for (int bj = 0; bj < R; ++bj) {
+    for (int bj = 0; bj < RJ; ++bj) {
       const int j = tc + 16 * bj;
       if (i < Q && j <= i) {
-        slot[i * Q + j] = -a[ai][bj];
-        slot[j * Q + i] = -a[ai][bj];
+        slot[i * Q + j] = -x[ai][bj];
+        slot[j * Q + i] = -x[ai][bj];
       }
     }
   }
@@ -302,7 +308,7 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, T* __restrict__ s
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BDDC_THREADS)
+__global__ void __launch_bounds__(SCHUR_THREADS)
 k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict__ facD, T* __restrict__ scratch,
           long long smem_cap, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -318,16 +324,17 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
   T* cb = reinterpret_cast<T*>(smraw);     // pivot columns, 2 x Q
   T* rb = cb + 2 * Q;                      // reciprocals of the pivots, 2
   T* A = (packed_size(Q) <= smem_cap) ? rb + 2 : Tm + QQ;
-  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-  constexpr int RREG = 11;   // register path: FP32 planes of up to 176 nodes
-  const bool regs = std::is_same<T, float>::value && Q <= 16 * RREG && (long long)Q * Q <= smem_cap;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;   // 32 x 16 owner grid
+  // register path: FP32 planes of up to 176 nodes (6 x 11 entries per thread)
+  constexpr int RI = 6, RJ = 11;
+  const bool regs = std::is_same<T, float>::value && Q <= 32 * RI && Q <= 16 * RJ && (long long)Q * Q <= smem_cap;
   for (int k = 0; k < g.gz; ++k) {
     T* slot = base + (long long)k * SS;
     if (regs) {
       if constexpr (std::is_same<T, float>::value)
-        schur_plane_regs<T, RREG>(Q, gx, gy, k, slot, k > 0 ? base + (long long)(k - 1) * SS : nullptr,
-                                  k > 0 ? base + (long long)(g.gz + k - 1) * SS : nullptr, cb, rb, rb + 2,
-                                  err, neumann ? 3 : 2);
+        schur_plane_regs<RI, RJ>(Q, gx, gy, k, slot, k > 0 ? base + (long long)(k - 1) * SS : nullptr,
+                                 k > 0 ? base + (long long)(g.gz + k - 1) * SS : nullptr, cb, rb, rb + 2,
+                                 err, neumann ? 3 : 2);
       continue;
     }
     if (k > 0) {
@@ -347,7 +354,7 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
       }
       __syncthreads();
       // S_k = D_k - B_k T (lower triangle, packed)
-      for (int i = tr; i < Q; i += 16) {
+      for (int i = tr; i < Q; i += 32) {
         const int ix = i % gx, iy = i / gx;
         const long long ro = (long long)i * (i + 1) / 2;
         for (int j = tc; j <= i; j += 16) {
@@ -362,7 +369,7 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
         }
       }
     } else {
-      for (int i = tr; i < Q; i += 16) {
+      for (int i = tr; i < Q; i += 32) {
         const long long ro = (long long)i * (i + 1) / 2;
         for (int j = tc; j <= i; j += 16) A[ro + j] = slot[(long long)i * Q + j];
       }
@@ -381,7 +388,7 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
       T* cn = cb + ((p + 1) & 1) * Q;
       const T r = rb[p & 1];
       const int q = p + 1;
-      for (int i = tr; i < Q; i += 16) {
+      for (int i = tr; i < Q; i += 32) {
         const T ci = c[i], cir = ci * r;
         const long long ro = (long long)i * (i + 1) / 2;
         for (int j = tc; j <= i; j += 16) {
@@ -405,7 +412,7 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
       __syncthreads();
     }
     // slot k <- S_k^{-1} = -A, both triangles
-    for (int i = tr; i < Q; i += 16) {
+    for (int i = tr; i < Q; i += 32) {
       const long long ro = (long long)i * (i + 1) / 2;
       for (int j = tc; j <= i; j += 16) {
         const T v = -A[ro + j];
@@ -1045,7 +1052,7 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
     const int maxQ = std::max(L.maxQN, L.maxQD);
     const size_t smb = 227 * 1024;
     const long long cap = (long long)(smb / sizeof(T)) - 2LL * maxQ - 2;
-    k_btschur<T><<<dim3(S, L.maxQD > 0 ? 2 : 1), BDDC_THREADS, smb, st>>>(L.subs, facN, facD, W, cap, L.err);
+    k_btschur<T><<<dim3(S, L.maxQD > 0 ? 2 : 1), SCHUR_THREADS, smb, st>>>(L.subs, facN, facD, W, cap, L.err);
     BDDC_COUNT(1);
   }
   if (ev) cudaEventRecord(ev[1], st);
