@@ -361,17 +361,17 @@ def main():
     setup_ms = info["setup_ms"]
     solve_ms = statistics.mean(s["solve_ms"] for s in stats)
     # rooflines.  The largest single kernel of the step (launch list in
-    # profiles/) is the local factorisation k_btchol: FP32 multiply-adds of
-    # the plane-block Cholesky factorisations over the phase's event time.
+    # profiles/) is the local factorisation k_btschur: multiply-adds of the
+    # inverse Schur complements over the phase's event time.
     nc = info["n_coarse"]
     fac_ms = info["phase_ms"][2]
     fac_tflops = 2.0 * info["local_factor_fma"] / (fac_ms * 1e-3) / 1e12
     peak_local = FP32_PEAK_TFLOPS if args.precision == "mixed" else FP64_PEAK_TFLOPS
-    roofline = {"kernel": "k_btchol (local Dirichlet + Neumann plane-block Cholesky, one launch)",
+    roofline = {"kernel": "k_btschur (local Dirichlet + Neumann inverse Schur complements, one launch)",
                 "bound": "alu", "achieved": round(fac_tflops, 4), "peak": peak_local, "unit": "TFLOP/s",
-                "frac": round(fac_tflops / peak_local, 4), "traffic": TRAFFIC.get("k_btchol"),
+                "frac": round(fac_tflops / peak_local, 4), "traffic": TRAFFIC.get("k_btschur"),
                 "algorithmic": f"{2 * info['local_factor_fma']:.3e} flop per launch (sum over subdomains and "
-                               "planes of Q^3/3 + Q^3/2 + 9 Q^2 multiply-adds)",
+                               "planes of Q^3/2 + 18 Q^2 multiply-adds)",
                 "peak_source": ("FP32 derived from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
                                 if args.precision == "mixed" else "GB300 FP64 nominal 1.25 TFLOP/s")}
     chol_ms = info["phase_ms"][5]

@@ -486,10 +486,11 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
       const int QN = (s.w[0] + 1) * (s.w[1] + 1);
       if (rows_per_chunk(QN, es) < 1 || (s.nc > 0 && (rows_per_chunk(s.nc, es) < 1 || rows_per_chunk(s.nB, es) < 1)))
         rows_ok = false;
+      if ((size_t)9 * QN * es > (size_t)CHB) rows_ok = false;   // a coupling's diagonals stream as one chunk
     }
     if (!rows_ok || L.maxQN > 2048 || L.maxNB > 2048 || L.maxNc > 2048 || smem > 227 * 1024)
       throw BddcError(BDDC_ERR_UNSUPPORTED, "subdomains too large for the streamed local solves "
-                                            "(at most 1024 FP64 / 2048 FP32 nodes per plane and 1024 coarse DOFs)");
+                                            "(at most 341 FP64 / 682 FP32 nodes per plane and 1024 coarse DOFs)");
   }
   h->launch_base = g_launches;
   // events: 0 start, 1 weights done, 2 Dirichlet, 3 Neumann, 4 basis, 5 assembly, 6 coarse factor

@@ -826,31 +826,52 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
   const int Q = gx * gy;
   const int R = rows_per_chunk(Q, (int)sizeof(T));
   const int nch = (Q + R - 1) / R;
-  const int ngr = 2 * nz - 1;
+  const int ngs = nch + 1;                 // slot chunks plus the coupling's diagonals
+  const int nlead = 2 * (nz - 1);          // groups followed by a stencil step
   const long long SS = slot_stride(Q);
-  // group bi: forward slot bi (bi < nz - 1) or backward slot nz - 1 - (bi - nz + 1)
+  // group bi: forward slot bi (bi < nz - 1) or backward slot 2 nz - 2 - bi;
+  // every group but the last (backward k = 0) ends with the diagonals of
+  // B_{bi+1} (forward) or B_k (backward), streamed like the slot rows
   auto slot_of = [&](int bi) { return bi < nz - 1 ? bi : 2 * nz - 2 - bi; };
+  auto locate = [&](int c, int& bi, int& lc) {
+    if (c < nlead * ngs) { bi = c / ngs; lc = c % ngs; }
+    else { bi = nlead; lc = c - nlead * ngs; }
+  };
   const ColLayout L = col_layout(Q);
   T acc[4] = {T(0), T(0), T(0), T(0)};
   auto src = [&](int c, const void*& p, unsigned& bytes) {
-    const int r0 = (c % nch) * R, nr = min(R, Q - r0);
-    p = fac + slot_of(c / nch) * SS + (long long)r0 * Q;
-    bytes = (unsigned)(nr * Q * sizeof(T));
+    int bi, lc;
+    locate(c, bi, lc);
+    const int k = slot_of(bi);
+    if (lc == nch) {
+      const int kb = bi < nz - 1 ? k + 1 : k;       // coupling of the stencil step
+      p = fac + (long long)(nz + kb - 1) * SS;
+      bytes = (unsigned)(9 * Q * sizeof(T));
+    } else {
+      const int r0 = lc * R, nr = min(R, Q - r0);
+      p = fac + k * SS + (long long)r0 * Q;
+      bytes = (unsigned)(nr * Q * sizeof(T));
+    }
   };
   auto use = [&](int c, const unsigned char* raw) {
-    const int bi = c / nch, lc = c % nch, k = slot_of(bi);
+    int bi, lc;
+    locate(c, bi, lc);
+    const int k = slot_of(bi);
     const bool fwd = bi < nz - 1;
-    const int r0 = lc * R, nr = min(R, Q - r0);
-    const T* in = (fwd || bi == nz - 1) ? v + (long long)k * Q : t;
-    col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, in + r0, acc);
-    if (lc != nch - 1) return;
-    __syncthreads();   // every row of the slot is consumed before outputs overwrite inputs
-    T* dst = fwd ? t : v + (long long)k * Q;
-    col_finish<T>(L, acc, part, [&](int cc, T sum) { dst[cc] = sum; });
-    __syncthreads();
+    if (lc < nch) {
+      const int r0 = lc * R, nr = min(R, Q - r0);
+      const T* in = (fwd || bi == nz - 1) ? v + (long long)k * Q : t;
+      col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, in + r0, acc);
+      if (lc == nch - 1) {
+        __syncthreads();   // every row of the slot is consumed before outputs overwrite inputs
+        T* dst = fwd ? t : v + (long long)k * Q;
+        col_finish<T>(L, acc, part, [&](int cc, T sum) { dst[cc] = sum; });
+      }
+      return;
+    }
+    const T* Bd = reinterpret_cast<const T*>(raw);
     if (fwd) {
       // v_{k+1} -= B_{k+1} t
-      const T* Bd = fac + (long long)(nz + k) * SS;
       T* vn = v + (long long)(k + 1) * Q;
       for (int i = threadIdx.x; i < Q; i += blockDim.x) {
         const int ix = i % gx, iy = i / gx;
@@ -862,9 +883,8 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
         }
         vn[i] -= a;
       }
-    } else if (k > 0) {
+    } else {
       // t = v_{k-1} - B_k^T v_k
-      const T* Bd = fac + (long long)(nz + k - 1) * SS;
       const T* vk = v + (long long)k * Q;
       const T* vp = v + (long long)(k - 1) * Q;
       for (int l = threadIdx.x; l < Q; l += blockDim.x) {
@@ -882,7 +902,7 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
       }
     }
   };
-  ring_run(ring, ngr * nch, src, use, err);
+  ring_run(ring, nlead * ngs + nch, src, use, err);
 }
 
 __host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 8 * NBUF; }
