@@ -315,7 +315,7 @@ void build_metadata(bddc_handle* h) {
   std::vector<int2> own_e;
   std::vector<LocalCoarse> verts, avgs;
   long long offD = 0, offN = 0, offW = 0, offY = 0, offG = 0, offL = 0, offPA = 0, offSc = 0, offAc = 0, offPhi = 0,
-            offB = 0, offVec = 0;
+            offB = 0, offVec = 0, offTC = 0;
   LocalLaunch& L = h->L;
   L.maxQD = L.maxNzD = L.maxND = L.maxQN = L.maxNzN = L.maxNN = L.maxNB = L.maxNc = 0;
   for (int sz = 0; sz < nsub[2]; ++sz)
@@ -382,13 +382,16 @@ void build_metadata(bddc_handle* h) {
         s.offPhi = offPhi; offPhi += padded((long long)s.nB * s.nc);
         s.offB = offB; offB += s.nB;
         s.offVec = offVec; offVec += NN;
+        s.offTC = offTC; offTC += (long long)pz * tc_kchunks(QN) * tc_chunk_floats(QN);
         L.maxQD = std::max(L.maxQD, QD); L.maxNzD = std::max(L.maxNzD, nzD); L.maxND = std::max(L.maxND, QD * nzD);
         L.maxQN = std::max(L.maxQN, QN); L.maxNzN = std::max(L.maxNzN, pz); L.maxNN = std::max(L.maxNN, NN);
         L.maxNB = std::max(L.maxNB, s.nB); L.maxNc = std::max(L.maxNc, s.nc);
         h->max_nc = std::max(h->max_nc, s.nc);
       }
   L.nsub = S;
-  h->L.mscratch_stride = (long long)L.maxQN * CW;
+  // multi-RHS scratch per (subdomain, column chunk): Q x 128 covers both the
+  // 64-column CUDA-core chunks and the 128-column tensor-core chunks
+  h->L.mscratch_stride = (long long)L.maxQN * 128;
   // coarse owners CSR, owners of a coarse DOF in subdomain order (stable
   // counting sort of the subdomain-ordered list)
   std::vector<int> ptr(nc + 1, 0);
@@ -421,7 +424,7 @@ void build_metadata(bddc_handle* h) {
 namespace {
 
 struct Layout {
-  long long D, N, W, Y, G, L, PA, Sc, Ac, Phi, B, Vec;
+  long long D, N, W, Y, G, L, PA, Sc, Ac, Phi, B, Vec, TC;
 };
 
 Layout layout_of(const bddc_handle* h) {
@@ -445,6 +448,7 @@ Layout layout_of(const bddc_handle* h) {
     o.Phi = std::max(o.Phi, s.offPhi + padded((long long)s.nB * s.nc));
     o.B = std::max(o.B, s.offB + s.nB);
     o.Vec = std::max(o.Vec, s.offVec + NN);
+    o.TC = std::max(o.TC, s.offTC + (long long)pz * tc_kchunks(QN) * tc_chunk_floats(QN));
   }
   return o;
 }
@@ -557,6 +561,9 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   L.Ac = (double*)h->dalloc(sizeof(double) * lay.Ac, true);
   const int nch = (L.maxNc + CW - 1) / CW;
   L.mscratch = h->dalloc(es * (size_t)L.nsub * nch * L.mscratch_stride, true);
+  // packed tensor-core tiles of the Neumann factors (FP32 path, planes of at
+  // most 256 nodes), setup only
+  L.tc = (!dbl && L.maxQN <= 256) ? h->dalloc(sizeof(float) * (size_t)std::max(lay.TC, 1LL), true) : nullptr;
   // weights (eq. W or Remark 1)
   double* pw = nullptr;
   if (h->opt.weights == BDDC_W_RHO) {

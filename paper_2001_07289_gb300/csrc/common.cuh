@@ -40,7 +40,15 @@ struct SubDesc {
   long long offPhi;   // Phi on the box surface: nB x nc, row-major (local type)
   long long offB;     // per-surface-node arrays: nB (weights, v_Gamma)
   long long offVec;   // apply: local Neumann vector, nN (local type)
+  long long offTC;    // setup: canonical 3xTF32 tiles of the Neumann S_k^{-1} (FP32 path)
 };
+
+// Tensor-core tiles of one Neumann plane inverse: per K chunk of 32 columns
+// and per 128-row tile a hi and a lo tile of 128 x 32 TF32 values (16 KiB
+// each) in the canonical K-major order; floats per (plane, K chunk).
+__host__ __device__ inline int tc_mtiles(int Q) { return (Q + 127) / 128; }
+__host__ __device__ inline int tc_kchunks(int Q) { return (Q + 31) / 32; }
+__host__ __device__ inline long long tc_chunk_floats(int Q) { return (long long)tc_mtiles(Q) * 8192; }
 
 // A coarse DOF as seen from one subdomain: the object's local node box
 // (inclusive ranges on the local Neumann grid) and its global number.

@@ -25,6 +25,7 @@
 #include "dense.cuh"
 #include "kernels.h"
 #include "stream.cuh"
+#include "umma.cuh"
 
 namespace bddc {
 
@@ -451,43 +452,279 @@ k_btsolve_multi(const SubDesc* __restrict__ subs, const T* __restrict__ fac, T* 
     cta_gemm<T>(Q, cw, Q, T(1), base + (long long)(k - 1) * SS, Q, false, Yk - (long long)Q * ld, ld, false, T(0),
                 U, cw, 0, 0, false, sm);
     const T* Bd = base + (long long)(nz + k - 1) * SS;
-    for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) {
-      const int i = e / cw, c = e % cw, ix = i % gx, iy = i / gx;
-      T acc = T(0);
-#pragma unroll
-      for (int o = 0; o < 9; ++o) {
-        const int dx = o % 3 - 1, dy = o / 3 - 1;
-        if (ix + dx >= 0 && ix + dx < gx && iy + dy >= 0 && iy + dy < gy)
-          acc += Bd[o * Q + i] * U[(i + dx + dy * gx) * cw + c];
-      }
-      Yk[(long long)i * ld + c] -= acc;
-    }
-    __syncthreads();
-  }
-  for (int k = nz - 1; k >= 0; --k) {
-    T* Yk = Yb + (long long)k * Q * ld;
-    if (k == nz - 1) {
-      for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) U[e] = Yk[(long long)(e / cw) * ld + e % cw];
-    } else {
-      const T* Bd = base + (long long)(nz + k) * SS;       // B_{k+1}
-      const T* Yn = Yk + (long long)Q * ld;
-      for (int e = threadIdx.x; e < Q * cw; e += blockDim.x) {
-        const int l = e / cw, c = e % cw, lx = l % gx, ly = l / gx;
+    const int c = threadIdx.x % CW;
+    if (c < cw)
+      for (int i = threadIdx.x / CW; i < Q; i += BDDC_THREADS / CW) {
+        const int ix = i % gx, iy = i / gx;
         T acc = T(0);
 #pragma unroll
         for (int o = 0; o < 9; ++o) {
           const int dx = o % 3 - 1, dy = o / 3 - 1;
-          if (lx - dx >= 0 && lx - dx < gx && ly - dy >= 0 && ly - dy < gy) {
-            const int i = l - dx - dy * gx;
-            acc += Bd[o * Q + i] * Yn[(long long)i * ld + c];
-          }
+          if (ix + dx >= 0 && ix + dx < gx && iy + dy >= 0 && iy + dy < gy)
+            acc += Bd[o * Q + i] * U[(i + dx + dy * gx) * cw + c];
         }
-        U[e] = Yk[(long long)l * ld + c] - acc;
+        Yk[(long long)i * ld + c] -= acc;
       }
+    __syncthreads();
+  }
+  for (int k = nz - 1; k >= 0; --k) {
+    T* Yk = Yb + (long long)k * Q * ld;
+    const int c = threadIdx.x % CW;
+    if (k == nz - 1) {
+      if (c < cw)
+        for (int l = threadIdx.x / CW; l < Q; l += BDDC_THREADS / CW) U[l * cw + c] = Yk[(long long)l * ld + c];
+    } else {
+      const T* Bd = base + (long long)(nz + k) * SS;       // B_{k+1}
+      const T* Yn = Yk + (long long)Q * ld;
+      if (c < cw)
+        for (int l = threadIdx.x / CW; l < Q; l += BDDC_THREADS / CW) {
+          const int lx = l % gx, ly = l / gx;
+          T acc = T(0);
+#pragma unroll
+          for (int o = 0; o < 9; ++o) {
+            const int dx = o % 3 - 1, dy = o / 3 - 1;
+            if (lx - dx >= 0 && lx - dx < gx && ly - dy >= 0 && ly - dy < gy) {
+              const int i = l - dx - dy * gx;
+              acc += Bd[o * Q + i] * Yn[(long long)i * ld + c];
+            }
+          }
+          U[l * cw + c] = Yk[(long long)l * ld + c] - acc;
+        }
     }
     __syncthreads();
     cta_gemm<T>(Q, cw, Q, T(1), base + (long long)k * SS, Q, false, U, cw, false, T(0), Yk, ld, 0, 0, false, sm);
   }
+}
+
+// ---------------------------------------------------------------------------
+// The same multi-RHS solves on the tensor cores (FP32 local path, Q <= 256):
+// every product S^{-1} X (Q x Q times Q x 128) runs as tcgen05.mma kind::tf32
+// with 3xTF32 splitting, two M tiles of 128 rows, accumulators in TMEM
+// (2 x 128 columns), K streamed in chunks of 32 through two shared-memory
+// stages (A hi/lo 2 x 32 KiB, B hi/lo 2 x 16 KiB each) so that staging chunk
+// n + 1 overlaps the MMAs of chunk n.  grid: (subdomain, 128-column chunk),
+// 256 threads; thread 0 issues the MMAs, every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int TC_N = 128, TC_KC = 32;
+constexpr unsigned TC_A_BYTES = 2u * 2u * 128u * TC_KC * 4u;   // up to two 128-row tiles, hi and lo
+constexpr unsigned TC_B_BYTES = (unsigned)TC_N * TC_KC * 4u;
+constexpr unsigned TC_STAGE_BYTES = TC_A_BYTES + 2u * TC_B_BYTES;
+
+// Packs the Neumann S_k^{-1} into the tiles the tensor cores read: per
+// (plane, K chunk of 32), for each 128-row tile a hi and a lo tile (3xTF32
+// split) in the canonical K-major order, so that the products load their A
+// operand with one bulk copy per chunk.  grid: (subdomain, plane, K chunk).
+__global__ void k_tc_pack(const SubDesc* __restrict__ subs, const float* __restrict__ facN, float* __restrict__ tiles) {
+  const SubDesc s = subs[blockIdx.x];
+  const Grid g = grid_of(s, 1);
+  const int Q = g.gx * g.gy, k = blockIdx.y, kc = blockIdx.z;
+  if (k >= g.gz || kc >= tc_kchunks(Q)) return;
+  const float* S = facN + s.offN + (long long)k * slot_stride(Q);
+  float* dst = tiles + s.offTC + ((long long)k * tc_kchunks(Q) + kc) * tc_chunk_floats(Q);
+  for (int e = threadIdx.x; e < tc_mtiles(Q) * 4096; e += blockDim.x) {
+    const int m = e >> 12, ei = e & 4095;
+    const int q = ei & 3, rr = (ei >> 2) & 7, cc = (ei >> 5) & 7, gg = ei >> 8;
+    const int r = m * 128 + gg * 8 + rr, col = kc * TC_KC + cc * 4 + q;
+    const float x = (r < Q && col < Q) ? S[r * Q + col] : 0.0f;
+    const float hi = umma::to_tf32(x);
+    dst[m * 8192 + ei] = hi;
+    dst[m * 8192 + 4096 + ei] = umma::to_tf32(x - hi);
+  }
+}
+
+struct TcState {
+  unsigned char* stage;   // 2 stages of TC_STAGE_BYTES
+  uint64_t* bar;          // per stage: the MMAs that read it have completed
+  uint64_t* tbar;         // per stage: the bulk copy of its A tiles has landed
+  uint32_t tmem;
+  int next;               // chunks issued so far (stage = next & 1)
+};
+
+// TMEM <- S (Q x Q, packed tiles of one plane) X (Q x ncol, ld ldx); on
+// return the products are complete and visible to every thread
+__device__ void tc_product(TcState& G, const float* __restrict__ Atiles, int Q, const float* __restrict__ X,
+                           long long ldx, int ncol, int* err) {
+  const int nkc = tc_kchunks(Q), nmt = tc_mtiles(Q);
+  const uint32_t idesc = umma::idesc_tf32(128, TC_N);
+  for (int kc = 0; kc < nkc; ++kc) {
+    const int b = G.next & 1;
+    unsigned char* st = G.stage + (size_t)b * TC_STAGE_BYTES;
+    if (threadIdx.x == 0) {
+      if (G.next >= 2) mbar_wait_bounded(&G.bar[b], (unsigned)(((G.next >> 1) - 1) & 1), err);
+      bulk_load(st, Atiles + (long long)kc * tc_chunk_floats(Q), (unsigned)nmt * 32768u, &G.tbar[b]);
+    }
+    __syncthreads();
+    float* Bhi = reinterpret_cast<float*>(st + TC_A_BYTES);
+    float* Blo = reinterpret_cast<float*>(st + TC_A_BYTES + TC_B_BYTES);
+    const int k0 = kc * TC_KC;
+    // B: row n of B is column n of X (K-major operand); all loads of a thread
+    // are issued before any conversion so that their latencies overlap
+    constexpr int NB = TC_N * TC_KC / BDDC_THREADS;
+    float xb[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int e = threadIdx.x + j * BDDC_THREADS;
+      const int kk = e / TC_N, n = e % TC_N, k = k0 + kk;
+      xb[j] = (n < ncol && k < Q) ? X[(long long)k * ldx + n] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int e = threadIdx.x + j * BDDC_THREADS;
+      const unsigned o = umma::kmajor_offset(e % TC_N, e / TC_N, TC_KC) >> 2;
+      const float hi = umma::to_tf32(xb[j]);
+      Bhi[o] = hi;
+      Blo[o] = umma::to_tf32(xb[j] - hi);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_wait_bounded(&G.tbar[b], (unsigned)((G.next >> 1) & 1), err);
+      umma::fence_after_sync();
+      const unsigned sbo = (TC_KC / 4) * 128;
+      const unsigned a0 = umma::smem_u32(st);
+      const unsigned b_hi = umma::smem_u32(Bhi), b_lo = umma::smem_u32(Blo);
+#pragma unroll
+      for (int ks = 0; ks < TC_KC / 8; ++ks) {
+        const unsigned ko = ks * 256;   // 8 TF32 values = two core matrices along K
+        const uint64_t bh = umma::smem_desc(b_hi + ko, 128, sbo), bl = umma::smem_desc(b_lo + ko, 128, sbo);
+        for (int m = 0; m < nmt; ++m) {
+          const unsigned a_hi = a0 + m * 32768u, a_lo = a_hi + 16384u;
+          const uint64_t ah = umma::smem_desc(a_hi + ko, 128, sbo), al = umma::smem_desc(a_lo + ko, 128, sbo);
+          const uint32_t d = G.tmem + (uint32_t)(m * TC_N);
+          umma::mma_tf32(d, ah, bh, idesc, kc > 0 || ks > 0);
+          umma::mma_tf32(d, ah, bl, idesc, true);
+          umma::mma_tf32(d, al, bh, idesc, true);
+        }
+      }
+      umma::commit(&G.bar[b]);
+    }
+    ++G.next;
+  }
+  if (threadIdx.x == 0) mbar_wait_bounded(&G.bar[(G.next - 1) & 1], (unsigned)(((G.next - 1) >> 1) & 1), err);
+  __syncthreads();
+  umma::fence_after_sync();
+}
+
+// dst[i][n] = product row i (i < Q, n < ncol), ld ldd; warps 0-3 read the
+// first 128 rows, warps 4-7 the second.  A lane holds one row, so each warp
+// turns its 32 x 32 blocks around in shared memory (the stages are idle once
+// the products are complete) and stores whole row segments.
+__device__ void tc_readback(const TcState& G, int Q, int ncol, float* __restrict__ dst, long long ldd) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, m = warp >> 2, quad = warp & 3;
+  const int row0 = m * 128 + quad * 32;
+  float* tb = reinterpret_cast<float*>(G.stage) + warp * 32 * 33;
+  for (int c = 0; c < TC_N; c += 32) {
+    float v[32];
+    umma::ld32(G.tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(m * TC_N + c), v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = v[j];
+    __syncwarp();
+    if (c + lane < ncol)
+      for (int r = 0; r < 32 && row0 + r < Q; ++r) dst[(long long)(row0 + r) * ldd + c + lane] = tb[r * 33 + lane];
+    __syncwarp();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+}
+
+// Stencil steps of the tensor-core solves, one column per thread and four
+// rows per step with every load issued before the arithmetic (the loads come
+// from L2; eight warps per SM cannot hide one row's latency at a time).
+// Bd: nine diagonals of the coupling in shared memory.
+//   forward:  Y_k[i][c] -= sum_o Bd[o][i] U[i + off_o][c]
+//   backward: U[l][c] = Y_k[l][c] - sum_o Bd[o][l - off_o] Y_{k+1}[l - off_o][c]
+template <bool FWD>
+__device__ void tc_stencil(int Q, int gx, int gy, int cw, const float* Bd, const float* __restrict__ src, long long lds,
+                           float* __restrict__ Yk, long long ld, float* __restrict__ U) {
+  constexpr int RS = 4, STEP = BDDC_THREADS / TC_N;
+  const int c = threadIdx.x % TC_N;
+  if (c >= cw) return;
+  for (int i0 = threadIdx.x / TC_N; i0 < Q; i0 += STEP * RS) {
+    // branch-free taps: out-of-plane neighbours read a valid row with weight
+    // 0, so every load of the step is issued before the first FMA
+    float sv[RS][9], w[RS][9], y[RS];
+#pragma unroll
+    for (int u = 0; u < RS; ++u) {
+      const int i = min(i0 + u * STEP, Q - 1), ix = i % gx, iy = i / gx;
+      y[u] = Yk[(long long)i * ld + c];
+#pragma unroll
+      for (int o = 0; o < 9; ++o) {
+        const int dx = o % 3 - 1, dy = o / 3 - 1;
+        const int sx = FWD ? dx : -dx, sy = FWD ? dy : -dy;
+        const bool ok = ix + sx >= 0 && ix + sx < gx && iy + sy >= 0 && iy + sy < gy;
+        const int j = ok ? i + sx + sy * gx : i;
+        w[u][o] = ok ? Bd[o * Q + (FWD ? i : j)] : 0.0f;
+        sv[u][o] = src[(long long)j * lds + c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RS; ++u) {
+      const int i = i0 + u * STEP;
+      float acc = 0.0f;
+#pragma unroll
+      for (int o = 0; o < 9; ++o) acc += w[u][o] * sv[u][o];
+      if (i < Q) {
+        if (FWD) Yk[(long long)i * ld + c] = y[u] - acc;
+        else U[i * TC_N + c] = y[u] - acc;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_btsolve_multi_tc(const SubDesc* __restrict__ subs, const float* __restrict__ fac,
+                   const float* __restrict__ tiles, float* __restrict__ Y, float* __restrict__ scratch,
+                   long long scratch_stride, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ uint32_t tmem_slot;
+  const SubDesc s = subs[blockIdx.x];
+  const int c0 = blockIdx.y * TC_N;
+  if (c0 >= s.nc) return;
+  const int cw = min(TC_N, s.nc - c0);
+  const Grid g = grid_of(s, 1);
+  const int Q = g.gx * g.gy, nz = g.gz, ld = s.nc, gx = g.gx, gy = g.gy;
+  const long long SS = slot_stride(Q);
+  const float* base = fac + s.offN;
+  float* Yb = Y + s.offY + c0;
+  float* U = scratch + ((long long)blockIdx.x * gridDim.y + blockIdx.y) * scratch_stride;   // Q x TC_N
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q) mbar_init(&bars[q], 1);
+    fence_barrier_init();
+  }
+  if (threadIdx.x < 32) umma::tmem_alloc(&tmem_slot, 2 * TC_N);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  TcState G{smraw, bars, bars + 2, tmem_slot, 0};
+  const float* At = tiles + s.offTC;
+  float* Bs = reinterpret_cast<float*>(smraw + 2 * TC_STAGE_BYTES);   // nine coupling diagonals
+  const long long plane_floats = (long long)tc_kchunks(Q) * tc_chunk_floats(Q);
+  for (int k = 1; k < nz; ++k) {
+    float* Yk = Yb + (long long)k * Q * ld;
+    tc_product(G, At + (long long)(k - 1) * plane_floats, Q, Yk - (long long)Q * ld, ld, cw, err);
+    tc_readback(G, Q, cw, U, TC_N);
+    const float* Bg = base + (long long)(nz + k - 1) * SS;
+    for (int e = threadIdx.x; e < 9 * Q; e += blockDim.x) Bs[e] = Bg[e];
+    __syncthreads();
+    tc_stencil<true>(Q, gx, gy, cw, Bs, U, TC_N, Yk, ld, nullptr);
+    __syncthreads();
+  }
+  for (int k = nz - 1; k >= 0; --k) {
+    float* Yk = Yb + (long long)k * Q * ld;
+    if (k == nz - 1) {
+      tc_product(G, At + (long long)k * plane_floats, Q, Yk, ld, cw, err);
+    } else {
+      const float* Bg = base + (long long)(nz + k) * SS;       // B_{k+1}
+      for (int e = threadIdx.x; e < 9 * Q; e += blockDim.x) Bs[e] = Bg[e];
+      __syncthreads();
+      tc_stencil<false>(Q, gx, gy, cw, Bs, Yk + (long long)Q * ld, ld, Yk, ld, U);
+      __syncthreads();
+      tc_product(G, At + (long long)k * plane_floats, Q, U, TC_N, cw, err);
+    }
+    tc_readback(G, Q, cw, Yk, ld);
+  }
+  if (threadIdx.x < 32) umma::tmem_dealloc(G.tmem, 2 * TC_N);
 }
 
 // ---------------------------------------------------------------------------
@@ -1080,9 +1317,19 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
   T* Y = (T*)L.Y; T* G = (T*)L.G; T* Lv = (T*)L.Lv; T* PA = (T*)L.PA; T* Sc = (T*)L.Sc; T* Phi = (T*)L.Phi;
   if (L.maxNc > 0) {  // one subdomain has no interface and no coarse space
     k_coarse_rhs<T><<<dim3(S, 64), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y);
-    int nch = (L.maxNc + CW - 1) / CW;
-    k_btsolve_multi<T><<<dim3(S, nch), BDDC_THREADS, sm, st>>>(L.subs, facN, Y, (T*)L.mscratch,
-                                                                 L.mscratch_stride);
+    if (std::is_same<T, float>::value && L.tc) {
+      k_tc_pack<<<dim3(S, L.maxNzN, tc_kchunks(L.maxQN)), BDDC_THREADS, 0, st>>>(L.subs, (const float*)L.facN,
+                                                                               (float*)L.tc);
+      const int nch = (L.maxNc + TC_N - 1) / TC_N;
+      k_btsolve_multi_tc<<<dim3(S, nch), BDDC_THREADS, 2 * TC_STAGE_BYTES + 9 * 256 * sizeof(float), st>>>(
+          L.subs, (const float*)L.facN, (const float*)L.tc, (float*)L.Y, (float*)L.mscratch, L.mscratch_stride,
+          L.err);
+      BDDC_COUNT(1);
+    } else {
+      const int nch = (L.maxNc + CW - 1) / CW;
+      k_btsolve_multi<T><<<dim3(S, nch), BDDC_THREADS, sm, st>>>(L.subs, facN, Y, (T*)L.mscratch,
+                                                                   L.mscratch_stride);
+    }
     k_constraint_means<T><<<dim3(S, 16), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, G);
     k_schur<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, G, Sc, Lv, W, L.err);
     int nrc = (L.maxNN + RB - 1) / RB;
@@ -1101,6 +1348,8 @@ void configure_local_kernels() {
   size_t sm = dense_smem<T>();
   cudaFuncSetAttribute(k_btschur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_btsolve_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_btsolve_multi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(2 * TC_STAGE_BYTES + 9 * 256 * sizeof(float)));
   cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_phi_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_dirichlet_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

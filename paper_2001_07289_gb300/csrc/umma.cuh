@@ -1,0 +1,110 @@
+// Fifth-generation tensor-core primitives (tcgen05, sm_100 family) for the
+// FP32 local products of the mixed path: operands in shared memory in the
+// canonical K-major layout without swizzle, FP32 accumulators in tensor
+// memory (TMEM), completion through an mbarrier.
+//
+// Canonical K-major layout, no swizzle: the matrix is cut into core matrices
+// of 8 rows x 16 bytes (4 TF32 values), each stored as 128 contiguous bytes
+// (row r of the core matrix at byte 16 r).  Core matrices adjacent along K
+// are LBO bytes apart, adjacent 8-row groups SBO bytes apart.  Here LBO = 128
+// and SBO = (K of the staged chunk / 4) * 128, i.e. element (r, k) of a chunk
+// with KC columns sits at (r/8) (KC/4) 128 + (k/4) 128 + (r%8) 16 + (k%4) 4.
+//
+// 3xTF32: an FP32 value x is split into hi = tf32(x) and lo = tf32(x - hi);
+// a product accumulates hi*hi + hi*lo + lo*hi, which keeps FP32-level
+// accuracy (the dropped lo*lo term is below FP32 rounding) on TF32 hardware.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bddc {
+namespace umma {
+
+__device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__host__ __device__ inline unsigned kmajor_offset(int r, int k, int kc) {
+  return (unsigned)(r >> 3) * (unsigned)(kc >> 2) * 128u + (unsigned)(k >> 2) * 128u + (unsigned)(r & 7) * 16u +
+         (unsigned)(k & 3) * 4u;
+}
+
+// shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), the
+// descriptor version of this architecture (bit 46), no swizzle
+__device__ inline uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major
+__host__ __device__ inline uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ inline float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// one warp allocates ncols TMEM columns (power of two >= 32), address -> *slot
+__device__ inline void tmem_alloc(uint32_t* slot, unsigned ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ inline void tmem_dealloc(uint32_t taddr, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ inline void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ inline void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] B[smem]^T for one K step of 8 TF32 values
+__device__ inline void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, bool accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
+      : "memory");
+}
+
+// the mbarrier receives one arrival when all tcgen05 operations issued so far
+// by this thread have completed
+__device__ inline void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ inline void ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ inline void ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+}  // namespace umma
+}  // namespace bddc
