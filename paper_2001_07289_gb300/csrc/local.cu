@@ -172,18 +172,28 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
   if (k > 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < Q; i += SCHUR_THREADS / 32)
-      for (int j = lane; j < Q; j += 32) {
-        const int jx = j % gx, jy = j / gx;
+    // per column j the nine weights and neighbour offsets are fixed, so a lane
+    // keeps them and walks rows; taps are branch-free (weight 0 off the plane)
+    // so the loads of a row are all in flight together
+    for (int j = lane; j < Q + 31 - (Q + 31) % 32; j += 32) {
+      const int jj = min(j, Q - 1), jx = jj % gx, jy = jj / gx;
+      float w[9];
+      int off[9];
+#pragma unroll
+      for (int o = 0; o < 9; ++o) {
+        const int dx = o % 3 - 1, dy = o / 3 - 1;
+        const bool ok = jx + dx >= 0 && jx + dx < gx && jy + dy >= 0 && jy + dy < gy;
+        w[o] = ok ? Bd[o * Q + jj] : 0.0f;
+        off[o] = ok ? dx + dy * gx : 0;
+      }
+      for (int i = warp; i < Q; i += SCHUR_THREADS / 32) {
+        const float* row = Sp + i * Q + jj;
         float acc = 0.0f;
 #pragma unroll
-        for (int o = 0; o < 9; ++o) {
-          const int dx = o % 3 - 1, dy = o / 3 - 1;
-          if (jx + dx >= 0 && jx + dx < gx && jy + dy >= 0 && jy + dy < gy)
-            acc += Sp[i * Q + j + dx + dy * gx] * Bd[o * Q + j];
-        }
-        Tm[i * Q + j] = acc;
+        for (int o = 0; o < 9; ++o) acc += row[off[o]] * w[o];
+        if (j < Q) Tm[i * Q + j] = acc;
       }
+    }
     __syncthreads();
   }
   float x[RI][RJ];
@@ -201,8 +211,9 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict
 #pragma unroll
           for (int o = 0; o < 9; ++o) {
             const int dx = o % 3 - 1, dy = o / 3 - 1;
-            if (ix + dx >= 0 && ix + dx < gx && iy + dy >= 0 && iy + dy < gy)
-              acc += Bd[o * Q + i] * Tm[(i + dx + dy * gx) * Q + j];
+            const bool ok = ix + dx >= 0 && ix + dx < gx && iy + dy >= 0 && iy + dy < gy;
+            const float wv = ok ? Bd[o * Q + i] : 0.0f;
+            acc += wv * Tm[(ok ? i + dx + dy * gx : i) * Q + j];
           }
           v -= acc;
         }
