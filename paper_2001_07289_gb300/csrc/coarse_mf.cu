@@ -429,8 +429,13 @@ k_mf_trsm(MFDev d, const int4* __restrict__ work) {
 }
 
 // A[i,l] -= A[i,j] A[l,j]^T
+// A[i,l] -= A[i,j] A[l,j]^T.  Look-ahead: the CTA that updates the diagonal
+// tile of the next pivot panel (i = l = j + 1 < pivot tiles) holds its final
+// value and factors it right away (Cholesky and explicit inverse), so the
+// next panel's trsm does not wait for a separate potrf launch.
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_syrk(MFDev d, const int4* __restrict__ work) {
+k_mf_syrk(MFDev d, const int4* __restrict__ work, double* pscratch, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double As[32 * 33], Bs[32 * 33];
   const int4 w = work[blockIdx.x];
   const int f = w.x, i = w.y, l = w.z, j = w.w;
@@ -443,6 +448,14 @@ k_mf_syrk(MFDev d, const int4* __restrict__ work) {
   double* A = d.F + d.foff[f];
   tile_gemm_f64<true>(ni, nl, nj, -1.0, A + ri * F + rj, F, A + rl * F + rj, F, 1.0, A + ri * F + rl, F, i == l,
                       As, Bs);
+  if (i == l && i == j + 1 && i < (np + FNB - 1) / FNB) {
+    __syncthreads();
+    DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
+    const bool ok = cta_chol_inv<double>(A + ri * F + ri, (int)F, d.Dinv + d.doff[f] + (long long)i * FNB * FNB, FNB,
+                                         ni, pscratch + (long long)f * 2048, sm);
+    if (!ok && threadIdx.x == 0)
+      if (atomicCAS(err, 0, 5) == 0) err[1] = f;
+  }
 }
 
 __device__ inline double mf_wsum(double v) {
@@ -629,6 +642,7 @@ void configure_mf_kernels() {
   cudaFuncSetAttribute(k_mf_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mf_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mf_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(k_mf_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(k_mf_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(2 * FNB * (FNB + 1) * sizeof(double)));
 }
@@ -735,6 +749,7 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
     maxpo = std::max(maxpo, (int)P.step_potrf[k].size() / 4);
   }
   P.pscratch = (double*)tmp_alloc(sizeof(double) * 2048 * (size_t)maxpo);
+  P.fscratch = (double*)tmp_alloc(sizeof(double) * 2048 * (size_t)P.nfront);
   // solve work lists: per level fwd items {front, row chunk}, bwd items {front, column chunk}
   std::vector<int> items;
   P.fwd_items_off.assign(P.nlevel, 0); P.fwd_items_len.assign(P.nlevel, 0);
@@ -790,9 +805,11 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st) {
       const int4* lp = P.d_lists + P.list_off[3 * step];
       const int4* lt = P.d_lists + P.list_off[3 * step + 1];
       const int4* ls = P.d_lists + P.list_off[3 * step + 2];
-      if (npo) { BDDC_COUNT(1); k_mf_potrf<<<npo, BDDC_THREADS, dsm, st>>>(d, lp, P.pscratch, err); }
+      // the first panel's diagonal tiles of the level; later ones are
+      // factored inside the previous step's syrk (look-ahead)
+      if (npo && j == 0) { BDDC_COUNT(1); k_mf_potrf<<<npo, BDDC_THREADS, dsm, st>>>(d, lp, P.pscratch, err); }
       if (ntr) { BDDC_COUNT(1); k_mf_trsm<<<ntr, BDDC_THREADS, tsm, st>>>(d, lt); }
-      if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, 0, st>>>(d, ls); }
+      if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, dsm, st>>>(d, ls, P.fscratch, err); }
     }
   }
   // solve matrices: Linv_P by tile rows, then G = L_UP Linv_P

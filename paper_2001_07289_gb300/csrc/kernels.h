@@ -112,6 +112,7 @@ struct MFPlan {
   std::vector<int> list_len;
   int4* d_lists = nullptr;
   double* pscratch = nullptr;       // potrf scratch: 2048 doubles per concurrent diagonal tile
+  double* fscratch = nullptr;       // look-ahead potrf scratch in the syrk steps: 2048 doubles per front
   // per level, on the device in one int array: fronts by level, each front's
   // children (CSR aligned with that list), and children by (level, slot)
   int maxslot = 0;
