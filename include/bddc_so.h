@@ -48,7 +48,13 @@ enum {
 
 enum { BDDC_FP64 = 0, BDDC_MIXED = 1 };      /* precision of the local solves   */
 enum { BDDC_W_CARD = 0, BDDC_W_RHO = 1 };    /* eq. (W) / Remark 1 weighting     */
-enum { BDDC_SEL_VEF = 0 };                   /* coarse objects: all of Theta-hat on Gamma */
+/* Constraint selection (Table 1, Section 5): which objects of Theta-hat on
+ * Gamma carry coarse DOFs.  VEF: vertices, edges and faces; VE: vertices and
+ * edges; VF: vertices and faces; V: vertices only.  Vertices are eliminated
+ * as primal DOFs, which keeps every local constrained Neumann matrix SPD, so
+ * selections without vertices (faces only, edges and faces) are rejected with
+ * BDDC_ERR_UNSUPPORTED. */
+enum { BDDC_SEL_VEF = 0, BDDC_SEL_VE = 1, BDDC_SEL_VF = 2, BDDC_SEL_V = 3 };
 
 typedef struct bddc_handle bddc_handle;
 
@@ -73,7 +79,7 @@ typedef struct {
     int precision;  /* BDDC_FP64 or BDDC_MIXED (FP32 local factors/solves, FP64 rest) */
     int weights;    /* BDDC_W_CARD or BDDC_W_RHO                                      */
     int L_elems;    /* >= 1                                                           */
-    int selection;  /* BDDC_SEL_VEF                                                   */
+    int selection;  /* BDDC_SEL_VEF, BDDC_SEL_VE, BDDC_SEL_VF or BDDC_SEL_V           */
     int use_graph;  /* 1: pcg_solve runs its whole loop as one CUDA graph (below)      */
     int maxit;      /* PCG iteration limit (<= 0: 2000)                               */
 } bddc_options;

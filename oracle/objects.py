@@ -12,9 +12,13 @@ Here:
     around the node.
   * objects = connected components (nodes sharing an element) of Gamma nodes
     with equal keys.
-  * type = number of axes along which the object extends (0 vertex, 1 edge,
-    2 face).  A one-node object is a point value whatever its name, so the
-    type only matters for the selection variants.
+  * type = by the number of sub-subdomains in the key (Section 3: the
+    objects are the vertices, edges and faces of Theta-hat, classified from
+    the list of sub-subdomains containing each DOF): 2 -> face, 3 or 4 ->
+    edge, more -> vertex.  In a tensor-product Theta-hat these are 2, 4 and
+    8, whatever the number of nodes of the object (a face between two
+    one-node intervals is still a face).  A one-node object is a point value
+    whatever its type, so the type only matters for the selection variants.
   * selection (Table 1 / Section 5.2 variants): "vef" keeps every object,
     "ve" vertices and edges, "f" faces only, "v" vertices only.
 """
@@ -117,13 +121,10 @@ def classify(nx: int, ny: int, nz: int, sub: np.ndarray, piece: np.ndarray) -> O
     splits = np.flatnonzero(np.diff(comp[order])) + 1
     groups = np.split(gamma[order], splits)
     # deterministic object order: by (type, lowest node id)
-    ix = lambda v: v % (nx + 1)
-    iy = lambda v: (v // (nx + 1)) % (ny + 1)
-    iz = lambda v: v // ((nx + 1) * (ny + 1))
     kinds = []
     for grp in groups:
-        ext = sum(int(f(grp).max() > f(grp).min()) for f in (ix, iy, iz))
-        kinds.append(min(ext, 2))
+        npieces = int(np.sum(node_pieces[grp[0]] >= 0))
+        kinds.append(2 if npieces == 2 else (1 if npieces <= 4 else 0))
     kinds = np.array(kinds, dtype=np.int64)
     first = np.array([grp.min() for grp in groups], dtype=np.int64)
     perm = np.lexsort((first, kinds))

@@ -21,7 +21,8 @@ BDDC_OK, BDDC_ERR_ARG, BDDC_ERR_NOT_SPD, BDDC_ERR_NOCONV = 0, -1, -2, -3
 BDDC_ERR_BREAKDOWN, BDDC_ERR_CUDA, BDDC_ERR_OOM, BDDC_ERR_TIMEOUT, BDDC_ERR_UNSUPPORTED = -4, -5, -6, -7, -8
 BDDC_FP64, BDDC_MIXED = 0, 1
 BDDC_W_CARD, BDDC_W_RHO = 0, 1
-BDDC_SEL_VEF = 0
+BDDC_SEL_VEF, BDDC_SEL_VE, BDDC_SEL_VF, BDDC_SEL_V = 0, 1, 2, 3
+SELECTIONS = {"vef": BDDC_SEL_VEF, "ve": BDDC_SEL_VE, "vf": BDDC_SEL_VF, "v": BDDC_SEL_V}
 
 
 class BddcError(RuntimeError):
@@ -116,7 +117,7 @@ def _stream() -> C.c_void_p:
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph):
+def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection="vef"):
     mesh = Mesh(nx, ny, nz, h)
     part = Partition()
     keep = []
@@ -127,14 +128,16 @@ def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph):
         part.cut[d] = C.cast(arr, C.POINTER(C.c_int))
     prec = {"fp64": BDDC_FP64, "mixed": BDDC_MIXED}[precision] if isinstance(precision, str) else precision
     wts = {"card": BDDC_W_CARD, "rho": BDDC_W_RHO}[weights] if isinstance(weights, str) else weights
-    opt = Options(prec, wts, L, BDDC_SEL_VEF, int(use_graph), maxit)
+    sel = SELECTIONS[selection] if isinstance(selection, str) else selection
+    opt = Options(prec, wts, L, sel, int(use_graph), maxit)
     return mesh, part, opt, keep
 
 
 def analyze(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int, h: float = 0.0,
-            precision="fp64", weights="card") -> dict:
+            precision="fp64", weights="card", selection="vef") -> dict:
     """bddc_analyze: host-only counts of objects and of the coarse elimination plan."""
-    mesh, part, opt, keep = _structs(nx, ny, nz, h if h > 0 else 1.0 / nx, cuts, L, precision, weights, 2000, False)
+    mesh, part, opt, keep = _structs(nx, ny, nz, h if h > 0 else 1.0 / nx, cuts, L, precision, weights, 2000, False,
+                                     selection)
     out = Analysis()
     _check(lib.bddc_analyze(C.byref(mesh), C.byref(part), C.byref(opt), C.byref(out)), None)
     return {k: getattr(out, k) for k, _ in Analysis._fields_}
@@ -145,12 +148,13 @@ class BDDC:
 
     def __init__(self, nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int,
                  alpha: torch.Tensor, h: float = 0.0, precision="fp64", weights="card",
-                 maxit: int = 2000, use_graph: bool = False):
+                 maxit: int = 2000, use_graph: bool = False, selection="vef"):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.h = h if h > 0 else 1.0 / nx
         self.n_nodes = (nx + 1) * (ny + 1) * (nz + 1)
         self.maxit = maxit
-        mesh, part, opt, keep = _structs(nx, ny, nz, self.h, cuts, L, precision, weights, maxit, use_graph)
+        mesh, part, opt, keep = _structs(nx, ny, nz, self.h, cuts, L, precision, weights, maxit, use_graph,
+                                         selection)
         self._handle = C.c_void_p()
         _check(lib.bddc_setup(C.byref(mesh), C.byref(part), C.byref(opt), _ptr(alpha), _stream(),
                               C.byref(self._handle)), None)
@@ -160,6 +164,7 @@ class BDDC:
         a = alpha if alpha is not None else torch.from_numpy(p.alpha).cuda()
         kw.setdefault("precision", p.precision)
         kw.setdefault("weights", p.weights)
+        kw.setdefault("selection", p.selection)
         return cls(p.nx, p.ny, p.nz, p.cuts, p.L, a, h=p.h, **kw)
 
     def _vec(self):
@@ -242,10 +247,11 @@ class BDDC:
 
 
 def solve_host(nx, ny, nz, cuts, L, alpha: np.ndarray, b: np.ndarray, rtol: float, h: float = 0.0,
-               precision="fp64", weights="card", maxit: int = 2000, use_graph: bool = False):
+               precision="fp64", weights="card", maxit: int = 2000, use_graph: bool = False,
+               selection="vef"):
     """bddc_solve_host: setup + PCG from host arrays, result in a host array."""
     h = h if h > 0 else 1.0 / nx
-    mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph)
+    mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection)
     a = np.ascontiguousarray(alpha, dtype=np.float64)
     bb = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros_like(bb)

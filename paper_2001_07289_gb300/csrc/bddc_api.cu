@@ -275,6 +275,10 @@ void build_metadata(bddc_handle* h) {
   // global objects: tuples of items on Gamma, off the Dirichlet boundary, non-empty
   const long long nt = (long long)nit[0] * nit[1] * nit[2];
   std::vector<int> objid(nt, -1);
+  // object type by its number of point items: 3 vertex, 2 edge, 1 face
+  const int sel = h->opt.selection;
+  const bool keep_edges = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VE;
+  const bool keep_faces = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VF;
   auto valid = [&](int ix, int iy, int iz) {
     int it[3] = {ix, iy, iz};
     bool on_gamma = false;
@@ -283,6 +287,8 @@ void build_metadata(bddc_handle* h) {
       if (k == 3 || h->ax[d].empty(it[d])) return false;
       if (k == 2) on_gamma = true;
     }
+    const int pts = !(ix & 1) + !(iy & 1) + !(iz & 1);
+    if ((pts == 2 && !keep_edges) || (pts == 1 && !keep_faces)) return false;
     return on_gamma;
   };
   int nc = 0, nvert = 0;
@@ -820,7 +826,10 @@ std::unique_ptr<bddc_handle> make_handle(const bddc_mesh* mesh, const bddc_parti
   if (opt->L_elems < 1) throw BddcError(BDDC_ERR_ARG, "L must be >= 1");
   if (opt->precision != BDDC_FP64 && opt->precision != BDDC_MIXED) throw BddcError(BDDC_ERR_ARG, "bad precision");
   if (opt->weights != BDDC_W_CARD && opt->weights != BDDC_W_RHO) throw BddcError(BDDC_ERR_ARG, "bad weights");
-  if (opt->selection != BDDC_SEL_VEF) throw BddcError(BDDC_ERR_UNSUPPORTED, "only the vef selection is built");
+  if (opt->selection < BDDC_SEL_VEF || opt->selection > BDDC_SEL_V)
+    throw BddcError(BDDC_ERR_UNSUPPORTED,
+                    "selection must keep the vertices (vef, ve, vf or v): vertices are the primal DOFs that keep "
+                    "the local constrained Neumann matrices SPD");
   std::unique_ptr<bddc_handle> h(new bddc_handle());
   h->mesh = *mesh;
   if (!(h->mesh.h > 0)) h->mesh.h = 1.0 / mesh->nx;

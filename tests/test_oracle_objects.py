@@ -45,9 +45,13 @@ def test_counts_match_closed_form(m, s, L):
 
 @pytest.mark.parametrize("m,s", [(2, 2), (3, 3), (2, 5)])
 def test_total_count_one_node_intervals(m, s):
-    """With L = 2 every interval holds one node; the object count is unchanged."""
+    """With L = 2 every interval holds one node; the object count is unchanged,
+    and so are the type counts: a face shared by two sub-subdomains stays a
+    face when it is a single node (types come from the sub-subdomain lists,
+    not from the object's extent)."""
     o = count_objects(m * s * 2, m, 2)
     assert len(o) == sum(tensor_counts(m, s).values())
+    assert o.counts() == tensor_counts(m, s)
 
 
 def test_workload_poisson16_counts():
