@@ -185,8 +185,11 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
     for (int o : B.piv[f]) P.gid.push_back(o);
     for (int o : B.upd[f]) P.gid.push_back(o);
     P.gid_off[f + 1] = (long long)P.gid.size();
+    // partial factorisation, in multiply-adds: Cholesky of the pivot block
+    // np^3/6, the panel solve L_UP = A_UP L_P^-T nu np^2/2, the update of the
+    // U block nu^2 np/2
     const double np = P.np[f], nu = P.nu[f];
-    P.flops += np * np * np / 3.0 + nu * np * np + nu * nu * np / 2.0;
+    P.flops += np * np * np / 6.0 + nu * np * np / 2.0 + nu * nu * np / 2.0;
   }
   if (pos != nc) throw std::runtime_error("nested dissection missed coarse objects");
   P.fpool = fo; P.dpool = dof; P.wpool = wo;
@@ -216,6 +219,7 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
     }
     for (int u = 0; u < nut; ++u)
       for (int s2 = 0; s2 < npt; ++s2) P.g_items.insert(P.g_items.end(), {f, u, s2, 0});
+    // solve matrices: Linv_P = L_P^-1 (np^3/6), G = L_UP Linv_P (nu np^2/2)
     P.flops += (double)P.np[f] * P.np[f] * P.np[f] / 6.0 + (double)P.nu[f] * P.np[f] * P.np[f] / 2.0;
   }
   P.tpool = to;
