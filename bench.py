@@ -344,7 +344,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, st_h = solve_host(p.nx, p.ny, p.nz, p.cuts, p.L, a_host, b_host, p.rtol, h=p.h,
-                             precision=args.precision, use_graph=not args.host_loop)
+                             precision=args.precision, weights=p.weights, selection=p.selection,
+                             use_graph=not args.host_loop)
         dt = time.perf_counter() - t0
         if k > 0:
             e2e_t.append(dt)
@@ -423,7 +424,7 @@ def main():
         "wall_s_timed_region": round(t_wall, 3),
         "gpu_launches": int(sum(i["launches"] for i in infos)),
         "e2e": {"value": round(n_free / statistics.mean(e2e_t) / 1e6, 4), "unit": "MDOF/s",
-                "ms": round(1e3 * statistics.mean(e2e_t), 3),
+                "ms": round(1e3 * statistics.mean(e2e_t), 3), "iterations": st_h["iterations"],
                 "h2d_bytes_per_step": int(8 * (p.n_elems + p.n_nodes)), "d2h_bytes_per_step": int(8 * p.n_nodes),
                 "api": "bddc_solve_host (host alpha, b, x; copies, setup, PCG, teardown inside)"},
         "clocks": clk.summary(),
