@@ -329,6 +329,7 @@ void build_metadata(bddc_handle* h) {
       for (int sx = 0; sx < nsub[0]; ++sx) {
         const int si = sx + nsub[0] * (sy + nsub[1] * sz);
         SubDesc& s = h->subs[si];
+        s.id = si;
         const int sl[3] = {sx, sy, sz};
         int ilo[3], ihi[3];
         for (int d = 0; d < 3; ++d) {
@@ -547,6 +548,18 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   L.m = m;
   L.alpha = h->alpha;
   L.subs = upload(h, h->subs, st);
+  {
+    // longest first: the per-subdomain kernels of uneven partitions take the
+    // subdomains in decreasing order of plane work (Q^2 per plane, Neumann
+    // grid), so that the large ones do not start last
+    std::vector<SubDesc> lpt(h->subs);
+    auto work = [](const SubDesc& d) {
+      const double q = (double)(d.w[0] + 1) * (d.w[1] + 1);
+      return q * q * (d.w[2] + 1);
+    };
+    std::stable_sort(lpt.begin(), lpt.end(), [&](const SubDesc& a, const SubDesc& b) { return work(a) > work(b); });
+    L.subs_lpt = upload(h, lpt, st);
+  }
   L.lc = upload(h, h->lc, st);
   L.facD = h->dalloc(es * lay.D);
   L.facN = h->dalloc(es * lay.N);

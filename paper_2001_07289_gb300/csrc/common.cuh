@@ -21,6 +21,7 @@
 namespace bddc {
 
 struct SubDesc {
+  int id;             // index of the subdomain (x fastest over the box grid)
   int e0[3];          // element origin of the box
   int w[3];           // box widths in elements
   int nB;             // box-surface nodes

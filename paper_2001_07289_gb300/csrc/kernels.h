@@ -25,6 +25,7 @@ struct LocalLaunch {
   long long mscratch_stride;
   void *Y, *G, *Lv, *PA, *Sc, *Phi, *vloc;
   void* PhiT;                      // transposed copy of Phi for the apply's column accumulations
+  const SubDesc* subs_lpt;         // the same descriptors, largest subdomains first
   void* tc;                        // packed 3xTF32 tiles of the Neumann S_k^{-1} (setup, FP32 path) or null
   double* Ac;
   double* delta;

@@ -168,7 +168,7 @@ constexpr int SCHUR_THREADS = 512;   // 32 x 16 owner grid
 template <int RI, int RJ>
 __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict__ slot,
                                  const float* __restrict__ Sp, const float* __restrict__ Bd, float* __restrict__ cb,
-                                 float* __restrict__ rb, float* __restrict__ Tm, int* err, int code) {
+                                 float* __restrict__ rb, float* __restrict__ Tm, int* err, int code, int sub_id) {
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
   if (k > 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -222,7 +222,7 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict
     }
   }
   auto publish_pivot = [&](int q, float d) {
-    if (!(d > 0.0f)) { set_error(err, code, blockIdx.x); d = 1.0f; }
+    if (!(d > 0.0f)) { set_error(err, code, sub_id); d = 1.0f; }
     rb[q & 1] = __frcp_rn(d);
   };
   if (tc == 0) {
@@ -346,7 +346,7 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
       if constexpr (std::is_same<T, float>::value)
         schur_plane_regs<RI, RJ>(Q, gx, gy, k, slot, k > 0 ? base + (long long)(k - 1) * SS : nullptr,
                                  k > 0 ? base + (long long)(g.gz + k - 1) * SS : nullptr, cb, rb, rb + 2,
-                                 err, neumann ? 3 : 2);
+                                 err, neumann ? 3 : 2, s.id);
       continue;
     }
     if (k > 0) {
@@ -391,7 +391,7 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
     for (int i = threadIdx.x; i < Q; i += blockDim.x) cb[i] = A[(long long)i * (i + 1) / 2];
     if (threadIdx.x == 0) {
       T d = A[0];
-      if (!(d > T(0))) { set_error(err, neumann ? 3 : 2, blockIdx.x); d = T(1); }
+      if (!(d > T(0))) { set_error(err, neumann ? 3 : 2, s.id); d = T(1); }
       rb[0] = T(1) / d;
     }
     __syncthreads();
@@ -413,7 +413,7 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
             cn[i] = v;
             if (i == q) {
               T d = v;
-              if (!(d > T(0))) { set_error(err, neumann ? 3 : 2, blockIdx.x); d = T(1); }
+              if (!(d > T(0))) { set_error(err, neumann ? 3 : 2, s.id); d = T(1); }
               rb[q & 1] = T(1) / d;
             }
           } else if (i == q && j < q) {
@@ -804,7 +804,7 @@ k_schur(const SubDesc* __restrict__ subs, T* __restrict__ G, T* __restrict__ Sc,
   T* Linv = Sc + s.offSc;       // na x na
   T* diag = scratch + s.offW;
   bool ok = cta_chol_inv<T>(S, nc, Linv, na, na, diag, sm);
-  if (!ok && threadIdx.x == 0) set_error(err, 4, blockIdx.x);
+  if (!ok && threadIdx.x == 0) set_error(err, 4, s.id);
   // S_c^{-1} = Linv^T Linv -> into the free S region, then back to Sc
   cta_gemm<T>(na, na, na, T(1), Linv, na, true, Linv, na, false, T(0), S, nc, 2, 2, false, sm);
   for (int e = threadIdx.x; e < na * na; e += blockDim.x) Linv[e] = S[(long long)(e / na) * nc + e % na];
@@ -1320,7 +1320,7 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
     const int maxQ = std::max(L.maxQN, L.maxQD);
     const size_t smb = 227 * 1024;
     const long long cap = (long long)(smb / sizeof(T)) - 2LL * maxQ - 2;
-    k_btschur<T><<<dim3(S, L.maxQD > 0 ? 2 : 1), SCHUR_THREADS, smb, st>>>(L.subs, facN, facD, W, cap, L.err);
+    k_btschur<T><<<dim3(S, L.maxQD > 0 ? 2 : 1), SCHUR_THREADS, smb, st>>>(L.subs_lpt, facN, facD, W, cap, L.err);
     BDDC_COUNT(1);
   }
   if (ev) cudaEventRecord(ev[1], st);
@@ -1333,12 +1333,12 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
                                                                                (float*)L.tc);
       const int nch = (L.maxNc + TC_N - 1) / TC_N;
       k_btsolve_multi_tc<<<dim3(S, nch), BDDC_THREADS, 2 * TC_STAGE_BYTES + 9 * 256 * sizeof(float), st>>>(
-          L.subs, (const float*)L.facN, (const float*)L.tc, (float*)L.Y, (float*)L.mscratch, L.mscratch_stride,
+          L.subs_lpt, (const float*)L.facN, (const float*)L.tc, (float*)L.Y, (float*)L.mscratch, L.mscratch_stride,
           L.err);
       BDDC_COUNT(1);
     } else {
       const int nch = (L.maxNc + CW - 1) / CW;
-      k_btsolve_multi<T><<<dim3(S, nch), BDDC_THREADS, sm, st>>>(L.subs, facN, Y, (T*)L.mscratch,
+      k_btsolve_multi<T><<<dim3(S, nch), BDDC_THREADS, sm, st>>>(L.subs_lpt, facN, Y, (T*)L.mscratch,
                                                                    L.mscratch_stride);
     }
     k_constraint_means<T><<<dim3(S, 16), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, G);
@@ -1386,14 +1386,14 @@ void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, do
   if (L.maxQD == 0) return;
   BDDC_COUNT(1);
   size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxND + L.maxQD + 2);
-  k_dirichlet_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facD, r, t, z, mode, L.err);
+  k_dirichlet_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.m, (const T*)L.facD, r, t, z, mode, L.err);
 }
 
 template <typename T>
 void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
   size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNB + 1 + L.maxNN + L.maxQN + 2);
   BDDC_COUNT(1);
-  k_neumann_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta, r,
+  k_neumann_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta, r,
                                                        t, (T*)L.vloc, L.rcl, L.err);
 }
 
@@ -1401,7 +1401,7 @@ template <typename T>
 void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t st) {
   size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNc + 1);
   BDDC_COUNT(1);
-  k_neumann_finish<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs, L.lc, (const T*)L.PhiT, (const T*)L.vloc, uc,
+  k_neumann_finish<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.lc, (const T*)L.PhiT, (const T*)L.vloc, uc,
                                                         L.vgam, L.err);
 }
 
