@@ -20,6 +20,7 @@
 // Local matrices are stored as z-plane blocks (see common.cuh); the factor of
 // each diagonal block is kept as its explicit inverse, so every sweep is a
 // sequence of dense products.
+#include <cooperative_groups.h>
 #include <type_traits>
 #include "common.cuh"
 #include "dense.cuh"
@@ -28,6 +29,8 @@
 #include "umma.cuh"
 
 namespace bddc {
+
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -1066,20 +1069,40 @@ __device__ inline void col_finish(const ColLayout& L, A acc[4], A* part, Out out
 // The 2 nz - 1 symmetric slots stream through the ring in that order and
 // their products are column accumulations (S^{-1} is symmetric, so rows are
 // columns); the nine-diagonal B_k and B_{k+1}^T products run between them.
-// v (nz*Q), t (Q), part (blockDim) in shared memory.
+// A subdomain is solved by a cluster of two CTAs: each streams one half of
+// the rows of every slot, and the two partial column sums meet through
+// distributed shared memory (rank 0's plus rank 1's, the same on both CTAs,
+// so both keep identical copies of v and t).  Each CTA streams the coupling
+// diagonals itself and runs the stencils redundantly.  Every CTA finishes
+// every slot and passes the same cluster barriers in the same order, whatever
+// its share of rows.  v (nz*Q), t (Q), part (blockDim), pb (2 Q) in shared
+// memory.
 // ---------------------------------------------------------------------------
+// rows of a row-major matrix (cols entries of es bytes per row) per rank when
+// nrank CTAs share it: ceil(rows / nrank) rounded up to the row step that
+// keeps a 16-byte alignment
+__device__ inline int split_rows(int rows, int cols, int es, int nrank) {
+  int step = 1;
+  while ((step * cols * es) % 16) ++step;
+  const int h = (rows + nrank - 1) / nrank;
+  return (h + step - 1) / step * step;
+}
+
 template <typename T>
 __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int gy, int nz, T* v, T* t, T* part,
-                             int* err) {
+                             T* pb, int* err) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
   const int Q = gx * gy;
   const int R = rows_per_chunk(Q, (int)sizeof(T));
-  const int nch = (Q + R - 1) / R;
+  // this CTA's rows of every slot: [rlo, rhi), in chunks of R rows; the split
+  // keeps every chunk start on a 16-byte boundary (bulk copies require it)
+  const int half = split_rows(Q, Q, (int)sizeof(T), nrank);
+  const int rlo = min(Q, rank * half), rhi = min(Q, rlo + half);
+  const int nch = (rhi - rlo + R - 1) / R;
   const int ngs = nch + 1;                 // slot chunks plus the coupling's diagonals
   const int nlead = 2 * (nz - 1);          // groups followed by a stencil step
   const long long SS = slot_stride(Q);
-  // group bi: forward slot bi (bi < nz - 1) or backward slot 2 nz - 2 - bi;
-  // every group but the last (backward k = 0) ends with the diagonals of
-  // B_{bi+1} (forward) or B_k (backward), streamed like the slot rows
   auto slot_of = [&](int bi) { return bi < nz - 1 ? bi : 2 * nz - 2 - bi; };
   auto locate = [&](int c, int& bi, int& lc) {
     if (c < nlead * ngs) { bi = c / ngs; lc = c % ngs; }
@@ -1087,6 +1110,20 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
   };
   const ColLayout L = col_layout(Q);
   T acc[4] = {T(0), T(0), T(0), T(0)};
+  // partial sums of the slot of group bi -> both CTAs' shares added in rank
+  // order -> dst (double-buffered by group, so that a CTA never overwrites a
+  // buffer its peer may still read)
+  auto finish = [&](int bi, T* dst) {
+    T* mine = pb + (bi & 1) * Q;
+    col_finish<T>(L, acc, part, [&](int cc, T sum) { mine[cc] = sum; });
+    cluster.sync();
+    for (int c = threadIdx.x; c < Q; c += blockDim.x) {
+      T s = T(0);
+      for (int r = 0; r < nrank; ++r) s += cluster.map_shared_rank(mine, r)[c];
+      dst[c] = s;
+    }
+    __syncthreads();
+  };
   auto src = [&](int c, const void*& p, unsigned& bytes) {
     int bi, lc;
     locate(c, bi, lc);
@@ -1096,7 +1133,7 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
       p = fac + (long long)(nz + kb - 1) * SS;
       bytes = (unsigned)(9 * Q * sizeof(T));
     } else {
-      const int r0 = lc * R, nr = min(R, Q - r0);
+      const int r0 = rlo + lc * R, nr = min(R, rhi - r0);
       p = fac + k * SS + (long long)r0 * Q;
       bytes = (unsigned)(nr * Q * sizeof(T));
     }
@@ -1107,16 +1144,13 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
     const int k = slot_of(bi);
     const bool fwd = bi < nz - 1;
     if (lc < nch) {
-      const int r0 = lc * R, nr = min(R, Q - r0);
+      const int r0 = rlo + lc * R, nr = min(R, rhi - r0);
       const T* in = (fwd || bi == nz - 1) ? v + (long long)k * Q : t;
       col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, in + r0, acc);
-      if (lc == nch - 1) {
-        __syncthreads();   // every row of the slot is consumed before outputs overwrite inputs
-        T* dst = fwd ? t : v + (long long)k * Q;
-        col_finish<T>(L, acc, part, [&](int cc, T sum) { dst[cc] = sum; });
-      }
       return;
     }
+    __syncthreads();   // every row of the slot is consumed before outputs overwrite inputs
+    finish(bi, fwd ? t : v + (long long)k * Q);
     const T* Bd = reinterpret_cast<const T*>(raw);
     if (fwd) {
       // v_{k+1} -= B_{k+1} t
@@ -1149,21 +1183,27 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
         t[l] = vp[l] - a;
       }
     }
+    // the next slot's accumulation reads what the stencil wrote; warps are
+    // not otherwise held together between chunks
+    __syncthreads();
   };
   ring_run(ring, nlead * ngs + nch, src, use, err);
+  // the last slot (backward, plane 0) has no stencil step after it
+  finish(nlead, v);
+  cluster.sync();   // the peer's last reads of this CTA's buffers are done
 }
 
-__host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 8 * NBUF; }
+__host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 16 * NBUF; }
 
 // Dirichlet solves of the apply.  mode 0: z_I = A_II^{-1} r_I;
 // mode 1: z_I = A_II^{-1} (r_I - t_I).  Writes the interior nodes of z only.
 template <typename T>
-__global__ void __launch_bounds__(APPLY_THREADS)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS)
 k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
                   const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ z, int mode,
                   int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  const SubDesc s = subs[blockIdx.x];
+  const SubDesc s = subs[blockIdx.x >> 1];   // a cluster of two CTAs per subdomain
   const Grid g = grid_of(s, 0);
   if (g.gz == 0) return;
   const int Q = g.gx * g.gy, n = Q * g.gz;
@@ -1171,6 +1211,7 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
   T* part = reinterpret_cast<T*>(smraw + ring_bytes());
   T* v = part + APPLY_THREADS;
   T* tq = v + n;
+  T* pb = tq + Q;
   ring_init(ring);
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
@@ -1180,7 +1221,8 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
     v[l] = (T)val;
   }
   __syncthreads();
-  sweep_stream<T>(ring, fac + s.offD, g.gx, g.gy, g.gz, v, tq, part, err);
+  sweep_stream<T>(ring, fac + s.offD, g.gx, g.gy, g.gz, v, tq, part, pb, err);
+  if ((blockIdx.x & 1) == 0)
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
     long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
@@ -1192,12 +1234,14 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
 // coarse right-hand side rc_i = Phi_i^T r_i, and the constrained Neumann solve
 // y = A_rr^{-1} r_i,r (into vloc).
 template <typename T>
-__global__ void __launch_bounds__(APPLY_THREADS)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS)
 k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac, const T* __restrict__ Phi, const double* __restrict__ delta,
                 const double* __restrict__ r, const double* __restrict__ t, T* __restrict__ vloc,
                 double* __restrict__ rcl, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  const SubDesc s = subs[blockIdx.x];
+  const SubDesc s = subs[blockIdx.x >> 1];   // a cluster of two CTAs per subdomain
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const int Q = px * py, n = Q * pz;
   Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
@@ -1205,6 +1249,7 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
   T* rg = part + APPLY_THREADS;
   T* v = rg + s.nB + 1;
   T* tq = v + n;
+  T* pb = tq + Q;   // 2 max(Q, nc) partial sums
   ring_init(ring);
   for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = T(0);
   __syncthreads();
@@ -1220,26 +1265,38 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
   __syncthreads();
   if (s.nc > 0) {
     // rc_i = Phi_i^T r_i in the local precision: columns of Phi accumulate
-    // over streamed rows
+    // over streamed rows, the rows split between the two CTAs and their
+    // partial sums added in rank order
     const int R = rows_per_chunk(s.nc, (int)sizeof(T));
-    const int nch = (s.nB + R - 1) / R;
+    const int half = split_rows(s.nB, s.nc, (int)sizeof(T), nrank);
+    const int rlo = min(s.nB, rank * half), rhi = min(s.nB, rlo + half);
+    const int nch = (rhi - rlo + R - 1) / R;
     const T* P = Phi + s.offPhi;
     const ColLayout L = col_layout(s.nc);
     T acc[4] = {T(0), T(0), T(0), T(0)};
     auto src = [&](int c, const void*& p, unsigned& bytes) {
-      const int r0 = c * R, nr = min(R, s.nB - r0);
+      const int r0 = rlo + c * R, nr = min(R, rhi - r0);
       p = P + (long long)r0 * s.nc;
       bytes = (unsigned)(nr * s.nc * sizeof(T));
     };
     auto use = [&](int c, const unsigned char* raw) {
-      const int r0 = c * R, nr = min(R, s.nB - r0);
+      const int r0 = rlo + c * R, nr = min(R, rhi - r0);
       col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, rg + r0, acc);
     };
     ring_run(ring, nch, src, use, err);
-    col_finish<T>(L, acc, part, [&](int cc, T sum) { rcl[s.cofs + cc] = (double)sum; });
+    col_finish<T>(L, acc, part, [&](int cc, T sum) { pb[cc] = sum; });
+    cluster.sync();
+    if (rank == 0)
+      for (int c = threadIdx.x; c < s.nc; c += blockDim.x) {
+        T sum = T(0);
+        for (int r = 0; r < nrank; ++r) sum += cluster.map_shared_rank(pb, r)[c];
+        rcl[s.cofs + c] = (double)sum;
+      }
+    cluster.sync();   // both CTAs' partial buffers are free again
   }
-  sweep_stream<T>(ring, fac + s.offN, px, py, pz, v, tq, part, err);
-  for (int l = threadIdx.x; l < n; l += blockDim.x) vloc[s.offVec + l] = v[l];
+  sweep_stream<T>(ring, fac + s.offN, px, py, pz, v, tq, part, pb, err);
+  if (rank == 0)
+    for (int l = threadIdx.x; l < n; l += blockDim.x) vloc[s.offVec + l] = v[l];
 }
 
 // v_i on the box surface: Phi_i (u_c|_i - [0; C_r y]) + y, as a column
@@ -1385,15 +1442,17 @@ template <typename T>
 void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, double* z, int mode, cudaStream_t st) {
   if (L.maxQD == 0) return;
   BDDC_COUNT(1);
-  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxND + L.maxQD + 2);
-  k_dirichlet_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.m, (const T*)L.facD, r, t, z, mode, L.err);
+  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxND + 3 * (size_t)L.maxQD + 2);
+  k_dirichlet_solve<T><<<2 * L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.m, (const T*)L.facD, r, t, z, mode,
+                                                             L.err);
 }
 
 template <typename T>
 void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
-  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNB + 1 + L.maxNN + L.maxQN + 2);
+  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNB + 1 + L.maxNN + L.maxQN +
+                                          2 * (size_t)std::max(L.maxQN, L.maxNc) + 2);
   BDDC_COUNT(1);
-  k_neumann_solve<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta, r,
+  k_neumann_solve<T><<<2 * L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta, r,
                                                        t, (T*)L.vloc, L.rcl, L.err);
 }
 

@@ -1,13 +1,15 @@
 // Streaming of row-major matrices from HBM into shared memory with 1-D bulk
 // asynchronous copies (cp.async.bulk, the TMA engine) completing on mbarriers.
 //
-// A CTA owns a ring of NBUF buffers of CHB bytes.  One thread issues the copy
-// of chunk c + NBUF as soon as chunk c has been consumed, so up to NBUF chunks
-// (144 KiB) are in flight per SM while the CTA computes.  Only that thread
-// polls the chunk's mbarrier; the others wait at a CTA barrier, so waiting
-// costs no issue slots and does not compete with the copies for shared memory.  Chunks must start on
-// 16-byte boundaries and their byte counts are rounded up to 16; callers pad
-// their allocations accordingly.  Every wait is bounded: a wait that gives up
+// A CTA owns a ring of NBUF buffers of CHB bytes with two mbarriers per
+// buffer: "full" completes when the buffer's copy has landed, "empty" when
+// every warp has finished reading it.  Every thread waits on "full" itself
+// and each warp arrives on "empty" after its use of the chunk, so warps run
+// ahead of each other up to the ring depth and no block-wide barrier is
+// needed per chunk; one thread (the producer) waits on "empty" before it
+// refills the buffer with chunk c + NBUF.  Chunks must start on 16-byte
+// boundaries and their byte counts are rounded up to 16; callers pad their
+// allocations accordingly.  Every wait is bounded: a wait that gives up
 // records error code 7 (timeout) and the kernel carries on to its end.
 #pragma once
 #include <cuda_runtime.h>
@@ -60,14 +62,21 @@ __device__ inline bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* er
 
 struct Ring {
   unsigned char* buf;  // NBUF * CHB bytes, 128-byte aligned
-  uint64_t* bar;       // NBUF mbarriers
+  uint64_t* bar;       // 2 NBUF mbarriers: full[0..NBUF), then empty[0..NBUF)
   int base;            // chunks consumed by earlier runs (slot / parity bookkeeping)
 };
+
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 
 // Initialise the ring's barriers (all threads call; ends with a barrier).
 __device__ inline void ring_init(Ring& r) {
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NBUF; ++s) mbar_init(&r.bar[s], 1);
+    for (int s = 0; s < NBUF; ++s) {
+      mbar_init(&r.bar[s], 1);
+      mbar_init(&r.bar[NBUF + s], blockDim.x / 32);
+    }
     fence_barrier_init();
   }
   r.base = 0;
@@ -76,34 +85,36 @@ __device__ inline void ring_init(Ring& r) {
 
 // Streams nchunks chunks: src(c, &ptr, &bytes) describes chunk c (ptr
 // 16-byte aligned, bytes > 0), use(c, smem) consumes it with every thread of
-// the CTA.  Ends with a barrier.
+// the CTA (use may contain block-wide barriers; every thread calls it for
+// every chunk).  Ends with a barrier.
 template <typename Src, typename Use>
 __device__ void ring_run(Ring& r, int nchunks, Src src, Use use, int* err) {
   const int first = r.base;
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < nchunks && c < NBUF; ++c) {
-      const void* p;
-      unsigned bytes;
-      src(c, p, bytes);
-      const int slot = (first + c) % NBUF;
-      bulk_load(r.buf + (size_t)slot * CHB, p, (bytes + 15u) & ~15u, &r.bar[slot]);
-    }
-  }
+  uint64_t* full = r.bar;
+  uint64_t* empty = r.bar + NBUF;
+  // the producer fills chunk g into slot g % NBUF once the chunk that last
+  // used the slot (g - NBUF) has been read by every warp
+  auto issue = [&](int c) {
+    const void* p;
+    unsigned bytes;
+    src(c, p, bytes);
+    const int g = first + c, slot = g % NBUF;
+    if (g >= NBUF) mbar_wait_bounded(&empty[slot], (unsigned)(((g / NBUF) - 1) & 1), err);
+    fence_proxy_async();
+    bulk_load(r.buf + (size_t)slot * CHB, p, (bytes + 15u) & ~15u, &full[slot]);
+  };
+  if (threadIdx.x == 0)
+    for (int c = 0; c < nchunks && c < NBUF; ++c) issue(c);
   for (int c = 0; c < nchunks; ++c) {
     const int g = first + c, slot = g % NBUF;
-    if (threadIdx.x == 0) mbar_wait_bounded(&r.bar[slot], (unsigned)((g / NBUF) & 1), err);
-    __syncthreads();
+    mbar_wait_bounded(&full[slot], (unsigned)((g / NBUF) & 1), err);
     use(c, r.buf + (size_t)slot * CHB);
-    __syncthreads();
-    if (threadIdx.x == 0 && c + NBUF < nchunks) {
-      const void* p;
-      unsigned bytes;
-      src(c + NBUF, p, bytes);
-      fence_proxy_async();
-      bulk_load(r.buf + (size_t)slot * CHB, p, (bytes + 15u) & ~15u, &r.bar[slot]);
-    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[slot]);
+    if (threadIdx.x == 0 && c + NBUF < nchunks) issue(c + NBUF);
   }
   r.base = first + nchunks;
+  __syncthreads();
 }
 
 // Rows of a row-major matrix with `cols` entries of `es` bytes per chunk: the
