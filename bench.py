@@ -414,6 +414,7 @@ def main():
         "setup_phases_ms": phases,
         "pcg_solve_repeat": dict(repeat, note="pcg_solve on a set-up handle, b resident, L2 flushed"),
         "precond_apply": {"ms": round(apply_ms, 4), "applies_per_s": round(1e3 / apply_ms, 1),
+                          "ctas_per_subdomain": info_apply.get("apply_cluster"),
                           "mdofs": round(n_free * 1e3 / apply_ms / 1e6, 2)},
         f"{other}_path": {"time_to_solution_ms": round(statistics.mean(other_times), 3),
                           "iterations": other_iters[-1], "setup_ms": round(other_info["setup_ms"], 3),

@@ -118,6 +118,8 @@ typedef struct {
                                  Schur complements of the plane blocks)           */
     long long apply_bytes;    /* bytes one bddc_apply must read from HBM: local
                                  factors (Dirichlet twice), Phi twice, coarse fronts */
+    int apply_cluster;        /* CTAs per subdomain in the apply's local solves,
+                                 chosen by timing (see bddc_setup)                 */
 } bddc_info_t;
 
 /* Host-only analysis of a problem, no GPU needed: the counts that bddc_setup
@@ -148,7 +150,12 @@ int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part,
  * of Theta-hat on Gamma; a vertex is a point value, an edge or face the mean
  * over its nodes.  alpha_dev is read during the call only.  On success *out
  * receives a new handle.  Errors: BDDC_ERR_ARG (bad sizes/cuts/L/options,
- * alpha <= 0 or not finite), BDDC_ERR_NOT_SPD, BDDC_ERR_OOM, BDDC_ERR_CUDA. */
+ * alpha <= 0 or not finite), BDDC_ERR_NOT_SPD, BDDC_ERR_OOM, BDDC_ERR_CUDA. *
+ * Autotuning: the first setup of a problem shape (precision, subdomain count,
+ * largest planes, largest local coarse space) in the process times one
+ * preconditioner apply with one and with two CTAs per subdomain in the local
+ * solves and keeps the faster for every later handle of that shape; that
+ * first setup takes about eight applies longer. */
 int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part,
                const bddc_options* opt, const double* alpha_dev, void* stream,
                bddc_handle** out);

@@ -20,6 +20,7 @@
 #include <mutex>
 #include <stdexcept>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "bddc_so.h"
@@ -560,6 +561,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     std::stable_sort(lpt.begin(), lpt.end(), [&](const SubDesc& a, const SubDesc& b) { return work(a) > work(b); });
     L.subs_lpt = upload(h, lpt, st);
   }
+  L.apply_cluster = 2;
   L.lc = upload(h, h->lc, st);
   L.facD = h->dalloc(es * lay.D);
   L.facN = h->dalloc(es * lay.N);
@@ -671,6 +673,53 @@ void apply_impl(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
 void apply(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
   if (h->local_double) apply_impl<double>(h, r, z, st);
   else apply_impl<float>(h, r, z, st);
+}
+
+// Autotuner of the apply schedule: one or two CTAs per subdomain in the
+// local solves.  Two halve each CTA's share of the streamed factor rows but
+// add an exchange per slot; which wins depends on how many subdomains there
+// are per SM and on their size, so the first setup of a shape times three
+// applies of each (after a warm-up, on a zero vector: the work does not
+// depend on the values) and the choice is kept per shape for the process.
+struct TuneKey {
+  int dbl, nsub, qn, qd, nc;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dbl, nsub, qn, qd, nc) < std::tie(o.dbl, o.nsub, o.qn, o.qd, o.nc);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+void tune_apply(bddc_handle* h, cudaStream_t st) {
+  LocalLaunch& L = h->L;
+  const TuneKey key{h->local_double, L.nsub, L.maxQN, L.maxQD, L.maxNc};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) { L.apply_cluster = it->second; return; }
+  }
+  CK(cudaMemsetAsync(h->r, 0, sizeof(double) * h->n_nodes, st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int pick = 2;
+  for (int c = 1; c <= 2; ++c) {
+    L.apply_cluster = c;
+    apply(h, h->r, h->z, st);
+    CK(cudaEventRecord(e0, st));
+    for (int k = 0; k < 3; ++k) apply(h, h->r, h->z, st);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) { best = ms; pick = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.apply_cluster = pick;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = pick;
 }
 
 }  // namespace
@@ -870,6 +919,8 @@ extern "C" int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, con
   std::unique_ptr<bddc_handle> h = make_handle(mesh, part, opt);
   cudaStream_t st = (cudaStream_t)stream;
   do_setup(h.get(), alpha_dev, st);
+  tune_apply(h.get(), st);
+  check_err_flags(h.get(), st);
   *out = h.release();
   return BDDC_OK;
   ABI_END(hnull)
@@ -1031,6 +1082,7 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   }
   info->local_factor_fma = fma;
   info->apply_bytes = bytes;
+  info->apply_cluster = h->L.apply_cluster;
   return BDDC_OK;
 }
 

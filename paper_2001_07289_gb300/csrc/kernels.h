@@ -26,6 +26,7 @@ struct LocalLaunch {
   void *Y, *G, *Lv, *PA, *Sc, *Phi, *vloc;
   void* PhiT;                      // transposed copy of Phi for the apply's column accumulations
   const SubDesc* subs_lpt;         // the same descriptors, largest subdomains first
+  int apply_cluster;               // CTAs per subdomain in the apply's local solves (1 or 2, tuned)
   void* tc;                        // packed 3xTF32 tiles of the Neumann S_k^{-1} (setup, FP32 path) or null
   double* Ac;
   double* delta;

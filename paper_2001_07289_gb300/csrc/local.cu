@@ -1114,6 +1114,11 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
   // order -> dst (double-buffered by group, so that a CTA never overwrites a
   // buffer its peer may still read)
   auto finish = [&](int bi, T* dst) {
+    if (nrank == 1) {   // a CTA of its own: straight to the destination
+      col_finish<T>(L, acc, part, [&](int cc, T sum) { dst[cc] = sum; });
+      __syncthreads();
+      return;
+    }
     T* mine = pb + (bi & 1) * Q;
     col_finish<T>(L, acc, part, [&](int cc, T sum) { mine[cc] = sum; });
     cluster.sync();
@@ -1190,7 +1195,7 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
   ring_run(ring, nlead * ngs + nch, src, use, err);
   // the last slot (backward, plane 0) has no stencil step after it
   finish(nlead, v);
-  cluster.sync();   // the peer's last reads of this CTA's buffers are done
+  if (nrank > 1) cluster.sync();   // the peer's last reads of this CTA's buffers are done
 }
 
 __host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 16 * NBUF; }
@@ -1198,12 +1203,13 @@ __host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 16 
 // Dirichlet solves of the apply.  mode 0: z_I = A_II^{-1} r_I;
 // mode 1: z_I = A_II^{-1} (r_I - t_I).  Writes the interior nodes of z only.
 template <typename T>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS)
+__global__ void __launch_bounds__(APPLY_THREADS)
 k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
                   const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ z, int mode,
                   int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  const SubDesc s = subs[blockIdx.x >> 1];   // a cluster of two CTAs per subdomain
+  // one cluster (of one or two CTAs, the launch decides) per subdomain
+  const SubDesc s = subs[blockIdx.x / cg::this_cluster().num_blocks()];
   const Grid g = grid_of(s, 0);
   if (g.gz == 0) return;
   const int Q = g.gx * g.gy, n = Q * g.gz;
@@ -1222,7 +1228,7 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
   }
   __syncthreads();
   sweep_stream<T>(ring, fac + s.offD, g.gx, g.gy, g.gz, v, tq, part, pb, err);
-  if ((blockIdx.x & 1) == 0)
+  if (cg::this_cluster().block_rank() == 0)
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
     long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
@@ -1234,14 +1240,15 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
 // coarse right-hand side rc_i = Phi_i^T r_i, and the constrained Neumann solve
 // y = A_rr^{-1} r_i,r (into vloc).
 template <typename T>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(APPLY_THREADS)
+__global__ void __launch_bounds__(APPLY_THREADS)
 k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac, const T* __restrict__ Phi, const double* __restrict__ delta,
                 const double* __restrict__ r, const double* __restrict__ t, T* __restrict__ vloc,
                 double* __restrict__ rcl, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  const SubDesc s = subs[blockIdx.x >> 1];   // a cluster of two CTAs per subdomain
+  // one cluster (of one or two CTAs, the launch decides) per subdomain
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
+  const SubDesc s = subs[blockIdx.x / nrank];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const int Q = px * py, n = Q * pz;
   Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
@@ -1284,15 +1291,19 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
       col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, rg + r0, acc);
     };
     ring_run(ring, nch, src, use, err);
-    col_finish<T>(L, acc, part, [&](int cc, T sum) { pb[cc] = sum; });
-    cluster.sync();
-    if (rank == 0)
-      for (int c = threadIdx.x; c < s.nc; c += blockDim.x) {
-        T sum = T(0);
-        for (int r = 0; r < nrank; ++r) sum += cluster.map_shared_rank(pb, r)[c];
-        rcl[s.cofs + c] = (double)sum;
-      }
-    cluster.sync();   // both CTAs' partial buffers are free again
+    if (nrank == 1) {
+      col_finish<T>(L, acc, part, [&](int cc, T sum) { rcl[s.cofs + cc] = (double)sum; });
+    } else {
+      col_finish<T>(L, acc, part, [&](int cc, T sum) { pb[cc] = sum; });
+      cluster.sync();
+      if (rank == 0)
+        for (int c = threadIdx.x; c < s.nc; c += blockDim.x) {
+          T sum = T(0);
+          for (int r = 0; r < nrank; ++r) sum += cluster.map_shared_rank(pb, r)[c];
+          rcl[s.cofs + c] = (double)sum;
+        }
+      cluster.sync();   // both CTAs' partial buffers are free again
+    }
   }
   sweep_stream<T>(ring, fac + s.offN, px, py, pz, v, tq, part, pb, err);
   if (rank == 0)
@@ -1438,13 +1449,31 @@ void launch_piece_alpha(const MeshDev& m, const double* alpha, const int* plo, c
   k_piece_alpha<<<blocks, 256, 0, st>>>(m, alpha, plo, phi, npx, npy, npz, pw);
 }
 
+// per-subdomain apply kernels: nsub clusters of csize CTAs (one or two)
+template <typename... KArgs, typename... Args>
+void launch_clustered(void (*kern)(KArgs...), int nsub, int csize, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nsub * csize));
+  cfg.blockDim = dim3(APPLY_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename T>
 void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, double* z, int mode, cudaStream_t st) {
   if (L.maxQD == 0) return;
   BDDC_COUNT(1);
   size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxND + 3 * (size_t)L.maxQD + 2);
-  k_dirichlet_solve<T><<<2 * L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.m, (const T*)L.facD, r, t, z, mode,
-                                                             L.err);
+  launch_clustered(k_dirichlet_solve<T>, L.nsub, L.apply_cluster, sm, st, L.subs_lpt, L.m, (const T*)L.facD, r, t,
+                   z, mode, L.err);
 }
 
 template <typename T>
@@ -1452,8 +1481,8 @@ void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cuda
   size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNB + 1 + L.maxNN + L.maxQN +
                                           2 * (size_t)std::max(L.maxQN, L.maxNc) + 2);
   BDDC_COUNT(1);
-  k_neumann_solve<T><<<2 * L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.m, (const T*)L.facN, (const T*)L.Phi, L.delta, r,
-                                                       t, (T*)L.vloc, L.rcl, L.err);
+  launch_clustered(k_neumann_solve<T>, L.nsub, L.apply_cluster, sm, st, L.subs_lpt, L.m, (const T*)L.facN,
+                   (const T*)L.Phi, L.delta, r, t, (T*)L.vloc, L.rcl, L.err);
 }
 
 template <typename T>
