@@ -203,6 +203,14 @@ int bddc_solve_host(const bddc_mesh* mesh, const bddc_partition* part,
 /* Sizes and timings of a handle. */
 int bddc_get_info(const bddc_handle* h, bddc_info_t* info);
 
+/* Overrides the autotuned apply schedule of a handle: ctas_per_subdomain = 1
+ * or 2 CTAs per subdomain in the local solves of bddc_apply (2: a thread-block
+ * cluster whose CTAs share each slot's rows).  Both give the same
+ * preconditioner up to the summation order of the partial sums.  Drops the
+ * handle's captured PCG graph (recaptured by the next pcg_solve).  The paper
+ * has no counterpart; BDDC_ERR_ARG for other values. */
+int bddc_set_apply_schedule(bddc_handle* h, int ctas_per_subdomain);
+
 /* Copies the coarse basis of subdomain `sub` restricted to the subdomain's
  * box-surface nodes into phi_host (n_surface x n_c,i, row-major, FP64), the
  * global coarse numbers of its columns into gid_host and the box-surface node

@@ -81,6 +81,7 @@ def _load():
     lib.bddc_solve_host.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), dp, dp, dp,
                                     C.c_double, C.POINTER(Stats)]
     lib.bddc_get_info.argtypes = [vp, C.POINTER(Info)]
+    lib.bddc_set_apply_schedule.argtypes = [vp, C.c_int]
     lib.bddc_analyze.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), C.POINTER(Analysis)]
     lib.bddc_get_coarse_basis.argtypes = [vp, ip, dp, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -89,7 +90,8 @@ def _load():
     lib.bddc_last_error.argtypes = [vp]
     lib.bddc_last_error.restype = C.c_char_p
     for f in ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
-              "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy"):
+              "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
+              "bddc_set_apply_schedule"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -98,7 +100,7 @@ lib = _load()
 
 EXPORTS = ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
            "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
-           "bddc_last_error")
+           "bddc_last_error", "bddc_set_apply_schedule")
 
 
 def _check(code: int, handle=None):
@@ -207,6 +209,10 @@ class BDDC:
                                                    device="cuda")
         _check(lib.bddc_gradient(self._handle, _ptr(u), _ptr(lam), _ptr(g), _stream()), self._handle)
         return g
+
+    def set_apply_schedule(self, ctas_per_subdomain: int):
+        """bddc_set_apply_schedule: 1 or 2 CTAs per subdomain in the apply's local solves."""
+        _check(lib.bddc_set_apply_schedule(self._handle, int(ctas_per_subdomain)), self._handle)
 
     def info(self) -> dict:
         i = Info()

@@ -1041,6 +1041,20 @@ extern "C" int bddc_solve_host(const bddc_mesh* mesh, const bddc_partition* part
   return rc;
 }
 
+extern "C" int bddc_set_apply_schedule(bddc_handle* h, int ctas_per_subdomain) {
+  if (!h) return BDDC_ERR_ARG;
+  ABI_BEGIN
+  if (ctas_per_subdomain != 1 && ctas_per_subdomain != 2)
+    throw BddcError(BDDC_ERR_ARG, "ctas_per_subdomain must be 1 or 2");
+  CK(cudaSetDevice(h->device));
+  CK(cudaDeviceSynchronize());
+  h->L.apply_cluster = ctas_per_subdomain;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+  return BDDC_OK;
+  ABI_END(h)
+}
+
 extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   if (!h || !info) return BDDC_ERR_ARG;
   info->n_sub = (int)h->subs.size();
