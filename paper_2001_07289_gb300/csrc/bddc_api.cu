@@ -204,6 +204,10 @@ struct bddc_handle {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t cap = nullptr;
+  // the coarse solve of the apply runs on aux beside the Neumann sweeps;
+  // fork and join order it against the caller's stream
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* xw = nullptr;
   long long graph_body_launches = 0;
   double* pinned = nullptr;
@@ -252,6 +256,9 @@ struct bddc_handle {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
+    if (aux) cudaStreamDestroy(aux);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     free_setup_only();
     for (auto& v : allocs) block_cache().put(device, v.first, v.second);
     if (pinned) cudaFreeHost(pinned);
@@ -492,7 +499,10 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     // memory ring and keeps one subdomain's vectors in shared memory
     const int es = h->local_double ? 8 : 4;
     const LocalLaunch& L = h->L;
-    const size_t smem = (size_t)NBUF * CHB + 8 * NBUF + (size_t)es * (512 + L.maxNB + 1 + L.maxNN + L.maxQN + 2);
+    const size_t ring = (size_t)NBUF * CHB + 16 * NBUF;
+    const size_t vec = std::max({(size_t)L.maxNN + 3 * (size_t)L.maxQN, (size_t)L.maxND + 3 * (size_t)L.maxQD,
+                                 (size_t)L.maxNB + 1 + L.maxNc});
+    const size_t smem = ring + (size_t)es * (APPLY_THREADS + vec + 2);
     bool rows_ok = true;
     for (const SubDesc& s : h->subs) {
       const int QN = (s.w[0] + 1) * (s.w[1] + 1);
@@ -503,6 +513,14 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     if (!rows_ok || L.maxQN > 2048 || L.maxNB > 2048 || L.maxNc > 2048 || smem > 227 * 1024)
       throw BddcError(BDDC_ERR_UNSUPPORTED, "subdomains too large for the streamed local solves "
                                             "(at most 341 FP64 / 682 FP32 nodes per plane and 1024 coarse DOFs)");
+  }
+  {
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    // the coarse chain is latency-bound: its blocks go first when SMs free up
+    CK(cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, hi));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   }
   h->launch_base = g_launches;
   // events: 0 start, 1 weights done, 2 Dirichlet, 3 Neumann, 4 basis, 5 assembly, 6 coarse factor
@@ -621,7 +639,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   configure_mf_kernels();
   mf_assemble(h->mf, L, h->color_subs, h->color_count, h->color_off, st);
   CK(cudaEventRecord(ev[5], st));
-  mf_factor(h->mf, h->err, st);
+  mf_factor(h->mf, h->err, st, h->aux, h->ev_fork, h->ev_join);
   CK(cudaEventRecord(ev[6], st));
   CK(cudaGetLastError());
   // apply / PCG work vectors
@@ -656,18 +674,32 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// The coarse correction and the local Neumann corrections are solved in
+// a-orthogonal spaces (Definition 1: each v_k from its own V_k), so once r_c
+// is formed the coarse solve runs on the auxiliary stream while the Neumann
+// sweeps run on st; v_i needs both.
+template <typename T>
+void apply_core(bddc_handle* h, const LocalLaunch& L, const double* r, double* z, double* uI, double* t, double* rc,
+                double* uc, double* wf, cudaStream_t st) {
+  launch_dirichlet<T>(L, r, nullptr, uI, 0, st);                       // V1: u_I = A_II^{-1} r_I
+  launch_operator(h->m, h->alpha, uI, t, nullptr, RED_BLOCKS, st);      // A u_I
+  launch_neumann_rhs<T>(L, r, t, st);                                  // r_i, Phi_i^T r_i
+  CK(cudaEventRecord(h->ev_fork, st));
+  CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+  launch_coarse_gather(h->cptr, h->cent, L.rcl, rc, h->n_coarse, h->aux);
+  mf_solve(h->mf, rc, uc, wf, h->aux);                                 // A_c u_c = r_c
+  CK(cudaEventRecord(h->ev_join, h->aux));
+  launch_neumann<T>(L, r, t, st);                                      // y = A_rr^{-1} r_i,r
+  CK(cudaStreamWaitEvent(st, h->ev_join, 0));
+  launch_neumann_finish<T>(L, uc, st);                                 // v_i on the surface
+  launch_interface_gather(h->m, L.subs, L.delta, L.vgam, z, st);       // E v
+  launch_operator(h->m, h->alpha, z, t, nullptr, RED_BLOCKS, st);      // A (E v)
+  launch_dirichlet<T>(L, r, t, z, 1, st);                              // (I - P) E v + u_I
+}
+
 template <typename T>
 void apply_impl(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
-  const LocalLaunch& L = h->L;
-  launch_dirichlet<T>(L, r, nullptr, h->uI, 0, st);                    // V1: u_I = A_II^{-1} r_I
-  launch_operator(h->m, h->alpha, h->uI, h->t, nullptr, RED_BLOCKS, st);  // A u_I
-  launch_neumann<T>(L, r, h->t, st);                                   // r_i, Phi^T r_i, y
-  launch_coarse_gather(h->cptr, h->cent, L.rcl, h->rc, h->n_coarse, st);
-  mf_solve(h->mf, h->rc, h->uc, h->mf.W, st);                          // A_c u_c = r_c
-  launch_neumann_finish<T>(L, h->uc, st);                              // v_i on the surface
-  launch_interface_gather(h->m, L.subs, L.delta, L.vgam, z, st);       // E v
-  launch_operator(h->m, h->alpha, z, h->t, nullptr, RED_BLOCKS, st);   // A (E v)
-  launch_dirichlet<T>(L, r, h->t, z, 1, st);                           // (I - P) E v + u_I
+  apply_core<T>(h, h->L, r, z, h->uI, h->t, h->rc, h->uc, h->mf.W, st);
 }
 
 void apply(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
@@ -1210,15 +1242,7 @@ void apply_noalloc_impl(bddc_handle* h, unsigned char* base, const double* r, do
   // the array keeps the previous call's contents; the interior solve writes
   // only interior nodes, so the rest of uI must start at zero
   CK(cudaMemsetAsync(uI, 0, sizeof(double) * N, st));
-  launch_dirichlet<T>(L, r, nullptr, uI, 0, st);
-  launch_operator(h->m, h->alpha, uI, t, nullptr, RED_BLOCKS, st);
-  launch_neumann<T>(L, r, t, st);
-  launch_coarse_gather(h->cptr, h->cent, L.rcl, rc, nc, st);
-  mf_solve(h->mf, rc, uc, wf, st);
-  launch_neumann_finish<T>(L, uc, st);
-  launch_interface_gather(h->m, L.subs, L.delta, L.vgam, z, st);
-  launch_operator(h->m, h->alpha, z, t, nullptr, RED_BLOCKS, st);
-  launch_dirichlet<T>(L, r, t, z, 1, st);
+  apply_core<T>(h, L, r, z, uI, t, rc, uc, wf, st);
 }
 
 size_t noalloc_bytes_needed(const bddc_handle* h) {

@@ -22,6 +22,7 @@
 // fronts (rows split across CTAs forward, columns backward).  Everything is
 // summed in a fixed order (no atomics).
 #include <stdexcept>
+#include <string>
 
 #include "common.cuh"
 #include "dense.cuh"
@@ -201,24 +202,25 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
     so += (long long)(P.np[f] + P.nu[f]) * P.np[f];
   }
   P.spool = so;
-  P.diag_items.clear(); P.g_items.clear(); P.trtri_steps.clear();
+  P.inv_items.assign(P.nlevel, std::vector<std::vector<int>>(2));
   P.toff.resize(nf);
   long long to = 0;
   for (int f = 0; f < nf; ++f) {
     const int npt = (P.np[f] + FNB - 1) / FNB, nut = (P.nu[f] + FNB - 1) / FNB;
     P.toff[f] = to;
     to += (long long)P.np[f] * P.np[f];
-    for (int t = 0; t < npt; ++t) P.diag_items.insert(P.diag_items.end(), {f, t, t, 0});
+    std::vector<std::vector<int>>& lv = P.inv_items[P.level_of[f]];
+    for (int t = 0; t < npt; ++t) lv[0].insert(lv[0].end(), {f, t, t, 0});
     // doubling: blocks of 2 hb tiles, A = first hb tiles, C = the rest
     int q = 0;
     for (int hb = 1; hb < npt; hb *= 2, ++q) {
-      if ((int)P.trtri_steps.size() <= q) P.trtri_steps.emplace_back();
+      if ((int)lv.size() <= 2 + q) lv.emplace_back();
       for (int b0 = 0; b0 + hb < npt; b0 += 2 * hb)
         for (int r = b0 + hb; r < std::min(b0 + 2 * hb, npt); ++r)
-          for (int c = b0; c < b0 + hb; ++c) P.trtri_steps[q].insert(P.trtri_steps[q].end(), {f, r, c, hb});
+          for (int c = b0; c < b0 + hb; ++c) lv[2 + q].insert(lv[2 + q].end(), {f, r, c, hb});
     }
     for (int u = 0; u < nut; ++u)
-      for (int s2 = 0; s2 < npt; ++s2) P.g_items.insert(P.g_items.end(), {f, u, s2, 0});
+      for (int s2 = 0; s2 < npt; ++s2) lv[1].insert(lv[1].end(), {f, u, s2, 0});
     // solve matrices: Linv_P = L_P^-1 (np^3/6), G = L_UP Linv_P (nu np^2/2)
     P.flops += (double)P.np[f] * P.np[f] * P.np[f] / 6.0 + (double)P.nu[f] * P.np[f] * P.np[f] / 2.0;
   }
@@ -687,15 +689,16 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
     push(P.step_trsm[k]);
     push(P.step_syrk[k]);
   }
-  P.inv_off.clear(); P.inv_len.clear();
-  auto push_inv = [&](const std::vector<int>& v) {
-    P.inv_off.push_back((long long)all.size() / 4);
-    P.inv_len.push_back((int)v.size() / 4);
-    all.insert(all.end(), v.begin(), v.end());
-  };
-  push_inv(P.diag_items);
-  push_inv(P.g_items);
-  for (size_t q = 0; q < P.trtri_steps.size(); ++q) push_inv(P.trtri_steps[q]);
+  P.inv_off.clear(); P.inv_len.clear(); P.inv_lvl_base.clear();
+  for (const auto& lv : P.inv_items) {
+    P.inv_lvl_base.push_back((int)P.inv_off.size());
+    for (const std::vector<int>& v : lv) {
+      P.inv_off.push_back((long long)all.size() / 4);
+      P.inv_len.push_back((int)v.size() / 4);
+      all.insert(all.end(), v.begin(), v.end());
+    }
+  }
+  P.inv_lvl_base.push_back((int)P.inv_off.size());
   P.tscratch = (double*)tmp_alloc(sizeof(double) * std::max<long long>(P.tpool, 1));
   P.d_toff = up(P.toff, alloc, st);
   P.d_lists = (int4*)tmp_alloc(sizeof(int) * std::max<size_t>(all.size(), 4));
@@ -787,12 +790,32 @@ void mf_assemble(const MFPlan& P, const LocalLaunch& L, const int* color_subs, c
   }
 }
 
-void mf_factor(const MFPlan& P, int* err, cudaStream_t st) {
+static void CK_MF(cudaError_t e) {
+  if (e != cudaSuccess) throw std::runtime_error(std::string("coarse factor: ") + cudaGetErrorString(e));
+}
+
+// Solve matrices of the fronts of one level: Linv_P by tile rows (diagonal
+// inverses, then the doubling steps), then G = L_UP Linv_P.  They read only
+// the level's own factor, final once its last panel step is done.
+static void mf_solve_matrices(const MFPlan& P, const MFDev& d, int l, cudaStream_t st) {
+  const int b = P.inv_lvl_base[l], e = P.inv_lvl_base[l + 1];
+  if (P.inv_len[b]) { BDDC_COUNT(1); k_mf_inv_diag<<<P.inv_len[b], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[b]); }
+  for (int q = b + 2; q < e; ++q)
+    if (P.inv_len[q]) {
+      BDDC_COUNT(2);
+      k_mf_trtri<<<P.inv_len[q], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[q], 0);
+      k_mf_trtri<<<P.inv_len[q], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[q], 1);
+    }
+  if (P.inv_len[b + 1]) { BDDC_COUNT(1); k_mf_g<<<P.inv_len[b + 1], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[b + 1]); }
+}
+
+void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join) {
   if (P.nfront == 0) return;
   MFDev d = dev_of(P);
   const int* slots = P.d_blob + P.blob_slots;
   const size_t dsm = sizeof(DenseSmem<double>);
   const size_t tsm = 2 * FNB * (FNB + 1) * sizeof(double);
+  const bool two = aux && fork && join;
   size_t step = 0;
   for (int l = P.nlevel - 1; l >= 0; --l) {
     for (int s = 0; s < P.maxslot; ++s) {
@@ -815,16 +838,16 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st) {
       if (ntr) { BDDC_COUNT(1); k_mf_trsm<<<ntr, BDDC_THREADS, tsm, st>>>(d, lt); }
       if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, dsm, st>>>(d, ls, P.fscratch, err); }
     }
-  }
-  // solve matrices: Linv_P by tile rows, then G = L_UP Linv_P
-  if (P.inv_len[0]) { BDDC_COUNT(1); k_mf_inv_diag<<<P.inv_len[0], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[0]); }
-  for (size_t q = 2; q < P.inv_len.size(); ++q)
-    if (P.inv_len[q]) {
-      BDDC_COUNT(2);
-      k_mf_trtri<<<P.inv_len[q], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[q], 0);
-      k_mf_trtri<<<P.inv_len[q], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[q], 1);
+    if (two) {
+      CK_MF(cudaEventRecord(fork, st));
+      CK_MF(cudaStreamWaitEvent(aux, fork, 0));
     }
-  if (P.inv_len[1]) { BDDC_COUNT(1); k_mf_g<<<P.inv_len[1], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[1]); }
+    mf_solve_matrices(P, d, l, two ? aux : st);
+  }
+  if (two) {
+    CK_MF(cudaEventRecord(join, aux));
+    CK_MF(cudaStreamWaitEvent(st, join, 0));
+  }
   BDDC_COUNT(1);
   k_mf_transpose<<<dim3(P.nfront, 16), BDDC_THREADS, 0, st>>>(d);
 }

@@ -45,6 +45,10 @@ template <typename T> void configure_local_kernels();
 template <typename T> size_t dense_smem();
 template <typename T>
 void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, double* z, int mode, cudaStream_t st);
+// weighted restriction r_i of r - t and the local coarse right-hand sides
+// rc_i = Phi_i^T r_i (into L.rcl)
+template <typename T> void launch_neumann_rhs(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st);
+// constrained Neumann solves y = A_rr^{-1} r_i,r (into L.vloc)
 template <typename T> void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st);
 template <typename T> void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t st);
 void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st);
@@ -95,10 +99,12 @@ struct MFPlan {
   long long* d_soff = nullptr;
   // L_P^{-1} by recursive doubling: at level q (half block hb = 2^q tiles)
   // the items {front, r, c, hb} cover every tile of the off-diagonal blocks
-  std::vector<std::vector<int>> trtri_steps;
-  std::vector<int> diag_items, g_items;        // int4 lists: {front, t, t, 0}, {front, ut, st, 0}
-  std::vector<long long> inv_off;              // device offsets of these lists
+  // per level of the front tree: [0] diagonal tiles {front, t, t, 0},
+  // [1] G tiles {front, ut, st, 0}, [2 + q] doubling step q
+  std::vector<std::vector<std::vector<int>>> inv_items;
+  std::vector<long long> inv_off;              // device offsets of these lists, level by level
   std::vector<int> inv_len;
+  std::vector<int> inv_lvl_base;               // per level: first index into inv_off / inv_len
   std::vector<long long> toff;                 // per front: np x np block of the product scratch
   long long tpool = 0;
   long long* d_toff = nullptr;
@@ -130,7 +136,10 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
                const std::function<void*(size_t)>& tmp_alloc, cudaStream_t st);
 void mf_assemble(const MFPlan& P, const LocalLaunch& L, const int* color_subs, const int* color_count_host,
                  const int* color_offset_host, cudaStream_t st);
-void mf_factor(const MFPlan& P, int* err, cudaStream_t st);
+// aux, fork, join (may be null): a second stream and two events; each
+// level's solve matrices are then built on aux while st factors the levels
+// above it, and st waits for aux before it returns
+void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join);
 // x = A_c^{-1} b; W: work vector pool of P.wpool doubles
 void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream_t st);
 void configure_mf_kernels();

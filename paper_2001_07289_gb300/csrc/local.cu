@@ -1004,8 +1004,6 @@ __global__ void k_transpose(const SubDesc* __restrict__ subs, const T* __restric
 // With ncol <= blockDim the threads form G = blockDim / ncol row groups (one
 // column each); otherwise every thread owns up to 4 columns.
 // ---------------------------------------------------------------------------
-constexpr int APPLY_THREADS = 512;
-
 struct ColLayout {
   int ncol, G, grp, col;  // col < 0: idle thread
 };
@@ -1236,75 +1234,102 @@ k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restri
   }
 }
 
-// Weighted restriction r_i = D_i R_i (r - t) on the box surface, the local
-// coarse right-hand side rc_i = Phi_i^T r_i, and the constrained Neumann solve
-// y = A_rr^{-1} r_i,r (into vloc).
-template <typename T>
-__global__ void __launch_bounds__(APPLY_THREADS)
-k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac, const T* __restrict__ Phi, const double* __restrict__ delta,
-                const double* __restrict__ r, const double* __restrict__ t, T* __restrict__ vloc,
-                double* __restrict__ rcl, int* err) {
-  extern __shared__ __align__(128) unsigned char smraw[];
-  // one cluster (of one or two CTAs, the launch decides) per subdomain
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
-  const SubDesc s = subs[blockIdx.x / nrank];
+// Weighted restriction r_i = D_i R_i (r - t) on the box surface into rg;
+// returns through set_v whether node b also starts the Neumann right-hand
+// side (the primal vertices are eliminated and keep zero).
+template <typename T, typename F>
+__device__ inline void neumann_restrict(const SubDesc& s, const MeshDev& m, const double* __restrict__ delta,
+                                        const double* __restrict__ r, const double* __restrict__ t, F&& put) {
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
-  const int Q = px * py, n = Q * pz;
-  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
-  T* rg = part + APPLY_THREADS;
-  T* v = rg + s.nB + 1;
-  T* tq = v + n;
-  T* pb = tq + Q;   // 2 max(Q, nc) partial sums
-  ring_init(ring);
-  for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = T(0);
-  __syncthreads();
   for (int b = threadIdx.x; b < s.nB; b += blockDim.x) {
     int ix, iy, iz;
     surf_coords(b, px, py, pz, ix, iy, iz);
     long long gi = nodeid(m.NX, m.NY, s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz);
     double d = delta[s.offB + b];
     double val = (d == 0.0) ? 0.0 : d * (r[gi] - t[gi]);
-    rg[b] = (T)val;
-    if (!neumann_fixed(m, s, ix, iy, iz)) v[ix + px * (iy + py * iz)] = (T)val;
+    put(b, ix + px * (iy + py * iz), !neumann_fixed(m, s, ix, iy, iz), (T)val);
   }
+}
+
+// The local coarse right-hand side rc_i = Phi_i^T r_i of the weighted
+// restriction r_i = D_i R_i (r - t), in the local precision: columns of Phi
+// accumulate over streamed rows, the rows split between the CTAs of the
+// cluster and their partial sums added in rank order.
+template <typename T>
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_neumann_rhs(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ Phi,
+              const double* __restrict__ delta, const double* __restrict__ r, const double* __restrict__ t,
+              double* __restrict__ rcl, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
+  const SubDesc s = subs[blockIdx.x / nrank];
+  if (s.nc == 0) return;   // both CTAs of the cluster see the same subdomain
+  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
+  T* rg = part + APPLY_THREADS;
+  T* pb = rg + s.nB + 1;   // nc partial sums
+  ring_init(ring);
+  neumann_restrict<T>(s, m, delta, r, t, [&](int b, int, bool, T val) { rg[b] = val; });
   __syncthreads();
-  if (s.nc > 0) {
-    // rc_i = Phi_i^T r_i in the local precision: columns of Phi accumulate
-    // over streamed rows, the rows split between the two CTAs and their
-    // partial sums added in rank order
-    const int R = rows_per_chunk(s.nc, (int)sizeof(T));
-    const int half = split_rows(s.nB, s.nc, (int)sizeof(T), nrank);
-    const int rlo = min(s.nB, rank * half), rhi = min(s.nB, rlo + half);
-    const int nch = (rhi - rlo + R - 1) / R;
-    const T* P = Phi + s.offPhi;
-    const ColLayout L = col_layout(s.nc);
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    auto src = [&](int c, const void*& p, unsigned& bytes) {
-      const int r0 = rlo + c * R, nr = min(R, rhi - r0);
-      p = P + (long long)r0 * s.nc;
-      bytes = (unsigned)(nr * s.nc * sizeof(T));
-    };
-    auto use = [&](int c, const unsigned char* raw) {
-      const int r0 = rlo + c * R, nr = min(R, rhi - r0);
-      col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, rg + r0, acc);
-    };
-    ring_run(ring, nch, src, use, err);
-    if (nrank == 1) {
-      col_finish<T>(L, acc, part, [&](int cc, T sum) { rcl[s.cofs + cc] = (double)sum; });
-    } else {
-      col_finish<T>(L, acc, part, [&](int cc, T sum) { pb[cc] = sum; });
-      cluster.sync();
-      if (rank == 0)
-        for (int c = threadIdx.x; c < s.nc; c += blockDim.x) {
-          T sum = T(0);
-          for (int r = 0; r < nrank; ++r) sum += cluster.map_shared_rank(pb, r)[c];
-          rcl[s.cofs + c] = (double)sum;
-        }
-      cluster.sync();   // both CTAs' partial buffers are free again
-    }
+  const int R = rows_per_chunk(s.nc, (int)sizeof(T));
+  const int half = split_rows(s.nB, s.nc, (int)sizeof(T), nrank);
+  const int rlo = min(s.nB, rank * half), rhi = min(s.nB, rlo + half);
+  const int nch = (rhi - rlo + R - 1) / R;
+  const T* P = Phi + s.offPhi;
+  const ColLayout L = col_layout(s.nc);
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  auto src = [&](int c, const void*& p, unsigned& bytes) {
+    const int r0 = rlo + c * R, nr = min(R, rhi - r0);
+    p = P + (long long)r0 * s.nc;
+    bytes = (unsigned)(nr * s.nc * sizeof(T));
+  };
+  auto use = [&](int c, const unsigned char* raw) {
+    const int r0 = rlo + c * R, nr = min(R, rhi - r0);
+    col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, rg + r0, acc);
+  };
+  ring_run(ring, nch, src, use, err);
+  if (nrank == 1) {
+    col_finish<T>(L, acc, part, [&](int cc, T sum) { rcl[s.cofs + cc] = (double)sum; });
+  } else {
+    col_finish<T>(L, acc, part, [&](int cc, T sum) { pb[cc] = sum; });
+    cluster.sync();
+    if (rank == 0)
+      for (int c = threadIdx.x; c < s.nc; c += blockDim.x) {
+        T sum = T(0);
+        for (int q = 0; q < nrank; ++q) sum += cluster.map_shared_rank(pb, q)[c];
+        rcl[s.cofs + c] = (double)sum;
+      }
+    cluster.sync();   // the peer's reads of this CTA's partial sums are done
   }
+}
+
+// The constrained Neumann solve y = A_rr^{-1} r_i,r (into vloc) of the
+// weighted restriction r_i = D_i R_i (r - t).
+template <typename T>
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
+                const double* __restrict__ delta, const double* __restrict__ r, const double* __restrict__ t,
+                T* __restrict__ vloc, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  // one cluster (of one or two CTAs, the launch decides) per subdomain
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const SubDesc s = subs[blockIdx.x / (int)cluster.num_blocks()];
+  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+  const int Q = px * py, n = Q * pz;
+  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
+  T* v = part + APPLY_THREADS;
+  T* tq = v + n;
+  T* pb = tq + Q;   // 2 Q partial sums
+  ring_init(ring);
+  for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = T(0);
+  __syncthreads();
+  neumann_restrict<T>(s, m, delta, r, t, [&](int, int l, bool free_node, T val) {
+    if (free_node) v[l] = val;
+  });
+  __syncthreads();
   sweep_stream<T>(ring, fac + s.offN, px, py, pz, v, tq, part, pb, err);
   if (rank == 0)
     for (int l = threadIdx.x; l < n; l += blockDim.x) vloc[s.offVec + l] = v[l];
@@ -1433,6 +1458,7 @@ void configure_local_kernels() {
   cudaFuncSetAttribute(k_phi_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_dirichlet_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_neumann_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(k_neumann_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_neumann_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
@@ -1477,12 +1503,20 @@ void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, do
 }
 
 template <typename T>
-void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
-  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNB + 1 + L.maxNN + L.maxQN +
-                                          2 * (size_t)std::max(L.maxQN, L.maxNc) + 2);
+void launch_neumann_rhs(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
+  if (L.maxNc == 0) return;
+  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNB + 1 + L.maxNc + 2);
   BDDC_COUNT(1);
-  launch_clustered(k_neumann_solve<T>, L.nsub, L.apply_cluster, sm, st, L.subs_lpt, L.m, (const T*)L.facN,
-                   (const T*)L.Phi, L.delta, r, t, (T*)L.vloc, L.rcl, L.err);
+  launch_clustered(k_neumann_rhs<T>, L.nsub, L.apply_cluster, sm, st, L.subs_lpt, L.m, (const T*)L.Phi, L.delta, r,
+                   t, L.rcl, L.err);
+}
+
+template <typename T>
+void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
+  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNN + 3 * (size_t)L.maxQN + 2);
+  BDDC_COUNT(1);
+  launch_clustered(k_neumann_solve<T>, L.nsub, L.apply_cluster, sm, st, L.subs_lpt, L.m, (const T*)L.facN, L.delta,
+                   r, t, (T*)L.vloc, L.err);
 }
 
 template <typename T>
@@ -1500,6 +1534,8 @@ template void configure_local_kernels<double>();
 template void launch_dirichlet<float>(const LocalLaunch&, const double*, const double*, double*, int, cudaStream_t);
 template void launch_dirichlet<double>(const LocalLaunch&, const double*, const double*, double*, int, cudaStream_t);
 template void launch_neumann<float>(const LocalLaunch&, const double*, const double*, cudaStream_t);
+template void launch_neumann_rhs<float>(const LocalLaunch&, const double*, const double*, cudaStream_t);
+template void launch_neumann_rhs<double>(const LocalLaunch&, const double*, const double*, cudaStream_t);
 template void launch_neumann<double>(const LocalLaunch&, const double*, const double*, cudaStream_t);
 template void launch_neumann_finish<float>(const LocalLaunch&, const double*, cudaStream_t);
 template void launch_neumann_finish<double>(const LocalLaunch&, const double*, cudaStream_t);

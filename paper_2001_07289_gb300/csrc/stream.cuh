@@ -20,6 +20,7 @@ namespace bddc {
 constexpr int NBUF = 6;
 constexpr int CHB = 24576;
 constexpr long long WAIT_TRIES = 1LL << 22;
+constexpr int APPLY_THREADS = 512;   // threads of the streaming apply kernels
 
 __device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
