@@ -165,13 +165,24 @@ constexpr int SCHUR_THREADS = 512;   // 32 x 16 owner grid
 // Register-resident plane step for Q <= 32 RI and Q <= 16 RJ (FP32): thread
 // (tr, tc) = (t / 16, t % 16) holds the entries (tr + 32 a, tc + 16 b) of S_k
 // in x[a][b] (entries above the diagonal or past Q are carried along and never
-// used), so a pivot costs RI + RJ shared-memory reads of the pivot column and
-// RI RJ FMAs per thread.  Tm: Q x Q shared memory for S_{k-1}^{-1} B_k^T.
-// Writes S_k^{-1} to slot.
+// used).  The pivots go in blocks K of SB = 16: the sweep over the pivots of K
+// equals, with D = X_KK,
+//   X_ij <- X_ij - X_iK D^{-1} X_Kj,  X_iK <- X_iK D^{-1},  X_KK <- -D^{-1}
+// (i, j outside K), so one warp inverts D by 16 single-pivot sweeps, the block
+// forms W = X_:K D^{-1}, and every thread applies the rank-16 update to its
+// registers: three barriers per 16 pivots.  Tm: Q x Q shared memory for
+// S_{k-1}^{-1} B_k^T; pw: the panel buffers (schur_panel_floats).  Writes
+// S_k^{-1} to slot.
+constexpr int SB = 16;    // pivots per block (the column block of one tc stride)
+constexpr int PST = 18;   // row stride of the panel buffers: 8-byte rows, conflict-free LDS.64
+constexpr int PNR = 192;  // panel rows: max(32 RI, 16 RJ) of the register grid
+__host__ __device__ constexpr int schur_panel_floats() { return 4 * PNR * PST + SB * (SB + 1); }
+
 template <int RI, int RJ>
 __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict__ slot,
-                                 const float* __restrict__ Sp, const float* __restrict__ Bd, float* __restrict__ cb,
-                                 float* __restrict__ rb, float* __restrict__ Tm, int* err, int code, int sub_id) {
+                                 const float* __restrict__ Sp, const float* __restrict__ Bd, float* __restrict__ pw,
+                                 float* __restrict__ Tm, int* err, int code, int sub_id) {
+  static_assert(32 * RI <= PNR && 16 * RJ <= PNR, "panel rows");
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
   if (k > 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -224,88 +235,136 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict
       x[ai][bj] = v;
     }
   }
-  auto publish_pivot = [&](int q, float d) {
-    if (!(d > 0.0f)) { set_error(err, code, sub_id); d = 1.0f; }
-    rb[q & 1] = __frcp_rn(d);
-  };
-  if (tc == 0) {
-#pragma unroll
-    for (int ai = 0; ai < RI; ++ai) {
-      const int i = tr + 32 * ai;
-      if (i < Q) cb[i] = x[ai][0];
-    }
-  }
-  if (threadIdx.x == 0) publish_pivot(0, x[0][0]);
-  __syncthreads();
-  for (int p = 0; p < Q; ++p) {
-    const float* c = cb + (p & 1) * Q;
-    float* cn = cb + ((p + 1) & 1) * Q;
-    const float r = rb[p & 1];
-    float ci[RI], cj[RJ];
-#pragma unroll
-    for (int t = 0; t < RI; ++t) {
-      const int i = tr + 32 * t;
-      ci[t] = (i < Q) ? c[i] * r : 0.0f;
-    }
-#pragma unroll
-    for (int t = 0; t < RJ; ++t) {
-      const int j = tc + 16 * t;
-      cj[t] = (j < Q) ? c[j] : 0.0f;
-    }
-#pragma unroll
-    for (int ai = 0; ai < RI; ++ai)
-#pragma unroll
-      for (int bj = 0; bj < RJ; ++bj) x[ai][bj] -= ci[ai] * cj[bj];
-    // row p: (p, j) <- c[j] / d, (p, p) <- -1/d;  column p: (i, p) <- c[i] / d
-    if (tr == (p & 31)) {
-      const int pa = p >> 5;
-#pragma unroll
-      for (int ai = 0; ai < RI; ++ai)
-        if (ai == pa) {
-#pragma unroll
-          for (int bj = 0; bj < RJ; ++bj) x[ai][bj] = (tc + 16 * bj == p) ? -r : cj[bj] * r;
-        }
-    }
-    if (tc == (p & 15)) {
-      const int pb = p >> 4;
+  float* Dm = pw + 4 * PNR * PST;   // D^{-1}, SB x (SB + 1)
+  const int nb = (Q + SB - 1) / SB;
+  for (int kb = 0; kb < nb; ++kb) {
+    const int p0 = kb * SB;
+    // double-buffered panels: a buffer is rewritten two blocks later, after
+    // the three barriers of the block in between
+    float* P = pw + (kb & 1) * 2 * PNR * PST;   // P[i][c] = X(i, p0 + c)
+    float* W = P + PNR * PST;                   // W[i][c] = (X_:K D^{-1})(i, c)
+    const int bj0 = p0 >> 4;                     // K = columns tc + 16 bj0
+    const int ai0 = p0 >> 5, tr0 = p0 & 31;      // K = rows tr + 32 ai0, tr in [tr0, tr0 + 16)
+    // (a) the panel from the lower triangle: entries (i, p0 + c) with
+    // i >= p0 + c from the owners of column p0 + c, the rest from the owners
+    // of row p0 + c; zero past Q (and in the columns of a short last block)
+    {
+      const int pc = p0 + tc;
 #pragma unroll
       for (int bj = 0; bj < RJ; ++bj)
-        if (bj == pb) {
+        if (bj == bj0) {
 #pragma unroll
-          for (int ai = 0; ai < RI; ++ai)
-            if (tr + 32 * ai != p) x[ai][bj] = ci[ai];
-        }
-    }
-    // publish column p + 1 and the reciprocal of its pivot
-    const int q = p + 1;
-    if (q < Q) {
-      if (tc == (q & 15)) {
-        const int qb = q >> 4;
-#pragma unroll
-        for (int bj = 0; bj < RJ; ++bj)
-          if (bj == qb) {
-#pragma unroll
-            for (int ai = 0; ai < RI; ++ai) {
-              const int i = tr + 32 * ai;
-              if (i >= q && i < Q) cn[i] = x[ai][bj];
-              if (i == q) publish_pivot(q, x[ai][bj]);
-            }
+          for (int ai = 0; ai < RI; ++ai) {
+            const int i = tr + 32 * ai;
+            if (pc >= Q || i >= Q) P[i * PST + tc] = 0.0f;
+            else if (i >= pc) P[i * PST + tc] = x[ai][bj];
           }
-      }
-      if (tr == (q & 31)) {
-        const int qa = q >> 5;
+        }
+      const int c = tr - tr0, pr = p0 + c;
+      if (c >= 0 && c < SB && pr < Q) {
 #pragma unroll
         for (int ai = 0; ai < RI; ++ai)
-          if (ai == qa) {
+          if (ai == ai0) {
 #pragma unroll
             for (int bj = 0; bj < RJ; ++bj) {
               const int j = tc + 16 * bj;
-              if (j < q) cn[j] = x[ai][bj];
+              if (j < pr) P[j * PST + c] = x[ai][bj];
             }
           }
       }
     }
     __syncthreads();
+    // (b) D^{-1} by one warp: lane m < 16 holds row m of D (identity rows and
+    // columns stand in for pivots past Q), 16 single-pivot sweeps
+    if (threadIdx.x < 32) {
+      const int m = threadIdx.x & 15;
+      float a[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c)
+        a[c] = (p0 + m < Q && p0 + c < Q) ? P[(p0 + m) * PST + c] : (m == c ? 1.0f : 0.0f);
+#pragma unroll
+      for (int q = 0; q < SB; ++q) {
+        float d = __shfl_sync(0xffffffffu, a[q], q);
+        if (!(d > 0.0f)) {
+          if (threadIdx.x == 0) set_error(err, code, sub_id);
+          d = 1.0f;
+        }
+        const float r = __frcp_rn(d);
+        const float cr = a[q] * r;
+#pragma unroll
+        for (int c = 0; c < SB; ++c)
+          if (c != q) {
+            const float rowq = __shfl_sync(0xffffffffu, a[c], q);
+            a[c] = (m == q) ? rowq * r : a[c] - cr * rowq;
+          }
+        a[q] = (m == q) ? -r : cr;
+      }
+      if (threadIdx.x < SB)
+#pragma unroll
+        for (int c = 0; c < SB; ++c) Dm[m * (SB + 1) + c] = -a[c];
+    }
+    __syncthreads();
+    // (c) W = X_:K D^{-1} for the rows outside K (zero elsewhere; unused)
+    {
+      float dcol[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) dcol[c] = Dm[c * (SB + 1) + tc];
+#pragma unroll
+      for (int ai = 0; ai < RI; ++ai) {
+        const int i = tr + 32 * ai;
+        float w = 0.0f;
+        if (i < Q && (i < p0 || i >= p0 + SB)) {
+          const float2* pr = reinterpret_cast<const float2*>(P + i * PST);
+#pragma unroll
+          for (int c2 = 0; c2 < SB / 2; ++c2) {
+            const float2 v = pr[c2];
+            w = fmaf(v.x, dcol[2 * c2], w);
+            w = fmaf(v.y, dcol[2 * c2 + 1], w);
+          }
+        }
+        W[i * PST + tc] = w;
+      }
+    }
+    __syncthreads();
+    // (d) rank-16 update X_ij -= W_i. P_j. (right for i, j outside K; the
+    // K rows and columns are overwritten next)
+#pragma unroll
+    for (int c2 = 0; c2 < SB / 2; ++c2) {
+      float2 pj[RJ];
+#pragma unroll
+      for (int bj = 0; bj < RJ; ++bj) pj[bj] = reinterpret_cast<const float2*>(P + (tc + 16 * bj) * PST)[c2];
+#pragma unroll
+      for (int ai = 0; ai < RI; ++ai) {
+        const float2 wi = reinterpret_cast<const float2*>(W + (tr + 32 * ai) * PST)[c2];
+#pragma unroll
+        for (int bj = 0; bj < RJ; ++bj) {
+          x[ai][bj] = fmaf(-wi.x, pj[bj].x, x[ai][bj]);
+          x[ai][bj] = fmaf(-wi.y, pj[bj].y, x[ai][bj]);
+        }
+      }
+    }
+    // (e) X_iK = W_iK, X_KK = -D^{-1}; rows of K: X_Kj = W_jK
+#pragma unroll
+    for (int bj = 0; bj < RJ; ++bj)
+      if (bj == bj0) {
+#pragma unroll
+        for (int ai = 0; ai < RI; ++ai) {
+          const int i = tr + 32 * ai;
+          x[ai][bj] = (i >= p0 && i < p0 + SB) ? -Dm[(i - p0) * (SB + 1) + tc] : W[i * PST + tc];
+        }
+      }
+    {
+      const int c = tr - tr0;
+      if (c >= 0 && c < SB) {
+#pragma unroll
+        for (int ai = 0; ai < RI; ++ai)
+          if (ai == ai0) {
+#pragma unroll
+            for (int bj = 0; bj < RJ; ++bj)
+              if (bj != bj0) x[ai][bj] = W[(tc + 16 * bj) * PST + c];
+          }
+      }
+    }
   }
 #pragma unroll
   for (int ai = 0; ai < RI; ++ai) {
@@ -342,14 +401,18 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;   // 32 x 16 owner grid
   // register path: FP32 planes of up to 176 nodes (6 x 11 entries per thread)
   constexpr int RI = 6, RJ = 11;
-  const bool regs = std::is_same<T, float>::value && Q <= 32 * RI && Q <= 16 * RJ && (long long)Q * Q <= smem_cap;
+  // shared memory: Tm (Q x Q), then the panel buffers at a 16-byte boundary
+  float* Tm_s = reinterpret_cast<float*>(smraw);
+  float* pw = Tm_s + (((long long)Q * Q + 3) & ~3LL);
+  const bool regs = std::is_same<T, float>::value && Q <= 32 * RI && Q <= 16 * RJ &&
+                    (((long long)Q * Q + 3) & ~3LL) + schur_panel_floats() <= smem_cap;
   for (int k = 0; k < g.gz; ++k) {
     T* slot = base + (long long)k * SS;
     if (regs) {
       if constexpr (std::is_same<T, float>::value)
         schur_plane_regs<RI, RJ>(Q, gx, gy, k, slot, k > 0 ? base + (long long)(k - 1) * SS : nullptr,
-                                 k > 0 ? base + (long long)(g.gz + k - 1) * SS : nullptr, cb, rb, rb + 2,
-                                 err, neumann ? 3 : 2, s.id);
+                                 k > 0 ? base + (long long)(g.gz + k - 1) * SS : nullptr, pw, Tm_s, err,
+                                 neumann ? 3 : 2, s.id);
       continue;
     }
     if (k > 0) {
