@@ -23,6 +23,7 @@ struct DenseSmem {
   T t2[TILE * TLD];
   T rd[TILE];
   T lv[TILE];
+  T r2[TILE];
   int flag;
 };
 
@@ -123,88 +124,91 @@ __device__ void cta_gemm(int M, int N, int K, T alpha,
 }
 
 // Thread map of the 32 x 32 tile routines: thread t owns row t / 8 and the
-// columns t % 8 + 8q, q = 0..3 (no integer division in the loops).
+// columns t % 8 + 8q, q = 0..3 (no integer division in the loops); warp w
+// holds rows 4w .. 4w + 3, so it skips the column groups past its last row
+// and the steps that no longer touch its rows.  FP64 runs at a small fraction
+// of the FP32 rate, so the routines keep floating-point instructions to one
+// multiply-add per touched entry and per step.
+
+__device__ inline float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ inline double rsqrt_t(double x) { return rsqrt(x); }
 
 // Unblocked Cholesky of an n x n (n <= 32) tile in shared memory (ld TLD),
-// lower triangle in place, one barrier per column: step c reads column c
-// unscaled and scales it on the fly (L[i][c] = S[i][c] / L[c][c]); the thread
-// that finishes S[c+1][c+1] takes its square root and reciprocal right away,
-// and column c is written back scaled in step c + 1, when nothing reads it.
-// A non-positive (or NaN) pivot sets sm.flag and is replaced by 1 so that the
+// lower triangle in place, one barrier per column.  Step c updates the
+// trailing entries with the unscaled column c: S[i][j] -= (S[i][c] / d_c)
+// S[j][c] (d_c the pivot), one product per row and one multiply-add per
+// entry; column c - 1 is scaled to L (times 1/sqrt(d)) in step c, when nothing
+// reads it, and the diagonal gets sqrt(d) at the end.  The thread that
+// finishes S[c+1][c+1] takes its reciprocal square root right away.  A
+// non-positive (or NaN) pivot sets sm.flag and is replaced by 1 so that the
 // computation stays finite.
 template <typename T>
 __device__ void tile_chol(T* S, int n, DenseSmem<T>& sm) {
-  const int tid = threadIdx.x, i = tid >> 3, cg = tid & 7;
+  const int tid = threadIdx.x, i = tid >> 3, cg = tid & 7, wlast = 4 * (tid >> 5) + 3;
   auto pivot = [&](int c, T d) {
     if (!(d > T(0))) { sm.flag = 1; d = T(1); }
-    const T l = sqrt(d);
-    sm.lv[c] = l;
-    sm.rd[c] = T(1) / l;
+    const T rl = rsqrt_t(d);
+    sm.lv[c] = d * rl;       // sqrt(d)
+    sm.rd[c] = rl;           // 1 / sqrt(d): scales column c
+    sm.r2[c] = rl * rl;      // 1 / d: the update's factor
   };
   if (tid == 0 && n > 0) pivot(0, S[0]);
   __syncthreads();
   for (int c = 0; c < n; ++c) {
-    const T r = sm.rd[c];
+    if (wlast >= c && i >= c && i < n) {
+      const T t = S[i * TLD + c] * sm.r2[c];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = cg + 8 * q;
-      if (i >= n || j >= n) continue;
-      if (c > 0 && j == c - 1 && i >= j)   // write back column c - 1
-        S[i * TLD + j] = (i == j) ? sm.lv[j] : S[i * TLD + j] * sm.rd[j];
-      if (j > c && j <= i) {
-        const T v = S[i * TLD + j] - (S[i * TLD + c] * r) * (S[j * TLD + c] * r);
-        S[i * TLD + j] = v;
-        if (i == c + 1 && j == c + 1) pivot(c + 1, v);
+      for (int q = 0; q < 4; ++q) {
+        if (8 * q > wlast) break;
+        const int j = cg + 8 * q;
+        if (c > 0 && j == c - 1 && i > j) S[i * TLD + j] *= sm.rd[j];   // L column c - 1
+        if (j > c && j <= i) {
+          const T v = S[i * TLD + j] - t * S[j * TLD + c];
+          S[i * TLD + j] = v;
+          if (i == c + 1 && j == c + 1) pivot(c + 1, v);
+        }
       }
     }
     __syncthreads();
   }
-  if (n > 0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = cg + 8 * q;
-      if (j == n - 1 && i == n - 1) S[i * TLD + j] = sm.lv[j];
-    }
-  }
+  if (tid < n) S[tid * TLD + tid] = sm.lv[tid];
   __syncthreads();
 }
 
 // X = L^{-1} for a lower n x n tile (both ld TLD); zeros above the diagonal.
 // rdiag: n entries of scratch for the reciprocal diagonal.  Right-looking
-// substitution on the identity, every thread of the CTA taking part: after
-// step k row k holds (delta - sum_{m<k} L[k][m] X[m][.]) and X[k][.] is that
-// row times 1/L[k][k]; step k subtracts L[i][k] X[k][j] from the rows below.
+// substitution, every thread of the CTA taking part: row i collects
+// -sum_{m<i} L[i][m] X[m][.] over the steps m = 0 .. i-1 and is scaled by
+// 1/L[i][i] in its last one (X[i][i] = 1/L[i][i] from the start), so step k
+// reads the finished row k and costs one multiply-add per entry.
 template <typename T>
 __device__ void tile_inv(const T* L, T* X, int n, T* rdiag) {
-  const int tid = threadIdx.x, i = tid >> 3, cg = tid & 7;
+  const int tid = threadIdx.x, i = tid >> 3, cg = tid & 7, wlast = 4 * (tid >> 5) + 3;
   if (tid < n) rdiag[tid] = T(1) / L[tid * TLD + tid];
+  __syncthreads();
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int j = cg + 8 * q;
-    X[i * TLD + j] = (i == j) ? T(1) : T(0);
+    X[i * TLD + j] = (i == j && i < n) ? rdiag[i] : T(0);
   }
   __syncthreads();
   for (int k = 0; k + 1 < n; ++k) {
-    const T rk = rdiag[k];
-    if (i > k && i < n) {
+    if (wlast > k && i > k && i < n) {
       const T lik = L[i * TLD + k];
+      const bool last = (i == k + 1);
+      const T ri = last ? rdiag[i] : T(1);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
+        if (8 * q > k) break;
         const int j = cg + 8 * q;
-        if (j <= k) X[i * TLD + j] -= lik * (X[k * TLD + j] * rk);
+        if (j <= k) {
+          const T v = X[i * TLD + j] - lik * X[k * TLD + j];
+          X[i * TLD + j] = last ? v * ri : v;
+        }
       }
     }
     __syncthreads();
   }
-  if (i < n) {
-    const T ri = rdiag[i];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = cg + 8 * q;
-      if (j <= i) X[i * TLD + j] *= ri;
-    }
-  }
-  __syncthreads();
 }
 
 // Blocked right-looking Cholesky S = L L^T (S n x n SPD, lower part read,

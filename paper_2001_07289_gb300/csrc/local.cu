@@ -327,7 +327,9 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict
     }
     __syncthreads();
     // (d) rank-16 update X_ij -= W_i. P_j. (right for i, j outside K; the
-    // K rows and columns are overwritten next)
+    // K rows and columns are overwritten next).  Register blocks with
+    // bj >= 2 ai + 2 hold only entries above the diagonal (j >= 32 ai + 32 > i),
+    // which nothing reads: they are skipped.
 #pragma unroll
     for (int c2 = 0; c2 < SB / 2; ++c2) {
       float2 pj[RJ];
@@ -338,6 +340,7 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict
         const float2 wi = reinterpret_cast<const float2*>(W + (tr + 32 * ai) * PST)[c2];
 #pragma unroll
         for (int bj = 0; bj < RJ; ++bj) {
+          if (bj >= 2 * ai + 2) continue;
           x[ai][bj] = fmaf(-wi.x, pj[bj].x, x[ai][bj]);
           x[ai][bj] = fmaf(-wi.y, pj[bj].y, x[ai][bj]);
         }
