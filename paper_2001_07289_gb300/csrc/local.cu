@@ -170,9 +170,10 @@ constexpr int SCHUR_THREADS = 512;   // 32 x 16 owner grid
 //   X_ij <- X_ij - X_iK D^{-1} X_Kj,  X_iK <- X_iK D^{-1},  X_KK <- -D^{-1}
 // (i, j outside K), so one warp inverts D by 16 single-pivot sweeps, the block
 // forms W = X_:K D^{-1}, and every thread applies the rank-16 update to its
-// registers: three barriers per 16 pivots.  Tm: Q x Q shared memory for
-// S_{k-1}^{-1} B_k^T; pw: the panel buffers (schur_panel_floats).  Writes
-// S_k^{-1} to slot.
+// registers: three barriers per 16 pivots.  Tm: Q x Q shared memory that
+// holds S_{k-1}^{-1} on entry (for k > 0), S_{k-1}^{-1} B_k^T while S_k is
+// formed, and S_k^{-1} on return; pw: the panel buffers (schur_panel_floats).
+// Writes S_k^{-1} to slot.
 constexpr int SB = 16;    // pivots per block (the column block of one tc stride)
 constexpr int PST = 18;   // row stride of the panel buffers: 8-byte rows, conflict-free LDS.64
 constexpr int PNR = 192;  // panel rows: max(32 RI, 16 RJ) of the register grid
@@ -180,33 +181,53 @@ __host__ __device__ constexpr int schur_panel_floats() { return 4 * PNR * PST + 
 
 template <int RI, int RJ>
 __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict__ slot,
-                                 const float* __restrict__ Sp, const float* __restrict__ Bd, float* __restrict__ pw,
-                                 float* __restrict__ Tm, int* err, int code, int sub_id) {
+                                 const float* __restrict__ Bd, float* __restrict__ pw, float* __restrict__ Tm,
+                                 int* err, int code, int sub_id) {
   static_assert(32 * RI <= PNR && 16 * RJ <= PNR, "panel rows");
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
   if (k > 0) {
+    // T = S_{k-1}^{-1} B_k^T in place in Tm, which holds S_{k-1}^{-1} (both
+    // triangles) from the previous plane: T[i][j] = sum_o S[i][j + off_o] w_o(j)
+    // is a stencil along row i, so a warp takes whole rows, reads the row's
+    // taps into registers and writes the row back.  Lane l keeps the nine
+    // weights of its columns j = l + 32 m (zero for taps off the plane, whose
+    // index is clamped to j).
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // per column j the nine weights and neighbour offsets are fixed, so a lane
-    // keeps them and walks rows; taps are branch-free (weight 0 off the plane)
-    // so the loads of a row are all in flight together
-    for (int j = lane; j < Q + 31 - (Q + 31) % 32; j += 32) {
-      const int jj = min(j, Q - 1), jx = jj % gx, jy = jj / gx;
-      float w[9];
-      int off[9];
+    constexpr int MJ = PNR / 32;
+    float w[MJ][9];
+    int jc[MJ];
+    unsigned okm[MJ];
+#pragma unroll
+    for (int m = 0; m < MJ; ++m) {
+      const int j = lane + 32 * m, jj = min(j, Q - 1), jx = jj % gx, jy = jj / gx;
+      jc[m] = jj;
+      okm[m] = 0;
 #pragma unroll
       for (int o = 0; o < 9; ++o) {
         const int dx = o % 3 - 1, dy = o / 3 - 1;
-        const bool ok = jx + dx >= 0 && jx + dx < gx && jy + dy >= 0 && jy + dy < gy;
-        w[o] = ok ? Bd[o * Q + jj] : 0.0f;
-        off[o] = ok ? dx + dy * gx : 0;
+        const bool ok = j < Q && jx + dx >= 0 && jx + dx < gx && jy + dy >= 0 && jy + dy < gy;
+        w[m][o] = ok ? Bd[o * Q + jj] : 0.0f;
+        okm[m] |= ok ? (1u << o) : 0u;
       }
-      for (int i = warp; i < Q; i += SCHUR_THREADS / 32) {
-        const float* row = Sp + i * Q + jj;
-        float acc = 0.0f;
+    }
+    for (int i = warp; i < Q; i += SCHUR_THREADS / 32) {
+      float* row = Tm + i * Q;
+      float acc[MJ];
 #pragma unroll
-        for (int o = 0; o < 9; ++o) acc += row[off[o]] * w[o];
-        if (j < Q) Tm[i * Q + j] = acc;
+      for (int m = 0; m < MJ; ++m) {
+        float a = 0.0f;
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+          const int dx = o % 3 - 1, dy = o / 3 - 1;
+          const int idx = ((okm[m] >> o) & 1u) ? jc[m] + dx + dy * gx : jc[m];
+          a = fmaf(row[idx], w[m][o], a);
+        }
+        acc[m] = a;
       }
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < MJ; ++m)
+        if (lane + 32 * m < Q) row[lane + 32 * m] = acc[m];
     }
     __syncthreads();
   }
@@ -378,6 +399,8 @@ __device__ void schur_plane_regs(int Q, int gx, int gy, int k, float* __restrict
       if (i < Q && j <= i) {
         slot[i * Q + j] = -x[ai][bj];
         slot[j * Q + i] = -x[ai][bj];
+        Tm[i * Q + j] = -x[ai][bj];   // S_k^{-1} for the next plane's T
+        Tm[j * Q + i] = -x[ai][bj];
       }
     }
   }
@@ -413,9 +436,8 @@ k_btschur(const SubDesc* __restrict__ subs, T* __restrict__ facN, T* __restrict_
     T* slot = base + (long long)k * SS;
     if (regs) {
       if constexpr (std::is_same<T, float>::value)
-        schur_plane_regs<RI, RJ>(Q, gx, gy, k, slot, k > 0 ? base + (long long)(k - 1) * SS : nullptr,
-                                 k > 0 ? base + (long long)(g.gz + k - 1) * SS : nullptr, pw, Tm_s, err,
-                                 neumann ? 3 : 2, s.id);
+        schur_plane_regs<RI, RJ>(Q, gx, gy, k, slot, k > 0 ? base + (long long)(g.gz + k - 1) * SS : nullptr, pw,
+                                 Tm_s, err, neumann ? 3 : 2, s.id);
       continue;
     }
     if (k > 0) {
