@@ -707,38 +707,53 @@ __device__ void tc_product(TcState& G, const float* __restrict__ Atiles, int Q, 
   umma::fence_after_sync();
 }
 
-// dst[i][n] = product row i (i < Q, n < ncol), ld ldd; warps 0-3 read the
-// first 128 rows, warps 4-7 the second.  A lane holds one row, so each warp
-// turns its 32 x 32 blocks around in shared memory (the stages are idle once
-// the products are complete) and stores whole row segments.
+// The product's rows also go to a shared-memory copy (row i at i * TC_N) in
+// the stage area past the readback's transpose buffers, where the stencil that
+// follows reads its nine taps per entry.
+constexpr unsigned TC_TB_BYTES = 8u * 32u * 33u * 4u;   // per-warp 32 x 33 transpose buffers
+__device__ inline float* tc_rows(const TcState& G) {
+  return reinterpret_cast<float*>(G.stage + ((TC_TB_BYTES + 127u) & ~127u));
+}
+
+// dst[i][n] = product row i (i < Q, n < ncol), ld ldd (dst may be null), and
+// the shared copy tc_rows(G); warps 0-3 read the first 128 rows, warps 4-7
+// the second.  A lane holds one row, so each warp turns its 32 x 32 blocks
+// around in shared memory (the stages are idle once the products are
+// complete) and stores whole row segments.
 __device__ void tc_readback(const TcState& G, int Q, int ncol, float* __restrict__ dst, long long ldd) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, m = warp >> 2, quad = warp & 3;
   const int row0 = m * 128 + quad * 32;
   float* tb = reinterpret_cast<float*>(G.stage) + warp * 32 * 33;
+  float* rows = tc_rows(G);
   for (int c = 0; c < TC_N; c += 32) {
     float v[32];
     umma::ld32(G.tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(m * TC_N + c), v);
 #pragma unroll
     for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = v[j];
     __syncwarp();
-    if (c + lane < ncol)
-      for (int r = 0; r < 32 && row0 + r < Q; ++r) dst[(long long)(row0 + r) * ldd + c + lane] = tb[r * 33 + lane];
+    for (int r = 0; r < 32 && row0 + r < Q; ++r) {
+      const float x = (c + lane < ncol) ? tb[r * 33 + lane] : 0.0f;
+      rows[(row0 + r) * TC_N + c + lane] = x;
+      if (dst && c + lane < ncol) dst[(long long)(row0 + r) * ldd + c + lane] = x;
+    }
     __syncwarp();
   }
   umma::fence_before_sync();
   __syncthreads();
 }
 
-// Stencil steps of the tensor-core solves, one column per thread and four
-// rows per step with every load issued before the arithmetic (the loads come
-// from L2; eight warps per SM cannot hide one row's latency at a time).
+// Stencil steps of the tensor-core solves, one column per thread and eight
+// rows per step with every load issued before the arithmetic.  The taps come
+// from the shared copy of the last product (src, row stride TC_N); the loads
+// of Y_k come from L2, eight rows in flight per thread.
 // Bd: nine diagonals of the coupling in shared memory.
 //   forward:  Y_k[i][c] -= sum_o Bd[o][i] U[i + off_o][c]
 //   backward: U[l][c] = Y_k[l][c] - sum_o Bd[o][l - off_o] Y_{k+1}[l - off_o][c]
 template <bool FWD>
-__device__ void tc_stencil(int Q, int gx, int gy, int cw, const float* Bd, const float* __restrict__ src, long long lds,
+__device__ void tc_stencil(int Q, int gx, int gy, int cw, const float* Bd, const float* __restrict__ src,
                            float* __restrict__ Yk, long long ld, float* __restrict__ U) {
-  constexpr int RS = 4, STEP = BDDC_THREADS / TC_N;
+  constexpr int RS = 8, STEP = BDDC_THREADS / TC_N;
+  constexpr long long lds = TC_N;
   const int c = threadIdx.x % TC_N;
   if (c >= cw) return;
   for (int i0 = threadIdx.x / TC_N; i0 < Q; i0 += STEP * RS) {
@@ -773,7 +788,7 @@ __device__ void tc_stencil(int Q, int gx, int gy, int cw, const float* Bd, const
   }
 }
 
-__global__ void __launch_bounds__(BDDC_THREADS)
+__global__ void __launch_bounds__(BDDC_THREADS, 1)
 k_btsolve_multi_tc(const SubDesc* __restrict__ subs, const float* __restrict__ fac,
                    const float* __restrict__ tiles, float* __restrict__ Y, float* __restrict__ scratch,
                    long long scratch_stride, int* err) {
@@ -805,11 +820,11 @@ k_btsolve_multi_tc(const SubDesc* __restrict__ subs, const float* __restrict__ f
   for (int k = 1; k < nz; ++k) {
     float* Yk = Yb + (long long)k * Q * ld;
     tc_product(G, At + (long long)(k - 1) * plane_floats, Q, Yk - (long long)Q * ld, ld, cw, err);
-    tc_readback(G, Q, cw, U, TC_N);
+    tc_readback(G, Q, cw, nullptr, 0);
     const float* Bg = base + (long long)(nz + k - 1) * SS;
     for (int e = threadIdx.x; e < 9 * Q; e += blockDim.x) Bs[e] = Bg[e];
     __syncthreads();
-    tc_stencil<true>(Q, gx, gy, cw, Bs, U, TC_N, Yk, ld, nullptr);
+    tc_stencil<true>(Q, gx, gy, cw, Bs, tc_rows(G), Yk, ld, nullptr);
     __syncthreads();
   }
   for (int k = nz - 1; k >= 0; --k) {
@@ -820,7 +835,7 @@ k_btsolve_multi_tc(const SubDesc* __restrict__ subs, const float* __restrict__ f
       const float* Bg = base + (long long)(nz + k) * SS;       // B_{k+1}
       for (int e = threadIdx.x; e < 9 * Q; e += blockDim.x) Bs[e] = Bg[e];
       __syncthreads();
-      tc_stencil<false>(Q, gx, gy, cw, Bs, Yk + (long long)Q * ld, ld, Yk, ld, U);
+      tc_stencil<false>(Q, gx, gy, cw, Bs, tc_rows(G), Yk, ld, U);   // taps: Y_{k+1}, kept by the readback
       __syncthreads();
       tc_product(G, At + (long long)k * plane_floats, Q, U, TC_N, cw, err);
     }
