@@ -7,6 +7,8 @@
 // zeros.  These routines are called from kernels that give one CTA to one
 // subdomain (or one RHS chunk of one subdomain).
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace bddc {
@@ -211,6 +213,100 @@ __device__ void tile_inv(const T* L, T* X, int n, T* rdiag) {
   }
 }
 
+// FP64 Cholesky and inverse of an n x n (n <= 32) tile in registers of
+// warps 0-3, one warp per SM sub-partition (FP64 runs at a small fraction of
+// the FP32 rate and a warp instruction costs the same with one lane or 32):
+// lane i holds row i, warp w the columns j = w + 4m (m < 8).  Step c: the
+// owner of column c + 1 first applies column c to it and takes its pivot
+// (reciprocal square root), so that the chain of pivots runs one warp ahead
+// of the remaining updates; one barrier per column.  The inverse then runs
+// by columns, each warp on its own eight columns of X = L^{-1} with no
+// barrier: Y[i][j] -= (L[i][k] / L[k][k]) Y[k][j] (row k of Y from lane k),
+// X[i][j] = Y[i][j] / L[i][i].  In: t0 lower triangle of S (ld TLD).  Out: t0
+// = L (zeros above), X (full, zeros above the diagonal).  Uses sm.lv, sm.r2
+// (the published column, double-buffered), sm.t2 (L[i][k] / L[k][k] by k),
+// sm.rd.  A non-positive pivot sets sm.flag and is replaced by 1.
+__device__ inline void tile_chol_inv_f64(double* t0, double* X, int n, DenseSmem<double>& sm) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool act = warp < 4;
+  double a[8];
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int j = warp + 4 * m;
+      a[m] = (lane < n && j < n) ? (j <= lane ? t0[lane * TLD + j] : 0.0) : (lane == j ? 1.0 : 0.0);
+    }
+  }
+  // column c of the calling warp, held in a[m] with c = warp + 4m: pivot,
+  // scale, publish
+  auto pivot = [&](int c, double col) -> double {
+    double d = __shfl_sync(0xffffffffu, col, c);
+    if (!(d > 0.0)) {
+      if (lane == 0) sm.flag = 1;
+      d = 1.0;
+    }
+    const double rl = rsqrt(d);
+    const double l = (lane == c) ? d * rl : (lane > c ? col * rl : 0.0);
+    double* pub = (c & 1) ? sm.r2 : sm.lv;
+    pub[lane] = l;
+    sm.t2[c * TLD + lane] = (lane > c) ? l * rl : 0.0;
+    if (lane == 0) sm.rd[c] = rl;
+    return l;
+  };
+  if (warp == 0 && n > 0) a[0] = pivot(0, a[0]);
+  __syncthreads();
+  for (int c = 0; c < n; ++c) {
+    if (act) {
+      const double* lc = (c & 1) ? sm.r2 : sm.lv;
+      const double li = lc[lane];
+      const int cn = c + 1;
+      const bool owner = cn < n && warp == (cn & 3);
+      if (owner) {
+        // the column by selects (an indexed register array would go to
+        // local memory)
+        const int mm = cn >> 2;
+        double col = a[0];
+#pragma unroll
+        for (int m = 1; m < 8; ++m) col = (m == mm) ? a[m] : col;
+        col = pivot(cn, fma(-li, lc[cn], col));
+#pragma unroll
+        for (int m = 0; m < 8; ++m) a[m] = (m == mm) ? col : a[m];
+      }
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int j = warp + 4 * m;
+        if (j > c && j < n && !(owner && j == cn)) a[m] = fma(-li, lc[j], a[m]);
+      }
+    }
+    __syncthreads();
+  }
+  if (act) {
+    // L back to t0; the inverse by columns
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int j = warp + 4 * m;
+      t0[lane * TLD + j] = (lane < n && j <= lane) ? a[m] : 0.0;
+    }
+    double y[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) y[m] = (lane == warp + 4 * m) ? 1.0 : 0.0;
+    for (int k = 0; k + 1 < n; ++k) {
+      const double lt = sm.t2[k * TLD + lane];   // zero for lane <= k
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        if (warp + 4 * m <= k) {
+          const double yk = __shfl_sync(0xffffffffu, y[m], k);
+          y[m] = fma(-lt, yk, y[m]);
+        }
+      }
+    }
+    const double ri = (lane < n) ? sm.rd[lane] : 0.0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) X[lane * TLD + warp + 4 * m] = y[m] * ri;
+  }
+  __syncthreads();
+}
+
 // Blocked right-looking Cholesky S = L L^T (S n x n SPD, lower part read,
 // overwritten by L) followed by the explicit inverse Linv = L^{-1} (written in
 // full, zeros above the diagonal).  diag: scratch for ceil(n/32) 32x32 tiles.
@@ -228,8 +324,12 @@ __device__ bool cta_chol_inv(T* S, int lds, T* Linv, int ldl, int n, T* diag, De
       sm.t0[i * TLD + j] = (i < nb && j <= i) ? S[(long long)(j0 + i) * lds + j0 + j] : T(0);
     }
     __syncthreads();
-    tile_chol(sm.t0, nb, sm);
-    tile_inv(sm.t0, sm.t1, nb, sm.rd);
+    if constexpr (std::is_same<T, double>::value) {
+      tile_chol_inv_f64(sm.t0, sm.t1, nb, sm);
+    } else {
+      tile_chol(sm.t0, nb, sm);
+      tile_inv(sm.t0, sm.t1, nb, sm.rd);
+    }
     {
       const int i = tid >> 3, cg = tid & 7;
 #pragma unroll

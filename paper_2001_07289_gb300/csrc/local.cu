@@ -742,48 +742,43 @@ __device__ void tc_readback(const TcState& G, int Q, int ncol, float* __restrict
   __syncthreads();
 }
 
-// Stencil steps of the tensor-core solves, one column per thread and eight
-// rows per step with every load issued before the arithmetic.  The taps come
-// from the shared copy of the last product (src, row stride TC_N); the loads
-// of Y_k come from L2, eight rows in flight per thread.
+// Stencil steps of the tensor-core solves, one column per thread.  The taps
+// come from the shared copy of the last product (src, row stride TC_N); the
+// loads of Y_k come from L2, so a thread first issues them for RS rows and
+// then does the arithmetic of those rows.
 // Bd: nine diagonals of the coupling in shared memory.
 //   forward:  Y_k[i][c] -= sum_o Bd[o][i] U[i + off_o][c]
 //   backward: U[l][c] = Y_k[l][c] - sum_o Bd[o][l - off_o] Y_{k+1}[l - off_o][c]
 template <bool FWD>
 __device__ void tc_stencil(int Q, int gx, int gy, int cw, const float* Bd, const float* __restrict__ src,
                            float* __restrict__ Yk, long long ld, float* __restrict__ U) {
-  constexpr int RS = 8, STEP = BDDC_THREADS / TC_N;
-  constexpr long long lds = TC_N;
+  constexpr int RS = 24, STEP = BDDC_THREADS / TC_N;
   const int c = threadIdx.x % TC_N;
   if (c >= cw) return;
   for (int i0 = threadIdx.x / TC_N; i0 < Q; i0 += STEP * RS) {
-    // branch-free taps: out-of-plane neighbours read a valid row with weight
-    // 0, so every load of the step is issued before the first FMA
-    float sv[RS][9], w[RS][9], y[RS];
+    float y[RS];
 #pragma unroll
     for (int u = 0; u < RS; ++u) {
-      const int i = min(i0 + u * STEP, Q - 1), ix = i % gx, iy = i / gx;
+      const int i = min(i0 + u * STEP, Q - 1);
       y[u] = Yk[(long long)i * ld + c];
+    }
+#pragma unroll
+    for (int u = 0; u < RS; ++u) {
+      const int i = i0 + u * STEP;
+      if (i >= Q) break;
+      const int ix = i % gx, iy = i / gx;
+      float acc = 0.0f;
 #pragma unroll
       for (int o = 0; o < 9; ++o) {
         const int dx = o % 3 - 1, dy = o / 3 - 1;
         const int sx = FWD ? dx : -dx, sy = FWD ? dy : -dy;
         const bool ok = ix + sx >= 0 && ix + sx < gx && iy + sy >= 0 && iy + sy < gy;
         const int j = ok ? i + sx + sy * gx : i;
-        w[u][o] = ok ? Bd[o * Q + (FWD ? i : j)] : 0.0f;
-        sv[u][o] = src[(long long)j * lds + c];
+        const float wv = ok ? Bd[o * Q + (FWD ? i : j)] : 0.0f;
+        acc = fmaf(wv, src[j * TC_N + c], acc);
       }
-    }
-#pragma unroll
-    for (int u = 0; u < RS; ++u) {
-      const int i = i0 + u * STEP;
-      float acc = 0.0f;
-#pragma unroll
-      for (int o = 0; o < 9; ++o) acc += w[u][o] * sv[u][o];
-      if (i < Q) {
-        if (FWD) Yk[(long long)i * ld + c] = y[u] - acc;
-        else U[i * TC_N + c] = y[u] - acc;
-      }
+      if (FWD) Yk[(long long)i * ld + c] = y[u] - acc;
+      else U[i * TC_N + c] = y[u] - acc;
     }
   }
 }
