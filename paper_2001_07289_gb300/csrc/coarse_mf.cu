@@ -21,6 +21,7 @@
 // level of a triangular solve is one parallel mat-vec over all the level's
 // fronts (rows split across CTAs forward, columns backward).  Everything is
 // summed in a fixed order (no atomics).
+#include <array>
 #include <stdexcept>
 #include <string>
 
@@ -203,6 +204,9 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
   }
   P.spool = so;
   P.inv_items.assign(P.nlevel, std::vector<std::vector<int>>(2));
+  // output tiles of the doubling steps {front, r, c, k0, k1}, by level and
+  // (step, mode)
+  std::vector<std::vector<std::vector<std::array<int, 5>>>> raw(P.nlevel);
   P.toff.resize(nf);
   long long to = 0;
   for (int f = 0; f < nf; ++f) {
@@ -211,13 +215,25 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
     to += (long long)P.np[f] * P.np[f];
     std::vector<std::vector<int>>& lv = P.inv_items[P.level_of[f]];
     for (int t = 0; t < npt; ++t) lv[0].insert(lv[0].end(), {f, t, t, 0});
-    // doubling: blocks of 2 hb tiles, A = first hb tiles, C = the rest
+    // doubling: blocks of 2 hb tiles, A = first hb tiles, C = the rest.  Each
+    // output tile (r, c) is a sum of tile products over a K range (mode 0:
+    // k in [c, cstart), mode 1: k in [cstart, r]); one CTA per product
+    // (lists 2 + 4q + {0, 2}) and one per output tile summing the products
+    // in order (lists 2 + 4q + {1, 3}), so the long sums of the last steps
+    // spread over many SMs and the result does not depend on scheduling.
     int q = 0;
     for (int hb = 1; hb < npt; hb *= 2, ++q) {
-      if ((int)lv.size() <= 2 + q) lv.emplace_back();
-      for (int b0 = 0; b0 + hb < npt; b0 += 2 * hb)
-        for (int r = b0 + hb; r < std::min(b0 + 2 * hb, npt); ++r)
-          for (int c = b0; c < b0 + hb; ++c) lv[2 + q].insert(lv[2 + q].end(), {f, r, c, hb});
+      while ((int)lv.size() < 2 + 4 * (q + 1)) lv.emplace_back();
+      if ((int)raw[P.level_of[f]].size() < 2 * (q + 1)) raw[P.level_of[f]].resize(2 * (q + 1));
+      for (int b0 = 0; b0 + hb < npt; b0 += 2 * hb) {
+        const int cstart = b0 + hb;
+        for (int r = cstart; r < std::min(b0 + 2 * hb, npt); ++r)
+          for (int c = b0; c < cstart; ++c)
+            for (int mode = 0; mode < 2; ++mode) {
+              const int k0 = mode ? cstart : c, k1 = mode ? r + 1 : cstart;
+              raw[P.level_of[f]][2 * q + mode].push_back({f, r, c, k0, k1});
+            }
+      }
     }
     for (int u = 0; u < nut; ++u)
       for (int s2 = 0; s2 < npt; ++s2) lv[1].insert(lv[1].end(), {f, u, s2, 0});
@@ -225,6 +241,22 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
     P.flops += (double)P.np[f] * P.np[f] * P.np[f] / 6.0 + (double)P.nu[f] * P.np[f] * P.np[f] / 2.0;
   }
   P.tpool = to;
+  // products over K chunks of ks tiles, ks chosen per list so that it has at
+  // most about 2048 products besides one per output tile
+  for (int l = 0; l < P.nlevel; ++l)
+    for (size_t qm = 0; qm < raw[l].size(); ++qm) {
+      long long total = 0;
+      for (const auto& t : raw[l][qm]) total += t[4] - t[3];
+      const int ks = (int)std::max<long long>(1, (total + 2047) / 2048);
+      std::vector<int>& parts = P.inv_items[l][2 + 2 * qm];
+      std::vector<int>& sums = P.inv_items[l][2 + 2 * qm + 1];
+      for (const auto& t : raw[l][qm]) {
+        const int first = (int)parts.size() / 4;
+        int cnt = 0;
+        for (int k = t[3]; k < t[4]; k += ks, ++cnt) parts.insert(parts.end(), {t[0], t[1], t[2], k | (std::min(ks, t[4] - k) << 16)});
+        sums.insert(sums.end(), {t[0], (t[1] << 16) | t[2], first, cnt});
+      }
+    }
   // child update rows -> positions in the parent front: a table of each
   // object's position in the current parent, stamped with the parent's id
   P.pmap_off.assign(nf + 1, 0);
@@ -488,29 +520,48 @@ __global__ void k_mf_inv_diag(MFDev d, const int4* __restrict__ work) {
   }
 }
 
-// one doubling step for every front at once; item {front, r, c, hb}: tile
-// (r, c) of the off-diagonal block [C rows] x [A cols] of a block of 2 hb
-// diagonal tiles.  mode 0: T = L_CA X_AA (X_AA lower, so k >= c);
-// mode 1: X_CA = -X_CC T (X_CC lower, so k <= r).
+// One partial product of a doubling step, item {front, r, c, k | nk << 16}
+// (K tiles k .. k + nk - 1), into its own 32 x 32 slot of the product scratch
+// (in item order):
+//   mode 0: sum_k L[r][k] X[k][c]   (T = L_CA X_AA)
+//   mode 1: sum_k X[r][k] T[k][c]   (X_CA = -X_CC T)
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_trtri(MFDev d, const int4* __restrict__ work, int mode) {
+k_mf_trtri_part(MFDev d, const int4* __restrict__ work, int mode, double* __restrict__ part) {
   __shared__ double As[32 * 33], Bs[32 * 33];
   const int4 w = work[blockIdx.x];
-  const int f = w.x, r = w.y, c = w.z, hb = w.w;
+  const int f = w.x, r = w.y, c = w.z, k = w.w & 0xffff, kt = w.w >> 16;
   const int np = d.np[f], nu = d.nu[f];
   const long long F = np + nu;
-  const int cstart = (c / (2 * hb)) * 2 * hb + hb;   // first tile of C = end of A
   const int r0 = r * FNB, nr = min(FNB, np - r0), c0 = c * FNB, nc = min(FNB, np - c0);
+  const int k0 = k * FNB, nk = min(FNB * kt, np - k0);
   const double* L = d.F + d.foff[f];
-  double* X = d.S + d.soff[f];
-  double* T = d.T + d.toff[f];
-  const int k1 = cstart * FNB;
+  const double* X = d.S + d.soff[f];
+  const double* T = d.T + d.toff[f];
+  double* out = part + (long long)blockIdx.x * FNB * FNB;
   if (mode == 0)
-    tile_gemm_f64<false>(nr, nc, k1 - c0, 1.0, L + r0 * F + c0, F, X + (long long)c0 * np + c0, np, 0.0,
-                         T + (long long)r0 * np + c0, np, false, As, Bs);
+    tile_gemm_f64<false>(nr, nc, nk, 1.0, L + r0 * F + k0, F, X + (long long)k0 * np + c0, np, 0.0, out, FNB, false,
+                         As, Bs);
   else
-    tile_gemm_f64<false>(nr, nc, r0 + nr - k1, -1.0, X + (long long)r0 * np + k1, np, T + (long long)k1 * np + c0,
-                         np, 0.0, X + (long long)r0 * np + c0, np, false, As, Bs);
+    tile_gemm_f64<false>(nr, nc, nk, 1.0, X + (long long)r0 * np + k0, np, T + (long long)k0 * np + c0, np, 0.0, out,
+                         FNB, false, As, Bs);
+}
+
+// Sum of the products of one output tile in item order, item {front,
+// r << 16 | c, first product, count}: mode 0 into T, mode 1 (negated) into X.
+__global__ void __launch_bounds__(BDDC_THREADS)
+k_mf_trtri_sum(MFDev d, const int4* __restrict__ work, int mode, const double* __restrict__ part) {
+  const int4 w = work[blockIdx.x];
+  const int f = w.x, r = w.y >> 16, c = w.y & 0xffff;
+  const int np = d.np[f];
+  const int r0 = r * FNB, nr = min(FNB, np - r0), c0 = c * FNB, nc = min(FNB, np - c0);
+  double* dst = (mode == 0 ? d.T + d.toff[f] : d.S + d.soff[f]) + (long long)r0 * np + c0;
+  for (int e = threadIdx.x; e < FNB * FNB; e += blockDim.x) {
+    const int i = e / FNB, j = e % FNB;
+    if (i >= nr || j >= nc) continue;
+    double acc = 0.0;
+    for (int q = 0; q < w.w; ++q) acc += part[(long long)(w.z + q) * FNB * FNB + e];
+    dst[(long long)i * np + j] = mode == 0 ? acc : -acc;
+  }
 }
 
 __global__ void __launch_bounds__(BDDC_THREADS)
@@ -700,6 +751,14 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
   }
   P.inv_lvl_base.push_back((int)P.inv_off.size());
   P.tscratch = (double*)tmp_alloc(sizeof(double) * std::max<long long>(P.tpool, 1));
+  {
+    // tile products of the doubling steps; the solve matrices of all levels
+    // are built in one stream, one list at a time
+    size_t maxparts = 1;
+    for (const auto& lv : P.inv_items)
+      for (size_t q = 2; q < lv.size(); q += 2) maxparts = std::max(maxparts, lv[q].size() / 4);
+    P.tpart = (double*)tmp_alloc(sizeof(double) * FNB * FNB * maxparts);
+  }
   P.d_toff = up(P.toff, alloc, st);
   P.d_lists = (int4*)tmp_alloc(sizeof(int) * std::max<size_t>(all.size(), 4));
   if (!all.empty()) cudaMemcpyAsync(P.d_lists, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, st);
@@ -800,11 +859,13 @@ static void CK_MF(cudaError_t e) {
 static void mf_solve_matrices(const MFPlan& P, const MFDev& d, int l, cudaStream_t st) {
   const int b = P.inv_lvl_base[l], e = P.inv_lvl_base[l + 1];
   if (P.inv_len[b]) { BDDC_COUNT(1); k_mf_inv_diag<<<P.inv_len[b], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[b]); }
-  for (int q = b + 2; q < e; ++q)
-    if (P.inv_len[q]) {
+  for (int q = b + 2; q + 3 < e; q += 4)
+    for (int mode = 0; mode < 2; ++mode) {
+      const int lp = q + 2 * mode, ls = lp + 1;
+      if (!P.inv_len[lp]) continue;
       BDDC_COUNT(2);
-      k_mf_trtri<<<P.inv_len[q], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[q], 0);
-      k_mf_trtri<<<P.inv_len[q], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[q], 1);
+      k_mf_trtri_part<<<P.inv_len[lp], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[lp], mode, P.tpart);
+      k_mf_trtri_sum<<<P.inv_len[ls], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[ls], mode, P.tpart);
     }
   if (P.inv_len[b + 1]) { BDDC_COUNT(1); k_mf_g<<<P.inv_len[b + 1], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[b + 1]); }
 }

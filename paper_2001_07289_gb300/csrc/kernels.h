@@ -100,7 +100,9 @@ struct MFPlan {
   // L_P^{-1} by recursive doubling: at level q (half block hb = 2^q tiles)
   // the items {front, r, c, hb} cover every tile of the off-diagonal blocks
   // per level of the front tree: [0] diagonal tiles {front, t, t, 0},
-  // [1] G tiles {front, ut, st, 0}, [2 + q] doubling step q
+  // [1] G tiles {front, ut, st, 0}, [2 + 4q + 2 mode] the tile products of
+  // doubling step q {front, r, c, k}, [2 + 4q + 2 mode + 1] their sums
+  // {front, r << 16 | c, first product, count}
   std::vector<std::vector<std::vector<int>>> inv_items;
   std::vector<long long> inv_off;              // device offsets of these lists, level by level
   std::vector<int> inv_len;
@@ -109,6 +111,7 @@ struct MFPlan {
   long long tpool = 0;
   long long* d_toff = nullptr;
   double* tscratch = nullptr;                  // L_CA X_AA products of the doubling steps
+  double* tpart = nullptr;                     // 32 x 32 tile products before their sums
   std::vector<int> fwd_items_off, bwd_items_off; // per level into the solve work lists
   int* d_solve_items = nullptr;                // int2 {front, chunk} lists for the solves
   std::vector<int> fwd_items_len, bwd_items_len;
