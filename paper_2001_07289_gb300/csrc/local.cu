@@ -1122,6 +1122,22 @@ template <typename A, typename T, typename X>
 __device__ inline void col_accumulate(const ColLayout& L, const T* __restrict__ ch, int nr, const X* __restrict__ x,
                                       A acc[4]) {
   if (L.col < 0) return;
+  if (L.G > 1) {
+    // one column per thread: four rows per step on separate partial sums, so
+    // that their shared-memory loads are in flight together
+    const int c = L.col, G = L.G;
+    A a0 = A(0), a1 = A(0), a2 = A(0), a3 = A(0);
+    int r = L.grp;
+    for (; r + 3 * G < nr; r += 4 * G) {
+      a0 += (A)ch[(long long)r * L.ncol + c] * (A)x[r];
+      a1 += (A)ch[(long long)(r + G) * L.ncol + c] * (A)x[r + G];
+      a2 += (A)ch[(long long)(r + 2 * G) * L.ncol + c] * (A)x[r + 2 * G];
+      a3 += (A)ch[(long long)(r + 3 * G) * L.ncol + c] * (A)x[r + 3 * G];
+    }
+    for (; r < nr; r += G) a0 += (A)ch[(long long)r * L.ncol + c] * (A)x[r];
+    acc[0] += (a0 + a1) + (a2 + a3);
+    return;
+  }
   for (int r = L.grp; r < nr; r += L.G) {
     const A xv = (A)x[r];
     const T* row = ch + (long long)r * L.ncol;
@@ -1212,7 +1228,7 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
   auto finish = [&](int bi, T* dst) {
     if (nrank == 1) {   // a CTA of its own: straight to the destination
       col_finish<T>(L, acc, part, [&](int cc, T sum) { dst[cc] = sum; });
-      __syncthreads();
+      if (L.G == 1) __syncthreads();   // (with row groups col_finish ends with one)
       return;
     }
     T* mine = pb + (bi & 1) * Q;
@@ -1250,7 +1266,9 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
       col_accumulate<T, T, T>(L, reinterpret_cast<const T*>(raw), nr, in + r0, acc);
       return;
     }
-    __syncthreads();   // every row of the slot is consumed before outputs overwrite inputs
+    // every row of the slot is consumed before outputs overwrite inputs (with
+    // row groups on one CTA, col_finish's barrier after the partials does it)
+    if (nrank > 1 || L.G == 1) __syncthreads();
     finish(bi, fwd ? t : v + (long long)k * Q);
     const T* Bd = reinterpret_cast<const T*>(raw);
     if (fwd) {
