@@ -208,6 +208,7 @@ struct bddc_handle {
   // fork and join order it against the caller's stream
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t setup_ev[7] = {};   // phase boundaries of the setup
   double* xw = nullptr;
   long long graph_body_launches = 0;
   double* pinned = nullptr;
@@ -259,6 +260,8 @@ struct bddc_handle {
     if (aux) cudaStreamDestroy(aux);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    for (cudaEvent_t e : setup_ev)
+      if (e) cudaEventDestroy(e);
     free_setup_only();
     for (auto& v : allocs) block_cache().put(device, v.first, v.second);
     if (pinned) cudaFreeHost(pinned);
@@ -267,10 +270,76 @@ struct bddc_handle {
 
 namespace {
 
+// Pinned staging for the uploads of a setup: host vectors are copied into
+// page-locked blocks and sent with cudaMemcpyAsync, which then returns without
+// waiting for the work queued before it (a copy from pageable memory may wait,
+// and the setup's host work between launches would then leave the GPU idle).
+// One setup at a time holds the pool; setups end with a stream
+// synchronisation, after which its blocks are free again.  The blocks live for
+// the process.
+struct PinnedPool {
+  std::mutex mu;
+  std::vector<std::pair<char*, size_t>> blocks;
+  size_t blk = 0, off = 0;
+  void* take(size_t bytes) {
+    bytes = (bytes + 63) & ~size_t(63);
+    while (blk < blocks.size() && off + bytes > blocks[blk].second) { ++blk; off = 0; }
+    if (blk == blocks.size()) {
+      const size_t sz = std::max<size_t>(bytes, blocks.empty() ? (size_t(4) << 20) : 2 * blocks.back().second);
+      char* p = nullptr;
+      if (cudaMallocHost((void**)&p, sz) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      blocks.emplace_back(p, sz);
+      off = 0;
+    }
+    void* r = blocks[blk].first + off;
+    off += bytes;
+    return r;
+  }
+};
+PinnedPool& pinned_pool() {
+  static PinnedPool* p = new PinnedPool;
+  return *p;
+}
+thread_local PinnedPool* t_stage = nullptr;
+
+// Holds the pool for one setup on the calling thread; on exit waits for the
+// stream, so that no copy from the pool is still in flight.
+struct StageSession {
+  std::unique_lock<std::mutex> lk;
+  cudaStream_t st;
+  explicit StageSession(cudaStream_t s) : lk(pinned_pool().mu), st(s) {
+    pinned_pool().blk = 0;
+    pinned_pool().off = 0;
+    t_stage = &pinned_pool();
+  }
+  ~StageSession() {
+    t_stage = nullptr;
+    cudaStreamSynchronize(st);
+  }
+};
+
+}  // namespace
+
+void bddc::stage_h2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return;
+  void* hp = t_stage ? t_stage->take(bytes) : nullptr;
+  if (hp) {
+    std::memcpy(hp, src, bytes);
+    CK(cudaMemcpyAsync(dst, hp, bytes, cudaMemcpyHostToDevice, st));
+  } else {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+  }
+}
+
+namespace {
+
 template <typename T>
 T* upload(bddc_handle* h, const std::vector<T>& v, cudaStream_t st) {
   T* d = h->dnew<T>(std::max<size_t>(v.size(), 1));
-  if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  stage_h2d(d, v.data(), sizeof(T) * v.size(), st);
   return d;
 }
 
@@ -524,14 +593,14 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   }
   h->launch_base = g_launches;
   // events: 0 start, 1 weights done, 2 Dirichlet, 3 Neumann, 4 basis, 5 assembly, 6 coarse factor
-  cudaEvent_t ev[7];
-  for (auto& e : ev) CK(cudaEventCreate(&e));
+  cudaEvent_t* ev = h->setup_ev;
+  for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&ev[k]));
   cudaEvent_t e0 = ev[0], e1 = ev[6];
   CK(cudaEventRecord(e0, st));
   // flags and alpha
   h->err = h->dnew<int>(2);
   int init[2] = {0, -1};
-  CK(cudaMemcpyAsync(h->err, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  stage_h2d(h->err, init, sizeof(init), st);
   const long long NE = (long long)M.nx * M.ny * M.nz;
   h->alpha = h->dnew<double>(NE);
   CK(cudaMemcpyAsync(h->alpha, alpha_dev, sizeof(double) * NE, cudaMemcpyDeviceToDevice, st));
@@ -660,10 +729,17 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->hist_a = h->dnew<double>(h->hist_cap);
   h->hist_b = h->dnew<double>(h->hist_cap);
   CK(cudaMallocHost((void**)&h->pinned, 64));
+  (void)e0;
+  (void)e1;
+}
+
+// The end of a setup: waits for the queued work, reads the device-side error
+// flags and the phase times, returns the setup-only blocks to the cache.
+void finish_setup(bddc_handle* h, cudaStream_t st) {
+  cudaEvent_t* ev = h->setup_ev;
   check_err_flags(h, st);
-  CK(cudaEventElapsedTime(&h->setup_ms, e0, e1));
+  CK(cudaEventElapsedTime(&h->setup_ms, ev[0], ev[6]));
   for (int k = 0; k < 6; ++k) CK(cudaEventElapsedTime(&h->phase_ms[k], ev[k], ev[k + 1]));
-  for (auto& e : ev) cudaEventDestroy(e);
   h->free_setup_only();
 }
 
@@ -950,9 +1026,13 @@ extern "C" int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, con
   if (!alpha_dev) throw BddcError(BDDC_ERR_ARG, "NULL argument");
   std::unique_ptr<bddc_handle> h = make_handle(mesh, part, opt);
   cudaStream_t st = (cudaStream_t)stream;
+  StageSession staging(st);   // the uploads of this setup go through pinned staging
   do_setup(h.get(), alpha_dev, st);
   tune_apply(h.get(), st);
-  check_err_flags(h.get(), st);
+  // the PCG graph (use_graph) is captured and instantiated on the host while
+  // the setup still runs on the device; it only records the handle's buffers
+  if (h->opt.use_graph) build_graph(h.get());
+  finish_setup(h.get(), st);
   *out = h.release();
   return BDDC_OK;
   ABI_END(hnull)

@@ -688,7 +688,7 @@ MFDev dev_of(const MFPlan& P) {
 template <typename T>
 T* up(const std::vector<T>& v, const std::function<void*(size_t)>& alloc, cudaStream_t st) {
   T* p = (T*)alloc(sizeof(T) * std::max<size_t>(v.size(), 1));
-  if (!v.empty()) cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+  stage_h2d(p, v.data(), sizeof(T) * v.size(), st);
   return p;
 }
 
@@ -761,7 +761,7 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
   }
   P.d_toff = up(P.toff, alloc, st);
   P.d_lists = (int4*)tmp_alloc(sizeof(int) * std::max<size_t>(all.size(), 4));
-  if (!all.empty()) cudaMemcpyAsync(P.d_lists, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, st);
+  stage_h2d(P.d_lists, all.data(), sizeof(int) * all.size(), st);
   // per level: fronts, their children (for the solves), children by slot (extend-add)
   std::vector<int> lv;
   P.lvl_fronts_off.assign(P.nlevel + 1, 0);

@@ -133,6 +133,10 @@ struct MFPlan {
   int* d_blob = nullptr;
 };
 
+// host -> device copy of setup metadata, through pinned staging while a
+// setup holds it (ordered in st, returns without waiting for st's queued work)
+void stage_h2d(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
 void mf_plan(MFPlan& P, const CoarseGeom& g, int nc);
 // alloc: memory kept for the solves; tmp_alloc: memory needed during setup only
 void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
