@@ -407,16 +407,18 @@ __global__ void k_mf_extend_add(MFDev d, const int* __restrict__ kids) {
   const int* map = d.pmap + d.pmap_off[c];
   const double* C = d.F + d.foff[c];
   double* Pm = d.F + d.foff[p];
-  const long long tri = (long long)nuc * (nuc + 1) / 2;
-  for (long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x; e < tri; e += (long long)gridDim.y * blockDim.x) {
-    // e -> (i, j) with j <= i
-    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-    while ((long long)i * (i + 1) / 2 > e) --i;
-    while ((long long)(i + 1) * (i + 2) / 2 <= e) ++i;
-    const int j = (int)(e - (long long)i * (i + 1) / 2);
-    const int pi = map[i], pj = map[j];
-    const int r = max(pi, pj), q = min(pi, pj);
-    Pm[(long long)r * Fp + q] += C[(long long)(npc + i) * Fc + npc + j];
+  // rows i of the update block round-robin over (blockIdx.y, warp), the
+  // lanes along the row's columns j <= i: no triangular index inversion,
+  // whose square root would run on the slow FP64 pipe for every entry
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = blockIdx.y * nw + warp; i < nuc; i += gridDim.y * nw) {
+    const int pi = map[i];
+    const double* crow = C + (long long)(npc + i) * Fc + npc;
+    for (int j = lane; j <= i; j += 32) {
+      const int pj = map[j];
+      const int r = max(pi, pj), q = min(pi, pj);
+      Pm[(long long)r * Fp + q] += crow[j];
+    }
   }
 }
 
