@@ -61,15 +61,25 @@ FP32_PEAK_TFLOPS = 80.5    # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 
 def _traffic():
-    """DRAM bytes per launch from the committed ncu summaries (null when absent)."""
+    """DRAM bytes per launch from the committed ncu summaries, by kernel, with
+    the workload and precision they were measured on."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            return {k: v.get("bytes_per_launch") for k, v in json.load(f).items()}
-    except (OSError, ValueError, AttributeError):
+            return json.load(f)
+    except (OSError, ValueError):
         return {}
 
 
 TRAFFIC = _traffic()
+
+
+def traffic_of(kernel, workload, precision):
+    """The measured bytes of one launch when they were taken on this workload
+    and precision, else None (counters from another size do not carry over)."""
+    e = TRAFFIC.get(kernel)
+    if isinstance(e, dict) and e.get("workload") == workload and e.get("precision") == precision:
+        return e.get("bytes_per_launch")
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -371,7 +381,8 @@ def main():
     peak_local = FP32_PEAK_TFLOPS if args.precision == "mixed" else FP64_PEAK_TFLOPS
     roofline = {"kernel": "k_btschur (local Dirichlet + Neumann inverse Schur complements, one launch)",
                 "bound": "alu", "achieved": round(fac_tflops, 4), "peak": peak_local, "unit": "TFLOP/s",
-                "frac": round(fac_tflops / peak_local, 4), "traffic": TRAFFIC.get("k_btschur"),
+                "frac": round(fac_tflops / peak_local, 4),
+                "traffic": traffic_of("k_btschur", args.workload, args.precision),
                 "algorithmic": f"{2 * info['local_factor_fma']:.3e} flop per launch (sum over subdomains and "
                                "planes of Q^3/2 + 18 Q^2 multiply-adds)",
                 "peak_source": ("FP32 derived from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
@@ -381,7 +392,8 @@ def main():
     apply_gbs = info_apply["apply_bytes"] / (apply_ms * 1e-3) / 1e9
     roofline_apply = {"kernel": "preconditioner apply (bddc_apply: streamed local sweeps, Phi, coarse fronts)",
                       "bound": "hbm", "achieved": round(apply_gbs, 2), "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                      "frac": round(apply_gbs / HBM_PEAK_GBS, 4), "traffic": TRAFFIC.get("apply"),
+                      "frac": round(apply_gbs / HBM_PEAK_GBS, 4),
+                      "traffic": traffic_of("apply", args.workload, args.precision),
                       "algorithmic": f"{info_apply['apply_bytes']} bytes per apply (factor halves read per "
                                      "sweep, Phi twice, coarse solve matrices twice)",
                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, burst)"}
