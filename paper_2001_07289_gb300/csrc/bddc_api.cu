@@ -595,8 +595,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   // events: 0 start, 1 weights done, 2 Dirichlet, 3 Neumann, 4 basis, 5 assembly, 6 coarse factor
   cudaEvent_t* ev = h->setup_ev;
   for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&ev[k]));
-  cudaEvent_t e0 = ev[0], e1 = ev[6];
-  CK(cudaEventRecord(e0, st));
+  CK(cudaEventRecord(ev[0], st));
   // flags and alpha
   h->err = h->dnew<int>(2);
   int init[2] = {0, -1};
@@ -729,8 +728,6 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->hist_a = h->dnew<double>(h->hist_cap);
   h->hist_b = h->dnew<double>(h->hist_cap);
   CK(cudaMallocHost((void**)&h->pinned, 64));
-  (void)e0;
-  (void)e1;
 }
 
 // The end of a setup: waits for the queued work, reads the device-side error

@@ -22,6 +22,7 @@
 // fronts (rows split across CTAs forward, columns backward).  Everything is
 // summed in a fixed order (no atomics).
 #include <array>
+#include <cstdint>
 #include <stdexcept>
 #include <string>
 
@@ -283,32 +284,29 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
       }
     }
   }
-  // work lists per (level, panel step)
-  P.step_potrf.clear(); P.step_trsm.clear(); P.step_syrk.clear();
-  P.list_len.clear();
+  // front tables per (level, panel step): the trsm items of front f at step j
+  // are the tiles i = j+1 .. nt-1 below the panel, the syrk items the pairs
+  // j+1 <= k <= i < nt of the trailing lower triangle
+  P.step_fronts.clear(); P.step_j.clear(); P.step_ntr.clear(); P.step_nsy.clear();
   for (int l = P.nlevel - 1; l >= 0; --l) {
     int maxpt = 0;
     for (int f : P.fronts_at_level[l]) maxpt = std::max(maxpt, (P.np[f] + FNB - 1) / FNB);
     for (int j = 0; j < maxpt; ++j) {
-      std::vector<int> po, tr, sy;
-      size_t ntr = 0, nsy = 0;
-      for (int f : P.fronts_at_level[l]) {
-        const int npt = (P.np[f] + FNB - 1) / FNB, nt = mf_ntiles(P.np[f], P.nu[f]);
-        if (j < npt) { ntr += nt - j - 1; nsy += (size_t)(nt - j - 1) * (nt - j) / 2; }
-      }
-      tr.reserve(4 * ntr);
-      sy.reserve(4 * nsy);
+      std::vector<int> tab;
+      long long ntr = 0, nsy = 0;
       for (int f : P.fronts_at_level[l]) {
         const int npt = (P.np[f] + FNB - 1) / FNB, nt = mf_ntiles(P.np[f], P.nu[f]);
         if (j >= npt) continue;
-        po.insert(po.end(), {f, j, j, 0});
-        for (int i = j + 1; i < nt; ++i) tr.insert(tr.end(), {f, i, j, 0});
-        for (int i = j + 1; i < nt; ++i)
-          for (int k = j + 1; k <= i; ++k) sy.insert(sy.end(), {f, i, k, j});
+        const long long m = nt - j - 1;
+        tab.insert(tab.end(), {f, nt, (int)ntr, (int)nsy});
+        ntr += m;
+        nsy += m * (m + 1) / 2;
       }
-      P.step_potrf.push_back(po);
-      P.step_trsm.push_back(tr);
-      P.step_syrk.push_back(sy);
+      if (nsy > INT32_MAX) throw std::runtime_error("coarse front too large for one panel step");
+      P.step_fronts.push_back(tab);
+      P.step_j.push_back(j);
+      P.step_ntr.push_back((int)ntr);
+      P.step_nsy.push_back((int)nsy);
     }
   }
 }
@@ -422,12 +420,24 @@ __global__ void k_mf_extend_add(MFDev d, const int* __restrict__ kids) {
   }
 }
 
+// Entry of a step's front table whose item range holds item b: the last
+// entry with first item <= b (syrk: field w, trsm: field z); empty ranges
+// are passed over because the next entry has the same first item.
+__device__ inline int mf_find_front(const int4* __restrict__ tab, int n, int b, bool syrk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int first = syrk ? tab[mid].w : tab[mid].z;
+    if (first <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_potrf(MFDev d, const int4* __restrict__ work, double* scratch, int* err) {
+k_mf_potrf(MFDev d, const int4* __restrict__ tab, double* scratch, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
-  const int4 w = work[blockIdx.x];
-  const int f = w.x, j = w.y;
+  const int f = tab[blockIdx.x].x, j = 0;   // the first panel of each front
   const int np = d.np[f], nu = d.nu[f];
   const long long F = np + nu;
   int r0, nr;
@@ -441,12 +451,12 @@ k_mf_potrf(MFDev d, const int4* __restrict__ work, double* scratch, int* err) {
 
 // A[i,j] <- A[i,j] Dinv_j^T (tile in shared memory)
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_trsm(MFDev d, const int4* __restrict__ work) {
+k_mf_trsm(MFDev d, const int4* __restrict__ tab, int nfr, int j) {
   extern __shared__ __align__(128) unsigned char smraw[];
   double* T = reinterpret_cast<double*>(smraw);       // FNB x (FNB+1)
   double* D = T + FNB * (FNB + 1);                    // FNB x (FNB+1)
-  const int4 w = work[blockIdx.x];
-  const int f = w.x, i = w.y, j = w.z;
+  const int4 fe = tab[mf_find_front(tab, nfr, (int)blockIdx.x, false)];
+  const int f = fe.x, i = j + 1 + ((int)blockIdx.x - fe.z);
   const int np = d.np[f], nu = d.nu[f];
   const long long F = np + nu;
   int ri, ni, rj, nj;
@@ -474,11 +484,16 @@ k_mf_trsm(MFDev d, const int4* __restrict__ work) {
 // value and factors it right away (Cholesky and explicit inverse), so the
 // next panel's trsm does not wait for a separate potrf launch.
 __global__ void __launch_bounds__(BDDC_THREADS)
-k_mf_syrk(MFDev d, const int4* __restrict__ work, double* pscratch, int* err) {
+k_mf_syrk(MFDev d, const int4* __restrict__ tab, int nfr, int j, double* pscratch, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double As[32 * 33], Bs[32 * 33];
-  const int4 w = work[blockIdx.x];
-  const int f = w.x, i = w.y, l = w.z, j = w.w;
+  const int4 fe = tab[mf_find_front(tab, nfr, (int)blockIdx.x, true)];
+  // local index t -> (r, c), c <= r, of the trailing triangle
+  const int t = (int)blockIdx.x - fe.w;
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (r > 0 && r * (r + 1) / 2 > t) --r;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  const int f = fe.x, i = j + 1 + r, l = j + 1 + (t - r * (r + 1) / 2);
   const int np = d.np[f], nu = d.nu[f];
   const long long F = np + nu;
   int ri, ni, rl, nl, rj, nj;
@@ -732,15 +747,10 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
   cudaMemsetAsync(P.S, 0, sizeof(double) * P.spool, st);
   // work lists
   std::vector<int> all;
-  P.list_off.clear();
-  auto push = [&](const std::vector<int>& v) {
-    P.list_off.push_back((long long)all.size() / 4);
-    all.insert(all.end(), v.begin(), v.end());
-  };
-  for (size_t k = 0; k < P.step_potrf.size(); ++k) {
-    push(P.step_potrf[k]);
-    push(P.step_trsm[k]);
-    push(P.step_syrk[k]);
+  P.step_off.clear();
+  for (const std::vector<int>& tab : P.step_fronts) {
+    P.step_off.push_back((long long)all.size() / 4);
+    all.insert(all.end(), tab.begin(), tab.end());
   }
   P.inv_off.clear(); P.inv_len.clear(); P.inv_lvl_base.clear();
   for (const auto& lv : P.inv_items) {
@@ -808,14 +818,8 @@ void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
   P.blob_slots = (long long)blob.size();
   blob.insert(blob.end(), slots.begin(), slots.end());
   P.d_blob = up(blob, alloc, st);
-  P.list_len.clear();
   int maxpo = 1;
-  for (size_t k = 0; k < P.step_potrf.size(); ++k) {
-    P.list_len.push_back((int)P.step_potrf[k].size() / 4);
-    P.list_len.push_back((int)P.step_trsm[k].size() / 4);
-    P.list_len.push_back((int)P.step_syrk[k].size() / 4);
-    maxpo = std::max(maxpo, (int)P.step_potrf[k].size() / 4);
-  }
+  for (const std::vector<int>& tab : P.step_fronts) maxpo = std::max(maxpo, (int)tab.size() / 4);
   P.pscratch = (double*)tmp_alloc(sizeof(double) * 2048 * (size_t)maxpo);
   P.fscratch = (double*)tmp_alloc(sizeof(double) * 2048 * (size_t)P.nfront);
   // solve work lists: per level fwd items {front, row chunk}, bwd items {front, column chunk}
@@ -891,15 +895,13 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cud
     int maxpt = 0;
     for (int f : P.fronts_at_level[l]) maxpt = std::max(maxpt, (P.np[f] + FNB - 1) / FNB);
     for (int j = 0; j < maxpt; ++j, ++step) {
-      const int npo = P.list_len[3 * step], ntr = P.list_len[3 * step + 1], nsy = P.list_len[3 * step + 2];
-      const int4* lp = P.d_lists + P.list_off[3 * step];
-      const int4* lt = P.d_lists + P.list_off[3 * step + 1];
-      const int4* ls = P.d_lists + P.list_off[3 * step + 2];
+      const int nfr = (int)P.step_fronts[step].size() / 4, ntr = P.step_ntr[step], nsy = P.step_nsy[step];
+      const int4* tab = P.d_lists + P.step_off[step];
       // the first panel's diagonal tiles of the level; later ones are
       // factored inside the previous step's syrk (look-ahead)
-      if (npo && j == 0) { BDDC_COUNT(1); k_mf_potrf<<<npo, BDDC_THREADS, dsm, st>>>(d, lp, P.pscratch, err); }
-      if (ntr) { BDDC_COUNT(1); k_mf_trsm<<<ntr, BDDC_THREADS, tsm, st>>>(d, lt); }
-      if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, dsm, st>>>(d, ls, P.fscratch, err); }
+      if (nfr && j == 0) { BDDC_COUNT(1); k_mf_potrf<<<nfr, BDDC_THREADS, dsm, st>>>(d, tab, P.pscratch, err); }
+      if (ntr) { BDDC_COUNT(1); k_mf_trsm<<<ntr, BDDC_THREADS, tsm, st>>>(d, tab, nfr, j); }
+      if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, dsm, st>>>(d, tab, nfr, j, P.fscratch, err); }
     }
     if (two) {
       CK_MF(cudaEventRecord(fork, st));

@@ -118,9 +118,13 @@ struct MFPlan {
   long long blob_lvl_index = 0;                // per front: its index in the level-ordered list
   int maxF = 0;
   // work lists per (level, panel step): int4 {front, i, l, j}, concatenated on the device
-  std::vector<std::vector<int>> step_potrf, step_trsm, step_syrk;
-  std::vector<long long> list_off;
-  std::vector<int> list_len;
+  // per (level, panel step j): the fronts still factoring, as int4 entries
+  // {front, tiles nt, first trsm item, first syrk item} (prefix counts); the
+  // kernels decode their item from the block index, so the lists, whose length
+  // grows as nt^3 per front, are not stored item by item
+  std::vector<std::vector<int>> step_fronts;
+  std::vector<int> step_j, step_ntr, step_nsy;
+  std::vector<long long> step_off;            // device offsets of the tables
   int4* d_lists = nullptr;
   double* pscratch = nullptr;       // potrf scratch: 2048 doubles per concurrent diagonal tile
   double* fscratch = nullptr;       // look-ahead potrf scratch in the syrk steps: 2048 doubles per front
