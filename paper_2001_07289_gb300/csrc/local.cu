@@ -111,19 +111,20 @@ __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const do
   if (k >= g.gz) return;
   const int Q = g.gx * g.gy;
   T* base = fac + (neumann ? s.offN : s.offD);
-  const long long QQ = (long long)Q * Q, SS = slot_stride(Q);
-  const long long n1 = (k > 0) ? 9LL * Q : 0;
-  for (long long e = (long long)blockIdx.z * blockDim.x + threadIdx.x; e < QQ + n1;
-       e += (long long)gridDim.z * blockDim.x) {
+  // a plane block has Q^2 + 9Q < 2^31 entries: 32-bit index arithmetic
+  const int QQ = Q * Q;
+  const long long SS = slot_stride(Q);
+  const int n1 = (k > 0) ? 9 * Q : 0;
+  for (int e = (int)(blockIdx.z * blockDim.x + threadIdx.x); e < QQ + n1; e += (int)(gridDim.z * blockDim.x)) {
     int a, bx, by, bz, dx, dy;
     if (e < QQ) {
-      a = (int)(e / Q);
-      const int b = (int)(e % Q);
+      a = e / Q;
+      const int b = e % Q;
       bx = b % g.gx; by = b / g.gx; bz = k;
       dx = bx - a % g.gx; dy = by - a / g.gx;
     } else {
-      const int o = (int)((e - QQ) / Q);
-      a = (int)((e - QQ) % Q);
+      const int o = (e - QQ) / Q;
+      a = (e - QQ) % Q;
       dx = o % 3 - 1; dy = o / 3 - 1;
       bx = a % g.gx + dx; by = a / g.gx + dy; bz = k - 1;
     }
