@@ -82,7 +82,16 @@ typedef struct {
     int selection;  /* BDDC_SEL_VEF, BDDC_SEL_VE, BDDC_SEL_VF or BDDC_SEL_V           */
     int use_graph;  /* 1: pcg_solve runs its whole loop as one CUDA graph (below)      */
     int maxit;      /* PCG iteration limit (<= 0: 2000)                               */
+    int beta_rule;  /* BDDC_BETA_STANDARD (0) or BDDC_BETA_FLEXIBLE (below)          */
 } bddc_options;
+
+/* PCG direction update p = z + beta p.  STANDARD (Section 5's PCG): beta =
+ * r_{k+1}.z_{k+1} / r_k.z_k.  FLEXIBLE (Polak-Ribiere): beta =
+ * r_{k+1}.(z_{k+1} - z_k) / r_k.z_k, one more dot product and node vector per
+ * iteration; the same in exact arithmetic for a symmetric B (r_{k+1}.z_k = 0),
+ * more robust when B varies between applications.  On the FP32-local path the
+ * two take the same number of iterations on the workloads tested here. */
+enum { BDDC_BETA_STANDARD = 0, BDDC_BETA_FLEXIBLE = 1 };
 
 /* Per-solve statistics.  alphas/betas: optional host arrays of `capacity`
  * entries that receive the CG coefficients (for Lanczos estimates). */
@@ -244,6 +253,26 @@ int bddc_get_coarse_matrix(const bddc_handle* h, double* ac_host);
  *     zeroed.
  * Arguments as for bddc_apply. */
 int bddc_apply_noalloc(bddc_handle* h, const double* r_dev, double* z_dev, void* stream);
+
+/* Test hooks: host-side fault injection for the failure paths (the paper has
+ * no counterpart).  Process-wide, not thread-safe; meant for tests only.
+ *   BDDC_DEBUG_NEGATE_NEUMANN_PIVOT / _DIRICHLET_PIVOT, value = subdomain id
+ *     (x fastest over the box grid; -1 = off): every later bddc_setup negates
+ *     the first diagonal entry of that subdomain's assembled local Neumann
+ *     (Dirichlet) matrix before factorising it, so the setup returns
+ *     BDDC_ERR_NOT_SPD and bddc_last_error(NULL) names the subdomain.  A
+ *     subdomain without interior nodes has no Dirichlet matrix: no effect.
+ *   BDDC_DEBUG_WAIT_TRIES, value = tries (< 0: the default): every bounded
+ *     device wait (bulk copies, tensor-core MMAs) reports a timeout after this
+ *     many unsuccessful tries, then still waits, bounded, for the work it
+ *     covers, so the results stay valid and nothing hangs; the next call that
+ *     reads the device status (pcg_solve, bddc_setup) returns
+ *     BDDC_ERR_TIMEOUT and clears it.  0 makes every wait report.
+ *   BDDC_DEBUG_CLEAR: every hook off.
+ * Returns BDDC_ERR_ARG for an unknown hook or value. */
+enum { BDDC_DEBUG_CLEAR = 0, BDDC_DEBUG_NEGATE_NEUMANN_PIVOT = 1, BDDC_DEBUG_NEGATE_DIRICHLET_PIVOT = 2,
+       BDDC_DEBUG_WAIT_TRIES = 3 };
+int bddc_debug_inject(int what, long long value);
 
 /* Frees every device and host resource of the handle (NULL is a no-op). */
 int bddc_destroy(bddc_handle* h);

@@ -22,7 +22,10 @@ BDDC_ERR_BREAKDOWN, BDDC_ERR_CUDA, BDDC_ERR_OOM, BDDC_ERR_TIMEOUT, BDDC_ERR_UNSU
 BDDC_FP64, BDDC_MIXED = 0, 1
 BDDC_W_CARD, BDDC_W_RHO = 0, 1
 BDDC_SEL_VEF, BDDC_SEL_VE, BDDC_SEL_VF, BDDC_SEL_V = 0, 1, 2, 3
+BDDC_DEBUG_CLEAR, BDDC_DEBUG_NEGATE_NEUMANN_PIVOT, BDDC_DEBUG_NEGATE_DIRICHLET_PIVOT, BDDC_DEBUG_WAIT_TRIES = 0, 1, 2, 3
 SELECTIONS = {"vef": BDDC_SEL_VEF, "ve": BDDC_SEL_VE, "vf": BDDC_SEL_VF, "v": BDDC_SEL_V}
+BDDC_BETA_STANDARD, BDDC_BETA_FLEXIBLE = 0, 1
+BETA_RULES = {"standard": BDDC_BETA_STANDARD, "flexible": BDDC_BETA_FLEXIBLE}
 
 
 class BddcError(RuntimeError):
@@ -41,7 +44,7 @@ class Partition(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("weights", C.c_int), ("L_elems", C.c_int),
-                ("selection", C.c_int), ("use_graph", C.c_int), ("maxit", C.c_int)]
+                ("selection", C.c_int), ("use_graph", C.c_int), ("maxit", C.c_int), ("beta_rule", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -87,11 +90,12 @@ def _load():
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.bddc_get_coarse_matrix.argtypes = [vp, dp]
     lib.bddc_destroy.argtypes = [vp]
+    lib.bddc_debug_inject.argtypes = [C.c_int, C.c_longlong]
     lib.bddc_last_error.argtypes = [vp]
     lib.bddc_last_error.restype = C.c_char_p
     for f in ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
               "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
-              "bddc_set_apply_schedule"):
+              "bddc_set_apply_schedule", "bddc_debug_inject"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -100,7 +104,7 @@ lib = _load()
 
 EXPORTS = ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
            "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
-           "bddc_last_error", "bddc_set_apply_schedule")
+           "bddc_last_error", "bddc_set_apply_schedule", "bddc_debug_inject")
 
 
 def _check(code: int, handle=None):
@@ -115,11 +119,24 @@ def _ptr(t: torch.Tensor) -> C.c_void_p:
     return C.c_void_p(t.data_ptr())
 
 
+def _vptr(t: torch.Tensor, n: int) -> C.c_void_p:
+    """_ptr for a vector the library reads or writes n entries of."""
+    if t.numel() != n:
+        raise ValueError(f"expected {n} entries, got {t.numel()}")
+    return _ptr(t)
+
+
+def debug_inject(what: int, value: int = 0):
+    """bddc_debug_inject: process-wide test hooks (negated pivot at the next
+    setups, lowered report limit of the bounded device waits, or clear)."""
+    _check(lib.bddc_debug_inject(int(what), int(value)), None)
+
+
 def _stream() -> C.c_void_p:
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection="vef"):
+def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection="vef", beta="standard"):
     mesh = Mesh(nx, ny, nz, h)
     part = Partition()
     keep = []
@@ -131,7 +148,7 @@ def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selec
     prec = {"fp64": BDDC_FP64, "mixed": BDDC_MIXED}[precision] if isinstance(precision, str) else precision
     wts = {"card": BDDC_W_CARD, "rho": BDDC_W_RHO}[weights] if isinstance(weights, str) else weights
     sel = SELECTIONS[selection] if isinstance(selection, str) else selection
-    opt = Options(prec, wts, L, sel, int(use_graph), maxit)
+    opt = Options(prec, wts, L, sel, int(use_graph), maxit, BETA_RULES[beta] if isinstance(beta, str) else beta)
     return mesh, part, opt, keep
 
 
@@ -150,15 +167,15 @@ class BDDC:
 
     def __init__(self, nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int,
                  alpha: torch.Tensor, h: float = 0.0, precision="fp64", weights="card",
-                 maxit: int = 2000, use_graph: bool = False, selection="vef"):
+                 maxit: int = 2000, use_graph: bool = False, selection="vef", beta="standard"):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.h = h if h > 0 else 1.0 / nx
         self.n_nodes = (nx + 1) * (ny + 1) * (nz + 1)
         self.maxit = maxit
         mesh, part, opt, keep = _structs(nx, ny, nz, self.h, cuts, L, precision, weights, maxit, use_graph,
-                                         selection)
+                                         selection, beta)
         self._handle = C.c_void_p()
-        _check(lib.bddc_setup(C.byref(mesh), C.byref(part), C.byref(opt), _ptr(alpha), _stream(),
+        _check(lib.bddc_setup(C.byref(mesh), C.byref(part), C.byref(opt), _vptr(alpha, nx * ny * nz), _stream(),
                               C.byref(self._handle)), None)
 
     @classmethod
@@ -174,19 +191,19 @@ class BDDC:
 
     def apply(self, r: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         z = out if out is not None else self._vec()
-        _check(lib.bddc_apply(self._handle, _ptr(r), _ptr(z), _stream()), self._handle)
+        _check(lib.bddc_apply(self._handle, _vptr(r, self.n_nodes), _vptr(z, self.n_nodes), _stream()), self._handle)
         return z
 
     def apply_noalloc(self, r: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         """bddc_apply_noalloc: the same z = B r with the library's fixed device
         array as work space (no device allocation inside the call)."""
         z = out if out is not None else self._vec()
-        _check(lib.bddc_apply_noalloc(self._handle, _ptr(r), _ptr(z), _stream()), self._handle)
+        _check(lib.bddc_apply_noalloc(self._handle, _vptr(r, self.n_nodes), _vptr(z, self.n_nodes), _stream()), self._handle)
         return z
 
     def operator(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         y = out if out is not None else self._vec()
-        _check(lib.bddc_operator(self._handle, _ptr(x), _ptr(y), _stream()), self._handle)
+        _check(lib.bddc_operator(self._handle, _vptr(x, self.n_nodes), _vptr(y, self.n_nodes), _stream()), self._handle)
         return y
 
     def solve(self, b: torch.Tensor, rtol: float, out: Optional[torch.Tensor] = None, raise_on_noconv=True):
@@ -195,7 +212,8 @@ class BDDC:
         al = (C.c_double * cap)()
         be = (C.c_double * cap)()
         st = Stats(0, 0, 0.0, 0.0, C.cast(al, C.POINTER(C.c_double)), C.cast(be, C.POINTER(C.c_double)), cap, 0.0)
-        code = lib.pcg_solve(self._handle, _ptr(b), _ptr(x), rtol, C.byref(st), _stream())
+        code = lib.pcg_solve(self._handle, _vptr(b, self.n_nodes), _vptr(x, self.n_nodes), rtol, C.byref(st),
+                             _stream())
         if code != BDDC_OK and (raise_on_noconv or code != BDDC_ERR_NOCONV):
             _check(code, self._handle)
         it = st.iterations
@@ -207,7 +225,8 @@ class BDDC:
     def gradient(self, u: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         g = out if out is not None else torch.empty(self.nx * self.ny * self.nz, dtype=torch.float64,
                                                    device="cuda")
-        _check(lib.bddc_gradient(self._handle, _ptr(u), _ptr(lam), _ptr(g), _stream()), self._handle)
+        _check(lib.bddc_gradient(self._handle, _vptr(u, self.n_nodes), _vptr(lam, self.n_nodes),
+                                 _vptr(g, self.nx * self.ny * self.nz), _stream()), self._handle)
         return g
 
     def set_apply_schedule(self, ctas_per_subdomain: int):
@@ -260,6 +279,8 @@ def solve_host(nx, ny, nz, cuts, L, alpha: np.ndarray, b: np.ndarray, rtol: floa
     mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection)
     a = np.ascontiguousarray(alpha, dtype=np.float64)
     bb = np.ascontiguousarray(b, dtype=np.float64)
+    if a.size != nx * ny * nz or bb.size != (nx + 1) * (ny + 1) * (nz + 1):
+        raise ValueError("alpha needs nx*ny*nz entries and b (nx+1)(ny+1)(nz+1)")
     x = np.zeros_like(bb)
     st = Stats(0, 0, 0.0, 0.0, None, None, 0, 0.0)
     code = lib.bddc_solve_host(C.byref(mesh), C.byref(part), C.byref(opt),

@@ -47,6 +47,16 @@ struct BddcError : std::runtime_error {
 
 thread_local std::string g_setup_error;
 
+// Test hooks set by bddc_debug_inject (process-wide): the subdomain whose
+// local matrix the next setups assemble with a negated pivot, and the tries
+// after which bounded device waits report a timeout.
+struct DebugHooks {
+  int negate_sub = -1;
+  int negate_neumann = 1;
+};
+DebugHooks g_debug;
+std::mutex g_debug_mu;
+
 // Device blocks of destroyed handles (and the setup scratch of live ones) are
 // kept per device and handed to later allocations of the same size class: a
 // solver that sets up one problem after another with the same shapes then
@@ -198,6 +208,8 @@ struct bddc_handle {
   double *uI = nullptr, *t = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *partial = nullptr, *scal = nullptr, *hist_a = nullptr, *hist_b = nullptr;
   int* ctl = nullptr;             // PCG control block {it, continue, converged, breakdown}
+  int flexible = 0;               // PCG beta by the flexible (Polak-Ribiere) rule; zp keeps the last z
+  double* zp = nullptr;
   int* err = nullptr;
   // PCG loop as one CUDA graph (use_graph): a kernel setting the loop condition,
   // then a while node whose body is one PCG iteration writing into xw
@@ -545,7 +557,12 @@ void check_err_flags(bddc_handle* h, cudaStream_t st) {
   const char* what[] = {"", "alpha must be finite and > 0 (element ", "non-positive pivot in the Dirichlet factor of subdomain ",
                         "non-positive pivot in the Neumann factor of subdomain ",
                         "non-positive pivot in S_c of subdomain ", "non-positive pivot in the coarse factor, front ",
-                        "", "a bounded wait for a bulk copy gave up in block "};
+                        "", "a bounded device wait ran past its limit in block "};
+  // the flags are cleared once read, so that a later call on the handle
+  // reports only its own failures
+  const int clear[2] = {0, -1};
+  CK(cudaMemcpyAsync(h->err, clear, sizeof(clear), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
   const int code = std::min(std::max(e[0], 0), 7);
   std::string msg = std::string(what[code]) + std::to_string(e[1]) + (code == 1 ? ")" : "");
   throw BddcError(code == 1 ? BDDC_ERR_ARG : code == 7 ? BDDC_ERR_TIMEOUT : BDDC_ERR_NOT_SPD, msg);
@@ -648,6 +665,18 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     L.subs_lpt = upload(h, lpt, st);
   }
   L.apply_cluster = 2;
+  {
+    std::lock_guard<std::mutex> lk(g_debug_mu);
+    L.negate_sub = -1;
+    if (g_debug.negate_sub >= 0 && g_debug.negate_sub < (int)h->subs.size()) {
+      const SubDesc& s = h->subs[g_debug.negate_sub];
+      const bool hasI = s.w[0] > 1 && s.w[1] > 1 && s.w[2] > 1;
+      if (g_debug.negate_neumann || hasI) {
+        L.negate_sub = g_debug.negate_sub;
+        L.negate_neumann = g_debug.negate_neumann;
+      }
+    }
+  }
   L.lc = upload(h, h->lc, st);
   L.facD = h->dalloc(es * lay.D);
   L.facN = h->dalloc(es * lay.N);
@@ -721,7 +750,9 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->z = h->dnew<double>(N);
   h->p = h->dnew<double>(N);
   h->q = h->dnew<double>(N);
-  h->partial = h->dnew<double>(RED_BLOCKS);
+  h->partial = h->dnew<double>(2 * RED_BLOCKS);
+  h->flexible = h->opt.beta_rule == BDDC_BETA_FLEXIBLE;
+  if (h->flexible) h->zp = h->dnew<double>(N);
   h->scal = h->dnew<double>(8);
   h->ctl = h->dnew<int>(4);
   h->hist_cap = h->opt.maxit > 0 ? h->opt.maxit : 2000;
@@ -839,9 +870,15 @@ void pcg_body(bddc_handle* h, double* x, const cudaGraphConditionalHandle* cond,
   const long long N = h->n_nodes;
   const int maxit = h->hist_cap;
   apply(h, h->r, h->z, st);
-  launch_dot(h->r, h->z, N, h->partial, st);
-  launch_finalize(h->partial, h->scal, 3, h->hist_b, h->ctl, maxit, 0.0, nullptr, st);
-  launch_update_p(h->p, h->z, h->scal, N, st);
+  if (h->flexible) {
+    launch_dot2(h->r, h->z, h->zp, N, h->partial, st);
+    launch_finalize(h->partial, h->scal, 5, h->hist_b, h->ctl, maxit, 0.0, nullptr, st);
+    launch_update_p_keep(h->p, h->zp, h->z, h->scal, N, st);
+  } else {
+    launch_dot(h->r, h->z, N, h->partial, st);
+    launch_finalize(h->partial, h->scal, 3, h->hist_b, h->ctl, maxit, 0.0, nullptr, st);
+    launch_update_p(h->p, h->z, h->scal, N, st);
+  }
   launch_operator(h->m, h->alpha, h->p, h->q, h->partial, RED_BLOCKS, st);
   launch_finalize(h->partial, h->scal, 1, h->hist_a, h->ctl, maxit, 0.0, nullptr, st);
   launch_update_xr(x, h->r, h->p, h->q, h->scal, N, h->partial, st);
@@ -916,6 +953,7 @@ int pcg_impl(bddc_handle* h, const double* b, double* x, double rtol, bddc_stats
   CK(cudaEventRecord(e0, st));
   CK(cudaMemsetAsync(xs, 0, sizeof(double) * N, st));
   CK(cudaMemsetAsync(h->p, 0, sizeof(double) * N, st));
+  if (h->flexible) CK(cudaMemsetAsync(h->zp, 0, sizeof(double) * N, st));
   launch_masked_copy(h->m, b, h->r, st);
   launch_dot(h->r, h->r, N, h->partial, st);
   launch_finalize(h->partial, h->scal, 4, nullptr, h->ctl, maxit, rtol, nullptr, st);
@@ -948,7 +986,6 @@ int pcg_impl(bddc_handle* h, const double* b, double* x, double rtol, bddc_stats
   int status = BDDC_OK;
   if (breakdown) status = BDDC_ERR_BREAKDOWN;
   else if (!converged) status = BDDC_ERR_NOCONV;
-  check_err_flags(h, st);   // device-side failures of the applies (bounded waits)
   if (stats) {
     stats->iterations = it;
     stats->converged = converged;
@@ -962,6 +999,7 @@ int pcg_impl(bddc_handle* h, const double* b, double* x, double rtol, bddc_stats
     if (stats->betas && nb > 0)
       CK(cudaMemcpy(stats->betas, h->hist_b, sizeof(double) * nb, cudaMemcpyDeviceToHost));
   }
+  check_err_flags(h, st);   // device-side failures of the applies (bounded waits)
   return status;
 }
 
@@ -993,6 +1031,8 @@ std::unique_ptr<bddc_handle> make_handle(const bddc_mesh* mesh, const bddc_parti
   if (opt->L_elems < 1) throw BddcError(BDDC_ERR_ARG, "L must be >= 1");
   if (opt->precision != BDDC_FP64 && opt->precision != BDDC_MIXED) throw BddcError(BDDC_ERR_ARG, "bad precision");
   if (opt->weights != BDDC_W_CARD && opt->weights != BDDC_W_RHO) throw BddcError(BDDC_ERR_ARG, "bad weights");
+  if (opt->beta_rule != BDDC_BETA_STANDARD && opt->beta_rule != BDDC_BETA_FLEXIBLE)
+    throw BddcError(BDDC_ERR_ARG, "bad beta_rule");
   if (opt->selection < BDDC_SEL_VEF || opt->selection > BDDC_SEL_V)
     throw BddcError(BDDC_ERR_UNSUPPORTED,
                     "selection must keep the vertices (vef, ve, vf or v): vertices are the primal DOFs that keep "
@@ -1257,6 +1297,28 @@ extern "C" int bddc_destroy(bddc_handle* h) {
   cudaDeviceSynchronize();
   delete h;
   return BDDC_OK;
+}
+
+extern "C" int bddc_debug_inject(int what, long long value) {
+  std::lock_guard<std::mutex> lk(g_debug_mu);
+  switch (what) {
+    case BDDC_DEBUG_CLEAR:
+      g_debug = DebugHooks{};
+      set_wait_report_tries(WAIT_TRIES);
+      break;
+    case BDDC_DEBUG_NEGATE_NEUMANN_PIVOT:
+    case BDDC_DEBUG_NEGATE_DIRICHLET_PIVOT:
+      if (value < -1 || value > 2147483647LL) return BDDC_ERR_ARG;
+      g_debug.negate_sub = (int)value;
+      g_debug.negate_neumann = what == BDDC_DEBUG_NEGATE_NEUMANN_PIVOT;
+      break;
+    case BDDC_DEBUG_WAIT_TRIES:
+      set_wait_report_tries(value < 0 ? WAIT_TRIES : std::min<long long>(value, WAIT_TRIES));
+      break;
+    default:
+      return BDDC_ERR_ARG;
+  }
+  return cudaGetLastError() == cudaSuccess ? BDDC_OK : BDDC_ERR_CUDA;
 }
 
 extern "C" const char* bddc_last_error(const bddc_handle* h) {

@@ -36,6 +36,8 @@ struct LocalLaunch {
   int maxQD, maxNzD, maxND;   // Dirichlet: plane size, planes, nodes
   int maxQN, maxNzN, maxNN;   // Neumann
   int maxNB, maxNc;
+  int negate_sub = -1;        // test hook: subdomain whose local matrix gets a negated pivot (-1: none)
+  int negate_neumann = 1;     // ... in its Neumann (1) or Dirichlet (0) matrix
 };
 
 // ev (may be null): 3 events recorded after the Dirichlet factorisation, the
@@ -52,6 +54,9 @@ template <typename T> void launch_neumann_rhs(const LocalLaunch& L, const double
 template <typename T> void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st);
 template <typename T> void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t st);
 void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st);
+// test hook: tries after which the bounded waits of the local kernels report
+// a timeout (they then still wait, bounded, for the work they cover)
+void set_wait_report_tries(long long tries);
 void launch_piece_alpha(const MeshDev& m, const double* alpha, const int* plo, const int* phi, int npx, int npy,
                         int npz, double* pw, cudaStream_t st);
 
@@ -175,5 +180,9 @@ void launch_loop_condition(const int* ctl, cudaGraphConditionalHandle cond, cuda
 void launch_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, long long n,
                       double* partial, cudaStream_t st);
 void launch_update_p(double* p, const double* z, const double* scal, long long n, cudaStream_t st);
+// flexible (Polak-Ribiere) recurrence: r.z and r.zp into 2 RED_BLOCKS partials;
+// p = z + beta p with zp = z
+void launch_dot2(const double* r, const double* z, const double* zp, long long n, double* partial, cudaStream_t st);
+void launch_update_p_keep(double* p, double* zp, const double* z, const double* scal, long long n, cudaStream_t st);
 
 }  // namespace bddc

@@ -1511,6 +1511,20 @@ k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict
 template <typename T>
 size_t dense_smem() { return sizeof(DenseSmem<T>); }
 
+// Test hook (host-side fault injection): negates the first diagonal entry of
+// one subdomain's assembled local matrix, Neumann or Dirichlet, so that its
+// factorisation meets a non-positive pivot.  One thread.
+template <typename T>
+__global__ void k_debug_negate(const SubDesc* __restrict__ subs, T* __restrict__ fac, int sub, int neumann) {
+  const SubDesc s = subs[sub];
+  T* base = fac + (neumann ? s.offN : s.offD);
+  base[0] = -base[0];
+}
+
+void set_wait_report_tries(long long tries) {
+  cudaMemcpyToSymbol(g_wait_report_tries, &tries, sizeof(tries));
+}
+
 template <typename T>
 void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) {
   const int S = L.nsub;
@@ -1523,6 +1537,10 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
   }
   k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1);
   BDDC_COUNT(1);
+  if (L.negate_sub >= 0) {
+    k_debug_negate<T><<<1, 1, 0, st>>>(L.subs, L.negate_neumann ? facN : facD, L.negate_sub, L.negate_neumann);
+    BDDC_COUNT(1);
+  }
   if (ev) cudaEventRecord(ev[0], st);
   // both factorisations in one launch: y = 0 Neumann, y = 1 Dirichlet; the
   // packed Schur matrix takes the shared memory left after the pivot columns

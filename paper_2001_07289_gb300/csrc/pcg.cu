@@ -40,12 +40,34 @@ void launch_dot(const double* a, const double* b, long long n, double* partial, 
   k_dot<<<RED_BLOCKS, 256, 0, st>>>(a, b, n, partial);
 }
 
+// r.z and r.zp in one pass: partials of the first in partial[0, RED_BLOCKS),
+// of the second in partial[RED_BLOCKS, 2 RED_BLOCKS)
+__global__ void k_dot2(const double* __restrict__ r, const double* __restrict__ z, const double* __restrict__ zp,
+                       long long n, double* __restrict__ partial) {
+  double s = 0.0, t = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    s = fma(ri, z[i], s);
+    t = fma(ri, zp[i], t);
+  }
+  block_partial_p(s, partial);
+  __syncthreads();
+  block_partial_p(t, partial + RED_BLOCKS);
+}
+
+void launch_dot2(const double* r, const double* z, const double* zp, long long n, double* partial, cudaStream_t st) {
+  BDDC_COUNT(1);
+  k_dot2<<<RED_BLOCKS, 256, 0, st>>>(r, z, zp, n, partial);
+}
+
 // One block sums the partials in a fixed order and updates the CG scalars and
 // the control block ctl = {it, continue, converged, breakdown}.
 //   op 4 (start):  bb = sum; threshold rtol ||b||_2 (Section 5 stopping rule),
 //                  it = 0, converged iff b = 0, continue iff not converged.
 //   op 3 (beta):   rz_new = sum; beta = 0 on the first iteration, else
 //                  rz_new / rz (hist[it - 1] = beta); rz = rz_new.
+//   op 5 (flexible beta): as op 3 with beta = (rz_new - r.z_prev) / rz, where
+//                  r.z_prev is the sum of the second partial array.
 //   op 1 (alpha):  pq = sum; alpha = rz / pq (hist[it] = alpha); breakdown if
 //                  pq <= 0 or alpha is not finite.
 //   op 2 (test):   rr = sum; ++it; converged iff ||r||_2 <= threshold and no
@@ -53,18 +75,26 @@ void launch_dot(const double* a, const double* b, long long n, double* partial, 
 // With use_cond the continue flag also sets the condition of the enclosing
 // graph's while node, which is what ends a PCG loop captured in a graph: it
 // grows by one per body, so the loop runs at most maxit times.
-__global__ void k_finalize(const double* __restrict__ partial, double* scal, int op, double* hist, int* ctl,
-                           int maxit, double rtol, cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ double ws[32];
+__device__ inline double fixed_order_sum(const double* __restrict__ partial, double* ws) {
   double v = 0.0;
   for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) v += partial[i];
   v = wsum(v);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) ws[warp] = v;
   __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+  __syncthreads();
+  return s;
+}
+
+__global__ void k_finalize(const double* __restrict__ partial, double* scal, int op, double* hist, int* ctl,
+                           int maxit, double rtol, cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double ws[32];
+  const double s = fixed_order_sum(partial, ws);
+  // op 5: the second sum, r_{k+1}.z_k
+  const double s2 = op == 5 ? fixed_order_sum(partial + RED_BLOCKS, ws) : 0.0;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
     int cont = -1;
     switch (op) {
       case 4: {
@@ -83,6 +113,20 @@ __global__ void k_finalize(const double* __restrict__ partial, double* scal, int
         double b = 0.0;
         if (it > 0) {
           b = s / scal[0];
+          if (!isfinite(b)) { ctl[3] = 1; b = 0.0; }
+          if (hist) hist[it - 1] = b;
+        }
+        scal[5] = b;
+        scal[0] = s;
+        break;
+      }
+      case 5: {
+        // Polak-Ribiere (flexible) beta: r_{k+1}.(z_{k+1} - z_k) / r_k.z_k
+        scal[4] = s;
+        const int it = ctl[0];
+        double b = 0.0;
+        if (it > 0) {
+          b = (s - s2) / scal[0];
           if (!isfinite(b)) { ctl[3] = 1; b = 0.0; }
           if (hist) hist[it - 1] = b;
         }
@@ -164,6 +208,22 @@ __global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z,
 void launch_update_p(double* p, const double* z, const double* scal, long long n, cudaStream_t st) {
   BDDC_COUNT(1);
   k_update_p<<<RED_BLOCKS, 256, 0, st>>>(p, z, scal, n);
+}
+
+// p = z + beta p and zp = z (the flexible recurrence keeps the last z)
+__global__ void k_update_p_keep(double* __restrict__ p, double* __restrict__ zp, const double* __restrict__ z,
+                                const double* __restrict__ scal, long long n) {
+  const double b = scal[5];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double zi = z[i];
+    p[i] = fma(b, p[i], zi);
+    zp[i] = zi;
+  }
+}
+
+void launch_update_p_keep(double* p, double* zp, const double* z, const double* scal, long long n, cudaStream_t st) {
+  BDDC_COUNT(1);
+  k_update_p_keep<<<RED_BLOCKS, 256, 0, st>>>(p, zp, z, scal, n);
 }
 
 }  // namespace bddc

@@ -9,8 +9,9 @@
 // needed per chunk; one thread (the producer) waits on "empty" before it
 // refills the buffer with chunk c + NBUF.  Chunks must start on 16-byte
 // boundaries and their byte counts are rounded up to 16; callers pad their
-// allocations accordingly.  Every wait is bounded: a wait that gives up
-// records error code 7 (timeout) and the kernel carries on to its end.
+// allocations accordingly.  Every wait is bounded: a wait that runs past its
+// limit records error code 7 (timeout), waits (bounded again) for the copy
+// it covers and the kernel carries on to its end.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -54,10 +55,22 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
+// Tries after which a bounded wait reports a timeout.  WAIT_TRIES unless a
+// test lowers it (bddc_debug_inject); one copy per translation unit.
+static __device__ long long g_wait_report_tries = WAIT_TRIES;
+
+// Waits for the phase with the given parity.  After g_wait_report_tries
+// unsuccessful tries it records error code 7 (timeout) with the block index;
+// the copy or MMA the barrier tracks is still this CTA's own work in flight,
+// so it then keeps waiting, for at most WAIT_TRIES more tries, before it
+// returns.  Returns whether the phase completed.
 __device__ inline bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
-  for (long long i = 0; i < WAIT_TRIES; ++i)
+  const long long report = g_wait_report_tries;
+  for (long long i = 0; i < report; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   if (err && atomicCAS(err, 0, 7) == 0) err[1] = blockIdx.x;
+  for (long long i = 0; i < WAIT_TRIES; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
 

@@ -1,0 +1,86 @@
+"""Full-size parity of the benched workload against the oracle.
+
+poisson48: 48^3 Q1 hexahedra on the unit cube, 4^3 box subdomains of 12^3,
+manufactured f, PCG rtol 1e-10 from x0 = 0 (Section 5's residual rule), at
+L = 4h (n_c = 4,167) and L = 2h (n_c = 18,639: every interface DOF is primal,
+so B = A^{-1} and PCG stops after one step, Section 3 with Theorem 1).  The GPU
+path runs through the C ABI in the launch configuration the bench times (PCG
+as one CUDA graph); the oracle's PCG with its two-level apply is the
+reference, element by element:
+
+- FP64 path: relative error <= 1e-10 and iteration counts within 1;
+- mixed path (FP32 local factors and solves, FP64 outer PCG): relative error
+  <= 1e-8 and iteration counts within 2;
+- both: the GPU's residual claim holds in the oracle's arithmetic, and one
+  preconditioner application matches the oracle's on a seeded vector
+  (relative to the vector's largest entry: 1e-10 FP64; 1e-4 mixed, FP32 unit
+  roundoff 6e-8 times the condition numbers, about 1e3, of the 12^3 local
+  constrained Neumann problems), which compares every level of the coarse
+  nested-dissection factor at this size.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bddc as orc  # noqa: E402
+from paper_2001_07289_gb300 import inputs  # noqa: E402
+
+if torch.cuda.is_available():
+    from paper_2001_07289_gb300.bddc import BDDC  # noqa: E402
+
+_cache = {}
+
+
+def oracle48(L):
+    """The oracle set up on poisson48 with subobject size L h, its PCG result
+    at rtol 1e-10 and one application on a seeded vector."""
+    if L not in _cache:
+        p = inputs.workload(1, L=L, precision="fp64")
+        ref = orc.build(p)
+        res = orc.pcg(ref.operator, ref.apply, p.b, p.rtol)
+        r = inputs.random_node_vector(p.nx, p.ny, p.nz, 31)
+        _cache[L] = (p, ref, res, r, ref.apply(r))
+    return _cache[L]
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("L,n_coarse", [(4, 4167), (2, 18639)])
+@pytest.mark.parametrize("precision,tol,dit,atol", [("fp64", 1e-10, 1, 1e-10), ("mixed", 1e-8, 2, 1e-4)])
+def test_poisson48_matches_oracle(L, n_coarse, precision, tol, dit, atol):
+    p, ref, res, r, Br = oracle48(L)
+    assert ref.n_coarse == n_coarse and res.converged
+    pre = BDDC.from_problem(p, precision=precision, use_graph=True)
+    assert pre.info()["n_coarse"] == n_coarse
+    # one application, element by element
+    z = pre.apply(cu(r)).cpu().numpy()
+    assert np.abs(z - Br).max() <= atol * np.abs(Br).max()
+    # the PCG solution
+    x, st = pre.solve(cu(p.b), p.rtol)
+    pre.close()
+    assert st["converged"]
+    assert abs(st["iterations"] - res.iterations) <= dit, (st["iterations"], res.iterations)
+    xg = x.cpu().numpy()
+    err = np.linalg.norm(xg - res.x) / np.linalg.norm(res.x)
+    assert err <= tol, err
+    bf = p.b * (1 - ref.bnd)
+    assert np.linalg.norm(bf - ref.operator(xg)) <= 1.01 * p.rtol * np.linalg.norm(bf)
+    if L == 2 and precision == "fp64":
+        assert st["iterations"] == res.iterations == 1
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-5)])
+def test_poisson48_L2_is_exact_inverse(precision, tol):
+    """L = 2h: every subobject holds one DOF, every interface DOF is primal,
+    W-tilde = U and B = A^{-1}; so B A x = x for any x (FP64 to rounding, the
+    mixed path to its FP32 local solves)."""
+    p = inputs.workload(1, L=2, precision=precision)
+    pre = BDDC.from_problem(p)
+    x = inputs.random_node_vector(p.nx, p.ny, p.nz, 9)
+    y = pre.apply(pre.operator(cu(x))).cpu().numpy()
+    pre.close()
+    assert np.abs(y - x).max() <= tol * np.abs(x).max()

@@ -31,10 +31,11 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("beta", ["standard", "flexible"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_graph_equals_host_loop(name):
+def test_graph_equals_host_loop(name, beta):
     p = CASES[name]()
-    host, graph = _pair(p)
+    host, graph = _pair(p, beta=beta)
     b = torch.from_numpy(p.b).cuda()
     xh, sh = host.solve(b, p.rtol)
     for rep in range(2):   # the second solve reuses the captured graph

@@ -71,11 +71,6 @@ def test_channels96_full_size():
     assert err <= 1e-8, err
 
 
-def _J(u, uobs, bnd):
-    d = np.where(bnd, 0.0, u - uobs)
-    return 0.5 * float(d @ d)
-
-
 def test_adjoint_autograd_matches_oracle_small():
     """BddcSolve backward against the oracle's adjoint gradient (direct solves)
     on a 12^3 mesh with a Gaussian-field coefficient; relative error <= 1e-6."""
@@ -94,11 +89,33 @@ def test_adjoint_autograd_matches_oracle_small():
     assert np.abs(g - want).max() <= 1e-6 * np.abs(want).max()
 
 
+def test_adjoint_autograd_matches_oracle_32():
+    """The same at 32^3 with 4^3 subdomains of 8^3 and L = 4h: the gradient
+    through the autograd Function (forward and adjoint PCG to 1e-13 on the
+    same handle) against the oracle's adjoint gradient from sparse direct
+    solves; relative error <= 1e-6."""
+    n = 32
+    p = inputs.box_problem(n, n, n, [inputs.uniform_cuts(n, 4)] * 3, 4,
+                           alpha=np.exp(inputs.gaussian_field(n, n, n, 0.1, 21)))
+    uobs = inputs.random_node_vector(n, n, n, 22) * 1e-3
+    bnd = fem.boundary_node_mask(n, n, n)
+    alpha = cu(p.alpha).requires_grad_(True)
+    u = BddcSolve.apply(alpha, cu(p.b), p, 1e-13)
+    J = 0.5 * torch.sum(torch.where(cu(bnd), 0.0, u - cu(uobs)) ** 2)
+    J.backward()
+    g = alpha.grad.cpu().numpy()
+    uo = orc.direct_solve(n, n, n, p.h, p.alpha, p.b)
+    lam = orc.direct_solve(n, n, n, p.h, p.alpha, np.where(bnd, 0.0, uo - uobs))
+    want = orc.gradient(n, n, n, p.h, uo, lam)
+    assert np.abs(g - want).max() <= 1e-6 * np.abs(want).max()
+
+
 def test_adjoint64_full_size():
     """Workload 4 (64^3, 4^3 subdomains, log alpha a Gaussian field, FP64):
     u_obs from a second field plus 1 % noise; the gradient from the autograd
     Function satisfies sum_e alpha_e g_e = -lambda^T b and matches central
-    differences in theta = log alpha (step 1e-6) along two seeded directions."""
+    differences in theta = log alpha (step 1e-6) along all 20 seeded
+    directions of the workload."""
     p = inputs.workload(4)
     n = p.nx
     bnd = fem.boundary_node_mask(n, n, n)
@@ -120,16 +137,21 @@ def test_adjoint64_full_size():
     rhs = -float(lam.cpu().numpy() @ p.b)
     assert abs(lhs - rhs) <= 1e-8 * abs(rhs)
     pre.close()
-    dirs = inputs.fd_directions(p.n_elems, count=2)
+    dirs = inputs.fd_directions(p.n_elems, count=20)
+    assert dirs.shape == (20, p.n_elems)
     t = 1e-6
     for d in dirs:
-        vals = []
+        us = []
         for sgn in (1.0, -1.0):
             pp = BDDC.from_problem(p, alpha=cu(p.alpha * np.exp(sgn * t * d)), precision="fp64")
-            us, _ = pp.solve(b, 1e-14, raise_on_noconv=False)
-            vals.append(_J(us.cpu().numpy(), uobs, bnd))
+            u_s, _ = pp.solve(b, 1e-14, raise_on_noconv=False)
+            us.append(np.where(bnd, 0.0, u_s.cpu().numpy()))
             pp.close()
-        fd = (vals[0] - vals[1]) / (2 * t)
+        # (J(+t) - J(-t)) / 2t in the product form 1/2 sum (u+ - u-)(u+ + u- - 2 u_obs):
+        # the same number without subtracting two values of J (about 10 each)
+        # that agree to nine digits
+        ob = np.where(bnd, 0.0, uobs)
+        fd = 0.5 * float((us[0] - us[1]) @ (us[0] + us[1] - 2.0 * ob)) / (2 * t)
         an = float(np.sum(g * p.alpha * d))
         assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
 
@@ -142,27 +164,53 @@ def _jitter(n, parts, seed, precision):
     return inputs.box_problem(n, n, n, cuts, 4, alpha=a, rtol=1e-10, precision=precision)
 
 
-@pytest.mark.parametrize("precision,tol,dit", [("fp64", 1e-10, 1), ("mixed", 1e-6, 12)])
-def test_jitter_recipe_matches_oracle(precision, tol, dit):
+def test_jitter_recipe_fp64_matches_oracle():
     """The jitter128 input recipe at 24^3 (3^3 jittered subdomains), run with
-    the PCG loop as a CUDA graph, against the oracle's PCG (about a hundred
-    iterations: alpha is not constant on subobjects).  The FP64 path follows
-    the oracle's iterates; the mixed path's FP32 local solves perturb a run
-    this long, so it gets a wider iteration window and is held to the
-    tolerance through its residual in the oracle's arithmetic."""
-    p = _jitter(24, 3, 91, precision)
-    ref = orc.build(inputs.box_problem(p.nx, p.ny, p.nz, p.cuts, p.L, alpha=p.alpha))
+    the PCG loop as a CUDA graph, against the oracle's PCG at rtol 1e-10
+    (about a hundred iterations: alpha is not constant on subobjects): the
+    FP64 path follows the oracle's iterates, relative error <= 1e-10 and
+    iteration counts within 1."""
+    p = _jitter(24, 3, 91, "fp64")
+    ref = orc.build(p)
     res = orc.pcg(ref.operator, ref.apply, p.b, p.rtol)
     pre = BDDC.from_problem(p, alpha=cu(p.alpha), use_graph=True)
     x, st = pre.solve(cu(p.b), p.rtol)
     pre.close()
     assert st["converged"] and res.converged
-    assert abs(st["iterations"] - res.iterations) <= dit, (st["iterations"], res.iterations)
+    assert abs(st["iterations"] - res.iterations) <= 1, (st["iterations"], res.iterations)
     xg = x.cpu().numpy()
-    err = np.linalg.norm(xg - res.x) / np.linalg.norm(res.x)
-    assert err <= tol, err
+    assert np.linalg.norm(xg - res.x) / np.linalg.norm(res.x) <= 1e-10
     bf = p.b * (1 - ref.bnd)
     assert np.linalg.norm(bf - ref.operator(xg)) <= 1.01 * p.rtol * np.linalg.norm(bf)
+
+
+@pytest.mark.parametrize("beta", ["standard", "flexible"])
+def test_jitter_recipe_mixed_matches_oracle(beta):
+    """The same recipe on the mixed path (FP32 local factors and solves),
+    compared as the tolerance reading for configurations that cannot meet
+    1e-8 at their own rtol prescribes: both solved to rtol 1e-12, relative
+    error <= 1e-8, the GPU's residual claim checked in the oracle's
+    arithmetic.  Iterations at the workload's rtol 1e-10: the FP32 local
+    solves add a measured 11 to the oracle's 102 (113 standard, 114 flexible
+    beta); storing only the Neumann factor, or only Phi, of the FP64 path in
+    FP32 already adds 8 and 7 (the constrained Neumann correction
+    Phi (u_c - C y) + y cancels large near-kernel components of y when alpha
+    varies by 1e4 between elements), so the window is 12 + 1."""
+    p = _jitter(24, 3, 91, "mixed")
+    ref = orc.build(inputs.box_problem(p.nx, p.ny, p.nz, p.cuts, p.L, alpha=p.alpha))
+    pre = BDDC.from_problem(p, alpha=cu(p.alpha), use_graph=True, beta=beta)
+    res10 = orc.pcg(ref.operator, ref.apply, p.b, 1e-10)
+    _, st = pre.solve(cu(p.b), 1e-10)
+    assert st["converged"] and res10.converged
+    assert 0 <= st["iterations"] - res10.iterations <= 13, (st["iterations"], res10.iterations)
+    res = orc.pcg(ref.operator, ref.apply, p.b, 1e-12)
+    x, st = pre.solve(cu(p.b), 1e-12)
+    pre.close()
+    assert st["converged"] and res.converged
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - res.x) / np.linalg.norm(res.x) <= 1e-8
+    bf = p.b * (1 - ref.bnd)
+    assert np.linalg.norm(bf - ref.operator(xg)) <= 1.01e-12 * np.linalg.norm(bf)
 
 
 def test_jitter128_full_size():

@@ -70,3 +70,26 @@ def test_apply_noalloc_after_larger_problem():
     assert np.abs(g - w).max() <= 1e-10 * np.abs(w).max()
     pb.close()
     ps.close()
+
+
+def test_apply_noalloc_rejects_a_problem_above_the_limit():
+    """A problem whose apply needs more work space than the fixed array holds
+    (112^3 nodes on the mixed path, about 36 MB against 32 MiB) is refused
+    with BDDC_ERR_ARG and a message giving the bytes needed; nothing is
+    launched, so the output vector is left as it was."""
+    import re
+    import paper_2001_07289_gb300.bddc as gb
+    n = 112
+    p = inputs.box_problem(n, n, n, [inputs.uniform_cuts(n, 8)] * 3, 4, precision="mixed")
+    pre = gb.BDDC.from_problem(p)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    r = torch.from_numpy(inputs.random_node_vector(n, n, n, 7)).cuda()
+    z = torch.full_like(r, 5.0)
+    code = gb.lib.bddc_apply_noalloc(pre._handle, gb._ptr(r), gb._ptr(z), stream)
+    assert code == gb.BDDC_ERR_ARG
+    msg = gb.lib.bddc_last_error(pre._handle).decode()
+    need = int(re.search(r"needs (\d+) bytes", msg).group(1))
+    assert need > (32 << 20)
+    torch.cuda.synchronize()
+    assert torch.all(z == 5.0)
+    pre.close()
