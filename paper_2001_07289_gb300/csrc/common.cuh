@@ -99,6 +99,24 @@ __device__ inline bool on_dirichlet(const MeshDev& m, int i, int j, int k) {
   return i == 0 || j == 0 || k == 0 || i == m.nx || j == m.ny || k == m.nz;
 }
 
+// Local grid of subdomain s: the Neumann grid (w+1 nodes per axis) or the
+// Dirichlet grid of interior nodes (w-1 per axis, empty if some w < 2).
+struct Grid {
+  int gx, gy, gz, off;  // local grid sizes; global coordinate = e0 + off + local
+};
+__device__ inline Grid grid_of(const SubDesc& s, int neumann) {
+  Grid g;
+  if (neumann) { g.gx = s.w[0] + 1; g.gy = s.w[1] + 1; g.gz = s.w[2] + 1; g.off = 0; }
+  else { g.gx = s.w[0] - 1; g.gy = s.w[1] - 1; g.gz = s.w[2] - 1; g.off = 1; }
+  if (g.gx <= 0 || g.gy <= 0 || g.gz <= 0) { g.gx = g.gy = g.gz = 0; }
+  return g;
+}
+
+// First device-side failure wins: error code and the subdomain (or front) id.
+__device__ inline void set_error(int* err, int code, int sub) {
+  if (atomicCAS(err, 0, code) == 0) err[1] = sub;
+}
+
 // Box-surface list of a px x py x pz grid.
 __host__ __device__ inline int surf_count(int px, int py, int pz) {
   int ring = 2 * px + 2 * (py - 2);

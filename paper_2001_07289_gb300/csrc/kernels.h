@@ -40,6 +40,13 @@ struct LocalLaunch {
   int negate_neumann = 1;     // ... in its Neumann (1) or Dirichlet (0) matrix
 };
 
+// schur_tc.cu: the local factorisations on the tensor cores (FP32 path,
+// planes of at most TCS_MAXQ nodes)
+constexpr int TCS_MAXQ = 176;
+size_t schur_tc_smem(int maxQ);
+void configure_schur_tc();
+void launch_schur_tc(const LocalLaunch& L, cudaStream_t st);
+
 // ev (may be null): 3 events recorded after the Dirichlet factorisation, the
 // Neumann factorisation and the coarse basis.
 template <typename T> void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev);

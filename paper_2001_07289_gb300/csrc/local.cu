@@ -70,21 +70,6 @@ __device__ inline bool neumann_fixed(const MeshDev& m, const SubDesc& s, int ix,
   return surf && m.ax[0].hat[gx] && m.ax[1].hat[gy] && m.ax[2].hat[gz];
 }
 
-struct Grid {
-  int gx, gy, gz, off;  // local grid sizes; global coordinate = e0 + off + local
-};
-__device__ inline Grid grid_of(const SubDesc& s, int neumann) {
-  Grid g;
-  if (neumann) { g.gx = s.w[0] + 1; g.gy = s.w[1] + 1; g.gz = s.w[2] + 1; g.off = 0; }
-  else { g.gx = s.w[0] - 1; g.gy = s.w[1] - 1; g.gz = s.w[2] - 1; g.off = 1; }
-  if (g.gx <= 0 || g.gy <= 0 || g.gz <= 0) { g.gx = g.gy = g.gz = 0; }
-  return g;
-}
-
-__device__ inline void set_error(int* err, int code, int sub) {
-  if (atomicCAS(err, 0, code) == 0) err[1] = sub;
-}
-
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 template <typename T>
@@ -1544,7 +1529,9 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
   if (ev) cudaEventRecord(ev[0], st);
   // both factorisations in one launch: y = 0 Neumann, y = 1 Dirichlet; the
   // packed Schur matrix takes the shared memory left after the pivot columns
-  {
+  if (std::is_same<T, float>::value && L.maxQN <= TCS_MAXQ && L.maxQD <= TCS_MAXQ) {
+    launch_schur_tc(L, st);   // rank-16 updates on the tensor cores, matrix in TMEM
+  } else {
     const int maxQ = std::max(L.maxQN, L.maxQD);
     const size_t smb = 227 * 1024;
     const long long cap = (long long)(smb / sizeof(T)) - 2LL * maxQ - 2;
@@ -1586,6 +1573,7 @@ template <typename T>
 void configure_local_kernels() {
   size_t sm = dense_smem<T>();
   cudaFuncSetAttribute(k_btschur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (std::is_same<T, float>::value) configure_schur_tc();
   cudaFuncSetAttribute(k_btsolve_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_btsolve_multi_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(2 * TC_STAGE_BYTES + 9 * 256 * sizeof(float)));
