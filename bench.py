@@ -13,7 +13,8 @@ value = free DOF solved per second (MDOF/s) over all ranks, i.e.
 n_free * N / time-to-solution.  Extra keys: preconditioner applies/s and MDOF/s
 (100 back-to-back bddc_apply), setup phases, iterations, roofline of the
 dominant phase, the oracle as CPU baseline, and end-to-end numbers through
-bddc_solve_host with host buffers.
+bddc_solve_host with host buffers; and (--no-workloads to skip) one timed
+step of each other workload (channels96, jitter128, adjoint64) on both paths.
 
 --impl reference times the FP64 CPU oracle (test infrastructure written from
 the paper) on the host cores, on a bounded sample of the same workload.
@@ -58,6 +59,31 @@ def _hbm_peak():
 
 HBM_PEAK_GBS = _hbm_peak()
 FP32_PEAK_TFLOPS = 80.5    # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+
+
+def _tf32_peak():
+    """Dense TF32 tensor peak: the measured BF16 GEMM rate times the nominal
+    TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "MEASURED_PEAKS.json bf16_tflops x 1.1/2.25"
+    except (OSError, KeyError, ValueError):
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 1.9 PFLOP/s x 1.1/2.25"
+
+
+TF32_PEAK_TFLOPS, TF32_PEAK_SOURCE = _tf32_peak()
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def _traffic():
@@ -192,6 +218,8 @@ def main():
                     help="run only the warm-up and timed steps (for profiler launch lists)")
     ap.add_argument("--only-applies", type=int, default=0,
                     help="set up once, then run this many preconditioner applies (for profiler launch lists)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the one-step lines of the other workloads (channels96, jitter128, adjoint64)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -215,9 +243,11 @@ def main():
     from paper_2001_07289_gb300 import inputs
     from paper_2001_07289_gb300.bddc import BDDC, solve_host
 
-    cpu_base = None
+    cpu_base = cpu_one = None
+    ncores = os.cpu_count() or 1
     if rank == 0 and world == 1 and args.workload == "poisson48" and not (args.no_cpu_baseline or args.only_steps):
-        cpu_base = run_oracle_subprocess("full", threads=1)
+        cpu_base = run_oracle_subprocess("full", threads=ncores)
+        cpu_one = run_oracle_subprocess("full", threads=1)
 
     torch.cuda.set_device(local_rank)
     if world > 1:
@@ -360,6 +390,12 @@ def main():
         if k > 0:
             e2e_t.append(dt)
 
+    # ---- one timed step of each other workload, both precisions
+    workloads = {}
+    if not args.no_workloads and args.workload == "poisson48" and world == 1:
+        for name in ("channels96", "jitter128", "adjoint64"):
+            workloads[name] = run_workload(name, flush, stream)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -377,16 +413,28 @@ def main():
     # inverse Schur complements over the phase's event time.
     nc = info["n_coarse"]
     fac_ms = info["phase_ms"][2]
-    fac_tflops = 2.0 * info["local_factor_fma"] / (fac_ms * 1e-3) / 1e12
-    peak_local = FP32_PEAK_TFLOPS if args.precision == "mixed" else FP64_PEAK_TFLOPS
-    roofline = {"kernel": "k_btschur (local Dirichlet + Neumann inverse Schur complements, one launch)",
-                "bound": "alu", "achieved": round(fac_tflops, 4), "peak": peak_local, "unit": "TFLOP/s",
-                "frac": round(fac_tflops / peak_local, 4),
-                "traffic": traffic_of("k_btschur", args.workload, args.precision),
-                "algorithmic": f"{2 * info['local_factor_fma']:.3e} flop per launch (sum over subdomains and "
-                               "planes of Q^3/2 + 18 Q^2 multiply-adds)",
-                "peak_source": ("FP32 derived from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-                                if args.precision == "mixed" else "GB300 FP64 nominal 1.25 TFLOP/s")}
+    # the method-level count: banded Cholesky of the local Dirichlet and
+    # Neumann matrices, sum of n b^2 (the kernel itself computes explicit
+    # inverse Schur complements, Q^3/2 + 18 Q^2 multiply-adds per plane)
+    fac_tflops = info["local_band_flops"] / (fac_ms * 1e-3) / 1e12
+    tc = info["factor_kernel"] == 1
+    if args.precision == "mixed":
+        peak_local, peak_src = (TF32_PEAK_TFLOPS, TF32_PEAK_SOURCE) if tc else (
+            FP32_PEAK_TFLOPS, "FP32 derived from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz")
+    else:
+        peak_local, peak_src = FP64_PEAK_TFLOPS, "GB300 FP64 nominal 1.25 TFLOP/s"
+    roofline = {"kernel": ("k_btschur_tc (local Dirichlet + Neumann inverse Schur complements, rank-16 updates "
+                           "on the tensor cores, one launch)" if tc else
+                           "k_btschur (local Dirichlet + Neumann inverse Schur complements, one launch)"),
+                "bound": "tensor" if tc else "alu", "achieved": round(fac_tflops, 4), "peak": round(peak_local, 1),
+                "unit": "TFLOP/s", "frac": round(fac_tflops / peak_local, 5),
+                "frac_of_fp32_simt": round(fac_tflops / FP32_PEAK_TFLOPS, 4),
+                "traffic": traffic_of("k_btschur_tc" if tc else "k_btschur", args.workload, args.precision),
+                "algorithmic": f"{info['local_band_flops']:.3e} flop per launch (banded Cholesky of the local "
+                               "Dirichlet and Neumann matrices: sum over subdomains of n_I b_I^2 + n_N b_N^2)",
+                "kernel_flop": f"{2 * info['local_factor_fma']:.3e} flop executed (explicit inverse Schur "
+                               "complements: Q^3/2 + 18 Q^2 multiply-adds per plane)",
+                "peak_source": peak_src + " (of measured)" if "MEASURED" in peak_src else peak_src}
     chol_ms = info["phase_ms"][5]
     chol_tflops = 2.0 * info["coarse_fma"] / (chol_ms * 1e-3) / 1e12
     apply_gbs = info_apply["apply_bytes"] / (apply_ms * 1e-3) / 1e9
@@ -443,12 +491,63 @@ def main():
         "clocks": clk.summary(),
     }
     if cpu_base:
-        out["cpu_baseline"] = {"value": round(cpu_base["mdofs"], 6), "unit": "MDOF/s", "cores": 1,
-                               "kind": "oracle", "sample": cpu_base["sample"] + " setup+PCG, 1 thread",
-                               "seconds": round(cpu_base["seconds"], 2), "iterations": cpu_base["iterations"]}
+        out["cpu_baseline"] = {"value": round(cpu_base["mdofs"], 6), "unit": "MDOF/s", "cores": ncores,
+                               "kind": "oracle", "cpu": cpu_model(),
+                               "sample": cpu_base["sample"] + f" setup+PCG, BLAS threads = {ncores} (numpy/scipy; "
+                                         "the sparse LU solves are single-threaded)",
+                               "seconds": round(cpu_base["seconds"], 2), "iterations": cpu_base["iterations"],
+                               "one_core": {"value": round(cpu_one["mdofs"], 6), "seconds": round(cpu_one["seconds"], 2),
+                                            "cores": 1}}
+    if workloads:
+        out["workloads"] = workloads
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_workload(name, flush, stream):
+    """One warm-up and one timed step (setup + PCG to the workload's rtol, L2
+    flushed before it) on each precision, and ten preconditioner applies."""
+    import torch
+    from paper_2001_07289_gb300 import inputs
+    from paper_2001_07289_gb300.bddc import BDDC
+    idx, desc = WORKLOADS[name]
+    p = inputs.workload(idx)
+    alpha = torch.from_numpy(p.alpha).cuda()
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+    out = {"workload": desc, "n_free": p.n_free}
+    for prec in ("mixed", "fp64"):
+        for k in range(2):
+            flush.fill_(5.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pre = BDDC.from_problem(p, alpha=alpha, precision=prec, use_graph=True, maxit=1000)
+            _, st = pre.solve(b, p.rtol, out=x)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if k == 0:
+                pre.close()
+        info = pre.info()
+        r = torch.from_numpy(inputs.random_node_vector(p.nx, p.ny, p.nz, 5)).cuda()
+        z = torch.empty_like(r)
+        pre.apply(r, out=z)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(10):
+            pre.apply(r, out=z)
+        a1.record(stream)
+        a1.synchronize()
+        apply_ms = a0.elapsed_time(a1) / 10
+        pre.close()
+        out[prec] = {"time_to_solution_ms": round(ms, 2), "mdofs": round(p.n_free / (ms * 1e-3) / 1e6, 4),
+                     "iterations": st["iterations"], "converged": st["converged"],
+                     "setup_ms": round(info["setup_ms"], 2), "solve_ms": round(st["solve_ms"], 2),
+                     "setup_phases_ms": [round(v, 2) for v in info["phase_ms"]], "n_coarse": info["n_coarse"],
+                     "precond_apply_ms": round(apply_ms, 4),
+                     "apply_mdofs": round(p.n_free * 1e3 / apply_ms / 1e6, 2)}
+    return out
 
 
 def run_reference(args, world):

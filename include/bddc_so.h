@@ -129,6 +129,13 @@ typedef struct {
                                  factors (Dirichlet twice), Phi twice, coarse fronts */
     int apply_cluster;        /* CTAs per subdomain in the apply's local solves,
                                  chosen by timing (see bddc_setup)                 */
+    double local_band_flops;  /* flops of banded Cholesky factorisations of the same
+                                 local matrices: sum over subdomains of n_I b_I^2 +
+                                 n_N b_N^2 (n free nodes, b = p_x p_y + p_x + 1 the
+                                 lexicographic half-bandwidth, p free nodes per axis);
+                                 the method-level count the roofline is quoted on   */
+    int factor_kernel;        /* local factorisations ran on: 0 CUDA cores (FP64 or
+                                 large planes), 1 tensor cores (FP32 path)          */
 } bddc_info_t;
 
 /* Host-only analysis of a problem, no GPU needed: the counts that bddc_setup

@@ -58,7 +58,8 @@ class Info(C.Structure):
                 ("max_local_coarse", C.c_int), ("n_free", C.c_longlong), ("bytes", C.c_longlong),
                 ("factor_bytes", C.c_longlong), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 6),
                 ("launches", C.c_longlong), ("coarse_fma", C.c_double), ("local_factor_fma", C.c_double),
-                ("apply_bytes", C.c_longlong), ("apply_cluster", C.c_int)]
+                ("apply_bytes", C.c_longlong), ("apply_cluster", C.c_int), ("local_band_flops", C.c_double),
+                ("factor_kernel", C.c_int)]
 
 
 class Analysis(C.Structure):

@@ -1246,6 +1246,27 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   info->local_factor_fma = fma;
   info->apply_bytes = bytes;
   info->apply_cluster = h->L.apply_cluster;
+  // banded-Cholesky count of the same local matrices: per problem n b^2 with
+  // n the free nodes and b the half-bandwidth of their lexicographic order
+  double band = 0.0;
+  for (const SubDesc& s : h->subs) {
+    for (int neu = 0; neu < 2; ++neu) {
+      double pf[3];
+      bool empty = false;
+      for (int d = 0; d < 3; ++d) {
+        const int lo = s.e0[d] + (neu ? 0 : 1), hi = s.e0[d] + s.w[d] - (neu ? 0 : 1);   // node range
+        const int n_d = (d == 0) ? h->mesh.nx : (d == 1) ? h->mesh.ny : h->mesh.nz;
+        const int flo = std::max(lo, 1), fhi = std::min(hi, n_d - 1);               // off the Dirichlet boundary
+        pf[d] = std::max(0, fhi - flo + 1);
+        if (pf[d] <= 0) empty = true;
+      }
+      if (empty) continue;
+      const double n = pf[0] * pf[1] * pf[2], b = pf[0] * pf[1] + pf[0] + 1;
+      band += n * b * b;
+    }
+  }
+  info->local_band_flops = band;
+  info->factor_kernel = (!h->local_double && h->L.maxQN <= TCS_MAXQ && h->L.maxQD <= TCS_MAXQ) ? 1 : 0;
   return BDDC_OK;
 }
 
