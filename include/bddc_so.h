@@ -136,6 +136,12 @@ typedef struct {
                                  the method-level count the roofline is quoted on   */
     int factor_kernel;        /* local factorisations ran on: 0 CUDA cores (FP64 or
                                  large planes), 1 tensor cores (FP32 path)          */
+    int n_buckets;            /* non-empty size buckets of the apply's local solves */
+    int bucket_subdomains[2]; /* per bucket: its subdomains (bucket 0: those whose
+                                 work vectors need a whole SM, bucket 1: the rest)  */
+    int bucket_ring[2];       /* per bucket: depth of the bulk-copy ring (6: one
+                                 CTA per SM, 4: two), tuned                         */
+    int bucket_ctas[2];       /* per bucket: CTAs per subdomain (1 or 2), tuned      */
 } bddc_info_t;
 
 /* Host-only analysis of a problem, no GPU needed: the counts that bddc_setup
@@ -167,11 +173,15 @@ int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part,
  * over its nodes.  alpha_dev is read during the call only.  On success *out
  * receives a new handle.  Errors: BDDC_ERR_ARG (bad sizes/cuts/L/options,
  * alpha <= 0 or not finite), BDDC_ERR_NOT_SPD, BDDC_ERR_OOM, BDDC_ERR_CUDA. *
- * Autotuning: the first setup of a problem shape (precision, subdomain count,
- * largest planes, largest local coarse space) in the process times one
- * preconditioner apply with one and with two CTAs per subdomain in the local
- * solves and keeps the faster for every later handle of that shape; that
- * first setup takes about eight applies longer. */
+ * Batching: the apply's per-subdomain kernels run in two size buckets (those
+ * whose work vectors leave room for two CTAs per SM with a shallow bulk-copy
+ * ring, and the rest), each one persistent launch per kernel, subdomains
+ * longest first.  Autotuning: the first setup of a problem shape (precision,
+ * subdomain count, largest planes, largest local coarse space, bucket sizes)
+ * in the process times three preconditioner applies per candidate schedule of
+ * each bucket (ring depth 6 or 4, one or two CTAs per subdomain) and keeps the
+ * fastest for every later handle of that shape; that first setup takes up to
+ * about 32 applies longer. */
 int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part,
                const bddc_options* opt, const double* alpha_dev, void* stream,
                bddc_handle** out);
@@ -221,11 +231,17 @@ int bddc_get_info(const bddc_handle* h, bddc_info_t* info);
 
 /* Overrides the autotuned apply schedule of a handle: ctas_per_subdomain = 1
  * or 2 CTAs per subdomain in the local solves of bddc_apply (2: a thread-block
- * cluster whose CTAs share each slot's rows).  Both give the same
- * preconditioner up to the summation order of the partial sums.  Drops the
- * handle's captured PCG graph (recaptured by the next pcg_solve).  The paper
- * has no counterpart; BDDC_ERR_ARG for other values. */
+ * cluster whose CTAs share each slot's rows), in every size bucket.  Both give
+ * the same preconditioner up to the summation order of the partial sums.
+ * Drops the handle's captured PCG graph (recaptured by the next pcg_solve).
+ * The paper has no counterpart; BDDC_ERR_ARG for other values. */
 int bddc_set_apply_schedule(bddc_handle* h, int ctas_per_subdomain);
+
+/* The same for one size bucket (0 or 1, see bddc_info_t), with the depth of
+ * its bulk-copy ring: 6 buffers (one CTA per SM) or 4 (two CTAs per SM, only
+ * for a bucket whose work vectors fit).  The ring depth does not change the
+ * arithmetic: results are bitwise the same.  BDDC_ERR_ARG for other values. */
+int bddc_set_bucket_schedule(bddc_handle* h, int bucket, int ring_depth, int ctas_per_subdomain);
 
 /* Copies the coarse basis of subdomain `sub` restricted to the subdomain's
  * box-surface nodes into phi_host (n_surface x n_c,i, row-major, FP64), the

@@ -59,7 +59,8 @@ class Info(C.Structure):
                 ("factor_bytes", C.c_longlong), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 6),
                 ("launches", C.c_longlong), ("coarse_fma", C.c_double), ("local_factor_fma", C.c_double),
                 ("apply_bytes", C.c_longlong), ("apply_cluster", C.c_int), ("local_band_flops", C.c_double),
-                ("factor_kernel", C.c_int)]
+                ("factor_kernel", C.c_int), ("n_buckets", C.c_int), ("bucket_subdomains", C.c_int * 2),
+                ("bucket_ring", C.c_int * 2), ("bucket_ctas", C.c_int * 2)]
 
 
 class Analysis(C.Structure):
@@ -86,6 +87,7 @@ def _load():
                                     C.c_double, C.POINTER(Stats)]
     lib.bddc_get_info.argtypes = [vp, C.POINTER(Info)]
     lib.bddc_set_apply_schedule.argtypes = [vp, C.c_int]
+    lib.bddc_set_bucket_schedule.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     lib.bddc_analyze.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), C.POINTER(Analysis)]
     lib.bddc_get_coarse_basis.argtypes = [vp, ip, dp, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -96,7 +98,7 @@ def _load():
     lib.bddc_last_error.restype = C.c_char_p
     for f in ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
               "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
-              "bddc_set_apply_schedule", "bddc_debug_inject"):
+              "bddc_set_apply_schedule", "bddc_set_bucket_schedule", "bddc_debug_inject"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -105,7 +107,7 @@ lib = _load()
 
 EXPORTS = ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
            "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
-           "bddc_last_error", "bddc_set_apply_schedule", "bddc_debug_inject")
+           "bddc_last_error", "bddc_set_apply_schedule", "bddc_set_bucket_schedule", "bddc_debug_inject")
 
 
 def _check(code: int, handle=None):
@@ -234,11 +236,17 @@ class BDDC:
         """bddc_set_apply_schedule: 1 or 2 CTAs per subdomain in the apply's local solves."""
         _check(lib.bddc_set_apply_schedule(self._handle, int(ctas_per_subdomain)), self._handle)
 
+    def set_bucket_schedule(self, bucket: int, ring_depth: int, ctas_per_subdomain: int):
+        """bddc_set_bucket_schedule: ring depth (6 or 4) and CTAs per subdomain of one size bucket."""
+        _check(lib.bddc_set_bucket_schedule(self._handle, int(bucket), int(ring_depth), int(ctas_per_subdomain)),
+               self._handle)
+
     def info(self) -> dict:
         i = Info()
         _check(lib.bddc_get_info(self._handle, C.byref(i)), self._handle)
         out = {k: getattr(i, k) for k, _ in Info._fields_}
-        out["phase_ms"] = list(out["phase_ms"])
+        for k in ("phase_ms", "bucket_subdomains", "bucket_ring", "bucket_ctas"):
+            out[k] = list(out[k])
         return out
 
     def coarse_basis(self, sub: int):

@@ -519,6 +519,31 @@ void build_metadata(bddc_handle* h) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// ring depth of the shallow apply configuration and the shared memory one CTA
+// may take so that two fit on an SM (228 KB per SM, 1 KB reserved per CTA)
+constexpr int SMALL_RING = 4;
+constexpr size_t SMALL_SMEM = 113 * 1024;
+
+bool dbl_local(const bddc_handle* h) { return h->local_double != 0; }
+
+BucketSizes sizes_of(const SubDesc& d) {
+  BucketSizes z{};
+  const bool hasI = d.w[0] > 1 && d.w[1] > 1 && d.w[2] > 1;
+  z.maxQD = hasI ? (d.w[0] - 1) * (d.w[1] - 1) : 0;
+  z.maxND = hasI ? z.maxQD * (d.w[2] - 1) : 0;
+  z.maxQN = (d.w[0] + 1) * (d.w[1] + 1);
+  z.maxNN = z.maxQN * (d.w[2] + 1);
+  z.maxNB = d.nB;
+  z.maxNc = d.nc;
+  return z;
+}
+
+void grow(BucketSizes& a, const BucketSizes& b) {
+  a.maxQD = std::max(a.maxQD, b.maxQD); a.maxND = std::max(a.maxND, b.maxND);
+  a.maxQN = std::max(a.maxQN, b.maxQN); a.maxNN = std::max(a.maxNN, b.maxNN);
+  a.maxNB = std::max(a.maxNB, b.maxNB); a.maxNc = std::max(a.maxNc, b.maxNc);
+}
+
 struct Layout {
   long long D, N, W, Y, G, L, PA, Sc, Ac, Phi, B, Vec, TC;
 };
@@ -663,8 +688,29 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     };
     std::stable_sort(lpt.begin(), lpt.end(), [&](const SubDesc& a, const SubDesc& b) { return work(a) > work(b); });
     L.subs_lpt = upload(h, lpt, st);
+    // size buckets of the apply: a subdomain whose work vectors leave room
+    // for two CTAs per SM with a ring of SMALL_RING buffers goes to bucket 1,
+    // the rest to bucket 0; both keep the longest-first order, start with
+    // the deepest ring and one CTA per subdomain, and are tuned below
+    const int es = dbl_local(h) ? 8 : 4;
+    std::vector<SubDesc> bk[MAX_BUCKETS];
+    BucketSizes bz[MAX_BUCKETS] = {};
+    for (const SubDesc& d : lpt) {
+      const BucketSizes one = sizes_of(d);
+      const int b = apply_smem(one, SMALL_RING, es) <= SMALL_SMEM ? 1 : 0;
+      bk[b].push_back(d);
+      grow(bz[b], one);
+    }
+    std::vector<SubDesc> all(bk[0]);
+    all.insert(all.end(), bk[1].begin(), bk[1].end());
+    const SubDesc* dev = upload(h, all, st);
+    L.nbucket = MAX_BUCKETS;
+    for (int b = 0; b < MAX_BUCKETS; ++b) {
+      L.bucket[b] = ApplyBucket{dev + (b ? bk[0].size() : 0), (int)bk[b].size(), NBUF};
+      L.bsize[b] = bz[b];
+      L.bcluster[b] = 1;
+    }
   }
-  L.apply_cluster = 2;
   {
     std::lock_guard<std::mutex> lk(g_debug_mu);
     L.negate_sub = -1;
@@ -811,51 +857,79 @@ void apply(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
   else apply_impl<float>(h, r, z, st);
 }
 
-// Autotuner of the apply schedule: one or two CTAs per subdomain in the
-// local solves.  Two halve each CTA's share of the streamed factor rows but
-// add an exchange per slot; which wins depends on how many subdomains there
-// are per SM and on their size, so the first setup of a shape times three
-// applies of each (after a warm-up, on a zero vector: the work does not
-// depend on the values) and the choice is kept per shape for the process.
+// Autotuner of the apply schedule, bucket by bucket: the depth of the bulk-
+// copy ring (the deepest, or the shallow one that lets two CTAs share an SM
+// when the bucket's work vectors fit) and one or two CTAs per subdomain in
+// the local solves.  Two CTAs halve each CTA's share of the streamed rows but
+// add an exchange per slot; a shallow ring doubles the CTAs in flight but
+// keeps fewer copies ahead of each; which wins depends on how many
+// subdomains there are per SM and on their size, so the first setup of a
+// shape times three applies of each candidate (after a warm-up, on a zero
+// vector: the work does not depend on the values), tuning one bucket at a
+// time with the others fixed, and the choice is kept per shape for the
+// process.
 struct TuneKey {
-  int dbl, nsub, qn, qd, nc;
+  int dbl, nsub, qn, qd, nc, b0, b1;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dbl, nsub, qn, qd, nc) < std::tie(o.dbl, o.nsub, o.qn, o.qd, o.nc);
+    return std::tie(dbl, nsub, qn, qd, nc, b0, b1) < std::tie(o.dbl, o.nsub, o.qn, o.qd, o.nc, o.b0, o.b1);
   }
 };
+struct TuneChoice {
+  int nb[MAX_BUCKETS], cluster[MAX_BUCKETS];
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune;
+std::map<TuneKey, TuneChoice> g_tune;
 
 void tune_apply(bddc_handle* h, cudaStream_t st) {
   LocalLaunch& L = h->L;
-  const TuneKey key{h->local_double, L.nsub, L.maxQN, L.maxQD, L.maxNc};
+  const TuneKey key{h->local_double, L.nsub, L.maxQN, L.maxQD, L.maxNc, L.bucket[0].count, L.bucket[1].count};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) { L.apply_cluster = it->second; return; }
+    if (it != g_tune.end()) {
+      for (int b = 0; b < MAX_BUCKETS; ++b) {
+        L.bucket[b].nb = it->second.nb[b];
+        L.bcluster[b] = it->second.cluster[b];
+      }
+      return;
+    }
   }
   CK(cudaMemsetAsync(h->r, 0, sizeof(double) * h->n_nodes, st));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int pick = 2;
-  for (int c = 1; c <= 2; ++c) {
-    L.apply_cluster = c;
-    apply(h, h->r, h->z, st);
-    CK(cudaEventRecord(e0, st));
-    for (int k = 0; k < 3; ++k) apply(h, h->r, h->z, st);
-    CK(cudaEventRecord(e1, st));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) { best = ms; pick = c; }
+  const int es = h->local_double ? 8 : 4;
+  for (int b = 0; b < MAX_BUCKETS; ++b) {
+    if (L.bucket[b].count == 0) continue;
+    float best = 1e30f;
+    int bnb = NBUF, bcl = 1;
+    for (int nb : {NBUF, SMALL_RING}) {
+      if (nb != NBUF && apply_smem(L.bsize[b], nb, es) > SMALL_SMEM) continue;
+      for (int c = 1; c <= 2; ++c) {
+        L.bucket[b].nb = nb;
+        L.bcluster[b] = c;
+        apply(h, h->r, h->z, st);
+        CK(cudaEventRecord(e0, st));
+        for (int k = 0; k < 3; ++k) apply(h, h->r, h->z, st);
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; bnb = nb; bcl = c; }
+      }
+    }
+    L.bucket[b].nb = bnb;
+    L.bcluster[b] = bcl;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  L.apply_cluster = pick;
+  TuneChoice ch{};
+  for (int b = 0; b < MAX_BUCKETS; ++b) {
+    ch.nb[b] = L.bucket[b].nb;
+    ch.cluster[b] = L.bcluster[b];
+  }
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = pick;
+  g_tune[key] = ch;
 }
 
 }  // namespace
@@ -1197,7 +1271,27 @@ extern "C" int bddc_set_apply_schedule(bddc_handle* h, int ctas_per_subdomain) {
     throw BddcError(BDDC_ERR_ARG, "ctas_per_subdomain must be 1 or 2");
   CK(cudaSetDevice(h->device));
   CK(cudaDeviceSynchronize());
-  h->L.apply_cluster = ctas_per_subdomain;
+  for (int b = 0; b < MAX_BUCKETS; ++b) h->L.bcluster[b] = ctas_per_subdomain;
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+  return BDDC_OK;
+  ABI_END(h)
+}
+
+extern "C" int bddc_set_bucket_schedule(bddc_handle* h, int bucket, int ring_depth, int ctas_per_subdomain) {
+  if (!h) return BDDC_ERR_ARG;
+  ABI_BEGIN
+  if (bucket < 0 || bucket >= MAX_BUCKETS) throw BddcError(BDDC_ERR_ARG, "bucket out of range");
+  if (ctas_per_subdomain != 1 && ctas_per_subdomain != 2)
+    throw BddcError(BDDC_ERR_ARG, "ctas_per_subdomain must be 1 or 2");
+  if (ring_depth != NBUF && ring_depth != SMALL_RING)
+    throw BddcError(BDDC_ERR_ARG, "ring_depth must be " + std::to_string(NBUF) + " or " + std::to_string(SMALL_RING));
+  if (ring_depth == SMALL_RING && apply_smem(h->L.bsize[bucket], SMALL_RING, h->local_double ? 8 : 4) > SMALL_SMEM)
+    throw BddcError(BDDC_ERR_ARG, "this bucket's work vectors do not fit the shallow ring");
+  CK(cudaSetDevice(h->device));
+  CK(cudaDeviceSynchronize());
+  h->L.bucket[bucket].nb = ring_depth;
+  h->L.bcluster[bucket] = ctas_per_subdomain;
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
   return BDDC_OK;
@@ -1245,7 +1339,17 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   }
   info->local_factor_fma = fma;
   info->apply_bytes = bytes;
-  info->apply_cluster = h->L.apply_cluster;
+  {
+    int nb = 0, first = -1;
+    for (int b = 0; b < MAX_BUCKETS; ++b) {
+      info->bucket_subdomains[b] = h->L.bucket[b].count;
+      info->bucket_ring[b] = h->L.bucket[b].count ? h->L.bucket[b].nb : 0;
+      info->bucket_ctas[b] = h->L.bucket[b].count ? h->L.bcluster[b] : 0;
+      if (h->L.bucket[b].count) { ++nb; if (first < 0) first = b; }
+    }
+    info->n_buckets = nb;
+    info->apply_cluster = first >= 0 ? h->L.bcluster[first] : 1;
+  }
   // banded-Cholesky count of the same local matrices: per problem n b^2 with
   // n the free nodes and b the half-bandwidth of their lexicographic order
   double band = 0.0;

@@ -14,6 +14,23 @@ extern long long g_launches;
 
 constexpr int CW = 64;       // RHS columns per CTA in the multi-RHS sweeps
 
+// A size bucket of the apply's per-subdomain kernels: its descriptors in
+// longest-first order (device), their number and the depth of the bulk-copy
+// ring its launches use.  A launch over a bucket is persistent: clusters take
+// the bucket's subdomains in turn.
+struct ApplyBucket {
+  const SubDesc* subs;
+  int count;
+  int nb;
+};
+
+constexpr int MAX_BUCKETS = 2;
+
+// Largest local sizes in a bucket (shared-memory sizing of its launches).
+struct BucketSizes {
+  int maxQD, maxND, maxQN, maxNN, maxNB, maxNc;
+};
+
 // Everything a batched local kernel needs (device pointers; local type erased).
 struct LocalLaunch {
   int nsub;
@@ -26,7 +43,6 @@ struct LocalLaunch {
   void *Y, *G, *Lv, *PA, *Sc, *Phi, *vloc;
   void* PhiT;                      // transposed copy of Phi for the apply's column accumulations
   const SubDesc* subs_lpt;         // the same descriptors, largest subdomains first
-  int apply_cluster;               // CTAs per subdomain in the apply's local solves (1 or 2, tuned)
   void* tc;                        // packed 3xTF32 tiles of the Neumann S_k^{-1} (setup, FP32 path) or null
   double* Ac;
   double* delta;
@@ -36,6 +52,13 @@ struct LocalLaunch {
   int maxQD, maxNzD, maxND;   // Dirichlet: plane size, planes, nodes
   int maxQN, maxNzN, maxNN;   // Neumann
   int maxNB, maxNc;
+  // size buckets of the apply: [0] subdomains whose work vectors leave no room
+  // for two CTAs per SM with a shallow ring, [1] the others (either may be
+  // empty); per bucket the ring depth and CTAs per subdomain (tuned)
+  int nbucket = 0;
+  ApplyBucket bucket[MAX_BUCKETS] = {};
+  BucketSizes bsize[MAX_BUCKETS] = {};
+  int bcluster[MAX_BUCKETS] = {1, 1};
   int negate_sub = -1;        // test hook: subdomain whose local matrix gets a negated pivot (-1: none)
   int negate_neumann = 1;     // ... in its Neumann (1) or Dirichlet (0) matrix
 };
@@ -64,6 +87,9 @@ void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st
 // test hook: tries after which the bounded waits of the local kernels report
 // a timeout (they then still wait, bounded, for the work they cover)
 void set_wait_report_tries(long long tries);
+// shared-memory bytes of the apply's per-subdomain kernels for bucket sizes
+// bs, ring depth nb and local element size es (the largest over the kernels)
+size_t apply_smem(const BucketSizes& bs, int nb, int es);
 void launch_piece_alpha(const MeshDev& m, const double* alpha, const int* plo, const int* phi, int npx, int npy,
                         int npz, double* pw, cudaStream_t st);
 

@@ -21,6 +21,9 @@
 // each diagonal block is kept as its explicit inverse, so every sweep is a
 // sequence of dense products.
 #include <cooperative_groups.h>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 #include "common.cuh"
 #include "dense.cuh"
@@ -1298,41 +1301,47 @@ __device__ void sweep_stream(Ring& ring, const T* __restrict__ fac, int gx, int 
   if (nrank > 1) cluster.sync();   // the peer's last reads of this CTA's buffers are done
 }
 
-__host__ __device__ inline size_t ring_bytes() { return (size_t)NBUF * CHB + 16 * NBUF; }
+// The apply's per-subdomain kernels are persistent over a bucket (see
+// ApplyBucket): cluster c of the launch takes the bucket's subdomains c,
+// c + clusters, ... in their longest-first order, with one ring for all of
+// them (its bookkeeping runs on across subdomains).
 
 // Dirichlet solves of the apply.  mode 0: z_I = A_II^{-1} r_I;
 // mode 1: z_I = A_II^{-1} (r_I - t_I).  Writes the interior nodes of z only.
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
-k_dirichlet_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
-                  const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ z, int mode,
-                  int* err) {
+k_dirichlet_solve(ApplyBucket B, MeshDev m, const T* __restrict__ fac, const double* __restrict__ r,
+                  const double* __restrict__ t, double* __restrict__ z, int mode, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  // one cluster (of one or two CTAs, the launch decides) per subdomain
-  const SubDesc s = subs[blockIdx.x / cg::this_cluster().num_blocks()];
-  const Grid g = grid_of(s, 0);
-  if (g.gz == 0) return;
-  const int Q = g.gx * g.gy, n = Q * g.gz;
-  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
-  T* v = part + APPLY_THREADS;
-  T* tq = v + n;
-  T* pb = tq + Q;
+  // clusters of one or two CTAs (the launch decides), one subdomain at a time
+  const int csz = (int)cg::this_cluster().num_blocks();
+  Ring ring = ring_at(smraw, B.nb);
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes(B.nb));
   ring_init(ring);
-  for (int l = threadIdx.x; l < n; l += blockDim.x) {
-    int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
-    long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
-    double val = r[gi];
-    if (mode) val -= t[gi];
-    v[l] = (T)val;
-  }
-  __syncthreads();
-  sweep_stream<T>(ring, fac + s.offD, g.gx, g.gy, g.gz, v, tq, part, pb, err);
-  if (cg::this_cluster().block_rank() == 0)
-  for (int l = threadIdx.x; l < n; l += blockDim.x) {
-    int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
-    long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
-    z[gi] = (double)v[l];
+  for (int si = (int)blockIdx.x / csz; si < B.count; si += (int)gridDim.x / csz) {
+    const SubDesc s = B.subs[si];
+    const Grid g = grid_of(s, 0);
+    if (g.gz == 0) continue;
+    const int Q = g.gx * g.gy, n = Q * g.gz;
+    T* v = part + APPLY_THREADS;
+    T* tq = v + n;
+    T* pb = tq + Q;
+    __syncthreads();   // the previous subdomain's stores from v are done
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+      int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
+      long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
+      double val = r[gi];
+      if (mode) val -= t[gi];
+      v[l] = (T)val;
+    }
+    __syncthreads();
+    sweep_stream<T>(ring, fac + s.offD, g.gx, g.gy, g.gz, v, tq, part, pb, err);
+    if (cg::this_cluster().block_rank() == 0)
+      for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        int ix = l % g.gx, iy = (l / g.gx) % g.gy, iz = l / Q;
+        long long gi = nodeid(m.NX, m.NY, s.e0[0] + 1 + ix, s.e0[1] + 1 + iy, s.e0[2] + 1 + iz);
+        z[gi] = (double)v[l];
+      }
   }
 }
 
@@ -1359,19 +1368,20 @@ __device__ inline void neumann_restrict(const SubDesc& s, const MeshDev& m, cons
 // cluster and their partial sums added in rank order.
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
-k_neumann_rhs(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ Phi,
-              const double* __restrict__ delta, const double* __restrict__ r, const double* __restrict__ t,
-              double* __restrict__ rcl, int* err) {
+k_neumann_rhs(ApplyBucket B, MeshDev m, const T* __restrict__ Phi, const double* __restrict__ delta,
+              const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ rcl, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
-  const SubDesc s = subs[blockIdx.x / nrank];
-  if (s.nc == 0) return;   // both CTAs of the cluster see the same subdomain
-  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
+  Ring ring = ring_at(smraw, B.nb);
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes(B.nb));
+  ring_init(ring);
+  for (int si = (int)blockIdx.x / nrank; si < B.count; si += (int)gridDim.x / nrank) {
+  const SubDesc s = B.subs[si];
+  if (s.nc == 0) continue;   // both CTAs of the cluster see the same subdomain
   T* rg = part + APPLY_THREADS;
   T* pb = rg + s.nB + 1;   // nc partial sums
-  ring_init(ring);
+  __syncthreads();          // the previous subdomain's reads of rg are done
   neumann_restrict<T>(s, m, delta, r, t, [&](int b, int, bool, T val) { rg[b] = val; });
   __syncthreads();
   const int R = rows_per_chunk(s.nc, (int)sizeof(T));
@@ -1404,28 +1414,30 @@ k_neumann_rhs(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__
       }
     cluster.sync();   // the peer's reads of this CTA's partial sums are done
   }
+  }
 }
 
 // The constrained Neumann solve y = A_rr^{-1} r_i,r (into vloc) of the
 // weighted restriction r_i = D_i R_i (r - t).
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
-k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict__ fac,
-                const double* __restrict__ delta, const double* __restrict__ r, const double* __restrict__ t,
-                T* __restrict__ vloc, int* err) {
+k_neumann_solve(ApplyBucket B, MeshDev m, const T* __restrict__ fac, const double* __restrict__ delta,
+                const double* __restrict__ r, const double* __restrict__ t, T* __restrict__ vloc, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  // one cluster (of one or two CTAs, the launch decides) per subdomain
+  // clusters of one or two CTAs (the launch decides), one subdomain at a time
   cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  const SubDesc s = subs[blockIdx.x / (int)cluster.num_blocks()];
+  const int rank = (int)cluster.block_rank(), csz = (int)cluster.num_blocks();
+  Ring ring = ring_at(smraw, B.nb);
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes(B.nb));
+  ring_init(ring);
+  for (int si = (int)blockIdx.x / csz; si < B.count; si += (int)gridDim.x / csz) {
+  const SubDesc s = B.subs[si];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const int Q = px * py, n = Q * pz;
-  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
   T* v = part + APPLY_THREADS;
   T* tq = v + n;
   T* pb = tq + Q;   // 2 Q partial sums
-  ring_init(ring);
+  __syncthreads();  // the previous subdomain's stores from v are done
   for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = T(0);
   __syncthreads();
   neumann_restrict<T>(s, m, delta, r, t, [&](int, int l, bool free_node, T val) {
@@ -1435,23 +1447,25 @@ k_neumann_solve(const SubDesc* __restrict__ subs, MeshDev m, const T* __restrict
   sweep_stream<T>(ring, fac + s.offN, px, py, pz, v, tq, part, pb, err);
   if (rank == 0)
     for (int l = threadIdx.x; l < n; l += blockDim.x) vloc[s.offVec + l] = v[l];
+  }
 }
 
 // v_i on the box surface: Phi_i (u_c|_i - [0; C_r y]) + y, as a column
 // accumulation over the rows of Phi_i^T.
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
-k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict__ lc,
-                 const T* __restrict__ PhiT, const T* __restrict__ vloc, const double* __restrict__ uc,
-                 double* __restrict__ vgam, int* err) {
+k_neumann_finish(ApplyBucket B, const LocalCoarse* __restrict__ lc, const T* __restrict__ PhiT,
+                 const T* __restrict__ vloc, const double* __restrict__ uc, double* __restrict__ vgam, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  const SubDesc s = subs[blockIdx.x];
-  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
-  Ring ring{smraw, reinterpret_cast<uint64_t*>(smraw + (size_t)NBUF * CHB), 0};
-  T* part = reinterpret_cast<T*>(smraw + ring_bytes());
+  Ring ring = ring_at(smraw, B.nb);
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes(B.nb));
   T* ut = part + APPLY_THREADS;
   ring_init(ring);
+  for (int si = (int)blockIdx.x; si < B.count; si += (int)gridDim.x) {
+  const SubDesc s = B.subs[si];
+  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const T* y = vloc + s.offVec;
+  __syncthreads();   // the previous subdomain's reads of ut are done
   for (int j = threadIdx.x; j < s.nc; j += blockDim.x) {
     const LocalCoarse c = lc[s.cofs + j];
     double val = uc[c.gid];
@@ -1488,6 +1502,7 @@ k_neumann_finish(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict
     ring_run(ring, nch, src, use, err);
   }
   col_finish<T>(L, acc, part, out);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1598,11 +1613,34 @@ void launch_piece_alpha(const MeshDev& m, const double* alpha, const int* plo, c
   k_piece_alpha<<<blocks, 256, 0, st>>>(m, alpha, plo, phi, npx, npy, npz, pw);
 }
 
-// per-subdomain apply kernels: nsub clusters of csize CTAs (one or two)
+// CTAs of `kern` (APPLY_THREADS threads, smem bytes) resident on the current
+// device at once; cached per (device, kernel, smem)
+int resident_ctas(const void* kern, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, size_t>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(dev, kern, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, APPLY_THREADS, smem);
+  const int n = std::max(1, per_sm) * std::max(1, sms);
+  cache[key] = n;
+  return n;
+}
+
+// per-subdomain apply kernels: persistent clusters of csize CTAs (one or
+// two) over one bucket; as many clusters as fit on the GPU at once, at most
+// one per subdomain
 template <typename... KArgs, typename... Args>
-void launch_clustered(void (*kern)(KArgs...), int nsub, int csize, size_t smem, cudaStream_t st, Args... args) {
+void launch_clustered(void (*kern)(KArgs...), const ApplyBucket& b, int csize, size_t smem, cudaStream_t st,
+                      Args... args) {
+  const int clusters = std::max(1, std::min(b.count, resident_ctas((const void*)kern, smem) / csize));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nsub * csize));
+  cfg.gridDim = dim3((unsigned)(clusters * csize));
   cfg.blockDim = dim3(APPLY_THREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
@@ -1616,38 +1654,59 @@ void launch_clustered(void (*kern)(KArgs...), int nsub, int csize, size_t smem, 
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+size_t apply_smem(const BucketSizes& bs, int nb, int es) {
+  const size_t vec = std::max({(size_t)bs.maxNN + 3 * (size_t)bs.maxQN, (size_t)bs.maxND + 3 * (size_t)bs.maxQD,
+                               (size_t)bs.maxNB + 1 + bs.maxNc});
+  return ring_bytes(nb) + (size_t)es * (APPLY_THREADS + vec + 2);
+}
+
 template <typename T>
 void launch_dirichlet(const LocalLaunch& L, const double* r, const double* t, double* z, int mode, cudaStream_t st) {
   if (L.maxQD == 0) return;
-  BDDC_COUNT(1);
-  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxND + 3 * (size_t)L.maxQD + 2);
-  launch_clustered(k_dirichlet_solve<T>, L.nsub, L.apply_cluster, sm, st, L.subs_lpt, L.m, (const T*)L.facD, r, t,
-                   z, mode, L.err);
+  for (int b = 0; b < L.nbucket; ++b) {
+    if (L.bucket[b].count == 0 || L.bsize[b].maxQD == 0) continue;
+    BDDC_COUNT(1);
+    const size_t sm = ring_bytes(L.bucket[b].nb) +
+                      sizeof(T) * ((size_t)APPLY_THREADS + L.bsize[b].maxND + 3 * (size_t)L.bsize[b].maxQD + 2);
+    launch_clustered(k_dirichlet_solve<T>, L.bucket[b], L.bcluster[b], sm, st, L.bucket[b], L.m, (const T*)L.facD, r,
+                     t, z, mode, L.err);
+  }
 }
 
 template <typename T>
 void launch_neumann_rhs(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
   if (L.maxNc == 0) return;
-  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNB + 1 + L.maxNc + 2);
-  BDDC_COUNT(1);
-  launch_clustered(k_neumann_rhs<T>, L.nsub, L.apply_cluster, sm, st, L.subs_lpt, L.m, (const T*)L.Phi, L.delta, r,
-                   t, L.rcl, L.err);
+  for (int b = 0; b < L.nbucket; ++b) {
+    if (L.bucket[b].count == 0) continue;
+    const size_t sm = ring_bytes(L.bucket[b].nb) +
+                      sizeof(T) * ((size_t)APPLY_THREADS + L.bsize[b].maxNB + 1 + L.bsize[b].maxNc + 2);
+    BDDC_COUNT(1);
+    launch_clustered(k_neumann_rhs<T>, L.bucket[b], L.bcluster[b], sm, st, L.bucket[b], L.m, (const T*)L.Phi, L.delta,
+                     r, t, L.rcl, L.err);
+  }
 }
 
 template <typename T>
 void launch_neumann(const LocalLaunch& L, const double* r, const double* t, cudaStream_t st) {
-  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNN + 3 * (size_t)L.maxQN + 2);
-  BDDC_COUNT(1);
-  launch_clustered(k_neumann_solve<T>, L.nsub, L.apply_cluster, sm, st, L.subs_lpt, L.m, (const T*)L.facN, L.delta,
-                   r, t, (T*)L.vloc, L.err);
+  for (int b = 0; b < L.nbucket; ++b) {
+    if (L.bucket[b].count == 0) continue;
+    const size_t sm = ring_bytes(L.bucket[b].nb) +
+                      sizeof(T) * ((size_t)APPLY_THREADS + L.bsize[b].maxNN + 3 * (size_t)L.bsize[b].maxQN + 2);
+    BDDC_COUNT(1);
+    launch_clustered(k_neumann_solve<T>, L.bucket[b], L.bcluster[b], sm, st, L.bucket[b], L.m, (const T*)L.facN,
+                     L.delta, r, t, (T*)L.vloc, L.err);
+  }
 }
 
 template <typename T>
 void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t st) {
-  size_t sm = ring_bytes() + sizeof(T) * ((size_t)APPLY_THREADS + L.maxNc + 1);
-  BDDC_COUNT(1);
-  k_neumann_finish<T><<<L.nsub, APPLY_THREADS, sm, st>>>(L.subs_lpt, L.lc, (const T*)L.PhiT, (const T*)L.vloc, uc,
-                                                        L.vgam, L.err);
+  for (int b = 0; b < L.nbucket; ++b) {
+    if (L.bucket[b].count == 0) continue;
+    const size_t sm = ring_bytes(L.bucket[b].nb) + sizeof(T) * ((size_t)APPLY_THREADS + L.bsize[b].maxNc + 1);
+    BDDC_COUNT(1);
+    launch_clustered(k_neumann_finish<T>, L.bucket[b], 1, sm, st, L.bucket[b], L.lc, (const T*)L.PhiT,
+                     (const T*)L.vloc, uc, L.vgam, L.err);
+  }
 }
 
 template void launch_setup_local<float>(const LocalLaunch&, cudaStream_t, cudaEvent_t*);

@@ -1,13 +1,13 @@
 // Streaming of row-major matrices from HBM into shared memory with 1-D bulk
 // asynchronous copies (cp.async.bulk, the TMA engine) completing on mbarriers.
 //
-// A CTA owns a ring of NBUF buffers of CHB bytes with two mbarriers per
+// A CTA owns a ring of nb buffers (NBUF or fewer) of CHB bytes with two mbarriers per
 // buffer: "full" completes when the buffer's copy has landed, "empty" when
 // every warp has finished reading it.  Every thread waits on "full" itself
 // and each warp arrives on "empty" after its use of the chunk, so warps run
 // ahead of each other up to the ring depth and no block-wide barrier is
 // needed per chunk; one thread (the producer) waits on "empty" before it
-// refills the buffer with chunk c + NBUF.  Chunks must start on 16-byte
+// refills the buffer with chunk c + nb.  Chunks must start on 16-byte
 // boundaries and their byte counts are rounded up to 16; callers pad their
 // allocations accordingly.  Every wait is bounded: a wait that runs past its
 // limit records error code 7 (timeout), waits (bounded again) for the copy
@@ -18,7 +18,7 @@
 
 namespace bddc {
 
-constexpr int NBUF = 6;
+constexpr int NBUF = 6;       // deepest ring (one CTA per SM); shallower rings leave room for two
 constexpr int CHB = 24576;
 constexpr long long WAIT_TRIES = 1LL << 22;
 constexpr int APPLY_THREADS = 512;   // threads of the streaming apply kernels
@@ -75,10 +75,19 @@ __device__ inline bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* er
 }
 
 struct Ring {
-  unsigned char* buf;  // NBUF * CHB bytes, 128-byte aligned
-  uint64_t* bar;       // 2 NBUF mbarriers: full[0..NBUF), then empty[0..NBUF)
+  unsigned char* buf;  // nb * CHB bytes, 128-byte aligned
+  uint64_t* bar;       // 2 nb mbarriers: full[0..nb), then empty[0..nb)
   int base;            // chunks consumed by earlier runs (slot / parity bookkeeping)
+  int nb;              // buffers in the ring (2 .. NBUF)
 };
+
+// Shared-memory bytes of a ring of nb buffers with its barriers.
+__host__ __device__ inline size_t ring_bytes(int nb) { return (size_t)nb * CHB + 16 * (size_t)nb; }
+
+// A ring of nb buffers at the start of a shared-memory block.
+__device__ inline Ring ring_at(unsigned char* smem, int nb) {
+  return Ring{smem, reinterpret_cast<uint64_t*>(smem + (size_t)nb * CHB), 0, nb};
+}
 
 __device__ inline void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -87,9 +96,9 @@ __device__ inline void mbar_arrive(uint64_t* bar) {
 // Initialise the ring's barriers (all threads call; ends with a barrier).
 __device__ inline void ring_init(Ring& r) {
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NBUF; ++s) {
+    for (int s = 0; s < r.nb; ++s) {
       mbar_init(&r.bar[s], 1);
-      mbar_init(&r.bar[NBUF + s], blockDim.x / 32);
+      mbar_init(&r.bar[r.nb + s], blockDim.x / 32);
     }
     fence_barrier_init();
   }
@@ -103,29 +112,29 @@ __device__ inline void ring_init(Ring& r) {
 // every chunk).  Ends with a barrier.
 template <typename Src, typename Use>
 __device__ void ring_run(Ring& r, int nchunks, Src src, Use use, int* err) {
-  const int first = r.base;
+  const int first = r.base, nb = r.nb;
   uint64_t* full = r.bar;
-  uint64_t* empty = r.bar + NBUF;
-  // the producer fills chunk g into slot g % NBUF once the chunk that last
-  // used the slot (g - NBUF) has been read by every warp
+  uint64_t* empty = r.bar + nb;
+  // the producer fills chunk g into slot g % nb once the chunk that last
+  // used the slot (g - nb) has been read by every warp
   auto issue = [&](int c) {
     const void* p;
     unsigned bytes;
     src(c, p, bytes);
-    const int g = first + c, slot = g % NBUF;
-    if (g >= NBUF) mbar_wait_bounded(&empty[slot], (unsigned)(((g / NBUF) - 1) & 1), err);
+    const int g = first + c, slot = g % nb;
+    if (g >= nb) mbar_wait_bounded(&empty[slot], (unsigned)(((g / nb) - 1) & 1), err);
     fence_proxy_async();
     bulk_load(r.buf + (size_t)slot * CHB, p, (bytes + 15u) & ~15u, &full[slot]);
   };
   if (threadIdx.x == 0)
-    for (int c = 0; c < nchunks && c < NBUF; ++c) issue(c);
+    for (int c = 0; c < nchunks && c < nb; ++c) issue(c);
   for (int c = 0; c < nchunks; ++c) {
-    const int g = first + c, slot = g % NBUF;
-    mbar_wait_bounded(&full[slot], (unsigned)((g / NBUF) & 1), err);
+    const int g = first + c, slot = g % nb;
+    mbar_wait_bounded(&full[slot], (unsigned)((g / nb) & 1), err);
     use(c, r.buf + (size_t)slot * CHB);
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[slot]);
-    if (threadIdx.x == 0 && c + NBUF < nchunks) issue(c + NBUF);
+    if (threadIdx.x == 0 && c + nb < nchunks) issue(c + nb);
   }
   r.base = first + nchunks;
   __syncthreads();
