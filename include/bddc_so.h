@@ -134,8 +134,10 @@ typedef struct {
                                  n_N b_N^2 (n free nodes, b = p_x p_y + p_x + 1 the
                                  lexicographic half-bandwidth, p free nodes per axis);
                                  the method-level count the roofline is quoted on   */
-    int factor_kernel;        /* local factorisations ran on: 0 CUDA cores (FP64 or
-                                 large planes), 1 tensor cores (FP32 path)          */
+    int factor_kernel;        /* 1 if the tensor cores factored the subdomains whose
+                                 planes fit them (FP32 path, tuned against the
+                                 CUDA-core sweep), 0 if the CUDA cores did all      */
+    int factor_tc_subdomains; /* subdomains factored on the tensor cores           */
     int n_buckets;            /* non-empty size buckets of the apply's local solves */
     int bucket_subdomains[2]; /* per bucket: its subdomains (bucket 0: those whose
                                  work vectors need a whole SM, bucket 1: the rest)  */
@@ -178,10 +180,11 @@ int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part,
  * ring, and the rest), each one persistent launch per kernel, subdomains
  * longest first.  Autotuning: the first setup of a problem shape (precision,
  * subdomain count, largest planes, largest local coarse space, bucket sizes)
- * in the process times three preconditioner applies per candidate schedule of
+ * in the process times five preconditioner applies per candidate schedule of
  * each bucket (ring depth 6 or 4, one or two CTAs per subdomain) and keeps the
- * fastest for every later handle of that shape; that first setup takes up to
- * about 32 applies longer. */
+ * fastest (the default, ring depth 6 and one CTA, unless another is at least
+ * 3 % faster) for every later handle of that shape; that first setup takes up
+ * to about 48 applies longer. */
 int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part,
                const bddc_options* opt, const double* alpha_dev, void* stream,
                bddc_handle** out);

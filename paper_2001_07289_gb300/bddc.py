@@ -59,7 +59,7 @@ class Info(C.Structure):
                 ("factor_bytes", C.c_longlong), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 6),
                 ("launches", C.c_longlong), ("coarse_fma", C.c_double), ("local_factor_fma", C.c_double),
                 ("apply_bytes", C.c_longlong), ("apply_cluster", C.c_int), ("local_band_flops", C.c_double),
-                ("factor_kernel", C.c_int), ("n_buckets", C.c_int), ("bucket_subdomains", C.c_int * 2),
+                ("factor_kernel", C.c_int), ("factor_tc_subdomains", C.c_int), ("n_buckets", C.c_int), ("bucket_subdomains", C.c_int * 2),
                 ("bucket_ring", C.c_int * 2), ("bucket_ctas", C.c_int * 2)]
 
 

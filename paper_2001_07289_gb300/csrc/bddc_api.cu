@@ -574,6 +574,50 @@ Layout layout_of(const bddc_handle* h) {
   return o;
 }
 
+// Autotuner of the local factorisations: for the planes that fit it, the
+// tensor-core kernel or the CUDA-core register sweep.  The first setup of a
+// shape (subdomains, largest planes, bucket size) in the process assembles
+// and factors the local matrices once with each and keeps the faster (the
+// tensor cores unless the sweep is at least 3 % faster) for every later
+// setup of that shape; the setup itself then assembles and factors again.
+struct FactorKey {
+  int nsub, qn, qd, n0;
+  bool operator<(const FactorKey& o) const {
+    return std::tie(nsub, qn, qd, n0) < std::tie(o.nsub, o.qn, o.qd, o.n0);
+  }
+};
+std::mutex g_ftune_mu;
+std::map<FactorKey, int> g_ftune;
+
+void tune_factor(bddc_handle* h, cudaStream_t st) {
+  LocalLaunch& L = h->L;
+  L.factor_tc = 1;
+  if (h->local_double || L.fbucket[0].count == 0) return;
+  const FactorKey key{L.nsub, L.fbucket[0].maxQN, L.fbucket[0].maxQD, L.fbucket[0].count};
+  {
+    std::lock_guard<std::mutex> lk(g_ftune_mu);
+    auto it = g_ftune.find(key);
+    if (it != g_ftune.end()) { L.factor_tc = it->second; return; }
+  }
+  configure_local_kernels<float>();
+  cudaEvent_t e[4];
+  for (auto& x : e) CK(cudaEventCreate(&x));
+  for (int v = 0; v < 2; ++v) {
+    launch_assemble<float>(L, st);
+    CK(cudaEventRecord(e[2 * v], st));
+    launch_factor<float>(L, 1 - v, st);
+    CK(cudaEventRecord(e[2 * v + 1], st));
+  }
+  CK(cudaEventSynchronize(e[3]));
+  float t_tc = 0.f, t_cc = 0.f;
+  CK(cudaEventElapsedTime(&t_tc, e[0], e[1]));
+  CK(cudaEventElapsedTime(&t_cc, e[2], e[3]));
+  for (auto& x : e) cudaEventDestroy(x);
+  L.factor_tc = t_cc < 0.97f * t_tc ? 0 : 1;
+  std::lock_guard<std::mutex> lk(g_ftune_mu);
+  g_ftune[key] = L.factor_tc;
+}
+
 void check_err_flags(bddc_handle* h, cudaStream_t st) {
   int e[2] = {0, -1};
   CK(cudaMemcpyAsync(e, h->err, sizeof(e), cudaMemcpyDeviceToHost, st));
@@ -704,6 +748,25 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     std::vector<SubDesc> all(bk[0]);
     all.insert(all.end(), bk[1].begin(), bk[1].end());
     const SubDesc* dev = upload(h, all, st);
+    // factorisation buckets: planes that fit the tensor-core kernel (FP32
+    // path) first, the rest second, both longest first
+    std::vector<SubDesc> fb[2];
+    FactorBucket fz[2] = {};
+    for (const SubDesc& d : lpt) {
+      const BucketSizes one = sizes_of(d);
+      const int b = (!dbl_local(h) && one.maxQN <= TCS_MAXQ && one.maxQD <= TCS_MAXQ) ? 0 : 1;
+      fb[b].push_back(d);
+      fz[b].maxQN = std::max(fz[b].maxQN, one.maxQN);
+      fz[b].maxQD = std::max(fz[b].maxQD, one.maxQD);
+    }
+    std::vector<SubDesc> fall(fb[0]);
+    fall.insert(fall.end(), fb[1].begin(), fb[1].end());
+    const SubDesc* fdev = upload(h, fall, st);
+    for (int b = 0; b < 2; ++b) {
+      fz[b].subs = fdev + (b ? fb[0].size() : 0);
+      fz[b].count = (int)fb[b].size();
+      L.fbucket[b] = fz[b];
+    }
     L.nbucket = MAX_BUCKETS;
     for (int b = 0; b < MAX_BUCKETS; ++b) {
       L.bucket[b] = ApplyBucket{dev + (b ? bk[0].size() : 0), (int)bk[b].size(), NBUF};
@@ -762,6 +825,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     launch_piece_alpha(m, h->alpha, dplo, dphi, npc[0], npc[1], npc[2], pw, st);
   }
   launch_weights(L, pw, st);
+  tune_factor(h, st);
   CK(cudaEventRecord(ev[1], st));
   // local factorisations and coarse basis
   if (dbl) setup_local<double>(h, st, ev + 2); else setup_local<float>(h, st, ev + 2);
@@ -864,10 +928,11 @@ void apply(bddc_handle* h, const double* r, double* z, cudaStream_t st) {
 // add an exchange per slot; a shallow ring doubles the CTAs in flight but
 // keeps fewer copies ahead of each; which wins depends on how many
 // subdomains there are per SM and on their size, so the first setup of a
-// shape times three applies of each candidate (after a warm-up, on a zero
+// shape times five applies of each candidate (after a warm-up, on a zero
 // vector: the work does not depend on the values), tuning one bucket at a
-// time with the others fixed, and the choice is kept per shape for the
-// process.
+// time with the others fixed; a candidate replaces the default (deepest ring,
+// one CTA per subdomain) only if it is at least 3 % faster, and the choice is
+// kept per shape for the process.
 struct TuneKey {
   int dbl, nsub, qn, qd, nc, b0, b1;
   bool operator<(const TuneKey& o) const {
@@ -910,12 +975,14 @@ void tune_apply(bddc_handle* h, cudaStream_t st) {
         L.bcluster[b] = c;
         apply(h, h->r, h->z, st);
         CK(cudaEventRecord(e0, st));
-        for (int k = 0; k < 3; ++k) apply(h, h->r, h->z, st);
+        for (int k = 0; k < 5; ++k) apply(h, h->r, h->z, st);
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; bnb = nb; bcl = c; }
+        // the first candidate (deepest ring, one CTA per subdomain) stays
+        // unless another is clearly faster: closer than 3 % is timing noise
+        if (ms < 0.97f * best || best == 1e30f) { best = ms; bnb = nb; bcl = c; }
       }
     }
     L.bucket[b].nb = bnb;
@@ -1370,7 +1437,8 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
     }
   }
   info->local_band_flops = band;
-  info->factor_kernel = (!h->local_double && h->L.maxQN <= TCS_MAXQ && h->L.maxQD <= TCS_MAXQ) ? 1 : 0;
+  info->factor_kernel = (!h->local_double && h->L.fbucket[0].count > 0 && h->L.factor_tc) ? 1 : 0;
+  info->factor_tc_subdomains = info->factor_kernel ? h->L.fbucket[0].count : 0;
   return BDDC_OK;
 }
 

@@ -26,6 +26,15 @@ struct ApplyBucket {
 
 constexpr int MAX_BUCKETS = 2;
 
+// A bucket of the local factorisations: bucket 0 holds the subdomains whose
+// planes fit the tensor-core kernel (FP32 path), bucket 1 the rest; longest
+// first.
+struct FactorBucket {
+  const SubDesc* subs;
+  int count;
+  int maxQN, maxQD;
+};
+
 // Largest local sizes in a bucket (shared-memory sizing of its launches).
 struct BucketSizes {
   int maxQD, maxND, maxQN, maxNN, maxNB, maxNc;
@@ -59,6 +68,8 @@ struct LocalLaunch {
   ApplyBucket bucket[MAX_BUCKETS] = {};
   BucketSizes bsize[MAX_BUCKETS] = {};
   int bcluster[MAX_BUCKETS] = {1, 1};
+  FactorBucket fbucket[2] = {};
+  int factor_tc = 1;          // bucket 0 on the tensor cores (1) or the CUDA cores (0), tuned
   int negate_sub = -1;        // test hook: subdomain whose local matrix gets a negated pivot (-1: none)
   int negate_neumann = 1;     // ... in its Neumann (1) or Dirichlet (0) matrix
 };
@@ -68,7 +79,11 @@ struct LocalLaunch {
 constexpr int TCS_MAXQ = 176;
 size_t schur_tc_smem(int maxQ);
 void configure_schur_tc();
-void launch_schur_tc(const LocalLaunch& L, cudaStream_t st);
+void launch_schur_tc(const LocalLaunch& L, const FactorBucket& B, cudaStream_t st);
+// assembly of the local plane blocks; the factorisations of every bucket
+// (tc: bucket 0 on the tensor cores)
+template <typename T> void launch_assemble(const LocalLaunch& L, cudaStream_t st);
+template <typename T> void launch_factor(const LocalLaunch& L, int tc, cudaStream_t st);
 
 // ev (may be null): 3 events recorded after the Dirichlet factorisation, the
 // Neumann factorisation and the coarse basis.

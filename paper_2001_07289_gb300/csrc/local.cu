@@ -1526,10 +1526,9 @@ void set_wait_report_tries(long long tries) {
 }
 
 template <typename T>
-void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) {
+void launch_assemble(const LocalLaunch& L, cudaStream_t st) {
   const int S = L.nsub;
-  T* facD = (T*)L.facD; T* facN = (T*)L.facN; T* W = (T*)L.scratch;
-  size_t sm = dense_smem<T>();
+  T* facD = (T*)L.facD; T* facN = (T*)L.facN;
   // local assembly (Dirichlet and Neumann plane blocks)
   if (L.maxQD > 0) {
     k_assemble<T><<<dim3(S, L.maxNzD, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facD, 0);
@@ -1541,18 +1540,39 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
     k_debug_negate<T><<<1, 1, 0, st>>>(L.subs, L.negate_neumann ? facN : facD, L.negate_sub, L.negate_neumann);
     BDDC_COUNT(1);
   }
-  if (ev) cudaEventRecord(ev[0], st);
-  // both factorisations in one launch: y = 0 Neumann, y = 1 Dirichlet; the
-  // packed Schur matrix takes the shared memory left after the pivot columns
-  if (std::is_same<T, float>::value && L.maxQN <= TCS_MAXQ && L.maxQD <= TCS_MAXQ) {
-    launch_schur_tc(L, st);   // rank-16 updates on the tensor cores, matrix in TMEM
-  } else {
-    const int maxQ = std::max(L.maxQN, L.maxQD);
+}
+
+// Both factorisations of every subdomain, per factorisation bucket: bucket
+// 0 (FP32, planes of at most TCS_MAXQ nodes) on the tensor cores when tc is
+// set, else like bucket 1 with the CUDA-core sweep (y = 0 Neumann, y = 1
+// Dirichlet in one launch; the packed Schur matrix takes the shared memory
+// left after the pivot columns).
+template <typename T>
+void launch_factor(const LocalLaunch& L, int tc, cudaStream_t st) {
+  T* facD = (T*)L.facD; T* facN = (T*)L.facN; T* W = (T*)L.scratch;
+  for (int b = 0; b < 2; ++b) {
+    const FactorBucket& B = L.fbucket[b];
+    if (B.count == 0) continue;
+    if (b == 0 && tc && std::is_same<T, float>::value) {
+      launch_schur_tc(L, B, st);   // rank-16 updates on the tensor cores, matrix in TMEM
+      continue;
+    }
+    const int maxQ = std::max(B.maxQN, B.maxQD);
     const size_t smb = 227 * 1024;
     const long long cap = (long long)(smb / sizeof(T)) - 2LL * maxQ - 2;
-    k_btschur<T><<<dim3(S, L.maxQD > 0 ? 2 : 1), SCHUR_THREADS, smb, st>>>(L.subs_lpt, facN, facD, W, cap, L.err);
+    k_btschur<T><<<dim3(B.count, B.maxQD > 0 ? 2 : 1), SCHUR_THREADS, smb, st>>>(B.subs, facN, facD, W, cap, L.err);
     BDDC_COUNT(1);
   }
+}
+
+template <typename T>
+void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) {
+  const int S = L.nsub;
+  T* facN = (T*)L.facN; T* W = (T*)L.scratch;
+  size_t sm = dense_smem<T>();
+  launch_assemble<T>(L, st);
+  if (ev) cudaEventRecord(ev[0], st);
+  launch_factor<T>(L, L.factor_tc, st);
   if (ev) cudaEventRecord(ev[1], st);
   // coarse basis
   T* Y = (T*)L.Y; T* G = (T*)L.G; T* Lv = (T*)L.Lv; T* PA = (T*)L.PA; T* Sc = (T*)L.Sc; T* Phi = (T*)L.Phi;
@@ -1710,6 +1730,8 @@ void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t 
 }
 
 template void launch_setup_local<float>(const LocalLaunch&, cudaStream_t, cudaEvent_t*);
+template void launch_assemble<float>(const LocalLaunch&, cudaStream_t);
+template void launch_factor<float>(const LocalLaunch&, int, cudaStream_t);
 template void launch_setup_local<double>(const LocalLaunch&, cudaStream_t, cudaEvent_t*);
 template void configure_local_kernels<float>();
 template void configure_local_kernels<double>();

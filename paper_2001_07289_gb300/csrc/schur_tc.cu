@@ -550,11 +550,10 @@ void configure_schur_tc() {
   cudaFuncSetAttribute(k_btschur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_tc_smem(TCS_MAXQ));
 }
 
-void launch_schur_tc(const LocalLaunch& L, cudaStream_t st) {
-  const int maxQ = std::max(L.maxQN, L.maxQD);
+void launch_schur_tc(const LocalLaunch& L, const FactorBucket& B, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_btschur_tc<<<dim3(L.nsub, L.maxQD > 0 ? 2 : 1), TCS_THREADS, schur_tc_smem(maxQ), st>>>(
-      L.subs_lpt, (float*)L.facN, (float*)L.facD, L.err);
+  k_btschur_tc<<<dim3(B.count, B.maxQD > 0 ? 2 : 1), TCS_THREADS, schur_tc_smem(std::max(B.maxQN, B.maxQD)), st>>>(
+      B.subs, (float*)L.facN, (float*)L.facD, L.err);
 }
 
 }  // namespace bddc
