@@ -50,11 +50,15 @@ enum { BDDC_FP64 = 0, BDDC_MIXED = 1 };      /* precision of the local solves   
 enum { BDDC_W_CARD = 0, BDDC_W_RHO = 1 };    /* eq. (W) / Remark 1 weighting     */
 /* Constraint selection (Table 1, Section 5): which objects of Theta-hat on
  * Gamma carry coarse DOFs.  VEF: vertices, edges and faces; VE: vertices and
- * edges; VF: vertices and faces; V: vertices only.  Vertices are eliminated
- * as primal DOFs, which keeps every local constrained Neumann matrix SPD, so
- * selections without vertices (faces only, edges and faces) are rejected with
- * BDDC_ERR_UNSUPPORTED. */
-enum { BDDC_SEL_VEF = 0, BDDC_SEL_VE = 1, BDDC_SEL_VF = 2, BDDC_SEL_V = 3 };
+ * edges; VF: vertices and faces; V: vertices only; F: faces only (the
+ * BDDC-SO(f) of Section 5.2); EF: edges and faces.  Vertices, when selected,
+ * are eliminated as primal DOFs; without them the local Neumann matrix of a
+ * floating subdomain (no face on the Dirichlet boundary) is singular, so one
+ * of its nodes is pinned and the exact constrained solves are recovered by a
+ * rank-one (Sherman-Morrison) correction.  The remark after Theorem 1 names
+ * all edge or all face subobjects as sufficient for acceptable paths and all
+ * vertex constraints as scalable but weaker, which the iteration counts show. */
+enum { BDDC_SEL_VEF = 0, BDDC_SEL_VE = 1, BDDC_SEL_VF = 2, BDDC_SEL_V = 3, BDDC_SEL_F = 4, BDDC_SEL_EF = 5 };
 
 typedef struct bddc_handle bddc_handle;
 
@@ -79,7 +83,7 @@ typedef struct {
     int precision;  /* BDDC_FP64 or BDDC_MIXED (FP32 local factors/solves, FP64 rest) */
     int weights;    /* BDDC_W_CARD or BDDC_W_RHO                                      */
     int L_elems;    /* >= 1                                                           */
-    int selection;  /* BDDC_SEL_VEF, BDDC_SEL_VE, BDDC_SEL_VF or BDDC_SEL_V           */
+    int selection;  /* BDDC_SEL_VEF, _VE, _VF, _V, _F or _EF                       */
     int use_graph;  /* 1: pcg_solve runs its whole loop as one CUDA graph (below)      */
     int maxit;      /* PCG iteration limit (<= 0: 2000)                               */
     int beta_rule;  /* BDDC_BETA_STANDARD (0) or BDDC_BETA_FLEXIBLE (below)          */
@@ -138,6 +142,8 @@ typedef struct {
                                  planes fit them (FP32 path, tuned against the
                                  CUDA-core sweep), 0 if the CUDA cores did all      */
     int factor_tc_subdomains; /* subdomains factored on the tensor cores           */
+    int pinned_subdomains;    /* floating subdomains pinned (selections without
+                                 vertices), with the rank-one correction           */
     int n_buckets;            /* non-empty size buckets of the apply's local solves */
     int bucket_subdomains[2]; /* per bucket: its subdomains (bucket 0: those whose
                                  work vectors need a whole SM, bucket 1: the rest)  */

@@ -21,9 +21,10 @@ BDDC_OK, BDDC_ERR_ARG, BDDC_ERR_NOT_SPD, BDDC_ERR_NOCONV = 0, -1, -2, -3
 BDDC_ERR_BREAKDOWN, BDDC_ERR_CUDA, BDDC_ERR_OOM, BDDC_ERR_TIMEOUT, BDDC_ERR_UNSUPPORTED = -4, -5, -6, -7, -8
 BDDC_FP64, BDDC_MIXED = 0, 1
 BDDC_W_CARD, BDDC_W_RHO = 0, 1
-BDDC_SEL_VEF, BDDC_SEL_VE, BDDC_SEL_VF, BDDC_SEL_V = 0, 1, 2, 3
+BDDC_SEL_VEF, BDDC_SEL_VE, BDDC_SEL_VF, BDDC_SEL_V, BDDC_SEL_F, BDDC_SEL_EF = 0, 1, 2, 3, 4, 5
 BDDC_DEBUG_CLEAR, BDDC_DEBUG_NEGATE_NEUMANN_PIVOT, BDDC_DEBUG_NEGATE_DIRICHLET_PIVOT, BDDC_DEBUG_WAIT_TRIES = 0, 1, 2, 3
-SELECTIONS = {"vef": BDDC_SEL_VEF, "ve": BDDC_SEL_VE, "vf": BDDC_SEL_VF, "v": BDDC_SEL_V}
+SELECTIONS = {"vef": BDDC_SEL_VEF, "ve": BDDC_SEL_VE, "vf": BDDC_SEL_VF, "v": BDDC_SEL_V, "f": BDDC_SEL_F,
+              "ef": BDDC_SEL_EF}
 BDDC_BETA_STANDARD, BDDC_BETA_FLEXIBLE = 0, 1
 BETA_RULES = {"standard": BDDC_BETA_STANDARD, "flexible": BDDC_BETA_FLEXIBLE}
 
@@ -59,7 +60,8 @@ class Info(C.Structure):
                 ("factor_bytes", C.c_longlong), ("setup_ms", C.c_double), ("phase_ms", C.c_double * 6),
                 ("launches", C.c_longlong), ("coarse_fma", C.c_double), ("local_factor_fma", C.c_double),
                 ("apply_bytes", C.c_longlong), ("apply_cluster", C.c_int), ("local_band_flops", C.c_double),
-                ("factor_kernel", C.c_int), ("factor_tc_subdomains", C.c_int), ("n_buckets", C.c_int), ("bucket_subdomains", C.c_int * 2),
+                ("factor_kernel", C.c_int), ("factor_tc_subdomains", C.c_int), ("pinned_subdomains", C.c_int),
+                ("n_buckets", C.c_int), ("bucket_subdomains", C.c_int * 2),
                 ("bucket_ring", C.c_int * 2), ("bucket_ctas", C.c_int * 2)]
 
 

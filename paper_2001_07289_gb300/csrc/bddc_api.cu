@@ -191,6 +191,7 @@ struct bddc_handle {
   std::vector<SubDesc> subs;
   std::vector<LocalCoarse> lc;
   int n_coarse = 0, n_vertices = 0, max_nc = 0;
+  int vert_primal = 1, n_pinned = 0;   // vertices eliminated; floating subdomains pinned without them
   long long n_nodes = 0, n_free = 0;
   LocalLaunch L{};
   MeshDev m{};
@@ -366,8 +367,10 @@ void build_metadata(bddc_handle* h) {
   std::vector<int> objid(nt, -1);
   // object type by its number of point items: 3 vertex, 2 edge, 1 face
   const int sel = h->opt.selection;
-  const bool keep_edges = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VE;
-  const bool keep_faces = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VF;
+  const bool keep_verts = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VE || sel == BDDC_SEL_VF || sel == BDDC_SEL_V;
+  const bool keep_edges = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VE || sel == BDDC_SEL_EF;
+  const bool keep_faces = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VF || sel == BDDC_SEL_F || sel == BDDC_SEL_EF;
+  h->vert_primal = keep_verts;
   auto valid = [&](int ix, int iy, int iz) {
     int it[3] = {ix, iy, iz};
     bool on_gamma = false;
@@ -377,7 +380,7 @@ void build_metadata(bddc_handle* h) {
       if (k == 2) on_gamma = true;
     }
     const int pts = !(ix & 1) + !(iy & 1) + !(iz & 1);
-    if ((pts == 2 && !keep_edges) || (pts == 1 && !keep_faces)) return false;
+    if ((pts == 3 && !keep_verts) || (pts == 2 && !keep_edges) || (pts == 1 && !keep_faces)) return false;
     return on_gamma;
   };
   int nc = 0, nvert = 0;
@@ -390,6 +393,7 @@ void build_metadata(bddc_handle* h) {
         }
   h->n_coarse = nc;
   h->n_vertices = nvert;
+  h->n_pinned = 0;
   for (int d = 0; d < 3; ++d) {
     h->geom.nitem[d] = nit[d];
     h->geom.nsub[d] = nsub[d];
@@ -428,6 +432,17 @@ void build_metadata(bddc_handle* h) {
           ihi[d] = h->ax[d].item[s.e0[d] + s.w[d]];
         }
         s.color = (sx & 1) + 2 * (sy & 1) + 4 * (sz & 1);
+        {
+          // floating: no face of the box on the Dirichlet boundary; without
+          // vertex primal DOFs its local Neumann matrix has the constants as
+          // kernel and gets pinned at local node 0
+          const int nd[3] = {h->mesh.nx, h->mesh.ny, h->mesh.nz};
+          bool floating = true;
+          for (int d = 0; d < 3; ++d)
+            if (s.e0[d] == 0 || s.e0[d] + s.w[d] == nd[d]) floating = false;
+          s.pin = (!keep_verts && floating) ? 1 : 0;
+          h->n_pinned += s.pin;
+        }
         const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
         // local coarse DOFs: vertices first, then averages, each lexicographic
         verts.clear();
@@ -657,7 +672,10 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     const size_t ring = (size_t)NBUF * CHB + 16 * NBUF;
     const size_t vec = std::max({(size_t)L.maxNN + 3 * (size_t)L.maxQN, (size_t)L.maxND + 3 * (size_t)L.maxQD,
                                  (size_t)L.maxNB + 1 + L.maxNc});
-    const size_t smem = ring + (size_t)es * (APPLY_THREADS + vec + 2);
+    size_t smem = ring + (size_t)es * (APPLY_THREADS + vec + 2);
+    if (h->n_pinned)   // the pinned solve also keeps C y (FP64) beside the Neumann vectors
+      smem = std::max(smem, ring + ((size_t)es * (APPLY_THREADS + L.maxNN + 3 * (size_t)L.maxQN) + 15) / 16 * 16 +
+                                sizeof(double) * (L.maxNc + 32));
     bool rows_ok = true;
     for (const SubDesc& s : h->subs) {
       const int QN = (s.w[0] + 1) * (s.w[1] + 1);
@@ -696,6 +714,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   // axis tables
   MeshDev& m = h->m;
   m.nx = M.nx; m.ny = M.ny; m.nz = M.nz;
+  m.vert_primal = h->vert_primal;
   m.NX = M.nx + 1; m.NY = M.ny + 1; m.NZ = M.nz + 1;
   m.h = M.h;
   for (int d = 0; d < 3; ++d) {
@@ -796,6 +815,13 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   L.vgam = h->dnew<double>(lay.B);
   L.vloc = h->dalloc(es * lay.Vec);
   L.rcl = h->dnew<double>(h->lc.size());
+  L.npin = h->n_pinned;
+  if (L.npin) {
+    L.zw = h->dnew<double>(lay.B);
+    L.zl = h->dnew<double>(std::max<size_t>(h->lc.size(), 1));
+    L.cpin = h->dnew<double>(h->subs.size());
+    L.pdot = h->dnew<double>(h->subs.size());
+  }
   L.err = h->err;
   L.scratch = h->dalloc(es * lay.W, true);
   L.Y = h->dalloc(es * lay.Y, true);
@@ -1174,10 +1200,8 @@ std::unique_ptr<bddc_handle> make_handle(const bddc_mesh* mesh, const bddc_parti
   if (opt->weights != BDDC_W_CARD && opt->weights != BDDC_W_RHO) throw BddcError(BDDC_ERR_ARG, "bad weights");
   if (opt->beta_rule != BDDC_BETA_STANDARD && opt->beta_rule != BDDC_BETA_FLEXIBLE)
     throw BddcError(BDDC_ERR_ARG, "bad beta_rule");
-  if (opt->selection < BDDC_SEL_VEF || opt->selection > BDDC_SEL_V)
-    throw BddcError(BDDC_ERR_UNSUPPORTED,
-                    "selection must keep the vertices (vef, ve, vf or v): vertices are the primal DOFs that keep "
-                    "the local constrained Neumann matrices SPD");
+  if (opt->selection < BDDC_SEL_VEF || opt->selection > BDDC_SEL_EF)
+    throw BddcError(BDDC_ERR_ARG, "bad selection");
   std::unique_ptr<bddc_handle> h(new bddc_handle());
   h->mesh = *mesh;
   if (!(h->mesh.h > 0)) h->mesh.h = 1.0 / mesh->nx;
@@ -1439,6 +1463,7 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   info->local_band_flops = band;
   info->factor_kernel = (!h->local_double && h->L.fbucket[0].count > 0 && h->L.factor_tc) ? 1 : 0;
   info->factor_tc_subdomains = info->factor_kernel ? h->L.fbucket[0].count : 0;
+  info->pinned_subdomains = h->n_pinned;
   return BDDC_OK;
 }
 
@@ -1458,6 +1483,15 @@ extern "C" int bddc_get_coarse_basis(const bddc_handle* h, int sub, double* phi_
       std::vector<float> tmp(cnt);
       CK(cudaMemcpy(tmp.data(), (float*)h->L.Phi + s.offPhi, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
       for (size_t i = 0; i < cnt; ++i) phi_host[i] = tmp[i];
+    }
+    if (s.pin) {   // Phi = Phi~ + c zeta_w zeta_l^T (the pinned subdomain's exact basis)
+      std::vector<double> zw(s.nB), zl(s.nc);
+      double c = 0.0;
+      CK(cudaMemcpy(zw.data(), h->L.zw + s.offB, sizeof(double) * s.nB, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(zl.data(), h->L.zl + s.cofs, sizeof(double) * s.nc, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(&c, h->L.cpin + s.id, sizeof(double), cudaMemcpyDeviceToHost));
+      for (int b = 0; b < s.nB; ++b)
+        for (int j = 0; j < s.nc; ++j) phi_host[(size_t)b * s.nc + j] += c * zw[b] * zl[j];
     }
   }
   if (gid_host)
@@ -1571,6 +1605,7 @@ void apply_noalloc_impl(bddc_handle* h, unsigned char* base, const double* r, do
   L.rcl = (double*)(base + carve(off, sizeof(double) * std::max<size_t>(h->lc.size(), 1)));
   L.vgam = (double*)(base + carve(off, sizeof(double) * std::max<long long>(h->n_surface_total, 1)));
   L.vloc = base + carve(off, sizeof(T) * std::max<long long>(h->n_local_nodes_total, 1));
+  if (L.npin) L.pdot = (double*)(base + carve(off, sizeof(double) * h->subs.size()));
   // the array keeps the previous call's contents; the interior solve writes
   // only interior nodes, so the rest of uI must start at zero
   CK(cudaMemsetAsync(uI, 0, sizeof(double) * N, st));
@@ -1587,6 +1622,7 @@ size_t noalloc_bytes_needed(const bddc_handle* h) {
   carve(off, sizeof(double) * std::max<size_t>(h->lc.size(), 1));
   carve(off, sizeof(double) * std::max<long long>(h->n_surface_total, 1));
   carve(off, es * std::max<long long>(h->n_local_nodes_total, 1));
+  if (h->L.npin) carve(off, sizeof(double) * h->subs.size());
   return off;
 }
 

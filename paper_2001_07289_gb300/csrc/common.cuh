@@ -29,6 +29,8 @@ struct SubDesc {
   int cofs;           // first entry of this subdomain in the local-coarse table
                       // (also the offset of its nc-vector of local coarse values)
   int color;          // (sx&1) + 2(sy&1) + 4(sz&1): same colour => no shared objects
+  int pin;            // 1: floating subdomain of a selection without vertices, whose
+                      // local Neumann matrix is made SPD by pinning local node 0
   long long offD;     // Dirichlet factor slots (local type)
   long long offN;     // Neumann factor slots (local type)
   long long offW;     // factorisation scratch: 2*QN^2 + 1024*ceil(QN/32) (local type)
@@ -76,6 +78,7 @@ struct AxisTables {
 struct MeshDev {
   int nx, ny, nz;
   int NX, NY, NZ;      // nodes per axis
+  int vert_primal;     // 1: the selection has vertices, eliminated as primal DOFs
   double h;
   AxisTables ax[3];
   int nsub[3];

@@ -69,6 +69,11 @@ struct LocalLaunch {
   BucketSizes bsize[MAX_BUCKETS] = {};
   int bcluster[MAX_BUCKETS] = {1, 1};
   FactorBucket fbucket[2] = {};
+  // pinned floating subdomains (selections without vertices): their count,
+  // zeta_w on the box surfaces (offB), zeta_l (cofs), the Sherman-Morrison
+  // factor c per subdomain, and a per-subdomain apply scalar zeta_w . r_i
+  int npin = 0;
+  double *zw = nullptr, *zl = nullptr, *cpin = nullptr, *pdot = nullptr;
   int factor_tc = 1;          // bucket 0 on the tensor cores (1) or the CUDA cores (0), tuned
   int negate_sub = -1;        // test hook: subdomain whose local matrix gets a negated pivot (-1: none)
   int negate_neumann = 1;     // ... in its Neumann (1) or Dirichlet (0) matrix

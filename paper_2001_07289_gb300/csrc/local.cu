@@ -65,12 +65,13 @@ __device__ inline double box_entry(const MeshDev& m, const double* __restrict__ 
 }
 
 // Local Neumann node fixed to zero in A_rr: on the Dirichlet boundary or a
-// primal point value (box-surface node at Theta-hat points on all three axes).
+// primal point value (box-surface node at Theta-hat points on all three axes,
+// when the selection has vertices).
 __device__ inline bool neumann_fixed(const MeshDev& m, const SubDesc& s, int ix, int iy, int iz) {
   int gx = s.e0[0] + ix, gy = s.e0[1] + iy, gz = s.e0[2] + iz;
   if (on_dirichlet(m, gx, gy, gz)) return true;
   bool surf = ix == 0 || iy == 0 || iz == 0 || ix == s.w[0] || iy == s.w[1] || iz == s.w[2];
-  return surf && m.ax[0].hat[gx] && m.ax[1].hat[gy] && m.ax[2].hat[gz];
+  return m.vert_primal && surf && m.ax[0].hat[gx] && m.ax[1].hat[gy] && m.ax[2].hat[gz];
 }
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -90,6 +91,12 @@ __device__ inline T warp_sum(T v) {
 // (dense Q x Q) and the coupling B_k = A_{k,k-1} to slot gz+k-1 as its nine
 // stencil diagonals: Bd[o][i] = B_k[i][i + dx + dy gx], o = 3 (dy+1) + dx+1
 // (zero where the neighbour is off the plane).
+// Weight d of the rank-one pin of a floating subdomain (see k_pin_zeta): the
+// diagonal entry of local node 0 spread over the Q nodes of local plane 0.
+__device__ inline double pin_weight(const MeshDev& m, const double* alpha, const SubDesc& s, int Q) {
+  return box_entry(m, alpha, s, s.e0[0], s.e0[1], s.e0[2], 0, 0, 0) / Q;
+}
+
 template <typename T>
 __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha,
                            T* __restrict__ fac, int neumann) {
@@ -125,6 +132,8 @@ __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const do
       else v = box_entry(m, alpha, s, s.e0[0] + g.off + ax, s.e0[1] + g.off + ay, s.e0[2] + g.off + k,
                          dx, dy, dz);
     }
+    // pinned floating subdomain: A + d w w^T with w the indicator of local plane 0
+    if (neumann && s.pin && k == 0 && e < QQ) v += pin_weight(m, alpha, s, Q);
     if (e < QQ) base[(long long)k * SS + e] = (T)v;
     else base[(long long)(g.gz + k - 1) * SS + (e - QQ)] = (T)v;
   }
@@ -960,7 +969,8 @@ template <typename T>
 __global__ void k_local_coarse_matrix(const SubDesc* __restrict__ subs, MeshDev m,
                                       const double* __restrict__ alpha, const LocalCoarse* __restrict__ lc,
                                       const T* __restrict__ Y, const T* __restrict__ Lv,
-                                      const T* __restrict__ Sc, double* __restrict__ Ac) {
+                                      const T* __restrict__ Sc, const double* __restrict__ zl,
+                                      const double* __restrict__ cpin, double* __restrict__ Ac) {
   const SubDesc s = subs[blockIdx.x];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const int nc = s.nc, nv = s.nv;
@@ -995,6 +1005,7 @@ __global__ void k_local_coarse_matrix(const SubDesc* __restrict__ subs, MeshDev 
     } else if (r >= nv && c >= nv) {
       int a = r - nv, b = c - nv;
       v = 0.5 * ((double)Sc[s.offSc + (long long)a * s.na + b] + (double)Sc[s.offSc + (long long)b * s.na + a]);
+      if (s.pin) v -= cpin[s.id] * zl[s.cofs + r] * zl[s.cofs + c];   // exact problem of a pinned subdomain
     } else if (r >= nv) {
       v = -(double)Lv[s.offL + (long long)(r - nv) * nv + c];
     } else {
@@ -1366,10 +1377,44 @@ __device__ inline void neumann_restrict(const SubDesc& s, const MeshDev& m, cons
 // restriction r_i = D_i R_i (r - t), in the local precision: columns of Phi
 // accumulate over streamed rows, the rows split between the CTAs of the
 // cluster and their partial sums added in rank order.
+// Block sum in FP64, fixed order (every thread calls; ends with a barrier).
+__device__ inline double block_sum_f64(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// Pinned subdomain (see k_pin_zeta): s_i = zeta_w . r_i into pdot, and
+// rc_i += c zeta_l s_i.  Every thread of the CTA calls, after rc_i is written
+// and a barrier; red (32 doubles of shared memory) is free scratch.
+struct PinData {
+  const double *zw, *zl, *cpin;
+  double* pdot;
+};
+
+template <typename T>
+__device__ inline void pin_rhs_impl(const SubDesc& s, const T* rg, const PinData& P, double* rcl, double* red) {
+  double a = 0.0;
+  for (int b = threadIdx.x; b < s.nB; b += blockDim.x) a += P.zw[s.offB + b] * (double)rg[b];
+  const double si = block_sum_f64(a, red);
+  if (threadIdx.x == 0) P.pdot[s.id] = si;
+  const double cf = P.cpin[s.id] * si;
+  for (int j = threadIdx.x; j < s.nc; j += blockDim.x) rcl[s.cofs + j] += cf * P.zl[s.cofs + j];
+  __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_neumann_rhs(ApplyBucket B, MeshDev m, const T* __restrict__ Phi, const double* __restrict__ delta,
-              const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ rcl, int* err) {
+              const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ rcl, PinData P0,
+              int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
@@ -1403,6 +1448,10 @@ k_neumann_rhs(ApplyBucket B, MeshDev m, const T* __restrict__ Phi, const double*
   ring_run(ring, nch, src, use, err);
   if (nrank == 1) {
     col_finish<T>(L, acc, part, [&](int cc, T sum) { rcl[s.cofs + cc] = (double)sum; });
+    if (s.pin) {
+      __syncthreads();   // col_finish's reads of part are done
+      pin_rhs_impl<T>(s, rg, P0, rcl, reinterpret_cast<double*>(part));
+    }
   } else {
     col_finish<T>(L, acc, part, [&](int cc, T sum) { pb[cc] = sum; });
     cluster.sync();
@@ -1412,6 +1461,10 @@ k_neumann_rhs(ApplyBucket B, MeshDev m, const T* __restrict__ Phi, const double*
         for (int q = 0; q < nrank; ++q) sum += cluster.map_shared_rank(pb, q)[c];
         rcl[s.cofs + c] = (double)sum;
       }
+    if (s.pin) {
+      __syncthreads();
+      if (rank == 0) pin_rhs_impl<T>(s, rg, P0, rcl, reinterpret_cast<double*>(part));
+    }
     cluster.sync();   // the peer's reads of this CTA's partial sums are done
   }
   }
@@ -1455,7 +1508,8 @@ k_neumann_solve(ApplyBucket B, MeshDev m, const T* __restrict__ fac, const doubl
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_neumann_finish(ApplyBucket B, const LocalCoarse* __restrict__ lc, const T* __restrict__ PhiT,
-                 const T* __restrict__ vloc, const double* __restrict__ uc, double* __restrict__ vgam, int* err) {
+                 const T* __restrict__ vloc, const double* __restrict__ uc, double* __restrict__ vgam, PinData P0,
+                 int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   Ring ring = ring_at(smraw, B.nb);
   T* part = reinterpret_cast<T*>(smraw + ring_bytes(B.nb));
@@ -1479,10 +1533,20 @@ k_neumann_finish(ApplyBucket B, const LocalCoarse* __restrict__ lc, const T* __r
     ut[j] = (T)val;
   }
   __syncthreads();
+  // pinned subdomain: v_i += c zeta_w (zeta_l . u_c,i + zeta_w . r_i)
+  double pin_cf = 0.0;
+  if (s.pin) {
+    double a = 0.0;
+    for (int j = threadIdx.x; j < s.nc; j += blockDim.x) a += P0.zl[s.cofs + j] * uc[lc[s.cofs + j].gid];
+    // part is free until col_finish (the loop-top barrier ended its last use)
+    pin_cf = P0.cpin[s.id] * (block_sum_f64(a, reinterpret_cast<double*>(part)) + P0.pdot[s.id]);
+  }
   auto out = [&](int b, T sum) {
     int ix, iy, iz;
     surf_coords(b, px, py, pz, ix, iy, iz);
-    vgam[s.offB + b] = (double)sum + (double)y[ix + px * (iy + py * iz)];
+    double vb = (double)sum + (double)y[ix + px * (iy + py * iz)];
+    if (s.pin) vb += pin_cf * P0.zw[s.offB + b];
+    vgam[s.offB + b] = vb;
   };
   const ColLayout L = col_layout(s.nB);
   T acc[4] = {T(0), T(0), T(0), T(0)};
@@ -1502,6 +1566,73 @@ k_neumann_finish(ApplyBucket B, const LocalCoarse* __restrict__ lc, const T* __r
     ring_run(ring, nch, src, use, err);
   }
   col_finish<T>(L, acc, part, out);
+  }
+}
+
+// Pinned subdomains (selections without vertices: the local Neumann matrix A
+// of a floating subdomain has the constants as kernel).  The factor holds
+// A~ = A + d w w^T, w the indicator of local plane 0 and d = A_00 / Q: spread
+// over a plane, the pin keeps cond(A~) near that of a Dirichlet problem
+// (pinning one node leaves the constants' Rayleigh quotient at A_00 / n and
+// costs FP32 three digits).  The exact constrained problem K = [A C^T; C 0]
+// = K~ - d u u^T (u = [w; 0]) follows from the pinned one by Sherman-Morrison:
+// K^{-1} = K~^{-1} + c zeta zeta^T with zeta = K~^{-1} u and c = d / (1 -
+// d u^T zeta).  Here zeta from the pinned factor: y = A~^{-1} w, zeta_l =
+// S_c^{-1} C y, zeta_w = y - Phi~ C y (Phi~ = X S_c^{-1}, every local coarse
+// DOF an average); zeta_w is kept on the box surface, which holds plane 0.
+// Then Phi = Phi~ + c zeta_w zeta_l^T, A_c^(i) = S_c^{-1} - c zeta_l
+// zeta_l^T, and the apply adds c zeta_l (zeta_w . r_i) to Phi^T r_i and
+// c zeta_w (zeta_l . u_c,i + zeta_w . r_i) to v_i.  One CTA per subdomain.
+template <typename T>
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_pin_zeta(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha, const T* __restrict__ fac,
+           const T* __restrict__ Phi, const T* __restrict__ Sc, const LocalCoarse* __restrict__ lc,
+           double* __restrict__ zw, double* __restrict__ zl, double* __restrict__ cpin, int* err) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const SubDesc s = subs[blockIdx.x];
+  if (!s.pin) return;
+  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
+  const int Q = px * py, n = Q * pz, nc = s.nc;
+  Ring ring = ring_at(smraw, NBUF);
+  T* part = reinterpret_cast<T*>(smraw + ring_bytes(NBUF));
+  T* v = part + APPLY_THREADS;
+  T* tq = v + n;
+  T* pb = tq + Q;
+  double* cy = reinterpret_cast<double*>(smraw + ring_bytes(NBUF) +
+                                         (((size_t)(APPLY_THREADS + n + 3 * Q) * sizeof(T) + 15) & ~(size_t)15));
+  ring_init(ring);
+  double* red = cy + nc;   // 32 doubles of reduction scratch
+  for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = (l < Q) ? T(1) : T(0);
+  __syncthreads();
+  sweep_stream<T>(ring, fac + s.offN, px, py, pz, v, tq, part, pb, err);   // v = A~^{-1} w
+  // C y: means over the averaging objects
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+    const LocalCoarse c = lc[s.cofs + j];
+    double sum = 0.0;
+    for (int iz = c.lo[2]; iz <= c.hi[2]; ++iz)
+      for (int iy = c.lo[1]; iy <= c.hi[1]; ++iy)
+        for (int ix = c.lo[0]; ix <= c.hi[0]; ++ix) sum += (double)v[ix + px * (iy + py * iz)];
+    cy[j] = sum / c.count;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+    double a = 0.0;
+    for (int q = 0; q < nc; ++q) a += (double)Sc[s.offSc + (long long)j * nc + q] * cy[q];
+    zl[s.cofs + j] = a;
+  }
+  double wz = 0.0;   // w . zeta_w: the surface nodes of plane 0
+  for (int b = threadIdx.x; b < s.nB; b += blockDim.x) {
+    int ix, iy, iz;
+    surf_coords(b, px, py, pz, ix, iy, iz);
+    double a = (double)v[ix + px * (iy + py * iz)];
+    for (int q = 0; q < nc; ++q) a -= (double)Phi[s.offPhi + (long long)b * nc + q] * cy[q];
+    zw[s.offB + b] = a;
+    if (iz == 0) wz += a;
+  }
+  wz = block_sum_f64(wz, red);
+  if (threadIdx.x == 0) {
+    const double d = pin_weight(m, alpha, s, Q);
+    cpin[s.id] = d / (1.0 - d * wz);
   }
 }
 
@@ -1598,7 +1729,14 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
     k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 1);
     k_phi_surface<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, PA, Phi);
     k_transpose<T><<<dim3(S, 1, 64), 256, 0, st>>>(L.subs, Phi, (T*)L.PhiT);
-    k_local_coarse_matrix<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y, Lv, Sc, L.Ac);
+    if (L.npin) {
+      const size_t smz = ring_bytes(NBUF) + (((size_t)APPLY_THREADS + L.maxNN + 3 * (size_t)L.maxQN) * sizeof(T) + 15) /
+                                                16 * 16 + sizeof(double) * (L.maxNc + 32);
+      k_pin_zeta<T><<<S, APPLY_THREADS, smz, st>>>(L.subs, L.m, L.alpha, facN, Phi, Sc, L.lc, L.zw, L.zl, L.cpin, L.err);
+      BDDC_COUNT(1);
+    }
+    k_local_coarse_matrix<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y, Lv, Sc, L.zl,
+                                                                     L.cpin, L.Ac);
     BDDC_COUNT(9);
   }
   if (ev) cudaEventRecord(ev[2], st);
@@ -1618,6 +1756,7 @@ void configure_local_kernels() {
   cudaFuncSetAttribute(k_neumann_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_neumann_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_neumann_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(k_pin_zeta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st) {
@@ -1702,7 +1841,7 @@ void launch_neumann_rhs(const LocalLaunch& L, const double* r, const double* t, 
                       sizeof(T) * ((size_t)APPLY_THREADS + L.bsize[b].maxNB + 1 + L.bsize[b].maxNc + 2);
     BDDC_COUNT(1);
     launch_clustered(k_neumann_rhs<T>, L.bucket[b], L.bcluster[b], sm, st, L.bucket[b], L.m, (const T*)L.Phi, L.delta,
-                     r, t, L.rcl, L.err);
+                     r, t, L.rcl, PinData{L.zw, L.zl, L.cpin, L.pdot}, L.err);
   }
 }
 
@@ -1725,7 +1864,7 @@ void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t 
     const size_t sm = ring_bytes(L.bucket[b].nb) + sizeof(T) * ((size_t)APPLY_THREADS + L.bsize[b].maxNc + 1);
     BDDC_COUNT(1);
     launch_clustered(k_neumann_finish<T>, L.bucket[b], 1, sm, st, L.bucket[b], L.lc, (const T*)L.PhiT,
-                     (const T*)L.vloc, uc, L.vgam, L.err);
+                     (const T*)L.vloc, uc, L.vgam, PinData{L.zw, L.zl, L.cpin, L.pdot}, L.err);
   }
 }
 

@@ -85,26 +85,25 @@ def test_jittered_workload_plan(gb):
     (20, 20, 20, [[3, 8, 12, 17], [5, 10, 15], [7]], 2),
     (36, 36, 36, [[12, 24]] * 3, 4),
 ])
-@pytest.mark.parametrize("sel", ["ve", "vf", "v"])
+@pytest.mark.parametrize("sel", ["ve", "vf", "v", "f", "ef"])
 def test_selection_variants_match_oracle(gb, case, sel):
-    """Selections that keep the vertices (Section 5's ve, vf, v variants):
-    the library's coarse objects are exactly the oracle's selected objects,
-    and the type counts are the vef counts with the dropped types removed."""
+    """Section 5's selection variants: the library's coarse objects are
+    exactly the oracle's selected objects, and the type counts are the vef
+    counts with the dropped types removed."""
     nx, ny, nz, cuts, L = case
     sub, piece = partition.box_labels(nx, ny, nz, cuts, L)
     o = objects.classify(nx, ny, nz, sub, piece)
     a = gb.analyze(nx, ny, nz, cuts, L, selection=sel)
     full = gb.analyze(nx, ny, nz, cuts, L)
     assert a["n_coarse"] == len(objects.select(o, sel))
-    keep = {"ve": ("n_vertices", "n_edges"), "vf": ("n_vertices", "n_faces"), "v": ("n_vertices",)}[sel]
+    keep = {"ve": ("n_vertices", "n_edges"), "vf": ("n_vertices", "n_faces"), "v": ("n_vertices",),
+            "f": ("n_faces",), "ef": ("n_edges", "n_faces")}[sel]
     for key in ("n_vertices", "n_edges", "n_faces"):
         assert a[key] == (full[key] if key in keep else 0)
     assert a["n_coarse"] == sum(full[k] for k in keep)
 
 
-def test_selections_without_vertices_rejected(gb):
-    """Face-only (and edge-and-face) selections would leave floating local
-    Neumann matrices singular under vertex elimination: refused."""
+def test_unknown_selection_rejected(gb):
     with pytest.raises(gb.BddcError) as e:
-        gb.analyze(16, 16, 16, [[8]] * 3, 4, selection=4)
-    assert e.value.code == -8
+        gb.analyze(16, 16, 16, [[8]] * 3, 4, selection=6)
+    assert e.value.code == gb.BDDC_ERR_ARG
