@@ -172,6 +172,35 @@ typedef struct {
 int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part,
                  const bddc_options* opt, bddc_analysis_t* out);
 
+/* Acceptable-path check (remark after Theorem 1: the bound rests on the
+ * auxiliary BDDC-A having, for every pair of neighbouring sub-subdomains, an
+ * acceptable path; all edge or all face subobjects on Gamma guarantee one).
+ * Host only; alpha_host (nx*ny*nz elements, x fastest, may be NULL for
+ * alpha = 1) gives each sub-subdomain rho = the mean of alpha over it.
+ * A pair is two sub-subdomains of different subdomains whose closures share
+ * a node off the Dirichlet boundary.  It is direct when it shares a selected
+ * edge or face object, or when every free node the two share is primal.
+ * Otherwise it needs a path of sub-subdomains in which consecutive ones share
+ * a face and either lie in one subdomain (continuity) or share a selected
+ * face object or only primal free nodes; the path's quality is min(1, min of
+ * rho over the path / min(rho_i, rho_j)) and the pair takes its best path's.
+ * Errors: BDDC_ERR_ARG as bddc_analyze; BDDC_ERR_UNSUPPORTED above 2^22
+ * sub-subdomains. */
+typedef struct {
+    long long n_pieces;        /* sub-subdomains                               */
+    long long n_pairs;         /* neighbouring pairs across Gamma              */
+    long long n_direct;        /* of which share a selected edge or face       */
+    long long n_without_path;  /* of which have no acceptable path             */
+    double min_ratio;          /* smallest best-path quality of the others (1 if none) */
+    long long worst_pair[2];   /* a pair without a path, else one of min_ratio
+                                  (-1 -1 when every pair is direct);
+                                  sub-subdomain ids a + na (b + nb c) of the
+                                  per-axis piece indices                    */
+} bddc_paths_t;
+
+int bddc_acceptable_paths(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt,
+                          const double* alpha_host, bddc_paths_t* out);
+
 /* Builds the BDDC-SO preconditioner (Section 3; Definition 1 with V1 = U_I,
  * Q1 = I, V2 = W-tilde, Q2 = (I - P)E): sub-partition and (sub)object
  * classification, weights of eq. (W) or Remark 1, local Dirichlet and

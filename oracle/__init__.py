@@ -15,6 +15,8 @@ The oracle is written from the paper's definitions, slow and direct:
   objects.py    classification of interface DOFs into (sub)objects by the set
                 of sub-subdomains containing them, selection vef / ve / f
                 (Section 3; Table 1 variants).
+  paths.py      the acceptable-path check of a selection (remark after
+                Theorem 1).
   weights.py    the weighting E of eq. (W) and the rho-weighting of Remark 1.
   bddc.py       the multispace BDDC preconditioner of Definition 1 with
                 V1 = U_I, Q1 = I, V2 = W-tilde, Q2 = (I - P)E (Section 3, last

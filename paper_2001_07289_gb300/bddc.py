@@ -72,6 +72,11 @@ class Analysis(C.Structure):
                 ("coarse_fma", C.c_double)]
 
 
+class Paths(C.Structure):
+    _fields_ = [("n_pieces", C.c_longlong), ("n_pairs", C.c_longlong), ("n_direct", C.c_longlong),
+                ("n_without_path", C.c_longlong), ("min_ratio", C.c_double), ("worst_pair", C.c_longlong * 2)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"BDDC-SO CUDA library not built: {LIB_PATH} is missing "
@@ -91,6 +96,8 @@ def _load():
     lib.bddc_set_apply_schedule.argtypes = [vp, C.c_int]
     lib.bddc_set_bucket_schedule.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     lib.bddc_analyze.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), C.POINTER(Analysis)]
+    lib.bddc_acceptable_paths.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), C.POINTER(Options), dp,
+                                          C.POINTER(Paths)]
     lib.bddc_get_coarse_basis.argtypes = [vp, ip, dp, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.bddc_get_coarse_matrix.argtypes = [vp, dp]
@@ -98,7 +105,7 @@ def _load():
     lib.bddc_debug_inject.argtypes = [C.c_int, C.c_longlong]
     lib.bddc_last_error.argtypes = [vp]
     lib.bddc_last_error.restype = C.c_char_p
-    for f in ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
+    for f in ("bddc_setup", "bddc_analyze", "bddc_acceptable_paths", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
               "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
               "bddc_set_apply_schedule", "bddc_set_bucket_schedule", "bddc_debug_inject"):
         getattr(lib, f).restype = C.c_int
@@ -107,7 +114,7 @@ def _load():
 
 lib = _load()
 
-EXPORTS = ("bddc_setup", "bddc_analyze", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
+EXPORTS = ("bddc_setup", "bddc_analyze", "bddc_acceptable_paths", "bddc_apply", "bddc_apply_noalloc", "bddc_operator", "pcg_solve", "bddc_gradient", "bddc_solve_host",
            "bddc_get_info", "bddc_get_coarse_basis", "bddc_get_coarse_matrix", "bddc_destroy",
            "bddc_last_error", "bddc_set_apply_schedule", "bddc_set_bucket_schedule", "bddc_debug_inject")
 
@@ -165,6 +172,25 @@ def analyze(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int, h:
     out = Analysis()
     _check(lib.bddc_analyze(C.byref(mesh), C.byref(part), C.byref(opt), C.byref(out)), None)
     return {k: getattr(out, k) for k, _ in Analysis._fields_}
+
+
+def acceptable_paths(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int, alpha=None,
+                     selection="vef") -> dict:
+    """bddc_acceptable_paths: host-only acceptable-path check of a selection;
+    alpha (nx*ny*nz element coefficients, x fastest) or None for alpha = 1."""
+    mesh, part, opt, keep = _structs(nx, ny, nz, 1.0 / nx, cuts, L, "fp64", "card", 2000, False, selection)
+    a = None
+    if alpha is not None:
+        a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(-1))
+        if a.size != nx * ny * nz:
+            raise ValueError(f"alpha has {a.size} entries, the mesh {nx * ny * nz} elements")
+    out = Paths()
+    _check(lib.bddc_acceptable_paths(C.byref(mesh), C.byref(part), C.byref(opt),
+                                     None if a is None else a.ctypes.data_as(C.POINTER(C.c_double)),
+                                     C.byref(out)), None)
+    d = {k: getattr(out, k) for k, _ in Paths._fields_}
+    d["worst_pair"] = list(d["worst_pair"])
+    return d
 
 
 class BDDC:

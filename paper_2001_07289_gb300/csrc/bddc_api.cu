@@ -1269,6 +1269,199 @@ extern "C" int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, c
   ABI_END(hnull)
 }
 
+// Acceptable paths (remark after Theorem 1).  Sub-subdomains are the tensor
+// pieces (a, b, c); two pieces touch when their indices differ by at most one
+// on every axis, and the items of the contact on an axis are the piece's
+// {lo point, interval, hi point} where the indices agree and the one point
+// between them where they differ.  A pair (pieces of different subdomains
+// whose contact holds a free node) is direct when the contact holds a
+// selected edge or face object or all its free nodes are primal.  Links:
+// pieces of one subdomain sharing a face (w is continuous inside a
+// subdomain), or pieces of two subdomains sharing a face that holds a
+// selected face object or only primal free nodes.  A path's bottleneck is the smallest rho on
+// it (ends included), so the best path of every pair is its path in a
+// maximum spanning forest of the links weighted by min(rho_u, rho_v)
+// (Kruskal), queried by binary lifting.
+extern "C" int bddc_acceptable_paths(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt,
+                                     const double* alpha_host, bddc_paths_t* out) {
+  bddc_handle* hnull = nullptr;
+  ABI_BEGIN
+  if (!out) throw BddcError(BDDC_ERR_ARG, "out is NULL");
+  std::unique_ptr<bddc_handle> h = make_handle(mesh, part, opt);
+  build_metadata(h.get());
+  const AxisHost* ax = h->ax;
+  int np[3];
+  for (int d = 0; d < 3; ++d) np[d] = (int)ax[d].piece_lo.size();
+  const long long P = (long long)np[0] * np[1] * np[2];
+  if (P > (1LL << 22)) throw BddcError(BDDC_ERR_UNSUPPORTED, "more than 2^22 sub-subdomains");
+  const int* nit = h->geom.nitem;
+  const std::vector<int>& objid = h->geom.objid;
+  auto pid = [&](int a, int b, int c) { return (long long)a + (long long)np[0] * (b + (long long)np[1] * c); };
+  // piece coefficient: the mean of alpha over the piece's elements (1 without alpha)
+  std::vector<double> rho(P, 1.0);
+  if (alpha_host) {
+    const bddc_mesh& M = h->mesh;
+    std::fill(rho.begin(), rho.end(), 0.0);
+    for (int k = 0; k < M.nz; ++k)
+      for (int j = 0; j < M.ny; ++j)
+        for (int i = 0; i < M.nx; ++i)
+          rho[pid(ax[0].piece[i], ax[1].piece[j], ax[2].piece[k])] +=
+              alpha_host[i + (long long)M.nx * (j + (long long)M.ny * k)];
+    for (int c = 0; c < np[2]; ++c)
+      for (int b = 0; b < np[1]; ++b)
+        for (int a = 0; a < np[0]; ++a)
+          rho[pid(a, b, c)] /= (double)(ax[0].piece_hi[a] - ax[0].piece_lo[a]) *
+                               (ax[1].piece_hi[b] - ax[1].piece_lo[b]) * (ax[2].piece_hi[c] - ax[2].piece_lo[c]);
+  }
+  // contact items of piece q and offset o on one axis
+  auto contact = [](int q, int o, int* it) -> int {
+    if (o == 0) { it[0] = 2 * q; it[1] = 2 * q + 1; it[2] = 2 * q + 2; return 3; }
+    it[0] = o > 0 ? 2 * q + 2 : 2 * q;
+    return 1;
+  };
+  auto slab = [&](int d, int q) { return ax[d].slab[ax[d].piece_lo[q]]; };
+  std::vector<std::pair<long long, long long>> pairs, links;
+  std::vector<char> direct;
+  for (int c = 0; c < np[2]; ++c)
+    for (int b = 0; b < np[1]; ++b)
+      for (int a = 0; a < np[0]; ++a)
+        for (int oz = -1; oz <= 1; ++oz)
+          for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+              const int q[3] = {a, b, c}, o[3] = {ox, oy, oz};
+              const int r[3] = {a + ox, b + oy, c + oz};
+              bool ok = true;
+              for (int d = 0; d < 3; ++d) ok = ok && r[d] >= 0 && r[d] < np[d];
+              if (!ok || pid(r[0], r[1], r[2]) <= pid(a, b, c)) continue;
+              bool same = true;
+              int nmove = 0;
+              for (int d = 0; d < 3; ++d) {
+                same = same && slab(d, q[d]) == slab(d, r[d]);
+                nmove += o[d] != 0;
+              }
+              if (same) {
+                if (nmove == 1) links.push_back({pid(a, b, c), pid(r[0], r[1], r[2])});
+                continue;
+              }
+              int it[3][3], n[3];
+              bool free_node = true;
+              for (int d = 0; d < 3; ++d) {
+                n[d] = contact(q[d], o[d], it[d]);
+                bool any = false;
+                for (int e = 0; e < n[d]; ++e) any = any || (!ax[d].empty(it[d][e]) && ax[d].item_kind[it[d][e]] != 3);
+                free_node = free_node && any;
+              }
+              if (!free_node) continue;
+              // every item tuple of the contact holding nodes off the Dirichlet
+              // boundary is an object on Gamma (one moving axis crosses a cut)
+              bool dir = false, face_link = false, all_primal = true;
+              for (int ez = 0; ez < n[2]; ++ez)
+                for (int ey = 0; ey < n[1]; ++ey)
+                  for (int ex = 0; ex < n[0]; ++ex) {
+                    const int ix = it[0][ex], iy = it[1][ey], iz = it[2][ez];
+                    if (ax[0].empty(ix) || ax[1].empty(iy) || ax[2].empty(iz) || ax[0].item_kind[ix] == 3 ||
+                        ax[1].item_kind[iy] == 3 || ax[2].item_kind[iz] == 3)
+                      continue;
+                    if (objid[ix + (long long)nit[0] * (iy + (long long)nit[1] * iz)] < 0) {
+                      all_primal = false;
+                      continue;
+                    }
+                    const int pts = !(ix & 1) + !(iy & 1) + !(iz & 1);
+                    if (pts <= 2) dir = true;
+                    if (pts == 1) face_link = true;
+                  }
+              pairs.push_back({pid(a, b, c), pid(r[0], r[1], r[2])});
+              direct.push_back(dir || all_primal);
+              if ((face_link || all_primal) && nmove == 1) links.push_back({pid(a, b, c), pid(r[0], r[1], r[2])});
+            }
+  // maximum spanning forest (Kruskal), edge weight min(rho_u, rho_v)
+  std::sort(links.begin(), links.end(), [&](const std::pair<long long, long long>& x,
+                                            const std::pair<long long, long long>& y) {
+    const double wx = std::min(rho[x.first], rho[x.second]), wy = std::min(rho[y.first], rho[y.second]);
+    return wx != wy ? wx > wy : x < y;
+  });
+  std::vector<long long> uf(P);
+  for (long long i = 0; i < P; ++i) uf[i] = i;
+  auto find = [&](long long x) {
+    while (uf[x] != x) { uf[x] = uf[uf[x]]; x = uf[x]; }
+    return x;
+  };
+  std::vector<std::vector<std::pair<long long, double>>> adj(P);
+  for (const auto& e : links) {
+    const long long u = find(e.first), v = find(e.second);
+    if (u == v) continue;
+    uf[u] = v;
+    const double w = std::min(rho[e.first], rho[e.second]);
+    adj[e.first].push_back({e.second, w});
+    adj[e.second].push_back({e.first, w});
+  }
+  // root every tree; binary lifting tables of ancestors and path minima
+  int LOG = 1;
+  while ((1LL << LOG) < P) ++LOG;
+  std::vector<long long> depth(P, -1), comp(P, -1);
+  std::vector<std::vector<long long>> up(LOG, std::vector<long long>(P));
+  std::vector<std::vector<double>> mn(LOG, std::vector<double>(P, INFINITY));
+  for (long long root = 0; root < P; ++root) {
+    if (depth[root] >= 0) continue;
+    std::vector<long long> stack{root};
+    depth[root] = 0;
+    comp[root] = root;
+    up[0][root] = root;
+    while (!stack.empty()) {
+      const long long u = stack.back();
+      stack.pop_back();
+      for (const auto& e : adj[u])
+        if (depth[e.first] < 0) {
+          depth[e.first] = depth[u] + 1;
+          comp[e.first] = root;
+          up[0][e.first] = u;
+          mn[0][e.first] = e.second;
+          stack.push_back(e.first);
+        }
+    }
+  }
+  for (int k = 1; k < LOG; ++k)
+    for (long long v = 0; v < P; ++v) {
+      up[k][v] = up[k - 1][up[k - 1][v]];
+      mn[k][v] = std::min(mn[k - 1][v], mn[k - 1][up[k - 1][v]]);
+    }
+  auto bottleneck = [&](long long u, long long v) {
+    double m = INFINITY;
+    if (depth[u] < depth[v]) std::swap(u, v);
+    for (int k = LOG - 1; k >= 0; --k)
+      if (depth[u] - (1LL << k) >= depth[v]) { m = std::min(m, mn[k][u]); u = up[k][u]; }
+    if (u == v) return m;
+    for (int k = LOG - 1; k >= 0; --k)
+      if (up[k][u] != up[k][v]) {
+        m = std::min({m, mn[k][u], mn[k][v]});
+        u = up[k][u];
+        v = up[k][v];
+      }
+    return std::min({m, mn[0][u], mn[0][v]});
+  };
+  *out = bddc_paths_t{};
+  out->n_pieces = P;
+  out->min_ratio = 1.0;
+  out->worst_pair[0] = out->worst_pair[1] = -1;
+  long long lone[2] = {-1, -1}, worst[2] = {-1, -1};
+  for (size_t k = 0; k < pairs.size(); ++k) {
+    const long long u = pairs[k].first, v = pairs[k].second;
+    ++out->n_pairs;
+    if (direct[k]) { ++out->n_direct; continue; }
+    if (comp[u] != comp[v]) {
+      if (out->n_without_path++ == 0) { lone[0] = u; lone[1] = v; }
+      continue;
+    }
+    const double ratio = std::min(1.0, bottleneck(u, v) / std::min(rho[u], rho[v]));
+    if (ratio < out->min_ratio || worst[0] < 0) { out->min_ratio = ratio; worst[0] = u; worst[1] = v; }
+  }
+  // a pair without a path, else the pair of the smallest ratio
+  out->worst_pair[0] = lone[0] >= 0 ? lone[0] : worst[0];
+  out->worst_pair[1] = lone[0] >= 0 ? lone[1] : worst[1];
+  return BDDC_OK;
+  ABI_END(hnull)
+}
+
 extern "C" int bddc_apply(bddc_handle* h, const double* r_dev, double* z_dev, void* stream) {
   if (!h) return BDDC_ERR_ARG;
   ABI_BEGIN
