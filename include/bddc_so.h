@@ -53,9 +53,12 @@ enum { BDDC_W_CARD = 0, BDDC_W_RHO = 1 };    /* eq. (W) / Remark 1 weighting    
  * edges; VF: vertices and faces; V: vertices only; F: faces only (the
  * BDDC-SO(f) of Section 5.2); EF: edges and faces.  Vertices, when selected,
  * are eliminated as primal DOFs; without them the local Neumann matrix of a
- * floating subdomain (no face on the Dirichlet boundary) is singular, so one
- * of its nodes is pinned and the exact constrained solves are recovered by a
- * rank-one (Sherman-Morrison) correction.  The remark after Theorem 1 names
+ * floating subdomain (no face on the Dirichlet boundary) is singular, so its
+ * factor holds A + sum_k rho_k c_k^T c_k over the averages c_k lying in one
+ * z-plane (an augmented Lagrangian: the constrained solves are unchanged and
+ * the local coarse matrix loses rho_k on its diagonal).  Such a subdomain
+ * without an average in one z-plane gives BDDC_ERR_UNSUPPORTED at setup.
+ * The remark after Theorem 1 names
  * all edge or all face subobjects as sufficient for acceptable paths and all
  * vertex constraints as scalable but weaker, which the iteration counts show. */
 enum { BDDC_SEL_VEF = 0, BDDC_SEL_VE = 1, BDDC_SEL_VF = 2, BDDC_SEL_V = 3, BDDC_SEL_F = 4, BDDC_SEL_EF = 5 };
@@ -70,10 +73,22 @@ typedef struct {
 
 /* Box partition Theta (Section 3): on axis d the subdomains are the slabs
  * between the ncut[d] interior cut planes cut[d][0] < ... (element indices in
- * (0, n_d)).  cut[d] is a host array; ncut[d] = 0 means one slab. */
+ * (0, n_d)).  cut[d] is a host array; ncut[d] = 0 means one slab.
+ *
+ * Sub-partition Theta-hat: piece == NULL gives the boxes of the remark on
+ * local subdivision in Section 3 (each subdomain side cut into pieces of at
+ * most options.L_elems elements).  Otherwise piece is a host array of
+ * nx*ny*nz sub-subdomain labels (x fastest, >= 0; elements with equal
+ * labels form one sub-subdomain, which must lie in one subdomain, else
+ * BDDC_ERR_ARG), e.g. material regions (Remark 1: a coefficient constant on
+ * each sub-subdomain).  The (sub)objects are then the connected sets of
+ * interface nodes with equal sets of surrounding sub-subdomains, typed by the
+ * size of that set (2 face, 3 or 4 edge, more vertex); one-node vertices are
+ * point values, every other object an average.  Read during the call only. */
 typedef struct {
     int ncut[3];
     const int* cut[3];
+    const int* piece;
 } bddc_partition;
 
 /* Options.  L_elems is the sub-object size L/h >= 1: every subdomain side of
@@ -142,8 +157,8 @@ typedef struct {
                                  planes fit them (FP32 path, tuned against the
                                  CUDA-core sweep), 0 if the CUDA cores did all      */
     int factor_tc_subdomains; /* subdomains factored on the tensor cores           */
-    int pinned_subdomains;    /* floating subdomains pinned (selections without
-                                 vertices), with the rank-one correction           */
+    int pinned_subdomains;    /* floating subdomains without a point value, whose
+                                 factors carry the augmented-Lagrangian terms      */
     int n_buckets;            /* non-empty size buckets of the apply's local solves */
     int bucket_subdomains[2]; /* per bucket: its subdomains (bucket 0: those whose
                                  work vectors need a whole SM, bucket 1: the rest)  */

@@ -264,8 +264,11 @@ class BDDCSO:
 
 
 def build(problem, selection: Optional[str] = None) -> BDDCSO:
-    """BDDC-SO for a paper_2001_07289_gb300.inputs.Problem (box partition)."""
+    """BDDC-SO for a paper_2001_07289_gb300.inputs.Problem (box partition;
+    sub-subdomains from problem.piece when given, else boxes of size L)."""
     sub, piece = partition.box_labels(problem.nx, problem.ny, problem.nz, problem.cuts, problem.L)
+    if getattr(problem, "piece", None) is not None:   # sub-subdomains given per element
+        piece = np.asarray(problem.piece, dtype=np.int64).reshape(-1)
     return BDDCSO(problem.nx, problem.ny, problem.nz, problem.h, problem.alpha, sub, piece,
                   selection or problem.selection, problem.weights)
 

@@ -40,7 +40,7 @@ class Mesh(C.Structure):
 
 
 class Partition(C.Structure):
-    _fields_ = [("ncut", C.c_int * 3), ("cut", C.POINTER(C.c_int) * 3)]
+    _fields_ = [("ncut", C.c_int * 3), ("cut", C.POINTER(C.c_int) * 3), ("piece", C.POINTER(C.c_int))]
 
 
 class Options(C.Structure):
@@ -148,7 +148,8 @@ def _stream() -> C.c_void_p:
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection="vef", beta="standard"):
+def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection="vef", beta="standard",
+             piece=None):
     mesh = Mesh(nx, ny, nz, h)
     part = Partition()
     keep = []
@@ -157,6 +158,12 @@ def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selec
         keep.append(arr)
         part.ncut[d] = len(cuts[d])
         part.cut[d] = C.cast(arr, C.POINTER(C.c_int))
+    if piece is not None:
+        lab = np.ascontiguousarray(np.asarray(piece).reshape(-1), dtype=np.int32)
+        if lab.size != nx * ny * nz:
+            raise ValueError(f"piece has {lab.size} labels, the mesh {nx * ny * nz} elements")
+        keep.append(lab)
+        part.piece = lab.ctypes.data_as(C.POINTER(C.c_int))
     prec = {"fp64": BDDC_FP64, "mixed": BDDC_MIXED}[precision] if isinstance(precision, str) else precision
     wts = {"card": BDDC_W_CARD, "rho": BDDC_W_RHO}[weights] if isinstance(weights, str) else weights
     sel = SELECTIONS[selection] if isinstance(selection, str) else selection
@@ -165,10 +172,11 @@ def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selec
 
 
 def analyze(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int, h: float = 0.0,
-            precision="fp64", weights="card", selection="vef") -> dict:
-    """bddc_analyze: host-only counts of objects and of the coarse elimination plan."""
+            precision="fp64", weights="card", selection="vef", piece=None) -> dict:
+    """bddc_analyze: host-only counts of objects and of the coarse elimination
+    plan; piece: optional per-element sub-subdomain labels (else boxes of L)."""
     mesh, part, opt, keep = _structs(nx, ny, nz, h if h > 0 else 1.0 / nx, cuts, L, precision, weights, 2000, False,
-                                     selection)
+                                     selection, piece=piece)
     out = Analysis()
     _check(lib.bddc_analyze(C.byref(mesh), C.byref(part), C.byref(opt), C.byref(out)), None)
     return {k: getattr(out, k) for k, _ in Analysis._fields_}
@@ -198,13 +206,13 @@ class BDDC:
 
     def __init__(self, nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int,
                  alpha: torch.Tensor, h: float = 0.0, precision="fp64", weights="card",
-                 maxit: int = 2000, use_graph: bool = False, selection="vef", beta="standard"):
+                 maxit: int = 2000, use_graph: bool = False, selection="vef", beta="standard", piece=None):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.h = h if h > 0 else 1.0 / nx
         self.n_nodes = (nx + 1) * (ny + 1) * (nz + 1)
         self.maxit = maxit
         mesh, part, opt, keep = _structs(nx, ny, nz, self.h, cuts, L, precision, weights, maxit, use_graph,
-                                         selection, beta)
+                                         selection, beta, piece=piece)
         self._handle = C.c_void_p()
         _check(lib.bddc_setup(C.byref(mesh), C.byref(part), C.byref(opt), _vptr(alpha, nx * ny * nz), _stream(),
                               C.byref(self._handle)), None)
@@ -215,6 +223,7 @@ class BDDC:
         kw.setdefault("precision", p.precision)
         kw.setdefault("weights", p.weights)
         kw.setdefault("selection", p.selection)
+        kw.setdefault("piece", getattr(p, "piece", None))
         return cls(p.nx, p.ny, p.nz, p.cuts, p.L, a, h=p.h, **kw)
 
     def _vec(self):
@@ -310,10 +319,11 @@ class BDDC:
 
 def solve_host(nx, ny, nz, cuts, L, alpha: np.ndarray, b: np.ndarray, rtol: float, h: float = 0.0,
                precision="fp64", weights="card", maxit: int = 2000, use_graph: bool = False,
-               selection="vef"):
+               selection="vef", piece=None):
     """bddc_solve_host: setup + PCG from host arrays, result in a host array."""
     h = h if h > 0 else 1.0 / nx
-    mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection)
+    mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection,
+                                     piece=piece)
     a = np.ascontiguousarray(alpha, dtype=np.float64)
     bb = np.ascontiguousarray(b, dtype=np.float64)
     if a.size != nx * ny * nz or bb.size != (nx + 1) * (ny + 1) * (nz + 1):

@@ -191,7 +191,21 @@ struct bddc_handle {
   std::vector<SubDesc> subs;
   std::vector<LocalCoarse> lc;
   int n_coarse = 0, n_vertices = 0, max_nc = 0;
-  int vert_primal = 1, n_pinned = 0;   // vertices eliminated; floating subdomains pinned without them
+  int n_pinned = 0;               // floating subdomains without a point-value coarse DOF, pinned
+  int pin_missing = -1;           // a pinned subdomain without an average in one z-plane
+  // sub-subdomains: per-element labels (Theta-hat given) or boxes of size L
+  bool labels = false;
+  std::vector<int> label_in;            // the caller's labels until renumbered
+  std::vector<int> epiece, piece_sub;   // per element: dense piece number; per piece: subdomain
+  int n_pieces = 0;
+  // coarse objects (selected), by coarse id: type (0 vertex, 1 edge, 2 face),
+  // cell (3 doubled subdomain coordinates), global nodes (CSR, ascending)
+  std::vector<int> okind, ocell;
+  std::vector<long long> onoff, onodes;
+  std::vector<int> item_objid;    // boxes of size L: item tuple -> coarse id or -1
+  int item_n[3] = {0, 0, 0};
+  std::vector<int> lcn, own;      // local node lists; local Neumann node -> local average
+  std::vector<unsigned char> vfix;   // per global node: point-value coarse DOF
   long long n_nodes = 0, n_free = 0;
   LocalLaunch L{};
   MeshDev m{};
@@ -356,56 +370,221 @@ T* upload(bddc_handle* h, const std::vector<T>& v, cudaStream_t st) {
   return d;
 }
 
-void build_metadata(bddc_handle* h) {
-  int nsub[3], nit[3];
-  for (int d = 0; d < 3; ++d) {
-    nsub[d] = (int)h->ax[d].slab_lo.size();
-    nit[d] = h->ax[d].nitem();
+// Sub-subdomain of every element: the box pieces of size L (per-axis piece
+// numbers, x fastest) or the given labels, renumbered densely by first
+// appearance; and the subdomain of every piece.
+void build_pieces(bddc_handle* h) {
+  const bddc_mesh& M = h->mesh;
+  const long long NE = (long long)M.nx * M.ny * M.nz;
+  const AxisHost* ax = h->ax;
+  const int nsx = (int)ax[0].slab_lo.size(), nsy = (int)ax[1].slab_lo.size();
+  auto sub_of = [&](int i, int j, int k) { return ax[0].slab[i] + nsx * (ax[1].slab[j] + nsy * ax[2].slab[k]); };
+  h->epiece.assign(NE, 0);
+  if (!h->labels) {
+    const int npx = (int)ax[0].piece_lo.size(), npy = (int)ax[1].piece_lo.size(), npz = (int)ax[2].piece_lo.size();
+    for (int k = 0; k < M.nz; ++k)
+      for (int j = 0; j < M.ny; ++j)
+        for (int i = 0; i < M.nx; ++i)
+          h->epiece[i + (long long)M.nx * (j + (long long)M.ny * k)] =
+              ax[0].piece[i] + npx * (ax[1].piece[j] + npy * ax[2].piece[k]);
+    h->n_pieces = npx * npy * npz;
+    h->piece_sub.assign(h->n_pieces, 0);
+    for (int c = 0; c < npz; ++c)
+      for (int b = 0; b < npy; ++b)
+        for (int a = 0; a < npx; ++a)
+          h->piece_sub[a + npx * (b + npy * c)] = sub_of(ax[0].piece_lo[a], ax[1].piece_lo[b], ax[2].piece_lo[c]);
+    return;
   }
-  // global objects: tuples of items on Gamma, off the Dirichlet boundary, non-empty
-  const long long nt = (long long)nit[0] * nit[1] * nit[2];
-  std::vector<int> objid(nt, -1);
-  // object type by its number of point items: 3 vertex, 2 edge, 1 face
+  std::map<int, int> dense;
+  h->piece_sub.clear();
+  for (int k = 0; k < M.nz; ++k)
+    for (int j = 0; j < M.ny; ++j)
+      for (int i = 0; i < M.nx; ++i) {
+        const long long e = i + (long long)M.nx * (j + (long long)M.ny * k);
+        const int lab = h->label_in[e];
+        const int si = sub_of(i, j, k);
+        auto it = dense.find(lab);
+        if (it == dense.end()) {
+          it = dense.emplace(lab, (int)h->piece_sub.size()).first;
+          h->piece_sub.push_back(si);
+        } else if (h->piece_sub[it->second] != si) {
+          throw BddcError(BDDC_ERR_ARG, "sub-subdomain label " + std::to_string(lab) + " spans two subdomains");
+        }
+        h->epiece[e] = it->second;
+      }
+  h->n_pieces = (int)h->piece_sub.size();
+}
+
+// The selected coarse objects, numbered in a fixed order: item tuples of the
+// box pieces (x fastest), or for labels connected components (nodes sharing
+// an element) of interface nodes with equal sets of surrounding pieces, in
+// the order of their first node.  Type by the number of pieces sharing the
+// object (Section 3): 2 face, 3 or 4 edge, more vertex; in box pieces the
+// item tuples with 1, 2 or 3 point items.
+void build_objects(bddc_handle* h, bool keep_v, bool keep_e, bool keep_f) {
+  const bddc_mesh& M = h->mesh;
+  const AxisHost* ax = h->ax;
+  const int NX = M.nx + 1, NY = M.ny + 1, NZ = M.nz + 1;
+  const int nsx = (int)ax[0].slab_lo.size(), nsy = (int)ax[1].slab_lo.size();
+  auto keep = [&](int kind) { return kind == 0 ? keep_v : (kind == 1 ? keep_e : keep_f); };
+  h->okind.clear();
+  h->ocell.clear();
+  h->onoff.assign(1, 0);
+  h->onodes.clear();
+  h->item_objid.clear();
+  if (!h->labels) {
+    int nit[3];
+    for (int d = 0; d < 3; ++d) nit[d] = h->item_n[d] = ax[d].nitem();
+    h->item_objid.assign((size_t)nit[0] * nit[1] * nit[2], -1);
+    for (int iz = 0; iz < nit[2]; ++iz)
+      for (int iy = 0; iy < nit[1]; ++iy)
+        for (int ix = 0; ix < nit[0]; ++ix) {
+          const int it[3] = {ix, iy, iz};
+          bool ok = true, on_gamma = false;
+          for (int d = 0; d < 3; ++d) {
+            const int k = ax[d].item_kind[it[d]];
+            if (k == 3 || ax[d].empty(it[d])) ok = false;
+            if (k == 2) on_gamma = true;
+          }
+          const int pts = !(ix & 1) + !(iy & 1) + !(iz & 1);
+          const int kind = pts == 3 ? 0 : (pts == 2 ? 1 : 2);
+          if (!ok || !on_gamma || !keep(kind)) continue;
+          h->item_objid[ix + (size_t)nit[0] * (iy + (size_t)nit[1] * iz)] = (int)h->okind.size();
+          h->okind.push_back(kind);
+          for (int d = 0; d < 3; ++d) {
+            const int sl = ax[d].slab[ax[d].item_lo[it[d]]];   // element right of the item's first node
+            h->ocell.push_back(ax[d].item_kind[it[d]] == 2 ? 2 * sl : 2 * sl + 1);
+          }
+          for (int z = ax[2].item_lo[iz]; z <= ax[2].item_hi[iz]; ++z)
+            for (int y = ax[1].item_lo[iy]; y <= ax[1].item_hi[iy]; ++y)
+              for (int x = ax[0].item_lo[ix]; x <= ax[0].item_hi[ix]; ++x) h->onodes.push_back(nodeid(NX, NY, x, y, z));
+          h->onoff.push_back((long long)h->onodes.size());
+        }
+    return;
+  }
+  // interface nodes (off the Dirichlet boundary, on a cut plane) and the
+  // sorted set of pieces of their eight elements
+  const long long NN = (long long)NX * NY * NZ;
+  std::vector<int> key_of(NN, -1);
+  std::map<std::vector<int>, int> keys;
+  std::vector<std::vector<int>> key_list;
+  for (int z = 1; z < M.nz; ++z)
+    for (int y = 1; y < M.ny; ++y)
+      for (int x = 1; x < M.nx; ++x) {
+        if (!ax[0].theta[x] && !ax[1].theta[y] && !ax[2].theta[z]) continue;
+        std::vector<int> k;
+        for (int dz = -1; dz <= 0; ++dz)
+          for (int dy = -1; dy <= 0; ++dy)
+            for (int dx = -1; dx <= 0; ++dx)
+              k.push_back(h->epiece[(x + dx) + (long long)M.nx * ((y + dy) + (long long)M.ny * (z + dz))]);
+        std::sort(k.begin(), k.end());
+        k.erase(std::unique(k.begin(), k.end()), k.end());
+        auto it = keys.find(k);
+        if (it == keys.end()) {
+          it = keys.emplace(k, (int)key_list.size()).first;
+          key_list.push_back(k);
+        }
+        key_of[nodeid(NX, NY, x, y, z)] = it->second;
+      }
+  std::vector<char> seen(NN, 0);
+  std::vector<long long> comp, stack;
+  for (long long n0 = 0; n0 < NN; ++n0) {
+    if (key_of[n0] < 0 || seen[n0]) continue;
+    const int key = key_of[n0];
+    comp.clear();
+    stack.assign(1, n0);
+    seen[n0] = 1;
+    while (!stack.empty()) {
+      const long long u = stack.back();
+      stack.pop_back();
+      comp.push_back(u);
+      const int ux = (int)(u % NX), uy = (int)((u / NX) % NY), uz = (int)(u / ((long long)NX * NY));
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int x = ux + dx, y = uy + dy, z = uz + dz;
+            if (x < 0 || y < 0 || z < 0 || x >= NX || y >= NY || z >= NZ) continue;
+            const long long v = nodeid(NX, NY, x, y, z);
+            if (seen[v] || key_of[v] != key) continue;
+            seen[v] = 1;
+            stack.push_back(v);
+          }
+    }
+    const std::vector<int>& k = key_list[key];
+    const int np = (int)k.size();
+    const int kind = np == 2 ? 2 : (np <= 4 ? 1 : 0);
+    if (!keep(kind)) continue;
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+    for (int p : k) {
+      const int si = h->piece_sub[p];
+      const int sc[3] = {si % nsx, (si / nsx) % nsy, si / (nsx * nsy)};
+      for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], sc[d]); hi[d] = std::max(hi[d], sc[d]); }
+    }
+    h->okind.push_back(kind);
+    for (int d = 0; d < 3; ++d) h->ocell.push_back(lo[d] == hi[d] ? 2 * lo[d] + 1 : 2 * hi[d]);
+    std::sort(comp.begin(), comp.end());
+    h->onodes.insert(h->onodes.end(), comp.begin(), comp.end());
+    h->onoff.push_back((long long)h->onodes.size());
+  }
+}
+
+void build_metadata(bddc_handle* h) {
+  int nsub[3];
+  for (int d = 0; d < 3; ++d) nsub[d] = (int)h->ax[d].slab_lo.size();
   const int sel = h->opt.selection;
   const bool keep_verts = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VE || sel == BDDC_SEL_VF || sel == BDDC_SEL_V;
   const bool keep_edges = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VE || sel == BDDC_SEL_EF;
   const bool keep_faces = sel == BDDC_SEL_VEF || sel == BDDC_SEL_VF || sel == BDDC_SEL_F || sel == BDDC_SEL_EF;
-  h->vert_primal = keep_verts;
-  auto valid = [&](int ix, int iy, int iz) {
-    int it[3] = {ix, iy, iz};
-    bool on_gamma = false;
-    for (int d = 0; d < 3; ++d) {
-      int k = h->ax[d].item_kind[it[d]];
-      if (k == 3 || h->ax[d].empty(it[d])) return false;
-      if (k == 2) on_gamma = true;
+  build_pieces(h);
+  build_objects(h, keep_verts, keep_edges, keep_faces);
+  const int nc = (int)h->okind.size();
+  const bddc_mesh& Mh = h->mesh;
+  const int NXh = Mh.nx + 1, NYh = Mh.ny + 1;
+  // point values: one-node vertex objects, eliminated as primal DOFs
+  h->vfix.assign((size_t)NXh * NYh * (Mh.nz + 1), 0);
+  int nvert = 0;
+  for (int g = 0; g < nc; ++g)
+    if (h->okind[g] == 0 && h->onoff[g + 1] - h->onoff[g] == 1) {
+      h->vfix[h->onodes[h->onoff[g]]] = 1;
+      ++nvert;
     }
-    const int pts = !(ix & 1) + !(iy & 1) + !(iz & 1);
-    if ((pts == 3 && !keep_verts) || (pts == 2 && !keep_edges) || (pts == 1 && !keep_faces)) return false;
-    return on_gamma;
-  };
-  int nc = 0, nvert = 0;
-  for (int iz = 0; iz < nit[2]; ++iz)
-    for (int iy = 0; iy < nit[1]; ++iy)
-      for (int ix = 0; ix < nit[0]; ++ix)
-        if (valid(ix, iy, iz)) {
-          objid[ix + (long long)nit[0] * (iy + (long long)nit[1] * iz)] = nc++;
-          if (!(ix & 1) && !(iy & 1) && !(iz & 1)) ++nvert;
-        }
   h->n_coarse = nc;
   h->n_vertices = nvert;
   h->n_pinned = 0;
-  for (int d = 0; d < 3; ++d) {
-    h->geom.nitem[d] = nit[d];
-    h->geom.nsub[d] = nsub[d];
-    h->geom.slab_item_lo[d].clear();
-    h->geom.slab_item_hi[d].clear();
-    for (int sl = 0; sl < nsub[d]; ++sl) {
-      h->geom.slab_item_lo[d].push_back(h->ax[d].item[h->ax[d].slab_lo[sl]]);
-      h->geom.slab_item_hi[d].push_back(h->ax[d].item[h->ax[d].slab_hi[sl]]);
-    }
+  h->pin_missing = -1;
+  // cells -> objects (CSR, ascending) for the nested dissection
+  {
+    CoarseGeom& G = h->geom;
+    int n3[3];
+    for (int d = 0; d < 3; ++d) { G.nsub[d] = nsub[d]; n3[d] = 2 * nsub[d] + 1; }
+    const long long ncell = (long long)n3[0] * n3[1] * n3[2];
+    G.cell_ptr.assign(ncell + 1, 0);
+    auto cid = [&](int g) {
+      return h->ocell[3 * g] + (long long)n3[0] * (h->ocell[3 * g + 1] + (long long)n3[1] * h->ocell[3 * g + 2]);
+    };
+    for (int g = 0; g < nc; ++g) ++G.cell_ptr[cid(g) + 1];
+    for (long long c = 0; c < ncell; ++c) G.cell_ptr[c + 1] += G.cell_ptr[c];
+    G.cell_obj.assign(nc, 0);
+    std::vector<int> fill(G.cell_ptr.begin(), G.cell_ptr.end() - 1);
+    for (int g = 0; g < nc; ++g) G.cell_obj[fill[cid(g)]++] = g;
   }
-  // subdomains
+  // objects of every subdomain (ascending coarse id): a cell coordinate
+  // 2s + 1 lies in slab s, 2s on the plane of slabs s - 1 and s
   const int S = nsub[0] * nsub[1] * nsub[2];
+  std::vector<std::vector<int>> sub_objs(S);
+  for (int g = 0; g < nc; ++g) {
+    int r0[3], r1[3];
+    for (int d = 0; d < 3; ++d) {
+      const int c = h->ocell[3 * g + d];
+      if (c & 1) { r0[d] = r1[d] = (c - 1) / 2; }
+      else { r0[d] = c / 2 - 1; r1[d] = c / 2; }
+    }
+    for (int sz = r0[2]; sz <= r1[2]; ++sz)
+      for (int sy = r0[1]; sy <= r1[1]; ++sy)
+        for (int sx = r0[0]; sx <= r1[0]; ++sx) sub_objs[sx + nsub[0] * (sy + nsub[1] * sz)].push_back(g);
+  }
+  h->lcn.clear();
+  h->own.clear();
   h->subs.assign(S, SubDesc{});
   h->lc.clear();
   // (coarse id, subdomain, local position) of every local coarse DOF, in
@@ -424,53 +603,60 @@ void build_metadata(bddc_handle* h) {
         SubDesc& s = h->subs[si];
         s.id = si;
         const int sl[3] = {sx, sy, sz};
-        int ilo[3], ihi[3];
         for (int d = 0; d < 3; ++d) {
           s.e0[d] = h->ax[d].slab_lo[sl[d]];
           s.w[d] = h->ax[d].slab_hi[sl[d]] - s.e0[d];
-          ilo[d] = h->ax[d].item[s.e0[d]];
-          ihi[d] = h->ax[d].item[s.e0[d] + s.w[d]];
         }
         s.color = (sx & 1) + 2 * (sy & 1) + 4 * (sz & 1);
-        {
-          // floating: no face of the box on the Dirichlet boundary; without
-          // vertex primal DOFs its local Neumann matrix has the constants as
-          // kernel and gets pinned at local node 0
-          const int nd[3] = {h->mesh.nx, h->mesh.ny, h->mesh.nz};
-          bool floating = true;
-          for (int d = 0; d < 3; ++d)
-            if (s.e0[d] == 0 || s.e0[d] + s.w[d] == nd[d]) floating = false;
-          s.pin = (!keep_verts && floating) ? 1 : 0;
-          h->n_pinned += s.pin;
-        }
         const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
-        // local coarse DOFs: vertices first, then averages, each lexicographic
+        // local coarse DOFs: point values first, then averages, each by coarse
+        // id; node lists on the local Neumann grid
         verts.clear();
         avgs.clear();
-        for (int iz = ilo[2]; iz <= ihi[2]; ++iz)
-          for (int iy = ilo[1]; iy <= ihi[1]; ++iy)
-            for (int ix = ilo[0]; ix <= ihi[0]; ++ix) {
-              int g = objid[ix + (long long)nit[0] * (iy + (long long)nit[1] * iz)];
-              if (g < 0) continue;
-              LocalCoarse c;
-              c.gid = g;
-              int it[3] = {ix, iy, iz};
-              int cnt = 1;
-              for (int d = 0; d < 3; ++d) {
-                c.lo[d] = (short)(h->ax[d].item_lo[it[d]] - s.e0[d]);
-                c.hi[d] = (short)(h->ax[d].item_hi[it[d]] - s.e0[d]);
-                cnt *= (c.hi[d] - c.lo[d] + 1);
-              }
-              c.count = cnt;
-              bool vert = !(ix & 1) && !(iy & 1) && !(iz & 1);
-              (vert ? verts : avgs).push_back(c);
-            }
+        for (int g : sub_objs[si]) {
+          LocalCoarse c;
+          c.gid = g;
+          c.count = (int)(h->onoff[g + 1] - h->onoff[g]);
+          c.off = (int)h->lcn.size();
+          for (long long q = h->onoff[g]; q < h->onoff[g + 1]; ++q) {
+            const long long nd = h->onodes[q];
+            const int x = (int)(nd % NXh) - s.e0[0], y = (int)((nd / NXh) % NYh) - s.e0[1],
+                      z = (int)(nd / ((long long)NXh * NYh)) - s.e0[2];
+            if (x < 0 || y < 0 || z < 0 || x > s.w[0] || y > s.w[1] || z > s.w[2])
+              throw std::runtime_error("coarse object outside a subdomain that shares it");
+            if (q == h->onoff[g]) { c.v[0] = (short)x; c.v[1] = (short)y; c.v[2] = (short)z; }
+            h->lcn.push_back(x + px * (y + py * z));
+          }
+          const bool point = h->okind[g] == 0 && c.count == 1;
+          (point ? verts : avgs).push_back(c);
+        }
         s.nv = (int)verts.size();
         s.na = (int)avgs.size();
         s.nc = s.nv + s.na;
         s.cofs = (int)h->lc.size();
         for (auto& c : verts) h->lc.push_back(c);
         for (auto& c : avgs) h->lc.push_back(c);
+        {
+          // floating: no face of the box on the Dirichlet boundary; without a
+          // point value its local Neumann matrix has the constants as kernel
+          // and gets pinned (augmented-Lagrangian terms, see k_pin_penalty),
+          // which needs an average whose nodes lie in one z-plane of the box
+          const int nd[3] = {h->mesh.nx, h->mesh.ny, h->mesh.nz};
+          bool floating = true;
+          for (int d = 0; d < 3; ++d)
+            if (s.e0[d] == 0 || s.e0[d] + s.w[d] == nd[d]) floating = false;
+          s.pin = (floating && s.nv == 0) ? 1 : 0;
+          h->n_pinned += s.pin;
+          if (s.pin) {
+            bool one = false;
+            for (const LocalCoarse& c : avgs) {
+              bool same = true;
+              for (int q = 1; q < c.count; ++q) same = same && h->lcn[c.off + q] / (px * py) == h->lcn[c.off] / (px * py);
+              one = one || same;
+            }
+            if (!one && h->pin_missing < 0) h->pin_missing = si;   // refused by the setup
+          }
+        }
         for (int j = 0; j < s.nc; ++j) {
           own_g.push_back(h->lc[s.cofs + j].gid);
           own_e.push_back(make_int2(si, s.cofs + j));
@@ -493,6 +679,11 @@ void build_metadata(bddc_handle* h) {
         s.offPhi = offPhi; offPhi += padded((long long)s.nB * s.nc);
         s.offB = offB; offB += s.nB;
         s.offVec = offVec; offVec += NN;
+        h->own.resize(offVec, -1);   // local Neumann node -> local average (or -1)
+        for (int a = 0; a < s.na; ++a) {
+          const LocalCoarse& c = h->lc[s.cofs + s.nv + a];
+          for (int q = 0; q < c.count; ++q) h->own[s.offVec + h->lcn[c.off + q]] = s.nv + a;
+        }
         s.offTC = offTC; offTC += (long long)pz * tc_kchunks(QN) * tc_chunk_floats(QN);
         L.maxQD = std::max(L.maxQD, QD); L.maxNzD = std::max(L.maxNzD, nzD); L.maxND = std::max(L.maxND, QD * nzD);
         L.maxQN = std::max(L.maxQN, QN); L.maxNzN = std::max(L.maxNzN, pz); L.maxNN = std::max(L.maxNN, NN);
@@ -513,7 +704,6 @@ void build_metadata(bddc_handle* h) {
     std::vector<int> fill(ptr.begin(), ptr.end() - 1);
     for (size_t q = 0; q < own_g.size(); ++q) ent[fill[own_g[q]]++] = own_e[q];
   }
-  h->geom.objid = std::move(objid);
   // colour lists
   std::vector<int> clist;
   for (int c = 0; c < 8; ++c) {
@@ -664,6 +854,9 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   h->n_nodes = (long long)(M.nx + 1) * (M.ny + 1) * (M.nz + 1);
   h->n_free = (long long)(M.nx - 1) * (M.ny - 1) * (M.nz - 1);
   build_metadata(h);
+  if (h->pin_missing >= 0)
+    throw BddcError(BDDC_ERR_UNSUPPORTED, "floating subdomain " + std::to_string(h->pin_missing) +
+                                              " has neither a point value nor an average within one z-plane");
   {
     // the apply streams rows of plane blocks and of Phi through the shared-
     // memory ring and keeps one subdomain's vectors in shared memory
@@ -672,10 +865,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     const size_t ring = (size_t)NBUF * CHB + 16 * NBUF;
     const size_t vec = std::max({(size_t)L.maxNN + 3 * (size_t)L.maxQN, (size_t)L.maxND + 3 * (size_t)L.maxQD,
                                  (size_t)L.maxNB + 1 + L.maxNc});
-    size_t smem = ring + (size_t)es * (APPLY_THREADS + vec + 2);
-    if (h->n_pinned)   // the pinned solve also keeps C y (FP64) beside the Neumann vectors
-      smem = std::max(smem, ring + ((size_t)es * (APPLY_THREADS + L.maxNN + 3 * (size_t)L.maxQN) + 15) / 16 * 16 +
-                                sizeof(double) * (L.maxNc + 32));
+    const size_t smem = ring + (size_t)es * (APPLY_THREADS + vec + 2);
     bool rows_ok = true;
     for (const SubDesc& s : h->subs) {
       const int QN = (s.w[0] + 1) * (s.w[1] + 1);
@@ -714,21 +904,18 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   // axis tables
   MeshDev& m = h->m;
   m.nx = M.nx; m.ny = M.ny; m.nz = M.nz;
-  m.vert_primal = h->vert_primal;
+  m.vfix = upload(h, h->vfix, st);
+  m.epiece = upload(h, h->epiece, st);
   m.NX = M.nx + 1; m.NY = M.ny + 1; m.NZ = M.nz + 1;
   m.h = M.h;
   for (int d = 0; d < 3; ++d) {
     AxisHost& a = h->ax[d];
-    m.ax[d].item = upload(h, a.item, st);
     m.ax[d].theta = upload(h, a.theta, st);
-    m.ax[d].hat = upload(h, a.hat, st);
     m.ax[d].slab = upload(h, a.slab, st);
-    m.ax[d].piece = upload(h, a.piece, st);
     m.ax[d].slab_lo = upload(h, a.slab_lo, st);
     m.ax[d].slab_hi = upload(h, a.slab_hi, st);
     m.ax[d].n = a.n;
     m.ax[d].nslab = (int)a.slab_lo.size();
-    m.ax[d].nitem = a.nitem();
     m.nsub[d] = (int)a.slab_lo.size();
   }
   const bool dbl = h->local_double;
@@ -806,6 +993,8 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     }
   }
   L.lc = upload(h, h->lc, st);
+  L.lcn = upload(h, h->lcn, st);
+  L.own = upload(h, h->own, st);
   L.facD = h->dalloc(es * lay.D);
   L.facN = h->dalloc(es * lay.N);
   L.Phi = h->dalloc(es * lay.Phi);
@@ -817,10 +1006,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   L.rcl = h->dnew<double>(h->lc.size());
   L.npin = h->n_pinned;
   if (L.npin) {
-    L.zw = h->dnew<double>(lay.B);
-    L.zl = h->dnew<double>(std::max<size_t>(h->lc.size(), 1));
-    L.cpin = h->dnew<double>(h->subs.size());
-    L.pdot = h->dnew<double>(h->subs.size());
+    L.pen = h->dnew<double>(std::max<size_t>(h->lc.size(), 1));
   }
   L.err = h->err;
   L.scratch = h->dalloc(es * lay.W, true);
@@ -838,17 +1024,20 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   // weights (eq. W or Remark 1)
   double* pw = nullptr;
   if (h->opt.weights == BDDC_W_RHO) {
-    std::vector<int> plo, phi;
-    int npc[3];
-    for (int d = 0; d < 3; ++d) {
-      npc[d] = (int)h->ax[d].piece_lo.size();
-      plo.insert(plo.end(), h->ax[d].piece_lo.begin(), h->ax[d].piece_lo.end());
-      phi.insert(phi.end(), h->ax[d].piece_hi.begin(), h->ax[d].piece_hi.end());
+    // elements of every piece, ascending (counting sort of the element labels)
+    const int np = h->n_pieces;
+    std::vector<long long> pe_off(np + 1, 0);
+    for (int p : h->epiece) ++pe_off[p + 1];
+    for (int p = 0; p < np; ++p) pe_off[p + 1] += pe_off[p];
+    std::vector<int> pe(h->epiece.size());
+    {
+      std::vector<long long> fill(pe_off.begin(), pe_off.end() - 1);
+      for (size_t e = 0; e < h->epiece.size(); ++e) pe[fill[h->epiece[e]]++] = (int)e;
     }
-    int* dplo = upload(h, plo, st);
-    int* dphi = upload(h, phi, st);
-    pw = (double*)h->dalloc(sizeof(double) * (size_t)npc[0] * npc[1] * npc[2], true);
-    launch_piece_alpha(m, h->alpha, dplo, dphi, npc[0], npc[1], npc[2], pw, st);
+    const long long* dpo = upload(h, pe_off, st);
+    const int* dpe = upload(h, pe, st);
+    pw = (double*)h->dalloc(sizeof(double) * (size_t)np, true);
+    launch_piece_alpha(h->alpha, dpo, dpe, np, pw, st);
   }
   launch_weights(L, pw, st);
   tune_factor(h, st);
@@ -1212,6 +1401,13 @@ std::unique_ptr<bddc_handle> make_handle(const bddc_mesh* mesh, const bddc_parti
     if (part->ncut[d] < 0 || (part->ncut[d] > 0 && !part->cut[d])) throw BddcError(BDDC_ERR_ARG, "bad cut list");
     h->ax[d].build(n[d], part->cut[d], part->ncut[d], opt->L_elems);
   }
+  if (part->piece) {
+    h->labels = true;
+    const long long NE = (long long)mesh->nx * mesh->ny * mesh->nz;
+    h->label_in.assign(part->piece, part->piece + NE);
+    for (int v : h->label_in)
+      if (v < 0) throw BddcError(BDDC_ERR_ARG, "sub-subdomain labels must be >= 0");
+  }
   for (int d = 0; d < 3; ++d)
     for (size_t s = 0; s < h->ax[d].slab_lo.size(); ++s)
       if (h->ax[d].slab_hi[s] - h->ax[d].slab_lo[s] > 4000) throw BddcError(BDDC_ERR_ARG, "subdomain too wide");
@@ -1251,14 +1447,9 @@ extern "C" int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, c
   *out = bddc_analysis_t{};
   out->n_sub = (int)h->subs.size();
   out->n_coarse = h->n_coarse;
-  const int* nit = h->geom.nitem;
-  for (int iz = 0; iz < nit[2]; ++iz)
-    for (int iy = 0; iy < nit[1]; ++iy)
-      for (int ix = 0; ix < nit[0]; ++ix)
-        if (h->geom.objid[ix + (long long)nit[0] * (iy + (long long)nit[1] * iz)] >= 0) {
-          int pts = !(ix & 1) + !(iy & 1) + !(iz & 1);
-          if (pts == 3) ++out->n_vertices; else if (pts == 2) ++out->n_edges; else ++out->n_faces;
-        }
+  for (int k : h->okind) {
+    if (k == 0) ++out->n_vertices; else if (k == 1) ++out->n_edges; else ++out->n_faces;
+  }
   out->max_local_coarse = h->max_nc;
   out->n_fronts = h->mf.nfront;
   out->n_levels = h->mf.nlevel;
@@ -1294,8 +1485,9 @@ extern "C" int bddc_acceptable_paths(const bddc_mesh* mesh, const bddc_partition
   for (int d = 0; d < 3; ++d) np[d] = (int)ax[d].piece_lo.size();
   const long long P = (long long)np[0] * np[1] * np[2];
   if (P > (1LL << 22)) throw BddcError(BDDC_ERR_UNSUPPORTED, "more than 2^22 sub-subdomains");
-  const int* nit = h->geom.nitem;
-  const std::vector<int>& objid = h->geom.objid;
+  if (h->labels) throw BddcError(BDDC_ERR_UNSUPPORTED, "the acceptable-path check takes box sub-subdomains (L)");
+  const int* nit = h->item_n;
+  const std::vector<int>& objid = h->item_objid;
   auto pid = [&](int a, int b, int c) { return (long long)a + (long long)np[0] * (b + (long long)np[1] * c); };
   // piece coefficient: the mean of alpha over the piece's elements (1 without alpha)
   std::vector<double> rho(P, 1.0);
@@ -1677,15 +1869,6 @@ extern "C" int bddc_get_coarse_basis(const bddc_handle* h, int sub, double* phi_
       CK(cudaMemcpy(tmp.data(), (float*)h->L.Phi + s.offPhi, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
       for (size_t i = 0; i < cnt; ++i) phi_host[i] = tmp[i];
     }
-    if (s.pin) {   // Phi = Phi~ + c zeta_w zeta_l^T (the pinned subdomain's exact basis)
-      std::vector<double> zw(s.nB), zl(s.nc);
-      double c = 0.0;
-      CK(cudaMemcpy(zw.data(), h->L.zw + s.offB, sizeof(double) * s.nB, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(zl.data(), h->L.zl + s.cofs, sizeof(double) * s.nc, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(&c, h->L.cpin + s.id, sizeof(double), cudaMemcpyDeviceToHost));
-      for (int b = 0; b < s.nB; ++b)
-        for (int j = 0; j < s.nc; ++j) phi_host[(size_t)b * s.nc + j] += c * zw[b] * zl[j];
-    }
   }
   if (gid_host)
     for (int j = 0; j < s.nc; ++j) gid_host[j] = h->lc[s.cofs + j].gid;
@@ -1798,7 +1981,6 @@ void apply_noalloc_impl(bddc_handle* h, unsigned char* base, const double* r, do
   L.rcl = (double*)(base + carve(off, sizeof(double) * std::max<size_t>(h->lc.size(), 1)));
   L.vgam = (double*)(base + carve(off, sizeof(double) * std::max<long long>(h->n_surface_total, 1)));
   L.vloc = base + carve(off, sizeof(T) * std::max<long long>(h->n_local_nodes_total, 1));
-  if (L.npin) L.pdot = (double*)(base + carve(off, sizeof(double) * h->subs.size()));
   // the array keeps the previous call's contents; the interior solve writes
   // only interior nodes, so the rest of uI must start at zero
   CK(cudaMemsetAsync(uI, 0, sizeof(double) * N, st));
@@ -1815,7 +1997,6 @@ size_t noalloc_bytes_needed(const bddc_handle* h) {
   carve(off, sizeof(double) * std::max<size_t>(h->lc.size(), 1));
   carve(off, sizeof(double) * std::max<long long>(h->n_surface_total, 1));
   carve(off, es * std::max<long long>(h->n_local_nodes_total, 1));
-  if (h->L.npin) carve(off, sizeof(double) * h->subs.size());
   return off;
 }
 

@@ -57,21 +57,22 @@ struct Box { int s0[3], s1[3]; };
 struct Builder {
   const CoarseGeom& g;
   MFPlan& P;
+  int nc3[3];
   std::vector<std::vector<int>> piv, upd;   // per front
   std::vector<std::vector<int>> children;
   std::vector<int> depth;
-  Builder(const CoarseGeom& g_, MFPlan& P_) : g(g_), P(P_) {}
-
-  int obj(int ix, int iy, int iz) const { return g.objid[ix + (long long)g.nitem[0] * (iy + (long long)g.nitem[1] * iz)]; }
-
-  // item range [lo, hi] (closed) of a box along axis d
-  void range(const Box& b, int d, int& lo, int& hi) const {
-    lo = g.slab_item_lo[d][b.s0[d]];
-    hi = g.slab_item_hi[d][b.s1[d] - 1];
+  Builder(const CoarseGeom& g_, MFPlan& P_) : g(g_), P(P_) {
+    for (int d = 0; d < 3; ++d) nc3[d] = 2 * g.nsub[d] + 1;
   }
 
-  // returns the front id created for this box (or -1 if the box and all its
-  // descendants hold no pivots); children ids collected into `kids`.
+  // objects of one cell, ascending
+  void cell(int cx, int cy, int cz, std::vector<int>& out) const {
+    const long long c = cx + (long long)nc3[0] * (cy + (long long)nc3[1] * cz);
+    for (int q = g.cell_ptr[c]; q < g.cell_ptr[c + 1]; ++q) out.push_back(g.cell_obj[q]);
+  }
+
+  // creates the fronts of this box and of its descendants; the ids of the
+  // fronts without a parent inside the box are collected into `kids`
   void build(const Box& b, std::vector<int>& kids) {
     int ext[3] = {b.s1[0] - b.s0[0], b.s1[1] - b.s0[1], b.s1[2] - b.s0[2]};
     if (ext[0] <= 1 && ext[1] <= 1 && ext[2] <= 1) return;
@@ -79,20 +80,18 @@ struct Builder {
     for (int d = 1; d < 3; ++d)
       if (ext[d] > ext[ax]) ax = d;
     const int mid = b.s0[ax] + ext[ax] / 2;
-    const int cut_item = g.slab_item_lo[ax][mid];
-    int lo[3], hi[3];
-    for (int d = 0; d < 3; ++d) range(b, d, lo[d], hi[d]);
-    // separator: item[ax] == cut_item, other items strictly inside the box
+    int lo[3], hi[3];   // closed cell range of the box
+    for (int d = 0; d < 3; ++d) { lo[d] = 2 * b.s0[d]; hi[d] = 2 * b.s1[d]; }
+    // separator: cells on the cut plane of `mid`, strictly inside the box
     std::vector<int> sep;
     {
       int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
-      int it[3];
-      it[ax] = cut_item;
+      int c[3];
+      c[ax] = 2 * mid;
       for (int j = lo[a2] + 1; j < hi[a2]; ++j)
         for (int i = lo[a1] + 1; i < hi[a1]; ++i) {
-          it[a1] = i; it[a2] = j;
-          int o = obj(it[0], it[1], it[2]);
-          if (o >= 0) sep.push_back(o);
+          c[a1] = i; c[a2] = j;
+          cell(c[0], c[1], c[2], sep);
         }
     }
     Box c0 = b, c1 = b;
@@ -105,15 +104,12 @@ struct Builder {
       for (int k : my_kids) kids.push_back(k);
       return;
     }
-    // update set: valid objects on the closed box boundary
+    // update set: objects in the cells of the closed box boundary
     std::vector<int> u;
-    for (int iz = lo[2]; iz <= hi[2]; ++iz)
-      for (int iy = lo[1]; iy <= hi[1]; ++iy) {
-        const bool yz_bnd = iy == lo[1] || iy == hi[1] || iz == lo[2] || iz == hi[2];
-        for (int ix = lo[0]; ix <= hi[0]; ix = (yz_bnd || ix == hi[0]) ? ix + 1 : hi[0]) {
-          int o = obj(ix, iy, iz);
-          if (o >= 0) u.push_back(o);
-        }
+    for (int cz = lo[2]; cz <= hi[2]; ++cz)
+      for (int cy = lo[1]; cy <= hi[1]; ++cy) {
+        const bool yz_bnd = cy == lo[1] || cy == hi[1] || cz == lo[2] || cz == hi[2];
+        for (int cx = lo[0]; cx <= hi[0]; cx = (yz_bnd || cx == hi[0]) ? cx + 1 : hi[0]) cell(cx, cy, cz, u);
       }
     std::sort(u.begin(), u.end());
     const int f = (int)piv.size();

@@ -29,8 +29,8 @@ struct SubDesc {
   int cofs;           // first entry of this subdomain in the local-coarse table
                       // (also the offset of its nc-vector of local coarse values)
   int color;          // (sx&1) + 2(sy&1) + 4(sz&1): same colour => no shared objects
-  int pin;            // 1: floating subdomain of a selection without vertices, whose
-                      // local Neumann matrix is made SPD by pinning local node 0
+  int pin;            // 1: floating subdomain without a point value, whose local
+                      // Neumann factor carries augmented-Lagrangian terms
   long long offD;     // Dirichlet factor slots (local type)
   long long offN;     // Neumann factor slots (local type)
   long long offW;     // factorisation scratch: 2*QN^2 + 1024*ceil(QN/32) (local type)
@@ -53,32 +53,32 @@ __host__ __device__ inline int tc_mtiles(int Q) { return (Q + 127) / 128; }
 __host__ __device__ inline int tc_kchunks(int Q) { return (Q + 31) / 32; }
 __host__ __device__ inline long long tc_chunk_floats(int Q) { return (long long)tc_mtiles(Q) * 8192; }
 
-// A coarse DOF as seen from one subdomain: the object's local node box
-// (inclusive ranges on the local Neumann grid) and its global number.
+// A coarse DOF as seen from one subdomain: its global number and the list of
+// the object's nodes on the local Neumann grid (entries off .. off + count - 1
+// of the local-node table, linear index ix + px (iy + py iz), ascending); v is
+// the first node's local position (the node itself for a point value).
 struct LocalCoarse {
   int gid;
-  short lo[3], hi[3];
+  int off;            // first entry in the local-node table
   int count;          // nodes in the object
+  short v[3];
 };
 
 // Per-axis tables (global), concatenated for the three axes.
 struct AxisTables {
-  const int* item;     // node -> item (points even, open intervals odd), size n+1
   const int* theta;    // node -> 1 on a Theta cut plane (interior), 0 else
-  const int* hat;      // node -> 1 on a Theta-hat piece boundary (incl. Theta), 0 else
   const int* slab;     // element -> slab index, size n
-  const int* piece;    // element -> piece index along the axis, size n
   const int* slab_lo;  // slab -> first element
   const int* slab_hi;  // slab -> one past last element
   int n;               // elements on this axis
   int nslab;
-  int nitem;
 };
 
 struct MeshDev {
   int nx, ny, nz;
   int NX, NY, NZ;      // nodes per axis
-  int vert_primal;     // 1: the selection has vertices, eliminated as primal DOFs
+  const unsigned char* vfix;  // per node: 1 for a point-value coarse DOF (eliminated as primal)
+  const int* epiece;   // per element: sub-subdomain (piece) number
   double h;
   AxisTables ax[3];
   int nsub[3];

@@ -47,6 +47,8 @@ struct LocalLaunch {
   MeshDev m;
   const double* alpha;
   const LocalCoarse* lc;
+  const int* lcn;               // local node lists of the coarse DOFs (LocalCoarse::off, count)
+  const int* own;               // per local Neumann node (offVec layout): local average index or -1
   void *facD, *facN, *scratch, *mscratch;
   long long mscratch_stride;
   void *Y, *G, *Lv, *PA, *Sc, *Phi, *vloc;
@@ -69,11 +71,10 @@ struct LocalLaunch {
   BucketSizes bsize[MAX_BUCKETS] = {};
   int bcluster[MAX_BUCKETS] = {1, 1};
   FactorBucket fbucket[2] = {};
-  // pinned floating subdomains (selections without vertices): their count,
-  // zeta_w on the box surfaces (offB), zeta_l (cofs), the Sherman-Morrison
-  // factor c per subdomain, and a per-subdomain apply scalar zeta_w . r_i
+  // pinned floating subdomains (selections without point values): their
+  // count and the augmented-Lagrangian weight rho per local coarse DOF (cofs)
   int npin = 0;
-  double *zw = nullptr, *zl = nullptr, *cpin = nullptr, *pdot = nullptr;
+  double* pen = nullptr;
   int factor_tc = 1;          // bucket 0 on the tensor cores (1) or the CUDA cores (0), tuned
   int negate_sub = -1;        // test hook: subdomain whose local matrix gets a negated pivot (-1: none)
   int negate_neumann = 1;     // ... in its Neumann (1) or Dirichlet (0) matrix
@@ -110,8 +111,8 @@ void set_wait_report_tries(long long tries);
 // shared-memory bytes of the apply's per-subdomain kernels for bucket sizes
 // bs, ring depth nb and local element size es (the largest over the kernels)
 size_t apply_smem(const BucketSizes& bs, int nb, int es);
-void launch_piece_alpha(const MeshDev& m, const double* alpha, const int* plo, const int* phi, int npx, int npy,
-                        int npz, double* pw, cudaStream_t st);
+void launch_piece_alpha(const double* alpha, const long long* pe_off, const int* pe, int np, double* pw,
+                        cudaStream_t st);
 
 // coarse.cu
 void launch_coarse_assemble(const LocalLaunch& L, const int* color_subs, const int* color_count_host,
@@ -120,11 +121,14 @@ void launch_coarse_gather(const int* ptr, const int2* ent, const double* rcl, do
 
 // coarse_mf.cu: multifrontal FP64 Cholesky of the coarse matrix in a nested-
 // dissection order over the subdomain grid.
+// Coarse objects by position at subdomain granularity: a "cell" has doubled
+// subdomain coordinates per axis, 2s + 1 inside slab s, 2s on the cut plane
+// between slabs s - 1 and s (0 and 2 nsub: the domain boundary); an object's
+// cell follows from the subdomains that share it.
 struct CoarseGeom {
-  int nitem[3];
   int nsub[3];
-  std::vector<int> objid;                       // item tuple (x fastest) -> coarse id or -1
-  std::vector<int> slab_item_lo[3], slab_item_hi[3];  // item of each slab's first / last node
+  std::vector<int> cell_ptr;   // CSR over cells (x fastest, (2 nsub + 1) per axis)
+  std::vector<int> cell_obj;   // coarse ids of each cell, ascending
 };
 
 struct MFPlan {

@@ -65,13 +65,11 @@ __device__ inline double box_entry(const MeshDev& m, const double* __restrict__ 
 }
 
 // Local Neumann node fixed to zero in A_rr: on the Dirichlet boundary or a
-// primal point value (box-surface node at Theta-hat points on all three axes,
-// when the selection has vertices).
+// primal point value (a selected one-node vertex object, eliminated).
 __device__ inline bool neumann_fixed(const MeshDev& m, const SubDesc& s, int ix, int iy, int iz) {
   int gx = s.e0[0] + ix, gy = s.e0[1] + iy, gz = s.e0[2] + iz;
   if (on_dirichlet(m, gx, gy, gz)) return true;
-  bool surf = ix == 0 || iy == 0 || iz == 0 || ix == s.w[0] || iy == s.w[1] || iz == s.w[2];
-  return m.vert_primal && surf && m.ax[0].hat[gx] && m.ax[1].hat[gy] && m.ax[2].hat[gz];
+  return m.vfix[nodeid(m.NX, m.NY, gx, gy, gz)] != 0;
 }
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -91,15 +89,44 @@ __device__ inline T warp_sum(T v) {
 // (dense Q x Q) and the coupling B_k = A_{k,k-1} to slot gz+k-1 as its nine
 // stencil diagonals: Bd[o][i] = B_k[i][i + dx + dy gx], o = 3 (dy+1) + dx+1
 // (zero where the neighbour is off the plane).
-// Weight d of the rank-one pin of a floating subdomain (see k_pin_zeta): the
-// diagonal entry of local node 0 spread over the Q nodes of local plane 0.
-__device__ inline double pin_weight(const MeshDev& m, const double* alpha, const SubDesc& s, int Q) {
-  return box_entry(m, alpha, s, s.e0[0], s.e0[1], s.e0[2], 0, 0, 0) / Q;
+// Pinned floating subdomains (selections without point values: the local
+// Neumann matrix A has the constants as kernel).  The factor holds
+// A~ = A + sum_k rho_k c_k^T c_k over the constraint rows c_k (averages)
+// whose nodes lie in one z-plane of the box, rho_k = the sum of A's diagonal
+// over the row's nodes; each term stays inside one diagonal plane block.
+// Every constrained problem prescribes C w, so c_k w is known and
+// [A~ C^T; C 0] has the same w as [A C^T; C 0] (an augmented Lagrangian):
+// the constrained solves and Phi need no correction, and only the local
+// coarse matrix changes, Phi^T A Phi = S~_c^{-1} - diag(rho).  pen holds
+// rho_k per local coarse DOF (0 for rows not penalised and in subdomains not
+// pinned); computed here, one CTA per subdomain, a thread per row.
+__global__ void k_pin_penalty(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha,
+                              const LocalCoarse* __restrict__ lc, const int* __restrict__ lcn,
+                              double* __restrict__ pen) {
+  const SubDesc s = subs[blockIdx.x];
+  const int px = s.w[0] + 1, py = s.w[1] + 1, Q = px * py;
+  for (int j = threadIdx.x; j < s.nc; j += blockDim.x) {
+    const LocalCoarse c = lc[s.cofs + j];
+    double rho = 0.0;
+    if (s.pin && j >= s.nv) {
+      const int z0 = lcn[c.off] / Q;
+      bool one_plane = true;
+      for (int q = 0; q < c.count; ++q) {
+        const int l = lcn[c.off + q];
+        one_plane = one_plane && l / Q == z0;
+        const int ix = l % px, iy = (l / px) % py, iz = l / Q;
+        rho += box_entry(m, alpha, s, s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz, 0, 0, 0);
+      }
+      if (!one_plane) rho = 0.0;
+    }
+    pen[s.cofs + j] = rho;
+  }
 }
 
 template <typename T>
 __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha,
-                           T* __restrict__ fac, int neumann) {
+                           T* __restrict__ fac, int neumann, const LocalCoarse* __restrict__ lc,
+                           const int* __restrict__ own, const double* __restrict__ pen) {
   const SubDesc s = subs[blockIdx.x];
   const Grid g = grid_of(s, neumann);
   const int k = blockIdx.y;
@@ -132,8 +159,14 @@ __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const do
       else v = box_entry(m, alpha, s, s.e0[0] + g.off + ax, s.e0[1] + g.off + ay, s.e0[2] + g.off + k,
                          dx, dy, dz);
     }
-    // pinned floating subdomain: A + d w w^T with w the indicator of local plane 0
-    if (neumann && s.pin && k == 0 && e < QQ) v += pin_weight(m, alpha, s, Q);
+    // pinned floating subdomain: rho_k c_k^T c_k of the rows of this plane (see k_pin_penalty)
+    if (neumann && s.pin && e < QQ) {
+      const int ja = own[s.offVec + (long long)k * Q + a], jb = own[s.offVec + (long long)k * Q + (e % Q)];
+      if (ja >= 0 && ja == jb) {
+        const double cnt = (double)lc[s.cofs + ja].count;
+        v += pen[s.cofs + ja] / (cnt * cnt);
+      }
+    }
     if (e < QQ) base[(long long)k * SS + e] = (T)v;
     else base[(long long)(g.gz + k - 1) * SS + (e - QQ)] = (T)v;
   }
@@ -841,10 +874,12 @@ k_btsolve_multi_tc(const SubDesc* __restrict__ subs, const float* __restrict__ f
 // coarse basis
 // ---------------------------------------------------------------------------
 
-// F = [-A_rv | C_r^T] on the local Neumann grid (rows), into Y.
+// F = [-A_rv | C_r^T] on the local Neumann grid (rows), into Y.  own: per
+// local Neumann node (at the subdomain's vector offset) the local index of
+// the average containing it, -1 if none.
 template <typename T>
 __global__ void k_coarse_rhs(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha,
-                             const LocalCoarse* __restrict__ lc, T* __restrict__ Y) {
+                             const LocalCoarse* __restrict__ lc, const int* __restrict__ own, T* __restrict__ Y) {
   const SubDesc s = subs[blockIdx.x];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const long long nN = (long long)px * py * pz;
@@ -857,11 +892,10 @@ __global__ void k_coarse_rhs(const SubDesc* __restrict__ subs, MeshDev m, const 
     if (!neumann_fixed(m, s, ix, iy, iz)) {
       const LocalCoarse c = lc[s.cofs + j];
       if (j < s.nv) {
-        int dx = c.lo[0] - ix, dy = c.lo[1] - iy, dz = c.lo[2] - iz;
+        int dx = c.v[0] - ix, dy = c.v[1] - iy, dz = c.v[2] - iz;
         if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1)
           v = -box_entry(m, alpha, s, s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz, dx, dy, dz);
-      } else if (ix >= c.lo[0] && ix <= c.hi[0] && iy >= c.lo[1] && iy <= c.hi[1] && iz >= c.lo[2] &&
-                 iz <= c.hi[2]) {
+      } else if (own[s.offVec + r] == j) {
         v = 1.0 / c.count;
       }
     }
@@ -872,18 +906,14 @@ __global__ void k_coarse_rhs(const SubDesc* __restrict__ subs, MeshDev m, const 
 // G = C_r Y (na x nc): means of Y's columns over the averaging objects.
 template <typename T>
 __global__ void k_constraint_means(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict__ lc,
-                                   const T* __restrict__ Y, T* __restrict__ G) {
+                                   const int* __restrict__ lcn, const T* __restrict__ Y, T* __restrict__ G) {
   const SubDesc s = subs[blockIdx.x];
-  const int px = s.w[0] + 1, py = s.w[1] + 1;
   const T* Yb = Y + s.offY;
   for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < s.na * s.nc; e += gridDim.y * blockDim.x) {
     int a = e / s.nc, j = e % s.nc;
     const LocalCoarse c = lc[s.cofs + s.nv + a];
     T sum = T(0);
-    for (int iz = c.lo[2]; iz <= c.hi[2]; ++iz)
-      for (int iy = c.lo[1]; iy <= c.hi[1]; ++iy)
-        for (int ix = c.lo[0]; ix <= c.hi[0]; ++ix)
-          sum += Yb[((long long)ix + px * (iy + (long long)py * iz)) * s.nc + j];
+    for (int q = 0; q < c.count; ++q) sum += Yb[(long long)lcn[c.off + q] * s.nc + j];
     G[s.offG + e] = sum / T(c.count);
   }
 }
@@ -956,7 +986,7 @@ __global__ void k_phi_surface(const SubDesc* __restrict__ subs, const LocalCoars
     if (j < s.nv) {
       const LocalCoarse c = lc[s.cofs + j];
       v = Y[s.offY + node * s.nc + j];
-      if (c.lo[0] == ix && c.lo[1] == iy && c.lo[2] == iz) v = T(1);
+      if (c.v[0] == ix && c.v[1] == iy && c.v[2] == iz) v = T(1);
     } else {
       v = PA[s.offPA + node * s.na + (j - s.nv)];
     }
@@ -969,8 +999,8 @@ template <typename T>
 __global__ void k_local_coarse_matrix(const SubDesc* __restrict__ subs, MeshDev m,
                                       const double* __restrict__ alpha, const LocalCoarse* __restrict__ lc,
                                       const T* __restrict__ Y, const T* __restrict__ Lv,
-                                      const T* __restrict__ Sc, const double* __restrict__ zl,
-                                      const double* __restrict__ cpin, double* __restrict__ Ac) {
+                                      const T* __restrict__ Sc, const double* __restrict__ pen,
+                                      double* __restrict__ Ac) {
   const SubDesc s = subs[blockIdx.x];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
   const int nc = s.nc, nv = s.nv;
@@ -989,14 +1019,14 @@ __global__ void k_local_coarse_matrix(const SubDesc* __restrict__ subs, MeshDev 
         for (int dz = -1; dz <= 1; ++dz)
           for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
-              int bx = vr.lo[0] + dx, by = vr.lo[1] + dy, bz = vr.lo[2] + dz;
+              int bx = vr.v[0] + dx, by = vr.v[1] + dy, bz = vr.v[2] + dz;
               if (bx < 0 || by < 0 || bz < 0 || bx >= px || by >= py || bz >= pz) continue;
               if (on_dirichlet(m, s.e0[0] + bx, s.e0[1] + by, s.e0[2] + bz)) continue;
               double phi;
-              if (bx == vc.lo[0] && by == vc.lo[1] && bz == vc.lo[2]) phi = 1.0;
+              if (bx == vc.v[0] && by == vc.v[1] && bz == vc.v[2]) phi = 1.0;
               else phi = (double)Y[s.offY + ((long long)bx + px * (by + (long long)py * bz)) * nc + col];
               if (phi == 0.0) continue;
-              acc += box_entry(m, alpha, s, s.e0[0] + vr.lo[0], s.e0[1] + vr.lo[1], s.e0[2] + vr.lo[2],
+              acc += box_entry(m, alpha, s, s.e0[0] + vr.v[0], s.e0[1] + vr.v[1], s.e0[2] + vr.v[2],
                                dx, dy, dz) * phi;
             }
         both[t] = acc;
@@ -1005,7 +1035,7 @@ __global__ void k_local_coarse_matrix(const SubDesc* __restrict__ subs, MeshDev 
     } else if (r >= nv && c >= nv) {
       int a = r - nv, b = c - nv;
       v = 0.5 * ((double)Sc[s.offSc + (long long)a * s.na + b] + (double)Sc[s.offSc + (long long)b * s.na + a]);
-      if (s.pin) v -= cpin[s.id] * zl[s.cofs + r] * zl[s.cofs + c];   // exact problem of a pinned subdomain
+      if (s.pin && r == c) v -= pen[s.cofs + r];   // Phi^T A Phi of a pinned subdomain (k_pin_penalty)
     } else if (r >= nv) {
       v = -(double)Lv[s.offL + (long long)(r - nv) * nv + c];
     } else {
@@ -1015,57 +1045,49 @@ __global__ void k_local_coarse_matrix(const SubDesc* __restrict__ subs, MeshDev 
   }
 }
 
-// Interface weights of eq. (W) (pw == nullptr) or Remark 1 (pw = mean alpha
-// per sub-subdomain) on every box-surface node of every subdomain.
+// Weights on the box surface of subdomain i (eq. (W), Remark 1): over the
+// sub-subdomains (pieces) of the elements around a node, the sum of their
+// weights inside Omega_i over the sum of all (pw = NULL: every piece counts
+// 1, the cardinality rule).  The pieces around a node are the distinct
+// labels of its up to eight elements, visited z, y, x.
 __global__ void k_weights(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ pw,
                           double* __restrict__ delta) {
   const SubDesc s = subs[blockIdx.x];
   const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
-  const int npx = m.ax[0].piece[m.nx - 1] + 1, npy = m.ax[1].piece[m.ny - 1] + 1;
+  int slabS[3];
+  for (int d = 0; d < 3; ++d) slabS[d] = m.ax[d].slab[s.e0[d]];
   for (int b = blockIdx.y * blockDim.x + threadIdx.x; b < s.nB; b += gridDim.y * blockDim.x) {
     int ix, iy, iz;
     surf_coords(b, px, py, pz, ix, iy, iz);
-    int gc[3] = {s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz};
+    const int gc[3] = {s.e0[0] + ix, s.e0[1] + iy, s.e0[2] + iz};
     if (on_dirichlet(m, gc[0], gc[1], gc[2])) { delta[s.offB + b] = 0.0; continue; }
-    int pc[3][2], inside[3][2], np[3];
-    for (int d = 0; d < 3; ++d) {
-      const AxisTables& A = m.ax[d];
-      int eL = gc[d] - 1, eR = gc[d];   // both inside the mesh: node not on the boundary
-      int slabS = A.slab[s.e0[d]];
-      if (A.piece[eL] == A.piece[eR]) {
-        np[d] = 1; pc[d][0] = A.piece[eR]; inside[d][0] = (A.slab[eR] == slabS);
-      } else {
-        np[d] = 2;
-        pc[d][0] = A.piece[eL]; inside[d][0] = (A.slab[eL] == slabS);
-        pc[d][1] = A.piece[eR]; inside[d][1] = (A.slab[eR] == slabS);
-      }
-    }
+    int seen[8], n = 0;
     double num = 0.0, den = 0.0;
-    for (int c = 0; c < np[2]; ++c)
-      for (int bb = 0; bb < np[1]; ++bb)
-        for (int a = 0; a < np[0]; ++a) {
-          double w = pw ? pw[pc[0][a] + (long long)npx * (pc[1][bb] + (long long)npy * pc[2][c])] : 1.0;
+    for (int dz = -1; dz <= 0; ++dz)
+      for (int dy = -1; dy <= 0; ++dy)
+        for (int dx = -1; dx <= 0; ++dx) {
+          const int ex = gc[0] + dx, ey = gc[1] + dy, ez = gc[2] + dz;   // inside: node off the boundary
+          const int p = m.epiece[ex + (long long)m.nx * (ey + (long long)m.ny * ez)];
+          bool dup = false;
+          for (int q = 0; q < n; ++q) dup = dup || seen[q] == p;
+          if (dup) continue;
+          seen[n++] = p;
+          const double w = pw ? pw[p] : 1.0;
           den += w;
-          if (inside[0][a] && inside[1][bb] && inside[2][c]) num += w;
+          if (m.ax[0].slab[ex] == slabS[0] && m.ax[1].slab[ey] == slabS[1] && m.ax[2].slab[ez] == slabS[2]) num += w;
         }
     delta[s.offB + b] = num / den;
   }
 }
 
-// Mean alpha of every sub-subdomain (piece), summed in a fixed order.
-__global__ void k_piece_alpha(MeshDev m, const double* __restrict__ alpha, const int* __restrict__ plo,
-                              const int* __restrict__ phi, int npx, int npy, int npz, double* __restrict__ pw) {
-  long long np = (long long)npx * npy * npz;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
-    int a = (int)(p % npx), b = (int)((p / npx) % npy), c = (int)(p / ((long long)npx * npy));
-    // plo/phi: concatenated per-axis piece element ranges (x, then y, then z)
-    int x0 = plo[a], x1 = phi[a], y0 = plo[npx + b], y1 = phi[npx + b], z0 = plo[npx + npy + c],
-        z1 = phi[npx + npy + c];
+// Mean alpha of every sub-subdomain (piece): its elements listed in
+// ascending order (pe_off, pe), summed in that order.
+__global__ void k_piece_alpha(const double* __restrict__ alpha, const long long* __restrict__ pe_off,
+                              const int* __restrict__ pe, int np, double* __restrict__ pw) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     double sum = 0.0;
-    for (int k = z0; k < z1; ++k)
-      for (int j = y0; j < y1; ++j)
-        for (int i = x0; i < x1; ++i) sum += alpha[(long long)i + (long long)m.nx * (j + (long long)m.ny * k)];
-    pw[p] = sum / ((double)(x1 - x0) * (y1 - y0) * (z1 - z0));
+    for (long long q = pe_off[p]; q < pe_off[p + 1]; ++q) sum += alpha[pe[q]];
+    pw[p] = sum / (double)(pe_off[p + 1] - pe_off[p]);
   }
 }
 
@@ -1377,44 +1399,10 @@ __device__ inline void neumann_restrict(const SubDesc& s, const MeshDev& m, cons
 // restriction r_i = D_i R_i (r - t), in the local precision: columns of Phi
 // accumulate over streamed rows, the rows split between the CTAs of the
 // cluster and their partial sums added in rank order.
-// Block sum in FP64, fixed order (every thread calls; ends with a barrier).
-__device__ inline double block_sum_f64(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  __syncthreads();
-  return s;
-}
-
-// Pinned subdomain (see k_pin_zeta): s_i = zeta_w . r_i into pdot, and
-// rc_i += c zeta_l s_i.  Every thread of the CTA calls, after rc_i is written
-// and a barrier; red (32 doubles of shared memory) is free scratch.
-struct PinData {
-  const double *zw, *zl, *cpin;
-  double* pdot;
-};
-
-template <typename T>
-__device__ inline void pin_rhs_impl(const SubDesc& s, const T* rg, const PinData& P, double* rcl, double* red) {
-  double a = 0.0;
-  for (int b = threadIdx.x; b < s.nB; b += blockDim.x) a += P.zw[s.offB + b] * (double)rg[b];
-  const double si = block_sum_f64(a, red);
-  if (threadIdx.x == 0) P.pdot[s.id] = si;
-  const double cf = P.cpin[s.id] * si;
-  for (int j = threadIdx.x; j < s.nc; j += blockDim.x) rcl[s.cofs + j] += cf * P.zl[s.cofs + j];
-  __syncthreads();
-}
-
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_neumann_rhs(ApplyBucket B, MeshDev m, const T* __restrict__ Phi, const double* __restrict__ delta,
-              const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ rcl, PinData P0,
-              int* err) {
+              const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ rcl, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
@@ -1448,10 +1436,6 @@ k_neumann_rhs(ApplyBucket B, MeshDev m, const T* __restrict__ Phi, const double*
   ring_run(ring, nch, src, use, err);
   if (nrank == 1) {
     col_finish<T>(L, acc, part, [&](int cc, T sum) { rcl[s.cofs + cc] = (double)sum; });
-    if (s.pin) {
-      __syncthreads();   // col_finish's reads of part are done
-      pin_rhs_impl<T>(s, rg, P0, rcl, reinterpret_cast<double*>(part));
-    }
   } else {
     col_finish<T>(L, acc, part, [&](int cc, T sum) { pb[cc] = sum; });
     cluster.sync();
@@ -1461,10 +1445,6 @@ k_neumann_rhs(ApplyBucket B, MeshDev m, const T* __restrict__ Phi, const double*
         for (int q = 0; q < nrank; ++q) sum += cluster.map_shared_rank(pb, q)[c];
         rcl[s.cofs + c] = (double)sum;
       }
-    if (s.pin) {
-      __syncthreads();
-      if (rank == 0) pin_rhs_impl<T>(s, rg, P0, rcl, reinterpret_cast<double*>(part));
-    }
     cluster.sync();   // the peer's reads of this CTA's partial sums are done
   }
   }
@@ -1507,9 +1487,9 @@ k_neumann_solve(ApplyBucket B, MeshDev m, const T* __restrict__ fac, const doubl
 // accumulation over the rows of Phi_i^T.
 template <typename T>
 __global__ void __launch_bounds__(APPLY_THREADS)
-k_neumann_finish(ApplyBucket B, const LocalCoarse* __restrict__ lc, const T* __restrict__ PhiT,
-                 const T* __restrict__ vloc, const double* __restrict__ uc, double* __restrict__ vgam, PinData P0,
-                 int* err) {
+k_neumann_finish(ApplyBucket B, const LocalCoarse* __restrict__ lc, const int* __restrict__ lcn,
+                 const T* __restrict__ PhiT, const T* __restrict__ vloc, const double* __restrict__ uc,
+                 double* __restrict__ vgam, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
   Ring ring = ring_at(smraw, B.nb);
   T* part = reinterpret_cast<T*>(smraw + ring_bytes(B.nb));
@@ -1525,28 +1505,16 @@ k_neumann_finish(ApplyBucket B, const LocalCoarse* __restrict__ lc, const T* __r
     double val = uc[c.gid];
     if (j >= s.nv) {
       double sum = 0.0;
-      for (int iz = c.lo[2]; iz <= c.hi[2]; ++iz)
-        for (int iy = c.lo[1]; iy <= c.hi[1]; ++iy)
-          for (int ix = c.lo[0]; ix <= c.hi[0]; ++ix) sum += (double)y[ix + px * (iy + py * iz)];
+      for (int q = 0; q < c.count; ++q) sum += (double)y[lcn[c.off + q]];
       val -= sum / c.count;
     }
     ut[j] = (T)val;
   }
   __syncthreads();
-  // pinned subdomain: v_i += c zeta_w (zeta_l . u_c,i + zeta_w . r_i)
-  double pin_cf = 0.0;
-  if (s.pin) {
-    double a = 0.0;
-    for (int j = threadIdx.x; j < s.nc; j += blockDim.x) a += P0.zl[s.cofs + j] * uc[lc[s.cofs + j].gid];
-    // part is free until col_finish (the loop-top barrier ended its last use)
-    pin_cf = P0.cpin[s.id] * (block_sum_f64(a, reinterpret_cast<double*>(part)) + P0.pdot[s.id]);
-  }
   auto out = [&](int b, T sum) {
     int ix, iy, iz;
     surf_coords(b, px, py, pz, ix, iy, iz);
-    double vb = (double)sum + (double)y[ix + px * (iy + py * iz)];
-    if (s.pin) vb += pin_cf * P0.zw[s.offB + b];
-    vgam[s.offB + b] = vb;
+    vgam[s.offB + b] = (double)sum + (double)y[ix + px * (iy + py * iz)];
   };
   const ColLayout L = col_layout(s.nB);
   T acc[4] = {T(0), T(0), T(0), T(0)};
@@ -1566,73 +1534,6 @@ k_neumann_finish(ApplyBucket B, const LocalCoarse* __restrict__ lc, const T* __r
     ring_run(ring, nch, src, use, err);
   }
   col_finish<T>(L, acc, part, out);
-  }
-}
-
-// Pinned subdomains (selections without vertices: the local Neumann matrix A
-// of a floating subdomain has the constants as kernel).  The factor holds
-// A~ = A + d w w^T, w the indicator of local plane 0 and d = A_00 / Q: spread
-// over a plane, the pin keeps cond(A~) near that of a Dirichlet problem
-// (pinning one node leaves the constants' Rayleigh quotient at A_00 / n and
-// costs FP32 three digits).  The exact constrained problem K = [A C^T; C 0]
-// = K~ - d u u^T (u = [w; 0]) follows from the pinned one by Sherman-Morrison:
-// K^{-1} = K~^{-1} + c zeta zeta^T with zeta = K~^{-1} u and c = d / (1 -
-// d u^T zeta).  Here zeta from the pinned factor: y = A~^{-1} w, zeta_l =
-// S_c^{-1} C y, zeta_w = y - Phi~ C y (Phi~ = X S_c^{-1}, every local coarse
-// DOF an average); zeta_w is kept on the box surface, which holds plane 0.
-// Then Phi = Phi~ + c zeta_w zeta_l^T, A_c^(i) = S_c^{-1} - c zeta_l
-// zeta_l^T, and the apply adds c zeta_l (zeta_w . r_i) to Phi^T r_i and
-// c zeta_w (zeta_l . u_c,i + zeta_w . r_i) to v_i.  One CTA per subdomain.
-template <typename T>
-__global__ void __launch_bounds__(APPLY_THREADS)
-k_pin_zeta(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha, const T* __restrict__ fac,
-           const T* __restrict__ Phi, const T* __restrict__ Sc, const LocalCoarse* __restrict__ lc,
-           double* __restrict__ zw, double* __restrict__ zl, double* __restrict__ cpin, int* err) {
-  extern __shared__ __align__(128) unsigned char smraw[];
-  const SubDesc s = subs[blockIdx.x];
-  if (!s.pin) return;
-  const int px = s.w[0] + 1, py = s.w[1] + 1, pz = s.w[2] + 1;
-  const int Q = px * py, n = Q * pz, nc = s.nc;
-  Ring ring = ring_at(smraw, NBUF);
-  T* part = reinterpret_cast<T*>(smraw + ring_bytes(NBUF));
-  T* v = part + APPLY_THREADS;
-  T* tq = v + n;
-  T* pb = tq + Q;
-  double* cy = reinterpret_cast<double*>(smraw + ring_bytes(NBUF) +
-                                         (((size_t)(APPLY_THREADS + n + 3 * Q) * sizeof(T) + 15) & ~(size_t)15));
-  ring_init(ring);
-  double* red = cy + nc;   // 32 doubles of reduction scratch
-  for (int l = threadIdx.x; l < n; l += blockDim.x) v[l] = (l < Q) ? T(1) : T(0);
-  __syncthreads();
-  sweep_stream<T>(ring, fac + s.offN, px, py, pz, v, tq, part, pb, err);   // v = A~^{-1} w
-  // C y: means over the averaging objects
-  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-    const LocalCoarse c = lc[s.cofs + j];
-    double sum = 0.0;
-    for (int iz = c.lo[2]; iz <= c.hi[2]; ++iz)
-      for (int iy = c.lo[1]; iy <= c.hi[1]; ++iy)
-        for (int ix = c.lo[0]; ix <= c.hi[0]; ++ix) sum += (double)v[ix + px * (iy + py * iz)];
-    cy[j] = sum / c.count;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-    double a = 0.0;
-    for (int q = 0; q < nc; ++q) a += (double)Sc[s.offSc + (long long)j * nc + q] * cy[q];
-    zl[s.cofs + j] = a;
-  }
-  double wz = 0.0;   // w . zeta_w: the surface nodes of plane 0
-  for (int b = threadIdx.x; b < s.nB; b += blockDim.x) {
-    int ix, iy, iz;
-    surf_coords(b, px, py, pz, ix, iy, iz);
-    double a = (double)v[ix + px * (iy + py * iz)];
-    for (int q = 0; q < nc; ++q) a -= (double)Phi[s.offPhi + (long long)b * nc + q] * cy[q];
-    zw[s.offB + b] = a;
-    if (iz == 0) wz += a;
-  }
-  wz = block_sum_f64(wz, red);
-  if (threadIdx.x == 0) {
-    const double d = pin_weight(m, alpha, s, Q);
-    cpin[s.id] = d / (1.0 - d * wz);
   }
 }
 
@@ -1662,10 +1563,14 @@ void launch_assemble(const LocalLaunch& L, cudaStream_t st) {
   T* facD = (T*)L.facD; T* facN = (T*)L.facN;
   // local assembly (Dirichlet and Neumann plane blocks)
   if (L.maxQD > 0) {
-    k_assemble<T><<<dim3(S, L.maxNzD, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facD, 0);
+    k_assemble<T><<<dim3(S, L.maxNzD, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facD, 0, L.lc, L.own, L.pen);
     BDDC_COUNT(1);
   }
-  k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1);
+  if (L.npin) {
+    k_pin_penalty<<<S, BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, L.lcn, L.pen);
+    BDDC_COUNT(1);
+  }
+  k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1, L.lc, L.own, L.pen);
   BDDC_COUNT(1);
   if (L.negate_sub >= 0) {
     k_debug_negate<T><<<1, 1, 0, st>>>(L.subs, L.negate_neumann ? facN : facD, L.negate_sub, L.negate_neumann);
@@ -1708,7 +1613,7 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
   // coarse basis
   T* Y = (T*)L.Y; T* G = (T*)L.G; T* Lv = (T*)L.Lv; T* PA = (T*)L.PA; T* Sc = (T*)L.Sc; T* Phi = (T*)L.Phi;
   if (L.maxNc > 0) {  // one subdomain has no interface and no coarse space
-    k_coarse_rhs<T><<<dim3(S, 64), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y);
+    k_coarse_rhs<T><<<dim3(S, 64), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, L.own, Y);
     if (std::is_same<T, float>::value && L.tc) {
       k_tc_pack<<<dim3(S, L.maxNzN, tc_kchunks(L.maxQN)), BDDC_THREADS, 0, st>>>(L.subs, (const float*)L.facN,
                                                                                (float*)L.tc);
@@ -1722,21 +1627,15 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
       k_btsolve_multi<T><<<dim3(S, nch), BDDC_THREADS, sm, st>>>(L.subs_lpt, facN, Y, (T*)L.mscratch,
                                                                    L.mscratch_stride);
     }
-    k_constraint_means<T><<<dim3(S, 16), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, G);
+    k_constraint_means<T><<<dim3(S, 16), BDDC_THREADS, 0, st>>>(L.subs, L.lc, L.lcn, Y, G);
     k_schur<T><<<S, BDDC_THREADS, sm, st>>>(L.subs, G, Sc, Lv, W, L.err);
     int nrc = (L.maxNN + RB - 1) / RB;
     k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 0);
     k_phi_rows<T><<<dim3(S, nrc), BDDC_THREADS, sm, st>>>(L.subs, Y, Lv, Sc, PA, 1);
     k_phi_surface<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.lc, Y, PA, Phi);
     k_transpose<T><<<dim3(S, 1, 64), 256, 0, st>>>(L.subs, Phi, (T*)L.PhiT);
-    if (L.npin) {
-      const size_t smz = ring_bytes(NBUF) + (((size_t)APPLY_THREADS + L.maxNN + 3 * (size_t)L.maxQN) * sizeof(T) + 15) /
-                                                16 * 16 + sizeof(double) * (L.maxNc + 32);
-      k_pin_zeta<T><<<S, APPLY_THREADS, smz, st>>>(L.subs, L.m, L.alpha, facN, Phi, Sc, L.lc, L.zw, L.zl, L.cpin, L.err);
-      BDDC_COUNT(1);
-    }
-    k_local_coarse_matrix<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y, Lv, Sc, L.zl,
-                                                                     L.cpin, L.Ac);
+    k_local_coarse_matrix<T><<<dim3(S, 32), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, Y, Lv, Sc, L.pen,
+                                                                     L.Ac);
     BDDC_COUNT(9);
   }
   if (ev) cudaEventRecord(ev[2], st);
@@ -1756,7 +1655,6 @@ void configure_local_kernels() {
   cudaFuncSetAttribute(k_neumann_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_neumann_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   cudaFuncSetAttribute(k_neumann_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  cudaFuncSetAttribute(k_pin_zeta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st) {
@@ -1764,12 +1662,11 @@ void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st
   k_weights<<<dim3(L.nsub, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, piece_w, L.delta);
 }
 
-void launch_piece_alpha(const MeshDev& m, const double* alpha, const int* plo, const int* phi, int npx, int npy,
-                        int npz, double* pw, cudaStream_t st) {
-  long long np = (long long)npx * npy * npz;
-  int blocks = (int)std::min<long long>((np + 255) / 256, 4096);
+void launch_piece_alpha(const double* alpha, const long long* pe_off, const int* pe, int np, double* pw,
+                        cudaStream_t st) {
+  int blocks = std::min((np + 255) / 256, 4096);
   BDDC_COUNT(1);
-  k_piece_alpha<<<blocks, 256, 0, st>>>(m, alpha, plo, phi, npx, npy, npz, pw);
+  k_piece_alpha<<<blocks, 256, 0, st>>>(alpha, pe_off, pe, np, pw);
 }
 
 // CTAs of `kern` (APPLY_THREADS threads, smem bytes) resident on the current
@@ -1841,7 +1738,7 @@ void launch_neumann_rhs(const LocalLaunch& L, const double* r, const double* t, 
                       sizeof(T) * ((size_t)APPLY_THREADS + L.bsize[b].maxNB + 1 + L.bsize[b].maxNc + 2);
     BDDC_COUNT(1);
     launch_clustered(k_neumann_rhs<T>, L.bucket[b], L.bcluster[b], sm, st, L.bucket[b], L.m, (const T*)L.Phi, L.delta,
-                     r, t, L.rcl, PinData{L.zw, L.zl, L.cpin, L.pdot}, L.err);
+                     r, t, L.rcl, L.err);
   }
 }
 
@@ -1863,8 +1760,8 @@ void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t 
     if (L.bucket[b].count == 0) continue;
     const size_t sm = ring_bytes(L.bucket[b].nb) + sizeof(T) * ((size_t)APPLY_THREADS + L.bsize[b].maxNc + 1);
     BDDC_COUNT(1);
-    launch_clustered(k_neumann_finish<T>, L.bucket[b], 1, sm, st, L.bucket[b], L.lc, (const T*)L.PhiT,
-                     (const T*)L.vloc, uc, L.vgam, PinData{L.zw, L.zl, L.cpin, L.pdot}, L.err);
+    launch_clustered(k_neumann_finish<T>, L.bucket[b], 1, sm, st, L.bucket[b], L.lc, L.lcn, (const T*)L.PhiT,
+                     (const T*)L.vloc, uc, L.vgam, L.err);
   }
 }
 

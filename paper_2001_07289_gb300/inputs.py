@@ -212,6 +212,7 @@ class Problem:
     rtol: float = 1e-10
     precision: str = "fp64"      # "fp64" or "mixed"
     selection: str = "vef"
+    piece: Optional[np.ndarray] = None   # per-element sub-subdomain labels (None: boxes of size L)
 
     @property
     def n_nodes(self) -> int:
@@ -224,6 +225,64 @@ class Problem:
     @property
     def n_elems(self) -> int:
         return self.nx * self.ny * self.nz
+
+
+def channel_mask(nx: int, ny: int, nz: int, per_axis: int, width: int, seed: int) -> np.ndarray:
+    """Per-element indicator (x fastest) of a system of straight channels:
+    per_axis bars of width x width elements running through the whole mesh
+    along each axis, at seeded transverse positions (the channels geometry of
+    Section 5.2 is only in a missing figure; this one is synthetic)."""
+    n = (nx, ny, nz)
+    mask = np.zeros((nz, ny, nx), dtype=bool)
+    u = uniform01(seed, 6 * per_axis)
+    q = 0
+    for d in range(3):
+        t1, t2 = (d + 1) % 3, (d + 2) % 3
+        for _ in range(per_axis):
+            a = 1 + int(u[q] * (n[t1] - width - 1))
+            b = 1 + int(u[q + 1] * (n[t2] - width - 1))
+            q += 2
+            sl = [slice(None)] * 3            # array axes are (z, y, x)
+            sl[2 - t1] = slice(a, a + width)
+            sl[2 - t2] = slice(b, b + width)
+            mask[tuple(sl)] = True
+    return mask.reshape(-1)
+
+
+def material_pieces(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], mask: np.ndarray) -> np.ndarray:
+    """Per-element sub-subdomain labels splitting every subdomain of the box
+    partition into its background and its channel part (Section 5.2: two
+    sub-subdomains per subdomain), numbered densely in the order of
+    2 subdomain + indicator."""
+    def slab(n, c):
+        return np.searchsorted(np.asarray(c, dtype=np.int64), np.arange(n), side="right")
+    sx, sy, sz = slab(nx, cuts[0]), slab(ny, cuts[1]), slab(nz, cuts[2])
+    nsx, nsy = len(cuts[0]) + 1, len(cuts[1]) + 1
+    sub = sx[None, None, :] + nsx * (sy[None, :, None] + nsy * sz[:, None, None])
+    key = 2 * sub.reshape(-1) + np.asarray(mask, dtype=np.int64).reshape(-1)
+    return np.unique(key, return_inverse=True)[1].reshape(-1).astype(np.int64)
+
+
+def channels_problem(n: int = 40, parts: int = 4, ell: float = 4.0, per_axis: int = 3, width: int = 2,
+                     seed: int = 0, sub_partition: str = "material", selection: str = "f", **kw) -> Problem:
+    """The channels experiment of Section 5.2 on synthetic channels: n^3
+    hexahedra, parts^3 box subdomains, alpha = 10^ell in the channels and 1
+    elsewhere, f = 1, rho-weights (Remark 1), PCG to rtol 1e-6.
+    sub_partition "material": Theta-hat = {background, channels} per
+    subdomain (BDDC-SO); "none": Theta-hat = Theta (standard BDDC)."""
+    mask = channel_mask(n, n, n, per_axis, width, BASE_SEED + 100 + seed)
+    alpha = np.where(mask, 10.0 ** ell, 1.0)
+    cuts = [uniform_cuts(n, parts)] * 3
+    if sub_partition == "material":
+        piece, L = material_pieces(n, n, n, cuts, mask), n
+    elif sub_partition == "none":
+        piece, L = None, n
+    else:
+        raise ValueError(sub_partition)
+    kw.setdefault("rtol", 1e-6)
+    kw.setdefault("weights", "rho")
+    return box_problem(n, n, n, cuts, L, alpha=alpha, name=f"channels{n}_l{ell:g}", selection=selection,
+                       piece=piece, **kw)
 
 
 def box_problem(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int,

@@ -4,9 +4,9 @@ edges and faces, and vertices only) on the GPU against the oracle built with the
 selection: apply, PCG iterations and solution, for the FP64 and mixed paths.
 
 Without vertices a floating subdomain's local Neumann matrix is singular; the
-library pins one node and corrects the constrained solves exactly (rank-one
-Sherman-Morrison update), so the 12^3 mesh with 3^3 subdomains, whose centre
-box is floating, is in the cases."""
+library factors A + sum rho_k c_k^T c_k over the averages lying in one z-plane
+(an augmented Lagrangian, exact for the constrained problems), so the 12^3
+mesh with 3^3 subdomains, whose centre box is floating, is in the cases."""
 import numpy as np
 import pytest
 
@@ -58,7 +58,7 @@ def test_selection_matches_oracle(name, sel, precision, tol, dit):
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 2e-4)])
 def test_faces_only_coarse_basis_identity(precision, tol):
     """C_i Phi_i = I for the pinned (floating) subdomain with faces only, the
-    basis being the exact saddle-point one after the rank-one correction
+    basis being the exact saddle-point one with the augmented factor
     (checked against the oracle's)."""
     from paper_2001_07289_gb300.bddc import BDDC
     p, ref = _case("floating", "f")
@@ -95,3 +95,13 @@ def test_fewer_constraints_more_iterations():
         pre.close()
     assert it["vef"] <= min(it["ve"], it["vf"], it["f"]), it
     assert it["v"] >= max(it["ve"], it["vf"]), it
+
+
+def test_floating_without_plane_average_refused():
+    """L = 1: every interface node is a vertex object, so faces only select
+    nothing and the floating centre box has no row to pin with."""
+    import paper_2001_07289_gb300.bddc as gb
+    p = inputs.box_problem(12, 12, 12, [[4, 8]] * 3, 1, selection="f")
+    with pytest.raises(gb.BddcError) as e:
+        gb.BDDC.from_problem(p)
+    assert e.value.code == gb.BDDC_ERR_UNSUPPORTED and "z-plane" in str(e.value)
