@@ -14,7 +14,8 @@ n_free * N / time-to-solution.  Extra keys: preconditioner applies/s and MDOF/s
 (100 back-to-back bddc_apply), setup phases, iterations, roofline of the
 dominant phase, the oracle as CPU baseline, and end-to-end numbers through
 bddc_solve_host with host buffers; and (--no-workloads to skip) one timed
-step of each other workload (channels96, jitter128, adjoint64) on both paths.
+step of each other workload (channels96, jitter128, adjoint64) on both paths,
+and Section 5.2's contrast study on the synthetic channels (channels40).
 
 --impl reference times the FP64 CPU oracle (test infrastructure written from
 the paper) on the host cores, on a bounded sample of the same workload.
@@ -219,7 +220,8 @@ def main():
     ap.add_argument("--only-applies", type=int, default=0,
                     help="set up once, then run this many preconditioner applies (for profiler launch lists)")
     ap.add_argument("--no-workloads", action="store_true",
-                    help="skip the one-step lines of the other workloads (channels96, jitter128, adjoint64)")
+                    help="skip the one-step lines of the other workloads (channels96, jitter128, adjoint64, "
+                         "channels40 contrast study)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -395,6 +397,7 @@ def main():
     if not args.no_workloads and args.workload == "poisson48" and world == 1:
         for name in ("channels96", "jitter128", "adjoint64"):
             workloads[name] = run_workload(name, flush, stream)
+        workloads["channels40"] = run_channels(flush, stream)
 
     if rank != 0:
         if world > 1:
@@ -547,6 +550,40 @@ def run_workload(name, flush, stream):
                      "setup_phases_ms": [round(v, 2) for v in info["phase_ms"]], "n_coarse": info["n_coarse"],
                      "precond_apply_ms": round(apply_ms, 4),
                      "apply_mdofs": round(p.n_free * 1e3 / apply_ms / 1e6, 2)}
+    return out
+
+
+def run_channels(flush, stream):
+    """Section 5.2's contrast study on the synthetic channels recipe (40^3, 4^3
+    subdomains, FP64, rho-weights, rtol 1e-6): PCG iterations and one timed
+    step (setup + PCG, L2 flushed, after one warm-up) of BDDC-SO(f) with
+    Theta-hat = {background, channels} per subdomain and of standard
+    BDDC(vef) with Theta-hat = Theta, for contrasts 10^2 .. 10^8."""
+    import torch
+    from paper_2001_07289_gb300 import inputs
+    from paper_2001_07289_gb300.bddc import BDDC
+    out = {"workload": "channels40: 40^3, 4^3 subdomains, 3 bars of 2x2 elements per axis, alpha = 10^ell in the "
+                       "channels, FP64, rho-weights, PCG rtol 1e-6"}
+    for key, sub, sel in (("bddc_so_f", "material", "f"), ("bddc_vef", "none", "vef")):
+        rows = []
+        for ell in (2, 4, 6, 8):
+            p = inputs.channels_problem(40, 4, ell, sub_partition=sub, selection=sel)
+            alpha = torch.from_numpy(p.alpha).cuda()
+            b = torch.from_numpy(p.b).cuda()
+            x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
+            for k in range(2):
+                flush.fill_(5.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pre = BDDC.from_problem(p, alpha=alpha, use_graph=True, maxit=2000)
+                _, st = pre.solve(b, p.rtol, out=x)
+                e1.record(stream)
+                e1.synchronize()
+                n_coarse = pre.info()["n_coarse"]
+                pre.close()
+            rows.append({"ell": ell, "iterations": st["iterations"], "converged": st["converged"],
+                         "time_to_solution_ms": round(e0.elapsed_time(e1), 2), "n_coarse": n_coarse})
+        out[key] = rows
     return out
 
 

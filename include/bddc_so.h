@@ -46,7 +46,12 @@ enum {
     BDDC_ERR_UNSUPPORTED = -8 /* valid request this build does not implement    */
 };
 
-enum { BDDC_FP64 = 0, BDDC_MIXED = 1 };      /* precision of the local solves   */
+/* Precision of the local factors and solves (the outer PCG, the weights and
+ * the coarse problem are FP64 either way).  BDDC_MIXED keeps the local
+ * factors in FP32: with coefficients spanning more than about two decades
+ * inside one subdomain its preconditioner loses the accuracy PCG needs
+ * (measured: contrast 1e4 in channels stalls PCG); use BDDC_FP64 there. */
+enum { BDDC_FP64 = 0, BDDC_MIXED = 1 };
 enum { BDDC_W_CARD = 0, BDDC_W_RHO = 1 };    /* eq. (W) / Remark 1 weighting     */
 /* Constraint selection (Table 1, Section 5): which objects of Theta-hat on
  * Gamma carry coarse DOFs.  VEF: vertices, edges and faces; VE: vertices and

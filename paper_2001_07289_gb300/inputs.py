@@ -227,20 +227,38 @@ class Problem:
         return self.nx * self.ny * self.nz
 
 
-def channel_mask(nx: int, ny: int, nz: int, per_axis: int, width: int, seed: int) -> np.ndarray:
+def channel_mask(nx: int, ny: int, nz: int, per_axis: int, width: int, seed: int,
+                 cuts: Optional[Sequence[Sequence[int]]] = None) -> np.ndarray:
     """Per-element indicator (x fastest) of a system of straight channels:
     per_axis bars of width x width elements running through the whole mesh
     along each axis, at seeded transverse positions (the channels geometry of
-    Section 5.2 is only in a missing figure; this one is synthetic)."""
+    Section 5.2 is only in a missing figure; this one is synthetic).  With
+    cuts, every bar lies inside one slab of each transverse axis, at least one
+    element away from its cut planes: a bar that straddled a cut plane
+    parallel to it would meet its continuation in a diagonal subdomain only
+    along an edge, leaving that pair of channel pieces without an acceptable
+    path under face constraints (remark after Theorem 1)."""
     n = (nx, ny, nz)
     mask = np.zeros((nz, ny, nx), dtype=bool)
     u = uniform01(seed, 6 * per_axis)
+
+    def position(t, v):
+        if cuts is None:
+            return 1 + int(v * (n[t] - width - 1))
+        b = [0] + list(cuts[t]) + [n[t]]
+        room = [(lo + 1, hi - 1 - width) for lo, hi in zip(b[:-1], b[1:]) if hi - 1 - width >= lo + 1]
+        if not room:
+            raise ValueError("slabs too thin for channels of this width")
+        k = min(int(v * len(room)), len(room) - 1)
+        lo, hi = room[k]
+        w = v * len(room) - k
+        return lo + min(int(w * (hi - lo + 1)), hi - lo)
+
     q = 0
     for d in range(3):
         t1, t2 = (d + 1) % 3, (d + 2) % 3
         for _ in range(per_axis):
-            a = 1 + int(u[q] * (n[t1] - width - 1))
-            b = 1 + int(u[q + 1] * (n[t2] - width - 1))
+            a, b = position(t1, u[q]), position(t2, u[q + 1])
             q += 2
             sl = [slice(None)] * 3            # array axes are (z, y, x)
             sl[2 - t1] = slice(a, a + width)
@@ -270,9 +288,9 @@ def channels_problem(n: int = 40, parts: int = 4, ell: float = 4.0, per_axis: in
     elsewhere, f = 1, rho-weights (Remark 1), PCG to rtol 1e-6.
     sub_partition "material": Theta-hat = {background, channels} per
     subdomain (BDDC-SO); "none": Theta-hat = Theta (standard BDDC)."""
-    mask = channel_mask(n, n, n, per_axis, width, BASE_SEED + 100 + seed)
-    alpha = np.where(mask, 10.0 ** ell, 1.0)
     cuts = [uniform_cuts(n, parts)] * 3
+    mask = channel_mask(n, n, n, per_axis, width, BASE_SEED + 100 + seed, cuts)
+    alpha = np.where(mask, 10.0 ** ell, 1.0)
     if sub_partition == "material":
         piece, L = material_pieces(n, n, n, cuts, mask), n
     elif sub_partition == "none":

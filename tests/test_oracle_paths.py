@@ -107,3 +107,24 @@ def test_quality_is_the_best_path_bottleneck_brute_force():
     assert sorted(r["quality"]) == sorted(diag)
     for (i, j), q in r["quality"].items():
         assert q == pytest.approx(best(i, j), rel=1e-12)
+
+
+def test_channels_need_paths_through_the_channels():
+    """Channels of contrast 10^6 on 20^3 with 2^3 subdomains, one channel
+    piece per subdomain (Section 5.2).  A bar straddling the cut plane
+    parallel to it meets its continuation in the diagonal subdomain only along
+    an edge: with faces only, that channel pair's best path crosses the
+    background, quality 1e-6.  The same bar inside a slab leaves every pair a
+    path through the channel (quality 1)."""
+    from paper_2001_07289_gb300 import inputs
+    n, cuts = 20, [[10]] * 3
+    sub, _ = partition.box_labels(n, n, n, cuts, n)
+    for y0, want in ((9, 1e-6), (4, 1.0)):   # bar along x at y in [y0, y0+2), z in [4, 6)
+        mask = np.zeros((n, n, n), dtype=bool)
+        mask[4:6, y0:y0 + 2, :] = True
+        mask = mask.reshape(-1)
+        piece = inputs.material_pieces(n, n, n, cuts, mask)
+        alpha = np.where(mask, 1e6, 1.0)
+        r = paths.acceptable_paths(n, n, n, sub, piece, alpha, "f")
+        assert r["n_without_path"] == 0
+        assert r["min_ratio"] == pytest.approx(want, rel=1e-12)
