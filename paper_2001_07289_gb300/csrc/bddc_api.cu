@@ -196,16 +196,16 @@ struct bddc_handle {
   // sub-subdomains: per-element labels (Theta-hat given) or boxes of size L
   bool labels = false;
   std::vector<int> label_in;            // the caller's labels until renumbered
-  std::vector<int> epiece, piece_sub;   // per element: dense piece number; per piece: subdomain
+  std::vector<int> epiece, piece_sub;   // labels: per element dense piece number; per piece: subdomain
   int n_pieces = 0;
   // coarse objects (selected), by coarse id: type (0 vertex, 1 edge, 2 face),
   // cell (3 doubled subdomain coordinates), global nodes (CSR, ascending)
   std::vector<int> okind, ocell;
-  std::vector<long long> onoff, onodes;
+  std::vector<long long> onoff;
+  std::vector<int> onodes;        // node coordinates (x, y, z) per object node
   std::vector<int> item_objid;    // boxes of size L: item tuple -> coarse id or -1
   int item_n[3] = {0, 0, 0};
-  std::vector<int> lcn, own;      // local node lists; local Neumann node -> local average
-  std::vector<unsigned char> vfix;   // per global node: point-value coarse DOF
+  std::vector<int> lcn;           // local node lists of the coarse DOFs
   long long n_nodes = 0, n_free = 0;
   LocalLaunch L{};
   MeshDev m{};
@@ -379,14 +379,9 @@ void build_pieces(bddc_handle* h) {
   const AxisHost* ax = h->ax;
   const int nsx = (int)ax[0].slab_lo.size(), nsy = (int)ax[1].slab_lo.size();
   auto sub_of = [&](int i, int j, int k) { return ax[0].slab[i] + nsx * (ax[1].slab[j] + nsy * ax[2].slab[k]); };
-  h->epiece.assign(NE, 0);
-  if (!h->labels) {
+  if (!h->labels) {   // the element table is computed on the device (k_box_pieces)
+    h->epiece.clear();
     const int npx = (int)ax[0].piece_lo.size(), npy = (int)ax[1].piece_lo.size(), npz = (int)ax[2].piece_lo.size();
-    for (int k = 0; k < M.nz; ++k)
-      for (int j = 0; j < M.ny; ++j)
-        for (int i = 0; i < M.nx; ++i)
-          h->epiece[i + (long long)M.nx * (j + (long long)M.ny * k)] =
-              ax[0].piece[i] + npx * (ax[1].piece[j] + npy * ax[2].piece[k]);
     h->n_pieces = npx * npy * npz;
     h->piece_sub.assign(h->n_pieces, 0);
     for (int c = 0; c < npz; ++c)
@@ -397,6 +392,7 @@ void build_pieces(bddc_handle* h) {
   }
   std::map<int, int> dense;
   h->piece_sub.clear();
+  h->epiece.assign(NE, 0);
   for (int k = 0; k < M.nz; ++k)
     for (int j = 0; j < M.ny; ++j)
       for (int i = 0; i < M.nx; ++i) {
@@ -436,6 +432,19 @@ void build_objects(bddc_handle* h, bool keep_v, bool keep_e, bool keep_f) {
     int nit[3];
     for (int d = 0; d < 3; ++d) nit[d] = h->item_n[d] = ax[d].nitem();
     h->item_objid.assign((size_t)nit[0] * nit[1] * nit[2], -1);
+    {
+      // capacity: objects lie on the cut planes; at most the items of those planes
+      long long nodes = 0, items = 0;
+      for (int d = 0; d < 3; ++d) {
+        const int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+        nodes += (long long)ax[d].cuts.size() * (ax[a1].n + 1) * (ax[a2].n + 1);
+        items += (long long)ax[d].cuts.size() * nit[a1] * nit[a2];
+      }
+      h->onodes.reserve(3 * nodes);
+      h->okind.reserve(items);
+      h->ocell.reserve(3 * items);
+      h->onoff.reserve(items + 1);
+    }
     for (int iz = 0; iz < nit[2]; ++iz)
       for (int iy = 0; iy < nit[1]; ++iy)
         for (int ix = 0; ix < nit[0]; ++ix) {
@@ -457,8 +466,8 @@ void build_objects(bddc_handle* h, bool keep_v, bool keep_e, bool keep_f) {
           }
           for (int z = ax[2].item_lo[iz]; z <= ax[2].item_hi[iz]; ++z)
             for (int y = ax[1].item_lo[iy]; y <= ax[1].item_hi[iy]; ++y)
-              for (int x = ax[0].item_lo[ix]; x <= ax[0].item_hi[ix]; ++x) h->onodes.push_back(nodeid(NX, NY, x, y, z));
-          h->onoff.push_back((long long)h->onodes.size());
+              for (int x = ax[0].item_lo[ix]; x <= ax[0].item_hi[ix]; ++x) h->onodes.insert(h->onodes.end(), {x, y, z});
+          h->onoff.push_back((long long)h->onodes.size() / 3);
         }
     return;
   }
@@ -523,8 +532,9 @@ void build_objects(bddc_handle* h, bool keep_v, bool keep_e, bool keep_f) {
     h->okind.push_back(kind);
     for (int d = 0; d < 3; ++d) h->ocell.push_back(lo[d] == hi[d] ? 2 * lo[d] + 1 : 2 * hi[d]);
     std::sort(comp.begin(), comp.end());
-    h->onodes.insert(h->onodes.end(), comp.begin(), comp.end());
-    h->onoff.push_back((long long)h->onodes.size());
+    for (long long u : comp)
+      h->onodes.insert(h->onodes.end(), {(int)(u % NX), (int)((u / NX) % NY), (int)(u / ((long long)NX * NY))});
+    h->onoff.push_back((long long)h->onodes.size() / 3);
   }
 }
 
@@ -538,16 +548,10 @@ void build_metadata(bddc_handle* h) {
   build_pieces(h);
   build_objects(h, keep_verts, keep_edges, keep_faces);
   const int nc = (int)h->okind.size();
-  const bddc_mesh& Mh = h->mesh;
-  const int NXh = Mh.nx + 1, NYh = Mh.ny + 1;
   // point values: one-node vertex objects, eliminated as primal DOFs
-  h->vfix.assign((size_t)NXh * NYh * (Mh.nz + 1), 0);
   int nvert = 0;
   for (int g = 0; g < nc; ++g)
-    if (h->okind[g] == 0 && h->onoff[g + 1] - h->onoff[g] == 1) {
-      h->vfix[h->onodes[h->onoff[g]]] = 1;
-      ++nvert;
-    }
+    if (h->okind[g] == 0 && h->onoff[g + 1] - h->onoff[g] == 1) ++nvert;
   h->n_coarse = nc;
   h->n_vertices = nvert;
   h->n_pinned = 0;
@@ -572,6 +576,8 @@ void build_metadata(bddc_handle* h) {
   // 2s + 1 lies in slab s, 2s on the plane of slabs s - 1 and s
   const int S = nsub[0] * nsub[1] * nsub[2];
   std::vector<std::vector<int>> sub_objs(S);
+  h->lcn.reserve(2 * h->onodes.size() / 3 + 8 * (size_t)nc);
+  h->lc.reserve(2 * (size_t)nc + 8 * (size_t)nc / 4);
   for (int g = 0; g < nc; ++g) {
     int r0[3], r1[3];
     for (int d = 0; d < 3; ++d) {
@@ -584,7 +590,6 @@ void build_metadata(bddc_handle* h) {
         for (int sx = r0[0]; sx <= r1[0]; ++sx) sub_objs[sx + nsub[0] * (sy + nsub[1] * sz)].push_back(g);
   }
   h->lcn.clear();
-  h->own.clear();
   h->subs.assign(S, SubDesc{});
   h->lc.clear();
   // (coarse id, subdomain, local position) of every local coarse DOF, in
@@ -619,9 +624,8 @@ void build_metadata(bddc_handle* h) {
           c.count = (int)(h->onoff[g + 1] - h->onoff[g]);
           c.off = (int)h->lcn.size();
           for (long long q = h->onoff[g]; q < h->onoff[g + 1]; ++q) {
-            const long long nd = h->onodes[q];
-            const int x = (int)(nd % NXh) - s.e0[0], y = (int)((nd / NXh) % NYh) - s.e0[1],
-                      z = (int)(nd / ((long long)NXh * NYh)) - s.e0[2];
+            const int x = h->onodes[3 * q] - s.e0[0], y = h->onodes[3 * q + 1] - s.e0[1],
+                      z = h->onodes[3 * q + 2] - s.e0[2];
             if (x < 0 || y < 0 || z < 0 || x > s.w[0] || y > s.w[1] || z > s.w[2])
               throw std::runtime_error("coarse object outside a subdomain that shares it");
             if (q == h->onoff[g]) { c.v[0] = (short)x; c.v[1] = (short)y; c.v[2] = (short)z; }
@@ -679,11 +683,6 @@ void build_metadata(bddc_handle* h) {
         s.offPhi = offPhi; offPhi += padded((long long)s.nB * s.nc);
         s.offB = offB; offB += s.nB;
         s.offVec = offVec; offVec += NN;
-        h->own.resize(offVec, -1);   // local Neumann node -> local average (or -1)
-        for (int a = 0; a < s.na; ++a) {
-          const LocalCoarse& c = h->lc[s.cofs + s.nv + a];
-          for (int q = 0; q < c.count; ++q) h->own[s.offVec + h->lcn[c.off + q]] = s.nv + a;
-        }
         s.offTC = offTC; offTC += (long long)pz * tc_kchunks(QN) * tc_chunk_floats(QN);
         L.maxQD = std::max(L.maxQD, QD); L.maxNzD = std::max(L.maxNzD, nzD); L.maxND = std::max(L.maxND, QD * nzD);
         L.maxQN = std::max(L.maxQN, QN); L.maxNzN = std::max(L.maxNzN, pz); L.maxNN = std::max(L.maxNN, NN);
@@ -904,9 +903,25 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   // axis tables
   MeshDev& m = h->m;
   m.nx = M.nx; m.ny = M.ny; m.nz = M.nz;
-  m.vfix = upload(h, h->vfix, st);
-  m.epiece = upload(h, h->epiece, st);
   m.NX = M.nx + 1; m.NY = M.ny + 1; m.NZ = M.nz + 1;
+  {
+    // point-value flags (marked below from the coarse lists) and the piece of
+    // every element: the given labels, or the box pieces computed here
+    unsigned char* vf = h->dnew<unsigned char>((size_t)h->n_nodes);
+    CK(cudaMemsetAsync(vf, 0, (size_t)h->n_nodes, st));
+    m.vfix = vf;
+    if (h->labels) {
+      m.epiece = upload(h, h->epiece, st);
+    } else {
+      int* ep = h->dnew<int>((size_t)NE);
+      const int* pa = upload(h, h->ax[0].piece, st);
+      const int* pb = upload(h, h->ax[1].piece, st);
+      const int* pc = upload(h, h->ax[2].piece, st);
+      launch_box_pieces(M.nx, M.ny, M.nz, pa, pb, pc, (int)h->ax[0].piece_lo.size(), (int)h->ax[1].piece_lo.size(),
+                        ep, st);
+      m.epiece = ep;
+    }
+  }
   m.h = M.h;
   for (int d = 0; d < 3; ++d) {
     AxisHost& a = h->ax[d];
@@ -994,7 +1009,12 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   }
   L.lc = upload(h, h->lc, st);
   L.lcn = upload(h, h->lcn, st);
-  L.own = upload(h, h->own, st);
+  {
+    int* own = h->dnew<int>((size_t)std::max(h->n_local_nodes_total, 1LL));
+    CK(cudaMemsetAsync(own, 0xFF, sizeof(int) * (size_t)std::max(h->n_local_nodes_total, 1LL), st));
+    L.own = own;
+    launch_mark_coarse(L, const_cast<unsigned char*>(m.vfix), own, st);
+  }
   L.facD = h->dalloc(es * lay.D);
   L.facN = h->dalloc(es * lay.N);
   L.Phi = h->dalloc(es * lay.Phi);
@@ -1023,7 +1043,18 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   L.tc = (!dbl && L.maxQN <= 256) ? h->dalloc(sizeof(float) * (size_t)std::max(lay.TC, 1LL), true) : nullptr;
   // weights (eq. W or Remark 1)
   double* pw = nullptr;
-  if (h->opt.weights == BDDC_W_RHO) {
+  if (h->opt.weights == BDDC_W_RHO && !h->labels) {
+    std::vector<int> plo, phi;
+    int npc[3];
+    for (int d = 0; d < 3; ++d) {
+      npc[d] = (int)h->ax[d].piece_lo.size();
+      plo.insert(plo.end(), h->ax[d].piece_lo.begin(), h->ax[d].piece_lo.end());
+      phi.insert(phi.end(), h->ax[d].piece_hi.begin(), h->ax[d].piece_hi.end());
+    }
+    pw = (double*)h->dalloc(sizeof(double) * (size_t)h->n_pieces, true);
+    launch_piece_alpha_box(h->alpha, M.nx, M.ny, upload(h, plo, st), upload(h, phi, st), npc[0], npc[1], npc[2], pw,
+                           st);
+  } else if (h->opt.weights == BDDC_W_RHO) {
     // elements of every piece, ascending (counting sort of the element labels)
     const int np = h->n_pieces;
     std::vector<long long> pe_off(np + 1, 0);

@@ -113,6 +113,11 @@ void set_wait_report_tries(long long tries);
 size_t apply_smem(const BucketSizes& bs, int nb, int es);
 void launch_piece_alpha(const double* alpha, const long long* pe_off, const int* pe, int np, double* pw,
                         cudaStream_t st);
+void launch_piece_alpha_box(const double* alpha, int nx, int ny, const int* plo, const int* phi, int npx, int npy,
+                            int npz, double* pw, cudaStream_t st);
+void launch_mark_coarse(const LocalLaunch& L, unsigned char* vfix, int* own, cudaStream_t st);
+void launch_box_pieces(int nx, int ny, int nz, const int* pa, const int* pb, const int* pc, int npx, int npy,
+                       int* epiece, cudaStream_t st);
 
 // coarse.cu
 void launch_coarse_assemble(const LocalLaunch& L, const int* color_subs, const int* color_count_host,

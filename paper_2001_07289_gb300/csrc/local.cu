@@ -1080,6 +1080,53 @@ __global__ void k_weights(const SubDesc* __restrict__ subs, MeshDev m, const dou
   }
 }
 
+// Device tables of the local kernels, from the coarse-DOF lists: the
+// point-value flag of every node (vfix, zeroed before; a vertex shared by
+// several subdomains gets the same value from each) and every subdomain's
+// local-node -> average map (own at the vector offsets, -1 before; the
+// objects of one subdomain are disjoint).  One CTA per subdomain.
+__global__ void k_mark_coarse(const SubDesc* __restrict__ subs, const LocalCoarse* __restrict__ lc,
+                              const int* __restrict__ lcn, int NX, int NY, unsigned char* __restrict__ vfix,
+                              int* __restrict__ own) {
+  const SubDesc s = subs[blockIdx.x];
+  for (int j = threadIdx.x; j < s.nc; j += blockDim.x) {
+    const LocalCoarse c = lc[s.cofs + j];
+    if (j < s.nv) {
+      vfix[nodeid(NX, NY, s.e0[0] + c.v[0], s.e0[1] + c.v[1], s.e0[2] + c.v[2])] = 1;
+    } else {
+      for (int q = 0; q < c.count; ++q) own[s.offVec + lcn[c.off + q]] = j;
+    }
+  }
+}
+
+// Box sub-subdomains: piece of every element from the per-axis piece
+// numbers, a + npx (b + npy c).
+__global__ void k_box_pieces(int nx, int ny, int nz, const int* __restrict__ pa, const int* __restrict__ pb,
+                             const int* __restrict__ pc, int npx, int npy, int* __restrict__ epiece) {
+  const long long ne = (long long)nx * ny * nz;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
+    epiece[e] = pa[i] + npx * (pb[j] + npy * pc[k]);
+  }
+}
+
+// Mean alpha of every box sub-subdomain: its element box [lo, hi) per axis
+// (concatenated x, y, z tables), summed over k, j, i ascending.
+__global__ void k_piece_alpha_box(const double* __restrict__ alpha, int nx, int ny, const int* __restrict__ plo,
+                                  const int* __restrict__ phi, int npx, int npy, int npz, double* __restrict__ pw) {
+  const long long np = (long long)npx * npy * npz;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(p % npx), b = (int)((p / npx) % npy), c = (int)(p / ((long long)npx * npy));
+    const int x0 = plo[a], x1 = phi[a], y0 = plo[npx + b], y1 = phi[npx + b], z0 = plo[npx + npy + c],
+              z1 = phi[npx + npy + c];
+    double sum = 0.0;
+    for (int k = z0; k < z1; ++k)
+      for (int j = y0; j < y1; ++j)
+        for (int i = x0; i < x1; ++i) sum += alpha[(long long)i + (long long)nx * (j + (long long)ny * k)];
+    pw[p] = sum / ((double)(x1 - x0) * (y1 - y0) * (z1 - z0));
+  }
+}
+
 // Mean alpha of every sub-subdomain (piece): its elements listed in
 // ascending order (pe_off, pe), summed in that order.
 __global__ void k_piece_alpha(const double* __restrict__ alpha, const long long* __restrict__ pe_off,
@@ -1660,6 +1707,27 @@ void configure_local_kernels() {
 void launch_weights(const LocalLaunch& L, const double* piece_w, cudaStream_t st) {
   BDDC_COUNT(1);
   k_weights<<<dim3(L.nsub, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, piece_w, L.delta);
+}
+
+void launch_mark_coarse(const LocalLaunch& L, unsigned char* vfix, int* own, cudaStream_t st) {
+  BDDC_COUNT(1);
+  k_mark_coarse<<<L.nsub, BDDC_THREADS, 0, st>>>(L.subs, L.lc, L.lcn, L.m.NX, L.m.NY, vfix, own);
+}
+
+void launch_box_pieces(int nx, int ny, int nz, const int* pa, const int* pb, const int* pc, int npx, int npy,
+                       int* epiece, cudaStream_t st) {
+  const long long ne = (long long)nx * ny * nz;
+  BDDC_COUNT(1);
+  k_box_pieces<<<(int)std::min<long long>((ne + 255) / 256, 8192), 256, 0, st>>>(nx, ny, nz, pa, pb, pc, npx, npy,
+                                                                                 epiece);
+}
+
+void launch_piece_alpha_box(const double* alpha, int nx, int ny, const int* plo, const int* phi, int npx, int npy,
+                            int npz, double* pw, cudaStream_t st) {
+  const long long np = (long long)npx * npy * npz;
+  BDDC_COUNT(1);
+  k_piece_alpha_box<<<(int)std::min<long long>((np + 255) / 256, 4096), 256, 0, st>>>(alpha, nx, ny, plo, phi, npx,
+                                                                                      npy, npz, pw);
 }
 
 void launch_piece_alpha(const double* alpha, const long long* pe_off, const int* pe, int np, double* pw,
