@@ -48,9 +48,11 @@ enum {
 
 /* Precision of the local factors and solves (the outer PCG, the weights and
  * the coarse problem are FP64 either way).  BDDC_MIXED keeps the local
- * factors in FP32: with coefficients spanning more than about two decades
- * inside one subdomain its preconditioner loses the accuracy PCG needs
- * (measured: contrast 1e4 in channels stalls PCG); use BDDC_FP64 there. */
+ * factors in FP32, whose error grows with the local condition number: a
+ * high-contrast inclusion that crosses a subdomain with few constraints on
+ * it (thin channels of contrast 1e4 with Theta-hat = Theta, or with faces
+ * only) can leave PCG without a usable preconditioner, while contrast 1e6 in
+ * blocks aligned with many subobjects works; use BDDC_FP64 when in doubt. */
 enum { BDDC_FP64 = 0, BDDC_MIXED = 1 };
 enum { BDDC_W_CARD = 0, BDDC_W_RHO = 1 };    /* eq. (W) / Remark 1 weighting     */
 /* Constraint selection (Table 1, Section 5): which objects of Theta-hat on
