@@ -15,6 +15,8 @@ The oracle is written from the paper's definitions, slow and direct:
   objects.py    classification of interface DOFs into (sub)objects by the set
                 of sub-subdomains containing them, selection vef / ve / f
                 (Section 3; Table 1 variants).
+  multilevel.py the second level of multilevel BDDC-SO (BDDC on the coarse
+                problem, Section 6).
   paths.py      the acceptable-path check of a selection (remark after
                 Theorem 1).
   weights.py    the weighting E of eq. (W) and the rho-weighting of Remark 1.

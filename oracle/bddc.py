@@ -234,18 +234,20 @@ class BDDCSO:
         kind, f = self.setup_two_level()[3]
         return sla.cho_solve((f, True), rc) if kind == "chol" else f.solve(rc)
 
-    def apply(self, r: np.ndarray) -> np.ndarray:
+    def apply(self, r: np.ndarray, coarse=None) -> np.ndarray:
         """z = B r on the full node grid (Dirichlet entries of r ignored, z's 0).
 
         The V2 solve in its two-level form: v2_i = Phi_i u_c|_i + w_i with
         A_c u_c = sum_i R_ci^T Phi_i^T r_i and w_i from the constrained local
-        problem [A_i C_i^T; C_i 0][w_i; mu_i] = [r_i; 0]."""
+        problem [A_i C_i^T; C_i 0][w_i; mu_i] = [r_i; 0].  coarse: a map
+        r_c -> u_c in place of the exact coarse solve (the multilevel
+        version, oracle/multilevel.py)."""
         bases, lus, _, _ = self.setup_two_level()
         v1, loc = self._v2_rhs_local(r)
         rc = np.zeros(self.n_coarse)
         for i in range(len(self.subs)):
             np.add.at(rc, self.coarse_dofs(i), bases[i].T @ loc[i])
-        uc = self.coarse_solve(rc)
+        uc = coarse(rc) if coarse is not None else self.coarse_solve(rc)
         w = []
         for i, s in enumerate(self.subs):
             nci = s.C.shape[0]
