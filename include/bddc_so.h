@@ -109,7 +109,22 @@ typedef struct {
     int use_graph;  /* 1: pcg_solve runs its whole loop as one CUDA graph (below)      */
     int maxit;      /* PCG iteration limit (<= 0: 2000)                               */
     int beta_rule;  /* BDDC_BETA_STANDARD (0) or BDDC_BETA_FLEXIBLE (below)          */
+    int ml_block;   /* 0: exact coarse solve; g >= 1: multilevel BDDC-SO (below)     */
 } bddc_options;
+
+/* Multilevel BDDC-SO (Section 6: the multilevel version removes the coarse
+ * problem's size limit).  With ml_block = g >= 1 the coarse problem is not
+ * factored: each apply preconditions it by one application of BDDC on the
+ * coarse level (Definition 1 once more), whose subdomains are blocks of
+ * g x g x g subdomains (the last block of an axis takes the rest), whose
+ * elements are the subdomains' local coarse matrices Phi_i^T A_i Phi_i, whose
+ * interface holds the coarse DOFs shared by two or more blocks, grouped into
+ * level-2 objects by the set of blocks sharing them (one constraint each: the
+ * mean of the object's coarse values), with weights 1 / (blocks sharing the
+ * DOF) and an exact level-2 coarse solve.  All of it FP64.  B stays SPD;
+ * the PCG iteration count grows (the condition number gains the coarse
+ * level's factor) while the coarse set-up and solve shrink.  Its work
+ * vectors are allocated at setup, so the allocation-free apply takes it too. */
 
 /* PCG direction update p = z + beta p.  STANDARD (Section 5's PCG): beta =
  * r_{k+1}.z_{k+1} / r_k.z_k.  FLEXIBLE (Polak-Ribiere): beta =
@@ -172,6 +187,8 @@ typedef struct {
     int bucket_ring[2];       /* per bucket: depth of the bulk-copy ring (6: one
                                  CTA per SM, 4: two), tuned                         */
     int bucket_ctas[2];       /* per bucket: CTAs per subdomain (1 or 2), tuned      */
+    int ml_blocks;            /* multilevel: blocks of the coarse level (0: exact coarse solve) */
+    int ml_coarse2;           /* multilevel: level-2 coarse DOFs (level-2 objects)  */
 } bddc_info_t;
 
 /* Host-only analysis of a problem, no GPU needed: the counts that bddc_setup

@@ -45,7 +45,8 @@ class Partition(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("weights", C.c_int), ("L_elems", C.c_int),
-                ("selection", C.c_int), ("use_graph", C.c_int), ("maxit", C.c_int), ("beta_rule", C.c_int)]
+                ("selection", C.c_int), ("use_graph", C.c_int), ("maxit", C.c_int), ("beta_rule", C.c_int),
+                ("ml_block", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -62,7 +63,8 @@ class Info(C.Structure):
                 ("apply_bytes", C.c_longlong), ("apply_cluster", C.c_int), ("local_band_flops", C.c_double),
                 ("factor_kernel", C.c_int), ("factor_tc_subdomains", C.c_int), ("pinned_subdomains", C.c_int),
                 ("n_buckets", C.c_int), ("bucket_subdomains", C.c_int * 2),
-                ("bucket_ring", C.c_int * 2), ("bucket_ctas", C.c_int * 2)]
+                ("bucket_ring", C.c_int * 2), ("bucket_ctas", C.c_int * 2), ("ml_blocks", C.c_int),
+                ("ml_coarse2", C.c_int)]
 
 
 class Analysis(C.Structure):
@@ -149,7 +151,7 @@ def _stream() -> C.c_void_p:
 
 
 def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection="vef", beta="standard",
-             piece=None):
+             piece=None, ml_block=0):
     mesh = Mesh(nx, ny, nz, h)
     part = Partition()
     keep = []
@@ -167,7 +169,8 @@ def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selec
     prec = {"fp64": BDDC_FP64, "mixed": BDDC_MIXED}[precision] if isinstance(precision, str) else precision
     wts = {"card": BDDC_W_CARD, "rho": BDDC_W_RHO}[weights] if isinstance(weights, str) else weights
     sel = SELECTIONS[selection] if isinstance(selection, str) else selection
-    opt = Options(prec, wts, L, sel, int(use_graph), maxit, BETA_RULES[beta] if isinstance(beta, str) else beta)
+    opt = Options(prec, wts, L, sel, int(use_graph), maxit, BETA_RULES[beta] if isinstance(beta, str) else beta,
+                  int(ml_block))
     return mesh, part, opt, keep
 
 
@@ -206,13 +209,14 @@ class BDDC:
 
     def __init__(self, nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int,
                  alpha: torch.Tensor, h: float = 0.0, precision="fp64", weights="card",
-                 maxit: int = 2000, use_graph: bool = False, selection="vef", beta="standard", piece=None):
+                 maxit: int = 2000, use_graph: bool = False, selection="vef", beta="standard", piece=None,
+                 ml_block: int = 0):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.h = h if h > 0 else 1.0 / nx
         self.n_nodes = (nx + 1) * (ny + 1) * (nz + 1)
         self.maxit = maxit
         mesh, part, opt, keep = _structs(nx, ny, nz, self.h, cuts, L, precision, weights, maxit, use_graph,
-                                         selection, beta, piece=piece)
+                                         selection, beta, piece=piece, ml_block=ml_block)
         self._handle = C.c_void_p()
         _check(lib.bddc_setup(C.byref(mesh), C.byref(part), C.byref(opt), _vptr(alpha, nx * ny * nz), _stream(),
                               C.byref(self._handle)), None)
@@ -319,11 +323,11 @@ class BDDC:
 
 def solve_host(nx, ny, nz, cuts, L, alpha: np.ndarray, b: np.ndarray, rtol: float, h: float = 0.0,
                precision="fp64", weights="card", maxit: int = 2000, use_graph: bool = False,
-               selection="vef", piece=None):
+               selection="vef", piece=None, ml_block: int = 0):
     """bddc_solve_host: setup + PCG from host arrays, result in a host array."""
     h = h if h > 0 else 1.0 / nx
     mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection,
-                                     piece=piece)
+                                     piece=piece, ml_block=ml_block)
     a = np.ascontiguousarray(alpha, dtype=np.float64)
     bb = np.ascontiguousarray(b, dtype=np.float64)
     if a.size != nx * ny * nz or bb.size != (nx + 1) * (ny + 1) * (nz + 1):

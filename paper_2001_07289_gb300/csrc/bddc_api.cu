@@ -216,6 +216,7 @@ struct bddc_handle {
   double* Ac_copy = nullptr;      // dense coarse matrix, kept for small problems (diagnostics)
   CoarseGeom geom;
   MFPlan mf;
+  MLPlan ml;                      // second level (options.ml_block > 0)
   int *cptr = nullptr, *color_subs = nullptr;
   int2* cent = nullptr;
   int color_count[8] = {0}, color_off[8] = {0};
@@ -1035,7 +1036,8 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   L.Lv = h->dalloc(es * lay.L, true);
   L.PA = h->dalloc(es * lay.PA, true);
   L.Sc = h->dalloc(es * lay.Sc, true);
-  L.Ac = (double*)h->dalloc(sizeof(double) * lay.Ac, true);
+  // the local coarse matrices stay for the apply of the multilevel coarse level
+  L.Ac = (double*)h->dalloc(sizeof(double) * lay.Ac, h->opt.ml_block <= 0);
   const int nch = (L.maxNc + CW - 1) / CW;
   L.mscratch = h->dalloc(es * (size_t)L.nsub * nch * L.mscratch_stride, true);
   // packed tensor-core tiles of the Neumann factors (FP32 path, planes of at
@@ -1086,14 +1088,25 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     CK(cudaMemsetAsync(h->Ac_copy, 0, sizeof(double) * (size_t)nc * nc, st));
     launch_coarse_assemble(L, h->color_subs, h->color_count, h->color_off, h->Ac_copy, nc, st);
   }
-  mf_plan(h->mf, h->geom, nc);
-  mf_upload(h->mf, [h](size_t b) { return h->dalloc(b); }, [h](size_t b) { return h->dalloc(b, true); }, st);
-  h->factor_bytes += 2 * sizeof(double) * (size_t)h->mf.spool;   // solve matrices and their transposes
-  configure_mf_kernels();
-  mf_assemble(h->mf, L, h->color_subs, h->color_count, h->color_off, st);
-  CK(cudaEventRecord(ev[5], st));
-  mf_factor(h->mf, h->err, st, h->aux, h->ev_fork, h->ev_join);
-  CK(cudaEventRecord(ev[6], st));
+  if (h->opt.ml_block > 0) {
+    // multilevel: the coarse problem gets BDDC on blocks of subdomains
+    const int nsub3[3] = {(int)h->ax[0].slab_lo.size(), (int)h->ax[1].slab_lo.size(), (int)h->ax[2].slab_lo.size()};
+    ml_plan(h->ml, h->opt.ml_block, nsub3, h->subs, h->lc, nc, h->h_cptr, h->h_cent);
+    CK(cudaEventRecord(ev[5], st));
+    ml_setup(h->ml, L, [h](size_t b) { return h->dalloc(b); }, [h](size_t b) { return h->dalloc(b, true); }, h->err,
+             st);
+    h->factor_bytes += 2 * sizeof(double) * (size_t)(h->ml.N.spool + h->ml.D.spool + h->ml.C.spool);
+    CK(cudaEventRecord(ev[6], st));
+  } else {
+    mf_plan(h->mf, h->geom, nc);
+    mf_upload(h->mf, [h](size_t b) { return h->dalloc(b); }, [h](size_t b) { return h->dalloc(b, true); }, st);
+    h->factor_bytes += 2 * sizeof(double) * (size_t)h->mf.spool;   // solve matrices and their transposes
+    configure_mf_kernels();
+    mf_assemble(h->mf, L, h->color_subs, h->color_count, h->color_off, st);
+    CK(cudaEventRecord(ev[5], st));
+    mf_factor(h->mf, h->err, st, h->aux, h->ev_fork, h->ev_join);
+    CK(cudaEventRecord(ev[6], st));
+  }
   CK(cudaGetLastError());
   // apply / PCG work vectors
   const long long N = h->n_nodes;
@@ -1147,7 +1160,10 @@ void apply_core(bddc_handle* h, const LocalLaunch& L, const double* r, double* z
   CK(cudaEventRecord(h->ev_fork, st));
   CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
   launch_coarse_gather(h->cptr, h->cent, L.rcl, rc, h->n_coarse, h->aux);
-  mf_solve(h->mf, rc, uc, wf, h->aux);                                 // A_c u_c = r_c
+  if (h->opt.ml_block > 0)
+    ml_apply(h->ml, L, h->cptr, h->cent, rc, uc, h->aux);                // u_c = M2 r_c (coarse-level BDDC)
+  else
+    mf_solve(h->mf, rc, uc, wf, h->aux);                               // A_c u_c = r_c
   CK(cudaEventRecord(h->ev_join, h->aux));
   launch_neumann<T>(L, r, t, st);                                      // y = A_rr^{-1} r_i,r
   CK(cudaStreamWaitEvent(st, h->ev_join, 0));
@@ -1420,6 +1436,7 @@ std::unique_ptr<bddc_handle> make_handle(const bddc_mesh* mesh, const bddc_parti
   if (opt->weights != BDDC_W_CARD && opt->weights != BDDC_W_RHO) throw BddcError(BDDC_ERR_ARG, "bad weights");
   if (opt->beta_rule != BDDC_BETA_STANDARD && opt->beta_rule != BDDC_BETA_FLEXIBLE)
     throw BddcError(BDDC_ERR_ARG, "bad beta_rule");
+  if (opt->ml_block < 0) throw BddcError(BDDC_ERR_ARG, "ml_block must be >= 0");
   if (opt->selection < BDDC_SEL_VEF || opt->selection > BDDC_SEL_EF)
     throw BddcError(BDDC_ERR_ARG, "bad selection");
   std::unique_ptr<bddc_handle> h(new bddc_handle());
@@ -1880,6 +1897,9 @@ extern "C" int bddc_get_info(const bddc_handle* h, bddc_info_t* info) {
   info->factor_kernel = (!h->local_double && h->L.fbucket[0].count > 0 && h->L.factor_tc) ? 1 : 0;
   info->factor_tc_subdomains = info->factor_kernel ? h->L.fbucket[0].count : 0;
   info->pinned_subdomains = h->n_pinned;
+  info->ml_blocks = h->opt.ml_block > 0 ? h->ml.nblock : 0;
+  info->ml_coarse2 = h->opt.ml_block > 0 ? h->ml.ncc : 0;
+  if (h->opt.ml_block > 0) info->coarse_fma = h->ml.flops;
   return BDDC_OK;
 }
 

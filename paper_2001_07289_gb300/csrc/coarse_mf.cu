@@ -121,22 +121,70 @@ struct Builder {
   }
 };
 
-void set_depth(Builder& B, int f, int d) {
+
+}  // namespace
+
+namespace {
+// The numeric plan of a front tree: pivots and update sets per front, the
+// children of every front, and the fronts without a parent (depth 0).
+struct FrontTree {
+  std::vector<std::vector<int>> piv, upd, children;
+  std::vector<int> depth;
+};
+
+void set_tree_depth(FrontTree& B, int f, int d) {
   B.depth[f] = d;
-  for (int c : B.children[f]) set_depth(B, c, d + 1);
+  for (int c : B.children[f]) set_tree_depth(B, c, d + 1);
 }
 
+void mf_plan_tree(MFPlan& P, FrontTree& B, const std::vector<int>& tops, int nc);
 }  // namespace
 
 void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
   P = MFPlan();
   P.nc = nc;
   if (nc == 0) return;
-  Builder B(g, P);
+  Builder Bd(g, P);
   Box root;
   for (int d = 0; d < 3; ++d) { root.s0[d] = 0; root.s1[d] = g.nsub[d]; }
   std::vector<int> tops;
-  B.build(root, tops);
+  Bd.build(root, tops);
+  FrontTree T;
+  T.piv = std::move(Bd.piv);
+  T.upd = std::move(Bd.upd);
+  T.children = std::move(Bd.children);
+  T.depth = std::move(Bd.depth);
+  mf_plan_tree(P, T, tops, nc);
+}
+
+// Independent dense fronts: front k eliminates ids off_k .. off_k + size_k - 1
+// (consecutive, in order) and updates nothing; all at depth 0, factored side
+// by side, and one solve treats every front at once.
+void mf_plan_independent(MFPlan& P, const std::vector<int>& sizes) {
+  P = MFPlan();
+  int nc = 0;
+  for (int n : sizes) nc += n;
+  P.nc = nc;
+  if (nc == 0) return;
+  FrontTree T;
+  std::vector<int> tops;
+  int off = 0;
+  for (int n : sizes) {
+    if (n == 0) continue;
+    std::vector<int> pv(n);
+    for (int q = 0; q < n; ++q) pv[q] = off + q;
+    off += n;
+    tops.push_back((int)T.piv.size());
+    T.piv.push_back(std::move(pv));
+    T.upd.emplace_back();
+    T.children.emplace_back();
+    T.depth.push_back(0);
+  }
+  mf_plan_tree(P, T, tops, nc);
+}
+
+namespace {
+void mf_plan_tree(MFPlan& P, FrontTree& B, const std::vector<int>& tops, int nc) {
   const int nf = (int)B.piv.size();
   P.nfront = nf;
   P.parent.assign(nf, -1);
@@ -146,7 +194,7 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
       P.parent[B.children[f][k]] = f;
       P.child_slot[B.children[f][k]] = (int)k;
     }
-  for (int t : tops) set_depth(B, t, 0);
+  for (int t : tops) set_tree_depth(B, t, 0);
   // several top fronts can exist only if the root box had no separator; they
   // are independent and all sit at depth 0
   P.level_of = B.depth;
@@ -306,6 +354,8 @@ void mf_plan(MFPlan& P, const CoarseGeom& g, int nc) {
     }
   }
 }
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // device kernels

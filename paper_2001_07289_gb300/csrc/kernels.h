@@ -209,6 +209,7 @@ struct MFPlan {
 void stage_h2d(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 void mf_plan(MFPlan& P, const CoarseGeom& g, int nc);
+void mf_plan_independent(MFPlan& P, const std::vector<int>& sizes);
 // alloc: memory kept for the solves; tmp_alloc: memory needed during setup only
 void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
                const std::function<void*(size_t)>& tmp_alloc, cudaStream_t st);
@@ -221,6 +222,56 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cud
 // x = A_c^{-1} b; W: work vector pool of P.wpool doubles
 void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream_t st);
 void configure_mf_kernels();
+
+// multilevel.cu: the second level of multilevel BDDC-SO, BDDC applied to the
+// coarse problem with blocks of g x g x g subdomains (Section 6).  Coarse
+// DOFs shared by two or more blocks form the coarse interface Gamma_2; they
+// are grouped into level-2 objects by the set of blocks sharing them, each
+// constraint the mean of the object's coarse values; weights 1 / (blocks
+// sharing the DOF).  Dense FP64 throughout, on independent multifrontal
+// fronts: N, the blocks' augmented matrices A_k + rho_k C_k^T C_k (exact for
+// the constrained problems, C_k w being prescribed); D, the blocks' interior
+// matrices; C, the level-2 coarse matrix.
+struct MLPlan {
+  int g = 0, nblock = 0, nc = 0, ncc = 0, NB = 0, NI = 0, NO = 0, maxm = 0;
+  // host: per block its block-space offset and size, interior offset and
+  // size, object-slot offset and count; its subdomains and colour
+  std::vector<int> boff, bn, ioff, bni, ooff, bm, bsub_ptr, bsub, bcolor;
+  std::vector<int> bgid;              // block-space slot -> coarse id
+  std::vector<int> iidx;              // block-space slot -> block-interior slot, -1 on Gamma_2
+  std::vector<int> igid;              // block-interior slot -> coarse id
+  std::vector<unsigned char> gam2;    // per coarse id: on Gamma_2
+  std::vector<double> w2;             // per coarse id: weight (1 inside a block)
+  std::vector<int> slot_ptr, slot_ent;  // coarse id -> its block-space slots (ascending block)
+  std::vector<int> oobj;              // object slot -> level-2 object
+  std::vector<int> obj_ptr, obj_ent;  // level-2 object -> its object slots (ascending block)
+  std::vector<int> orow_ptr, orow_ent;  // object slot -> block-space slots of the object's DOFs
+  std::vector<int> sub2blk;           // level-1 local-coarse entry (lc index) -> block-space slot
+  std::vector<int> nfront_of, dfront_of;   // block -> front of plan N / D (-1: none)
+  MFPlan N, D, C;
+  // device
+  int *d_boff = nullptr, *d_bn = nullptr, *d_ooff = nullptr, *d_bm = nullptr, *d_bsub_ptr = nullptr,
+      *d_bsub = nullptr, *d_bgid = nullptr, *d_iidx = nullptr, *d_igid = nullptr, *d_slot_ptr = nullptr,
+      *d_slot_ent = nullptr, *d_oobj = nullptr, *d_obj_ptr = nullptr, *d_obj_ent = nullptr,
+      *d_orow_ptr = nullptr, *d_orow_ent = nullptr, *d_sub2blk = nullptr, *d_nfront = nullptr,
+      *d_dfront = nullptr, *d_bcolor_list = nullptr;
+  std::vector<int> color_off, color_cnt;   // blocks by colour (no two of one colour share an object)
+  unsigned char* d_gam2 = nullptr;
+  double *d_w2 = nullptr, *rho = nullptr, *X = nullptr, *Psi = nullptr, *Acck = nullptr;
+  long long *d_accoff = nullptr;
+  std::vector<long long> accoff;      // per block: offset of its m x m level-2 matrix
+  // apply work vectors
+  double *bI = nullptr, *uIb = nullptr, *sI = nullptr, *u = nullptr, *tl = nullptr, *t = nullptr, *rb = nullptr,
+         *y = nullptr, *v = nullptr, *rs = nullptr, *rcc = nullptr, *ucc = nullptr, *vg = nullptr;
+  double flops = 0;                   // factorisation multiply-adds of the three plans
+};
+
+void ml_plan(MLPlan& P, int g, const int nsub[3], const std::vector<SubDesc>& subs, const std::vector<LocalCoarse>& lc,
+             int nc, const std::vector<int>& cptr, const std::vector<int2>& cent);
+void ml_setup(MLPlan& P, const LocalLaunch& L, const std::function<void*(size_t)>& alloc,
+              const std::function<void*(size_t)>& tmp_alloc, int* err, cudaStream_t st);
+void ml_apply(const MLPlan& P, const LocalLaunch& L, const int* cptr, const int2* cent, const double* rc, double* uc,
+              cudaStream_t st);
 
 // stencil.cu
 void launch_operator(const MeshDev& m, const double* alpha, const double* x, double* y, double* dot_partial,
