@@ -121,7 +121,8 @@ typedef struct {
  * interface holds the coarse DOFs shared by two or more blocks, grouped into
  * level-2 objects by the set of blocks sharing them (one constraint each: the
  * mean of the object's coarse values), with weights 1 / (blocks sharing the
- * DOF) and an exact level-2 coarse solve.  All of it FP64.  B stays SPD;
+ * DOF) (BDDC_W_CARD) or diagonal stiffness scaling, the coarse-level analogue
+ * of Remark 1 (BDDC_W_RHO), and an exact level-2 coarse solve.  All of it FP64.  B stays SPD;
  * the PCG iteration count grows (the condition number gains the coarse
  * level's factor) while the coarse set-up and solve shrink.  Its work
  * vectors are allocated at setup, so the allocation-free apply takes it too. */

@@ -19,7 +19,11 @@ with the coarse problem in the place of the fine one:
     them (for box blocks each such set is connected), typed by its size (2
     face, 3 or 4 edge, more vertex), all selected, each constraint the mean
     of the object's coarse DOF values (a one-DOF object: its value);
-  * weights: 1 / (number of blocks sharing the DOF) (eq. (W) with blocks);
+  * weights: 1 / (number of blocks sharing the DOF) (eq. (W) with blocks),
+    or, with Remark 1's rho-weights on the first level, stiffness scaling
+    on the second, the coarse-level analogue of Remark 1 (the coarse level
+    has no coefficient of its own): delta_k(j) = (A_k)_jj / sum over the
+    blocks k' sharing j of (A_k')_jj;
   * the level-2 coarse problem (one DOF per level-2 object) solved exactly.
 
 M2 is then a BDDC preconditioner of A_c and the three-level preconditioner
@@ -38,9 +42,9 @@ import scipy.linalg as sla
 
 
 class CoarseBDDC:
-    def __init__(self, ref, nsub: Sequence[int], g: int):
+    def __init__(self, ref, nsub: Sequence[int], g: int, weights: str = "card"):
         """ref: an oracle BDDCSO; nsub: subdomains per axis; g: block width in
-        subdomains."""
+        subdomains; weights: "card" or "stiffness" (see the module text)."""
         bases, _, Ac, _ = ref.setup_two_level()
         self.Ac = np.asarray(Ac.todense()) if hasattr(Ac, "todense") else np.asarray(Ac)
         nc = ref.n_coarse
@@ -76,7 +80,16 @@ class CoarseBDDC:
             self.bdofs.append(d)
             self.Ab.append(A)
         self.gamma2 = np.array([len(b) >= 2 for b in self.bset])
-        self.w2 = np.array([1.0 / len(b) if len(b) >= 2 else 1.0 for b in self.bset])
+        # weights per block on its own DOFs
+        if weights == "card":
+            self.wb = [np.array([1.0 / len(self.bset[int(j)]) for j in d]) for d in self.bdofs]
+        elif weights == "stiffness":
+            dsum = np.zeros(nc)
+            for d, A in zip(self.bdofs, self.Ab):
+                np.add.at(dsum, d, np.diag(A))
+            self.wb = [np.diag(A) / dsum[d] for d, A in zip(self.bdofs, self.Ab)]
+        else:
+            raise ValueError(weights)
         # level-2 objects: Gamma_2 DOFs grouped by their block set
         groups: Dict[frozenset, List[int]] = {}
         for j in range(nc):
@@ -129,7 +142,7 @@ class CoarseBDDC:
         vg = np.zeros(self.nc)
         for k, d in enumerate(self.bdofs):
             gl = self.gamma2[d]
-            np.add.at(vg, d[gl], self.w2[d[gl]] * v_blocks[k][gl])
+            np.add.at(vg, d[gl], self.wb[k][gl] * v_blocks[k][gl])
         t = self.Ac @ vg
         t[self.gamma2] = 0.0
         return uI + vg - self._interior(t)
@@ -138,8 +151,8 @@ class CoarseBDDC:
         uI = self._interior(r)
         res = r - self.Ac @ uI
         loc = []
-        for d in self.bdofs:
-            rk = np.where(self.gamma2[d], self.w2[d] * res[d], 0.0)
+        for k, d in enumerate(self.bdofs):
+            rk = np.where(self.gamma2[d], self.wb[k] * res[d], 0.0)
             loc.append(rk)
         return uI, loc
 

@@ -1093,8 +1093,8 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
     const int nsub3[3] = {(int)h->ax[0].slab_lo.size(), (int)h->ax[1].slab_lo.size(), (int)h->ax[2].slab_lo.size()};
     ml_plan(h->ml, h->opt.ml_block, nsub3, h->subs, h->lc, nc, h->h_cptr, h->h_cent);
     CK(cudaEventRecord(ev[5], st));
-    ml_setup(h->ml, L, [h](size_t b) { return h->dalloc(b); }, [h](size_t b) { return h->dalloc(b, true); }, h->err,
-             st);
+    ml_setup(h->ml, L, [h](size_t b) { return h->dalloc(b); }, [h](size_t b) { return h->dalloc(b, true); },
+             h->opt.weights == BDDC_W_RHO, h->err, st);
     h->factor_bytes += 2 * sizeof(double) * (size_t)(h->ml.N.spool + h->ml.D.spool + h->ml.C.spool);
     CK(cudaEventRecord(ev[6], st));
   } else {

@@ -227,8 +227,8 @@ void configure_mf_kernels();
 // coarse problem with blocks of g x g x g subdomains (Section 6).  Coarse
 // DOFs shared by two or more blocks form the coarse interface Gamma_2; they
 // are grouped into level-2 objects by the set of blocks sharing them, each
-// constraint the mean of the object's coarse values; weights 1 / (blocks
-// sharing the DOF).  Dense FP64 throughout, on independent multifrontal
+// constraint the mean of the object's coarse values; weights per block slot
+// (w2s): 1 / (blocks sharing the DOF) or diagonal stiffness scaling.  Dense FP64 throughout, on independent multifrontal
 // fronts: N, the blocks' augmented matrices A_k + rho_k C_k^T C_k (exact for
 // the constrained problems, C_k w being prescribed); D, the blocks' interior
 // matrices; C, the level-2 coarse matrix.
@@ -257,7 +257,7 @@ struct MLPlan {
       *d_dfront = nullptr, *d_bcolor_list = nullptr;
   std::vector<int> color_off, color_cnt;   // blocks by colour (no two of one colour share an object)
   unsigned char* d_gam2 = nullptr;
-  double *d_w2 = nullptr, *rho = nullptr, *X = nullptr, *Psi = nullptr, *Acck = nullptr;
+  double *d_w2 = nullptr, *w2s = nullptr, *rho = nullptr, *X = nullptr, *Psi = nullptr, *Acck = nullptr;
   long long *d_accoff = nullptr;
   std::vector<long long> accoff;      // per block: offset of its m x m level-2 matrix
   // apply work vectors
@@ -269,7 +269,7 @@ struct MLPlan {
 void ml_plan(MLPlan& P, int g, const int nsub[3], const std::vector<SubDesc>& subs, const std::vector<LocalCoarse>& lc,
              int nc, const std::vector<int>& cptr, const std::vector<int2>& cent);
 void ml_setup(MLPlan& P, const LocalLaunch& L, const std::function<void*(size_t)>& alloc,
-              const std::function<void*(size_t)>& tmp_alloc, int* err, cudaStream_t st);
+              const std::function<void*(size_t)>& tmp_alloc, int stiffness, int* err, cudaStream_t st);
 void ml_apply(const MLPlan& P, const LocalLaunch& L, const int* cptr, const int2* cent, const double* rc, double* uc,
               cudaStream_t st);
 

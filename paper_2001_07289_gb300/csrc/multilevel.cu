@@ -9,7 +9,10 @@
 //   * V1 = the block-interior coarse DOFs, V2 = W-tilde_2 with one
 //     constraint per level-2 object (Gamma_2 DOFs with equal block sets),
 //     the mean of the object's coarse values;
-//   * weights 1 / (blocks sharing the DOF); the level-2 coarse problem exact.
+//   * weights 1 / (blocks sharing the DOF), or with Remark 1's rho-weights on
+//     the first level stiffness scaling on the second (the diagonal of A_k
+//     over its sum across the blocks sharing the DOF); the level-2 coarse
+//     problem exact.
 // Everything is FP64 and dense per block, factored as independent fronts of
 // the multifrontal code (coarse_mf.cu): every tile of every block's front
 // goes to its own CTA, and one solve call treats all blocks.  A floating
@@ -263,6 +266,30 @@ __global__ void k_ml_penalty(const int* __restrict__ boff, const int* __restrict
   }
 }
 
+// Level-2 weights per block-space slot: the diagonal of A_k (before the
+// augmented terms) into dsl, then w = 1 / (blocks sharing the DOF) or
+// dsl / (sum of dsl over the blocks sharing the DOF).
+__global__ void k_ml_diag(const int* __restrict__ boff, const int* __restrict__ bn, const int* __restrict__ nfront,
+                          const long long* __restrict__ nfoff, const double* __restrict__ FN, double* __restrict__ dsl) {
+  const int k = blockIdx.x;
+  if (nfront[k] < 0) return;
+  const int n = bn[k];
+  const double* A = FN + nfoff[nfront[k]];
+  for (int p = threadIdx.x; p < n; p += blockDim.x) dsl[boff[k] + p] = A[(long long)p * n + p];
+}
+
+__global__ void k_ml_slot_weights(const int* __restrict__ bgid, const int* __restrict__ slot_ptr,
+                                  const int* __restrict__ slot_ent, const double* __restrict__ dsl, int stiffness,
+                                  double* __restrict__ w, int NB) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < NB; s += gridDim.x * blockDim.x) {
+    const int g = bgid[s], e0 = slot_ptr[g], e1 = slot_ptr[g + 1];
+    if (!stiffness) { w[s] = 1.0 / (double)(e1 - e0); continue; }
+    double sum = 0.0;
+    for (int e = e0; e < e1; ++e) sum += dsl[slot_ent[e]];
+    w[s] = dsl[s] / sum;
+  }
+}
+
 // column c of C^T in every block's space (zero where a block has fewer rows)
 __global__ void k_ml_rhs_col(const int* __restrict__ boff, const int* __restrict__ bn, const int* __restrict__ ooff,
                              const int* __restrict__ bm, const int* __restrict__ orow_ptr,
@@ -355,11 +382,11 @@ __global__ void k_ml_local_matvec(const SubDesc* __restrict__ subs, const LocalC
 
 // r_k = D_2 R_k (r_c - A_c u_I) on Gamma_2, zero inside the blocks
 __global__ void k_ml_block_rhs(const int* __restrict__ bgid, const unsigned char* __restrict__ gam2,
-                               const double* __restrict__ w2, const double* __restrict__ rc,
+                               const double* __restrict__ w2s, const double* __restrict__ rc,
                                const double* __restrict__ t, double* __restrict__ rb, int NB) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < NB; s += gridDim.x * blockDim.x) {
     const int g = bgid[s];
-    rb[s] = gam2[g] ? w2[g] * (rc[g] - t[g]) : 0.0;
+    rb[s] = gam2[g] ? w2s[s] * (rc[g] - t[g]) : 0.0;
   }
 }
 
@@ -378,15 +405,16 @@ __global__ void k_ml_psiT(const int* __restrict__ boff, const int* __restrict__ 
   }
 }
 
-// dst[i] = scale_i sum over ent[ptr[i] .. ptr[i+1]) of src (mask: 0 -> dst 0)
+// dst[i] = sum over ent[ptr[i] .. ptr[i+1]) of w[ent] src[ent] (w NULL: 1;
+// mask: 0 -> dst 0), in the order of the list
 __global__ void k_ml_csr_sum(const int* __restrict__ ptr, const int* __restrict__ ent, const double* __restrict__ src,
-                             const double* __restrict__ scale, const unsigned char* __restrict__ mask,
+                             const double* __restrict__ w, const unsigned char* __restrict__ mask,
                              double* __restrict__ dst, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (mask && !mask[i]) { dst[i] = 0.0; continue; }
     double s = 0.0;
-    for (int e = ptr[i]; e < ptr[i + 1]; ++e) s += src[ent[e]];
-    dst[i] = scale ? scale[i] * s : s;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) s += (w ? w[ent[e]] : 1.0) * src[ent[e]];
+    dst[i] = s;
   }
 }
 
@@ -428,7 +456,7 @@ inline int grid_of_n(long long n) { return (int)std::max<long long>(1, std::min<
 }  // namespace
 
 void ml_setup(MLPlan& P, const LocalLaunch& L, const std::function<void*(size_t)>& alloc,
-              const std::function<void*(size_t)>& tmp_alloc, int* err, cudaStream_t st) {
+              const std::function<void*(size_t)>& tmp_alloc, int stiffness, int* err, cudaStream_t st) {
   const int NBk = P.nblock;
   P.d_boff = up(P.boff, alloc, st);
   P.d_bn = up(P.bn, alloc, st);
@@ -469,6 +497,14 @@ void ml_setup(MLPlan& P, const LocalLaunch& L, const std::function<void*(size_t)
   k_ml_assemble<<<NBk, BDDC_THREADS, 0, st>>>(L.subs, L.Ac, P.d_bsub_ptr, P.d_bsub, P.d_sub2blk, P.d_boff, P.d_bn,
                                              P.d_iidx, P.d_nfront, P.d_dfront, P.N.d_foff, P.D.d_foff, P.D.d_np,
                                              P.N.F, P.D.F);
+  {
+    double* dsl = (double*)tmp_alloc(sizeof(double) * (size_t)std::max(P.NB, 1));
+    P.w2s = (double*)alloc(sizeof(double) * (size_t)std::max(P.NB, 1));
+    BDDC_COUNT(2);
+    k_ml_diag<<<NBk, BDDC_THREADS, 0, st>>>(P.d_boff, P.d_bn, P.d_nfront, P.N.d_foff, P.N.F, dsl);
+    k_ml_slot_weights<<<grid_of_n(P.NB), 256, 0, st>>>(P.d_bgid, P.d_slot_ptr, P.d_slot_ent, dsl, stiffness, P.w2s,
+                                                       P.NB);
+  }
   k_ml_penalty<<<NBk, BDDC_THREADS, 0, st>>>(P.d_boff, P.d_bn, P.d_ooff, P.d_bm, P.d_orow_ptr, P.d_orow_ent,
                                             P.d_nfront, P.N.d_foff, P.N.F, P.rho);
   mf_factor(P.N, err, st, nullptr, nullptr, nullptr);
@@ -543,7 +579,7 @@ void ml_apply(const MLPlan& P, const LocalLaunch& L, const int* cptr, const int2
   BDDC_COUNT(2);
   k_ml_local_matvec<<<L.nsub, BDDC_THREADS, 0, st>>>(L.subs, L.lc, L.Ac, P.u, P.tl);
   launch_coarse_gather(cptr, cent, P.tl, P.t, nc, st);
-  k_ml_block_rhs<<<grid_of_n(P.NB), 256, 0, st>>>(P.d_bgid, P.d_gam2, P.d_w2, rc, P.t, P.rb, P.NB);
+  k_ml_block_rhs<<<grid_of_n(P.NB), 256, 0, st>>>(P.d_bgid, P.d_gam2, P.w2s, rc, P.t, P.rb, P.NB);
   // level-2 coarse correction
   if (P.ncc > 0) {
     BDDC_COUNT(2);
@@ -559,7 +595,7 @@ void ml_apply(const MLPlan& P, const LocalLaunch& L, const int* cptr, const int2
       P.d_boff, P.d_bn, P.d_ooff, P.d_bm, P.d_orow_ptr, P.d_orow_ent, P.d_oobj, P.Psi, std::max(P.NB, 1), P.ucc,
       P.y, P.v);
   // v_Gamma = sum_k R_k^T D_2 v_k, then the harmonic extension into the blocks
-  k_ml_csr_sum<<<grid_of_n(nc), 256, 0, st>>>(P.d_slot_ptr, P.d_slot_ent, P.v, P.d_w2, P.d_gam2, uc, nc);
+  k_ml_csr_sum<<<grid_of_n(nc), 256, 0, st>>>(P.d_slot_ptr, P.d_slot_ent, P.v, P.w2s, P.d_gam2, uc, nc);
   if (P.NI > 0) {
     BDDC_COUNT(4);
     k_ml_local_matvec<<<L.nsub, BDDC_THREADS, 0, st>>>(L.subs, L.lc, L.Ac, uc, P.tl);

@@ -1,7 +1,7 @@
 """Multilevel BDDC-SO on the GPU (options.ml_block = g: the coarse problem
 preconditioned by BDDC on blocks of g^3 subdomains, Section 6) against the
 oracle's three-level preconditioner (oracle/multilevel.py) on the same
-inputs: one application (1e-10 FP64, 2e-5 mixed) and PCG (iterations within
+inputs (level-2 weights: cardinality, or stiffness scaling with rho-weights): one application (1e-10 FP64, 2e-5 mixed) and PCG (iterations within
 1 / 2 of the oracle's, solution 1e-10 / 1e-8); the level-2 sizes; and one
 block holding every subdomain, where the coarse level is the exact coarse
 solve and the apply equals the two-level one to rounding."""
@@ -31,7 +31,7 @@ def case(name):
         a = inputs.alpha_loguniform(nx, ny, nz, -1, 1, 8)
         p = inputs.box_problem(nx, ny, nz, cuts, L, alpha=a, weights=w, rtol=1e-10)
         ref = orc.build(p)
-        m2 = ml.CoarseBDDC(ref, nsub, g)
+        m2 = ml.CoarseBDDC(ref, nsub, g, "stiffness" if w == "rho" else "card")
         res = orc.pcg(ref.operator, lambda r: ref.apply(r, coarse=m2.apply), p.b, p.rtol)
         _cache[name] = (p, ref, m2, res, g)
     return _cache[name]

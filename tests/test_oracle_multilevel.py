@@ -4,7 +4,9 @@ the coarse problem A_c with blocks of subdomains.
 - the two-level form (level-2 basis Psi, exact level-2 coarse solve) equals
   Definition 1 solved as one global constrained system on the blocks;
 - M2 is a BDDC preconditioner of A_c: symmetric, lambda_min(M2 A_c) >= 1
-  (the multispace bound behind Theorem 1, now on the coarse level);
+  (the multispace bound behind Theorem 1, now on the coarse level), with
+  cardinality and with stiffness-scaled weights (each a partition of unity:
+  the bound needs only that);
 - one block holding every subdomain: no coarse interface, M2 = A_c^{-1}, so
   the three-level preconditioner is the two-level one;
 - the three-level preconditioner B3 is symmetric with lambda_min(B3 A) >= 1,
@@ -26,9 +28,10 @@ CASES = {
 def build(name):
     nx, ny, nz, cuts, L, nsub, g = CASES[name]
     a = inputs.alpha_loguniform(nx, ny, nz, -1, 1, 4)
-    p = inputs.box_problem(nx, ny, nz, cuts, L, alpha=a, weights="rho" if name == "rho" else "card")
+    rho = name == "rho"
+    p = inputs.box_problem(nx, ny, nz, cuts, L, alpha=a, weights="rho" if rho else "card")
     ref = orc.build(p)
-    return p, ref, ml.CoarseBDDC(ref, nsub, g)
+    return p, ref, ml.CoarseBDDC(ref, nsub, g, "stiffness" if rho else "card")
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -42,7 +45,7 @@ def test_two_level_form_equals_definition(name):
         assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
 
 
-@pytest.mark.parametrize("name", ["uniform", "ragged"])
+@pytest.mark.parametrize("name", ["uniform", "ragged", "rho"])
 def test_coarse_level_is_bddc(name):
     _, ref, m2 = build(name)
     M = np.array([m2.apply(e) for e in np.eye(ref.n_coarse)]).T
@@ -83,3 +86,12 @@ def test_three_level_spectrum_and_pcg():
     r3 = orc.pcg(ref.operator, lambda r: ref.apply(r, coarse=m2.apply), p.b, 1e-10)
     assert r3.converged and r3.iterations >= r2.iterations
     assert np.linalg.norm(r3.x - r2.x) <= 1e-9 * np.linalg.norm(r2.x)
+
+
+def test_weights_partition_of_unity():
+    for name, kind in (("ragged", "card"), ("rho", "stiffness")):
+        _, ref, m2 = build(name)
+        tot = np.zeros(ref.n_coarse)
+        for d, w in zip(m2.bdofs, m2.wb):
+            np.add.at(tot, d, w)
+        assert np.abs(tot - 1).max() < 1e-13
