@@ -14,7 +14,8 @@ n_free * N / time-to-solution.  Extra keys: preconditioner applies/s and MDOF/s
 (100 back-to-back bddc_apply), setup phases, iterations, roofline of the
 dominant phase, the oracle as CPU baseline, and end-to-end numbers through
 bddc_solve_host with host buffers; and (--no-workloads to skip) one timed
-step of each other workload (channels96, jitter128, adjoint64) on both paths,
+step of each other workload (channels96, jitter128, adjoint64, and jitter128 with the
+multilevel coarse level) on both paths,
 and Section 5.2's contrast study on the synthetic channels (channels40).
 
 --impl reference times the FP64 CPU oracle (test infrastructure written from
@@ -47,6 +48,8 @@ WORKLOADS = {
     "adjoint64": (4, "adjoint64 forward solve: 64^3, 4^3 subdomains of 16^3, L=4h, log alpha Gaussian "
                      "field, f=1, PCG rtol 1e-10"),
 }
+# the same workloads with the multilevel coarse level (blocks of g^3 subdomains)
+ML_WORKLOADS = {"jitter128_ml2": ("jitter128", 2)}
 FP64_PEAK_TFLOPS = 1.25    # GB300 FP64 (FMA and DMMA) nominal; probe measured 1.19
 
 
@@ -397,6 +400,8 @@ def main():
     if not args.no_workloads and args.workload == "poisson48" and world == 1:
         for name in ("channels96", "jitter128", "adjoint64"):
             workloads[name] = run_workload(name, flush, stream)
+        for name, (base, g) in ML_WORKLOADS.items():
+            workloads[name] = run_workload(base, flush, stream, ml_block=g)
         workloads["channels40"] = run_channels(flush, stream)
 
     if rank != 0:
@@ -508,13 +513,17 @@ def main():
         dist.destroy_process_group()
 
 
-def run_workload(name, flush, stream):
+def run_workload(name, flush, stream, ml_block=0):
     """One warm-up and one timed step (setup + PCG to the workload's rtol, L2
-    flushed before it) on each precision, and ten preconditioner applies."""
+    flushed before it) on each precision, and ten preconditioner applies;
+    ml_block > 0: the multilevel coarse level with blocks of ml_block^3
+    subdomains."""
     import torch
     from paper_2001_07289_gb300 import inputs
     from paper_2001_07289_gb300.bddc import BDDC
     idx, desc = WORKLOADS[name]
+    if ml_block:
+        desc += f"; multilevel, coarse level on blocks of {ml_block}^3 subdomains"
     p = inputs.workload(idx)
     alpha = torch.from_numpy(p.alpha).cuda()
     b = torch.from_numpy(p.b).cuda()
@@ -525,7 +534,7 @@ def run_workload(name, flush, stream):
             flush.fill_(5.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            pre = BDDC.from_problem(p, alpha=alpha, precision=prec, use_graph=True, maxit=1000)
+            pre = BDDC.from_problem(p, alpha=alpha, precision=prec, use_graph=True, maxit=1000, ml_block=ml_block)
             _, st = pre.solve(b, p.rtol, out=x)
             e1.record(stream)
             e1.synchronize()
@@ -548,6 +557,7 @@ def run_workload(name, flush, stream):
                      "iterations": st["iterations"], "converged": st["converged"],
                      "setup_ms": round(info["setup_ms"], 2), "solve_ms": round(st["solve_ms"], 2),
                      "setup_phases_ms": [round(v, 2) for v in info["phase_ms"]], "n_coarse": info["n_coarse"],
+                     "ml_blocks": info["ml_blocks"], "ml_coarse2": info["ml_coarse2"],
                      "precond_apply_ms": round(apply_ms, 4),
                      "apply_mdofs": round(p.n_free * 1e3 / apply_ms / 1e6, 2)}
     return out
