@@ -570,8 +570,8 @@ k_btsolve_multi(const SubDesc* __restrict__ subs, const T* __restrict__ fac, T* 
                 T* __restrict__ scratch, long long scratch_stride) {
   extern __shared__ __align__(128) unsigned char smraw[];
   DenseSmem<T>& sm = *reinterpret_cast<DenseSmem<T>*>(smraw);
-  const SubDesc s = subs[blockIdx.x];
-  const int c0 = blockIdx.y * CW;
+  const SubDesc s = subs[blockIdx.y];   // chunks of one subdomain launch side by side (L2 reuse of its factor)
+  const int c0 = blockIdx.x * CW;
   if (c0 >= s.nc) return;
   const int cw = min(CW, s.nc - c0);
   const Grid g = grid_of(s, 1);
@@ -579,7 +579,7 @@ k_btsolve_multi(const SubDesc* __restrict__ subs, const T* __restrict__ fac, T* 
   const long long SS = slot_stride(Q);
   const T* base = fac + s.offN;
   T* Yb = Y + s.offY + c0;
-  T* U = scratch + ((long long)blockIdx.x * gridDim.y + blockIdx.y) * scratch_stride;   // Q x cw
+  T* U = scratch + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * scratch_stride;   // Q x cw
   for (int k = 1; k < nz; ++k) {
     T* Yk = Yb + (long long)k * Q * ld;
     cta_gemm<T>(Q, cw, Q, T(1), base + (long long)(k - 1) * SS, Q, false, Yk - (long long)Q * ld, ld, false, T(0),
@@ -821,8 +821,8 @@ k_btsolve_multi_tc(const SubDesc* __restrict__ subs, const float* __restrict__ f
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bars[4];
   __shared__ uint32_t tmem_slot;
-  const SubDesc s = subs[blockIdx.x];
-  const int c0 = blockIdx.y * TC_N;
+  const SubDesc s = subs[blockIdx.y];   // chunks of one subdomain launch side by side (L2 reuse of its factor)
+  const int c0 = blockIdx.x * TC_N;
   if (c0 >= s.nc) return;
   const int cw = min(TC_N, s.nc - c0);
   const Grid g = grid_of(s, 1);
@@ -830,7 +830,7 @@ k_btsolve_multi_tc(const SubDesc* __restrict__ subs, const float* __restrict__ f
   const long long SS = slot_stride(Q);
   const float* base = fac + s.offN;
   float* Yb = Y + s.offY + c0;
-  float* U = scratch + ((long long)blockIdx.x * gridDim.y + blockIdx.y) * scratch_stride;   // Q x TC_N
+  float* U = scratch + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * scratch_stride;   // Q x TC_N
   if (threadIdx.x == 0) {
     for (int q = 0; q < 4; ++q) mbar_init(&bars[q], 1);
     fence_barrier_init();
@@ -1665,13 +1665,13 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
       k_tc_pack<<<dim3(S, L.maxNzN, tc_kchunks(L.maxQN)), BDDC_THREADS, 0, st>>>(L.subs, (const float*)L.facN,
                                                                                (float*)L.tc);
       const int nch = (L.maxNc + TC_N - 1) / TC_N;
-      k_btsolve_multi_tc<<<dim3(S, nch), BDDC_THREADS, 2 * TC_STAGE_BYTES + 9 * 256 * sizeof(float), st>>>(
+      k_btsolve_multi_tc<<<dim3(nch, S), BDDC_THREADS, 2 * TC_STAGE_BYTES + 9 * 256 * sizeof(float), st>>>(
           L.subs_lpt, (const float*)L.facN, (const float*)L.tc, (float*)L.Y, (float*)L.mscratch, L.mscratch_stride,
           L.err);
       BDDC_COUNT(1);
     } else {
       const int nch = (L.maxNc + CW - 1) / CW;
-      k_btsolve_multi<T><<<dim3(S, nch), BDDC_THREADS, sm, st>>>(L.subs_lpt, facN, Y, (T*)L.mscratch,
+      k_btsolve_multi<T><<<dim3(nch, S), BDDC_THREADS, sm, st>>>(L.subs_lpt, facN, Y, (T*)L.mscratch,
                                                                    L.mscratch_stride);
     }
     k_constraint_means<T><<<dim3(S, 16), BDDC_THREADS, 0, st>>>(L.subs, L.lc, L.lcn, Y, G);
