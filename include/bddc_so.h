@@ -187,7 +187,7 @@ typedef struct {
                                  work vectors need a whole SM, bucket 1: the rest)  */
     int bucket_ring[2];       /* per bucket: depth of the bulk-copy ring (6: one
                                  CTA per SM, 4: two), tuned                         */
-    int bucket_ctas[2];       /* per bucket: CTAs per subdomain (1 or 2), tuned      */
+    int bucket_ctas[2];       /* per bucket: CTAs per subdomain (1, 2 or 4), tuned   */
     int ml_blocks;            /* multilevel: blocks of the coarse level (0: exact coarse solve) */
     int ml_coarse2;           /* multilevel: level-2 coarse DOFs (level-2 objects)  */
 } bddc_info_t;
@@ -256,10 +256,10 @@ int bddc_acceptable_paths(const bddc_mesh* mesh, const bddc_partition* part, con
  * longest first.  Autotuning: the first setup of a problem shape (precision,
  * subdomain count, largest planes, largest local coarse space, bucket sizes)
  * in the process times five preconditioner applies per candidate schedule of
- * each bucket (ring depth 6 or 4, one or two CTAs per subdomain) and keeps the
- * fastest (the default, ring depth 6 and one CTA, unless another is at least
- * 3 % faster) for every later handle of that shape; that first setup takes up
- * to about 48 applies longer. */
+ * each bucket (ring depth 6 or 4, one, two or four CTAs per subdomain) and
+ * keeps the fastest (the default, ring depth 6 and one CTA, unless another is
+ * at least 3 % faster) for every later handle of that shape; that first setup
+ * takes up to about 72 applies longer. */
 int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part,
                const bddc_options* opt, const double* alpha_dev, void* stream,
                bddc_handle** out);
@@ -307,10 +307,11 @@ int bddc_solve_host(const bddc_mesh* mesh, const bddc_partition* part,
 /* Sizes and timings of a handle. */
 int bddc_get_info(const bddc_handle* h, bddc_info_t* info);
 
-/* Overrides the autotuned apply schedule of a handle: ctas_per_subdomain = 1
- * or 2 CTAs per subdomain in the local solves of bddc_apply (2: a thread-block
- * cluster whose CTAs share each slot's rows), in every size bucket.  Both give
- * the same preconditioner up to the summation order of the partial sums.
+/* Overrides the autotuned apply schedule of a handle: ctas_per_subdomain = 1,
+ * 2 or 4 CTAs per subdomain in the local solves of bddc_apply (2, 4: a
+ * thread-block cluster whose CTAs share each slot's rows), in every size
+ * bucket.  All give the same preconditioner up to the summation order of the
+ * partial sums.
  * Drops the handle's captured PCG graph (recaptured by the next pcg_solve).
  * The paper has no counterpart; BDDC_ERR_ARG for other values. */
 int bddc_set_apply_schedule(bddc_handle* h, int ctas_per_subdomain);

@@ -274,7 +274,7 @@ class BDDC:
         return g
 
     def set_apply_schedule(self, ctas_per_subdomain: int):
-        """bddc_set_apply_schedule: 1 or 2 CTAs per subdomain in the apply's local solves."""
+        """bddc_set_apply_schedule: 1, 2 or 4 CTAs per subdomain in the apply's local solves."""
         _check(lib.bddc_set_apply_schedule(self._handle, int(ctas_per_subdomain)), self._handle)
 
     def set_bucket_schedule(self, bucket: int, ring_depth: int, ctas_per_subdomain: int):

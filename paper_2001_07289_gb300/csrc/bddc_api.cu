@@ -1232,7 +1232,7 @@ void tune_apply(bddc_handle* h, cudaStream_t st) {
     int bnb = NBUF, bcl = 1;
     for (int nb : {NBUF, SMALL_RING}) {
       if (nb != NBUF && apply_smem(L.bsize[b], nb, es) > SMALL_SMEM) continue;
-      for (int c = 1; c <= 2; ++c) {
+      for (int c : {1, 2, 4}) {
         L.bucket[b].nb = nb;
         L.bcluster[b] = c;
         apply(h, h->r, h->z, st);
@@ -1791,8 +1791,8 @@ extern "C" int bddc_solve_host(const bddc_mesh* mesh, const bddc_partition* part
 extern "C" int bddc_set_apply_schedule(bddc_handle* h, int ctas_per_subdomain) {
   if (!h) return BDDC_ERR_ARG;
   ABI_BEGIN
-  if (ctas_per_subdomain != 1 && ctas_per_subdomain != 2)
-    throw BddcError(BDDC_ERR_ARG, "ctas_per_subdomain must be 1 or 2");
+  if (ctas_per_subdomain != 1 && ctas_per_subdomain != 2 && ctas_per_subdomain != 4)
+    throw BddcError(BDDC_ERR_ARG, "ctas_per_subdomain must be 1, 2 or 4");
   CK(cudaSetDevice(h->device));
   CK(cudaDeviceSynchronize());
   for (int b = 0; b < MAX_BUCKETS; ++b) h->L.bcluster[b] = ctas_per_subdomain;
@@ -1806,8 +1806,8 @@ extern "C" int bddc_set_bucket_schedule(bddc_handle* h, int bucket, int ring_dep
   if (!h) return BDDC_ERR_ARG;
   ABI_BEGIN
   if (bucket < 0 || bucket >= MAX_BUCKETS) throw BddcError(BDDC_ERR_ARG, "bucket out of range");
-  if (ctas_per_subdomain != 1 && ctas_per_subdomain != 2)
-    throw BddcError(BDDC_ERR_ARG, "ctas_per_subdomain must be 1 or 2");
+  if (ctas_per_subdomain != 1 && ctas_per_subdomain != 2 && ctas_per_subdomain != 4)
+    throw BddcError(BDDC_ERR_ARG, "ctas_per_subdomain must be 1, 2 or 4");
   if (ring_depth != NBUF && ring_depth != SMALL_RING)
     throw BddcError(BDDC_ERR_ARG, "ring_depth must be " + std::to_string(NBUF) + " or " + std::to_string(SMALL_RING));
   if (ring_depth == SMALL_RING && apply_smem(h->L.bsize[bucket], SMALL_RING, h->local_double ? 8 : 4) > SMALL_SMEM)

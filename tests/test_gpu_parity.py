@@ -259,21 +259,23 @@ def test_zero_rhs():
 @pytest.mark.parametrize("name", ["poisson16", "ragged_L3", "jitter_L1"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
 def test_apply_schedules_agree(name, precision, tol):
-    """The apply's local solves on one CTA per subdomain and on a two-CTA
-    cluster (rows of every slot split, partial sums exchanged through
+    """The apply's local solves on one CTA per subdomain and on clusters of
+    two or four CTAs (rows of every slot split, partial sums exchanged through
     distributed shared memory) give the same preconditioner up to summation
-    order, on the same handle; the autotuned choice is one of the two."""
+    order, on the same handle; the autotuned choice is one of them (jitter_L1
+    has planes of a few nodes, where four CTAs leave some with no rows)."""
     p, _ = oracle_for(name)
     pre = gpu(p, precision)
-    assert pre.info()["apply_cluster"] in (1, 2)
+    assert pre.info()["apply_cluster"] in (1, 2, 4)
     r = cu(inputs.random_node_vector(p.nx, p.ny, p.nz, 21))
     out = {}
-    for c in (1, 2):
+    for c in (1, 2, 4):
         pre.set_apply_schedule(c)
         out[c] = pre.apply(r).cpu().numpy()
         x, st = pre.solve(cu(p.b), 1e-10, raise_on_noconv=False)
         out[(c, "it")] = st["iterations"]
-    assert np.abs(out[1] - out[2]).max() <= tol * np.abs(out[1]).max()
-    assert abs(out[(1, "it")] - out[(2, "it")]) <= 1
+    for c in (2, 4):
+        assert np.abs(out[1] - out[c]).max() <= tol * np.abs(out[1]).max()
+        assert abs(out[(1, "it")] - out[(c, "it")]) <= 1
     with pytest.raises(BddcError):
         pre.set_apply_schedule(3)
