@@ -49,7 +49,8 @@ WORKLOADS = {
                      "field, f=1, PCG rtol 1e-10"),
 }
 # the same workloads with the multilevel coarse level (blocks of g^3 subdomains)
-ML_WORKLOADS = {"jitter128_ml2": ("jitter128", 2)}
+ML_WORKLOADS = {"jitter128_ml2": ("jitter128", 2, 4, ("mixed", "fp64")),
+                "jitter128_L2_ml2": ("jitter128", 2, 2, ("mixed",))}
 FP64_PEAK_TFLOPS = 1.25    # GB300 FP64 (FMA and DMMA) nominal; probe measured 1.19
 
 
@@ -400,8 +401,8 @@ def main():
     if not args.no_workloads and args.workload == "poisson48" and world == 1:
         for name in ("channels96", "jitter128", "adjoint64"):
             workloads[name] = run_workload(name, flush, stream)
-        for name, (base, g) in ML_WORKLOADS.items():
-            workloads[name] = run_workload(base, flush, stream, ml_block=g)
+        for name, (base, g, L, precs) in ML_WORKLOADS.items():
+            workloads[name] = run_workload(base, flush, stream, ml_block=g, L=L, precisions=precs)
         workloads["channels40"] = run_channels(flush, stream)
 
     if rank != 0:
@@ -513,7 +514,7 @@ def main():
         dist.destroy_process_group()
 
 
-def run_workload(name, flush, stream, ml_block=0):
+def run_workload(name, flush, stream, ml_block=0, L=None, precisions=("mixed", "fp64")):
     """One warm-up and one timed step (setup + PCG to the workload's rtol, L2
     flushed before it) on each precision, and ten preconditioner applies;
     ml_block > 0: the multilevel coarse level with blocks of ml_block^3
@@ -524,12 +525,14 @@ def run_workload(name, flush, stream, ml_block=0):
     idx, desc = WORKLOADS[name]
     if ml_block:
         desc += f"; multilevel, coarse level on blocks of {ml_block}^3 subdomains"
-    p = inputs.workload(idx)
+    if L is not None:
+        desc = desc.replace("L=4h", f"L={L}h")
+    p = inputs.workload(idx, L=L)
     alpha = torch.from_numpy(p.alpha).cuda()
     b = torch.from_numpy(p.b).cuda()
     x = torch.zeros(p.n_nodes, dtype=torch.float64, device="cuda")
     out = {"workload": desc, "n_free": p.n_free}
-    for prec in ("mixed", "fp64"):
+    for prec in precisions:
         for k in range(2):
             flush.fill_(5.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
