@@ -366,45 +366,55 @@ struct MFDev {
   double *F, *Dinv, *W, *S, *T, *ST;
 };
 
-// One 32 x 32 FP64 output tile on one CTA of 256 threads, two rows by two
-// columns per thread: C = beta C + alpha sum_k A[i][k] op(B)[k][j] with
-// op(B)[k][j] = B[k][j] (TB false) or B[j][k] (TB true), k < K, row-major
-// operands; with lower only j <= i is written.  m, n <= 32.  K runs in 32-deep
-// slices staged in shared memory (As, Bs: 32 x 33 each); at two FP64 FMAs per
-// clock per SM the slice's arithmetic hides its loads, so every warp computes
-// rather than blocking registers.  beta = 0 does not read C.
+// One FNB x FNB FP64 output tile on one CTA of 256 threads (a 16 x 16 grid,
+// FNB/16 rows by FNB/16 columns per thread): C = beta C + alpha sum_k
+// A[i][k] op(B)[k][j] with op(B)[k][j] = B[k][j] (TB false) or B[j][k] (TB
+// true), k < K, row-major operands; with lower only j <= i is written.
+// m, n <= FNB.  K runs in FNB-deep slices staged in shared memory (As, Bs:
+// FNB x (FNB + 1) each); at two FP64 FMAs per clock per SM the slice's
+// arithmetic hides its loads, so every warp computes rather than blocking
+// registers.  beta = 0 does not read C.
+static_assert(FNB == 16 || FNB == 32, "tile width: 16 or 32");
 template <bool TB>
 __device__ void tile_gemm_f64(int m, int n, int K, double alpha, const double* __restrict__ A, long long lda,
                               const double* __restrict__ B, long long ldb, double beta, double* C, long long ldc,
                               bool lower, double* As, double* Bs) {
+  constexpr int TP = FNB / 16, LD = FNB + 1;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  double c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = 0.0;
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    const int kb = min(32, K - k0);
-    for (int idx = tid; idx < 1024; idx += BDDC_THREADS) {
-      const int r = idx >> 5, kk = idx & 31;
-      As[r * 33 + kk] = (r < m && kk < kb) ? A[r * lda + k0 + kk] : 0.0;
-      if (TB) Bs[kk * 33 + r] = (r < n && kk < kb) ? B[r * ldb + k0 + kk] : 0.0;
-      else Bs[r * 33 + kk] = (r < kb && kk < n) ? B[(long long)(k0 + r) * ldb + kk] : 0.0;
+  double acc[TP][TP];
+#pragma unroll
+  for (int a = 0; a < TP; ++a)
+#pragma unroll
+    for (int b = 0; b < TP; ++b) acc[a][b] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += FNB) {
+    const int kb = min(FNB, K - k0);
+    for (int idx = tid; idx < FNB * FNB; idx += BDDC_THREADS) {
+      const int r = idx / FNB, kk = idx % FNB;
+      As[r * LD + kk] = (r < m && kk < kb) ? A[r * lda + k0 + kk] : 0.0;
+      if (TB) Bs[kk * LD + r] = (r < n && kk < kb) ? B[r * ldb + k0 + kk] : 0.0;
+      else Bs[r * LD + kk] = (r < kb && kk < n) ? B[(long long)(k0 + r) * ldb + kk] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      const double a0 = As[(2 * ty) * 33 + kk], a1 = As[(2 * ty + 1) * 33 + kk];
-      const double b0 = Bs[kk * 33 + tx], b1 = Bs[kk * 33 + tx + 16];
-      c00 = fma(a0, b0, c00);
-      c01 = fma(a0, b1, c01);
-      c10 = fma(a1, b0, c10);
-      c11 = fma(a1, b1, c11);
+    for (int kk = 0; kk < FNB; ++kk) {
+      double av[TP], bv[TP];
+#pragma unroll
+      for (int q = 0; q < TP; ++q) {
+        av[q] = As[(TP * ty + q) * LD + kk];
+        bv[q] = Bs[kk * LD + tx + 16 * q];
+      }
+#pragma unroll
+      for (int a = 0; a < TP; ++a)
+#pragma unroll
+        for (int b = 0; b < TP; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
     __syncthreads();
   }
-  const double acc[2][2] = {{c00, c01}, {c10, c11}};
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < TP; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int r = 2 * ty + a, c = tx + 16 * b;
+    for (int b = 0; b < TP; ++b) {
+      const int r = TP * ty + a, c = tx + 16 * b;
       if (r < m && c < n && (!lower || c <= r)) {
         double* p = C + r * ldc + c;
         *p = (beta == 0.0) ? alpha * acc[a][b] : fma(beta, *p, alpha * acc[a][b]);
