@@ -76,3 +76,29 @@ def test_one_block_is_the_two_level_preconditioner():
     assert pre.info()["ml_blocks"] == 1 and pre.info()["ml_coarse2"] == 0
     z3 = pre.apply(r).cpu().numpy()
     assert np.abs(z3 - z2).max() <= 1e-11 * np.abs(z2).max()
+
+
+@pytest.mark.parametrize("sel,piece", [("f", False), ("vef", True), ("f", True)])
+def test_multilevel_with_other_sub_partitions(sel, piece):
+    """The second level on top of faces-only selections (floating subdomains
+    pinned by augmented-Lagrangian terms) and of label-given sub-subdomains
+    (synthetic channels, rho-weights, so stiffness-scaled level-2 weights):
+    FP64 apply and PCG against the oracle."""
+    if piece:
+        p = inputs.channels_problem(24, 3, 2, selection=sel, rtol=1e-10)
+    else:
+        a = inputs.alpha_loguniform(18, 18, 18, -1, 1, 6)
+        p = inputs.box_problem(18, 18, 18, [[6, 12]] * 3, 3, alpha=a, selection=sel, rtol=1e-10)
+    ref = orc.build(p)
+    m2 = ml.CoarseBDDC(ref, (3, 3, 3), 2, "stiffness" if p.weights == "rho" else "card")
+    pre = BDDC.from_problem(p, precision="fp64", ml_block=2)
+    assert pre.info()["ml_coarse2"] == m2.ncc
+    r = inputs.random_node_vector(p.nx, p.ny, p.nz, 3)
+    z = pre.apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    want = ref.apply(r, coarse=m2.apply)
+    assert np.abs(z - want).max() <= 1e-10 * np.abs(want).max()
+    x, st = pre.solve(torch.from_numpy(p.b).cuda(), p.rtol)
+    pre.close()
+    res = orc.pcg(ref.operator, lambda v: ref.apply(v, coarse=m2.apply), p.b, p.rtol)
+    assert st["converged"] and abs(st["iterations"] - res.iterations) <= 1
+    assert np.linalg.norm(x.cpu().numpy() - res.x) <= 1e-10 * np.linalg.norm(res.x)
