@@ -217,13 +217,14 @@ int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part,
  * acceptable path; all edge or all face subobjects on Gamma guarantee one).
  * Host only; alpha_host (nx*ny*nz elements, x fastest, may be NULL for
  * alpha = 1) gives each sub-subdomain rho = the mean of alpha over it.
- * A pair is two sub-subdomains of different subdomains whose closures share
- * a node off the Dirichlet boundary.  It is direct when it shares a selected
+ * A pair is two sub-subdomains of different subdomains around one interface
+ * node off the Dirichlet boundary.  It is direct when it shares a selected
  * edge or face object, or when every free node the two share is primal.
  * Otherwise it needs a path of sub-subdomains in which consecutive ones share
  * a face and either lie in one subdomain (continuity) or share a selected
  * face object or only primal free nodes; the path's quality is min(1, min of
  * rho over the path / min(rho_i, rho_j)) and the pair takes its best path's.
+ * Sub-subdomains are those of the partition (boxes of size L or labels).
  * Errors: BDDC_ERR_ARG as bddc_analyze; BDDC_ERR_UNSUPPORTED above 2^22
  * sub-subdomains. */
 typedef struct {
@@ -234,8 +235,9 @@ typedef struct {
     double min_ratio;          /* smallest best-path quality of the others (1 if none) */
     long long worst_pair[2];   /* a pair without a path, else one of min_ratio
                                   (-1 -1 when every pair is direct);
-                                  sub-subdomain ids a + na (b + nb c) of the
-                                  per-axis piece indices                    */
+                                  sub-subdomain ids: box pieces a + na (b +
+                                  nb c) of the per-axis piece indices, labels
+                                  renumbered by first element               */
 } bddc_paths_t;
 
 int bddc_acceptable_paths(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt,

@@ -186,10 +186,12 @@ def analyze(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int, h:
 
 
 def acceptable_paths(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int, alpha=None,
-                     selection="vef") -> dict:
+                     selection="vef", piece=None) -> dict:
     """bddc_acceptable_paths: host-only acceptable-path check of a selection;
-    alpha (nx*ny*nz element coefficients, x fastest) or None for alpha = 1."""
-    mesh, part, opt, keep = _structs(nx, ny, nz, 1.0 / nx, cuts, L, "fp64", "card", 2000, False, selection)
+    alpha (nx*ny*nz element coefficients, x fastest) or None for alpha = 1;
+    piece: optional per-element sub-subdomain labels (else boxes of L)."""
+    mesh, part, opt, keep = _structs(nx, ny, nz, 1.0 / nx, cuts, L, "fp64", "card", 2000, False, selection,
+                                     piece=piece)
     a = None
     if alpha is not None:
         a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(-1))

@@ -203,8 +203,6 @@ struct bddc_handle {
   std::vector<int> okind, ocell;
   std::vector<long long> onoff;
   std::vector<int> onodes;        // node coordinates (x, y, z) per object node
-  std::vector<int> item_objid;    // boxes of size L: item tuple -> coarse id or -1
-  int item_n[3] = {0, 0, 0};
   std::vector<int> lcn;           // local node lists of the coarse DOFs
   long long n_nodes = 0, n_free = 0;
   LocalLaunch L{};
@@ -428,11 +426,9 @@ void build_objects(bddc_handle* h, bool keep_v, bool keep_e, bool keep_f) {
   h->ocell.clear();
   h->onoff.assign(1, 0);
   h->onodes.clear();
-  h->item_objid.clear();
   if (!h->labels) {
     int nit[3];
-    for (int d = 0; d < 3; ++d) nit[d] = h->item_n[d] = ax[d].nitem();
-    h->item_objid.assign((size_t)nit[0] * nit[1] * nit[2], -1);
+    for (int d = 0; d < 3; ++d) nit[d] = ax[d].nitem();
     {
       // capacity: objects lie on the cut planes; at most the items of those planes
       long long nodes = 0, items = 0;
@@ -459,7 +455,6 @@ void build_objects(bddc_handle* h, bool keep_v, bool keep_e, bool keep_f) {
           const int pts = !(ix & 1) + !(iy & 1) + !(iz & 1);
           const int kind = pts == 3 ? 0 : (pts == 2 ? 1 : 2);
           if (!ok || !on_gamma || !keep(kind)) continue;
-          h->item_objid[ix + (size_t)nit[0] * (iy + (size_t)nit[1] * iz)] = (int)h->okind.size();
           h->okind.push_back(kind);
           for (int d = 0; d < 3; ++d) {
             const int sl = ax[d].slab[ax[d].item_lo[it[d]]];   // element right of the item's first node
@@ -1508,19 +1503,18 @@ extern "C" int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, c
   ABI_END(hnull)
 }
 
-// Acceptable paths (remark after Theorem 1).  Sub-subdomains are the tensor
-// pieces (a, b, c); two pieces touch when their indices differ by at most one
-// on every axis, and the items of the contact on an axis are the piece's
-// {lo point, interval, hi point} where the indices agree and the one point
-// between them where they differ.  A pair (pieces of different subdomains
-// whose contact holds a free node) is direct when the contact holds a
-// selected edge or face object or all its free nodes are primal.  Links:
-// pieces of one subdomain sharing a face (w is continuous inside a
-// subdomain), or pieces of two subdomains sharing a face that holds a
-// selected face object or only primal free nodes.  A path's bottleneck is the smallest rho on
-// it (ends included), so the best path of every pair is its path in a
-// maximum spanning forest of the links weighted by min(rho_u, rho_v)
-// (Kruskal), queried by binary lifting.
+// Acceptable paths (remark after Theorem 1), on the sub-subdomains of the
+// handle (box pieces or labels).  A pair is two pieces of different
+// subdomains around one interface node off the Dirichlet boundary; its
+// contact is open while one such node lies in no selected object.  Direct:
+// the two share a selected edge or face object (both in the object's set of
+// surrounding pieces) or their contact is not open.  Links: pieces sharing an
+// element face that lie in one subdomain (w is continuous inside a
+// subdomain), or lie in two and share a selected face object or a contact
+// that is not open.  A path's bottleneck is the smallest rho on it (ends
+// included), so the best path of every pair is its path in a maximum
+// spanning forest of the links weighted by min(rho_u, rho_v) (Kruskal),
+// queried by binary lifting.
 extern "C" int bddc_acceptable_paths(const bddc_mesh* mesh, const bddc_partition* part, const bddc_options* opt,
                                      const double* alpha_host, bddc_paths_t* out) {
   bddc_handle* hnull = nullptr;
@@ -1528,92 +1522,106 @@ extern "C" int bddc_acceptable_paths(const bddc_mesh* mesh, const bddc_partition
   if (!out) throw BddcError(BDDC_ERR_ARG, "out is NULL");
   std::unique_ptr<bddc_handle> h = make_handle(mesh, part, opt);
   build_metadata(h.get());
+  const bddc_mesh& M = h->mesh;
   const AxisHost* ax = h->ax;
-  int np[3];
-  for (int d = 0; d < 3; ++d) np[d] = (int)ax[d].piece_lo.size();
-  const long long P = (long long)np[0] * np[1] * np[2];
+  const long long P = h->n_pieces;
   if (P > (1LL << 22)) throw BddcError(BDDC_ERR_UNSUPPORTED, "more than 2^22 sub-subdomains");
-  if (h->labels) throw BddcError(BDDC_ERR_UNSUPPORTED, "the acceptable-path check takes box sub-subdomains (L)");
-  const int* nit = h->item_n;
-  const std::vector<int>& objid = h->item_objid;
-  auto pid = [&](int a, int b, int c) { return (long long)a + (long long)np[0] * (b + (long long)np[1] * c); };
-  // piece coefficient: the mean of alpha over the piece's elements (1 without alpha)
-  std::vector<double> rho(P, 1.0);
-  if (alpha_host) {
-    const bddc_mesh& M = h->mesh;
-    std::fill(rho.begin(), rho.end(), 0.0);
+  const int NX = M.nx + 1, NY = M.ny + 1;
+  const long long NE = (long long)M.nx * M.ny * M.nz;
+  // the piece of every element (the labels, or the box pieces)
+  std::vector<int> ep;
+  if (h->labels) {
+    ep = h->epiece;
+  } else {
+    ep.assign(NE, 0);
+    const int npx = (int)ax[0].piece_lo.size(), npy = (int)ax[1].piece_lo.size();
     for (int k = 0; k < M.nz; ++k)
       for (int j = 0; j < M.ny; ++j)
         for (int i = 0; i < M.nx; ++i)
-          rho[pid(ax[0].piece[i], ax[1].piece[j], ax[2].piece[k])] +=
-              alpha_host[i + (long long)M.nx * (j + (long long)M.ny * k)];
-    for (int c = 0; c < np[2]; ++c)
-      for (int b = 0; b < np[1]; ++b)
-        for (int a = 0; a < np[0]; ++a)
-          rho[pid(a, b, c)] /= (double)(ax[0].piece_hi[a] - ax[0].piece_lo[a]) *
-                               (ax[1].piece_hi[b] - ax[1].piece_lo[b]) * (ax[2].piece_hi[c] - ax[2].piece_lo[c]);
+          ep[i + (long long)M.nx * (j + (long long)M.ny * k)] = ax[0].piece[i] + npx * (ax[1].piece[j] + npy * ax[2].piece[k]);
   }
-  // contact items of piece q and offset o on one axis
-  auto contact = [](int q, int o, int* it) -> int {
-    if (o == 0) { it[0] = 2 * q; it[1] = 2 * q + 1; it[2] = 2 * q + 2; return 3; }
-    it[0] = o > 0 ? 2 * q + 2 : 2 * q;
-    return 1;
+  auto elem = [&](int i, int j, int k) { return ep[i + (long long)M.nx * (j + (long long)M.ny * k)]; };
+  // piece coefficient: the mean of alpha over the piece's elements (1 without alpha)
+  std::vector<double> rho(P, 1.0);
+  if (alpha_host) {
+    std::vector<double> sum(P, 0.0);
+    std::vector<long long> cnt(P, 0);
+    for (long long e = 0; e < NE; ++e) { sum[ep[e]] += alpha_host[e]; ++cnt[ep[e]]; }
+    for (long long q = 0; q < P; ++q) rho[q] = sum[q] / (double)cnt[q];
+  }
+  // primal nodes: the nodes of the selected objects
+  std::vector<unsigned char> primal((size_t)NX * NY * (M.nz + 1), 0);
+  for (size_t q = 0; q < h->onodes.size(); q += 3)
+    primal[nodeid(NX, NY, h->onodes[q], h->onodes[q + 1], h->onodes[q + 2])] = 1;
+  auto pieces_at = [&](int x, int y, int z, std::vector<int>& k) {
+    k.clear();
+    for (int dz = -1; dz <= 0; ++dz)
+      for (int dy = -1; dy <= 0; ++dy)
+        for (int dx = -1; dx <= 0; ++dx) k.push_back(elem(x + dx, y + dy, z + dz));
+    std::sort(k.begin(), k.end());
+    k.erase(std::unique(k.begin(), k.end()), k.end());
   };
-  auto slab = [&](int d, int q) { return ax[d].slab[ax[d].piece_lo[q]]; };
+  auto key = [&](long long a, long long b) { return a * P + b; };
+  // pairs around interface nodes, and which contacts are open
+  std::map<long long, char> pair_open;   // (a, b), a < b -> contact open
+  std::vector<int> k;
+  for (int z = 1; z < M.nz; ++z)
+    for (int y = 1; y < M.ny; ++y)
+      for (int x = 1; x < M.nx; ++x) {
+        if (!ax[0].theta[x] && !ax[1].theta[y] && !ax[2].theta[z]) continue;
+        pieces_at(x, y, z, k);
+        const bool open = !primal[nodeid(NX, NY, x, y, z)];
+        for (size_t a = 0; a < k.size(); ++a)
+          for (size_t b = a + 1; b < k.size(); ++b) {
+            if (h->piece_sub[k[a]] == h->piece_sub[k[b]]) continue;
+            char& o = pair_open[key(k[a], k[b])];
+            o = (char)(o | (open ? 1 : 0));
+          }
+      }
+  // selected edge and face objects: pairs of their surrounding pieces
+  std::map<long long, char> shares_obj;   // 1: edge or face object, 2: face object
+  for (size_t g = 0; g < h->okind.size(); ++g) {
+    if (h->okind[g] == 0) continue;
+    const long long q = 3 * h->onoff[g];
+    pieces_at(h->onodes[q], h->onodes[q + 1], h->onodes[q + 2], k);
+    for (size_t a = 0; a < k.size(); ++a)
+      for (size_t b = a + 1; b < k.size(); ++b) {
+        char& o = shares_obj[key(k[a], k[b])];
+        o = (char)std::max<int>(o, h->okind[g] == 2 ? 2 : 1);
+      }
+  }
   std::vector<std::pair<long long, long long>> pairs, links;
   std::vector<char> direct;
-  for (int c = 0; c < np[2]; ++c)
-    for (int b = 0; b < np[1]; ++b)
-      for (int a = 0; a < np[0]; ++a)
-        for (int oz = -1; oz <= 1; ++oz)
-          for (int oy = -1; oy <= 1; ++oy)
-            for (int ox = -1; ox <= 1; ++ox) {
-              const int q[3] = {a, b, c}, o[3] = {ox, oy, oz};
-              const int r[3] = {a + ox, b + oy, c + oz};
-              bool ok = true;
-              for (int d = 0; d < 3; ++d) ok = ok && r[d] >= 0 && r[d] < np[d];
-              if (!ok || pid(r[0], r[1], r[2]) <= pid(a, b, c)) continue;
-              bool same = true;
-              int nmove = 0;
-              for (int d = 0; d < 3; ++d) {
-                same = same && slab(d, q[d]) == slab(d, r[d]);
-                nmove += o[d] != 0;
-              }
-              if (same) {
-                if (nmove == 1) links.push_back({pid(a, b, c), pid(r[0], r[1], r[2])});
-                continue;
-              }
-              int it[3][3], n[3];
-              bool free_node = true;
-              for (int d = 0; d < 3; ++d) {
-                n[d] = contact(q[d], o[d], it[d]);
-                bool any = false;
-                for (int e = 0; e < n[d]; ++e) any = any || (!ax[d].empty(it[d][e]) && ax[d].item_kind[it[d][e]] != 3);
-                free_node = free_node && any;
-              }
-              if (!free_node) continue;
-              // every item tuple of the contact holding nodes off the Dirichlet
-              // boundary is an object on Gamma (one moving axis crosses a cut)
-              bool dir = false, face_link = false, all_primal = true;
-              for (int ez = 0; ez < n[2]; ++ez)
-                for (int ey = 0; ey < n[1]; ++ey)
-                  for (int ex = 0; ex < n[0]; ++ex) {
-                    const int ix = it[0][ex], iy = it[1][ey], iz = it[2][ez];
-                    if (ax[0].empty(ix) || ax[1].empty(iy) || ax[2].empty(iz) || ax[0].item_kind[ix] == 3 ||
-                        ax[1].item_kind[iy] == 3 || ax[2].item_kind[iz] == 3)
-                      continue;
-                    if (objid[ix + (long long)nit[0] * (iy + (long long)nit[1] * iz)] < 0) {
-                      all_primal = false;
-                      continue;
-                    }
-                    const int pts = !(ix & 1) + !(iy & 1) + !(iz & 1);
-                    if (pts <= 2) dir = true;
-                    if (pts == 1) face_link = true;
-                  }
-              pairs.push_back({pid(a, b, c), pid(r[0], r[1], r[2])});
-              direct.push_back(dir || all_primal);
-              if ((face_link || all_primal) && nmove == 1) links.push_back({pid(a, b, c), pid(r[0], r[1], r[2])});
-            }
+  for (const auto& pr : pair_open) {
+    const long long a = pr.first / P, b = pr.first % P;
+    auto it = shares_obj.find(pr.first);
+    pairs.push_back({a, b});
+    direct.push_back((it != shares_obj.end()) || !pr.second);
+  }
+  // links: element-face contacts
+  {
+    std::map<long long, char> seen;
+    auto contact = [&](int pa, int pb) {
+      if (pa == pb) return;
+      const long long a = std::min(pa, pb), b = std::max(pa, pb);
+      if (!seen.emplace(key(a, b), 1).second) return;
+      bool link = h->piece_sub[a] == h->piece_sub[b];
+      if (!link) {
+        auto it = shares_obj.find(key(a, b));
+        auto po = pair_open.find(key(a, b));
+        link = (it != shares_obj.end() && it->second == 2) || po == pair_open.end() || !po->second;
+      }
+      if (link) links.push_back({a, b});
+    };
+    for (int z = 0; z < M.nz; ++z)
+      for (int y = 0; y < M.ny; ++y)
+        for (int x = 0; x < M.nx; ++x) {
+          const int pe = elem(x, y, z);
+          if (x + 1 < M.nx) contact(pe, elem(x + 1, y, z));
+          if (y + 1 < M.ny) contact(pe, elem(x, y + 1, z));
+          if (z + 1 < M.nz) contact(pe, elem(x, y, z + 1));
+        }
+  }
   // maximum spanning forest (Kruskal), edge weight min(rho_u, rho_v)
   std::sort(links.begin(), links.end(), [&](const std::pair<long long, long long>& x,
                                             const std::pair<long long, long long>& y) {

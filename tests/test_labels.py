@@ -65,12 +65,24 @@ def test_label_errors(gb):
         gb.analyze(n, n, n, cuts, 4, piece=piece[:-1])
 
 
-def test_paths_refuse_labels(gb):
-    """The acceptable-path check is written for box sub-subdomains."""
-    p = inputs.channels_problem(20, 2, 2, per_axis=2)
-    import ctypes as C
-    mesh, part, opt, keep = gb._structs(20, 20, 20, 1.0 / 20, p.cuts, p.L, "fp64", "card", 100, False, "f",
-                                        piece=p.piece)
-    out = gb.Paths()
-    code = gb.lib.bddc_acceptable_paths(C.byref(mesh), C.byref(part), C.byref(opt), None, C.byref(out))
-    assert code == gb.BDDC_ERR_UNSUPPORTED
+@pytest.mark.parametrize("n,parts,ell,straddle", [(20, 2, 6, True), (20, 2, 6, False), (24, 3, 4, False)])
+@pytest.mark.parametrize("sel", ["f", "vef", "v"])
+def test_paths_with_labels_match_oracle(gb, n, parts, ell, straddle, sel):
+    """The acceptable-path check on label-given sub-subdomains (channels),
+    library against oracle: counts exactly, smallest quality to rounding."""
+    from oracle import paths
+    cuts = [inputs.uniform_cuts(n, parts)] * 3
+    if straddle:   # one bar along x across the cut plane y = n/2 (quality 10^-ell under faces only)
+        m = np.zeros((n, n, n), dtype=bool)
+        m[4:6, n // 2 - 1:n // 2 + 1, :] = True
+        mask = m.reshape(-1)
+    else:
+        mask = inputs.channel_mask(n, n, n, 3, 2, 11, cuts)
+    piece = inputs.material_pieces(n, n, n, cuts, mask)
+    alpha = np.where(mask, 10.0 ** ell, 1.0)
+    got = gb.acceptable_paths(n, n, n, cuts, n, alpha=alpha, selection=sel, piece=piece)
+    sub, _ = partition.box_labels(n, n, n, cuts, n)
+    ref = paths.acceptable_paths(n, n, n, sub, piece, alpha, sel)
+    for k in ("n_pieces", "n_pairs", "n_direct", "n_without_path"):
+        assert got[k] == ref[k], (k, got[k], ref[k])
+    assert got["min_ratio"] == pytest.approx(ref["min_ratio"], rel=1e-12)
