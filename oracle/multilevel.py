@@ -19,6 +19,10 @@ with the coarse problem in the place of the fine one:
     them (for box blocks each such set is connected), typed by its size (2
     face, 3 or 4 edge, more vertex), all selected, each constraint the mean
     of the object's coarse DOF values (a one-DOF object: its value);
+    with sub-blocks of s x s x s subdomains inside every block (BDDC-SO on
+    the coarse level: Section 6 points at the freedom to define subobjects
+    on every coarser level), the Gamma_2 DOFs are grouped by the set of
+    sub-blocks sharing them instead;
   * weights: 1 / (number of blocks sharing the DOF) (eq. (W) with blocks),
     or, with Remark 1's rho-weights on the first level, stiffness scaling
     on the second, the coarse-level analogue of Remark 1 (the coarse level
@@ -42,9 +46,10 @@ import scipy.linalg as sla
 
 
 class CoarseBDDC:
-    def __init__(self, ref, nsub: Sequence[int], g: int, weights: str = "card"):
+    def __init__(self, ref, nsub: Sequence[int], g: int, weights: str = "card", sub: int = 0):
         """ref: an oracle BDDCSO; nsub: subdomains per axis; g: block width in
-        subdomains; weights: "card" or "stiffness" (see the module text)."""
+        subdomains; weights: "card" or "stiffness" (see the module text); sub:
+        sub-block width in subdomains for level-2 subobjects (0: none)."""
         bases, _, Ac, _ = ref.setup_two_level()
         self.Ac = np.asarray(Ac.todense()) if hasattr(Ac, "todense") else np.asarray(Ac)
         nc = ref.n_coarse
@@ -52,12 +57,18 @@ class CoarseBDDC:
         nsx, nsy, nsz = nsub
         nbx, nby, nbz = (-(-nsx // g), -(-nsy // g), -(-nsz // g))
         self.nblock = nbx * nby * nbz
-        block_of_sub = []
+        block_of_sub, part_of_sub = [], []
         for i in range(nsx * nsy * nsz):
             sx, sy, sz = i % nsx, (i // nsx) % nsy, i // (nsx * nsy)
-            block_of_sub.append(sx // g + nbx * (sy // g + nby * (sz // g)))
+            b = sx // g + nbx * (sy // g + nby * (sz // g))
+            block_of_sub.append(b)
+            if sub:   # sub-block inside the block: local coordinates // sub
+                part_of_sub.append((b, (sx % g) // sub, (sy % g) // sub, (sz % g) // sub))
+            else:
+                part_of_sub.append((b,))
         # local coarse matrices and the blocks sharing each coarse DOF
         blocks_of: List[set] = [set() for _ in range(nc)]
+        parts_of: List[set] = [set() for _ in range(nc)]
         self.sub_dofs, self.sub_Ac = [], []
         for i, s in enumerate(ref.subs):
             gi = ref.coarse_dofs(i)
@@ -65,6 +76,7 @@ class CoarseBDDC:
             self.sub_Ac.append(bases[i].T @ (s.A @ bases[i]))
             for j in gi:
                 blocks_of[int(j)].add(block_of_sub[i])
+                parts_of[int(j)].add(part_of_sub[i])
         self.bset = [frozenset(b) for b in blocks_of]
         # block DOF sets (sorted) and assembled block matrices
         self.bdofs: List[np.ndarray] = []
@@ -94,7 +106,7 @@ class CoarseBDDC:
         groups: Dict[frozenset, List[int]] = {}
         for j in range(nc):
             if self.gamma2[j]:
-                groups.setdefault(self.bset[j], []).append(j)
+                groups.setdefault(frozenset(parts_of[j]), []).append(j)
         self.objs = [np.array(v, dtype=np.int64) for v in sorted(groups.values(), key=lambda v: v[0])]
         self.obj_blocks = [self.bset[int(o[0])] for o in self.objs]
         self.kind = np.array([2 if len(b) == 2 else (1 if len(b) <= 4 else 0) for b in self.obj_blocks])

@@ -95,3 +95,27 @@ def test_weights_partition_of_unity():
         for d, w in zip(m2.bdofs, m2.wb):
             np.add.at(tot, d, w)
         assert np.abs(tot - 1).max() < 1e-13
+
+
+@pytest.mark.parametrize("name", ["uniform", "ragged"])
+def test_level2_subobjects(name):
+    """Sub-blocks of one subdomain inside the blocks (subobjects on the coarse
+    level, Section 6): the two forms still agree, lambda_min(M2 A_c) >= 1, and
+    since every block-level constraint is implied by the finer ones W-tilde_2
+    shrinks, so lambda_max (the largest value of the BDDC Rayleigh quotient
+    over W-tilde_2) cannot grow."""
+    nx, ny, nz, cuts, L, nsub, g = CASES[name]
+    a = inputs.alpha_loguniform(nx, ny, nz, -1, 1, 4)
+    p = inputs.box_problem(nx, ny, nz, cuts, L, alpha=a)
+    ref = orc.build(p)
+    ev = {}
+    for sub in (0, 1):
+        m2 = ml.CoarseBDDC(ref, nsub, g, "card", sub)
+        r = np.random.default_rng(4).standard_normal(ref.n_coarse)
+        x, y = m2.apply(r), m2.apply_definition(r)
+        assert np.abs(x - y).max() <= 1e-12 * np.abs(x).max()
+        M = np.array([m2.apply(e) for e in np.eye(ref.n_coarse)]).T
+        e = np.linalg.eigvals(M @ m2.Ac).real
+        assert e.min() >= 1 - 1e-10
+        ev[sub] = (m2.ncc, e.max())
+    assert ev[1][0] > ev[0][0] and ev[1][1] <= ev[0][1] * (1 + 1e-10)
