@@ -97,7 +97,7 @@ def test_weights_partition_of_unity():
         assert np.abs(tot - 1).max() < 1e-13
 
 
-@pytest.mark.parametrize("name", ["uniform", "ragged"])
+@pytest.mark.parametrize("name", ["rho"])
 def test_level2_subobjects(name):
     """Sub-blocks of one subdomain inside the blocks (subobjects on the coarse
     level, Section 6): the two forms still agree, lambda_min(M2 A_c) >= 1, and
