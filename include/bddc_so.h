@@ -110,6 +110,7 @@ typedef struct {
     int maxit;      /* PCG iteration limit (<= 0: 2000)                               */
     int beta_rule;  /* BDDC_BETA_STANDARD (0) or BDDC_BETA_FLEXIBLE (below)          */
     int ml_block;   /* 0: exact coarse solve; g >= 1: multilevel BDDC-SO (below)     */
+    int ml_sub;     /* multilevel: sub-block width s for level-2 subobjects (0: none) */
 } bddc_options;
 
 /* Multilevel BDDC-SO (Section 6: the multilevel version removes the coarse
@@ -122,7 +123,12 @@ typedef struct {
  * level-2 objects by the set of blocks sharing them (one constraint each: the
  * mean of the object's coarse values), with weights 1 / (blocks sharing the
  * DOF) (BDDC_W_CARD) or diagonal stiffness scaling, the coarse-level analogue
- * of Remark 1 (BDDC_W_RHO), and an exact level-2 coarse solve.  All of it FP64.  B stays SPD;
+ * of Remark 1 (BDDC_W_RHO), and an exact level-2 coarse solve (by fronts of a
+ * nested dissection of the block grid).  ml_sub = s >= 1 puts subobjects on
+ * the coarse level, as Section 6 suggests: every block is cut into sub-blocks
+ * of s x s x s subdomains and the level-2 objects group the interface coarse
+ * DOFs by the set of sub-blocks sharing them (more level-2 coarse DOFs, fewer
+ * PCG iterations).  All of it FP64.  B stays SPD;
  * the PCG iteration count grows (the condition number gains the coarse
  * level's factor) while the coarse set-up and solve shrink.  Its work
  * vectors are allocated at setup, so the allocation-free apply takes it too. */

@@ -46,7 +46,7 @@ class Partition(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("weights", C.c_int), ("L_elems", C.c_int),
                 ("selection", C.c_int), ("use_graph", C.c_int), ("maxit", C.c_int), ("beta_rule", C.c_int),
-                ("ml_block", C.c_int)]
+                ("ml_block", C.c_int), ("ml_sub", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -151,7 +151,7 @@ def _stream() -> C.c_void_p:
 
 
 def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection="vef", beta="standard",
-             piece=None, ml_block=0):
+             piece=None, ml_block=0, ml_sub=0):
     mesh = Mesh(nx, ny, nz, h)
     part = Partition()
     keep = []
@@ -170,7 +170,7 @@ def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selec
     wts = {"card": BDDC_W_CARD, "rho": BDDC_W_RHO}[weights] if isinstance(weights, str) else weights
     sel = SELECTIONS[selection] if isinstance(selection, str) else selection
     opt = Options(prec, wts, L, sel, int(use_graph), maxit, BETA_RULES[beta] if isinstance(beta, str) else beta,
-                  int(ml_block))
+                  int(ml_block), int(ml_sub))
     return mesh, part, opt, keep
 
 
@@ -212,13 +212,13 @@ class BDDC:
     def __init__(self, nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int,
                  alpha: torch.Tensor, h: float = 0.0, precision="fp64", weights="card",
                  maxit: int = 2000, use_graph: bool = False, selection="vef", beta="standard", piece=None,
-                 ml_block: int = 0):
+                 ml_block: int = 0, ml_sub: int = 0):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.h = h if h > 0 else 1.0 / nx
         self.n_nodes = (nx + 1) * (ny + 1) * (nz + 1)
         self.maxit = maxit
         mesh, part, opt, keep = _structs(nx, ny, nz, self.h, cuts, L, precision, weights, maxit, use_graph,
-                                         selection, beta, piece=piece, ml_block=ml_block)
+                                         selection, beta, piece=piece, ml_block=ml_block, ml_sub=ml_sub)
         self._handle = C.c_void_p()
         _check(lib.bddc_setup(C.byref(mesh), C.byref(part), C.byref(opt), _vptr(alpha, nx * ny * nz), _stream(),
                               C.byref(self._handle)), None)
@@ -325,11 +325,11 @@ class BDDC:
 
 def solve_host(nx, ny, nz, cuts, L, alpha: np.ndarray, b: np.ndarray, rtol: float, h: float = 0.0,
                precision="fp64", weights="card", maxit: int = 2000, use_graph: bool = False,
-               selection="vef", piece=None, ml_block: int = 0):
+               selection="vef", piece=None, ml_block: int = 0, ml_sub: int = 0):
     """bddc_solve_host: setup + PCG from host arrays, result in a host array."""
     h = h if h > 0 else 1.0 / nx
     mesh, part, opt, keep = _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selection,
-                                     piece=piece, ml_block=ml_block)
+                                     piece=piece, ml_block=ml_block, ml_sub=ml_sub)
     a = np.ascontiguousarray(alpha, dtype=np.float64)
     bb = np.ascontiguousarray(b, dtype=np.float64)
     if a.size != nx * ny * nz or bb.size != (nx + 1) * (ny + 1) * (nz + 1):

@@ -1086,7 +1086,7 @@ void do_setup(bddc_handle* h, const double* alpha_dev, cudaStream_t st) {
   if (h->opt.ml_block > 0) {
     // multilevel: the coarse problem gets BDDC on blocks of subdomains
     const int nsub3[3] = {(int)h->ax[0].slab_lo.size(), (int)h->ax[1].slab_lo.size(), (int)h->ax[2].slab_lo.size()};
-    ml_plan(h->ml, h->opt.ml_block, nsub3, h->subs, h->lc, nc, h->h_cptr, h->h_cent);
+    ml_plan(h->ml, h->opt.ml_block, h->opt.ml_sub, nsub3, h->subs, h->lc, nc, h->h_cptr, h->h_cent);
     CK(cudaEventRecord(ev[5], st));
     ml_setup(h->ml, L, [h](size_t b) { return h->dalloc(b); }, [h](size_t b) { return h->dalloc(b, true); },
              h->opt.weights == BDDC_W_RHO, h->err, st);
@@ -1432,6 +1432,8 @@ std::unique_ptr<bddc_handle> make_handle(const bddc_mesh* mesh, const bddc_parti
   if (opt->beta_rule != BDDC_BETA_STANDARD && opt->beta_rule != BDDC_BETA_FLEXIBLE)
     throw BddcError(BDDC_ERR_ARG, "bad beta_rule");
   if (opt->ml_block < 0) throw BddcError(BDDC_ERR_ARG, "ml_block must be >= 0");
+  if (opt->ml_sub < 0 || (opt->ml_sub > 0 && opt->ml_block == 0))
+    throw BddcError(BDDC_ERR_ARG, "ml_sub must be >= 0, and needs ml_block");
   if (opt->selection < BDDC_SEL_VEF || opt->selection > BDDC_SEL_EF)
     throw BddcError(BDDC_ERR_ARG, "bad selection");
   std::unique_ptr<bddc_handle> h(new bddc_handle());

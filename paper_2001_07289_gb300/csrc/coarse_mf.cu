@@ -452,6 +452,23 @@ __global__ void k_mf_assemble(MFDev d, const SubDesc* __restrict__ subs, const L
   }
 }
 
+// Dense local matrices added into the fronts: item list[blockIdx.x] has an
+// m x m row-major matrix at vals + moff[item] on the global ids
+// gidmap[goff[item] ..]; the items of one launch share no global id.
+__global__ void k_mf_add_local(MFDev d, const int* __restrict__ list, const int* __restrict__ goff,
+                               const int* __restrict__ msz, const long long* __restrict__ moff,
+                               const int* __restrict__ gidmap, const double* __restrict__ vals) {
+  const int it = list[blockIdx.x], m = msz[it];
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < m * m; e += gridDim.y * blockDim.x) {
+    const int ga = gidmap[goff[it] + e / m], gb = gidmap[goff[it] + e % m];
+    const int f = d.fr[d.ord[ga] <= d.ord[gb] ? ga : gb];
+    const int ra = mf_pos(d, f, ga), rb = mf_pos(d, f, gb);
+    if (ra < 0 || rb < 0) continue;
+    const long long F = d.np[f] + d.nu[f];
+    d.F[d.foff[f] + ra * F + rb] += vals[moff[it] + e];
+  }
+}
+
 // child update matrices (lower triangle) into the parents; one launch per slot
 __global__ void k_mf_extend_add(MFDev d, const int* __restrict__ kids) {
   const int c = kids[blockIdx.x];
@@ -909,6 +926,14 @@ void mf_assemble(const MFPlan& P, const LocalLaunch& L, const int* color_subs, c
     k_mf_assemble<<<dim3(color_count_host[c], 16), BDDC_THREADS, 0, st>>>(d, L.subs, L.lc,
                                                                           color_subs + color_offset_host[c], L.Ac);
   }
+}
+
+void mf_add_local(const MFPlan& P, const int* list, int nitems, const int* goff, const int* msz,
+                  const long long* moff, const int* gidmap, const double* vals, cudaStream_t st) {
+  if (P.nfront == 0 || nitems == 0) return;
+  MFDev d = dev_of(P);
+  BDDC_COUNT(1);
+  k_mf_add_local<<<dim3(nitems, 16), BDDC_THREADS, 0, st>>>(d, list, goff, msz, moff, gidmap, vals);
 }
 
 static void CK_MF(cudaError_t e) {

@@ -210,6 +210,10 @@ void stage_h2d(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 void mf_plan(MFPlan& P, const CoarseGeom& g, int nc);
 void mf_plan_independent(MFPlan& P, const std::vector<int>& sizes);
+// dense local matrices (m x m row-major, global ids per item) into the
+// fronts; the listed items share no global id
+void mf_add_local(const MFPlan& P, const int* list, int nitems, const int* goff, const int* msz,
+                  const long long* moff, const int* gidmap, const double* vals, cudaStream_t st);
 // alloc: memory kept for the solves; tmp_alloc: memory needed during setup only
 void mf_upload(MFPlan& P, const std::function<void*(size_t)>& alloc,
                const std::function<void*(size_t)>& tmp_alloc, cudaStream_t st);
@@ -231,9 +235,12 @@ void configure_mf_kernels();
 // (w2s): 1 / (blocks sharing the DOF) or diagonal stiffness scaling.  Dense FP64 throughout, on independent multifrontal
 // fronts: N, the blocks' augmented matrices A_k + rho_k C_k^T C_k (exact for
 // the constrained problems, C_k w being prescribed); D, the blocks' interior
-// matrices; C, the level-2 coarse matrix.
+// matrices; C, the level-2 coarse matrix, by fronts of a nested dissection
+// of the block grid.  With sub-blocks of `sub` subdomains inside the blocks
+// (BDDC-SO on the coarse level), level-2 objects group the Gamma_2 DOFs by
+// the set of sub-blocks sharing them.
 struct MLPlan {
-  int g = 0, nblock = 0, nc = 0, ncc = 0, NB = 0, NI = 0, NO = 0, maxm = 0;
+  int g = 0, sub = 0, nblock = 0, nc = 0, ncc = 0, NB = 0, NI = 0, NO = 0, maxm = 0;
   // host: per block its block-space offset and size, interior offset and
   // size, object-slot offset and count; its subdomains and colour
   std::vector<int> boff, bn, ioff, bni, ooff, bm, bsub_ptr, bsub, bcolor;
@@ -266,8 +273,8 @@ struct MLPlan {
   double flops = 0;                   // factorisation multiply-adds of the three plans
 };
 
-void ml_plan(MLPlan& P, int g, const int nsub[3], const std::vector<SubDesc>& subs, const std::vector<LocalCoarse>& lc,
-             int nc, const std::vector<int>& cptr, const std::vector<int2>& cent);
+void ml_plan(MLPlan& P, int g, int sub, const int nsub[3], const std::vector<SubDesc>& subs,
+             const std::vector<LocalCoarse>& lc, int nc, const std::vector<int>& cptr, const std::vector<int2>& cent);
 void ml_setup(MLPlan& P, const LocalLaunch& L, const std::function<void*(size_t)>& alloc,
               const std::function<void*(size_t)>& tmp_alloc, int stiffness, int* err, cudaStream_t st);
 void ml_apply(const MLPlan& P, const LocalLaunch& L, const int* cptr, const int2* cent, const double* rc, double* uc,

@@ -44,19 +44,23 @@ T* up(const std::vector<T>& v, const std::function<void*(size_t)>& alloc, cudaSt
 // ---------------------------------------------------------------------------
 // host plan
 // ---------------------------------------------------------------------------
-void ml_plan(MLPlan& P, int g, const int nsub[3], const std::vector<SubDesc>& subs, const std::vector<LocalCoarse>& lc,
-             int nc, const std::vector<int>& cptr, const std::vector<int2>& cent) {
+void ml_plan(MLPlan& P, int g, int sub, const int nsub[3], const std::vector<SubDesc>& subs,
+             const std::vector<LocalCoarse>& lc, int nc, const std::vector<int>& cptr, const std::vector<int2>& cent) {
   P = MLPlan();
   P.g = g;
+  P.sub = sub;
   P.nc = nc;
   const int nb[3] = {(nsub[0] + g - 1) / g, (nsub[1] + g - 1) / g, (nsub[2] + g - 1) / g};
   const int NBk = nb[0] * nb[1] * nb[2];
   P.nblock = NBk;
   const int S = (int)subs.size();
-  std::vector<int> bos(S);
+  std::vector<int> bos(S), pos_(S);
+  const int nsb = sub > 0 ? (g + sub - 1) / sub : 1;   // sub-blocks per block and axis
   for (int si = 0; si < S; ++si) {
     const int sx = si % nsub[0], sy = (si / nsub[0]) % nsub[1], sz = si / (nsub[0] * nsub[1]);
     bos[si] = sx / g + nb[0] * (sy / g + nb[1] * (sz / g));
+    const int local = sub > 0 ? ((sx % g) / sub + nsb * ((sy % g) / sub + nsb * ((sz % g) / sub))) : 0;
+    pos_[si] = bos[si] * nsb * nsb * nsb + local;    // sub-block id
   }
   P.bsub_ptr.assign(NBk + 1, 0);
   for (int si = 0; si < S; ++si) ++P.bsub_ptr[bos[si] + 1];
@@ -71,12 +75,17 @@ void ml_plan(MLPlan& P, int g, const int nsub[3], const std::vector<SubDesc>& su
     const int bx = k % nb[0], by = (k / nb[0]) % nb[1], bz = k / (nb[0] * nb[1]);
     P.bcolor[k] = (bx & 1) + 2 * (by & 1) + 4 * (bz & 1);
   }
-  // blocks sharing each coarse DOF (ascending)
-  std::vector<std::vector<int>> bl(nc);
+  // blocks and sub-blocks sharing each coarse DOF (ascending)
+  std::vector<std::vector<int>> bl(nc), pl(nc);
   for (int j = 0; j < nc; ++j) {
-    for (int e = cptr[j]; e < cptr[j + 1]; ++e) bl[j].push_back(bos[cent[e].x]);
-    std::sort(bl[j].begin(), bl[j].end());
-    bl[j].erase(std::unique(bl[j].begin(), bl[j].end()), bl[j].end());
+    for (int e = cptr[j]; e < cptr[j + 1]; ++e) {
+      bl[j].push_back(bos[cent[e].x]);
+      pl[j].push_back(pos_[cent[e].x]);
+    }
+    for (auto* v : {&bl[j], &pl[j]}) {
+      std::sort(v->begin(), v->end());
+      v->erase(std::unique(v->begin(), v->end()), v->end());
+    }
   }
   P.gam2.assign(nc, 0);
   P.w2.assign(nc, 1.0);
@@ -133,14 +142,15 @@ void ml_plan(MLPlan& P, int g, const int nsub[3], const std::vector<SubDesc>& su
     P.ioff[k + 1] = P.ioff[k] + P.bni[k];
   }
   P.NI = P.ioff[NBk];
-  // level-2 objects: Gamma_2 DOFs by block set, numbered by first DOF
+  // level-2 objects: Gamma_2 DOFs by sub-block set (the block set without
+  // sub-blocks), numbered by first DOF
   std::map<std::vector<int>, int> sets;
   std::vector<std::vector<int>> odofs, oblk;
   for (int j = 0; j < nc; ++j) {
     if (!P.gam2[j]) continue;
-    auto it = sets.find(bl[j]);
+    auto it = sets.find(pl[j]);
     if (it == sets.end()) {
-      it = sets.emplace(bl[j], (int)odofs.size()).first;
+      it = sets.emplace(pl[j], (int)odofs.size()).first;
       odofs.emplace_back();
       oblk.push_back(bl[j]);
     }
@@ -189,7 +199,33 @@ void ml_plan(MLPlan& P, int g, const int nsub[3], const std::vector<SubDesc>& su
   }
   mf_plan_independent(P.N, P.bn);
   mf_plan_independent(P.D, P.bni);
-  if (P.ncc > 0) mf_plan_independent(P.C, std::vector<int>{P.ncc});
+  if (P.ncc > 0) {
+    // level-2 coarse: nested dissection of the block grid; an object's cell
+    // follows from its block set (2b + 1 inside block b, 2b on the plane of
+    // blocks b - 1 and b)
+    CoarseGeom G;
+    int n3[3];
+    for (int d = 0; d < 3; ++d) { G.nsub[d] = nb[d]; n3[d] = 2 * nb[d] + 1; }
+    const long long ncell = (long long)n3[0] * n3[1] * n3[2];
+    std::vector<long long> cellid(P.ncc);
+    for (int q = 0; q < P.ncc; ++q) {
+      int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+      for (int k : oblk[q]) {
+        const int c[3] = {k % nb[0], (k / nb[0]) % nb[1], k / (nb[0] * nb[1])};
+        for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], c[d]); hi[d] = std::max(hi[d], c[d]); }
+      }
+      int cc[3];
+      for (int d = 0; d < 3; ++d) cc[d] = lo[d] == hi[d] ? 2 * lo[d] + 1 : 2 * hi[d];
+      cellid[q] = cc[0] + (long long)n3[0] * (cc[1] + (long long)n3[1] * cc[2]);
+    }
+    G.cell_ptr.assign(ncell + 1, 0);
+    for (int q = 0; q < P.ncc; ++q) ++G.cell_ptr[cellid[q] + 1];
+    for (long long c = 0; c < ncell; ++c) G.cell_ptr[c + 1] += G.cell_ptr[c];
+    G.cell_obj.assign(P.ncc, 0);
+    std::vector<int> fill(G.cell_ptr.begin(), G.cell_ptr.end() - 1);
+    for (int q = 0; q < P.ncc; ++q) G.cell_obj[fill[cellid[q]]++] = q;
+    mf_plan(P.C, G, P.ncc);
+  }
   P.flops = P.N.flops + P.D.flops + P.C.flops;
   // blocks by colour
   P.color_off.assign(9, 0);
@@ -338,19 +374,6 @@ k_ml_schur(const int* __restrict__ boff, const int* __restrict__ bn, const int* 
     double s = 0.0;
     for (int r = 0; r < m; ++r) s += X[(long long)r * NB + b0 + p] * S[r * m + c];
     Psi[(long long)c * NB + b0 + p] = s;
-  }
-}
-
-// level-2 coarse matrix, one colour of blocks per launch (blocks of one
-// colour share no object): sum of S_k^{-1} - rho_k I over the blocks
-__global__ void k_ml_cc_assemble(const int* __restrict__ list, const int* __restrict__ ooff,
-                                 const int* __restrict__ bm, const int* __restrict__ oobj,
-                                 const long long* __restrict__ accoff, const double* __restrict__ Acck, int ncc,
-                                 double* __restrict__ FC) {
-  const int k = list[blockIdx.x], m = bm[k];
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int q1 = oobj[ooff[k] + e / m], q2 = oobj[ooff[k] + e % m];
-    FC[(long long)q1 * ncc + q2] += Acck[accoff[k] + e];
   }
 }
 
@@ -534,12 +557,10 @@ void ml_setup(MLPlan& P, const LocalLaunch& L, const std::function<void*(size_t)
                                              P.d_accoff, P.rho, P.X, (int)NB, Sw, Lw, Dg, P.Acck, P.Psi, err);
   }
   if (P.ncc > 0) {
-    for (int c = 0; c < 8; ++c) {
-      if (!P.color_cnt[c]) continue;
-      BDDC_COUNT(1);
-      k_ml_cc_assemble<<<P.color_cnt[c], BDDC_THREADS, 0, st>>>(P.d_bcolor_list + P.color_off[c], P.d_ooff, P.d_bm,
-                                                                P.d_oobj, P.d_accoff, P.Acck, P.ncc, P.C.F);
-    }
+    // S_k^{-1} - rho_k I into the level-2 fronts, one colour of blocks at a time
+    for (int c = 0; c < 8; ++c)
+      mf_add_local(P.C, P.d_bcolor_list + P.color_off[c], P.color_cnt[c], P.d_ooff, P.d_bm, P.d_accoff, P.d_oobj,
+                   P.Acck, st);
     mf_factor(P.C, err, st, nullptr, nullptr, nullptr);
   }
   // apply work vectors

@@ -102,3 +102,38 @@ def test_multilevel_with_other_sub_partitions(sel, piece):
     res = orc.pcg(ref.operator, lambda v: ref.apply(v, coarse=m2.apply), p.b, p.rtol)
     assert st["converged"] and abs(st["iterations"] - res.iterations) <= 1
     assert np.linalg.norm(x.cpu().numpy() - res.x) <= 1e-10 * np.linalg.norm(res.x)
+
+
+@pytest.mark.parametrize("dims,cuts,nsub,g,sub", [
+    ((16, 16, 16), [[4, 8, 12]] * 3, (4, 4, 4), 2, 1),        # 2^3 blocks of 2^3 single-subdomain sub-blocks
+    ((18, 18, 18), [[3, 6, 9, 12, 15]] * 3, (6, 6, 6), 2, 0),  # 3^3 blocks: a nested-dissection tree at level 2
+    ((18, 18, 18), [[3, 6, 9, 12, 15]] * 3, (6, 6, 6), 3, 2),  # ragged sub-blocks (2 + 1 per block and axis)
+])
+def test_multilevel_subobjects_match_oracle(dims, cuts, nsub, g, sub):
+    """Level-2 subobjects (ml_sub = s: level-2 objects split by the sets of
+    s^3 sub-blocks sharing them, Section 6) and level-2 coarse problems
+    factored by fronts of a nested dissection of the block grid: FP64 apply
+    and PCG against the oracle's three-level preconditioner."""
+    nx, ny, nz = dims
+    a = inputs.alpha_loguniform(nx, ny, nz, -1, 1, 9)
+    p = inputs.box_problem(nx, ny, nz, cuts, 2, alpha=a, rtol=1e-10)
+    ref = orc.build(p)
+    m2 = ml.CoarseBDDC(ref, nsub, g, "card", sub=sub)
+    pre = BDDC.from_problem(p, precision="fp64", ml_block=g, ml_sub=sub)
+    info = pre.info()
+    assert (info["ml_blocks"], info["ml_coarse2"]) == (m2.nblock, m2.ncc)
+    r = inputs.random_node_vector(nx, ny, nz, 6)
+    z = pre.apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    want = ref.apply(r, coarse=m2.apply)
+    assert np.abs(z - want).max() <= 1e-10 * np.abs(want).max()
+    x, st = pre.solve(torch.from_numpy(p.b).cuda(), p.rtol)
+    pre.close()
+    res = orc.pcg(ref.operator, lambda v: ref.apply(v, coarse=m2.apply), p.b, p.rtol)
+    assert st["converged"] and abs(st["iterations"] - res.iterations) <= 1
+    assert np.linalg.norm(x.cpu().numpy() - res.x) <= 1e-10 * np.linalg.norm(res.x)
+
+
+def test_ml_sub_needs_ml_block():
+    p = inputs.box_problem(8, 8, 8, [[4]] * 3, 2)
+    with pytest.raises(RuntimeError, match="ml_sub"):
+        BDDC.from_problem(p, ml_sub=1)
