@@ -543,11 +543,19 @@ k_mf_trsm(MFDev d, const int4* __restrict__ tab, int nfr, int j) {
     D[r * (FNB + 1) + c] = (r < nj && c < nj) ? Dg[r * FNB + c] : 0.0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < ni * nj; e += blockDim.x) {
-    int r = e / nj, c = e % nj;
+  // lanes along the rows, one output column per warp at a time, so that the
+  // triangular loop (k <= c) has the same length in every lane of a warp;
+  // warp w takes the columns w, 15 - w, 16 + w, 31 - w (66 multiply-adds)
+  static_assert(FNB == 32 && BDDC_THREADS == 256, "column split for 32-wide tiles and 8 warps");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cols[4] = {warp, 15 - warp, 16 + warp, 31 - warp};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = cols[q];
+    if (c >= nj) continue;
     double s = 0.0;
-    for (int k = 0; k <= c; ++k) s = fma(T[r * (FNB + 1) + k], D[c * (FNB + 1) + k], s);
-    A[(ri + r) * F + rj + c] = s;
+    for (int k = 0; k <= c; ++k) s = fma(T[lane * (FNB + 1) + k], D[c * (FNB + 1) + k], s);
+    if (lane < ni) A[(ri + lane) * F + rj + c] = s;
   }
 }
 

@@ -214,95 +214,135 @@ __device__ void tile_inv(const T* L, T* X, int n, T* rdiag) {
 }
 
 // FP64 Cholesky and inverse of an n x n (n <= 32) tile in registers of
-// warps 0-3, one warp per SM sub-partition (FP64 runs at a small fraction of
-// the FP32 rate and a warp instruction costs the same with one lane or 32):
-// lane i holds row i, warp w the columns j = w + 4m (m < 8).  Step c: the
-// owner of column c + 1 first applies column c to it and takes its pivot
-// (reciprocal square root), so that the chain of pivots runs one warp ahead
-// of the remaining updates; one barrier per column.  The inverse then runs
-// by columns, each warp on its own eight columns of X = L^{-1} with no
-// barrier: Y[i][j] -= (L[i][k] / L[k][k]) Y[k][j] (row k of Y from lane k),
-// X[i][j] = Y[i][j] / L[i][i].  In: t0 lower triangle of S (ld TLD).  Out: t0
-// = L (zeros above), X (full, zeros above the diagonal).  Uses sm.lv, sm.r2
-// (the published column, double-buffered), sm.t2 (L[i][k] / L[k][k] by k),
-// sm.rd.  A non-positive pivot sets sm.flag and is replaced by 1.
+// warps 0-3, one warp per SM sub-partition (FP64 issue costs about the same
+// per warp instruction whether one lane or 32 are active, so each FP64
+// instruction on the pivot chain counts): lane i holds row i, warp w the
+// columns j = w + 4m (m < 8) of the factor (a) and of the inverse (y).
+// Columns are published through shared memory with two counters instead of
+// a barrier per column: when column k of L is out, the owner of column k + 1
+// applies it to that column, takes the pivot (reciprocal square root) and
+// publishes column k + 1 at once; only then does it, like the other warps,
+// apply column k to its remaining columns and take the inverse's step k:
+// Y[i][j] -= (L[i][k] / L[k][k]) Y[k][j] (row k of Y from lane k), with
+// X[i][j] = Y[i][j] / L[i][i] at the end.  The chain of pivots thus waits on
+// one multiply-add per column, not on the slowest warp's whole step.  The
+// operations per entry and their order are those of the plain right-looking
+// algorithm.  In: t0 lower triangle of S (ld TLD).  Out: t0 = L (zeros
+// above), X (full, zeros above the diagonal).  Uses sm.As (columns of L, ld
+// 32), sm.t2 (L[i][k] / L[k][k] by k, ld 32), sm.rd, sm.r2 (the two
+// counters).  A non-positive pivot, or a publication wait that runs past its
+// bound, sets sm.flag (the pivot is replaced by 1).
 __device__ inline void tile_chol_inv_f64(double* t0, double* X, int n, DenseSmem<double>& sm) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool act = warp < 4;
-  double a[8];
-  if (act) {
+  double* colL = &sm.As[0][0];
+  double* colT = sm.t2;
+  volatile int* pubL = reinterpret_cast<volatile int*>(sm.r2);
+  volatile int* pubT = pubL + 1;
+  if (threadIdx.x == 0) { pubL[0] = 0; pubT[0] = 0; }
+  __syncthreads();
+  if (warp < 4 && n > 0) {
+    double a[8], y[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int j = warp + 4 * m;
-      a[m] = (lane < n && j < n) ? (j <= lane ? t0[lane * TLD + j] : 0.0) : (lane == j ? 1.0 : 0.0);
+      a[m] = (lane < n && j < n && j <= lane) ? t0[lane * TLD + j] : 0.0;
+      y[m] = (lane == j) ? 1.0 : 0.0;
     }
-  }
-  // column c of the calling warp, held in a[m] with c = warp + 4m: pivot,
-  // scale, publish
-  auto pivot = [&](int c, double col) -> double {
-    double d = __shfl_sync(0xffffffffu, col, c);
-    if (!(d > 0.0)) {
-      if (lane == 0) sm.flag = 1;
-      d = 1.0;
-    }
-    const double rl = rsqrt(d);
-    const double l = (lane == c) ? d * rl : (lane > c ? col * rl : 0.0);
-    double* pub = (c & 1) ? sm.r2 : sm.lv;
-    pub[lane] = l;
-    sm.t2[c * TLD + lane] = (lane > c) ? l * rl : 0.0;
-    if (lane == 0) sm.rd[c] = rl;
-    return l;
-  };
-  if (warp == 0 && n > 0) a[0] = pivot(0, a[0]);
-  __syncthreads();
-  for (int c = 0; c < n; ++c) {
-    if (act) {
-      const double* lc = (c & 1) ? sm.r2 : sm.lv;
-      const double li = lc[lane];
-      const int cn = c + 1;
-      const bool owner = cn < n && warp == (cn & 3);
+    // waits (all lanes) until counter p reaches v; bounded
+    auto wait_for = [&](volatile int* p, int v) {
+      long long tries = 0;
+      while (*p < v) {
+        if (++tries > (1LL << 24)) {
+          sm.flag = 1;
+          break;
+        }
+      }
+      __threadfence_block();
+    };
+    // pivot of column c, held in col by this warp: publishes L's column c,
+    // then L[i][c] / L[c][c] and 1 / L[c][c]; returns the L column
+    auto pivot = [&](int c, double col) -> double {
+      double d = __shfl_sync(0xffffffffu, col, c);
+      const long long bits = __double_as_longlong(d);
+      if (!(bits > 0 && bits < 0x7ff0000000000000LL)) {   // not a positive finite number
+        if (lane == 0) sm.flag = 1;
+        d = 1.0;
+        col = (lane == c) ? 1.0 : col;
+      }
+      const double rl = rsqrt(d);
+      const double l = (lane >= c) ? col * rl : 0.0;
+      colL[c * 32 + lane] = l;
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) *pubL = c + 1;
+      colT[c * 32 + lane] = (lane > c) ? l * rl : 0.0;
+      if (lane == 0) sm.rd[c] = rl;
+      __threadfence_block();
+      __syncwarp();
+      wait_for(pubT, c);   // the counters only grow: column c - 1 first
+      if (lane == 0) *pubT = c + 1;
+      return l;
+    };
+    if (warp == 0) a[0] = pivot(0, a[0]);
+    for (int k = 0; k < n; ++k) {
+      wait_for(pubL, k + 1);
+      const double lk = colL[k * 32 + lane];
+      const int cn = k + 1;
+      const bool owner = cn < n && (cn & 3) == warp;
       if (owner) {
-        // the column by selects (an indexed register array would go to
-        // local memory)
         const int mm = cn >> 2;
         double col = a[0];
 #pragma unroll
         for (int m = 1; m < 8; ++m) col = (m == mm) ? a[m] : col;
-        col = pivot(cn, fma(-li, lc[cn], col));
+        col = pivot(cn, fma(-lk, colL[k * 32 + cn], col));
 #pragma unroll
         for (int m = 0; m < 8; ++m) a[m] = (m == mm) ? col : a[m];
       }
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int j = warp + 4 * m;
-        if (j > c && j < n && !(owner && j == cn)) a[m] = fma(-li, lc[j], a[m]);
+      // column k on this warp's columns j > k (minus the pivot column just
+      // taken), and the inverse's step k on its columns j <= k.  An FP64
+      // instruction whose predicate is off still costs its issue slot, so
+      // the ranges are entered by a jump (switch with fall-through) instead
+      // of predicating all eight.  Columns j >= n hold zeros and stay zero.
+      const int m0 = (k >= warp) ? ((k - warp) >> 2) + 1 : 0;   // first column j > k
+#define BDDC_FSTEP(m) a[m] = fma(-lk, colL[k * 32 + warp + 4 * (m)], a[m])
+      switch (owner ? m0 + 1 : m0) {
+        case 0: BDDC_FSTEP(0); [[fallthrough]];
+        case 1: BDDC_FSTEP(1); [[fallthrough]];
+        case 2: BDDC_FSTEP(2); [[fallthrough]];
+        case 3: BDDC_FSTEP(3); [[fallthrough]];
+        case 4: BDDC_FSTEP(4); [[fallthrough]];
+        case 5: BDDC_FSTEP(5); [[fallthrough]];
+        case 6: BDDC_FSTEP(6); [[fallthrough]];
+        case 7: BDDC_FSTEP(7); [[fallthrough]];
+        default: break;
+      }
+#undef BDDC_FSTEP
+      if (k + 1 < n) {
+        wait_for(pubT, k + 1);
+        const double lt = colT[k * 32 + lane];   // zero for lane <= k
+#define BDDC_ISTEP(m) y[m] = fma(-lt, __shfl_sync(0xffffffffu, y[m], k), y[m])
+        switch (m0) {
+          case 8: BDDC_ISTEP(7); [[fallthrough]];
+          case 7: BDDC_ISTEP(6); [[fallthrough]];
+          case 6: BDDC_ISTEP(5); [[fallthrough]];
+          case 5: BDDC_ISTEP(4); [[fallthrough]];
+          case 4: BDDC_ISTEP(3); [[fallthrough]];
+          case 3: BDDC_ISTEP(2); [[fallthrough]];
+          case 2: BDDC_ISTEP(1); [[fallthrough]];
+          case 1: BDDC_ISTEP(0); [[fallthrough]];
+          default: break;
+        }
+#undef BDDC_ISTEP
       }
     }
-    __syncthreads();
-  }
-  if (act) {
-    // L back to t0; the inverse by columns
+    wait_for(pubT, n);
+    const double ri = (lane < n) ? sm.rd[lane] : 0.0;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int j = warp + 4 * m;
       t0[lane * TLD + j] = (lane < n && j <= lane) ? a[m] : 0.0;
+      X[lane * TLD + j] = y[m] * ri;
     }
-    double y[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) y[m] = (lane == warp + 4 * m) ? 1.0 : 0.0;
-    for (int k = 0; k + 1 < n; ++k) {
-      const double lt = sm.t2[k * TLD + lane];   // zero for lane <= k
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        if (warp + 4 * m <= k) {
-          const double yk = __shfl_sync(0xffffffffu, y[m], k);
-          y[m] = fma(-lt, yk, y[m]);
-        }
-      }
-    }
-    const double ri = (lane < n) ? sm.rd[lane] : 0.0;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) X[lane * TLD + warp + 4 * m] = y[m] * ri;
   }
   __syncthreads();
 }
