@@ -47,6 +47,15 @@ __host__ __device__ inline void mf_tile(int t, int np, int nu, int& r0, int& nr)
   else { int u = t - npt; r0 = np + u * FNB; nr = min(FNB, nu - u * FNB); }
 }
 
+// Programmatic dependent launch of the panel-step chain: a kernel's CTAs may
+// be scheduled while the previous kernel in the stream finishes; they wait
+// here for its completion (and its memory) before reading anything, then
+// allow the next kernel to be scheduled in turn.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 // ---------------------------------------------------------------------------
 // symbolic analysis (host)
 // ---------------------------------------------------------------------------
@@ -471,6 +480,7 @@ __global__ void k_mf_add_local(MFDev d, const int* __restrict__ list, const int*
 
 // child update matrices (lower triangle) into the parents; one launch per slot
 __global__ void k_mf_extend_add(MFDev d, const int* __restrict__ kids) {
+  pdl_enter();
   const int c = kids[blockIdx.x];
   const int p = d.parent[c];
   const int npc = d.np[c], nuc = d.nu[c];
@@ -508,6 +518,7 @@ __device__ inline int mf_find_front(const int4* __restrict__ tab, int n, int b, 
 
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_potrf(MFDev d, const int4* __restrict__ tab, double* scratch, int* err) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char smraw[];
   DenseSmem<double>& sm = *reinterpret_cast<DenseSmem<double>*>(smraw);
   const int f = tab[blockIdx.x].x, j = 0;   // the first panel of each front
@@ -525,6 +536,7 @@ k_mf_potrf(MFDev d, const int4* __restrict__ tab, double* scratch, int* err) {
 // A[i,j] <- A[i,j] Dinv_j^T (tile in shared memory)
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_trsm(MFDev d, const int4* __restrict__ tab, int nfr, int j) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char smraw[];
   double* T = reinterpret_cast<double*>(smraw);       // FNB x (FNB+1)
   double* D = T + FNB * (FNB + 1);                    // FNB x (FNB+1)
@@ -566,6 +578,7 @@ k_mf_trsm(MFDev d, const int4* __restrict__ tab, int nfr, int j) {
 // next panel's trsm does not wait for a separate potrf launch.
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_syrk(MFDev d, const int4* __restrict__ tab, int nfr, int j, double* pscratch, int* err) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ double As[32 * 33], Bs[32 * 33];
   const int4 fe = tab[mf_find_front(tab, nfr, (int)blockIdx.x, true)];
@@ -948,6 +961,22 @@ static void CK_MF(cudaError_t e) {
   if (e != cudaSuccess) throw std::runtime_error(std::string("coarse factor: ") + cudaGetErrorString(e));
 }
 
+// launch with programmatic stream serialisation (the kernel starts with pdl_enter)
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(BDDC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CK_MF(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
+
 // Solve matrices of the fronts of one level: Linv_P by tile rows (diagonal
 // inverses, then the doubling steps), then G = L_UP Linv_P.  They read only
 // the level's own factor, final once its last panel step is done.
@@ -978,7 +1007,7 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cud
       const int a = P.slot_off[(size_t)l * P.maxslot + s], b = P.slot_off[(size_t)l * P.maxslot + s + 1];
       if (b > a) {
         BDDC_COUNT(1);
-        k_mf_extend_add<<<dim3(b - a, 32), BDDC_THREADS, 0, st>>>(d, slots + a);
+        launch_pdl(k_mf_extend_add, dim3(b - a, 32), 0, st, d, slots + a);
       }
     }
     int maxpt = 0;
@@ -988,9 +1017,9 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cud
       const int4* tab = P.d_lists + P.step_off[step];
       // the first panel's diagonal tiles of the level; later ones are
       // factored inside the previous step's syrk (look-ahead)
-      if (nfr && j == 0) { BDDC_COUNT(1); k_mf_potrf<<<nfr, BDDC_THREADS, dsm, st>>>(d, tab, P.pscratch, err); }
-      if (ntr) { BDDC_COUNT(1); k_mf_trsm<<<ntr, BDDC_THREADS, tsm, st>>>(d, tab, nfr, j); }
-      if (nsy) { BDDC_COUNT(1); k_mf_syrk<<<nsy, BDDC_THREADS, dsm, st>>>(d, tab, nfr, j, P.fscratch, err); }
+      if (nfr && j == 0) { BDDC_COUNT(1); launch_pdl(k_mf_potrf, dim3(nfr), dsm, st, d, tab, P.pscratch, err); }
+      if (ntr) { BDDC_COUNT(1); launch_pdl(k_mf_trsm, dim3(ntr), tsm, st, d, tab, nfr, j); }
+      if (nsy) { BDDC_COUNT(1); launch_pdl(k_mf_syrk, dim3(nsy), dsm, st, d, tab, nfr, j, P.fscratch, err); }
     }
     if (two) {
       CK_MF(cudaEventRecord(fork, st));
