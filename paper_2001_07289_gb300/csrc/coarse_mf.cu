@@ -47,15 +47,6 @@ __host__ __device__ inline void mf_tile(int t, int np, int nu, int& r0, int& nr)
   else { int u = t - npt; r0 = np + u * FNB; nr = min(FNB, nu - u * FNB); }
 }
 
-// Programmatic dependent launch of the panel-step chain: a kernel's CTAs may
-// be scheduled while the previous kernel in the stream finishes; they wait
-// here for its completion (and its memory) before reading anything, then
-// allow the next kernel to be scheduled in turn.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" :::);
-}
-
 // ---------------------------------------------------------------------------
 // symbolic analysis (host)
 // ---------------------------------------------------------------------------
@@ -619,6 +610,7 @@ __device__ inline double mf_wsum(double v) {
 // X_ts = -Dinv_t sum_{k=s}^{t-1} L_tk X_ks) and G = L_UP X.
 // ---------------------------------------------------------------------------
 __global__ void k_mf_inv_diag(MFDev d, const int4* __restrict__ work) {
+  pdl_enter();
   const int4 w = work[blockIdx.x];
   const int f = w.x, t = w.y;
   const int np = d.np[f];
@@ -638,6 +630,7 @@ __global__ void k_mf_inv_diag(MFDev d, const int4* __restrict__ work) {
 //   mode 1: sum_k X[r][k] T[k][c]   (X_CA = -X_CC T)
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_trtri_part(MFDev d, const int4* __restrict__ work, int mode, double* __restrict__ part) {
+  pdl_enter();
   __shared__ double As[32 * 33], Bs[32 * 33];
   const int4 w = work[blockIdx.x];
   const int f = w.x, r = w.y, c = w.z, k = w.w & 0xffff, kt = w.w >> 16;
@@ -661,6 +654,7 @@ k_mf_trtri_part(MFDev d, const int4* __restrict__ work, int mode, double* __rest
 // r << 16 | c, first product, count}: mode 0 into T, mode 1 (negated) into X.
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_trtri_sum(MFDev d, const int4* __restrict__ work, int mode, const double* __restrict__ part) {
+  pdl_enter();
   const int4 w = work[blockIdx.x];
   const int f = w.x, r = w.y >> 16, c = w.y & 0xffff;
   const int np = d.np[f];
@@ -677,6 +671,7 @@ k_mf_trtri_sum(MFDev d, const int4* __restrict__ work, int mode, const double* _
 
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_g(MFDev d, const int4* __restrict__ work) {
+  pdl_enter();
   __shared__ double As[32 * 33], Bs[32 * 33];
   const int4 w = work[blockIdx.x];
   const int f = w.x, ut = w.y, st = w.z;
@@ -694,6 +689,7 @@ k_mf_g(MFDev d, const int4* __restrict__ work) {
 // S_f^T for the backward solve, 32 x 32 tiles through shared memory;
 // grid (front, tile stride)
 __global__ void k_mf_transpose(MFDev d) {
+  pdl_enter();
   __shared__ double t[32][33];
   const int f = blockIdx.x;
   const int np = d.np[f], F = np + d.nu[f];
@@ -735,6 +731,7 @@ __device__ inline double mf_row_dot(const double* __restrict__ row, const double
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_fwd(MFDev d, const int2* __restrict__ items, const int* __restrict__ kid_ptr, const int* __restrict__ kid_list,
          const int* __restrict__ lvl_index, const double* __restrict__ b) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char smraw[];
   double* w = reinterpret_cast<double*>(smraw);
   const int2 it = items[blockIdx.x];
@@ -763,6 +760,7 @@ k_mf_fwd(MFDev d, const int2* __restrict__ items, const int* __restrict__ kid_pt
 // of S_f^T against [y_P; x_U]
 __global__ void __launch_bounds__(BDDC_THREADS)
 k_mf_bwd(MFDev d, const int2* __restrict__ items, double* x) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char smraw[];
   double* vec = reinterpret_cast<double*>(smraw);        // [y_P; x_U]
   const int2 it = items[blockIdx.x];
@@ -961,20 +959,11 @@ static void CK_MF(cudaError_t e) {
   if (e != cudaSuccess) throw std::runtime_error(std::string("coarse factor: ") + cudaGetErrorString(e));
 }
 
-// launch with programmatic stream serialisation (the kernel starts with pdl_enter)
+// the kernels of the panel-step chain and of the solves start with
+// pdl_enter(): launched with programmatic stream serialisation
 template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(BDDC_THREADS);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  CK_MF(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+static void launch_mf(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+  CK_MF(launch_pdl(kern, grid, dim3(BDDC_THREADS), smem, st, args...));
 }
 
 // Solve matrices of the fronts of one level: Linv_P by tile rows (diagonal
@@ -982,16 +971,16 @@ static void launch_pdl(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStrea
 // the level's own factor, final once its last panel step is done.
 static void mf_solve_matrices(const MFPlan& P, const MFDev& d, int l, cudaStream_t st) {
   const int b = P.inv_lvl_base[l], e = P.inv_lvl_base[l + 1];
-  if (P.inv_len[b]) { BDDC_COUNT(1); k_mf_inv_diag<<<P.inv_len[b], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[b]); }
+  if (P.inv_len[b]) { BDDC_COUNT(1); launch_mf(k_mf_inv_diag, dim3(P.inv_len[b]), 0, st, d, P.d_lists + P.inv_off[b]); }
   for (int q = b + 2; q + 3 < e; q += 4)
     for (int mode = 0; mode < 2; ++mode) {
       const int lp = q + 2 * mode, ls = lp + 1;
       if (!P.inv_len[lp]) continue;
       BDDC_COUNT(2);
-      k_mf_trtri_part<<<P.inv_len[lp], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[lp], mode, P.tpart);
-      k_mf_trtri_sum<<<P.inv_len[ls], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[ls], mode, P.tpart);
+      launch_mf(k_mf_trtri_part, dim3(P.inv_len[lp]), 0, st, d, P.d_lists + P.inv_off[lp], mode, P.tpart);
+      launch_mf(k_mf_trtri_sum, dim3(P.inv_len[ls]), 0, st, d, P.d_lists + P.inv_off[ls], mode, (const double*)P.tpart);
     }
-  if (P.inv_len[b + 1]) { BDDC_COUNT(1); k_mf_g<<<P.inv_len[b + 1], BDDC_THREADS, 0, st>>>(d, P.d_lists + P.inv_off[b + 1]); }
+  if (P.inv_len[b + 1]) { BDDC_COUNT(1); launch_mf(k_mf_g, dim3(P.inv_len[b + 1]), 0, st, d, P.d_lists + P.inv_off[b + 1]); }
 }
 
 void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join) {
@@ -1007,7 +996,7 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cud
       const int a = P.slot_off[(size_t)l * P.maxslot + s], b = P.slot_off[(size_t)l * P.maxslot + s + 1];
       if (b > a) {
         BDDC_COUNT(1);
-        launch_pdl(k_mf_extend_add, dim3(b - a, 32), 0, st, d, slots + a);
+        launch_mf(k_mf_extend_add, dim3(b - a, 32), 0, st, d, slots + a);
       }
     }
     int maxpt = 0;
@@ -1017,9 +1006,9 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cud
       const int4* tab = P.d_lists + P.step_off[step];
       // the first panel's diagonal tiles of the level; later ones are
       // factored inside the previous step's syrk (look-ahead)
-      if (nfr && j == 0) { BDDC_COUNT(1); launch_pdl(k_mf_potrf, dim3(nfr), dsm, st, d, tab, P.pscratch, err); }
-      if (ntr) { BDDC_COUNT(1); launch_pdl(k_mf_trsm, dim3(ntr), tsm, st, d, tab, nfr, j); }
-      if (nsy) { BDDC_COUNT(1); launch_pdl(k_mf_syrk, dim3(nsy), dsm, st, d, tab, nfr, j, P.fscratch, err); }
+      if (nfr && j == 0) { BDDC_COUNT(1); launch_mf(k_mf_potrf, dim3(nfr), dsm, st, d, tab, P.pscratch, err); }
+      if (ntr) { BDDC_COUNT(1); launch_mf(k_mf_trsm, dim3(ntr), tsm, st, d, tab, nfr, j); }
+      if (nsy) { BDDC_COUNT(1); launch_mf(k_mf_syrk, dim3(nsy), dsm, st, d, tab, nfr, j, P.fscratch, err); }
     }
     if (two) {
       CK_MF(cudaEventRecord(fork, st));
@@ -1032,7 +1021,7 @@ void mf_factor(const MFPlan& P, int* err, cudaStream_t st, cudaStream_t aux, cud
     CK_MF(cudaStreamWaitEvent(st, join, 0));
   }
   BDDC_COUNT(1);
-  k_mf_transpose<<<dim3(P.nfront, 16), BDDC_THREADS, 0, st>>>(d);
+  launch_mf(k_mf_transpose, dim3(P.nfront, 16), 0, st, d);
 }
 
 void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream_t st) {
@@ -1046,11 +1035,11 @@ void mf_solve(const MFPlan& P, const double* b, double* x, double* W, cudaStream
   const size_t sm = sizeof(double) * (size_t)P.maxF;
   for (int l = P.nlevel - 1; l >= 0; --l) {
     BDDC_COUNT(1);
-    k_mf_fwd<<<P.fwd_items_len[l], BDDC_THREADS, sm, st>>>(d, items + P.fwd_items_off[l], kptr, klist, lidx, b);
+    launch_mf(k_mf_fwd, dim3(P.fwd_items_len[l]), sm, st, d, items + P.fwd_items_off[l], kptr, klist, lidx, b);
   }
   for (int l = 0; l < P.nlevel; ++l) {
     BDDC_COUNT(1);
-    k_mf_bwd<<<P.bwd_items_len[l], BDDC_THREADS, sm, st>>>(d, items + P.bwd_items_off[l], x);
+    launch_mf(k_mf_bwd, dim3(P.bwd_items_len[l]), sm, st, d, items + P.bwd_items_off[l], x);
   }
 }
 

@@ -20,6 +20,16 @@
 
 namespace bddc {
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may have its CTAs scheduled while the previous kernel of the
+// stream finishes; they wait here for its completion (and its memory) before
+// reading anything, then let the next kernel be scheduled in turn.  Without
+// that launch attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 struct SubDesc {
   int id;             // index of the subdomain (x fastest over the box grid)
   int e0[3];          // element origin of the box

@@ -12,6 +12,23 @@ namespace bddc {
 extern long long g_launches;
 #define BDDC_COUNT(n) (::bddc::g_launches += (n))
 
+// Launch with programmatic stream serialisation, for kernels that start with
+// pdl_enter(): the launch overlaps the previous kernel's tail.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 constexpr int CW = 64;       // RHS columns per CTA in the multi-RHS sweeps
 
 // A size bucket of the apply's per-subdomain kernels: its descriptors in

@@ -1393,6 +1393,7 @@ __global__ void __launch_bounds__(APPLY_THREADS)
 k_dirichlet_solve(ApplyBucket B, MeshDev m, const T* __restrict__ fac, const double* __restrict__ r,
                   const double* __restrict__ t, double* __restrict__ z, int mode, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
+  pdl_enter();
   // clusters of one or two CTAs (the launch decides), one subdomain at a time
   const int csz = (int)cg::this_cluster().num_blocks();
   Ring ring = ring_at(smraw, B.nb);
@@ -1451,6 +1452,7 @@ __global__ void __launch_bounds__(APPLY_THREADS)
 k_neumann_rhs(ApplyBucket B, MeshDev m, const T* __restrict__ Phi, const double* __restrict__ delta,
               const double* __restrict__ r, const double* __restrict__ t, double* __restrict__ rcl, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
+  pdl_enter();
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank(), nrank = (int)cluster.num_blocks();
   Ring ring = ring_at(smraw, B.nb);
@@ -1504,6 +1506,7 @@ __global__ void __launch_bounds__(APPLY_THREADS)
 k_neumann_solve(ApplyBucket B, MeshDev m, const T* __restrict__ fac, const double* __restrict__ delta,
                 const double* __restrict__ r, const double* __restrict__ t, T* __restrict__ vloc, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
+  pdl_enter();
   // clusters of one or two CTAs (the launch decides), one subdomain at a time
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank(), csz = (int)cluster.num_blocks();
@@ -1538,6 +1541,7 @@ k_neumann_finish(ApplyBucket B, const LocalCoarse* __restrict__ lc, const int* _
                  const T* __restrict__ PhiT, const T* __restrict__ vloc, const double* __restrict__ uc,
                  double* __restrict__ vgam, int* err) {
   extern __shared__ __align__(128) unsigned char smraw[];
+  pdl_enter();
   Ring ring = ring_at(smraw, B.nb);
   T* part = reinterpret_cast<T*>(smraw + ring_bytes(B.nb));
   T* ut = part + APPLY_THREADS;
@@ -1768,13 +1772,17 @@ void launch_clustered(void (*kern)(KArgs...), const ApplyBucket& b, int csize, s
   cfg.blockDim = dim3(APPLY_THREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)csize;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  // the apply kernels start with pdl_enter(): the launch overlaps the
+  // previous kernel's tail
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 

@@ -39,6 +39,7 @@ __device__ inline void block_partial(double v, double* partial) {
 __global__ void __launch_bounds__(256)
 k_operator(MeshDev m, const double* __restrict__ alpha, const double* __restrict__ x, double* __restrict__ y,
            double* __restrict__ dot_partial) {
+  pdl_enter();
   const long long N = (long long)m.NX * m.NY * m.NZ;
   const long long sx = 1, sy = m.NX, sz = (long long)m.NX * m.NY;
   double dot = 0.0;
@@ -86,7 +87,7 @@ k_operator(MeshDev m, const double* __restrict__ alpha, const double* __restrict
 void launch_operator(const MeshDev& m, const double* alpha, const double* x, double* y, double* dot_partial,
                      int nblocks, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_operator<<<nblocks, 256, 0, st>>>(m, alpha, x, y, dot_partial);
+  launch_pdl(k_operator, dim3(nblocks), dim3(256), 0, st, m, alpha, x, y, dot_partial);
 }
 
 // g_e = -h * lambda_e^T K u_e  (the derivative of J(u(alpha)) in alpha_e when
@@ -132,6 +133,7 @@ void launch_gradient(const MeshDev& m, const double* u, const double* lam, doubl
 // follow from the per-axis slab tables, so the sum order is fixed.
 __global__ void k_interface_gather(MeshDev m, const SubDesc* __restrict__ subs, const double* __restrict__ delta,
                                    const double* __restrict__ vgam, double* __restrict__ z) {
+  pdl_enter();
   const long long N = (long long)m.NX * m.NY * m.NZ;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N;
        g += (long long)gridDim.x * blockDim.x) {
@@ -162,7 +164,7 @@ void launch_interface_gather(const MeshDev& m, const SubDesc* subs, const double
   long long N = (long long)m.NX * m.NY * m.NZ;
   int blocks = (int)std::min<long long>((N + 255) / 256, 152 * 16);
   BDDC_COUNT(1);
-  k_interface_gather<<<blocks, 256, 0, st>>>(m, subs, delta, vgam, z);
+  launch_pdl(k_interface_gather, dim3(blocks), dim3(256), 0, st, m, subs, delta, vgam, z);
 }
 
 __global__ void k_check_alpha(const double* __restrict__ a, long long n, int* err) {
