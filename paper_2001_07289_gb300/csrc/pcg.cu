@@ -29,6 +29,7 @@ __device__ inline void block_partial_p(double v, double* partial) {
 
 __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, long long n,
                       double* __restrict__ partial) {
+  pdl_enter();
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     s = fma(a[i], b[i], s);
@@ -37,13 +38,14 @@ __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b
 
 void launch_dot(const double* a, const double* b, long long n, double* partial, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_dot<<<RED_BLOCKS, 256, 0, st>>>(a, b, n, partial);
+  launch_pdl(k_dot, dim3(RED_BLOCKS), dim3(256), 0, st, a, b, n, partial);
 }
 
 // r.z and r.zp in one pass: partials of the first in partial[0, RED_BLOCKS),
 // of the second in partial[RED_BLOCKS, 2 RED_BLOCKS)
 __global__ void k_dot2(const double* __restrict__ r, const double* __restrict__ z, const double* __restrict__ zp,
                        long long n, double* __restrict__ partial) {
+  pdl_enter();
   double s = 0.0, t = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double ri = r[i];
@@ -57,7 +59,7 @@ __global__ void k_dot2(const double* __restrict__ r, const double* __restrict__ 
 
 void launch_dot2(const double* r, const double* z, const double* zp, long long n, double* partial, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_dot2<<<RED_BLOCKS, 256, 0, st>>>(r, z, zp, n, partial);
+  launch_pdl(k_dot2, dim3(RED_BLOCKS), dim3(256), 0, st, r, z, zp, n, partial);
 }
 
 // One block sums the partials in a fixed order and updates the CG scalars and
@@ -90,6 +92,7 @@ __device__ inline double fixed_order_sum(const double* __restrict__ partial, dou
 
 __global__ void k_finalize(const double* __restrict__ partial, double* scal, int op, double* hist, int* ctl,
                            int maxit, double rtol, cudaGraphConditionalHandle cond, int use_cond) {
+  pdl_enter();
   __shared__ double ws[32];
   const double s = fixed_order_sum(partial, ws);
   // op 5: the second sum, r_{k+1}.z_k
@@ -163,23 +166,26 @@ __global__ void k_finalize(const double* __restrict__ partial, double* scal, int
 void launch_finalize(const double* partial, double* scal, int op, double* hist, int* ctl, int maxit, double rtol,
                      const cudaGraphConditionalHandle* cond, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_finalize<<<1, 256, 0, st>>>(partial, scal, op, hist, ctl, maxit, rtol, cond ? *cond : 0, cond ? 1 : 0);
+  launch_pdl(k_finalize, dim3(1), dim3(256), 0, st, partial, scal, op, hist, ctl, maxit, rtol,
+             cond ? *cond : (cudaGraphConditionalHandle)0, cond ? 1 : 0);
 }
 
 // Sets the condition of a graph's while node from ctl[1] (the continue flag).
 __global__ void k_loop_condition(const int* ctl, cudaGraphConditionalHandle cond) {
+  pdl_enter();
   if (threadIdx.x == 0) cudaGraphSetConditional(cond, ctl[1] ? 1u : 0u);
 }
 
 void launch_loop_condition(const int* ctl, cudaGraphConditionalHandle cond, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_loop_condition<<<1, 32, 0, st>>>(ctl, cond);
+  launch_pdl(k_loop_condition, dim3(1), dim3(32), 0, st, ctl, cond);
 }
 
 // x += alpha p; r -= alpha q; partials of r.r
 __global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
                             const double* __restrict__ q, const double* __restrict__ scal, long long n,
                             double* __restrict__ partial) {
+  pdl_enter();
   const double a = scal[2];
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -194,12 +200,13 @@ __global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r, cons
 void launch_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, long long n,
                       double* partial, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_update_xr<<<RED_BLOCKS, 256, 0, st>>>(x, r, p, q, scal, n, partial);
+  launch_pdl(k_update_xr, dim3(RED_BLOCKS), dim3(256), 0, st, x, r, p, q, scal, n, partial);
 }
 
 // p = z + beta p
 __global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ scal,
                            long long n) {
+  pdl_enter();
   const double b = scal[5];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     p[i] = fma(b, p[i], z[i]);
@@ -207,12 +214,13 @@ __global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z,
 
 void launch_update_p(double* p, const double* z, const double* scal, long long n, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_update_p<<<RED_BLOCKS, 256, 0, st>>>(p, z, scal, n);
+  launch_pdl(k_update_p, dim3(RED_BLOCKS), dim3(256), 0, st, p, z, scal, n);
 }
 
 // p = z + beta p and zp = z (the flexible recurrence keeps the last z)
 __global__ void k_update_p_keep(double* __restrict__ p, double* __restrict__ zp, const double* __restrict__ z,
                                 const double* __restrict__ scal, long long n) {
+  pdl_enter();
   const double b = scal[5];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double zi = z[i];
@@ -223,7 +231,7 @@ __global__ void k_update_p_keep(double* __restrict__ p, double* __restrict__ zp,
 
 void launch_update_p_keep(double* p, double* zp, const double* z, const double* scal, long long n, cudaStream_t st) {
   BDDC_COUNT(1);
-  k_update_p_keep<<<RED_BLOCKS, 256, 0, st>>>(p, zp, z, scal, n);
+  launch_pdl(k_update_p_keep, dim3(RED_BLOCKS), dim3(256), 0, st, p, zp, z, scal, n);
 }
 
 }  // namespace bddc
