@@ -803,7 +803,7 @@ void tune_factor(bddc_handle* h, cudaStream_t st) {
   cudaEvent_t e[4];
   for (auto& x : e) CK(cudaEventCreate(&x));
   for (int v = 0; v < 2; ++v) {
-    launch_assemble<float>(L, st);
+    launch_assemble<float>(L, 1 - v, st);
     CK(cudaEventRecord(e[2 * v], st));
     launch_factor<float>(L, 1 - v, st);
     CK(cudaEventRecord(e[2 * v + 1], st));

@@ -125,6 +125,25 @@ __device__ inline Grid grid_of(const SubDesc& s, int neumann) {
   return g;
 }
 
+// In-plane stencil taps of the plane blocks D_k for the tensor-core
+// factorisation (FP32 path): nine values per node, tap o = (dx + 1) + 3 (dy + 1)
+// of node a at o Q + a, plane k after k 9Q values, in the subdomain's
+// factorisation scratch (Neumann part first, then Dirichlet, as the CUDA-core
+// sweep lays it out).  Used when the subdomain goes to the tensor-core kernel
+// (tc, planes of at most maxq nodes in both problems), its Neumann matrix
+// carries no augmented-Lagrangian term (dense in the plane) and the taps fit
+// the scratch part; off receives the part's first entry.
+__device__ inline bool plane_taps(const SubDesc& s, int neumann, int tc, int maxq, long long* off) {
+  const Grid gN = grid_of(s, 1), gD = grid_of(s, 0);
+  const long long QN = (long long)gN.gx * gN.gy, QD = (long long)gD.gx * gD.gy;
+  const long long partN = 2 * QN * QN + 1024 * ((max((int)QN, s.na) + 31) / 32);
+  const long long partD = 2 * QD * QD + 1024 * ((QD + 31) / 32);
+  *off = s.offW + (neumann ? 0 : partN);
+  const Grid& g = neumann ? gN : gD;
+  const long long taps = 9LL * g.gx * g.gy * g.gz;
+  return tc && QN <= maxq && QD <= maxq && !(neumann && s.pin) && taps <= (neumann ? partN : partD);
+}
+
 // First device-side failure wins: error code and the subdomain (or front) id.
 __device__ inline void set_error(int* err, int code, int sub) {
   if (atomicCAS(err, 0, code) == 0) err[1] = sub;

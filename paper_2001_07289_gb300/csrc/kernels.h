@@ -105,7 +105,9 @@ void configure_schur_tc();
 void launch_schur_tc(const LocalLaunch& L, const FactorBucket& B, cudaStream_t st);
 // assembly of the local plane blocks; the factorisations of every bucket
 // (tc: bucket 0 on the tensor cores)
-template <typename T> void launch_assemble(const LocalLaunch& L, cudaStream_t st);
+// tc: the factorisation that follows runs on the tensor cores (FP32 path):
+// D_k of its subdomains as in-plane taps (plane_taps)
+template <typename T> void launch_assemble(const LocalLaunch& L, int tc, cudaStream_t st);
 template <typename T> void launch_factor(const LocalLaunch& L, int tc, cudaStream_t st);
 
 // ev (may be null): 3 events recorded after the Dirichlet factorisation, the

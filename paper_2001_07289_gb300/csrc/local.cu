@@ -123,32 +123,38 @@ __global__ void k_pin_penalty(const SubDesc* __restrict__ subs, MeshDev m, const
   }
 }
 
+// D_k as a dense Q x Q block in slot k, or (tc, see plane_taps) as its nine
+// in-plane taps per node in the factorisation scratch; B_k as nine taps per
+// node in slot nz + k - 1.
 template <typename T>
 __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const double* __restrict__ alpha,
                            T* __restrict__ fac, int neumann, const LocalCoarse* __restrict__ lc,
-                           const int* __restrict__ own, const double* __restrict__ pen) {
+                           const int* __restrict__ own, const double* __restrict__ pen, T* __restrict__ scratch,
+                           int tc) {
   const SubDesc s = subs[blockIdx.x];
   const Grid g = grid_of(s, neumann);
   const int k = blockIdx.y;
   if (k >= g.gz) return;
   const int Q = g.gx * g.gy;
   T* base = fac + (neumann ? s.offN : s.offD);
+  long long toff = 0;
+  const bool taps = plane_taps(s, neumann, tc, TCS_MAXQ, &toff);
   // a plane block has Q^2 + 9Q < 2^31 entries: 32-bit index arithmetic
-  const int QQ = Q * Q;
+  const int nd = taps ? 9 * Q : Q * Q;
   const long long SS = slot_stride(Q);
   const int n1 = (k > 0) ? 9 * Q : 0;
-  for (int e = (int)(blockIdx.z * blockDim.x + threadIdx.x); e < QQ + n1; e += (int)(gridDim.z * blockDim.x)) {
+  for (int e = (int)(blockIdx.z * blockDim.x + threadIdx.x); e < nd + n1; e += (int)(gridDim.z * blockDim.x)) {
     int a, bx, by, bz, dx, dy;
-    if (e < QQ) {
+    if (e < nd && !taps) {
       a = e / Q;
       const int b = e % Q;
       bx = b % g.gx; by = b / g.gx; bz = k;
       dx = bx - a % g.gx; dy = by - a / g.gx;
     } else {
-      const int o = (e - QQ) / Q;
-      a = (e - QQ) % Q;
+      const int o = (e < nd ? e : e - nd) / Q;
+      a = (e < nd ? e : e - nd) % Q;
       dx = o % 3 - 1; dy = o / 3 - 1;
-      bx = a % g.gx + dx; by = a / g.gx + dy; bz = k - 1;
+      bx = a % g.gx + dx; by = a / g.gx + dy; bz = e < nd ? k : k - 1;
     }
     const int ax = a % g.gx, ay = a / g.gx, dz = bz - k;
     double v = 0.0;
@@ -160,15 +166,16 @@ __global__ void k_assemble(const SubDesc* __restrict__ subs, MeshDev m, const do
                          dx, dy, dz);
     }
     // pinned floating subdomain: rho_k c_k^T c_k of the rows of this plane (see k_pin_penalty)
-    if (neumann && s.pin && e < QQ) {
+    if (neumann && s.pin && e < nd) {
       const int ja = own[s.offVec + (long long)k * Q + a], jb = own[s.offVec + (long long)k * Q + (e % Q)];
       if (ja >= 0 && ja == jb) {
         const double cnt = (double)lc[s.cofs + ja].count;
         v += pen[s.cofs + ja] / (cnt * cnt);
       }
     }
-    if (e < QQ) base[(long long)k * SS + e] = (T)v;
-    else base[(long long)(g.gz + k - 1) * SS + (e - QQ)] = (T)v;
+    if (e >= nd) base[(long long)(g.gz + k - 1) * SS + (e - nd)] = (T)v;
+    else if (taps) scratch[toff + 9LL * Q * k + e] = (T)v;
+    else base[(long long)k * SS + e] = (T)v;
   }
 }
 
@@ -1598,8 +1605,16 @@ size_t dense_smem() { return sizeof(DenseSmem<T>); }
 // one subdomain's assembled local matrix, Neumann or Dirichlet, so that its
 // factorisation meets a non-positive pivot.  One thread.
 template <typename T>
-__global__ void k_debug_negate(const SubDesc* __restrict__ subs, T* __restrict__ fac, int sub, int neumann) {
+__global__ void k_debug_negate(const SubDesc* __restrict__ subs, T* __restrict__ fac, int sub, int neumann,
+                               T* __restrict__ scratch, int tc) {
   const SubDesc s = subs[sub];
+  long long toff = 0;
+  if (plane_taps(s, neumann, tc, TCS_MAXQ, &toff)) {
+    const Grid g = grid_of(s, neumann);
+    T* c = scratch + toff + 4LL * g.gx * g.gy;   // centre tap of node 0, plane 0
+    *c = -*c;
+    return;
+  }
   T* base = fac + (neumann ? s.offN : s.offD);
   base[0] = -base[0];
 }
@@ -1609,22 +1624,25 @@ void set_wait_report_tries(long long tries) {
 }
 
 template <typename T>
-void launch_assemble(const LocalLaunch& L, cudaStream_t st) {
+void launch_assemble(const LocalLaunch& L, int tc, cudaStream_t st) {
   const int S = L.nsub;
-  T* facD = (T*)L.facD; T* facN = (T*)L.facN;
+  T* facD = (T*)L.facD; T* facN = (T*)L.facN; T* W = (T*)L.scratch;
+  tc = (tc && std::is_same<T, float>::value) ? 1 : 0;   // the tensor-core factorisation reads plane taps
   // local assembly (Dirichlet and Neumann plane blocks)
   if (L.maxQD > 0) {
-    k_assemble<T><<<dim3(S, L.maxNzD, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facD, 0, L.lc, L.own, L.pen);
+    k_assemble<T><<<dim3(S, L.maxNzD, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facD, 0, L.lc, L.own, L.pen,
+                                                                 W, tc);
     BDDC_COUNT(1);
   }
   if (L.npin) {
     k_pin_penalty<<<S, BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, L.lc, L.lcn, L.pen);
     BDDC_COUNT(1);
   }
-  k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1, L.lc, L.own, L.pen);
+  k_assemble<T><<<dim3(S, L.maxNzN, 8), BDDC_THREADS, 0, st>>>(L.subs, L.m, L.alpha, facN, 1, L.lc, L.own, L.pen,
+                                                               W, tc);
   BDDC_COUNT(1);
   if (L.negate_sub >= 0) {
-    k_debug_negate<T><<<1, 1, 0, st>>>(L.subs, L.negate_neumann ? facN : facD, L.negate_sub, L.negate_neumann);
+    k_debug_negate<T><<<1, 1, 0, st>>>(L.subs, L.negate_neumann ? facN : facD, L.negate_sub, L.negate_neumann, W, tc);
     BDDC_COUNT(1);
   }
 }
@@ -1657,7 +1675,7 @@ void launch_setup_local(const LocalLaunch& L, cudaStream_t st, cudaEvent_t* ev) 
   const int S = L.nsub;
   T* facN = (T*)L.facN; T* W = (T*)L.scratch;
   size_t sm = dense_smem<T>();
-  launch_assemble<T>(L, st);
+  launch_assemble<T>(L, L.factor_tc, st);
   if (ev) cudaEventRecord(ev[0], st);
   launch_factor<T>(L, L.factor_tc, st);
   if (ev) cudaEventRecord(ev[1], st);
@@ -1842,7 +1860,7 @@ void launch_neumann_finish(const LocalLaunch& L, const double* uc, cudaStream_t 
 }
 
 template void launch_setup_local<float>(const LocalLaunch&, cudaStream_t, cudaEvent_t*);
-template void launch_assemble<float>(const LocalLaunch&, cudaStream_t);
+template void launch_assemble<float>(const LocalLaunch&, int, cudaStream_t);
 template void launch_factor<float>(const LocalLaunch&, int, cudaStream_t);
 template void launch_setup_local<double>(const LocalLaunch&, cudaStream_t, cudaEvent_t*);
 template void configure_local_kernels<float>();

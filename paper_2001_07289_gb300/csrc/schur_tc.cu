@@ -92,12 +92,15 @@ __device__ inline void bar_arrive(int id, int n) { asm volatile("bar.arrive %0, 
 size_t schur_tc_smem(int) { return TCS_END; }
 
 __global__ void __launch_bounds__(TCS_THREADS, 1)
-k_btschur_tc(const SubDesc* __restrict__ subs, float* __restrict__ facN, float* __restrict__ facD, int* err) {
+k_btschur_tc(const SubDesc* __restrict__ subs, float* __restrict__ facN, float* __restrict__ facD,
+             const float* __restrict__ scratch, int* err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   const SubDesc s = subs[blockIdx.x];
   const int neumann = blockIdx.y == 0;
   const Grid g = grid_of(s, neumann);
   if (g.gz == 0) return;
+  long long toff = 0;
+  const bool taps = plane_taps(s, neumann, 1, TCS_MAXQ, &toff);   // D_k as in-plane taps (k_assemble)
   const int Q = g.gx * g.gy, gx = g.gx, gy = g.gy;
   const int Qp = (Q + 15) & ~15, TS = tcs_ts(Q), nmt = (Q + 127) / 128, nch = Qp / 16, nb = Qp / 16;
   const long long SS = slot_stride(Q);
@@ -258,10 +261,30 @@ k_btschur_tc(const SubDesc* __restrict__ subs, float* __restrict__ facN, float* 
       const int m = it / nch, cc = it % nch;
       const int i = 128 * m + 32 * q + lane;
       float v[16];
+      if (taps) {
+        // the row's nine taps land in columns i - gx - 1 .. i + gx + 1
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int j = 16 * cc + c;
-        v[c] = (i < Q && j < Q) ? slot[(long long)j * Q + i] : 0.0f;   // D_k symmetric: coalesced
+        for (int c = 0; c < 16; ++c) v[c] = 0.0f;
+        if (i < Q && 16 * cc <= i + gx + 1 && 16 * cc + 15 >= i - gx - 1) {
+          const float* Dt = scratch + toff + 9LL * Q * k;
+          const int ix = i % gx, iy = i / gx;
+#pragma unroll
+          for (int o = 0; o < 9; ++o) {
+            const int dx = o % 3 - 1, dy = o / 3 - 1;
+            if (ix + dx < 0 || ix + dx >= gx || iy + dy < 0 || iy + dy >= gy) continue;
+            const int c0 = i + dx + dy * gx - 16 * cc;
+            if (c0 < 0 || c0 >= 16) continue;
+            const float dv = Dt[o * Q + i];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = (c == c0) ? dv : v[c];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int j = 16 * cc + c;
+          v[c] = (i < Q && j < Q) ? slot[(long long)j * Q + i] : 0.0f;   // D_k symmetric: coalesced
+        }
       }
       if (k > 0 && i < Q) {
         const int ix = i % gx, iy = i / gx;
@@ -553,7 +576,7 @@ void configure_schur_tc() {
 void launch_schur_tc(const LocalLaunch& L, const FactorBucket& B, cudaStream_t st) {
   BDDC_COUNT(1);
   k_btschur_tc<<<dim3(B.count, B.maxQD > 0 ? 2 : 1), TCS_THREADS, schur_tc_smem(std::max(B.maxQN, B.maxQD)), st>>>(
-      B.subs, (float*)L.facN, (float*)L.facD, L.err);
+      B.subs, (float*)L.facN, (float*)L.facD, (const float*)L.scratch, L.err);
 }
 
 }  // namespace bddc
