@@ -441,14 +441,20 @@ __global__ void k_mf_assemble(MFDev d, const SubDesc* __restrict__ subs, const L
                               const int* __restrict__ list, const double* __restrict__ Ac) {
   const SubDesc s = subs[list[blockIdx.x]];
   const int n = s.nc;
-  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < n * n; e += gridDim.y * blockDim.x) {
-    const int a = e / n, b = e % n;
-    const int ga = lc[s.cofs + a].gid, gb = lc[s.cofs + b].gid;
-    const int f = d.fr[d.ord[ga] <= d.ord[gb] ? ga : gb];
-    const int ra = mf_pos(d, f, ga), rb = mf_pos(d, f, gb);
-    if (ra < 0 || rb < 0) continue;
-    const long long F = d.np[f] + d.nu[f];
-    d.F[d.foff[f] + ra * F + rb] += Ac[s.offAc + e];
+  // the fronts are factored from their lower triangles only: entry (a, b),
+  // b <= a, goes to the lower of its two front positions; rows over the
+  // warps, the lanes along a row
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int a = blockIdx.y * nw + warp; a < n; a += gridDim.y * nw) {
+    const int ga = lc[s.cofs + a].gid;
+    for (int b = lane; b <= a; b += 32) {
+      const int gb = lc[s.cofs + b].gid;
+      const int f = d.fr[d.ord[ga] <= d.ord[gb] ? ga : gb];
+      const int ra = mf_pos(d, f, ga), rb = mf_pos(d, f, gb);
+      if (ra < 0 || rb < 0) continue;
+      const long long F = d.np[f] + d.nu[f];
+      d.F[d.foff[f] + (long long)max(ra, rb) * F + min(ra, rb)] += Ac[s.offAc + (long long)a * n + b];
+    }
   }
 }
 
@@ -942,7 +948,7 @@ void mf_assemble(const MFPlan& P, const LocalLaunch& L, const int* color_subs, c
   for (int c = 0; c < 8; ++c) {
     if (color_count_host[c] == 0) continue;
     BDDC_COUNT(1);
-    k_mf_assemble<<<dim3(color_count_host[c], 16), BDDC_THREADS, 0, st>>>(d, L.subs, L.lc,
+    k_mf_assemble<<<dim3(color_count_host[c], 32), BDDC_THREADS, 0, st>>>(d, L.subs, L.lc,
                                                                           color_subs + color_offset_host[c], L.Ac);
   }
 }
