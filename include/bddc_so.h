@@ -210,6 +210,9 @@ typedef struct {
     int max_front;        /* largest front (pivots + update set)               */
     long long front_entries;  /* sum of squared front sizes (FP64 storage)    */
     double coarse_fma;    /* multiply-adds of the coarse factorisation         */
+    int ml_blocks;        /* multilevel (options.ml_block > 0): blocks of the coarse level, else 0 */
+    int ml_coarse2;       /* multilevel: level-2 coarse DOFs (level-2 objects)  */
+    int ml_fronts2;       /* multilevel: fronts of the level-2 coarse Cholesky  */
 } bddc_analysis_t;
 
 /* Partition, sub-partition (Section 3 remark on local subdivision), object

@@ -71,7 +71,8 @@ class Analysis(C.Structure):
     _fields_ = [("n_sub", C.c_int), ("n_coarse", C.c_int), ("n_vertices", C.c_int), ("n_edges", C.c_int),
                 ("n_faces", C.c_int), ("max_local_coarse", C.c_int), ("n_fronts", C.c_int),
                 ("n_levels", C.c_int), ("max_front", C.c_int), ("front_entries", C.c_longlong),
-                ("coarse_fma", C.c_double)]
+                ("coarse_fma", C.c_double), ("ml_blocks", C.c_int), ("ml_coarse2", C.c_int),
+                ("ml_fronts2", C.c_int)]
 
 
 class Paths(C.Structure):
@@ -175,11 +176,13 @@ def _structs(nx, ny, nz, h, cuts, L, precision, weights, maxit, use_graph, selec
 
 
 def analyze(nx: int, ny: int, nz: int, cuts: Sequence[Sequence[int]], L: int, h: float = 0.0,
-            precision="fp64", weights="card", selection="vef", piece=None) -> dict:
+            precision="fp64", weights="card", selection="vef", piece=None, ml_block: int = 0,
+            ml_sub: int = 0) -> dict:
     """bddc_analyze: host-only counts of objects and of the coarse elimination
-    plan; piece: optional per-element sub-subdomain labels (else boxes of L)."""
+    plan; piece: optional per-element sub-subdomain labels (else boxes of L);
+    ml_block / ml_sub: the level-2 sizes of the multilevel coarse level."""
     mesh, part, opt, keep = _structs(nx, ny, nz, h if h > 0 else 1.0 / nx, cuts, L, precision, weights, 2000, False,
-                                     selection, piece=piece)
+                                     selection, piece=piece, ml_block=ml_block, ml_sub=ml_sub)
     out = Analysis()
     _check(lib.bddc_analyze(C.byref(mesh), C.byref(part), C.byref(opt), C.byref(out)), None)
     return {k: getattr(out, k) for k, _ in Analysis._fields_}

@@ -1501,6 +1501,13 @@ extern "C" int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, c
   for (int f = 0; f < h->mf.nfront; ++f) out->max_front = std::max(out->max_front, h->mf.np[f] + h->mf.nu[f]);
   out->front_entries = h->mf.fpool;
   out->coarse_fma = h->mf.flops;
+  if (h->opt.ml_block > 0) {
+    const int nsub3[3] = {(int)h->ax[0].slab_lo.size(), (int)h->ax[1].slab_lo.size(), (int)h->ax[2].slab_lo.size()};
+    ml_plan(h->ml, h->opt.ml_block, h->opt.ml_sub, nsub3, h->subs, h->lc, h->n_coarse, h->h_cptr, h->h_cent);
+    out->ml_blocks = h->ml.nblock;
+    out->ml_coarse2 = h->ml.ncc;
+    out->ml_fronts2 = h->ml.C.nfront;
+  }
   return BDDC_OK;
   ABI_END(hnull)
 }
